@@ -1,0 +1,211 @@
+/*
+ * qtensor.h -- C ABI of the GB300 lightcone tensor-network QAOA library.
+ *
+ * Method: arXiv:2106.15740, "Importance of Diagonal Gates in Tensor Network
+ * Simulations".  The MaxCut energy E = sum_{(j,k)} (1 - <Z_j Z_k>)/2
+ * (§QAOA algorithm) is computed edge by edge; each <Z_j Z_k> is the full
+ * contraction of a reverse-lightcone tensor network (§QAOA algorithm,
+ * lightcone paragraph) in which diagonal gates -- the ZZ phase and the Z
+ * observable -- are tensors on the existing indices of their qubits instead of
+ * new 4-index gate tensors (§Diagonal gate simplification, eq. (example)).  The
+ * network is contracted by bucket elimination (§Tensor network contraction):
+ * for each variable in a greedy min-fill order, every tensor holding it is
+ * multiplied and the variable is summed out.
+ *
+ * Conventions.  Layer q (1..p) applies exp(-i gamma_q Z_j Z_k) on every edge
+ * and then exp(-i beta_q X) on every qubit, starting from |+>^n.  Angles are
+ * radians, float64.  Batched angle arrays are row-major [B][p].
+ *
+ * Errors.  Every call returns a qt_status; no call aborts or throws across
+ * the ABI.  On failure, qt_last_error() returns a thread-local message that
+ * stays valid until the next failing call on the same thread.  Output
+ * arguments are left untouched on failure unless stated otherwise.
+ *
+ * Ownership.  The caller owns every buffer it passes.  Handles returned by
+ * the library (qt_network, qt_plan) are owned by the caller and released with
+ * the matching *_free call.  Build calls copy the graph and the angles they
+ * are given.  Device workspace is caller-allocated memory on the current CUDA
+ * device; the library never allocates device memory on its own (plans hold
+ * their device-side descriptors in that workspace).
+ *
+ * Streams.  `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ * stream).  Calls taking device pointers are asynchronous on that stream;
+ * calls taking host pointers synchronise the stream before returning.
+ */
+#ifndef QTENSOR_H
+#define QTENSOR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  QT_OK = 0,
+  QT_EINVAL = 1,    /* invalid argument (graph, p, edge, angle, size, pointer) */
+  QT_ENOMEM = 2,    /* workspace smaller than the plan needs, or host allocation failed */
+  QT_EWIDTH = 3,    /* contraction width above the plan's width budget */
+  QT_ECUDA = 4,     /* a CUDA runtime call failed (message names it) */
+  QT_ETIMEOUT = 5,  /* a bounded device-side wait gave up; results are invalid */
+  QT_ESTATE = 6     /* call not valid in the handle's current state */
+} qt_status;
+
+typedef enum {
+  QT_C128 = 0,      /* complex128 storage and arithmetic */
+  QT_C64 = 1        /* complex64 storage, FP32 arithmetic; FP64 edge product and energy sum */
+} qt_dtype;
+
+typedef enum {
+  QT_MODE_PER_BUCKET = 0, /* one kernel launch per bucket, edges one after another */
+  QT_MODE_PERSISTENT = 1  /* one persistent launch over all (edge, bucket, tile) tasks */
+} qt_mode;
+
+/* Simple undirected graph.  edges[2*i], edges[2*i+1] are the endpoints of
+ * edge i, 0 <= u < v < n_vertices, no repeated edge.  (§QAOA algorithm: the
+ * MaxCut instance G=(V,E).) */
+typedef struct {
+  int32_t n_vertices;
+  int32_t n_edges;
+  const int32_t* edges;
+} qt_graph;
+
+typedef struct qt_network qt_network;
+typedef struct qt_plan qt_plan;
+
+/* Tensor kinds of a lightcone network (qt_network_tensor). */
+typedef enum {
+  QT_T_PLUS = 0,    /* |+> leaf [1,1]/sqrt(2) on a qubit's first variable */
+  QT_T_ZZ = 1,      /* diagonal ZZ phase exp(-i gamma_q z_a z_b) on two variables */
+  QT_T_MIX = 2,     /* mixer <new| exp(-i beta_q X) |old> on (new, old) */
+  QT_T_OBS = 3      /* observable Z: [1,-1] on a qubit's top variable */
+} qt_tensor_kind;
+
+/* Build the reverse-lightcone network of edge `edge` (0-based index into
+ * g->edges) for depth p >= 1 with angles gamma[p], beta[p] (host pointers).
+ * §QAOA algorithm (eq. (1), (2), lightcone paragraph), §Diagonal gate
+ * simplification.  Variables get canonical ids: qubits of the lightcone in
+ * ascending order; per qubit the ket variables v^0..v^m, then the bra
+ * variables w^{m-1}..w^0 (v^m is shared by ket and bra).  On success *out owns
+ * a new handle.  QT_EINVAL for a bad graph, p < 1, edge out of range,
+ * non-finite angle or NULL pointer. */
+qt_status qt_build_lightcone(const qt_graph* g, int32_t p, const double* gamma,
+                             const double* beta, int32_t edge, qt_network** out);
+
+/* Number of variables and tensors of a network. */
+qt_status qt_network_info(const qt_network* net, int32_t* n_vars, int32_t* n_tensors);
+
+/* Describe tensor t: kind (qt_tensor_kind), layer q (1..p; 0 for |+>, p for
+ * the observable), conj (1 for the bra copy), rank (1 or 2) and its variable
+ * ids vars[0..rank-1] (for QT_T_MIX: vars[0] = new, vars[1] = old). */
+qt_status qt_network_tensor(const qt_network* net, int32_t t, int32_t* kind, int32_t* layer,
+                            int32_t* conj, int32_t* rank, int32_t vars[2]);
+
+/* Greedy min-fill elimination order (§Tensor network contraction: the order
+ * sets the largest intermediate).  Repeatedly eliminates the variable with the
+ * smallest (fill-in, degree, id) in the interaction graph (a clique on each
+ * tensor's variables).  `order` must hold n_vars entries; on success *n_vars
+ * is set and *width is the largest degree at elimination (the rank of the
+ * largest bucket result, the contraction width C of §Results). */
+qt_status qt_order(const qt_network* net, int32_t* order, int32_t* n_vars, int32_t* width);
+
+/* Device workspace, in bytes, that qt_contract needs for this network and order. */
+qt_status qt_contract_workspace_size(const qt_network* net, const int32_t* order,
+                                     qt_dtype dtype, size_t* bytes);
+
+/* Contract the network on the GPU in the given order (bucket elimination,
+ * one kernel launch per bucket) and write <Z_j Z_k> to out_zz[0] (real part)
+ * and out_zz[1] (imaginary part, zero up to rounding).  `order` is a host
+ * array (a permutation of the variables).  `workspace` is device memory of at
+ * least qt_contract_workspace_size bytes, 256-byte aligned.  Synchronises
+ * `stream`.  QT_EINVAL if order is not a permutation, QT_ENOMEM if the
+ * workspace is too small. */
+qt_status qt_contract(qt_network* net, const int32_t* order, qt_dtype dtype, void* stream,
+                      void* workspace, size_t ws_bytes, double out_zz[2]);
+
+void qt_network_free(qt_network* net);
+
+/* Energy plans: every edge lightcone of a graph, planned once (structure,
+ * order, bucket descriptors, memory layout) for `batch` angle sets.  The plan
+ * depends on the graph and p only, never on the angles. */
+typedef struct {
+  int32_t batch;          /* B >= 1 angle sets per call */
+  int32_t dtype;          /* qt_dtype */
+  int32_t mode;           /* qt_mode */
+  int32_t gradient;       /* 1: plan also computes dE/dgamma, dE/dbeta (adjoint sweep) */
+  int32_t max_width;      /* width budget; an edge above it fails with QT_EWIDTH (<=0: 34) */
+  int32_t pad_;
+  int64_t max_workspace;  /* cap on workspace bytes (<=0: no cap); sets edge concurrency */
+} qt_plan_options;
+
+/* Fill `opt` with defaults: batch 1, QT_C128, QT_MODE_PER_BUCKET, no gradient. */
+void qt_plan_options_default(qt_plan_options* opt);
+
+qt_status qt_plan_create(const qt_graph* g, int32_t p, const qt_plan_options* opt, qt_plan** out);
+
+/* Workspace bytes the plan needs (device memory, 256-byte aligned base). */
+qt_status qt_plan_workspace_size(const qt_plan* plan, size_t* bytes);
+
+/* Plan statistics: number of edges, maximum width over edges, total buckets,
+ * algorithmic bytes moved by the bucket kernels per call (inputs that are
+ * intermediates and leaf factors read once, outputs written once, times B and
+ * the element size) and real FLOPs per call. */
+qt_status qt_plan_stats(const qt_plan* plan, int32_t* n_edges, int32_t* max_width,
+                        int64_t* n_buckets, double* alg_bytes, double* flops);
+
+/* Per-edge widths (n_edges entries, host array). */
+qt_status qt_plan_edge_widths(const qt_plan* plan, int32_t* widths);
+
+/* Evaluate the plan with DEVICE pointers, asynchronously on `stream`:
+ *   gamma, beta : [B][p] float64 angles
+ *   energy      : [B] float64, E = sum_e (1 - Re<Z_j Z_k>_e)/2
+ *   edge_zz     : [n_edges][B][2] float64 (re, im) per edge, or NULL
+ *   grad        : [B][2p] float64 (dE/dgamma_1..p, dE/dbeta_1..p), or NULL;
+ *                 requires a plan created with gradient = 1
+ * The workspace must stay untouched until the stream reaches the end of the
+ * call.  Errors found by the device (a timed-out wait) are reported by the
+ * next qt_plan_check call. */
+qt_status qt_plan_energy(qt_plan* plan, const double* gamma, const double* beta, double* energy,
+                         double* edge_zz, double* grad, void* workspace, size_t ws_bytes,
+                         void* stream);
+
+/* Synchronise `stream` and report a device-side failure of earlier calls on
+ * this plan (QT_ETIMEOUT) or QT_OK. */
+qt_status qt_plan_check(qt_plan* plan, void* stream);
+
+/* Same as qt_plan_energy with HOST pointers: copies the angles to the device,
+ * evaluates, copies the results back and synchronises `stream`. */
+qt_status qt_plan_energy_host(qt_plan* plan, const double* gamma, const double* beta,
+                              double* energy, double* edge_zz, double* grad, void* workspace,
+                              size_t ws_bytes, void* stream);
+
+/* Kernel timing for roofline reports.  When profiling is on, every
+ * qt_plan_energy call records a pair of CUDA events on its stream around the
+ * bucket-contraction launch(es) (not the leaf-factor or energy kernels).
+ * qt_plan_kernel_times synchronises those events and writes up to `cap`
+ * durations in milliseconds, oldest first, to ms[]; *n gets the number
+ * written; the recorded list is then cleared. */
+qt_status qt_plan_set_profiling(qt_plan* plan, int32_t on);
+qt_status qt_plan_kernel_times(qt_plan* plan, float* ms, int32_t cap, int32_t* n);
+
+void qt_plan_free(qt_plan* plan);
+
+/* One-shot energy (and gradient if grad != NULL) with HOST pointers: plans
+ * the graph for B angle sets in `dtype` (persistent mode), evaluates and
+ * frees the plan.  workspace/ws_bytes as for qt_plan_energy; the size comes
+ * from qt_energy_workspace_size with the same arguments. */
+qt_status qt_energy_workspace_size(const qt_graph* g, int32_t p, int32_t B, qt_dtype dtype,
+                                   int32_t gradient, size_t* bytes);
+qt_status qt_energy(const qt_graph* g, int32_t p, const double* gamma, const double* beta,
+                    int32_t B, qt_dtype dtype, void* stream, void* workspace, size_t ws_bytes,
+                    double* energy, double* grad);
+
+/* Thread-local message of the last failing call ("" if none). */
+const char* qt_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QTENSOR_H */

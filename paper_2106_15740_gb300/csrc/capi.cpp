@@ -1,0 +1,314 @@
+// extern "C" entry points declared in include/qtensor.h.  Argument checks,
+// handle management and error reporting; the work is in network.cpp,
+// order.cpp, buckets.cpp, engine.cpp and the CUDA kernels.
+#include <cmath>
+#include <new>
+
+#include "engine.h"
+#include "kernels_api.h"
+
+namespace qt {
+
+static thread_local std::string g_last_error;
+
+qt_status fail(qt_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+static qt_status check_angles(const double* a, int64_t n, const char* name) {
+  if (!a) return fail(QT_EINVAL, std::string(name) + " is NULL");
+  for (int64_t i = 0; i < n; ++i)
+    if (!std::isfinite(a[i])) return fail(QT_EINVAL, std::string(name) + " has a non-finite angle");
+  return QT_OK;
+}
+
+// Build, order and bucket-plan every edge network of a graph.
+static qt_status plan_edges(const Graph& G, int32_t p, int32_t max_width, Plan* P) {
+  P->edges.clear();
+  P->widths.clear();
+  for (int32_t e = 0; e < (int32_t)G.eu.size(); ++e) {
+    Network net;
+    build_lightcone(G, p, e, &net);
+    std::vector<int32_t> order;
+    const int32_t w = min_fill_order(net, &order);
+    if (w > max_width)
+      return fail(QT_EWIDTH, "edge " + std::to_string(e) + " has contraction width " + std::to_string(w) +
+                                 " above the budget " + std::to_string(max_width));
+    EdgePlan ep;
+    qt_status st = make_edge_plan(net, order, &ep);
+    if (st != QT_OK) return st;
+    P->widths.push_back(ep.width);
+    P->edges.push_back(std::move(ep));
+  }
+  return QT_OK;
+}
+
+}  // namespace qt
+
+using namespace qt;
+
+extern "C" {
+
+const char* qt_last_error(void) { return g_last_error.c_str(); }
+
+qt_status qt_build_lightcone(const qt_graph* g, int32_t p, const double* gamma, const double* beta, int32_t edge,
+                             qt_network** out) {
+  if (!out) return fail(QT_EINVAL, "out is NULL");
+  if (p < 1 || p > 64) return fail(QT_EINVAL, "p must be in [1, 64]");
+  Graph G;
+  qt_status st = make_graph(g, &G);
+  if (st != QT_OK) return st;
+  if (edge < 0 || edge >= (int32_t)G.eu.size()) return fail(QT_EINVAL, "edge index out of range");
+  if ((st = check_angles(gamma, p, "gamma")) != QT_OK) return st;
+  if ((st = check_angles(beta, p, "beta")) != QT_OK) return st;
+  qt_network* h = new (std::nothrow) qt_network;
+  if (!h) return fail(QT_ENOMEM, "host allocation failed");
+  build_lightcone(G, p, edge, &h->net);
+  h->net.gamma.assign(gamma, gamma + p);
+  h->net.beta.assign(beta, beta + p);
+  *out = h;
+  return QT_OK;
+}
+
+qt_status qt_network_info(const qt_network* net, int32_t* n_vars, int32_t* n_tensors) {
+  if (!net) return fail(QT_EINVAL, "network is NULL");
+  if (n_vars) *n_vars = net->net.n_vars;
+  if (n_tensors) *n_tensors = (int32_t)net->net.tensors.size();
+  return QT_OK;
+}
+
+qt_status qt_network_tensor(const qt_network* net, int32_t t, int32_t* kind, int32_t* layer, int32_t* conj,
+                            int32_t* rank, int32_t vars[2]) {
+  if (!net) return fail(QT_EINVAL, "network is NULL");
+  if (t < 0 || t >= (int32_t)net->net.tensors.size()) return fail(QT_EINVAL, "tensor index out of range");
+  const Tensor& T = net->net.tensors[t];
+  if (kind) *kind = T.kind;
+  if (layer) *layer = T.layer;
+  if (conj) *conj = T.conj;
+  if (rank) *rank = T.rank;
+  if (vars) {
+    vars[0] = T.v[0];
+    vars[1] = T.rank > 1 ? T.v[1] : -1;
+  }
+  return QT_OK;
+}
+
+qt_status qt_order(const qt_network* net, int32_t* order, int32_t* n_vars, int32_t* width) {
+  if (!net || !order) return fail(QT_EINVAL, "network or order is NULL");
+  std::vector<int32_t> o;
+  const int32_t w = min_fill_order(net->net, &o);
+  std::copy(o.begin(), o.end(), order);
+  if (n_vars) *n_vars = net->net.n_vars;
+  if (width) *width = w;
+  return QT_OK;
+}
+
+static qt_status contract_plan(const qt_network* net, const int32_t* order, qt_dtype dtype, Plan* P) {
+  if (!net || !order) return fail(QT_EINVAL, "network or order is NULL");
+  if (dtype != QT_C128 && dtype != QT_C64) return fail(QT_EINVAL, "unknown dtype");
+  std::vector<int32_t> o(order, order + net->net.n_vars);
+  EdgePlan ep;
+  qt_status st = make_edge_plan(net->net, o, &ep);
+  if (st != QT_OK) return st;
+  qt_plan_options_default(&P->opt);
+  P->opt.dtype = dtype;
+  P->opt.mode = QT_MODE_PER_BUCKET;
+  P->p = net->net.p;
+  P->elem_bytes = dtype == QT_C64 ? 8 : 16;
+  P->widths = {ep.width};
+  P->edges.push_back(std::move(ep));
+  return compile_plan(P);
+}
+
+qt_status qt_contract_workspace_size(const qt_network* net, const int32_t* order, qt_dtype dtype, size_t* bytes) {
+  if (!bytes) return fail(QT_EINVAL, "bytes is NULL");
+  Plan P;
+  qt_status st = contract_plan(net, order, dtype, &P);
+  if (st != QT_OK) return st;
+  *bytes = P.ws.total;
+  return QT_OK;
+}
+
+qt_status qt_contract(qt_network* net, const int32_t* order, qt_dtype dtype, void* stream, void* workspace,
+                      size_t ws_bytes, double out_zz[2]) {
+  if (!out_zz) return fail(QT_EINVAL, "out_zz is NULL");
+  if (!net || net->net.gamma.size() != (size_t)net->net.p) return fail(QT_EINVAL, "network has no angles");
+  Plan P;
+  qt_status st = contract_plan(net, order, dtype, &P);
+  if (st != QT_OK) return st;
+  double energy = 0.0, zz[2] = {0.0, 0.0};
+  qt_plan h;
+  h.P = std::move(P);
+  st = qt_plan_energy_host(&h, net->net.gamma.data(), net->net.beta.data(), &energy, zz, nullptr, workspace,
+                           ws_bytes, stream);
+  if (st != QT_OK) return st;
+  out_zz[0] = zz[0];
+  out_zz[1] = zz[1];
+  return QT_OK;
+}
+
+void qt_network_free(qt_network* net) { delete net; }
+
+void qt_plan_options_default(qt_plan_options* opt) {
+  if (!opt) return;
+  opt->batch = 1;
+  opt->dtype = QT_C128;
+  opt->mode = QT_MODE_PER_BUCKET;
+  opt->gradient = 0;
+  opt->max_width = 34;
+  opt->pad_ = 0;
+  opt->max_workspace = 0;
+}
+
+qt_status qt_plan_create(const qt_graph* g, int32_t p, const qt_plan_options* opt, qt_plan** out) {
+  if (!out) return fail(QT_EINVAL, "out is NULL");
+  if (p < 1 || p > 64) return fail(QT_EINVAL, "p must be in [1, 64]");
+  qt_plan_options o;
+  qt_plan_options_default(&o);
+  if (opt) o = *opt;
+  if (o.batch < 1) return fail(QT_EINVAL, "batch must be >= 1");
+  if (o.dtype != QT_C128 && o.dtype != QT_C64) return fail(QT_EINVAL, "unknown dtype");
+  if (o.mode != QT_MODE_PER_BUCKET && o.mode != QT_MODE_PERSISTENT) return fail(QT_EINVAL, "unknown mode");
+  if (o.gradient) return fail(QT_EINVAL, "gradient plans are not available in this build");
+  if (o.max_width <= 0) o.max_width = 34;
+  if (o.max_width > 31) o.max_width = 31;
+  qt_plan* h = new (std::nothrow) qt_plan;
+  if (!h) return fail(QT_ENOMEM, "host allocation failed");
+  qt_status st = make_graph(g, &h->P.G);
+  if (st == QT_OK) {
+    h->P.p = p;
+    h->P.opt = o;
+    h->P.elem_bytes = o.dtype == QT_C64 ? 8 : 16;
+    st = plan_edges(h->P.G, p, o.max_width, &h->P);
+  }
+  if (st == QT_OK) st = compile_plan(&h->P);
+  if (st != QT_OK) {
+    delete h;
+    return st;
+  }
+  *out = h;
+  return QT_OK;
+}
+
+qt_status qt_plan_workspace_size(const qt_plan* plan, size_t* bytes) {
+  if (!plan || !bytes) return fail(QT_EINVAL, "plan or bytes is NULL");
+  *bytes = plan->P.ws.total;
+  return QT_OK;
+}
+
+qt_status qt_plan_stats(const qt_plan* plan, int32_t* n_edges, int32_t* max_width, int64_t* n_buckets,
+                        double* alg_bytes, double* flops) {
+  if (!plan) return fail(QT_EINVAL, "plan is NULL");
+  const Plan& P = plan->P;
+  if (n_edges) *n_edges = (int32_t)P.edges.size();
+  if (max_width) {
+    int32_t w = 0;
+    for (int32_t x : P.widths) w = std::max(w, x);
+    *max_width = w;
+  }
+  if (n_buckets) *n_buckets = (int64_t)P.buckets.size();
+  if (alg_bytes) *alg_bytes = P.alg_bytes;
+  if (flops) *flops = P.flops;
+  return QT_OK;
+}
+
+qt_status qt_plan_edge_widths(const qt_plan* plan, int32_t* widths) {
+  if (!plan || !widths) return fail(QT_EINVAL, "plan or widths is NULL");
+  std::copy(plan->P.widths.begin(), plan->P.widths.end(), widths);
+  return QT_OK;
+}
+
+qt_status qt_plan_energy(qt_plan* plan, const double* gamma, const double* beta, double* energy, double* edge_zz,
+                         double* grad, void* workspace, size_t ws_bytes, void* stream) {
+  if (!plan) return fail(QT_EINVAL, "plan is NULL");
+  return run_plan(&plan->P, gamma, beta, energy, edge_zz, grad, workspace, ws_bytes, stream);
+}
+
+qt_status qt_plan_check(qt_plan* plan, void* stream) {
+  if (!plan) return fail(QT_EINVAL, "plan is NULL");
+  return check_plan(&plan->P, stream);
+}
+
+qt_status qt_plan_energy_host(qt_plan* plan, const double* gamma, const double* beta, double* energy,
+                              double* edge_zz, double* grad, void* workspace, size_t ws_bytes, void* stream) {
+  if (!plan) return fail(QT_EINVAL, "plan is NULL");
+  Plan& P = plan->P;
+  const int32_t B = P.opt.batch, p = P.p, ne = (int32_t)P.edges.size();
+  qt_status st;
+  if ((st = check_angles(gamma, (int64_t)B * p, "gamma")) != QT_OK) return st;
+  if ((st = check_angles(beta, (int64_t)B * p, "beta")) != QT_OK) return st;
+  if (!workspace) return fail(QT_EINVAL, "workspace is NULL");
+  if (ws_bytes < P.ws.total) return fail(QT_ENOMEM, "workspace smaller than the plan needs");
+  cudaStream_t s = (cudaStream_t)stream;
+  char* base = (char*)workspace;
+  double* d_gamma = (double*)(base + P.ws.angles);
+  double* d_beta = d_gamma + (size_t)B * p;
+  double* d_energy = (double*)(base + P.ws.results);
+  double* d_zz = d_energy + B;
+  double* d_grad = d_zz + (size_t)ne * B * 2;
+  cudaError_t ce;
+  if ((ce = cudaMemcpyAsync(d_gamma, gamma, sizeof(double) * B * p, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (ce = cudaMemcpyAsync(d_beta, beta, sizeof(double) * B * p, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return fail(QT_ECUDA, std::string("angle upload: ") + cudaGetErrorString(ce));
+  st = run_plan(&P, d_gamma, d_beta, d_energy, edge_zz ? d_zz : nullptr, grad ? d_grad : nullptr, workspace,
+                ws_bytes, stream);
+  if (st != QT_OK) return st;
+  if (energy && (ce = cudaMemcpyAsync(energy, d_energy, sizeof(double) * B, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return fail(QT_ECUDA, std::string("energy download: ") + cudaGetErrorString(ce));
+  if (edge_zz &&
+      (ce = cudaMemcpyAsync(edge_zz, d_zz, sizeof(double) * ne * B * 2, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return fail(QT_ECUDA, std::string("edge_zz download: ") + cudaGetErrorString(ce));
+  if (grad &&
+      (ce = cudaMemcpyAsync(grad, d_grad, sizeof(double) * B * 2 * p, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return fail(QT_ECUDA, std::string("grad download: ") + cudaGetErrorString(ce));
+  return check_plan(&P, stream);
+}
+
+qt_status qt_plan_set_profiling(qt_plan* plan, int32_t on) {
+  if (!plan) return fail(QT_EINVAL, "plan is NULL");
+  plan->P.profile = on != 0;
+  return QT_OK;
+}
+
+qt_status qt_plan_kernel_times(qt_plan* plan, float* ms, int32_t cap, int32_t* n) {
+  if (!plan || (!ms && cap > 0)) return fail(QT_EINVAL, "plan or ms is NULL");
+  return plan_kernel_times(&plan->P, ms, cap, n);
+}
+
+void qt_plan_free(qt_plan* plan) { delete plan; }
+
+qt_status qt_energy_workspace_size(const qt_graph* g, int32_t p, int32_t B, qt_dtype dtype, int32_t gradient,
+                                   size_t* bytes) {
+  if (!bytes) return fail(QT_EINVAL, "bytes is NULL");
+  qt_plan_options o;
+  qt_plan_options_default(&o);
+  o.batch = B;
+  o.dtype = dtype;
+  o.mode = QT_MODE_PERSISTENT;
+  o.gradient = gradient;
+  qt_plan* h = nullptr;
+  qt_status st = qt_plan_create(g, p, &o, &h);
+  if (st != QT_OK) return st;
+  *bytes = h->P.ws.total;
+  qt_plan_free(h);
+  return QT_OK;
+}
+
+qt_status qt_energy(const qt_graph* g, int32_t p, const double* gamma, const double* beta, int32_t B,
+                    qt_dtype dtype, void* stream, void* workspace, size_t ws_bytes, double* energy, double* grad) {
+  qt_plan_options o;
+  qt_plan_options_default(&o);
+  o.batch = B;
+  o.dtype = dtype;
+  o.mode = QT_MODE_PERSISTENT;
+  o.gradient = grad ? 1 : 0;
+  qt_plan* h = nullptr;
+  qt_status st = qt_plan_create(g, p, &o, &h);
+  if (st != QT_OK) return st;
+  st = qt_plan_energy_host(h, gamma, beta, energy, nullptr, grad, workspace, ws_bytes, stream);
+  qt_plan_free(h);
+  return st;
+}
+
+}  // extern "C"

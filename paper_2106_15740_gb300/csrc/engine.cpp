@@ -1,0 +1,424 @@
+// Plan compiler and executor of the energy path.
+//
+// compile_plan turns the bucket plans of every edge network into device
+// records (qt_device.h) and lays out the workspace:
+//   [ctrl | done counters | buckets | tasks | leaf factors | scalar table |
+//    angles | results | trig table | data]
+// data = [leaf-factor pool | scalar results | intermediate arenas].
+// Intermediates of one edge live in an arena planned by first-fit with
+// free-on-consume: a bucket's output is allocated before its inputs are
+// released, so a bucket never writes over what it reads.
+//
+// Execution (run_plan): angle table -> leaf factors -> buckets -> energy.
+// QT_MODE_PER_BUCKET launches one kernel per bucket, edge after edge, all
+// edges sharing one arena.  QT_MODE_PERSISTENT issues one persistent launch
+// over a queue of bucket tiles; edges are spread over "slots" (one arena
+// each), buckets of one slot form a chain (each waits for the previous one),
+// and the queue interleaves the slots round-robin so independent work fills
+// the GPU while a chain waits.
+#include "engine.h"
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <queue>
+
+#include "kernels_api.h"
+
+namespace qt {
+
+namespace {
+
+struct Arena {
+  std::map<int64_t, int64_t> free_;
+  int64_t top = 0, peak = 0;
+  int64_t alloc(int64_t n) {
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= n) {
+        const int64_t o = it->first, rem = it->second - n;
+        free_.erase(it);
+        if (rem) free_[o + n] = rem;
+        return o;
+      }
+    }
+    const int64_t o = top;
+    top += n;
+    peak = std::max(peak, top);
+    return o;
+  }
+  void release(int64_t o, int64_t n) {
+    auto it = free_.emplace(o, n).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+        it = pv;
+      }
+    }
+    if (it->first + it->second == top) {
+      top = it->first;
+      free_.erase(it);
+    }
+  }
+};
+
+void fill_runs(uint32_t mask, DevInput* in) {
+  int32_t n = 0, dst = 0, bit = 0;
+  while (bit < 32) {
+    if (!((mask >> bit) & 1u)) {
+      ++bit;
+      continue;
+    }
+    const int32_t start = bit;
+    while (bit < 32 && ((mask >> bit) & 1u)) ++bit;
+    const int32_t len = bit - start;
+    if (n < kDevMaxRuns) in->run[n] = (uint32_t)start | (uint32_t)len << 8 | (uint32_t)dst << 16;
+    ++n;
+    dst += len;
+  }
+  in->mask = mask;
+  in->nruns = n <= kDevMaxRuns ? n : -1;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+qt_status compile_plan(Plan* P) {
+  const int32_t B = P->opt.batch;
+  const int32_t es = P->elem_bytes;
+  const int64_t al = 256 / es;  // elements per 256 bytes
+  auto align_el = [&](int64_t x) { return (x + al - 1) / al * al; };
+  const int32_t n_edges = (int32_t)P->edges.size();
+  const int vb = vector_width(P->opt.dtype, B);
+
+  // Per-edge memory plans.
+  std::vector<std::vector<int64_t>> out_off(n_edges);
+  std::vector<int64_t> peak(n_edges), cost(n_edges);
+  int64_t leaf_pool = 0, scal_pool = 0;
+  std::vector<std::vector<int64_t>> leaf_off(n_edges);
+  P->alg_bytes = 0.0;
+  P->flops = 0.0;
+  for (int32_t e = 0; e < n_edges; ++e) {
+    const EdgePlan& ep = P->edges[e];
+    const int32_t nb = (int32_t)ep.buckets.size();
+    Arena arena;
+    out_off[e].assign(nb, 0);
+    leaf_off[e].assign(nb, -1);
+    double ebytes = 0.0;
+    for (int32_t i = 0; i < nb; ++i) {
+      const Bucket& bk = ep.buckets[i];
+      const int64_t rows = (int64_t)1 << bk.out_rank;
+      if (bk.out_rank == 0) {
+        out_off[e][i] = scal_pool;  // relative to the scalar pool
+        scal_pool += align_el(B);
+      } else {
+        out_off[e][i] = arena.alloc(align_el(rows * B));
+      }
+      double bytes = (double)rows;  // output write
+      for (size_t k = 0; k < bk.in_src.size(); ++k) {
+        if (bk.in_src[k] >= 0) {
+          const Bucket& src = ep.buckets[bk.in_src[k]];
+          arena.release(out_off[e][bk.in_src[k]], align_el(((int64_t)1 << src.out_rank) * B));
+          bytes += (double)((int64_t)1 << bk.in_rank[k]);
+        }
+      }
+      if (bk.leaf_rank > 0) {
+        leaf_off[e][i] = leaf_pool;
+        leaf_pool += align_el(((int64_t)1 << bk.leaf_rank) * B);
+      }
+      ebytes += bytes;
+      const double nin = (double)bk.in_src.size();
+      P->flops += (double)B * (double)rows * (2.0 * 6.0 * (nin - 1.0) + 2.0);
+    }
+    peak[e] = arena.peak;
+    cost[e] = (int64_t)ebytes;
+    P->alg_bytes += ebytes * (double)B * (double)es;
+  }
+
+  // Arena placement: per-bucket mode shares one arena; persistent mode uses slots.
+  std::vector<int64_t> edge_base(n_edges, 0);
+  int64_t arena_total = 0;
+  std::vector<std::vector<int32_t>> slot_edges;
+  const bool persistent = P->opt.mode == QT_MODE_PERSISTENT;
+  if (!persistent) {
+    for (int32_t e = 0; e < n_edges; ++e) arena_total = std::max(arena_total, peak[e]);
+    P->n_slots = 1;
+  } else {
+    std::vector<int32_t> by_cost(n_edges);
+    for (int32_t e = 0; e < n_edges; ++e) by_cost[e] = e;
+    std::stable_sort(by_cost.begin(), by_cost.end(), [&](int32_t a, int32_t b) { return cost[a] > cost[b]; });
+    const int64_t fixed = leaf_pool + scal_pool;
+    const int64_t cap_el = P->opt.max_workspace > 0 ? P->opt.max_workspace / es : INT64_MAX;
+    int32_t S = n_edges;
+    for (;;) {
+      slot_edges.assign(S, {});
+      std::vector<int64_t> load(S, 0), speak(S, 0);
+      using Item = std::pair<int64_t, int32_t>;
+      std::priority_queue<Item, std::vector<Item>, std::greater<Item>> heap;
+      for (int32_t s = 0; s < S; ++s) heap.push({0, s});
+      for (int32_t e : by_cost) {
+        auto [l, s] = heap.top();
+        heap.pop();
+        slot_edges[s].push_back(e);
+        speak[s] = std::max(speak[s], peak[e]);
+        heap.push({l + cost[e] + 1, s});
+      }
+      int64_t total = 0;
+      for (int32_t s = 0; s < S; ++s) total += speak[s];
+      if (total + fixed <= cap_el || S == 1) {
+        if (total + fixed > cap_el) return fail(QT_ENOMEM, "plan does not fit max_workspace even one edge at a time");
+        int64_t base = 0;
+        for (int32_t s = 0; s < S; ++s) {
+          for (int32_t e : slot_edges[s]) edge_base[e] = base;
+          base += speak[s];
+        }
+        arena_total = base;
+        break;
+      }
+      S = std::max(1, S * 7 / 8 < S - 1 ? S * 7 / 8 : S - 1);
+    }
+    P->n_slots = S;
+  }
+
+  // Data region: [leaf pool | scalars | arenas].
+  const int64_t scal_base = leaf_pool;
+  const int64_t arena_base = scal_base + scal_pool;
+  P->data_elems = arena_base + arena_total;
+
+  // Device records.
+  P->buckets.clear();
+  P->edge_first.assign(n_edges + 1, 0);
+  P->leaf.clear();
+  P->scal_off.clear();
+  P->scal_begin.assign(n_edges + 1, 0);
+  for (int32_t e = 0; e < n_edges; ++e) {
+    const EdgePlan& ep = P->edges[e];
+    P->edge_first[e] = (int32_t)P->buckets.size();
+    for (int32_t i = 0; i < (int32_t)ep.buckets.size(); ++i) {
+      const Bucket& bk = ep.buckets[i];
+      DevBucket d;
+      std::memset(&d, 0, sizeof(d));
+      d.out_rank = bk.out_rank;
+      d.n_rows = (int64_t)1 << bk.out_rank;
+      d.out_off = bk.out_rank == 0 ? scal_base + out_off[e][i] : arena_base + edge_base[e] + out_off[e][i];
+      d.n_in = (int32_t)bk.in_src.size();
+      d.dep = -1;
+      d.ntask = 1;
+      for (int32_t k = 0; k < d.n_in; ++k) {
+        const int32_t src = bk.in_src[k];
+        if (src >= 0) {
+          const Bucket& sb = ep.buckets[src];
+          d.in[k].off = sb.out_rank == 0 ? scal_base + out_off[e][src] : arena_base + edge_base[e] + out_off[e][src];
+        } else {
+          d.in[k].off = leaf_off[e][i];
+          DevLeafFactor lf;
+          std::memset(&lf, 0, sizeof(lf));
+          lf.off = leaf_off[e][i];
+          lf.rank = bk.leaf_rank;
+          lf.n_leaves = (int32_t)bk.leaves.size();
+          for (int32_t l = 0; l < lf.n_leaves; ++l) {
+            const LeafRef& L = bk.leaves[l];
+            uint32_t w = (uint32_t)L.kind | (uint32_t)L.conj << 2 | (uint32_t)L.rank << 3 |
+                         (uint32_t)(L.bit[0] < 0 ? 0 : L.bit[0]) << 5 |
+                         (uint32_t)(L.bit[1] < 0 ? 0 : L.bit[1]) << 10 | (uint32_t)L.layer << 16;
+            lf.leaf[l] = w;
+          }
+          P->leaf.push_back(lf);
+        }
+        fill_runs(bk.in_mask[k], &d.in[k]);
+      }
+      P->buckets.push_back(d);
+    }
+    for (int32_t s : ep.scalars) P->scal_off.push_back(scal_base + out_off[e][s]);
+    P->scal_begin[e + 1] = (int32_t)P->scal_off.size();
+  }
+  P->edge_first[n_edges] = (int32_t)P->buckets.size();
+
+  // Persistent queue.
+  P->tasks.clear();
+  P->tile_items = 256 * 16;
+  if (persistent) {
+    const int32_t S = P->n_slots;
+    std::vector<size_t> ei(S, 0);
+    std::vector<int32_t> bi(S, 0), prev(S, -1);
+    bool any = true;
+    while (any) {
+      any = false;
+      for (int32_t s = 0; s < S; ++s) {
+        if (ei[s] >= slot_edges[s].size()) continue;
+        any = true;
+        const int32_t e = slot_edges[s][ei[s]];
+        const int32_t gb = P->edge_first[e] + bi[s];
+        DevBucket& d = P->buckets[gb];
+        const int64_t items = B == 1 ? d.n_rows : d.n_rows * (B / vb);
+        const int64_t nt = (items + P->tile_items - 1) / P->tile_items;
+        if (nt > INT32_MAX / 2) return fail(QT_EWIDTH, "bucket too large for the task queue");
+        d.ntask = (int32_t)nt;
+        d.dep = prev[s];
+        for (int32_t t = 0; t < d.ntask; ++t) P->tasks.push_back(DevTask{gb, t});
+        if ((int64_t)P->tasks.size() > INT32_MAX / 2) return fail(QT_EWIDTH, "task queue too long");
+        prev[s] = gb;
+        if (++bi[s] == (int32_t)P->edges[e].buckets.size()) {
+          bi[s] = 0;
+          ++ei[s];
+        }
+      }
+    }
+  }
+
+  // Workspace layout.
+  WsLayout& L = P->ws;
+  const int32_t p = P->p;
+  size_t o = 0;
+  L.ctrl = o;
+  o = align256(o + sizeof(DevCtrl));
+  L.done = o;
+  o = align256(o + sizeof(int32_t) * P->buckets.size());
+  L.buckets = o;
+  o = align256(o + sizeof(DevBucket) * P->buckets.size());
+  L.tasks = o;
+  o = align256(o + sizeof(DevTask) * P->tasks.size());
+  L.leaf = o;
+  o = align256(o + sizeof(DevLeafFactor) * P->leaf.size());
+  L.scal_off = o;
+  o = align256(o + sizeof(int64_t) * P->scal_off.size());
+  L.scal_begin = o;
+  o = align256(o + sizeof(int32_t) * P->scal_begin.size());
+  L.angles = o;
+  o = align256(o + sizeof(double) * 2 * (size_t)B * p);
+  L.results = o;
+  o = align256(o + sizeof(double) * ((size_t)B + (size_t)n_edges * B * 2 + (size_t)B * 2 * p));
+  L.trig = o;
+  o = align256(o + sizeof(double) * 4 * (size_t)B * p);
+  L.data = o;
+  o = align256(o + (size_t)es * (size_t)P->data_elems);
+  L.total = o;
+  P->bound_ws = nullptr;
+  return QT_OK;
+}
+
+static qt_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(QT_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define QT_CUDA(call)                          \
+  do {                                         \
+    cudaError_t err_ = (call);                 \
+    if (err_ != cudaSuccess) return cuda_fail(err_, #call); \
+  } while (0)
+
+qt_status run_plan(Plan* P, const double* gamma, const double* beta, double* energy, double* edge_zz,
+                   double* grad, void* ws, size_t ws_bytes, void* stream) {
+  if (!ws) return fail(QT_EINVAL, "workspace is NULL");
+  if (((uintptr_t)ws & 255u) != 0) return fail(QT_EINVAL, "workspace is not 256-byte aligned");
+  if (ws_bytes < P->ws.total)
+    return fail(QT_ENOMEM, "workspace has " + std::to_string(ws_bytes) + " bytes, plan needs " +
+                               std::to_string(P->ws.total));
+  if (!gamma || !beta) return fail(QT_EINVAL, "angle pointer is NULL");
+  if (grad) return fail(QT_ESTATE, "gradient requested from a plan without the adjoint sweep");
+  cudaStream_t s = (cudaStream_t)stream;
+  char* base = (char*)ws;
+  const WsLayout& L = P->ws;
+  const int32_t B = P->opt.batch;
+  const int dtype = P->opt.dtype;
+  int dev = -1;
+  QT_CUDA(cudaGetDevice(&dev));
+  if (P->bound_ws != ws || P->device != dev) {
+    if (!P->buckets.empty())
+      QT_CUDA(cudaMemcpyAsync(base + L.buckets, P->buckets.data(), sizeof(DevBucket) * P->buckets.size(),
+                              cudaMemcpyHostToDevice, s));
+    if (!P->tasks.empty())
+      QT_CUDA(cudaMemcpyAsync(base + L.tasks, P->tasks.data(), sizeof(DevTask) * P->tasks.size(),
+                              cudaMemcpyHostToDevice, s));
+    if (!P->leaf.empty())
+      QT_CUDA(cudaMemcpyAsync(base + L.leaf, P->leaf.data(), sizeof(DevLeafFactor) * P->leaf.size(),
+                              cudaMemcpyHostToDevice, s));
+    if (!P->scal_off.empty())
+      QT_CUDA(cudaMemcpyAsync(base + L.scal_off, P->scal_off.data(), sizeof(int64_t) * P->scal_off.size(),
+                              cudaMemcpyHostToDevice, s));
+    QT_CUDA(cudaMemcpyAsync(base + L.scal_begin, P->scal_begin.data(), sizeof(int32_t) * P->scal_begin.size(),
+                            cudaMemcpyHostToDevice, s));
+    QT_CUDA(cudaStreamSynchronize(s));  // host vectors may change after return
+    P->bound_ws = ws;
+    P->device = dev;
+  }
+  void* data = base + L.data;
+  double* trig = (double*)(base + L.trig);
+  QT_CUDA(cudaMemsetAsync(base + L.ctrl, 0, L.buckets - L.ctrl, s));  // ctrl + done counters
+  QT_CUDA(launch_trig(gamma, beta, P->p, B, trig, s));
+  QT_CUDA(launch_leaf_factors(dtype, (const DevLeafFactor*)(base + L.leaf), (int32_t)P->leaf.size(), trig, P->p,
+                              B, data, s));
+  const DevBucket* dbk = (const DevBucket*)(base + L.buckets);
+  cudaEvent_t ev_stop = nullptr;
+  if (P->profile) {
+    if (P->events_used == P->events.size()) {
+      cudaEvent_t a, b;
+      QT_CUDA(cudaEventCreate(&a));
+      QT_CUDA(cudaEventCreate(&b));
+      P->events.push_back({a, b});
+    }
+    QT_CUDA(cudaEventRecord(P->events[P->events_used].first, s));
+    ev_stop = P->events[P->events_used].second;
+    ++P->events_used;
+  }
+  if (P->opt.mode == QT_MODE_PERSISTENT) {
+    int per_sm = 0;
+    QT_CUDA(persistent_occupancy(dtype, B, &per_sm));
+    int n_sm = 0;
+    QT_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+    const int32_t grid = std::max(1, per_sm) * n_sm;
+    QT_CUDA(launch_persistent(dtype, dbk, (const DevTask*)(base + L.tasks), (int32_t)P->tasks.size(),
+                              (DevCtrl*)(base + L.ctrl), (int32_t*)(base + L.done), B, data, P->tile_items, grid,
+                              1 << 25, s));
+  } else {
+    int n_sm = 0;
+    QT_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+    for (size_t i = 0; i < P->buckets.size(); ++i)
+      QT_CUDA(launch_bucket(dtype, P->buckets[i], B, data, n_sm * 8, s));
+  }
+  if (ev_stop) QT_CUDA(cudaEventRecord(ev_stop, s));
+  QT_CUDA(launch_energy(dtype, data, (const int64_t*)(base + L.scal_off), (const int32_t*)(base + L.scal_begin),
+                        (int32_t)P->edges.size(), B, energy, edge_zz, s));
+  return QT_OK;
+}
+
+qt_status check_plan(Plan* P, void* stream) {
+  QT_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  if (!P->bound_ws) return QT_OK;
+  const void* ws = P->bound_ws;
+  DevCtrl c;
+  QT_CUDA(cudaMemcpy(&c, (const char*)ws + P->ws.ctrl, sizeof(c), cudaMemcpyDeviceToHost));
+  if (c.status == QT_ETIMEOUT)
+    return fail(QT_ETIMEOUT, "persistent queue wait timed out on bucket " + std::to_string(c.spins));
+  if (c.status != 0) return fail((qt_status)c.status, "device reported an error");
+  return QT_OK;
+}
+
+qt_status plan_kernel_times(Plan* P, float* ms, int32_t cap, int32_t* n) {
+  int32_t k = 0;
+  for (size_t i = 0; i < P->events_used; ++i) {
+    QT_CUDA(cudaEventSynchronize(P->events[i].second));
+    float t = 0.f;
+    QT_CUDA(cudaEventElapsedTime(&t, P->events[i].first, P->events[i].second));
+    if (k < cap) ms[k++] = t;
+  }
+  P->events_used = 0;
+  if (n) *n = k;
+  return QT_OK;
+}
+
+Plan::~Plan() {
+  for (auto& e : events) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+}
+
+}  // namespace qt

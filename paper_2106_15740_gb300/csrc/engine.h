@@ -1,0 +1,69 @@
+// Energy plans: all edge networks of a graph compiled into device records.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <utility>
+#include <vector>
+
+#include "qt_device.h"
+#include "qt_internal.h"
+
+struct qt_network {
+  qt::Network net;
+};
+
+namespace qt {
+
+struct WsLayout {
+  size_t ctrl = 0, done = 0, buckets = 0, tasks = 0, leaf = 0, scal_off = 0, scal_begin = 0;
+  size_t angles = 0, results = 0, trig = 0, data = 0, total = 0;
+};
+
+struct Plan {
+  Graph G;
+  int32_t p = 0;
+  qt_plan_options opt{};
+  int32_t elem_bytes = 16;
+  std::vector<EdgePlan> edges;
+  std::vector<int32_t> widths;
+
+  // device images (uploaded into the workspace)
+  std::vector<DevBucket> buckets;          // all edges, concatenated
+  std::vector<int32_t> edge_first;         // first bucket of each edge (n_edges + 1)
+  std::vector<DevLeafFactor> leaf;
+  std::vector<DevTask> tasks;
+  std::vector<int64_t> scal_off;           // element offsets of scalar results
+  std::vector<int32_t> scal_begin;         // CSR over edges
+  int64_t tile_items = 0;
+  int32_t n_slots = 0;
+  int64_t data_elems = 0;
+  WsLayout ws;
+
+  // statistics
+  double alg_bytes = 0.0, flops = 0.0;
+
+  // state
+  const void* bound_ws = nullptr;
+  int device = -1;
+
+  // profiling: event pairs around the contraction, one per call
+  bool profile = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+  size_t events_used = 0;
+  ~Plan();
+};
+
+// Compile edge plans into device records and a workspace layout.
+qt_status compile_plan(Plan* P);
+// Evaluate with device pointers on a stream.
+qt_status run_plan(Plan* P, const double* gamma, const double* beta, double* energy, double* edge_zz,
+                   double* grad, void* ws, size_t ws_bytes, void* stream);
+qt_status check_plan(Plan* P, void* stream);
+qt_status plan_kernel_times(Plan* P, float* ms, int32_t cap, int32_t* n);
+
+}  // namespace qt
+
+struct qt_plan {
+  qt::Plan P;
+};

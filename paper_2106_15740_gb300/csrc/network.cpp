@@ -1,0 +1,108 @@
+// Graph validation and reverse-lightcone network construction.
+//
+// §QAOA algorithm: E = sum over edges of a two-qubit local term; gates that
+// commute through the local observable cancel against their conjugates (the
+// lightcone).  §Diagonal gate simplification, eq. (example): a diagonal gate
+// is a tensor on the indices its qubits already carry, so the ZZ phase of
+// eq. (zz_gates_circ) becomes a rank-2 tensor with no new variable, and only
+// the mixer X^{2 beta} opens a new variable.
+#include <algorithm>
+#include <cmath>
+#include <set>
+
+#include "qt_internal.h"
+
+namespace qt {
+
+qt_status make_graph(const qt_graph* g, Graph* out) {
+  if (!g) return fail(QT_EINVAL, "graph is NULL");
+  if (g->n_vertices < 2) return fail(QT_EINVAL, "graph needs at least 2 vertices");
+  if (g->n_edges < 1) return fail(QT_EINVAL, "graph needs at least 1 edge");
+  if (!g->edges) return fail(QT_EINVAL, "graph edge array is NULL");
+  Graph G;
+  G.n = g->n_vertices;
+  G.adj.assign(G.n, {});
+  std::set<std::pair<int32_t, int32_t>> seen;
+  for (int32_t i = 0; i < g->n_edges; ++i) {
+    int32_t a = g->edges[2 * i], b = g->edges[2 * i + 1];
+    if (a < 0 || b < 0 || a >= G.n || b >= G.n)
+      return fail(QT_EINVAL, "edge " + std::to_string(i) + " has a vertex out of range");
+    if (a == b) return fail(QT_EINVAL, "edge " + std::to_string(i) + " is a self-loop");
+    int32_t u = std::min(a, b), v = std::max(a, b);
+    if (!seen.insert({u, v}).second)
+      return fail(QT_EINVAL, "edge " + std::to_string(i) + " repeats an earlier edge");
+    G.eu.push_back(u);
+    G.ev.push_back(v);
+    G.adj[u].push_back(v);
+    G.adj[v].push_back(u);
+  }
+  for (auto& a : G.adj) std::sort(a.begin(), a.end());
+  *out = std::move(G);
+  return QT_OK;
+}
+
+void build_lightcone(const Graph& g, int32_t p, int32_t edge, Network* net) {
+  const int32_t j = g.eu[edge], k = g.ev[edge];
+  // top[u] = largest q with u in R_q (R_p = {j,k}, R_{q-1} = R_q + N(R_q));
+  // u belongs to R_q exactly for q <= top[u], so top[u] is its mixer count.
+  std::vector<int32_t> top(g.n, -1);
+  top[j] = top[k] = p;
+  for (int32_t q = p; q >= 1; --q)
+    for (int32_t u = 0; u < g.n; ++u)
+      if (top[u] >= q)
+        for (int32_t w : g.adj[u]) top[w] = std::max(top[w], q - 1);
+
+  // Canonical ids: qubits ascending; ket v^0..v^m, then bra w^{m-1}..w^0.
+  std::vector<int32_t> ket_base(g.n, -1), bra_base(g.n, -1);
+  int32_t nv = 0;
+  for (int32_t u = 0; u < g.n; ++u) {
+    if (top[u] < 0) continue;
+    ket_base[u] = nv;
+    nv += top[u] + 1;
+    bra_base[u] = nv;          // bra level l (< m) has id bra_base + (m-1-l)
+    nv += top[u];
+  }
+  auto ket = [&](int32_t u, int32_t l) { return ket_base[u] + l; };
+  auto bra = [&](int32_t u, int32_t l) {
+    return l == top[u] ? ket_base[u] + l : bra_base[u] + (top[u] - 1 - l);
+  };
+
+  net->p = p;
+  net->edge = edge;
+  net->n_vars = nv;
+  net->tensors.clear();
+  auto add = [&](int8_t kind, int8_t layer, int8_t conj, int32_t a, int32_t b) {
+    Tensor t;
+    t.kind = kind;
+    t.layer = layer;
+    t.conj = conj;
+    t.rank = b < 0 ? 1 : 2;
+    t.v[0] = a;
+    t.v[1] = b;
+    net->tensors.push_back(t);
+  };
+  for (int32_t u = 0; u < g.n; ++u) {
+    if (top[u] < 0) continue;
+    add(QT_T_PLUS, 0, 0, ket(u, 0), -1);
+    add(QT_T_PLUS, 0, 1, bra(u, 0), -1);
+  }
+  for (int32_t q = 1; q <= p; ++q) {
+    for (size_t e = 0; e < g.eu.size(); ++e) {
+      int32_t a = g.eu[e], b = g.ev[e];
+      if (top[a] >= q || top[b] >= q) {
+        add(QT_T_ZZ, (int8_t)q, 0, ket(a, q - 1), ket(b, q - 1));
+        add(QT_T_ZZ, (int8_t)q, 1, bra(a, q - 1), bra(b, q - 1));
+      }
+    }
+    for (int32_t u = 0; u < g.n; ++u) {
+      if (top[u] >= q) {
+        add(QT_T_MIX, (int8_t)q, 0, ket(u, q), ket(u, q - 1));
+        add(QT_T_MIX, (int8_t)q, 1, bra(u, q), bra(u, q - 1));
+      }
+    }
+  }
+  add(QT_T_OBS, (int8_t)p, 0, ket(j, top[j]), -1);
+  add(QT_T_OBS, (int8_t)p, 0, ket(k, top[k]), -1);
+}
+
+}  // namespace qt

@@ -1,0 +1,89 @@
+// Internal host-side structures of the lightcone tensor-network library.
+// Method: arXiv:2106.15740 (§QAOA algorithm, §Tensor network contraction,
+// §Diagonal gate simplification).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "qtensor.h"
+
+namespace qt {
+
+// Thread-local error message helpers (capi.cpp).
+qt_status fail(qt_status s, const std::string& msg);
+
+// ---------------------------------------------------------------- graph ----
+struct Graph {
+  int32_t n = 0;
+  std::vector<int32_t> eu, ev;              // edge endpoints, eu[i] < ev[i]
+  std::vector<std::vector<int32_t>> adj;    // sorted neighbour lists
+};
+qt_status make_graph(const qt_graph* g, Graph* out);
+
+// -------------------------------------------------------------- network ----
+// One lightcone tensor.  Every tensor of this network has rank 1 or 2 and
+// its value is a closed-form function of (kind, layer, conj) and the angles
+// of its layer; the network stores structure only.
+struct Tensor {
+  int8_t kind;      // qt_tensor_kind
+  int8_t rank;      // 1 or 2
+  int8_t conj;      // 1 for the bra copy (elementwise complex conjugate)
+  int8_t layer;     // 1..p for ZZ/MIX, 0 for PLUS, p for OBS
+  int32_t v[2];     // variable ids; MIX: v[0] = new, v[1] = old
+};
+
+struct Network {
+  int32_t p = 0;
+  int32_t edge = -1;
+  int32_t n_vars = 0;
+  std::vector<Tensor> tensors;
+  std::vector<double> gamma, beta;          // angles of a single evaluation (may be empty)
+};
+
+// Build the reverse-lightcone network of edge `edge` (structure only).
+void build_lightcone(const Graph& g, int32_t p, int32_t edge, Network* net);
+
+// ---------------------------------------------------------------- order ----
+// Greedy min-fill over the interaction graph; returns the width.
+int32_t min_fill_order(const Network& net, std::vector<int32_t>* order);
+
+// ----------------------------------------------------------------- plan ----
+constexpr int kMaxIn = 8;        // inputs per bucket (intermediates + one leaf factor)
+constexpr int kMaxLeafRank = 10; // variables of one leaf factor
+constexpr int kMaxLeaves = 16;   // leaves folded into one leaf factor
+
+// A leaf folded into a bucket's leaf factor: value from (kind, layer, conj),
+// bit positions of its variables inside the leaf factor's index.
+struct LeafRef {
+  int8_t kind, layer, conj, rank;
+  int8_t bit[2];
+};
+
+// One bucket of bucket elimination (§Tensor network contraction): the
+// product of its inputs summed over the eliminated variable.
+struct Bucket {
+  int32_t var;                       // eliminated variable
+  int32_t out_rank;                  // |U| - 1
+  std::vector<int32_t> out_vars;     // sorted by elimination position (bit 0 first)
+  // inputs: intermediates (producer bucket id) and at most one leaf factor (-1)
+  std::vector<int32_t> in_src;       // producer bucket index, or -1 for the leaf factor
+  std::vector<uint32_t> in_mask;     // bit j set if out_vars[j] is an index of the input
+  std::vector<int32_t> in_rank;      // rank of the input (includes the eliminated var)
+  std::vector<LeafRef> leaves;       // leaves folded into the leaf factor
+  int32_t leaf_rank = 0;             // rank of the leaf factor (0 if none)
+  int32_t consumer = -1;             // bucket consuming the output (-1: scalar result)
+};
+
+struct EdgePlan {
+  int32_t edge = -1;
+  int32_t width = 0;
+  std::vector<Bucket> buckets;
+  std::vector<int32_t> scalars;      // buckets whose result has rank 0
+};
+
+// Turn (network, order) into buckets (§Tensor network contraction).
+qt_status make_edge_plan(const Network& net, const std::vector<int32_t>& order, EdgePlan* ep);
+
+}  // namespace qt

@@ -1,0 +1,112 @@
+"""Torch-facing helpers: device workspace, current stream, plan lifetime.
+
+PyTorch provides the device memory (one uint8 workspace tensor per plan)
+and the stream; every step of the contraction runs in the library's CUDA
+kernels behind the C ABI.  There is no CPU path: without the built library
+or a CUDA device these helpers raise.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import binding as qb
+
+DTYPES = {"c128": qb.QT_C128, "c64": qb.QT_C64}
+MODES = {"per_bucket": qb.QT_MODE_PER_BUCKET, "persistent": qb.QT_MODE_PERSISTENT}
+
+
+def _stream_handle(device):
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+class EnergyPlan:
+    """All edge lightcones of one graph, planned once for `batch` angle sets.
+
+    ``energy(gamma, beta)`` takes float64 CUDA tensors of shape [batch, p] and
+    returns E[batch] (and per-edge <Z_j Z_k> if asked), asynchronously on the
+    current stream.  ``energy_host`` takes numpy arrays and synchronises.
+    """
+
+    def __init__(self, n_vertices, edges, p, batch=1, dtype="c128", mode="persistent",
+                 max_workspace=0, max_width=0, device="cuda:0", gradient=False):
+        self.n_vertices, self.p, self.batch = int(n_vertices), int(p), int(batch)
+        self.edges = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
+        self.device = torch.device(device)
+        opt = qb.qt_plan_options_default()
+        opt.batch = self.batch
+        opt.dtype = DTYPES[dtype]
+        opt.mode = MODES[mode]
+        opt.gradient = int(bool(gradient))
+        opt.max_width = int(max_width)
+        opt.max_workspace = int(max_workspace)
+        self.plan = qb.qt_plan_create(self.n_vertices, self.edges, self.p, opt)
+        self.ws_bytes = qb.qt_plan_workspace_size(self.plan)
+        self.stats = qb.qt_plan_stats(self.plan)
+        self.widths = qb.qt_plan_edge_widths(self.plan, len(self.edges))
+        self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+
+    @property
+    def n_edges(self):
+        return len(self.edges)
+
+    def energy(self, gamma, beta, edge_zz=False, grad=False, out=None):
+        B, p = self.batch, self.p
+        for t in (gamma, beta):
+            if t.dtype != torch.float64 or t.device != self.device or tuple(t.shape) != (B, p):
+                raise ValueError(f"angles must be float64 [{B}, {p}] on {self.device}")
+        gamma, beta = gamma.contiguous(), beta.contiguous()
+        energy = out if out is not None else torch.empty(B, dtype=torch.float64, device=self.device)
+        zz = torch.empty((self.n_edges, B, 2), dtype=torch.float64, device=self.device) if edge_zz else None
+        g = torch.empty((B, 2 * p), dtype=torch.float64, device=self.device) if grad else None
+        qb.qt_plan_energy(self.plan, gamma.data_ptr(), beta.data_ptr(), energy.data_ptr(),
+                          zz.data_ptr() if zz is not None else 0, g.data_ptr() if g is not None else 0,
+                          self.workspace.data_ptr(), self.ws_bytes, _stream_handle(self.device))
+        res = [energy]
+        if edge_zz:
+            res.append(zz)
+        if grad:
+            res.append(g)
+        return res[0] if len(res) == 1 else tuple(res)
+
+    def check(self):
+        """Synchronise and raise if a device-side wait timed out."""
+        qb.qt_plan_check(self.plan, _stream_handle(self.device))
+
+    def energy_host(self, gamma, beta, edge_zz=False, grad=False):
+        B, p = self.batch, self.p
+        ga = np.ascontiguousarray(np.asarray(gamma, dtype=np.float64).reshape(B, p))
+        be = np.ascontiguousarray(np.asarray(beta, dtype=np.float64).reshape(B, p))
+        energy = np.empty(B)
+        zz = np.empty((self.n_edges, B, 2)) if edge_zz else None
+        g = np.empty((B, 2 * p)) if grad else None
+        qb.qt_plan_energy_host(self.plan, ga, be, energy, zz, g, self.workspace.data_ptr(), self.ws_bytes,
+                               _stream_handle(self.device))
+        res = [energy] + ([zz] if edge_zz else []) + ([g] if grad else [])
+        return res[0] if len(res) == 1 else tuple(res)
+
+    def close(self):
+        if getattr(self, "plan", None):
+            qb.qt_plan_free(self.plan)
+            self.plan = None
+        self.workspace = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def contract_edge(n_vertices, edges, p, gamma, beta, edge, dtype="c128", device="cuda:0"):
+    """<Z_j Z_k> of one edge through qt_build_lightcone / qt_order / qt_contract.
+    Returns (value, width)."""
+    net = qb.qt_build_lightcone(n_vertices, edges, p, gamma, beta, edge)
+    try:
+        order, width = qb.qt_order(net)
+        nbytes = qb.qt_contract_workspace_size(net, order, DTYPES[dtype])
+        ws = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        val = qb.qt_contract(net, order, DTYPES[dtype], _stream_handle(torch.device(device)), ws.data_ptr(), nbytes)
+    finally:
+        qb.qt_network_free(net)
+    return val, width

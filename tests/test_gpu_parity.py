@@ -1,0 +1,209 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Tolerances (from the precision of each path): |d<Z_j Z_k>| <= 1e-10 for
+complex128 and <= 1e-5 for complex64 (FP32 products, one FP32 add per
+bucket, FP64 edge product and energy sum).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import lightcone as lc
+from oracle import statevector as sv
+from workloads import complete_graph, erdos_renyi_graph, random_angles, random_regular_graph, workload
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"c128": 1e-10, "c64": 1e-5}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib(qtlib):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return qtlib
+
+
+def _plan(n, edges, p, batch, dtype, mode, **kw):
+    from paper_2106_15740_gb300.energy import EnergyPlan
+    return EnergyPlan(n, edges, p, batch=batch, dtype=dtype, mode=mode, device="cuda:0", **kw)
+
+
+def _run(plan, gamma, beta):
+    g = torch.tensor(np.asarray(gamma).reshape(plan.batch, plan.p), device="cuda:0")
+    b = torch.tensor(np.asarray(beta).reshape(plan.batch, plan.p), device="cuda:0")
+    e, zz = plan.energy(g, b, edge_zz=True)
+    plan.check()
+    return e.cpu().numpy(), zz.cpu().numpy()
+
+
+def _oracle_zz(n, edges, p, g, b, sel=None):
+    sel = range(len(edges)) if sel is None else sel
+    return np.array([lc.lightcone_zz(n, edges, p, g, b, e)[0] for e in sel])
+
+
+# ------------------------------------------------------------ qt_contract --
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_contract_single_networks(dtype):
+    from paper_2106_15740_gb300.energy import contract_edge
+    n, edges, p, g, b = workload("n16_p1")
+    ref = sv.edge_zz(n, edges, g[0], b[0])
+    for e in range(len(edges)):
+        val, width = contract_edge(n, edges, p, g[0], b[0], e, dtype=dtype)
+        assert abs(val.real - ref[e]) <= TOL[dtype]
+        assert abs(val.imag) <= TOL[dtype]
+
+
+def test_contract_p3_networks_c128():
+    from paper_2106_15740_gb300.energy import contract_edge
+    n, edges, p, g, b = workload("n100_p3")
+    for e in (0, 17, 77, 149):
+        val, width = contract_edge(n, edges, p, g[0], b[0], e)
+        ref, w_ref = lc.lightcone_zz(n, edges, p, g[0], b[0], e)
+        assert width == w_ref
+        assert abs(val - ref) <= TOL["c128"]
+
+
+# ------------------------------------------------------------ energy plans --
+
+@pytest.mark.parametrize("mode", ["per_bucket", "persistent"])
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_n16_p1_all_edges_vs_statevector(mode, dtype):
+    n, edges, p, g, b = workload("n16_p1", batch=3)
+    plan = _plan(n, edges, p, 3, dtype, mode)
+    e, zz = _run(plan, g, b)
+    for k in range(3):
+        ref = sv.edge_zz(n, edges, g[k], b[k])
+        np.testing.assert_allclose(zz[:, k, 0], ref, atol=TOL[dtype], rtol=0)
+        np.testing.assert_allclose(zz[:, k, 1], 0, atol=TOL[dtype])
+        assert abs(e[k] - 0.5 * (len(edges) - ref.sum())) <= TOL[dtype] * len(edges)
+
+
+@pytest.mark.parametrize("mode", ["per_bucket", "persistent"])
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_n100_p3_all_edges_vs_oracle(mode, dtype):
+    n, edges, p, g, b = workload("n100_p3")
+    plan = _plan(n, edges, p, 1, dtype, mode)
+    e, zz = _run(plan, g, b)
+    ref = _oracle_zz(n, edges, p, g[0], b[0])
+    np.testing.assert_allclose(zz[:, 0, 0], ref.real, atol=TOL[dtype], rtol=0)
+    np.testing.assert_allclose(zz[:, 0, 1], ref.imag, atol=TOL[dtype], rtol=0)
+    assert abs(e[0] - 0.5 * np.sum(1 - ref.real)) <= TOL[dtype] * len(edges)
+
+
+def test_n100_p4_batched_c64_vs_oracle():
+    """The batched workload: 150 edges x 64 angle sets, one persistent launch.
+    The oracle checks every edge on 2 angle sets and a seeded sample of
+    16 edges on 4 more."""
+    n, edges, p, g, b = workload("n100_p4", batch=64)
+    plan = _plan(n, edges, p, 64, "c64", "persistent")
+    e, zz = _run(plan, g, b)
+    for k in (0, 63):
+        ref = _oracle_zz(n, edges, p, g[k], b[k])
+        np.testing.assert_allclose(zz[:, k, 0], ref.real, atol=TOL["c64"], rtol=0)
+        np.testing.assert_allclose(zz[:, k, 1], ref.imag, atol=TOL["c64"], rtol=0)
+    rng = np.random.default_rng(1234)
+    sel = sorted(rng.choice(len(edges), 16, replace=False))
+    for k in rng.choice(np.arange(1, 63), 4, replace=False):
+        ref = _oracle_zz(n, edges, p, g[k], b[k], sel)
+        np.testing.assert_allclose(zz[sel, k, 0], ref.real, atol=TOL["c64"], rtol=0)
+    # energies are the edge sums
+    np.testing.assert_allclose(e, 0.5 * np.sum(1 - zz[:, :, 0], axis=0), atol=1e-12)
+
+
+def test_persistent_equals_per_bucket_bitwise():
+    """Both modes evaluate every output element with the same arithmetic."""
+    n, edges, p, g, b = workload("n100_p3", batch=4)
+    out = []
+    for mode in ("per_bucket", "persistent"):
+        out.append(_run(_plan(n, edges, p, 4, "c128", mode), g, b)[1])
+    assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("batch", [2, 3, 5, 8])
+def test_batch_shapes(batch):
+    """Even batches use the 2-wide complex64 vectors, odd ones the scalar path."""
+    n, edges = 12, random_regular_graph(12, 3, 9)
+    p = 2
+    g, b = random_angles(batch, p, 99)
+    for dtype in ("c128", "c64"):
+        plan = _plan(n, edges, p, batch, dtype, "persistent")
+        e, zz = _run(plan, g, b)
+        for k in range(batch):
+            ref = sv.edge_zz(n, edges, g[k], b[k])
+            np.testing.assert_allclose(zz[:, k, 0], ref, atol=TOL[dtype], rtol=0)
+
+
+def test_edge_cases_small_graphs():
+    cases = [
+        (2, np.array([[0, 1]], dtype=np.int32), 1),
+        (2, np.array([[0, 1]], dtype=np.int32), 3),
+        (4, complete_graph(4), 2),
+        (9, erdos_renyi_graph(9, 0.4, 5), 2),
+        (6, np.array([[0, 1], [1, 2], [4, 5]], dtype=np.int32), 2),   # isolated vertex 3
+    ]
+    for n, edges, p in cases:
+        g, b = random_angles(2, p, n * 10 + p)
+        for dtype in ("c128", "c64"):
+            for mode in ("per_bucket", "persistent"):
+                plan = _plan(n, edges, p, 2, dtype, mode)
+                e, zz = _run(plan, g, b)
+                for k in range(2):
+                    ref = sv.edge_zz(n, edges, g[k], b[k])
+                    np.testing.assert_allclose(zz[:, k, 0], ref, atol=TOL[dtype], rtol=0)
+
+
+def test_gamma_zero_and_symmetries_on_device():
+    n, edges, p, g, b = workload("n100_p3", batch=4)
+    g = g.copy()
+    g[1] = 0.0                        # gamma = 0 -> E = |E|/2
+    g[2], b[2] = -g[3], -b[3]         # E(-g, -b) = E(g, b)
+    plan = _plan(n, edges, p, 4, "c128", "persistent")
+    e, zz = _run(plan, g, b)
+    assert abs(e[1] - len(edges) / 2) < 1e-10
+    assert abs(e[2] - e[3]) < 1e-10
+    assert np.all(np.abs(zz[:, :, 0]) <= 1 + 1e-12)
+
+
+def test_host_pointer_call_matches_device_call():
+    n, edges, p, g, b = workload("n100_p3", batch=2)
+    plan = _plan(n, edges, p, 2, "c64", "persistent")
+    e_dev, zz_dev = _run(plan, g, b)
+    e_host, zz_host = plan.energy_host(g, b, edge_zz=True)
+    assert np.array_equal(e_dev, e_host) and np.array_equal(zz_dev, zz_host)
+
+
+def test_one_shot_qt_energy():
+    from paper_2106_15740_gb300 import binding as qb
+    n, edges, p, g, b = workload("n16_p1", batch=4)
+    nbytes = qb.qt_energy_workspace_size(n, edges, p, 4, qb.QT_C128, 0)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda:0")
+    energy = np.empty(4)
+    qb.qt_energy(n, edges, p, np.ascontiguousarray(g), np.ascontiguousarray(b), 4, qb.QT_C128,
+                 torch.cuda.current_stream().cuda_stream, ws.data_ptr(), nbytes, energy)
+    ref = [sv.energy(n, edges, g[k], b[k]) for k in range(4)]
+    np.testing.assert_allclose(energy, ref, atol=1e-9)
+
+
+def test_workspace_cap_limits_concurrency():
+    """A workspace cap lowers the number of edges in flight, not the result."""
+    n, edges, p, g, b = workload("n100_p3", batch=2)
+    full = _plan(n, edges, p, 2, "c128", "persistent")
+    capped = _plan(n, edges, p, 2, "c128", "persistent", max_workspace=full.ws_bytes // 4)
+    assert capped.ws_bytes < full.ws_bytes
+    assert np.array_equal(_run(full, g, b)[1], _run(capped, g, b)[1])
+
+
+def test_workspace_too_small_is_an_error():
+    from paper_2106_15740_gb300 import binding as qb
+    n, edges, p, g, b = workload("n16_p1")
+    plan = _plan(n, edges, p, 1, "c128", "persistent")
+    gd = torch.tensor(g, device="cuda:0")
+    bd = torch.tensor(b, device="cuda:0")
+    out = torch.empty(1, dtype=torch.float64, device="cuda:0")
+    with pytest.raises(qb.QTError) as ei:
+        qb.qt_plan_energy(plan.plan, gd.data_ptr(), bd.data_ptr(), out.data_ptr(), 0, 0,
+                          plan.workspace.data_ptr(), plan.ws_bytes - 1, torch.cuda.current_stream().cuda_stream)
+    assert ei.value.status == qb.QT_ENOMEM

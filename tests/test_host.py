@@ -1,0 +1,127 @@
+"""Host-side logic of the C ABI, no GPU: symbol exports, network structure,
+min-fill order parity with the oracle, argument validation."""
+import re
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+from oracle import lightcone as lc
+from workloads import complete_graph, random_angles, random_regular_graph, workload
+
+ROOT = Path(__file__).resolve().parent.parent
+
+
+def test_library_exports_every_declared_symbol(qtlib):
+    header = (ROOT / "include" / "qtensor.h").read_text()
+    declared = set(re.findall(r"\b(qt_[a-z_]+)\s*\(", header))
+    assert len(declared) >= 15
+    for name in sorted(declared):
+        assert hasattr(qtlib, name), name
+    from paper_2106_15740_gb300 import binding as qb
+    assert set(qb.EXPORTS) <= declared
+
+
+def _lib_network(n, edges, p, g, b, e):
+    from paper_2106_15740_gb300 import binding as qb
+    net = qb.qt_build_lightcone(n, edges, p, g, b, e)
+    nv, nt = qb.qt_network_info(net)
+    tensors = [qb.qt_network_tensor(net, t) for t in range(nt)]
+    order, width = qb.qt_order(net)
+    qb.qt_network_free(net)
+    return nv, tensors, list(order), width
+
+
+@pytest.mark.parametrize("name,count", [("n16_p1", 24), ("n100_p3", 150), ("n100_p4", 40), ("n60_p4", 30)])
+def test_network_and_order_match_oracle_bitwise(qtlib, name, count):
+    """Same variables, same tensors (by kind/layer/side), same min-fill order
+    and width as the oracle's independent implementation."""
+    n, edges, p, g, b = workload(name)
+    kinds = {0: "leaf", 1: "zz", 2: "mix", 3: "obs"}
+    for e in range(0, len(edges), max(1, len(edges) // count)):
+        nv, tensors, order, width = _lib_network(n, edges, p, g[0], b[0], e)
+        net = lc.build_lightcone(n, edges, p, g[0], b[0], e)
+        assert nv == net.n_vars
+        mine = sorted((kinds[k], lay if k in (1, 2) else 0, "bra" if c else "ket",
+                       tuple(v for v in vs if v >= 0)) for k, lay, c, r, vs in tensors)
+        theirs = sorted((tag[0], tag[1] if tag[0] in ("zz", "mix") else 0, tag[2], tuple(vs))
+                        for (vs, _), tag in zip(net.tensors, net.tags))
+        assert mine == theirs
+        o, w = lc.min_fill_order(net.n_vars, [vs for vs, _ in net.tensors])
+        assert order == o and width == w
+
+
+def test_plan_widths_and_stats(qtlib):
+    from paper_2106_15740_gb300 import binding as qb
+    n, edges, p, g, b = workload("n100_p3")
+    opt = qb.qt_plan_options_default()
+    opt.batch = 4
+    opt.dtype = qb.QT_C64
+    opt.mode = qb.QT_MODE_PERSISTENT
+    plan = qb.qt_plan_create(n, edges, p, opt)
+    st = qb.qt_plan_stats(plan)
+    widths = qb.qt_plan_edge_widths(plan, len(edges))
+    qb.qt_plan_free(plan)
+    ref = [lc.min_fill_order(*(lambda net: (net.n_vars, [vs for vs, _ in net.tensors]))(
+        lc.build_lightcone(n, edges, p, g[0], b[0], e)))[1] for e in range(len(edges))]
+    assert list(widths) == ref
+    assert st["n_edges"] == 150 and st["max_width"] == max(ref)
+    assert st["alg_bytes"] > 0 and st["flops"] > 0
+
+
+@pytest.mark.parametrize("bad", [
+    dict(edges=[[0, 0]]), dict(edges=[[0, 5]]), dict(edges=[[0, 1], [1, 0]]), dict(edges=[[-1, 1]]),
+])
+def test_invalid_graphs_rejected(qtlib, bad):
+    from paper_2106_15740_gb300 import binding as qb
+    with pytest.raises(qb.QTError) as ei:
+        qb.qt_build_lightcone(3, np.array(bad["edges"]), 1, [0.1], [0.2], 0)
+    assert ei.value.status == qb.QT_EINVAL
+
+
+def test_invalid_arguments_rejected(qtlib):
+    from paper_2106_15740_gb300 import binding as qb
+    edges = complete_graph(4)
+    for kwargs in (dict(p=0, e=0, g=[0.1]), dict(p=1, e=6, g=[0.1]), dict(p=1, e=0, g=[np.nan])):
+        with pytest.raises(qb.QTError) as ei:
+            qb.qt_build_lightcone(4, edges, kwargs["p"], kwargs["g"], [0.2] * max(1, kwargs["p"]), kwargs["e"])
+        assert ei.value.status == qb.QT_EINVAL
+    opt = qb.qt_plan_options_default()
+    opt.batch = 0
+    with pytest.raises(qb.QTError):
+        qb.qt_plan_create(4, edges, 1, opt)
+
+
+def test_width_budget(qtlib):
+    from paper_2106_15740_gb300 import binding as qb
+    n, edges, p, g, b = workload("n100_p3")
+    opt = qb.qt_plan_options_default()
+    opt.max_width = 8
+    with pytest.raises(qb.QTError) as ei:
+        qb.qt_plan_create(n, edges, p, opt)
+    assert ei.value.status == qb.QT_EWIDTH
+
+
+def test_contract_rejects_bad_order(qtlib):
+    from paper_2106_15740_gb300 import binding as qb
+    n, edges, p, g, b = workload("n16_p1")
+    net = qb.qt_build_lightcone(n, edges, p, g[0], b[0], 0)
+    try:
+        order, _ = qb.qt_order(net)
+        order[1] = order[0]
+        with pytest.raises(qb.QTError) as ei:
+            qb.qt_contract_workspace_size(net, order, qb.QT_C128)
+        assert ei.value.status == qb.QT_EINVAL
+    finally:
+        qb.qt_network_free(net)
+
+
+def test_workspace_grows_with_batch_and_precision(qtlib):
+    from paper_2106_15740_gb300 import binding as qb
+    n, edges, p, g, b = workload("n16_p1")
+    sizes = {}
+    for B in (1, 8):
+        for dt in (qb.QT_C64, qb.QT_C128):
+            sizes[(B, dt)] = qb.qt_energy_workspace_size(n, edges, p, B, dt, 0)
+    assert sizes[(8, qb.QT_C64)] > sizes[(1, qb.QT_C64)]
+    assert sizes[(8, qb.QT_C128)] > sizes[(8, qb.QT_C64)]
