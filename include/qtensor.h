@@ -189,6 +189,25 @@ qt_status qt_plan_energy_host(qt_plan* plan, const double* gamma, const double* 
 qt_status qt_plan_set_profiling(qt_plan* plan, int32_t on);
 qt_status qt_plan_kernel_times(qt_plan* plan, float* ms, int32_t cap, int32_t* n);
 
+/* Allocation-free evaluation (the paper has no counterpart; this serves
+ * callers that may not allocate device memory while they run, e.g. a service
+ * holding a fixed device-memory budget or a plug-in whose host application
+ * owns all device allocations).  Same as qt_plan_energy without the gradient,
+ * but the plan's scratch space lives in a device array of
+ * qt_static_scratch_bytes() bytes built into the library (held on every device
+ * that loads the library until exit) instead of a caller workspace.  gamma,
+ * beta, energy ([B]) and edge_zz ([n_edges][B][2] or NULL) are device pointers;
+ * the call is asynchronous on `stream`.  Allocates no device memory.  The
+ * first call on a device looks up the array's address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.
+ * Every call re-uploads the plan's descriptors and clears its counters, since
+ * all calls share the array; calls that overlap on the GPU race.  QT_ENOMEM
+ * (with the sizes in the message) if the plan's workspace size is above
+ * qt_static_scratch_bytes(). */
+qt_status qt_plan_energy_static(qt_plan* plan, const double* gamma, const double* beta,
+                                double* energy, double* edge_zz, void* stream);
+size_t qt_static_scratch_bytes(void);
+
 void qt_plan_free(qt_plan* plan);
 
 /* One-shot energy (and gradient if grad != NULL) with HOST pointers: plans

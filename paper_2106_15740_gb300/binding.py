@@ -28,7 +28,8 @@ EXPORTS = [
     "qt_plan_options_default", "qt_plan_create", "qt_plan_workspace_size", "qt_plan_stats",
     "qt_plan_edge_widths", "qt_plan_energy", "qt_plan_check", "qt_plan_energy_host",
     "qt_plan_free", "qt_energy_workspace_size", "qt_energy", "qt_last_error",
-    "qt_plan_set_profiling", "qt_plan_kernel_times",
+    "qt_plan_set_profiling", "qt_plan_kernel_times", "qt_plan_energy_static",
+    "qt_static_scratch_bytes",
 ]
 
 
@@ -78,6 +79,7 @@ def lib():
             "qt_energy": [C.POINTER(qt_graph), i32, pd, pd, i32, i32, vp, vp, sz, pd, pd],
             "qt_plan_set_profiling": [vp, i32],
             "qt_plan_kernel_times": [vp, C.POINTER(C.c_float), i32, pi32],
+            "qt_plan_energy_static": [vp, vp, vp, vp, vp, vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -91,6 +93,8 @@ def lib():
         L.qt_plan_free.restype = None
         L.qt_plan_options_default.argtypes = [C.POINTER(qt_plan_options)]
         L.qt_plan_options_default.restype = None
+        L.qt_static_scratch_bytes.argtypes = []
+        L.qt_static_scratch_bytes.restype = C.c_size_t
         _lib = L
     return _lib
 
@@ -226,6 +230,18 @@ def qt_plan_kernel_times(plan, cap=4096):
     n = C.c_int32()
     _check(lib().qt_plan_kernel_times(plan, ms, int(cap), C.byref(n)))
     return [ms[i] for i in range(n.value)]
+
+
+def qt_plan_energy_static(plan, gamma_ptr, beta_ptr, energy_ptr, edge_zz_ptr, stream):
+    """Device-pointer call that uses the library's built-in scratch array
+    instead of a caller workspace (allocates no device memory)."""
+    vp = C.c_void_p
+    _check(lib().qt_plan_energy_static(plan, vp(gamma_ptr), vp(beta_ptr), vp(energy_ptr),
+                                       vp(edge_zz_ptr or None), vp(stream)))
+
+
+def qt_static_scratch_bytes():
+    return lib().qt_static_scratch_bytes()
 
 
 def qt_plan_free(plan):
