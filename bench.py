@@ -181,6 +181,7 @@ def run_ours(args):
 
     n, edges, p, _, _ = workload(WORKLOAD["name"])
     B = WORKLOAD["batch"]
+    profile_only = (WORKLOAD["name"], B) != ("n100_p4", 64)
     gamma, beta = random_angles(B, p, 1002 + 7919 * rank)
     t_plan = time.perf_counter()
     plan = EnergyPlan(n, edges, p, batch=B, dtype=WORKLOAD["dtype"], mode="persistent", device=dev)
@@ -245,7 +246,7 @@ def run_ours(args):
         res = {
             "metric": METRIC, "value": units * world / (ms * 1e-3), "unit": "edge_evals/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": WORKLOAD["dtype"],
             "data": "synthetic",
             "config": {"workload": "random 3-regular N=100 p=4 (seed 2), 150 edge lightcones x 64 angle sets, "
                                    "complex64 + FP64 sums, persistent launch",
@@ -262,6 +263,8 @@ def run_ours(args):
             "gpu_launches": 4 * args.steps,
             "clocks": clk,
         }
+        if profile_only:
+            res["profile_only"] = f"{WORKLOAD} (not the bench workload)"
         if not args.no_cpu_baseline:
             res["cpu_baseline"] = cpu_baseline()
         print(json.dumps(res))
@@ -276,7 +279,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch", type=int, default=None, help="profiling only: angle sets per GPU")
+    ap.add_argument("--workload", default=None, help="profiling only: named workload of workloads.py")
+    ap.add_argument("--dtype", default=None, choices=["c64", "c128"], help="profiling only")
     args = ap.parse_args()
+    for key in ("batch", "workload", "dtype"):
+        val = getattr(args, key)
+        if val is not None:
+            WORKLOAD["name" if key == "workload" else key] = val
+            args.no_cpu_baseline = True
     (ROOT / "gpurun_out").mkdir(exist_ok=True)
     if args.impl == "reference":
         run_reference(args)

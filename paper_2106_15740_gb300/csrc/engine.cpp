@@ -88,6 +88,8 @@ void fill_runs(uint32_t mask, DevInput* in) {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+constexpr int32_t kMaxGroup = 4096;  // buckets in one single-tile group task
+
 }  // namespace
 
 qt_status compile_plan(Plan* P) {
@@ -96,7 +98,6 @@ qt_status compile_plan(Plan* P) {
   const int64_t al = 256 / es;  // elements per 256 bytes
   auto align_el = [&](int64_t x) { return (x + al - 1) / al * al; };
   const int32_t n_edges = (int32_t)P->edges.size();
-  const int vb = vector_width(P->opt.dtype, B);
 
   // Per-edge memory plans.
   std::vector<std::vector<int64_t>> out_off(n_edges);
@@ -218,6 +219,7 @@ qt_status compile_plan(Plan* P) {
           d.in[k].off = sb.out_rank == 0 ? scal_base + out_off[e][src] : arena_base + edge_base[e] + out_off[e][src];
         } else {
           d.in[k].off = leaf_off[e][i];
+          d.in[k].flags = kInLeaf;
           DevLeafFactor lf;
           std::memset(&lf, 0, sizeof(lf));
           lf.off = leaf_off[e][i];
@@ -243,7 +245,8 @@ qt_status compile_plan(Plan* P) {
 
   // Persistent queue.
   P->tasks.clear();
-  P->tile_items = 256 * 16;
+  const TileGeom geom = tile_geom(P->opt.dtype, B);
+  P->tile_items = geom.R;
   if (persistent) {
     const int32_t S = P->n_slots;
     std::vector<size_t> ei(S, 0);
@@ -255,17 +258,30 @@ qt_status compile_plan(Plan* P) {
         if (ei[s] >= slot_edges[s].size()) continue;
         any = true;
         const int32_t e = slot_edges[s][ei[s]];
+        const int32_t nb_e = (int32_t)P->edges[e].buckets.size();
         const int32_t gb = P->edge_first[e] + bi[s];
         DevBucket& d = P->buckets[gb];
-        const int64_t items = B == 1 ? d.n_rows : d.n_rows * (B / vb);
-        const int64_t nt = (items + P->tile_items - 1) / P->tile_items;
+        const int64_t nt = (d.n_rows + geom.R - 1) / geom.R;
         if (nt > INT32_MAX / 2) return fail(QT_EWIDTH, "bucket too large for the task queue");
-        d.ntask = (int32_t)nt;
         d.dep = prev[s];
-        for (int32_t t = 0; t < d.ntask; ++t) P->tasks.push_back(DevTask{gb, t});
+        if (nt == 1) {
+          // group the run of single-tile buckets that starts here
+          int32_t k = 1;
+          while (bi[s] + k < nb_e && k < kMaxGroup && P->buckets[gb + k].n_rows <= geom.R) ++k;
+          for (int32_t j = 0; j < k; ++j) {
+            P->buckets[gb + j].ntask = 1;
+            if (j > 0) P->buckets[gb + j].dep = -1;
+          }
+          P->tasks.push_back(DevTask{gb, -k});
+          prev[s] = gb + k - 1;
+          bi[s] += k - 1;  // the increment below moves past the group
+        } else {
+          d.ntask = (int32_t)nt;
+          for (int32_t t = 0; t < d.ntask; ++t) P->tasks.push_back(DevTask{gb, t});
+          prev[s] = gb;
+        }
         if ((int64_t)P->tasks.size() > INT32_MAX / 2) return fail(QT_EWIDTH, "task queue too long");
-        prev[s] = gb;
-        if (++bi[s] == (int32_t)P->edges[e].buckets.size()) {
+        if (++bi[s] == nb_e) {
           bi[s] = 0;
           ++ei[s];
         }
@@ -375,8 +391,8 @@ qt_status run_plan(Plan* P, const double* gamma, const double* beta, double* ene
     QT_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
     const int32_t grid = std::max(1, per_sm) * n_sm;
     QT_CUDA(launch_persistent(dtype, dbk, (const DevTask*)(base + L.tasks), (int32_t)P->tasks.size(),
-                              (DevCtrl*)(base + L.ctrl), (int32_t*)(base + L.done), B, data, P->tile_items, grid,
-                              1 << 25, s));
+                              (DevCtrl*)(base + L.ctrl), (int32_t*)(base + L.done), B, data, P->data_elems, grid,
+                              P->spin_limit, s));
   } else {
     int n_sm = 0;
     QT_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
@@ -395,6 +411,10 @@ qt_status check_plan(Plan* P, void* stream) {
   const void* ws = P->bound_ws;
   DevCtrl c;
   QT_CUDA(cudaMemcpy(&c, (const char*)ws + P->ws.ctrl, sizeof(c), cudaMemcpyDeviceToHost));
+  if (c.bad_kind != 0)
+    return fail(QT_EINVAL, "device check: kind " + std::to_string(c.bad_kind) + " bucket " +
+                               std::to_string(c.bad_bucket) + " input " + std::to_string(c.bad_input) + " index " +
+                               std::to_string(c.bad_index));
   if (c.status == QT_ETIMEOUT)
     return fail(QT_ETIMEOUT, "persistent queue wait timed out on bucket " + std::to_string(c.spins));
   if (c.status != 0) return fail((qt_status)c.status, "device reported an error");

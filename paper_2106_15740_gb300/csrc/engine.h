@@ -35,7 +35,8 @@ struct Plan {
   std::vector<DevTask> tasks;
   std::vector<int64_t> scal_off;           // element offsets of scalar results
   std::vector<int32_t> scal_begin;         // CSR over edges
-  int64_t tile_items = 0;
+  int64_t tile_items = 0;                  // output rows per warp tile
+  int32_t spin_limit = 1 << 22;            // polls of a bounded dependency wait
   int32_t n_slots = 0;
   int64_t data_elems = 0;
   WsLayout ws;

@@ -81,76 +81,110 @@ __global__ void leaf_factor_kernel(const DevLeafFactor* __restrict__ lf, int32_t
   }
 }
 
-// One launch per bucket (the plain per-bucket path).
+// One launch per bucket (the plain per-bucket path): warp w of the grid
+// takes tiles w, w + n_warps, ... of the bucket.
 template <class Real, int VB, bool PAIR>
-__global__ void __launch_bounds__(256) bucket_kernel(const DevBucket d, Real* __restrict__ data,
-                                                     int32_t B, int32_t bshift, int64_t n_items) {
-  bucket_range<Real, VB, PAIR, false>(d, data, B, bshift, 0, n_items,
-                                      (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
-                                      (int64_t)gridDim.x * blockDim.x);
+__global__ void __launch_bounds__(256, 4) bucket_kernel(const DevBucket d, Real* __restrict__ data, const TileGeom g,
+                                                     int64_t n_tiles) {
+  __shared__ WarpTile tiles[8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  WarpTile* w = &tiles[wid];
+  load_bucket(&w->d, &d, lane);
+  __syncwarp();
+  lane_parts(w, g, lane);
+  __syncwarp();
+  const int64_t n_warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid; t < n_tiles; t += n_warps) {
+    const int64_t r0 = t * g.R;
+    const int64_t r1 = r0 + g.R < d.n_rows ? r0 + g.R : d.n_rows;
+    warp_tile<Real, VB, PAIR, false>(w, data, g, r0, r1, lane);
+    __syncwarp();
+  }
 }
 
 __device__ __forceinline__ int32_t ld_acquire(const int32_t* p) {
   int32_t v;
-  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  asm volatile("ld.acquire.gpu.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
 
-// Persistent queue: CTAs take tasks (bucket tile) in queue order.  A task
-// first waits until its bucket's predecessor (the previous bucket of the
-// same edge chain) has all its tiles done.  Every predecessor comes earlier
-// in the queue, so it was taken by a CTA that is running, and the wait ends.
-// The wait is bounded: after `spin_limit` polls it records QT_ETIMEOUT and
-// every CTA stops taking tasks.
+// Persistent queue, one task = one warp tile or one group of single-tile
+// buckets.  Each warp takes tasks in queue order (lane 0: atomicAdd on the
+// queue head, issued one task ahead so its latency overlaps a tile), waits
+// until the task's bucket's predecessor in its edge chain has all its tiles
+// done, evaluates the tile(s) and counts the bucket's tile done.  Every
+// awaited tile comes earlier in the queue and is held by a running warp that
+// only waits on still earlier tiles, so every wait ends.  Waits are bounded:
+// after `spin_limit` polls (or as soon as another warp has failed) the warp
+// records QT_ETIMEOUT in the control word and no warp takes a task after that.
+// Consecutive tiles of one bucket on a warp reuse its record and skip the
+// wait (done counters only grow).
 template <class Real, int VB, bool PAIR>
-__global__ void __launch_bounds__(256) persistent_kernel(const DevBucket* __restrict__ buckets,
-                                                         const DevTask* __restrict__ tasks, int32_t n_tasks,
-                                                         DevCtrl* ctrl, int32_t* done, Real* __restrict__ data,
-                                                         int32_t B, int32_t bshift, int64_t tile_items,
-                                                         int32_t spin_limit) {
-  __shared__ DevBucket sd;
-  __shared__ int32_t s_task;
-  for (;;) {
-    if (threadIdx.x == 0) {
-      int32_t t = n_tasks;
-      if (*((volatile int32_t*)&ctrl->status) == 0) t = atomicAdd(&ctrl->head, 1);
-      if (t < n_tasks) {
-        const int32_t dep = buckets[tasks[t].bucket].dep;
+__global__ void __launch_bounds__(256, 4) persistent_kernel(const DevBucket* __restrict__ buckets,
+                                                            const DevTask* __restrict__ tasks, int32_t n_tasks,
+                                                            DevCtrl* ctrl, int32_t* done, Real* __restrict__ data,
+                                                            const TileGeom g, int32_t spin_limit) {
+  __shared__ WarpTile tiles[8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  WarpTile* w = &tiles[wid];
+  // Lane 0 makes every scheduling decision; the warp acts on broadcasts.
+  int32_t t = 0, cached = -1;  // cached: bucket whose record and lane parts are in *w
+  if (lane == 0) t = atomicAdd(&ctrl->head, 1);
+  t = __shfl_sync(0xffffffffu, t, 0);
+  while (t < n_tasks) {
+    int32_t t_next = n_tasks, failed = 0;
+    const DevTask task = tasks[t];
+    if (lane == 0) {
+      if (*((volatile int32_t*)&ctrl->status) == 0) t_next = atomicAdd(&ctrl->head, 1);
+      if (task.bucket != cached) {
+        const int32_t dep = buckets[task.bucket].dep;
         if (dep >= 0) {
           const int32_t need = buckets[dep].ntask;
           int32_t polls = 0;
           while (ld_acquire(done + dep) < need) {
-            if (++polls > spin_limit) {
-              atomicCAS(&ctrl->status, 0, (int32_t)QT_ETIMEOUT);
-              ctrl->spins = dep;
-              t = n_tasks;
+            ++polls;
+            if (polls > spin_limit || ((polls & 63) == 0 && *((volatile int32_t*)&ctrl->status) != 0)) {
+              if (atomicCAS(&ctrl->status, 0, (int32_t)QT_ETIMEOUT) == 0) ctrl->spins = dep;
+              failed = 1;
               break;
             }
-            __nanosleep(64);
+            __nanosleep(100);
           }
         }
       }
-      s_task = t;
     }
-    __syncthreads();
-    const int32_t t = s_task;
-    if (t >= n_tasks) break;
-    const DevTask task = tasks[t];
-    {
-      const int32_t* src = reinterpret_cast<const int32_t*>(buckets + task.bucket);
-      int32_t* dst = reinterpret_cast<int32_t*>(&sd);
-      for (int32_t i = threadIdx.x; i < (int32_t)(sizeof(DevBucket) / 4); i += blockDim.x) dst[i] = src[i];
+    failed = __shfl_sync(0xffffffffu, failed, 0);
+    t_next = __shfl_sync(0xffffffffu, t_next, 0);
+    if (failed) break;
+    const int32_t n_group = task.tile < 0 ? -task.tile : 1;
+    for (int32_t k = 0; k < n_group; ++k) {
+      const int32_t b = task.bucket + k;
+      if (b != cached) {  // uniform: every lane holds the same b and cached
+        load_bucket(&w->d, buckets + b, lane);
+        __syncwarp();
+        lane_parts(w, g, lane);
+        __syncwarp();
+        cached = b;
+      }
+#ifdef QT_DEVICE_CHECKS
+      if (w->d.n_in < 1 || w->d.n_in > kDevMaxIn || w->d.n_rows < 1) {
+        if (lane == 0 && atomicCAS(&ctrl->bad_kind, 0, 4) == 0) {
+          ctrl->bad_bucket = b;
+          ctrl->bad_index = w->d.n_in;
+          atomicCAS(&ctrl->status, 0, (int32_t)QT_EINVAL);
+        }
+        break;
+      }
+#endif
+      const int64_t r0 = task.tile < 0 ? 0 : (int64_t)task.tile * g.R;
+      const int64_t r1 = r0 + g.R < w->d.n_rows ? r0 + g.R : w->d.n_rows;
+      warp_tile<Real, VB, PAIR, true>(w, data, g, r0, r1, lane, ctrl, b);
+      __syncwarp();  // the next bucket of a group reads what this one wrote
     }
-    __syncthreads();
-    const int64_t n_items = PAIR ? sd.n_rows : sd.n_rows * (B / VB);
-    const int64_t e0 = (int64_t)task.tile * tile_items;
-    const int64_t e1 = e0 + tile_items < n_items ? e0 + tile_items : n_items;
-    bucket_range<Real, VB, PAIR, true>(sd, data, B, bshift, e0, e1, threadIdx.x, blockDim.x);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
-      atomicAdd(done + task.bucket, 1);
-    }
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) atomicAdd(done + task.bucket + n_group - 1, 1);
+    t = t_next;
   }
 }
 
@@ -186,12 +220,6 @@ __global__ void energy_kernel(const Real* __restrict__ data, const int64_t* __re
 
 // ------------------------------------------------------------- launchers ---
 
-static int items_shift(int32_t B, int vb) {
-  const int32_t per = B / vb;
-  if (per <= 0 || (per & (per - 1))) return -1;
-  return __builtin_ctz((unsigned)per);
-}
-
 cudaError_t launch_trig(const double* gamma, const double* beta, int32_t p, int32_t B, double* trig,
                         cudaStream_t s) {
   const int32_t n = B * p;
@@ -212,54 +240,77 @@ cudaError_t launch_leaf_factors(int dtype, const DevLeafFactor* lf, int32_t n_lf
 
 int vector_width(int dtype, int32_t B) { return (dtype == QT_C64 && B > 1 && B % 2 == 0) ? 2 : 1; }
 
+TileGeom tile_geom(int dtype, int32_t B) {
+  TileGeom g;
+  const int vb = vector_width(dtype, B);
+  g.B = B;
+  g.Bv = B == 1 ? 1 : B / vb;
+  if (g.Bv <= 32) {
+    int rp = 1;
+    while (rp * 2 * g.Bv <= 32) rp *= 2;
+    g.RP = rp;
+    g.VC = 1;
+  } else {
+    g.RP = 1;
+    g.VC = (g.Bv + 31) / 32;
+  }
+  int P = 1;
+  while (P * 2 * g.VC <= kLaneItems) P *= 2;
+  g.P = P;
+  g.R = P * g.RP;
+  g.data_elems = 0;
+  return g;
+}
+
 cudaError_t launch_bucket(int dtype, const DevBucket& d, int32_t B, void* data, int32_t max_blocks,
                           cudaStream_t s) {
   const int vb = vector_width(dtype, B);
   const bool pair = (B == 1);
-  const int64_t n_items = pair ? d.n_rows : d.n_rows * (B / vb);
-  const int bshift = items_shift(B, vb);
-  int64_t blocks = (n_items + 255) / 256;
+  const TileGeom g = tile_geom(dtype, B);
+  const int64_t n_tiles = (d.n_rows + g.R - 1) / g.R;
+  int64_t blocks = (n_tiles + 7) / 8;
   if (blocks > max_blocks) blocks = max_blocks;
   if (blocks < 1) blocks = 1;
   if (dtype == QT_C64) {
     if (pair)
-      dev::bucket_kernel<float, 1, true><<<(int)blocks, 256, 0, s>>>(d, (float*)data, B, bshift, n_items);
+      dev::bucket_kernel<float, 1, true><<<(int)blocks, 256, 0, s>>>(d, (float*)data, g, n_tiles);
     else if (vb == 2)
-      dev::bucket_kernel<float, 2, false><<<(int)blocks, 256, 0, s>>>(d, (float*)data, B, bshift, n_items);
+      dev::bucket_kernel<float, 2, false><<<(int)blocks, 256, 0, s>>>(d, (float*)data, g, n_tiles);
     else
-      dev::bucket_kernel<float, 1, false><<<(int)blocks, 256, 0, s>>>(d, (float*)data, B, bshift, n_items);
+      dev::bucket_kernel<float, 1, false><<<(int)blocks, 256, 0, s>>>(d, (float*)data, g, n_tiles);
   } else {
     if (pair)
-      dev::bucket_kernel<double, 1, true><<<(int)blocks, 256, 0, s>>>(d, (double*)data, B, bshift, n_items);
+      dev::bucket_kernel<double, 1, true><<<(int)blocks, 256, 0, s>>>(d, (double*)data, g, n_tiles);
     else
-      dev::bucket_kernel<double, 1, false><<<(int)blocks, 256, 0, s>>>(d, (double*)data, B, bshift, n_items);
+      dev::bucket_kernel<double, 1, false><<<(int)blocks, 256, 0, s>>>(d, (double*)data, g, n_tiles);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_persistent(int dtype, const DevBucket* buckets, const DevTask* tasks, int32_t n_tasks,
-                              DevCtrl* ctrl, int32_t* done, int32_t B, void* data, int64_t tile_items,
+                              DevCtrl* ctrl, int32_t* done, int32_t B, void* data, int64_t data_elems,
                               int32_t grid, int32_t spin_limit, cudaStream_t s) {
   const int vb = vector_width(dtype, B);
   const bool pair = (B == 1);
-  const int bshift = items_shift(B, vb);
+  TileGeom g = tile_geom(dtype, B);
+  g.data_elems = data_elems;
   if (dtype == QT_C64) {
     if (pair)
       dev::persistent_kernel<float, 1, true><<<grid, 256, 0, s>>>(buckets, tasks, n_tasks, ctrl, done,
-                                                                  (float*)data, B, bshift, tile_items, spin_limit);
+                                                                  (float*)data, g, spin_limit);
     else if (vb == 2)
       dev::persistent_kernel<float, 2, false><<<grid, 256, 0, s>>>(buckets, tasks, n_tasks, ctrl, done,
-                                                                   (float*)data, B, bshift, tile_items, spin_limit);
+                                                                   (float*)data, g, spin_limit);
     else
       dev::persistent_kernel<float, 1, false><<<grid, 256, 0, s>>>(buckets, tasks, n_tasks, ctrl, done,
-                                                                   (float*)data, B, bshift, tile_items, spin_limit);
+                                                                   (float*)data, g, spin_limit);
   } else {
     if (pair)
       dev::persistent_kernel<double, 1, true><<<grid, 256, 0, s>>>(buckets, tasks, n_tasks, ctrl, done,
-                                                                   (double*)data, B, bshift, tile_items, spin_limit);
+                                                                   (double*)data, g, spin_limit);
     else
       dev::persistent_kernel<double, 1, false><<<grid, 256, 0, s>>>(buckets, tasks, n_tasks, ctrl, done,
-                                                                    (double*)data, B, bshift, tile_items, spin_limit);
+                                                                    (double*)data, g, spin_limit);
   }
   return cudaGetLastError();
 }

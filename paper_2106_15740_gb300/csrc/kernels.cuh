@@ -19,6 +19,7 @@
 #include <cstdint>
 
 #include "qt_device.h"
+#include "qtensor.h"
 
 namespace qt {
 namespace dev {
@@ -122,69 +123,206 @@ __device__ __forceinline__ uint32_t pext_in(uint32_t y, const DevInput& in) {
   return k;
 }
 
-// Rows/vectors of one bucket in [e0, e1), work items split over `nthr` threads.
-// PAIR (B == 1): item = output row y.  Otherwise item = (y, v) with v the
-// vector of VB angle sets, items per row = B / VB = 1 << bshift when
-// bshift >= 0, else B / VB by division.
-template <class Real, int VB, bool PAIR, bool CG>
-__device__ __forceinline__ void bucket_range(const DevBucket& d, Real* __restrict__ data, int32_t B,
-                                             int32_t bshift, int64_t e0, int64_t e1, int64_t tid,
-                                             int64_t nthr) {
+#ifdef QT_DEVICE_CHECKS
+// Debug build: an element range outside the data region is recorded in the
+// control word (first failure wins) and the access is skipped.
+__device__ __forceinline__ bool qt_in_range(DevCtrl* ctrl, int64_t lo, int64_t span, int64_t n, int kind,
+                                            int bucket, int input) {
+  if (lo >= 0 && lo + span <= n) return true;
+  if (ctrl && atomicCAS(&ctrl->bad_kind, 0, kind) == 0) {
+    ctrl->bad_bucket = bucket;
+    ctrl->bad_input = input;
+    ctrl->bad_index = lo;
+    atomicCAS(&ctrl->status, 0, (int32_t)QT_EINVAL);
+  }
+  return false;
+}
+#define QT_RANGE_OK(lo, span, kind, input) qt_in_range(ctrl, (lo), (span), g.data_elems, (kind), dbg_bucket, (input))
+#else
+#define QT_RANGE_OK(lo, span, kind, input) true
+#endif
+
+// Per-warp shared state of one tile: the bucket record and the pass table
+// tab[i][p] = pext(r0 + p * RP, mask_i).
+struct WarpTile {
+  DevBucket d;
+  uint32_t tab[kDevMaxIn][kLaneItems];
+  uint32_t lpart[kDevMaxIn][32];  // pext(i_lane, mask) per input and lane
+};
+
+// Copy a bucket record into the warp's shared slot with typed member
+// assignments (lane i < n_in copies input i, lane 31 the header), so every
+// later read of the slot sees the stores through its own type.  Call with
+// all 32 lanes; the caller synchronises the warp before reading the slot.
+__device__ __forceinline__ void load_bucket(DevBucket* dst, const DevBucket* src, int lane) {
+  const int n_in = src->n_in;
+  if (lane < kDevMaxIn && lane < n_in) dst->in[lane] = src->in[lane];
+  if (lane == 31) {
+    dst->out_off = src->out_off;
+    dst->n_rows = src->n_rows;
+    dst->out_rank = src->out_rank;
+    dst->n_in = n_in;
+    dst->dep = src->dep;
+    dst->ntask = src->ntask;
+  }
+}
+
+template <class Real, bool CG>
+__device__ __forceinline__ Pack<Real, 2> ldpair_in(const Real* data, int64_t e, bool leaf) {
+  return leaf ? ldpair<Real, false>(data, e) : ldpair<Real, CG>(data, e);
+}
+template <class Real, int VB, bool CG>
+__device__ __forceinline__ Pack<Real, VB> ldv_in(const Real* data, int64_t e, bool leaf) {
+  return leaf ? ldv<Real, VB, false>(data, e) : ldv<Real, VB, CG>(data, e);
+}
+
+// One warp evaluates output rows [r0, r1) of the bucket in w->d (all B angle
+// sets).  r0 is a multiple of g.R.  Each lane keeps pext(i_lane, mask) per
+// input in registers; per item an input row is one broadcast table read plus
+// one add, then two loads (x = 0 and x = 1), complex products in registers,
+// one add for the sum over x and one store.  Loads of U items are issued
+// before they are used.
+// Lane -> (row within a pass, vector) of the tile geometry.
+__device__ __forceinline__ void lane_slot(const TileGeom& g, int lane, int* rip, int* v0, bool* on) {
+  if (g.Bv <= 32) {
+    *rip = lane / g.Bv;
+    *v0 = lane - *rip * g.Bv;
+    *on = *rip < g.RP;
+  } else {
+    *rip = 0;
+    *v0 = lane;
+    *on = true;
+  }
+}
+
+// Per-lane part pext(i_lane, mask) of every input of the bucket in w->d,
+// into w->lpart.  Call with all 32 lanes after the record is in place; the
+// caller synchronises the warp before the parts are read.
+__device__ __forceinline__ void lane_parts(WarpTile* w, const TileGeom& g, int lane) {
+  int rip, v0;
+  bool on;
+  lane_slot(g, lane, &rip, &v0, &on);
+  const int n_in = w->d.n_in;
+  for (int i = 0; i < n_in; ++i) w->lpart[i][lane] = pext_in((uint32_t)rip, w->d.in[i]);
+}
+
+template <class Real, int VB, bool PAIR, bool CG, int U = 2>
+__device__ __forceinline__ void warp_tile(WarpTile* w, Real* __restrict__ data,
+                                          const TileGeom& g, int64_t r0, int64_t r1, int lane,
+                                          DevCtrl* ctrl = nullptr, int dbg_bucket = -1) {
+  (void)ctrl;
+  (void)dbg_bucket;
   using C = typename Cx<Real>::T;
-  const int32_t bv_per_row = B / VB;
+  const DevBucket& d = w->d;
   const int n_in = d.n_in;
-  for (int64_t e = e0 + tid; e < e1; e += nthr) {
-    int64_t y, bv;
-    if (PAIR) {
-      y = e;
-      bv = 0;
-    } else if (bshift >= 0) {
-      y = e >> bshift;
-      bv = e - (y << bshift);
-    } else {
-      y = e / bv_per_row;
-      bv = e - y * bv_per_row;
+  const int B = g.B;
+  int rip, v0;
+  bool lane_on;
+  lane_slot(g, lane, &rip, &v0, &lane_on);
+  // pass table: tab[i][p] = pext(r0 + p * RP, mask_i)
+  const int P = g.P;
+  for (int pp = lane; pp < P; pp += 32) {
+    const uint32_t yp = (uint32_t)(r0 + (int64_t)pp * g.RP);
+    for (int i = 0; i < n_in; ++i) w->tab[i][pp] = pext_in(yp, d.in[i]);
+  }
+  __syncwarp();
+  const uint32_t* lp_col = &w->lpart[0][lane];  // lp_col[32 * i] = part of input i
+  const int Q = P * g.VC;
+  for (int q0 = 0; q0 < Q; q0 += U) {
+    int pp[U];
+    uint32_t y[U];  // output rows < 2^31
+    int32_t vv[U];
+    bool ok[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int q = q0 + u;
+      const int p = q / g.VC;
+      const int vc = q - p * g.VC;
+      pp[u] = q < Q ? p : 0;
+      y[u] = (uint32_t)r0 + (uint32_t)(pp[u] * g.RP + rip);
+      vv[u] = vc * 32 + v0;
+      ok[u] = lane_on && q < Q && (int64_t)y[u] < r1 && (g.Bv <= 32 || vv[u] < g.Bv);
+      if (!ok[u]) {  // idle items recompute a valid element and do not store
+        y[u] = (uint32_t)r0;
+        vv[u] = 0;
+      }
     }
     if (PAIR) {
-      C p0, p1;
-      for (int i = 0; i < n_in; ++i) {
-        const DevInput& in = d.in[i];
-        const int64_t r0 = in.off + 2 * (int64_t)pext_in((uint32_t)y, in);
-        const Pack<Real, 2> q = ldpair<Real, CG>(data, r0);  // rows x = 0 and x = 1
-        const C a0 = q.c[0], a1 = q.c[1];
-        if (i == 0) {
-          p0 = a0;
-          p1 = a1;
-        } else {
-          p0 = cmul<Real>(p0, a0);
-          p1 = cmul<Real>(p1, a1);
-        }
-      }
-      Pack<Real, 1> o{{cadd<Real>(p0, p1)}};
-      stv<Real, 1>(data, d.out_off + y, o);
-    } else {
-      Pack<Real, VB> p0, p1;
-      for (int i = 0; i < n_in; ++i) {
-        const DevInput& in = d.in[i];
-        const int64_t r0 = 2 * (int64_t)pext_in((uint32_t)y, in);
-        const int64_t base = in.off + r0 * B + bv * VB;
-        Pack<Real, VB> a0 = ldv<Real, VB, CG>(data, base);
-        Pack<Real, VB> a1 = ldv<Real, VB, CG>(data, base + B);
-        if (i == 0) {
-          p0 = a0;
-          p1 = a1;
-        } else {
+      C p0[U], p1[U];
 #pragma unroll
-          for (int v = 0; v < VB; ++v) {
-            p0.c[v] = cmul<Real>(p0.c[v], a0.c[v]);
-            p1.c[v] = cmul<Real>(p1.c[v], a1.c[v]);
+      for (int i = 0; i < kDevMaxIn; ++i) {
+        if (i >= n_in) break;
+        const int64_t off = d.in[i].off;
+        const bool leaf = d.in[i].flags & kInLeaf;
+        Pack<Real, 2> a[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const uint32_t k = ok[u] ? w->tab[i][pp[u]] + lp_col[32 * i] : 0u;
+          if (QT_RANGE_OK(off + 2 * (int64_t)k, 2, 1, i))
+            a[u] = ldpair_in<Real, CG>(data, off + 2 * (int64_t)k, leaf);
+          else
+            a[u] = Pack<Real, 2>{};
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (i == 0) {
+            p0[u] = a[u].c[0];
+            p1[u] = a[u].c[1];
+          } else {
+            p0[u] = cmul<Real>(p0[u], a[u].c[0]);
+            p1[u] = cmul<Real>(p1[u], a[u].c[1]);
           }
         }
       }
-      Pack<Real, VB> o;
 #pragma unroll
-      for (int v = 0; v < VB; ++v) o.c[v] = cadd<Real>(p0.c[v], p1.c[v]);
-      stv<Real, VB>(data, d.out_off + y * B + bv * VB, o);
+      for (int u = 0; u < U; ++u) {
+        if (!ok[u]) continue;
+        Pack<Real, 1> o{{cadd<Real>(p0[u], p1[u])}};
+        if (QT_RANGE_OK(d.out_off + (int64_t)y[u], 1, 2, -1)) stv<Real, 1>(data, d.out_off + (int64_t)y[u], o);
+      }
+    } else {
+      Pack<Real, VB> p0[U], p1[U];
+#pragma unroll
+      for (int i = 0; i < kDevMaxIn; ++i) {
+        if (i >= n_in) break;
+        const int64_t off = d.in[i].off;
+        const bool leaf = d.in[i].flags & kInLeaf;
+        Pack<Real, VB> a0[U], a1[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const uint32_t k = ok[u] ? w->tab[i][pp[u]] + lp_col[32 * i] : 0u;
+          const int64_t base = off + (int64_t)(2 * k) * B + (int64_t)(vv[u] * VB);
+          if (QT_RANGE_OK(base, B + VB, 1, i)) {
+            a0[u] = ldv_in<Real, VB, CG>(data, base, leaf);
+            a1[u] = ldv_in<Real, VB, CG>(data, base + B, leaf);
+          } else {
+            a0[u] = Pack<Real, VB>{};
+            a1[u] = Pack<Real, VB>{};
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (i == 0) {
+            p0[u] = a0[u];
+            p1[u] = a1[u];
+          } else {
+#pragma unroll
+            for (int v = 0; v < VB; ++v) {
+              p0[u].c[v] = cmul<Real>(p0[u].c[v], a0[u].c[v]);
+              p1[u].c[v] = cmul<Real>(p1[u].c[v], a1[u].c[v]);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (!ok[u]) continue;
+        Pack<Real, VB> o;
+#pragma unroll
+        for (int v = 0; v < VB; ++v) o.c[v] = cadd<Real>(p0[u].c[v], p1[u].c[v]);
+        if (QT_RANGE_OK(d.out_off + (int64_t)y[u] * B + (int64_t)(vv[u] * VB), VB, 2, -1))
+          stv<Real, VB>(data, d.out_off + (int64_t)y[u] * B + (int64_t)(vv[u] * VB), o);
+      }
     }
   }
 }

@@ -24,6 +24,25 @@ struct DevInput {
   uint32_t mask;
   int32_t nruns;
   uint32_t run[kDevMaxRuns];   // src | len << 8 | dst << 16
+  int32_t flags;               // kInLeaf: written before the launch, read through L1
+  int32_t pad;
+};
+constexpr int32_t kInLeaf = 1;
+
+// Work split of a bucket into warp tiles (same for every bucket of a plan,
+// fixed by B).  A warp tile covers R = P * RP consecutive output rows,
+// R a power of two and tiles aligned to R, so for row y = r0 + p*RP + i
+// (i < RP) the input index pext(y) = pext(r0 + p*RP) + pext(i) with no carry:
+// the first term is one table entry per pass, the second one register per lane.
+//   Bv = vectors of VB angle sets per row (1 for B == 1)
+//   Bv <= 32: RP = largest power of two <= 32 / Bv rows per pass; lane ->
+//             (row i = lane / Bv, vector lane % Bv); lanes >= RP * Bv idle
+//   Bv >  32: RP = 1; VC = ceil(Bv / 32) vector chunks per row
+//   P = passes per tile (power of two), P * VC <= kLaneItems
+constexpr int kLaneItems = 64;
+struct TileGeom {
+  int32_t B, Bv, RP, VC, P, R;
+  int64_t data_elems;  // size of the data region, for the QT_DEVICE_CHECKS build
 };
 
 struct DevBucket {
@@ -46,7 +65,10 @@ struct DevLeafFactor {
   uint32_t leaf[kDevMaxLeaves];
 };
 
-// Persistent-queue task: tile `tile` of bucket `bucket`.
+// Persistent-queue task.  tile >= 0: tile `tile` of bucket `bucket`.
+// tile < 0: a group of -tile consecutive buckets of one edge chain, starting
+// at `bucket`, each small enough for a single tile; one warp runs them in
+// order with no global synchronisation between them.
 struct DevTask {
   int32_t bucket;
   int32_t tile;
@@ -57,7 +79,10 @@ struct DevCtrl {
   int32_t head;      // next task of the persistent queue
   int32_t status;    // 0 ok, else a qt_status set by the device
   int32_t spins;     // diagnostic: bucket index of the wait that timed out
-  int32_t pad;
+  int32_t bad_kind;  // QT_DEVICE_CHECKS build: 1 load, 2 store, 3 record; 0 none
+  int32_t bad_bucket;
+  int32_t bad_input;
+  int64_t bad_index;
 };
 
 }  // namespace qt
