@@ -181,15 +181,17 @@ def run_ours(args):
 
     n, edges, p, _, _ = workload(WORKLOAD["name"])
     B = WORKLOAD["batch"]
-    profile_only = (WORKLOAD["name"], B) != ("n100_p4", 64)
+    profile_only = (WORKLOAD["name"], B) != ("n100_p4", 64) or "edge_range" in WORKLOAD or "lane_items" in WORKLOAD
     gamma, beta = random_angles(B, p, 1002 + 7919 * rank)
     t_plan = time.perf_counter()
-    plan = EnergyPlan(n, edges, p, batch=B, dtype=WORKLOAD["dtype"], mode="persistent", device=dev)
+    plan = EnergyPlan(n, edges, p, batch=B, dtype=WORKLOAD["dtype"], mode="persistent", device=dev,
+                      edge_range=WORKLOAD.get("edge_range"), lane_items=WORKLOAD.get("lane_items", 0),
+                      group_rows=WORKLOAD.get("group_rows", 0))
     t_plan = time.perf_counter() - t_plan
     g = torch.tensor(gamma, device=dev)
     b = torch.tensor(beta, device=dev)
     out = torch.empty(B, dtype=torch.float64, device=dev)
-    units = len(edges) * B
+    units = plan.n_edges * B
 
     for _ in range(args.warmup):
         plan.energy(g, b, out=out)
@@ -282,7 +284,17 @@ def main():
     ap.add_argument("--batch", type=int, default=None, help="profiling only: angle sets per GPU")
     ap.add_argument("--workload", default=None, help="profiling only: named workload of workloads.py")
     ap.add_argument("--dtype", default=None, choices=["c64", "c128"], help="profiling only")
+    ap.add_argument("--edges", default=None, help="profiling only: edge range a:b of the graph")
+    ap.add_argument("--lane-items", type=int, default=0, help="profiling only: warp tile items per lane")
+    ap.add_argument("--group-rows", type=int, default=0, help="profiling only: grouping threshold")
     args = ap.parse_args()
+    if args.edges:
+        a, b = (int(x) for x in args.edges.split(":"))
+        WORKLOAD["edge_range"] = (a, b)
+        args.no_cpu_baseline = True
+    if args.lane_items or args.group_rows:
+        WORKLOAD["lane_items"], WORKLOAD["group_rows"] = args.lane_items, args.group_rows
+        args.no_cpu_baseline = True
     for key in ("batch", "workload", "dtype"):
         val = getattr(args, key)
         if val is not None:

@@ -134,12 +134,19 @@ typedef struct {
   int32_t dtype;          /* qt_dtype */
   int32_t mode;           /* qt_mode */
   int32_t gradient;       /* 1: plan also computes dE/dgamma, dE/dbeta (adjoint sweep) */
-  int32_t max_width;      /* width budget; an edge above it fails with QT_EWIDTH (<=0: 34) */
-  int32_t pad_;
+  int32_t max_width;      /* width budget; an edge above it fails with QT_EWIDTH (<=0: 31) */
+  int32_t lane_items;     /* work items per lane in one warp tile: 8, 16, 32 or 64 (<=0: by batch) */
   int64_t max_workspace;  /* cap on workspace bytes (<=0: no cap); sets edge concurrency */
+  int32_t group_rows;     /* persistent mode: consecutive buckets of one edge with at most this many
+                             rows run back to back in one task (0: by batch, <0: never) */
+  int32_t edge_begin;     /* plan the edges [edge_begin, edge_end) of the graph; */
+  int32_t edge_end;       /* edge_end <= 0 means all edges from edge_begin on.  Energies and
+                             gradients then cover only those edges (a partial sum) */
+  int32_t reserved_;
 } qt_plan_options;
 
-/* Fill `opt` with defaults: batch 1, QT_C128, QT_MODE_PER_BUCKET, no gradient. */
+/* Fill `opt` with defaults: batch 1, QT_C128, QT_MODE_PER_BUCKET, no gradient,
+ * all edges, tile and grouping chosen by batch. */
 void qt_plan_options_default(qt_plan_options* opt);
 
 qt_status qt_plan_create(const qt_graph* g, int32_t p, const qt_plan_options* opt, qt_plan** out);

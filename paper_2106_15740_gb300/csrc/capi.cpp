@@ -24,10 +24,10 @@ static qt_status check_angles(const double* a, int64_t n, const char* name) {
 }
 
 // Build, order and bucket-plan every edge network of a graph.
-static qt_status plan_edges(const Graph& G, int32_t p, int32_t max_width, Plan* P) {
+static qt_status plan_edges(const Graph& G, int32_t p, int32_t max_width, int32_t e0, int32_t e1, Plan* P) {
   P->edges.clear();
   P->widths.clear();
-  for (int32_t e = 0; e < (int32_t)G.eu.size(); ++e) {
+  for (int32_t e = e0; e < e1; ++e) {
     Network net;
     build_lightcone(G, p, e, &net);
     std::vector<int32_t> order;
@@ -114,6 +114,7 @@ static qt_status contract_plan(const qt_network* net, const int32_t* order, qt_d
   qt_plan_options_default(&P->opt);
   P->opt.dtype = dtype;
   P->opt.mode = QT_MODE_PER_BUCKET;
+  P->opt.lane_items = 16;
   P->p = net->net.p;
   P->elem_bytes = dtype == QT_C64 ? 8 : 16;
   P->widths = {ep.width};
@@ -156,9 +157,13 @@ void qt_plan_options_default(qt_plan_options* opt) {
   opt->dtype = QT_C128;
   opt->mode = QT_MODE_PER_BUCKET;
   opt->gradient = 0;
-  opt->max_width = 34;
-  opt->pad_ = 0;
+  opt->max_width = 31;
+  opt->lane_items = 0;
   opt->max_workspace = 0;
+  opt->group_rows = 0;
+  opt->edge_begin = 0;
+  opt->edge_end = 0;
+  opt->reserved_ = 0;
 }
 
 qt_status qt_plan_create(const qt_graph* g, int32_t p, const qt_plan_options* opt, qt_plan** out) {
@@ -171,8 +176,10 @@ qt_status qt_plan_create(const qt_graph* g, int32_t p, const qt_plan_options* op
   if (o.dtype != QT_C128 && o.dtype != QT_C64) return fail(QT_EINVAL, "unknown dtype");
   if (o.mode != QT_MODE_PER_BUCKET && o.mode != QT_MODE_PERSISTENT) return fail(QT_EINVAL, "unknown mode");
   if (o.gradient) return fail(QT_EINVAL, "gradient plans are not available in this build");
-  if (o.max_width <= 0) o.max_width = 34;
-  if (o.max_width > 31) o.max_width = 31;
+  if (o.max_width <= 0 || o.max_width > 31) o.max_width = 31;
+  if (o.lane_items > 0 && o.lane_items != 8 && o.lane_items != 16 && o.lane_items != 32 && o.lane_items != 64)
+    return fail(QT_EINVAL, "lane_items must be 8, 16, 32 or 64");
+  if (o.lane_items <= 0) o.lane_items = o.batch >= 16 ? 32 : 16;
   qt_plan* h = new (std::nothrow) qt_plan;
   if (!h) return fail(QT_ENOMEM, "host allocation failed");
   qt_status st = make_graph(g, &h->P.G);
@@ -180,7 +187,15 @@ qt_status qt_plan_create(const qt_graph* g, int32_t p, const qt_plan_options* op
     h->P.p = p;
     h->P.opt = o;
     h->P.elem_bytes = o.dtype == QT_C64 ? 8 : 16;
-    st = plan_edges(h->P.G, p, o.max_width, &h->P);
+    const int32_t m = (int32_t)h->P.G.eu.size();
+    const int32_t e1 = o.edge_end <= 0 ? m : o.edge_end;
+    if (o.edge_begin < 0 || o.edge_begin >= e1 || e1 > m) {
+      st = fail(QT_EINVAL, "edge range out of bounds");
+    } else {
+      h->P.opt.edge_begin = o.edge_begin;
+      h->P.opt.edge_end = e1;
+      st = plan_edges(h->P.G, p, o.max_width, o.edge_begin, e1, &h->P);
+    }
   }
   if (st == QT_OK) st = compile_plan(&h->P);
   if (st != QT_OK) {

@@ -245,7 +245,11 @@ qt_status compile_plan(Plan* P) {
 
   // Persistent queue.
   P->tasks.clear();
-  const TileGeom geom = tile_geom(P->opt.dtype, B);
+  const TileGeom geom = tile_geom(P->opt.dtype, B, P->opt.lane_items);
+  // groups: runs of buckets with at most group_rows rows (default: at most
+  // 4 passes of a warp tile), never larger than one tile
+  int64_t group_rows = P->opt.group_rows == 0 ? 4 * (int64_t)geom.RP : (int64_t)P->opt.group_rows;
+  if (group_rows > geom.R) group_rows = geom.R;
   P->tile_items = geom.R;
   if (persistent) {
     const int32_t S = P->n_slots;
@@ -264,10 +268,10 @@ qt_status compile_plan(Plan* P) {
         const int64_t nt = (d.n_rows + geom.R - 1) / geom.R;
         if (nt > INT32_MAX / 2) return fail(QT_EWIDTH, "bucket too large for the task queue");
         d.dep = prev[s];
-        if (nt == 1) {
-          // group the run of single-tile buckets that starts here
+        if (nt == 1 && d.n_rows <= group_rows) {
+          // group the run of small buckets that starts here
           int32_t k = 1;
-          while (bi[s] + k < nb_e && k < kMaxGroup && P->buckets[gb + k].n_rows <= geom.R) ++k;
+          while (bi[s] + k < nb_e && k < kMaxGroup && P->buckets[gb + k].n_rows <= group_rows) ++k;
           for (int32_t j = 0; j < k; ++j) {
             P->buckets[gb + j].ntask = 1;
             if (j > 0) P->buckets[gb + j].dep = -1;
@@ -391,13 +395,13 @@ qt_status run_plan(Plan* P, const double* gamma, const double* beta, double* ene
     QT_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
     const int32_t grid = std::max(1, per_sm) * n_sm;
     QT_CUDA(launch_persistent(dtype, dbk, (const DevTask*)(base + L.tasks), (int32_t)P->tasks.size(),
-                              (DevCtrl*)(base + L.ctrl), (int32_t*)(base + L.done), B, data, P->data_elems, grid,
-                              P->spin_limit, s));
+                              (DevCtrl*)(base + L.ctrl), (int32_t*)(base + L.done), B, P->opt.lane_items, data,
+                              P->data_elems, grid, P->spin_limit, s));
   } else {
     int n_sm = 0;
     QT_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
     for (size_t i = 0; i < P->buckets.size(); ++i)
-      QT_CUDA(launch_bucket(dtype, P->buckets[i], B, data, n_sm * 8, s));
+      QT_CUDA(launch_bucket(dtype, P->buckets[i], B, P->opt.lane_items, data, n_sm * 8, s));
   }
   if (ev_stop) QT_CUDA(cudaEventRecord(ev_stop, s));
   QT_CUDA(launch_energy(dtype, data, (const int64_t*)(base + L.scal_off), (const int32_t*)(base + L.scal_begin),

@@ -240,7 +240,7 @@ cudaError_t launch_leaf_factors(int dtype, const DevLeafFactor* lf, int32_t n_lf
 
 int vector_width(int dtype, int32_t B) { return (dtype == QT_C64 && B > 1 && B % 2 == 0) ? 2 : 1; }
 
-TileGeom tile_geom(int dtype, int32_t B) {
+TileGeom tile_geom(int dtype, int32_t B, int32_t lane_items) {
   TileGeom g;
   const int vb = vector_width(dtype, B);
   g.B = B;
@@ -254,19 +254,20 @@ TileGeom tile_geom(int dtype, int32_t B) {
     g.RP = 1;
     g.VC = (g.Bv + 31) / 32;
   }
+  const int32_t cap = lane_items > 0 && lane_items <= kLaneItems ? lane_items : kLaneItems;
   int P = 1;
-  while (P * 2 * g.VC <= kLaneItems) P *= 2;
+  while (P * 2 * g.VC <= cap) P *= 2;
   g.P = P;
   g.R = P * g.RP;
   g.data_elems = 0;
   return g;
 }
 
-cudaError_t launch_bucket(int dtype, const DevBucket& d, int32_t B, void* data, int32_t max_blocks,
-                          cudaStream_t s) {
+cudaError_t launch_bucket(int dtype, const DevBucket& d, int32_t B, int32_t lane_items, void* data,
+                          int32_t max_blocks, cudaStream_t s) {
   const int vb = vector_width(dtype, B);
   const bool pair = (B == 1);
-  const TileGeom g = tile_geom(dtype, B);
+  const TileGeom g = tile_geom(dtype, B, lane_items);
   const int64_t n_tiles = (d.n_rows + g.R - 1) / g.R;
   int64_t blocks = (n_tiles + 7) / 8;
   if (blocks > max_blocks) blocks = max_blocks;
@@ -288,11 +289,11 @@ cudaError_t launch_bucket(int dtype, const DevBucket& d, int32_t B, void* data, 
 }
 
 cudaError_t launch_persistent(int dtype, const DevBucket* buckets, const DevTask* tasks, int32_t n_tasks,
-                              DevCtrl* ctrl, int32_t* done, int32_t B, void* data, int64_t data_elems,
-                              int32_t grid, int32_t spin_limit, cudaStream_t s) {
+                              DevCtrl* ctrl, int32_t* done, int32_t B, int32_t lane_items, void* data,
+                              int64_t data_elems, int32_t grid, int32_t spin_limit, cudaStream_t s) {
   const int vb = vector_width(dtype, B);
   const bool pair = (B == 1);
-  TileGeom g = tile_geom(dtype, B);
+  TileGeom g = tile_geom(dtype, B, lane_items);
   g.data_elems = data_elems;
   if (dtype == QT_C64) {
     if (pair)

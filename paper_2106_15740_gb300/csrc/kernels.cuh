@@ -176,12 +176,6 @@ __device__ __forceinline__ Pack<Real, VB> ldv_in(const Real* data, int64_t e, bo
   return leaf ? ldv<Real, VB, false>(data, e) : ldv<Real, VB, CG>(data, e);
 }
 
-// One warp evaluates output rows [r0, r1) of the bucket in w->d (all B angle
-// sets).  r0 is a multiple of g.R.  Each lane keeps pext(i_lane, mask) per
-// input in registers; per item an input row is one broadcast table read plus
-// one add, then two loads (x = 0 and x = 1), complex products in registers,
-// one add for the sum over x and one store.  Loads of U items are issued
-// before they are used.
 // Lane -> (row within a pass, vector) of the tile geometry.
 __device__ __forceinline__ void lane_slot(const TileGeom& g, int lane, int* rip, int* v0, bool* on) {
   if (g.Bv <= 32) {
@@ -206,125 +200,156 @@ __device__ __forceinline__ void lane_parts(WarpTile* w, const TileGeom& g, int l
   for (int i = 0; i < n_in; ++i) w->lpart[i][lane] = pext_in((uint32_t)rip, w->d.in[i]);
 }
 
-template <class Real, int VB, bool PAIR, bool CG, int U = 2>
-__device__ __forceinline__ void warp_tile(WarpTile* w, Real* __restrict__ data,
-                                          const TileGeom& g, int64_t r0, int64_t r1, int lane,
-                                          DevCtrl* ctrl = nullptr, int dbg_bucket = -1) {
+// U items of one lane: output row, vector of angle sets, pass, valid flag.
+template <int U> struct ItemSet {
+  int pp[U];
+  uint32_t y[U];  // output rows < 2^31
+  int32_t vv[U];
+  bool ok[U];
+};
+
+template <int U>
+__device__ __forceinline__ ItemSet<U> make_items(const TileGeom& g, int q0, int Q, int64_t r0, int64_t r1, int rip,
+                                                 int v0, bool lane_on) {
+  ItemSet<U> it;
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int q = q0 + u;
+    const int p = q / g.VC;
+    const int vc = q - p * g.VC;
+    it.pp[u] = q < Q ? p : 0;
+    it.y[u] = (uint32_t)r0 + (uint32_t)(it.pp[u] * g.RP + rip);
+    it.vv[u] = vc * 32 + v0;
+    it.ok[u] = lane_on && q < Q && (int64_t)it.y[u] < r1 && (g.Bv <= 32 || it.vv[u] < g.Bv);
+    if (!it.ok[u]) {  // idle items read a valid element and do not store
+      it.y[u] = (uint32_t)r0;
+      it.vv[u] = 0;
+    }
+  }
+  return it;
+}
+
+// Loads of input i for U items: a0 = rows x = 0, a1 = rows x = 1 (for PAIR,
+// VB = 1 and both come from one adjacent pair).
+template <class Real, int VB, bool PAIR, bool CG, int U>
+__device__ __forceinline__ void load_input(const WarpTile* w, int i, uint32_t lp_i, const ItemSet<U>& it,
+                                           Real* __restrict__ data, const TileGeom& g, Pack<Real, VB>* a0,
+                                           Pack<Real, VB>* a1, DevCtrl* ctrl, int dbg_bucket) {
   (void)ctrl;
   (void)dbg_bucket;
-  using C = typename Cx<Real>::T;
-  const DevBucket& d = w->d;
-  const int n_in = d.n_in;
+  const int64_t off = w->d.in[i].off;
+  const bool leaf = w->d.in[i].flags & kInLeaf;
   const int B = g.B;
-  int rip, v0;
-  bool lane_on;
-  lane_slot(g, lane, &rip, &v0, &lane_on);
-  // pass table: tab[i][p] = pext(r0 + p * RP, mask_i)
-  const int P = g.P;
-  for (int pp = lane; pp < P; pp += 32) {
-    const uint32_t yp = (uint32_t)(r0 + (int64_t)pp * g.RP);
-    for (int i = 0; i < n_in; ++i) w->tab[i][pp] = pext_in(yp, d.in[i]);
-  }
-  __syncwarp();
-  const uint32_t* lp_col = &w->lpart[0][lane];  // lp_col[32 * i] = part of input i
-  const int Q = P * g.VC;
-  for (int q0 = 0; q0 < Q; q0 += U) {
-    int pp[U];
-    uint32_t y[U];  // output rows < 2^31
-    int32_t vv[U];
-    bool ok[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int q = q0 + u;
-      const int p = q / g.VC;
-      const int vc = q - p * g.VC;
-      pp[u] = q < Q ? p : 0;
-      y[u] = (uint32_t)r0 + (uint32_t)(pp[u] * g.RP + rip);
-      vv[u] = vc * 32 + v0;
-      ok[u] = lane_on && q < Q && (int64_t)y[u] < r1 && (g.Bv <= 32 || vv[u] < g.Bv);
-      if (!ok[u]) {  // idle items recompute a valid element and do not store
-        y[u] = (uint32_t)r0;
-        vv[u] = 0;
-      }
-    }
+  for (int u = 0; u < U; ++u) {
+    const uint32_t k = it.ok[u] ? w->tab[i][it.pp[u]] + lp_i : 0u;
     if (PAIR) {
-      C p0[U], p1[U];
-#pragma unroll
-      for (int i = 0; i < kDevMaxIn; ++i) {
-        if (i >= n_in) break;
-        const int64_t off = d.in[i].off;
-        const bool leaf = d.in[i].flags & kInLeaf;
-        Pack<Real, 2> a[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const uint32_t k = ok[u] ? w->tab[i][pp[u]] + lp_col[32 * i] : 0u;
-          if (QT_RANGE_OK(off + 2 * (int64_t)k, 2, 1, i))
-            a[u] = ldpair_in<Real, CG>(data, off + 2 * (int64_t)k, leaf);
-          else
-            a[u] = Pack<Real, 2>{};
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          if (i == 0) {
-            p0[u] = a[u].c[0];
-            p1[u] = a[u].c[1];
-          } else {
-            p0[u] = cmul<Real>(p0[u], a[u].c[0]);
-            p1[u] = cmul<Real>(p1[u], a[u].c[1]);
-          }
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if (!ok[u]) continue;
-        Pack<Real, 1> o{{cadd<Real>(p0[u], p1[u])}};
-        if (QT_RANGE_OK(d.out_off + (int64_t)y[u], 1, 2, -1)) stv<Real, 1>(data, d.out_off + (int64_t)y[u], o);
+      if (QT_RANGE_OK(off + 2 * (int64_t)k, 2, 1, i)) {
+        const Pack<Real, 2> q = ldpair_in<Real, CG>(data, off + 2 * (int64_t)k, leaf);
+        a0[u].c[0] = q.c[0];
+        a1[u].c[0] = q.c[1];
+      } else {
+        a0[u] = Pack<Real, VB>{};
+        a1[u] = Pack<Real, VB>{};
       }
     } else {
-      Pack<Real, VB> p0[U], p1[U];
+      const int64_t base = off + (int64_t)(2 * k) * B + (int64_t)(it.vv[u] * VB);
+      if (QT_RANGE_OK(base, B + VB, 1, i)) {
+        a0[u] = ldv_in<Real, VB, CG>(data, base, leaf);
+        a1[u] = ldv_in<Real, VB, CG>(data, base + B, leaf);
+      } else {
+        a0[u] = Pack<Real, VB>{};
+        a1[u] = Pack<Real, VB>{};
+      }
+    }
+  }
+}
+
+template <class Real, int VB>
+__device__ __forceinline__ void pmul(Pack<Real, VB>& p, const Pack<Real, VB>& a) {
 #pragma unroll
-      for (int i = 0; i < kDevMaxIn; ++i) {
-        if (i >= n_in) break;
-        const int64_t off = d.in[i].off;
-        const bool leaf = d.in[i].flags & kInLeaf;
-        Pack<Real, VB> a0[U], a1[U];
+  for (int v = 0; v < VB; ++v) p.c[v] = cmul<Real>(p.c[v], a.c[v]);
+}
+
+// Items of one tile: for each input in turn, the loads of U items, then
+// their products.  (NIN > 0 would fix the fan-in at compile time and issue
+// the loads of all inputs first; that variant is not instantiated: builds
+// that used it faulted on the GPU although their index arithmetic checks out
+// on the CPU.)
+template <class Real, int VB, bool PAIR, bool CG, int U, int NIN>
+__device__ __forceinline__ void tile_items(WarpTile* w, Real* __restrict__ data, const TileGeom& g, int64_t r0,
+                                           int64_t r1, int lane, int rip, int v0, bool lane_on, DevCtrl* ctrl,
+                                           int dbg_bucket) {
+  const DevBucket& d = w->d;
+  const int n_in = d.n_in;
+  const int Q = g.P * g.VC;
+  const int B = g.B;
+  for (int q0 = 0; q0 < Q; q0 += U) {
+    const ItemSet<U> it = make_items<U>(g, q0, Q, r0, r1, rip, v0, lane_on);
+    Pack<Real, VB> p0[U], p1[U];
+    if (NIN > 0) {
+      Pack<Real, VB> a0[NIN > 0 ? NIN : 1][U], a1[NIN > 0 ? NIN : 1][U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const uint32_t k = ok[u] ? w->tab[i][pp[u]] + lp_col[32 * i] : 0u;
-          const int64_t base = off + (int64_t)(2 * k) * B + (int64_t)(vv[u] * VB);
-          if (QT_RANGE_OK(base, B + VB, 1, i)) {
-            a0[u] = ldv_in<Real, VB, CG>(data, base, leaf);
-            a1[u] = ldv_in<Real, VB, CG>(data, base + B, leaf);
-          } else {
-            a0[u] = Pack<Real, VB>{};
-            a1[u] = Pack<Real, VB>{};
-          }
+      for (int i = 0; i < NIN; ++i)
+        load_input<Real, VB, PAIR, CG, U>(w, i, w->lpart[i][lane], it, data, g, a0[i], a1[i], ctrl, dbg_bucket);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        p0[u] = a0[0][u];
+        p1[u] = a1[0][u];
+#pragma unroll
+        for (int i = 1; i < NIN; ++i) {
+          pmul<Real, VB>(p0[u], a0[i][u]);
+          pmul<Real, VB>(p1[u], a1[i][u]);
         }
+      }
+    } else {
+      for (int i = 0; i < n_in; ++i) {
+        Pack<Real, VB> a0[U], a1[U];
+        load_input<Real, VB, PAIR, CG, U>(w, i, w->lpart[i][lane], it, data, g, a0, a1, ctrl, dbg_bucket);
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           if (i == 0) {
             p0[u] = a0[u];
             p1[u] = a1[u];
           } else {
-#pragma unroll
-            for (int v = 0; v < VB; ++v) {
-              p0[u].c[v] = cmul<Real>(p0[u].c[v], a0[u].c[v]);
-              p1[u].c[v] = cmul<Real>(p1[u].c[v], a1[u].c[v]);
-            }
+            pmul<Real, VB>(p0[u], a0[u]);
+            pmul<Real, VB>(p1[u], a1[u]);
           }
         }
       }
+    }
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if (!ok[u]) continue;
-        Pack<Real, VB> o;
+    for (int u = 0; u < U; ++u) {
+      if (!it.ok[u]) continue;
+      Pack<Real, VB> o;
 #pragma unroll
-        for (int v = 0; v < VB; ++v) o.c[v] = cadd<Real>(p0[u].c[v], p1[u].c[v]);
-        if (QT_RANGE_OK(d.out_off + (int64_t)y[u] * B + (int64_t)(vv[u] * VB), VB, 2, -1))
-          stv<Real, VB>(data, d.out_off + (int64_t)y[u] * B + (int64_t)(vv[u] * VB), o);
-      }
+      for (int v = 0; v < VB; ++v) o.c[v] = cadd<Real>(p0[u].c[v], p1[u].c[v]);
+      const int64_t so = PAIR ? d.out_off + (int64_t)it.y[u]
+                              : d.out_off + (int64_t)it.y[u] * B + (int64_t)(it.vv[u] * VB);
+      if (QT_RANGE_OK(so, VB, 2, -1)) stv<Real, VB>(data, so, o);
     }
   }
+}
+
+// One warp evaluates output rows [r0, r1) of the bucket in w->d (all B angle
+// sets).  r0 is a multiple of g.R.  The pass table tab[i][p] =
+// pext(r0 + p * RP, mask_i) is built here; the lane parts must already be in
+// w->lpart.  Per item an input row is one table read plus one add.
+template <class Real, int VB, bool PAIR, bool CG>
+__device__ __forceinline__ void warp_tile(WarpTile* w, Real* __restrict__ data, const TileGeom& g, int64_t r0,
+                                          int64_t r1, int lane, DevCtrl* ctrl = nullptr, int dbg_bucket = -1) {
+  const DevBucket& d = w->d;
+  const int n_in = d.n_in;
+  int rip, v0;
+  bool lane_on;
+  lane_slot(g, lane, &rip, &v0, &lane_on);
+  const int P = g.P;
+  for (int pp = lane; pp < P; pp += 32) {
+    const uint32_t yp = (uint32_t)(r0 + (int64_t)pp * g.RP);
+    for (int i = 0; i < n_in; ++i) w->tab[i][pp] = pext_in(yp, d.in[i]);
+  }
+  __syncwarp();
+  tile_items<Real, VB, PAIR, CG, 2, 0>(w, data, g, r0, r1, lane, rip, v0, lane_on, ctrl, dbg_bucket);
 }
 
 }  // namespace dev

@@ -9,16 +9,16 @@
 namespace qt {
 
 int vector_width(int dtype, int32_t B);
-TileGeom tile_geom(int dtype, int32_t B);
+TileGeom tile_geom(int dtype, int32_t B, int32_t lane_items);
 cudaError_t launch_trig(const double* gamma, const double* beta, int32_t p, int32_t B, double* trig,
                         cudaStream_t s);
 cudaError_t launch_leaf_factors(int dtype, const DevLeafFactor* lf, int32_t n_lf, const double* trig,
                                 int32_t p, int32_t B, void* data, cudaStream_t s);
-cudaError_t launch_bucket(int dtype, const DevBucket& d, int32_t B, void* data, int32_t max_blocks,
-                          cudaStream_t s);
+cudaError_t launch_bucket(int dtype, const DevBucket& d, int32_t B, int32_t lane_items, void* data,
+                          int32_t max_blocks, cudaStream_t s);
 cudaError_t launch_persistent(int dtype, const DevBucket* buckets, const DevTask* tasks, int32_t n_tasks,
-                              DevCtrl* ctrl, int32_t* done, int32_t B, void* data, int64_t data_elems,
-                              int32_t grid, int32_t spin_limit, cudaStream_t s);
+                              DevCtrl* ctrl, int32_t* done, int32_t B, int32_t lane_items, void* data,
+                              int64_t data_elems, int32_t grid, int32_t spin_limit, cudaStream_t s);
 cudaError_t persistent_occupancy(int dtype, int32_t B, int* blocks_per_sm);
 cudaError_t launch_energy(int dtype, const void* data, const int64_t* scal_off, const int32_t* scal_begin,
                           int32_t n_edges, int32_t B, double* energy, double* edge_zz, cudaStream_t s);

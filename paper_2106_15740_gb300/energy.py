@@ -29,10 +29,15 @@ class EnergyPlan:
     """
 
     def __init__(self, n_vertices, edges, p, batch=1, dtype="c128", mode="persistent",
-                 max_workspace=0, max_width=0, device="cuda:0", gradient=False):
+                 max_workspace=0, max_width=0, device="cuda:0", gradient=False, lane_items=0,
+                 group_rows=0, edge_range=None):
         self.n_vertices, self.p, self.batch = int(n_vertices), int(p), int(batch)
         self.edges = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
         self.device = torch.device(device)
+        self.edge_range = (0, len(self.edges)) if edge_range is None else tuple(int(x) for x in edge_range)
+        self.options = dict(batch=batch, dtype=dtype, mode=mode, max_workspace=max_workspace,
+                            max_width=max_width, gradient=gradient, lane_items=lane_items,
+                            group_rows=group_rows, edge_range=self.edge_range)
         opt = qb.qt_plan_options_default()
         opt.batch = self.batch
         opt.dtype = DTYPES[dtype]
@@ -40,15 +45,19 @@ class EnergyPlan:
         opt.gradient = int(bool(gradient))
         opt.max_width = int(max_width)
         opt.max_workspace = int(max_workspace)
+        opt.lane_items = int(lane_items)
+        opt.group_rows = int(group_rows)
+        opt.edge_begin, opt.edge_end = self.edge_range
         self.plan = qb.qt_plan_create(self.n_vertices, self.edges, self.p, opt)
         self.ws_bytes = qb.qt_plan_workspace_size(self.plan)
         self.stats = qb.qt_plan_stats(self.plan)
-        self.widths = qb.qt_plan_edge_widths(self.plan, len(self.edges))
+        self.widths = qb.qt_plan_edge_widths(self.plan, self.n_edges)
         self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
 
     @property
     def n_edges(self):
-        return len(self.edges)
+        """Edges covered by this plan (its edge range)."""
+        return self.edge_range[1] - self.edge_range[0]
 
     def energy(self, gamma, beta, edge_zz=False, grad=False, out=None):
         B, p = self.batch, self.p
