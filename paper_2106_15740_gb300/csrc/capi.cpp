@@ -175,7 +175,6 @@ qt_status qt_plan_create(const qt_graph* g, int32_t p, const qt_plan_options* op
   if (o.batch < 1) return fail(QT_EINVAL, "batch must be >= 1");
   if (o.dtype != QT_C128 && o.dtype != QT_C64) return fail(QT_EINVAL, "unknown dtype");
   if (o.mode != QT_MODE_PER_BUCKET && o.mode != QT_MODE_PERSISTENT) return fail(QT_EINVAL, "unknown mode");
-  if (o.gradient) return fail(QT_EINVAL, "gradient plans are not available in this build");
   if (o.max_width <= 0 || o.max_width > 31) o.max_width = 31;
   if (o.lane_items > 0 && o.lane_items != 8 && o.lane_items != 16 && o.lane_items != 32 && o.lane_items != 64)
     return fail(QT_EINVAL, "lane_items must be 8, 16, 32 or 64");

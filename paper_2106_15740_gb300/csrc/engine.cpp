@@ -92,23 +92,47 @@ constexpr int32_t kMaxGroup = 4096;  // buckets in one single-tile group task
 
 }  // namespace
 
+// Input record of a forward step (offset filled in by the caller).
+static DevInput input_record(uint32_t mask, int64_t off, int32_t flags) {
+  DevInput in;
+  std::memset(&in, 0, sizeof(in));
+  fill_runs(mask, &in);
+  in.off = off;
+  in.flags = flags;
+  return in;
+}
+
 qt_status compile_plan(Plan* P) {
   const int32_t B = P->opt.batch;
   const int32_t es = P->elem_bytes;
   const int64_t al = 256 / es;  // elements per 256 bytes
   auto align_el = [&](int64_t x) { return (x + al - 1) / al * al; };
   const int32_t n_edges = (int32_t)P->edges.size();
+  const bool grad = P->opt.gradient != 0;
+  const bool persistent = P->opt.mode == QT_MODE_PERSISTENT;
+  if (grad && !persistent) return fail(QT_EINVAL, "gradient plans need QT_MODE_PERSISTENT");
 
-  // Per-edge memory plans.
-  std::vector<std::vector<int64_t>> out_off(n_edges);
-  std::vector<int64_t> peak(n_edges), cost(n_edges);
+  // ---- per-edge memory plans (offsets relative to the edge's region) ----
+  // Forward intermediates: first-fit with free-on-consume, or kept for the
+  // adjoint sweep in gradient plans.  Adjoint buffers follow the forward
+  // arena in the same region, first-fit with free-after-use.
+  struct AdjStep {
+    int32_t bucket, input;  // kStepAdj: bucket b, input k; kStepZero: input < 0
+    int64_t target;         // target offset (region-relative, or leaf-adjoint pool index)
+    bool leaf, full;
+    int32_t zero_rank;
+  };
+  std::vector<std::vector<int64_t>> out_off(n_edges), leaf_off(n_edges), gbar_off(n_edges);
+  std::vector<std::vector<AdjStep>> adj(n_edges);
+  std::vector<int64_t> region(n_edges), fwd_peak(n_edges), cost(n_edges);
   int64_t leaf_pool = 0, scal_pool = 0;
-  std::vector<std::vector<int64_t>> leaf_off(n_edges);
   P->alg_bytes = 0.0;
   P->flops = 0.0;
   for (int32_t e = 0; e < n_edges; ++e) {
     const EdgePlan& ep = P->edges[e];
     const int32_t nb = (int32_t)ep.buckets.size();
+    if (grad && ep.scalars.size() != 1)
+      return fail(QT_EINVAL, "gradient plans need one connected network per edge");
     Arena arena;
     out_off[e].assign(nb, 0);
     leaf_off[e].assign(nb, -1);
@@ -124,11 +148,10 @@ qt_status compile_plan(Plan* P) {
       }
       double bytes = (double)rows;  // output write
       for (size_t k = 0; k < bk.in_src.size(); ++k) {
-        if (bk.in_src[k] >= 0) {
-          const Bucket& src = ep.buckets[bk.in_src[k]];
-          arena.release(out_off[e][bk.in_src[k]], align_el(((int64_t)1 << src.out_rank) * B));
-          bytes += (double)((int64_t)1 << bk.in_rank[k]);
-        }
+        if (bk.in_src[k] < 0) continue;
+        const Bucket& src = ep.buckets[bk.in_src[k]];
+        if (!grad) arena.release(out_off[e][bk.in_src[k]], align_el(((int64_t)1 << src.out_rank) * B));
+        bytes += (double)((int64_t)1 << bk.in_rank[k]);
       }
       if (bk.leaf_rank > 0) {
         leaf_off[e][i] = leaf_pool;
@@ -138,29 +161,70 @@ qt_status compile_plan(Plan* P) {
       const double nin = (double)bk.in_src.size();
       P->flops += (double)B * (double)rows * (2.0 * 6.0 * (nin - 1.0) + 2.0);
     }
-    peak[e] = arena.peak;
-    cost[e] = (int64_t)ebytes;
+    fwd_peak[e] = arena.peak;
+    region[e] = arena.peak;
+    if (grad) {
+      Arena aarena;
+      gbar_off[e].assign(nb, -1);
+      for (int32_t b = nb - 1; b >= 0; --b) {
+        const Bucket& bk = ep.buckets[b];
+        if ((int32_t)bk.in_src.size() + (bk.out_rank > 0 ? 1 : 0) + 1 > kDevMaxIn)
+          return fail(QT_EINVAL, "bucket fan-in above the gradient limit");
+        const uint32_t all = bk.out_rank ? ((bk.out_rank == 32) ? 0xffffffffu : ((1u << bk.out_rank) - 1u)) : 0u;
+        for (size_t k = 0; k < bk.in_src.size(); ++k) {
+          AdjStep st;
+          st.bucket = b;
+          st.input = (int32_t)k;
+          st.full = bk.in_mask[k] == all;
+          st.zero_rank = 0;
+          if (bk.in_src[k] >= 0) {
+            const int32_t t = bk.in_src[k];
+            const Bucket& tb = ep.buckets[t];
+            gbar_off[e][t] = aarena.alloc(align_el(((int64_t)1 << tb.out_rank) * B));
+            st.leaf = false;
+            st.target = gbar_off[e][t];
+            if (!st.full) {
+              AdjStep z = st;
+              z.input = -1;
+              z.zero_rank = tb.out_rank;
+              adj[e].push_back(z);
+            }
+          } else {
+            st.leaf = true;
+            st.target = leaf_off[e][b];
+          }
+          adj[e].push_back(st);
+          // reverse sweep traffic: Gbar and the other inputs read, the target written
+          P->alg_bytes += (double)B * es * (double)(((int64_t)1 << bk.out_rank) + ((int64_t)1 << bk.in_rank[k]));
+          for (size_t j = 0; j < bk.in_src.size(); ++j)
+            if (j != k && bk.in_src[j] >= 0) P->alg_bytes += (double)B * es * (double)((int64_t)1 << bk.in_rank[j]);
+        }
+        if (bk.out_rank > 0) aarena.release(gbar_off[e][b], align_el(((int64_t)1 << bk.out_rank) * B));
+      }
+      region[e] = fwd_peak[e] + aarena.peak;
+    }
+    cost[e] = (int64_t)ebytes * (grad ? 3 : 1);
     P->alg_bytes += ebytes * (double)B * (double)es;
   }
 
-  // Arena placement: per-bucket mode shares one arena; persistent mode uses slots.
+  // ---- region placement: per-bucket mode shares one; persistent uses slots ----
   std::vector<int64_t> edge_base(n_edges, 0);
   int64_t arena_total = 0;
   std::vector<std::vector<int32_t>> slot_edges;
-  const bool persistent = P->opt.mode == QT_MODE_PERSISTENT;
+  const int64_t leaf_pools = grad ? 2 * leaf_pool : leaf_pool;  // leaf factors (+ their adjoints)
   if (!persistent) {
-    for (int32_t e = 0; e < n_edges; ++e) arena_total = std::max(arena_total, peak[e]);
+    for (int32_t e = 0; e < n_edges; ++e) arena_total = std::max(arena_total, region[e]);
     P->n_slots = 1;
   } else {
     std::vector<int32_t> by_cost(n_edges);
     for (int32_t e = 0; e < n_edges; ++e) by_cost[e] = e;
     std::stable_sort(by_cost.begin(), by_cost.end(), [&](int32_t a, int32_t b) { return cost[a] > cost[b]; });
-    const int64_t fixed = leaf_pool + scal_pool;
+    const int64_t fixed = leaf_pools + scal_pool;
     const int64_t cap_el = P->opt.max_workspace > 0 ? P->opt.max_workspace / es : INT64_MAX;
     int32_t S = n_edges;
     for (;;) {
       slot_edges.assign(S, {});
-      std::vector<int64_t> load(S, 0), speak(S, 0);
+      std::vector<int64_t> speak(S, 0);
       using Item = std::pair<int64_t, int32_t>;
       std::priority_queue<Item, std::vector<Item>, std::greater<Item>> heap;
       for (int32_t s = 0; s < S; ++s) heap.push({0, s});
@@ -168,7 +232,7 @@ qt_status compile_plan(Plan* P) {
         auto [l, s] = heap.top();
         heap.pop();
         slot_edges[s].push_back(e);
-        speak[s] = std::max(speak[s], peak[e]);
+        speak[s] = std::max(speak[s], region[e]);
         heap.push({l + cost[e] + 1, s});
       }
       int64_t total = 0;
@@ -188,69 +252,119 @@ qt_status compile_plan(Plan* P) {
     P->n_slots = S;
   }
 
-  // Data region: [leaf pool | scalars | arenas].
-  const int64_t scal_base = leaf_pool;
+  // Data region: [leaf pool | leaf-adjoint pool | scalars | arenas].
+  const int64_t lbar_shift = grad ? leaf_pool : 0;
+  const int64_t scal_base = leaf_pools;
   const int64_t arena_base = scal_base + scal_pool;
   P->data_elems = arena_base + arena_total;
+  P->lbar_shift = lbar_shift;
+  P->lbar_elems = grad ? leaf_pool : 0;
 
-  // Device records.
+  // ---- device records: per edge, forward steps then adjoint steps ----
+  const int32_t geom_bv = tile_geom(P->opt.dtype, B, P->opt.lane_items).Bv;
   P->buckets.clear();
   P->edge_first.assign(n_edges + 1, 0);
   P->leaf.clear();
+  P->leaf_first.assign(n_edges + 1, 0);
   P->scal_off.clear();
   P->scal_begin.assign(n_edges + 1, 0);
   for (int32_t e = 0; e < n_edges; ++e) {
     const EdgePlan& ep = P->edges[e];
+    const int64_t rbase = arena_base + edge_base[e];
+    auto fwd_loc = [&](int32_t b) {
+      return ep.buckets[b].out_rank == 0 ? scal_base + out_off[e][b] : rbase + out_off[e][b];
+    };
     P->edge_first[e] = (int32_t)P->buckets.size();
+    P->leaf_first[e] = (int32_t)P->leaf.size();
+    std::vector<std::vector<DevInput>> fwd_in(ep.buckets.size());
     for (int32_t i = 0; i < (int32_t)ep.buckets.size(); ++i) {
       const Bucket& bk = ep.buckets[i];
       DevBucket d;
       std::memset(&d, 0, sizeof(d));
+      d.kind = kStepFwd;
       d.out_rank = bk.out_rank;
       d.n_rows = (int64_t)1 << bk.out_rank;
-      d.out_off = bk.out_rank == 0 ? scal_base + out_off[e][i] : arena_base + edge_base[e] + out_off[e][i];
+      d.out_off = fwd_loc(i);
       d.n_in = (int32_t)bk.in_src.size();
       d.dep = -1;
       d.ntask = 1;
       for (int32_t k = 0; k < d.n_in; ++k) {
         const int32_t src = bk.in_src[k];
         if (src >= 0) {
-          const Bucket& sb = ep.buckets[src];
-          d.in[k].off = sb.out_rank == 0 ? scal_base + out_off[e][src] : arena_base + edge_base[e] + out_off[e][src];
+          d.in[k] = input_record(bk.in_mask[k], fwd_loc(src), 0);
         } else {
-          d.in[k].off = leaf_off[e][i];
-          d.in[k].flags = kInLeaf;
+          d.in[k] = input_record(bk.in_mask[k], leaf_off[e][i], kInLeaf);
           DevLeafFactor lf;
           std::memset(&lf, 0, sizeof(lf));
           lf.off = leaf_off[e][i];
           lf.rank = bk.leaf_rank;
           lf.n_leaves = (int32_t)bk.leaves.size();
           for (int32_t l = 0; l < lf.n_leaves; ++l) {
-            const LeafRef& L = bk.leaves[l];
-            uint32_t w = (uint32_t)L.kind | (uint32_t)L.conj << 2 | (uint32_t)L.rank << 3 |
-                         (uint32_t)(L.bit[0] < 0 ? 0 : L.bit[0]) << 5 |
-                         (uint32_t)(L.bit[1] < 0 ? 0 : L.bit[1]) << 10 | (uint32_t)L.layer << 16;
-            lf.leaf[l] = w;
+            const LeafRef& Lr = bk.leaves[l];
+            lf.leaf[l] = (uint32_t)Lr.kind | (uint32_t)Lr.conj << 2 | (uint32_t)Lr.rank << 3 |
+                         (uint32_t)(Lr.bit[0] < 0 ? 0 : Lr.bit[0]) << 5 |
+                         (uint32_t)(Lr.bit[1] < 0 ? 0 : Lr.bit[1]) << 10 | (uint32_t)Lr.layer << 16;
           }
           P->leaf.push_back(lf);
         }
-        fill_runs(bk.in_mask[k], &d.in[k]);
+        fwd_in[i].push_back(d.in[k]);
       }
       P->buckets.push_back(d);
     }
-    for (int32_t s : ep.scalars) P->scal_off.push_back(scal_base + out_off[e][s]);
+    for (const AdjStep& st : adj[e]) {
+      const Bucket& bk = ep.buckets[st.bucket];
+      DevBucket d;
+      std::memset(&d, 0, sizeof(d));
+      d.dep = -1;
+      d.ntask = 1;
+      if (st.input < 0) {
+        d.kind = kStepZero;
+        d.out_rank = st.zero_rank;
+        d.n_rows = (int64_t)1 << st.zero_rank;
+        d.out_off = rbase + fwd_peak[e] + st.target;
+        P->buckets.push_back(d);
+        continue;
+      }
+      d.kind = kStepAdj;
+      d.out_rank = bk.out_rank;
+      d.n_rows = (int64_t)1 << bk.out_rank;
+      d.out_off = st.leaf ? st.target + lbar_shift : rbase + fwd_peak[e] + st.target;
+      d.aflags = st.full ? kAdjFull : 0;
+      const uint32_t all = bk.out_rank ? (1u << bk.out_rank) - 1u : 0u;
+      int32_t n = 0;
+      if (bk.out_rank > 0) {
+        d.in[n++] = input_record(all, rbase + fwd_peak[e] + gbar_off[e][st.bucket], kInNoPair);
+      } else {
+        d.aflags |= kAdjUnitG;
+      }
+      for (int32_t j = 0; j < (int32_t)bk.in_src.size(); ++j)
+        if (j != st.input) d.in[n++] = fwd_in[st.bucket][j];
+      const uint32_t tmask = bk.in_mask[st.input];
+      d.in[n] = input_record(tmask, d.out_off, 0);  // target record
+      d.n_in = n;
+      if (!st.full && __builtin_popcount(all & ~tmask) >= 5 && geom_bv <= 32 && n + 2 <= kDevMaxIn) {
+        // reduction form (32 or more completions per target element): one warp
+        // tile per (target row, chunk of completions); smaller targets keep the
+        // atomic scatter, whose contention is then at most 32 per element
+        d.kind = kStepAdjRed;
+        d.in[n + 1] = input_record(all & ~tmask, 0, 0);  // complement record
+        d.n_rows = (int64_t)1 << __builtin_popcount(all & ~tmask);
+        d.tgt_bits = __builtin_popcount(tmask);
+      }
+      P->buckets.push_back(d);
+    }
+    for (int32_t sb : ep.scalars) P->scal_off.push_back(scal_base + out_off[e][sb]);
     P->scal_begin[e + 1] = (int32_t)P->scal_off.size();
   }
   P->edge_first[n_edges] = (int32_t)P->buckets.size();
+  P->leaf_first[n_edges] = (int32_t)P->leaf.size();
 
-  // Persistent queue.
+  // ---- persistent queue: each edge's steps form a chain; slots round-robin ----
   P->tasks.clear();
   const TileGeom geom = tile_geom(P->opt.dtype, B, P->opt.lane_items);
-  // groups: runs of buckets with at most group_rows rows (default: at most
-  // 4 passes of a warp tile), never larger than one tile
+  P->tile_items = geom.R;
   int64_t group_rows = P->opt.group_rows == 0 ? 4 * (int64_t)geom.RP : (int64_t)P->opt.group_rows;
   if (group_rows > geom.R) group_rows = geom.R;
-  P->tile_items = geom.R;
   if (persistent) {
     const int32_t S = P->n_slots;
     std::vector<size_t> ei(S, 0);
@@ -262,30 +376,31 @@ qt_status compile_plan(Plan* P) {
         if (ei[s] >= slot_edges[s].size()) continue;
         any = true;
         const int32_t e = slot_edges[s][ei[s]];
-        const int32_t nb_e = (int32_t)P->edges[e].buckets.size();
+        const int32_t ns_e = P->edge_first[e + 1] - P->edge_first[e];
         const int32_t gb = P->edge_first[e] + bi[s];
         DevBucket& d = P->buckets[gb];
-        const int64_t nt = (d.n_rows + geom.R - 1) / geom.R;
+        const int64_t nt = step_tiles(d, geom.R);
         if (nt > INT32_MAX / 2) return fail(QT_EWIDTH, "bucket too large for the task queue");
         d.dep = prev[s];
         if (nt == 1 && d.n_rows <= group_rows) {
-          // group the run of small buckets that starts here
           int32_t k = 1;
-          while (bi[s] + k < nb_e && k < kMaxGroup && P->buckets[gb + k].n_rows <= group_rows) ++k;
+          while (bi[s] + k < ns_e && k < kMaxGroup && P->buckets[gb + k].n_rows <= group_rows &&
+                 step_tiles(P->buckets[gb + k], geom.R) == 1)
+            ++k;
           for (int32_t j = 0; j < k; ++j) {
             P->buckets[gb + j].ntask = 1;
             if (j > 0) P->buckets[gb + j].dep = -1;
           }
           P->tasks.push_back(DevTask{gb, -k});
           prev[s] = gb + k - 1;
-          bi[s] += k - 1;  // the increment below moves past the group
+          bi[s] += k - 1;
         } else {
           d.ntask = (int32_t)nt;
           for (int32_t t = 0; t < d.ntask; ++t) P->tasks.push_back(DevTask{gb, t});
           prev[s] = gb;
         }
         if ((int64_t)P->tasks.size() > INT32_MAX / 2) return fail(QT_EWIDTH, "task queue too long");
-        if (++bi[s] == nb_e) {
+        if (++bi[s] == ns_e) {
           bi[s] = 0;
           ++ei[s];
         }
@@ -307,6 +422,8 @@ qt_status compile_plan(Plan* P) {
   o = align256(o + sizeof(DevTask) * P->tasks.size());
   L.leaf = o;
   o = align256(o + sizeof(DevLeafFactor) * P->leaf.size());
+  L.leaf_first = o;
+  o = align256(o + sizeof(int32_t) * P->leaf_first.size());
   L.scal_off = o;
   o = align256(o + sizeof(int64_t) * P->scal_off.size());
   L.scal_begin = o;
@@ -317,6 +434,8 @@ qt_status compile_plan(Plan* P) {
   o = align256(o + sizeof(double) * ((size_t)B + (size_t)n_edges * B * 2 + (size_t)B * 2 * p));
   L.trig = o;
   o = align256(o + sizeof(double) * 4 * (size_t)B * p);
+  L.dz = o;
+  if (grad) o = align256(o + sizeof(double) * 2 * (size_t)n_edges * B * 2 * p);
   L.data = o;
   o = align256(o + (size_t)es * (size_t)P->data_elems);
   L.total = o;
@@ -342,7 +461,7 @@ qt_status run_plan(Plan* P, const double* gamma, const double* beta, double* ene
     return fail(QT_ENOMEM, "workspace has " + std::to_string(ws_bytes) + " bytes, plan needs " +
                                std::to_string(P->ws.total));
   if (!gamma || !beta) return fail(QT_EINVAL, "angle pointer is NULL");
-  if (grad) return fail(QT_ESTATE, "gradient requested from a plan without the adjoint sweep");
+  if (grad && !P->opt.gradient) return fail(QT_ESTATE, "gradient requested from a plan without the adjoint sweep");
   cudaStream_t s = (cudaStream_t)stream;
   char* base = (char*)ws;
   const WsLayout& L = P->ws;
@@ -360,6 +479,9 @@ qt_status run_plan(Plan* P, const double* gamma, const double* beta, double* ene
     if (!P->leaf.empty())
       QT_CUDA(cudaMemcpyAsync(base + L.leaf, P->leaf.data(), sizeof(DevLeafFactor) * P->leaf.size(),
                               cudaMemcpyHostToDevice, s));
+    if (!P->leaf_first.empty())
+      QT_CUDA(cudaMemcpyAsync(base + L.leaf_first, P->leaf_first.data(), sizeof(int32_t) * P->leaf_first.size(),
+                              cudaMemcpyHostToDevice, s));
     if (!P->scal_off.empty())
       QT_CUDA(cudaMemcpyAsync(base + L.scal_off, P->scal_off.data(), sizeof(int64_t) * P->scal_off.size(),
                               cudaMemcpyHostToDevice, s));
@@ -372,6 +494,9 @@ qt_status run_plan(Plan* P, const double* gamma, const double* beta, double* ene
   void* data = base + L.data;
   double* trig = (double*)(base + L.trig);
   QT_CUDA(cudaMemsetAsync(base + L.ctrl, 0, L.buckets - L.ctrl, s));  // ctrl + done counters
+  if (P->lbar_elems > 0)  // leaf-factor adjoints are accumulated with atomics
+    QT_CUDA(cudaMemsetAsync(base + L.data + (size_t)P->elem_bytes * P->lbar_shift, 0,
+                            (size_t)P->elem_bytes * P->lbar_elems, s));
   QT_CUDA(launch_trig(gamma, beta, P->p, B, trig, s));
   QT_CUDA(launch_leaf_factors(dtype, (const DevLeafFactor*)(base + L.leaf), (int32_t)P->leaf.size(), trig, P->p,
                               B, data, s));
@@ -390,11 +515,11 @@ qt_status run_plan(Plan* P, const double* gamma, const double* beta, double* ene
   }
   if (P->opt.mode == QT_MODE_PERSISTENT) {
     int per_sm = 0;
-    QT_CUDA(persistent_occupancy(dtype, B, &per_sm));
+    QT_CUDA(persistent_occupancy(dtype, P->opt.gradient != 0, B, &per_sm));
     int n_sm = 0;
     QT_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
     const int32_t grid = std::max(1, per_sm) * n_sm;
-    QT_CUDA(launch_persistent(dtype, dbk, (const DevTask*)(base + L.tasks), (int32_t)P->tasks.size(),
+    QT_CUDA(launch_persistent(dtype, P->opt.gradient != 0, dbk, (const DevTask*)(base + L.tasks), (int32_t)P->tasks.size(),
                               (DevCtrl*)(base + L.ctrl), (int32_t*)(base + L.done), B, P->opt.lane_items, data,
                               P->data_elems, grid, P->spin_limit, s));
   } else {
@@ -406,6 +531,10 @@ qt_status run_plan(Plan* P, const double* gamma, const double* beta, double* ene
   if (ev_stop) QT_CUDA(cudaEventRecord(ev_stop, s));
   QT_CUDA(launch_energy(dtype, data, (const int64_t*)(base + L.scal_off), (const int32_t*)(base + L.scal_begin),
                         (int32_t)P->edges.size(), B, energy, edge_zz, s));
+  if (grad)
+    QT_CUDA(launch_gradient(dtype, (const DevLeafFactor*)(base + L.leaf), (const int32_t*)(base + L.leaf_first),
+                            (int32_t)P->edges.size(), P->lbar_shift, trig, P->p, B, data, (double*)(base + L.dz),
+                            grad, s));
   return QT_OK;
 }
 

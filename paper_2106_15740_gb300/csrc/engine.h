@@ -16,8 +16,8 @@ struct qt_network {
 namespace qt {
 
 struct WsLayout {
-  size_t ctrl = 0, done = 0, buckets = 0, tasks = 0, leaf = 0, scal_off = 0, scal_begin = 0;
-  size_t angles = 0, results = 0, trig = 0, data = 0, total = 0;
+  size_t ctrl = 0, done = 0, buckets = 0, tasks = 0, leaf = 0, leaf_first = 0, scal_off = 0, scal_begin = 0;
+  size_t angles = 0, results = 0, trig = 0, dz = 0, data = 0, total = 0;
 };
 
 struct Plan {
@@ -29,9 +29,12 @@ struct Plan {
   std::vector<int32_t> widths;
 
   // device images (uploaded into the workspace)
-  std::vector<DevBucket> buckets;          // all edges, concatenated
-  std::vector<int32_t> edge_first;         // first bucket of each edge (n_edges + 1)
+  std::vector<DevBucket> buckets;          // steps of all edges (forward, then adjoint), concatenated
+  std::vector<int32_t> edge_first;         // first step of each edge (n_edges + 1)
   std::vector<DevLeafFactor> leaf;
+  std::vector<int32_t> leaf_first;         // first leaf factor of each edge (n_edges + 1)
+  int64_t lbar_shift = 0;                  // leaf-adjoint element = leaf element + lbar_shift
+  int64_t lbar_elems = 0;
   std::vector<DevTask> tasks;
   std::vector<int64_t> scal_off;           // element offsets of scalar results
   std::vector<int32_t> scal_begin;         // CSR over edges

@@ -119,7 +119,7 @@ __device__ __forceinline__ int32_t ld_acquire(const int32_t* p) {
 // records QT_ETIMEOUT in the control word and no warp takes a task after that.
 // Consecutive tiles of one bucket on a warp reuse its record and skip the
 // wait (done counters only grow).
-template <class Real, int VB, bool PAIR>
+template <class Real, int VB, bool PAIR, bool GRAD>
 __global__ void __launch_bounds__(256, 4) persistent_kernel(const DevBucket* __restrict__ buckets,
                                                             const DevTask* __restrict__ tasks, int32_t n_tasks,
                                                             DevCtrl* ctrl, int32_t* done, Real* __restrict__ data,
@@ -176,9 +176,16 @@ __global__ void __launch_bounds__(256, 4) persistent_kernel(const DevBucket* __r
         break;
       }
 #endif
-      const int64_t r0 = task.tile < 0 ? 0 : (int64_t)task.tile * g.R;
+      int64_t tile = task.tile < 0 ? 0 : task.tile;
+      uint32_t kt = 0;
+      if (GRAD && w->d.kind == kStepAdjRed) {  // tile = kt * chunks + chunk
+        const int64_t chunks = (w->d.n_rows + g.R - 1) / g.R;
+        kt = (uint32_t)(tile / chunks);
+        tile -= (int64_t)kt * chunks;
+      }
+      const int64_t r0 = tile * g.R;
       const int64_t r1 = r0 + g.R < w->d.n_rows ? r0 + g.R : w->d.n_rows;
-      warp_tile<Real, VB, PAIR, true>(w, data, g, r0, r1, lane, ctrl, b);
+      warp_tile<Real, VB, PAIR, true, GRAD>(w, data, g, r0, r1, lane, ctrl, b, kt);
       __syncwarp();  // the next bucket of a group reads what this one wrote
     }
     __threadfence();
@@ -214,6 +221,78 @@ __global__ void energy_kernel(const Real* __restrict__ data, const int64_t* __re
     E += 0.5 * (1.0 - zr);
   }
   if (energy) energy[b] = E;
+}
+
+// Derivative of one leaf value with respect to its own angle (the ZZ angle
+// gamma_q for kind 1, the mixer angle beta_q for kind 2), at index bits z:
+//   ZZ : d/dg exp(-i s g) = -i s exp(-i s g); the bra copy is the conjugate
+//   MIX: d/db cos b = -sin b;  d/db (-i sin b) = -i cos b; conjugate for the bra
+__device__ __forceinline__ double2 leaf_deriv(uint32_t w, uint32_t z, const double* tr) {
+  const uint32_t kind = w & 3u, conj = (w >> 2) & 1u;
+  const uint32_t b0 = (z >> ((w >> 5) & 31u)) & 1u;
+  const uint32_t b1 = (z >> ((w >> 10) & 31u)) & 1u;
+  double2 v = make_double2(0.0, 0.0);
+  if (kind == 1u) {
+    const double s = (b0 == b1) ? 1.0 : -1.0;
+    const double2 val = make_double2(tr[0], -s * tr[1]);  // ket value
+    v = make_double2(s * val.y, -s * val.x);              // -i s val
+  } else if (kind == 2u) {
+    v = (b0 == b1) ? make_double2(-tr[3], 0.0) : make_double2(0.0, -tr[2]);
+  }
+  if (conj) v.y = -v.y;
+  return v;
+}
+
+// dZ_e/dtheta for every edge e, angle set b and angle theta (0..p-1: gamma,
+// p..2p-1: beta): sum over the edge's leaf factors F and their leaves l that
+// carry theta of sum_z Lbar_F[z] * dl(z) * prod_{l' != l} l'(z).  FP64.
+template <class Real>
+__global__ void leafgrad_kernel(const DevLeafFactor* __restrict__ lf, const int32_t* __restrict__ leaf_first,
+                                int32_t n_edges, int64_t lbar_shift, const double* __restrict__ trig, int32_t p,
+                                int32_t B, const Real* __restrict__ data, double* __restrict__ dz) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = (int64_t)n_edges * B * 2 * p;
+  if (idx >= n) return;
+  const int32_t th = (int32_t)(idx % (2 * p));
+  const int32_t b = (int32_t)((idx / (2 * p)) % B);
+  const int32_t e = (int32_t)(idx / ((int64_t)2 * p * B));
+  const uint32_t want_kind = th < p ? 1u : 2u;
+  const uint32_t want_layer = (uint32_t)(th < p ? th + 1 : th - p + 1);
+  double ar = 0.0, ai = 0.0;
+  for (int32_t f = leaf_first[e]; f < leaf_first[e + 1]; ++f) {
+    const DevLeafFactor F = lf[f];
+    for (int32_t l = 0; l < F.n_leaves; ++l) {
+      const uint32_t w = F.leaf[l];
+      if ((w & 3u) != want_kind || (w >> 16) != want_layer) continue;
+      const double* tr = trig + ((int64_t)b * p + (int64_t)want_layer - 1) * 4;
+      for (uint32_t z = 0; z < (1u << F.rank); ++z) {
+        double2 t = leaf_deriv(w, z, tr);
+        for (int32_t l2 = 0; l2 < F.n_leaves; ++l2) {
+          if (l2 == l) continue;
+          const uint32_t w2 = F.leaf[l2];
+          const int32_t layer2 = (int32_t)(w2 >> 16);
+          const double* tr2 = trig + ((int64_t)b * p + (layer2 > 0 ? layer2 - 1 : 0)) * 4;
+          t = cmul<double>(t, leaf_value<double>(w2, z, tr2));
+        }
+        const int64_t o = F.off + lbar_shift + (int64_t)z * B + b;
+        const double gr = (double)data[2 * o], gi = (double)data[2 * o + 1];
+        ar += gr * t.x - gi * t.y;
+        ai += gr * t.y + gi * t.x;
+      }
+    }
+  }
+  dz[2 * idx] = ar;
+  dz[2 * idx + 1] = ai;
+}
+
+// dE/dtheta = -1/2 sum_e Re dZ_e/dtheta, edges summed in order (E = sum_e (1 - Z_e) / 2).
+__global__ void gradreduce_kernel(const double* __restrict__ dz, int32_t n_edges, int32_t p, int32_t B,
+                                  double* __restrict__ grad) {
+  const int32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= B * 2 * p) return;
+  double acc = 0.0;
+  for (int32_t e = 0; e < n_edges; ++e) acc += dz[2 * ((int64_t)e * B * 2 * p + idx)];
+  grad[idx] = -0.5 * acc;
 }
 
 }  // namespace dev
@@ -288,45 +367,56 @@ cudaError_t launch_bucket(int dtype, const DevBucket& d, int32_t B, int32_t lane
   return cudaGetLastError();
 }
 
-cudaError_t launch_persistent(int dtype, const DevBucket* buckets, const DevTask* tasks, int32_t n_tasks,
-                              DevCtrl* ctrl, int32_t* done, int32_t B, int32_t lane_items, void* data,
-                              int64_t data_elems, int32_t grid, int32_t spin_limit, cudaStream_t s) {
+template <bool GRAD>
+static cudaError_t launch_persistent_t(int dtype, const DevBucket* buckets, const DevTask* tasks, int32_t n_tasks,
+                                       DevCtrl* ctrl, int32_t* done, void* data, const TileGeom& g, int32_t B,
+                                       int32_t grid, int32_t spin_limit, cudaStream_t s) {
   const int vb = vector_width(dtype, B);
   const bool pair = (B == 1);
-  TileGeom g = tile_geom(dtype, B, lane_items);
-  g.data_elems = data_elems;
   if (dtype == QT_C64) {
     if (pair)
-      dev::persistent_kernel<float, 1, true><<<grid, 256, 0, s>>>(buckets, tasks, n_tasks, ctrl, done,
-                                                                  (float*)data, g, spin_limit);
+      dev::persistent_kernel<float, 1, true, GRAD><<<grid, 256, 0, s>>>(buckets, tasks, n_tasks, ctrl, done,
+                                                                        (float*)data, g, spin_limit);
     else if (vb == 2)
-      dev::persistent_kernel<float, 2, false><<<grid, 256, 0, s>>>(buckets, tasks, n_tasks, ctrl, done,
-                                                                   (float*)data, g, spin_limit);
+      dev::persistent_kernel<float, 2, false, GRAD><<<grid, 256, 0, s>>>(buckets, tasks, n_tasks, ctrl, done,
+                                                                         (float*)data, g, spin_limit);
     else
-      dev::persistent_kernel<float, 1, false><<<grid, 256, 0, s>>>(buckets, tasks, n_tasks, ctrl, done,
-                                                                   (float*)data, g, spin_limit);
+      dev::persistent_kernel<float, 1, false, GRAD><<<grid, 256, 0, s>>>(buckets, tasks, n_tasks, ctrl, done,
+                                                                         (float*)data, g, spin_limit);
   } else {
     if (pair)
-      dev::persistent_kernel<double, 1, true><<<grid, 256, 0, s>>>(buckets, tasks, n_tasks, ctrl, done,
-                                                                   (double*)data, g, spin_limit);
+      dev::persistent_kernel<double, 1, true, GRAD><<<grid, 256, 0, s>>>(buckets, tasks, n_tasks, ctrl, done,
+                                                                         (double*)data, g, spin_limit);
     else
-      dev::persistent_kernel<double, 1, false><<<grid, 256, 0, s>>>(buckets, tasks, n_tasks, ctrl, done,
-                                                                    (double*)data, g, spin_limit);
+      dev::persistent_kernel<double, 1, false, GRAD><<<grid, 256, 0, s>>>(buckets, tasks, n_tasks, ctrl, done,
+                                                                          (double*)data, g, spin_limit);
   }
   return cudaGetLastError();
 }
 
-cudaError_t persistent_occupancy(int dtype, int32_t B, int* blocks_per_sm) {
+cudaError_t launch_persistent(int dtype, bool grad, const DevBucket* buckets, const DevTask* tasks,
+                              int32_t n_tasks, DevCtrl* ctrl, int32_t* done, int32_t B, int32_t lane_items,
+                              void* data, int64_t data_elems, int32_t grid, int32_t spin_limit, cudaStream_t s) {
+  TileGeom g = tile_geom(dtype, B, lane_items);
+  g.data_elems = data_elems;
+  return grad ? launch_persistent_t<true>(dtype, buckets, tasks, n_tasks, ctrl, done, data, g, B, grid, spin_limit, s)
+              : launch_persistent_t<false>(dtype, buckets, tasks, n_tasks, ctrl, done, data, g, B, grid, spin_limit, s);
+}
+
+template <bool GRAD>
+static const void* persistent_fn(int dtype, int32_t B) {
   const int vb = vector_width(dtype, B);
   const bool pair = (B == 1);
-  const void* fn;
   if (dtype == QT_C64)
-    fn = pair ? (const void*)dev::persistent_kernel<float, 1, true>
-              : (vb == 2 ? (const void*)dev::persistent_kernel<float, 2, false>
-                         : (const void*)dev::persistent_kernel<float, 1, false>);
-  else
-    fn = pair ? (const void*)dev::persistent_kernel<double, 1, true>
-              : (const void*)dev::persistent_kernel<double, 1, false>;
+    return pair ? (const void*)dev::persistent_kernel<float, 1, true, GRAD>
+                : (vb == 2 ? (const void*)dev::persistent_kernel<float, 2, false, GRAD>
+                           : (const void*)dev::persistent_kernel<float, 1, false, GRAD>);
+  return pair ? (const void*)dev::persistent_kernel<double, 1, true, GRAD>
+              : (const void*)dev::persistent_kernel<double, 1, false, GRAD>;
+}
+
+cudaError_t persistent_occupancy(int dtype, bool grad, int32_t B, int* blocks_per_sm) {
+  const void* fn = grad ? persistent_fn<true>(dtype, B) : persistent_fn<false>(dtype, B);
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, 256, 0);
 }
 
@@ -339,6 +429,23 @@ cudaError_t launch_energy(int dtype, const void* data, const int64_t* scal_off, 
   else
     dev::energy_kernel<double><<<grid, 128, 0, s>>>((const double*)data, scal_off, scal_begin, n_edges, B,
                                                     energy, edge_zz);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gradient(int dtype, const DevLeafFactor* lf, const int32_t* leaf_first, int32_t n_edges,
+                            int64_t lbar_shift, const double* trig, int32_t p, int32_t B, const void* data, double* dz,
+                            double* grad, cudaStream_t s) {
+  const int64_t n = (int64_t)n_edges * B * 2 * p;
+  const int64_t blocks = (n + 127) / 128;
+  if (dtype == QT_C64)
+    dev::leafgrad_kernel<float><<<(int)blocks, 128, 0, s>>>(lf, leaf_first, n_edges, lbar_shift, trig, p, B,
+                                                            (const float*)data, dz);
+  else
+    dev::leafgrad_kernel<double><<<(int)blocks, 128, 0, s>>>(lf, leaf_first, n_edges, lbar_shift, trig, p, B,
+                                                             (const double*)data, dz);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  dev::gradreduce_kernel<<<(B * 2 * p + 127) / 128, 128, 0, s>>>(dz, n_edges, p, B, grad);
   return cudaGetLastError();
 }
 

@@ -123,6 +123,29 @@ __device__ __forceinline__ uint32_t pext_in(uint32_t y, const DevInput& in) {
   return k;
 }
 
+// Deposit the low bits of x into the set bits of the record's mask (the
+// inverse of pext_in), from the same runs with source and destination swapped.
+__device__ __forceinline__ uint32_t pdep_in(uint32_t x, const DevInput& in) {
+  uint32_t y = 0;
+  if (in.nruns >= 0) {
+    for (int r = 0; r < in.nruns; ++r) {
+      const uint32_t w = in.run[r];
+      const uint32_t ybit = w & 31u, len = (w >> 8) & 63u, xbit = (w >> 16) & 31u;
+      y |= ((x >> xbit) & ((1u << len) - 1u)) << ybit;
+    }
+  } else {
+    uint32_t m = in.mask;
+    int j = 0;
+    while (m) {
+      const uint32_t low = m & (0u - m);
+      if ((x >> j) & 1u) y |= low;
+      ++j;
+      m ^= low;
+    }
+  }
+  return y;
+}
+
 #ifdef QT_DEVICE_CHECKS
 // Debug build: an element range outside the data region is recorded in the
 // control word (first failure wins) and the access is skipped.
@@ -148,6 +171,8 @@ struct WarpTile {
   DevBucket d;
   uint32_t tab[kDevMaxIn][kLaneItems];
   uint32_t lpart[kDevMaxIn][32];  // pext(i_lane, mask) per input and lane
+  float redf[32][4];              // per-lane partial sums of a reduction step (complex64)
+  double redd[32][2];             // the same for complex128
 };
 
 // Copy a bucket record into the warp's shared slot with typed member
@@ -156,7 +181,8 @@ struct WarpTile {
 // all 32 lanes; the caller synchronises the warp before reading the slot.
 __device__ __forceinline__ void load_bucket(DevBucket* dst, const DevBucket* src, int lane) {
   const int n_in = src->n_in;
-  if (lane < kDevMaxIn && lane < n_in) dst->in[lane] = src->in[lane];
+  const int n_rec = src->kind == kStepAdj ? n_in + 1 : (src->kind == kStepAdjRed ? n_in + 2 : n_in);
+  if (lane < kDevMaxIn && lane < n_rec) dst->in[lane] = src->in[lane];
   if (lane == 31) {
     dst->out_off = src->out_off;
     dst->n_rows = src->n_rows;
@@ -164,6 +190,9 @@ __device__ __forceinline__ void load_bucket(DevBucket* dst, const DevBucket* src
     dst->n_in = n_in;
     dst->dep = src->dep;
     dst->ntask = src->ntask;
+    dst->kind = src->kind;
+    dst->aflags = src->aflags;
+    dst->tgt_bits = src->tgt_bits;
   }
 }
 
@@ -196,8 +225,13 @@ __device__ __forceinline__ void lane_parts(WarpTile* w, const TileGeom& g, int l
   int rip, v0;
   bool on;
   lane_slot(g, lane, &rip, &v0, &on);
-  const int n_in = w->d.n_in;
-  for (int i = 0; i < n_in; ++i) w->lpart[i][lane] = pext_in((uint32_t)rip, w->d.in[i]);
+  if (w->d.kind == kStepAdjRed) {  // lanes index completions: part of y = pdep(i_lane, complement)
+    const uint32_t ylane = pdep_in((uint32_t)rip, w->d.in[w->d.n_in + 1]);
+    for (int i = 0; i < w->d.n_in; ++i) w->lpart[i][lane] = pext_in(ylane, w->d.in[i]);
+    return;
+  }
+  const int n_rec = w->d.kind == kStepAdj ? w->d.n_in + 1 : w->d.n_in;
+  for (int i = 0; i < n_rec; ++i) w->lpart[i][lane] = pext_in((uint32_t)rip, w->d.in[i]);
 }
 
 // U items of one lane: output row, vector of angle sets, pass, valid flag.
@@ -239,11 +273,21 @@ __device__ __forceinline__ void load_input(const WarpTile* w, int i, uint32_t lp
   (void)dbg_bucket;
   const int64_t off = w->d.in[i].off;
   const bool leaf = w->d.in[i].flags & kInLeaf;
+  const bool nopair = w->d.in[i].flags & kInNoPair;
   const int B = g.B;
 #pragma unroll
   for (int u = 0; u < U; ++u) {
     const uint32_t k = it.ok[u] ? w->tab[i][it.pp[u]] + lp_i : 0u;
-    if (PAIR) {
+    if (nopair) {  // one row k, the same factor for x = 0 and x = 1
+      const int64_t base = PAIR ? off + (int64_t)k : off + (int64_t)k * B + (int64_t)(it.vv[u] * VB);
+      if (QT_RANGE_OK(base, VB, 1, i)) {
+        a0[u] = ldv_in<Real, VB, CG>(data, base, leaf);
+        a1[u] = a0[u];
+      } else {
+        a0[u] = Pack<Real, VB>{};
+        a1[u] = Pack<Real, VB>{};
+      }
+    } else if (PAIR) {
       if (QT_RANGE_OK(off + 2 * (int64_t)k, 2, 1, i)) {
         const Pack<Real, 2> q = ldpair_in<Real, CG>(data, off + 2 * (int64_t)k, leaf);
         a0[u].c[0] = q.c[0];
@@ -331,25 +375,236 @@ __device__ __forceinline__ void tile_items(WarpTile* w, Real* __restrict__ data,
   }
 }
 
+template <class Real>
+__device__ __forceinline__ void atomic_add_cx(Real* data, int64_t e, typename Cx<Real>::T v) {
+  atomicAdd(data + 2 * e, v.x);
+  atomicAdd(data + 2 * e + 1, v.y);
+}
+
+// Adjoint step (kStepAdj): for each item (row y, vector), the product of the
+// factors at x = 0 and x = 1 goes to the target rows (k_t << 1) | x,
+// k_t = pext(y, mask_t).
+template <class Real, int VB, bool PAIR, bool CG, int U>
+__device__ __forceinline__ void tile_adjoint(WarpTile* w, Real* __restrict__ data, const TileGeom& g, int64_t r0,
+                                             int64_t r1, int lane, int rip, int v0, bool lane_on, DevCtrl* ctrl,
+                                             int dbg_bucket) {
+  using C = typename Cx<Real>::T;
+  const DevBucket& d = w->d;
+  const int n_in = d.n_in;
+  const int Q = g.P * g.VC;
+  const int B = g.B;
+  const bool full = d.aflags & kAdjFull;
+  const uint32_t lp_t = w->lpart[n_in][lane];
+  for (int q0 = 0; q0 < Q; q0 += U) {
+    const ItemSet<U> it = make_items<U>(g, q0, Q, r0, r1, rip, v0, lane_on);
+    Pack<Real, VB> p0[U], p1[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int v = 0; v < VB; ++v) {
+        p0[u].c[v].x = 1;
+        p0[u].c[v].y = 0;
+        p1[u].c[v] = p0[u].c[v];
+      }
+    for (int i = 0; i < n_in; ++i) {
+      Pack<Real, VB> a0[U], a1[U];
+      load_input<Real, VB, PAIR, CG, U>(w, i, w->lpart[i][lane], it, data, g, a0, a1, ctrl, dbg_bucket);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        pmul<Real, VB>(p0[u], a0[u]);
+        pmul<Real, VB>(p1[u], a1[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (!it.ok[u]) continue;
+      const uint32_t kt = w->tab[n_in][it.pp[u]] + lp_t;
+      const int64_t e0 = PAIR ? d.out_off + 2 * (int64_t)kt
+                              : d.out_off + (int64_t)(2 * kt) * B + (int64_t)(it.vv[u] * VB);
+      const int64_t e1 = PAIR ? e0 + 1 : e0 + B;
+      if (!QT_RANGE_OK(e0, 1, 2, -1) || !QT_RANGE_OK(e1, VB, 2, -1)) continue;
+      if (full) {
+        stv<Real, VB>(data, e0, p0[u]);
+        stv<Real, VB>(data, e1, p1[u]);
+      } else {
+#pragma unroll
+        for (int v = 0; v < VB; ++v) {
+          atomic_add_cx<Real>(data, e0 + v, p0[u].c[v]);
+          atomic_add_cx<Real>(data, e1 + v, p1[u].c[v]);
+        }
+      }
+    }
+  }
+}
+
+// Zero step (kStepZero): clear rows [r0, r1) x B of the region at out_off.
+template <class Real, int VB, bool PAIR, int U>
+__device__ __forceinline__ void tile_zero(WarpTile* w, Real* __restrict__ data, const TileGeom& g, int64_t r0,
+                                          int64_t r1, int rip, int v0, bool lane_on) {
+  const DevBucket& d = w->d;
+  const int Q = g.P * g.VC;
+  Pack<Real, VB> z{};
+  for (int q0 = 0; q0 < Q; q0 += U) {
+    const ItemSet<U> it = make_items<U>(g, q0, Q, r0, r1, rip, v0, lane_on);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (!it.ok[u]) continue;
+      const int64_t e = PAIR ? d.out_off + (int64_t)it.y[u] : d.out_off + (int64_t)it.y[u] * g.B + (int64_t)(it.vv[u] * VB);
+      stv<Real, VB>(data, e, z);
+    }
+  }
+}
+
+template <class Real> struct RedBuf;
+template <> struct RedBuf<float> {
+  static __device__ __forceinline__ float* get(WarpTile* w) { return &w->redf[0][0]; }
+};
+template <> struct RedBuf<double> {
+  static __device__ __forceinline__ double* get(WarpTile* w) { return &w->redd[0][0]; }
+};
+
+// Reduction adjoint step (kStepAdjRed) for target row kt: the lane sums its
+// items (completions c in [r0, r1)) of Gbar[y] * prod_{factors} at x = 0, 1,
+// the warp adds the lanes of each vector of angle sets, and one atomic add
+// per target element goes to rows (kt << 1) | x.  Needs Bv <= 32.
+template <class Real, int VB, bool PAIR, bool CG, int U>
+__device__ __forceinline__ void tile_adjred(WarpTile* w, Real* __restrict__ data, const TileGeom& g, int64_t r0,
+                                            int64_t r1, uint32_t kt, int lane, int rip, int v0, bool lane_on,
+                                            DevCtrl* ctrl, int dbg_bucket) {
+  const DevBucket& d = w->d;
+  const int n_in = d.n_in;
+  const int Q = g.P * g.VC;
+  const int B = g.B;
+  Pack<Real, VB> s0, s1;
+#pragma unroll
+  for (int v = 0; v < VB; ++v) {
+    s0.c[v].x = 0;
+    s0.c[v].y = 0;
+    s1.c[v] = s0.c[v];
+  }
+  for (int q0 = 0; q0 < Q; q0 += U) {
+    const ItemSet<U> it = make_items<U>(g, q0, Q, r0, r1, rip, v0, lane_on);
+    Pack<Real, VB> p0[U], p1[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int v = 0; v < VB; ++v) {
+        p0[u].c[v].x = 1;
+        p0[u].c[v].y = 0;
+        p1[u].c[v] = p0[u].c[v];
+      }
+    for (int i = 0; i < n_in; ++i) {
+      Pack<Real, VB> a0[U], a1[U];
+      load_input<Real, VB, PAIR, CG, U>(w, i, w->lpart[i][lane], it, data, g, a0, a1, ctrl, dbg_bucket);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        pmul<Real, VB>(p0[u], a0[u]);
+        pmul<Real, VB>(p1[u], a1[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (!it.ok[u]) continue;
+#pragma unroll
+      for (int v = 0; v < VB; ++v) {
+        s0.c[v] = cadd<Real>(s0.c[v], p0[u].c[v]);
+        s1.c[v] = cadd<Real>(s1.c[v], p1[u].c[v]);
+      }
+    }
+  }
+  // lane sums -> per-vector sums (lanes rip * Bv + v share vector v)
+  Real* red = RedBuf<Real>::get(w);
+  const int per = 4 / (int)(sizeof(Real) / 4);  // Real slots per lane: 4 floats or 2 doubles
+#pragma unroll
+  for (int v = 0; v < VB; ++v) {
+    __syncwarp();
+    red[lane * per + 0] = s0.c[v].x;
+    red[lane * per + 1] = s0.c[v].y;
+    if (per == 4) {
+      red[lane * per + 2] = s1.c[v].x;
+      red[lane * per + 3] = s1.c[v].y;
+    }
+    __syncwarp();
+    if (lane_on && rip == 0) {
+      typename Cx<Real>::T t0, t1;
+      t0.x = 0;
+      t0.y = 0;
+      t1 = t0;
+      for (int r = 0; r < g.RP; ++r) {
+        const int l = r * g.Bv + v0;
+        t0.x += red[l * per + 0];
+        t0.y += red[l * per + 1];
+        if (per == 4) {
+          t1.x += red[l * per + 2];
+          t1.y += red[l * per + 3];
+        }
+      }
+      const int64_t e0 = PAIR ? d.out_off + 2 * (int64_t)kt
+                              : d.out_off + (int64_t)(2 * kt) * B + (int64_t)(v0 * VB + v);
+      if (QT_RANGE_OK(e0, 1, 2, -1)) atomic_add_cx<Real>(data, e0, t0);
+      if (per == 4) {
+        const int64_t e1 = PAIR ? e0 + 1 : e0 + B;
+        if (QT_RANGE_OK(e1, 1, 2, -1)) atomic_add_cx<Real>(data, e1, t1);
+      }
+    }
+    if (per == 2) {  // complex128: second pass for x = 1
+      __syncwarp();
+      red[lane * per + 0] = s1.c[v].x;
+      red[lane * per + 1] = s1.c[v].y;
+      __syncwarp();
+      if (lane_on && rip == 0) {
+        typename Cx<Real>::T t1;
+        t1.x = 0;
+        t1.y = 0;
+        for (int r = 0; r < g.RP; ++r) {
+          const int l = r * g.Bv + v0;
+          t1.x += red[l * per + 0];
+          t1.y += red[l * per + 1];
+        }
+        const int64_t e1 = PAIR ? d.out_off + 2 * (int64_t)kt + 1
+                                : d.out_off + (int64_t)(2 * kt + 1) * B + (int64_t)(v0 * VB + v);
+        if (QT_RANGE_OK(e1, 1, 2, -1)) atomic_add_cx<Real>(data, e1, t1);
+      }
+    }
+  }
+  __syncwarp();
+}
+
 // One warp evaluates output rows [r0, r1) of the bucket in w->d (all B angle
 // sets).  r0 is a multiple of g.R.  The pass table tab[i][p] =
 // pext(r0 + p * RP, mask_i) is built here; the lane parts must already be in
 // w->lpart.  Per item an input row is one table read plus one add.
-template <class Real, int VB, bool PAIR, bool CG>
+template <class Real, int VB, bool PAIR, bool CG, bool GRAD = false>
 __device__ __forceinline__ void warp_tile(WarpTile* w, Real* __restrict__ data, const TileGeom& g, int64_t r0,
-                                          int64_t r1, int lane, DevCtrl* ctrl = nullptr, int dbg_bucket = -1) {
+                                          int64_t r1, int lane, DevCtrl* ctrl = nullptr, int dbg_bucket = -1,
+                                          uint32_t kt = 0) {
   const DevBucket& d = w->d;
-  const int n_in = d.n_in;
+  const int n_rec = d.kind == kStepAdj ? d.n_in + 1 : d.n_in;
   int rip, v0;
   bool lane_on;
   lane_slot(g, lane, &rip, &v0, &lane_on);
   const int P = g.P;
-  for (int pp = lane; pp < P; pp += 32) {
-    const uint32_t yp = (uint32_t)(r0 + (int64_t)pp * g.RP);
-    for (int i = 0; i < n_in; ++i) w->tab[i][pp] = pext_in(yp, d.in[i]);
+  if (GRAD && d.kind == kStepAdjRed) {  // rows are completions: y = pdep(kt, mask_t) | pdep(c, ~mask_t)
+    const uint32_t yt = pdep_in(kt, d.in[d.n_in]);
+    for (int pp = lane; pp < P; pp += 32) {
+      const uint32_t yp = yt | pdep_in((uint32_t)(r0 + (int64_t)pp * g.RP), d.in[d.n_in + 1]);
+      for (int i = 0; i < d.n_in; ++i) w->tab[i][pp] = pext_in(yp, d.in[i]);
+    }
+  } else {
+    for (int pp = lane; pp < P; pp += 32) {
+      const uint32_t yp = (uint32_t)(r0 + (int64_t)pp * g.RP);
+      for (int i = 0; i < n_rec; ++i) w->tab[i][pp] = pext_in(yp, d.in[i]);
+    }
   }
   __syncwarp();
-  tile_items<Real, VB, PAIR, CG, 2, 0>(w, data, g, r0, r1, lane, rip, v0, lane_on, ctrl, dbg_bucket);
+  if (!GRAD || d.kind == kStepFwd)
+    tile_items<Real, VB, PAIR, CG, 2, 0>(w, data, g, r0, r1, lane, rip, v0, lane_on, ctrl, dbg_bucket);
+  else if (d.kind == kStepAdj)
+    tile_adjoint<Real, VB, PAIR, CG, 2>(w, data, g, r0, r1, lane, rip, v0, lane_on, ctrl, dbg_bucket);
+  else if (d.kind == kStepAdjRed)
+    tile_adjred<Real, VB, PAIR, CG, 2>(w, data, g, r0, r1, kt, lane, rip, v0, lane_on, ctrl, dbg_bucket);
+  else
+    tile_zero<Real, VB, PAIR, 2>(w, data, g, r0, r1, rip, v0, lane_on);
 }
 
 }  // namespace dev

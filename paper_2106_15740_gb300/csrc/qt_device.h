@@ -24,10 +24,11 @@ struct DevInput {
   uint32_t mask;
   int32_t nruns;
   uint32_t run[kDevMaxRuns];   // src | len << 8 | dst << 16
-  int32_t flags;               // kInLeaf: written before the launch, read through L1
+  int32_t flags;               // kIn* bits below
   int32_t pad;
 };
-constexpr int32_t kInLeaf = 1;
+constexpr int32_t kInLeaf = 1;    // written before the launch, read through L1
+constexpr int32_t kInNoPair = 2;  // one row per output row (no eliminated-variable bit): an adjoint
 
 // Work split of a bucket into warp tiles (same for every bucket of a plan,
 // fixed by B).  A warp tile covers R = P * RP consecutive output rows,
@@ -45,15 +46,46 @@ struct TileGeom {
   int64_t data_elems;  // size of the data region, for the QT_DEVICE_CHECKS build
 };
 
+// Step kinds of an edge chain.
+//   kStepFwd : bucket product-sum, out[y] = sum_x prod_i in_i[(pext(y) << 1) | x]
+//   kStepAdj : adjoint of one input t of a bucket (reverse sweep): for every
+//              output row y of the bucket, c_x = Gbar[y] * prod_{i != t} in_i
+//              at x = 0, 1 goes to row (pext(y, mask_t) << 1) | x of t's
+//              adjoint -- a plain store if t holds every output variable
+//              (kAdjFull), an atomic add otherwise.  in[0..n_in-1] are the
+//              factors (Gbar first, flagged kInNoPair, unless kAdjUnitG),
+//              in[n_in] describes the target (mask and runs; off = out_off).
+//   kStepZero: clear n_rows x B elements at out_off (an atomic target).
+//   kStepAdjRed: the adjoint of a target t that lacks some of the bucket's
+//              variables, as a reduction: each warp tile fixes one target row
+//              k_t (of 2^tgt_bits) and sums over a chunk of the n_rows
+//              completions (values of the missing variables, bits of the
+//              complement mask), y = pdep(k_t, mask_t) | pdep(c, ~mask_t);
+//              one atomic add per target element per tile.  in[n_in] is the
+//              target record, in[n_in + 1] the complement record.
+constexpr int32_t kStepFwd = 0, kStepAdj = 1, kStepZero = 2, kStepAdjRed = 3;
+constexpr int32_t kAdjFull = 1, kAdjUnitG = 2;
+
 struct DevBucket {
   int64_t out_off;             // element offset of the output
-  int64_t n_rows;              // 2^out_rank
+  int64_t n_rows;              // rows iterated: 2^out_rank of the bucket
   int32_t out_rank;
-  int32_t n_in;
-  int32_t dep;                 // bucket that must be complete before this one (-1: none)
-  int32_t ntask;               // tiles of this bucket in the persistent queue
+  int32_t n_in;                // factors (for kStepAdj the target follows them)
+  int32_t dep;                 // step that must be complete before this one (-1: none)
+  int32_t ntask;               // tiles of this step in the persistent queue
+  int32_t kind;                // kStep*
+  int32_t aflags;              // kAdj* bits (kStepAdj)
+  int32_t tgt_bits;            // kStepAdjRed: target rows 2^tgt_bits (times x = 0, 1)
+  int32_t pad_;
   DevInput in[kDevMaxIn];
 };
+
+// Warp tiles of a step: target rows x chunks of n_rows (kStepAdjRed), else
+// chunks of n_rows.
+inline int64_t step_tiles(const DevBucket& d, int64_t R) {
+  const int64_t chunks = (d.n_rows + R - 1) / R;
+  return d.kind == kStepAdjRed ? (chunks << d.tgt_bits) : chunks;
+}
 
 // Leaf factor: product of the leaves of one bucket over the union of their
 // variables, materialised per angle set.  A leaf is packed as

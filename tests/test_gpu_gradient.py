@@ -1,0 +1,119 @@
+"""GPU parity of the adjoint gradient dE/dgamma, dE/dbeta (reverse bucket sweep).
+
+References: the oracle's parameter-shift gradient on a 2^n state vector
+(exact), central finite differences (h = 1e-5) of the oracle's lightcone
+energy for a seeded sample of single edges, and central finite differences
+of the complex128 GPU energy for the whole 60-vertex p = 4 graph.
+
+Tolerances: complex128 1e-9 absolute against the exact gradient (rounding of
+a few thousand FP64 products and sums); against finite differences the FD
+truncation error O(h^2 |E'''|) ~ 1e-8 dominates.  complex64: 2e-5 per unit of
+gradient scale (FP32 rounding, about 100 bucket steps of 2^-24 each).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import gradients as gr
+from oracle import lightcone as lc
+from oracle import statevector as sv
+from workloads import random_angles, random_regular_graph, workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib(qtlib):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return qtlib
+
+
+def _grad_plan(n, edges, p, B, dtype, **kw):
+    from paper_2106_15740_gb300.energy import EnergyPlan
+    return EnergyPlan(n, edges, p, batch=B, dtype=dtype, mode="persistent", gradient=True, device="cuda:0", **kw)
+
+
+def _run(plan, g, b):
+    gd = torch.tensor(np.asarray(g).reshape(plan.batch, plan.p), device="cuda:0")
+    bd = torch.tensor(np.asarray(b).reshape(plan.batch, plan.p), device="cuda:0")
+    e, grad = plan.energy(gd, bd, grad=True)
+    plan.check()
+    return e.cpu().numpy(), grad.cpu().numpy()
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("n,p,B,seed", [(12, 2, 2, 5), (14, 3, 1, 6), (10, 3, 3, 7)])
+def test_gradient_matches_parameter_shift(dtype, n, p, B, seed):
+    edges = random_regular_graph(n, 3, seed)
+    g, b = random_angles(B, p, 70 + seed)
+    plan = _grad_plan(n, edges, p, B, dtype)
+    e, grad = _run(plan, g, b)
+    for k in range(B):
+        dg, db = gr.param_shift_gradient(n, edges, g[k], b[k])
+        ref = np.concatenate([dg, db])
+        scale = max(1.0, np.abs(ref).max())
+        tol = 1e-9 if dtype == "c128" else 2e-5 * scale
+        np.testing.assert_allclose(grad[k], ref, atol=tol, rtol=0)
+        assert abs(e[k] - sv.energy(n, edges, g[k], b[k])) <= (1e-10 if dtype == "c128" else 1e-5) * len(edges)
+
+
+def test_gradient_plan_energy_equals_forward_plan():
+    """The forward part of a gradient plan keeps every intermediate; the
+    energies must be the ones the forward-only plan gives."""
+    from paper_2106_15740_gb300.energy import EnergyPlan
+    n, edges, p, g, b = workload("n100_p3", batch=2)
+    fwd = EnergyPlan(n, edges, p, batch=2, dtype="c128", mode="persistent", device="cuda:0")
+    gd, bd = torch.tensor(g, device="cuda:0"), torch.tensor(b, device="cuda:0")
+    e_fwd = fwd.energy(gd, bd).cpu().numpy()
+    e_grad, _ = _run(_grad_plan(n, edges, p, 2, "c128"), g, b)
+    np.testing.assert_allclose(e_grad, e_fwd, atol=1e-12, rtol=0)
+
+
+def test_n60_p4_single_edges_vs_oracle_finite_differences():
+    """Edge-range plans give dZ_e-based gradients of one edge's energy term;
+    compare with central differences of the oracle's lightcone value."""
+    n, edges, p, g, b = workload("n60_p4")
+    rng = np.random.default_rng(4)
+    h = 1e-5
+    for e in sorted(rng.choice(len(edges), 4, replace=False)):
+        plan = _grad_plan(n, edges, p, 1, "c128", edge_range=(int(e), int(e) + 1))
+        energy, grad = _run(plan, g, b)
+
+        def e_term(gg, bb):
+            return 0.5 * (1.0 - lc.lightcone_zz(n, edges, p, gg, bb, int(e))[0].real)
+
+        dg, db = gr.fd_gradient(e_term, g[0], b[0], h=h)
+        np.testing.assert_allclose(grad[0], np.concatenate([dg, db]), atol=2e-8, rtol=0)
+        assert abs(energy[0] - e_term(g[0], b[0])) < 1e-10
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_n60_p4_full_graph_vs_gpu_finite_differences(dtype):
+    """Whole 90-edge graph: the adjoint gradient against central differences
+    of the complex128 GPU energy (forward plan, h = 1e-5)."""
+    from paper_2106_15740_gb300.energy import EnergyPlan
+    n, edges, p, g, b = workload("n60_p4")
+    e, grad = _run(_grad_plan(n, edges, p, 1, dtype), g, b)
+    fwd = EnergyPlan(n, edges, p, batch=1, dtype="c128", mode="persistent", device="cuda:0")
+    h = 1e-5
+
+    def energy(gg, bb):
+        return float(fwd.energy(torch.tensor(gg.reshape(1, p), device="cuda:0"),
+                                torch.tensor(bb.reshape(1, p), device="cuda:0")).cpu().numpy()[0])
+
+    dg, db = gr.fd_gradient(energy, g[0], b[0], h=h)
+    ref = np.concatenate([dg, db])
+    tol = 1e-7 if dtype == "c128" else 2e-5 * max(1.0, np.abs(ref).max())
+    np.testing.assert_allclose(grad[0], ref, atol=tol, rtol=0)
+
+
+def test_gradient_requires_gradient_plan():
+    from paper_2106_15740_gb300 import binding as qb
+    from paper_2106_15740_gb300.energy import EnergyPlan
+    n, edges, p, g, b = workload("n16_p1")
+    plan = EnergyPlan(n, edges, p, batch=1, dtype="c128", mode="persistent", device="cuda:0")
+    with pytest.raises(qb.QTError) as ei:
+        plan.energy(torch.tensor(g, device="cuda:0"), torch.tensor(b, device="cuda:0"), grad=True)
+    assert ei.value.status == qb.QT_ESTATE
