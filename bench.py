@@ -158,6 +158,55 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def _time_calls(plan, g, b, grad, reps, torch):
+    """Mean device time (ms) of `reps` plan evaluations after two warm-ups."""
+    for _ in range(2):
+        plan.energy(g, b, grad=grad)
+    plan.check()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(reps):
+        plan.energy(g, b, grad=grad)
+    t1.record()
+    torch.cuda.synchronize()
+    plan.check()
+    return t0.elapsed_time(t1) / reps
+
+
+def gradient_and_comparator(dev, torch):
+    """Energy-gradient throughput on the 60-vertex p = 4 workload (8 angles,
+    one angle set, complex64 adjoint sweep), and the plain per-edge complex128
+    contraction (one kernel launch per bucket, edge after edge, one angle set
+    at a time) on the gradient workload and on the bench workload."""
+    from paper_2106_15740_gb300.energy import EnergyPlan
+    from workloads import workload
+    out = {}
+    n, edges, p, g, b = workload("n60_p4")
+    gd, bd = torch.tensor(g, device=dev), torch.tensor(b, device=dev)
+    plan = EnergyPlan(n, edges, p, batch=1, dtype="c64", mode="persistent", gradient=True, device=dev)
+    ms_grad = _time_calls(plan, gd, bd, True, 5, torch)
+    plan.close()
+    plan = EnergyPlan(n, edges, p, batch=1, dtype="c128", mode="per_bucket", device=dev)
+    ms_loop = _time_calls(plan, gd, bd, False, 3, torch)
+    plan.close()
+    out["grad"] = {"metric": "energy-grad evals/sec", "value": 1e3 / ms_grad, "unit": "grad_evals/s",
+                   "ms_per_eval": ms_grad, "dtype": "c64",
+                   "workload": "random 3-regular N=60 p=4 (seed 3), 90 edge lightcones, dE/dgamma and dE/dbeta "
+                               "(8 angles) by the adjoint bucket sweep, one angle set",
+                   "per_edge_c128_forward_ms": ms_loop,
+                   "speedup_vs_per_edge_c128_forward": ms_loop / ms_grad}
+    n, edges, p, g, b = workload("n100_p4", batch=1)
+    gd, bd = torch.tensor(g, device=dev), torch.tensor(b, device=dev)
+    plan = EnergyPlan(n, edges, p, batch=1, dtype="c128", mode="per_bucket", device=dev)
+    ms_one = _time_calls(plan, gd, bd, False, 2, torch)
+    plan.close()
+    out["per_edge_c128_loop"] = {"ms_per_angle_set": ms_one, "ms_per_step_equivalent": 64 * ms_one,
+                                 "edge_evals_per_s": len(edges) / (ms_one * 1e-3),
+                                 "what": "same graph, complex128, one launch per bucket, edges one after "
+                                         "another, one angle set per call (64 calls = one bench step)"}
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -268,6 +317,8 @@ def run_ours(args):
         if profile_only:
             res["profile_only"] = f"{WORKLOAD} (not the bench workload)"
         if not args.no_cpu_baseline:
+            res.update(gradient_and_comparator(dev, torch))
+            res["per_edge_c128_loop"]["speedup_of_value"] = res["value"] / res["per_edge_c128_loop"]["edge_evals_per_s"]
             res["cpu_baseline"] = cpu_baseline()
         print(json.dumps(res))
     if pg:

@@ -215,6 +215,17 @@ qt_status qt_plan_energy_static(qt_plan* plan, const double* gamma, const double
                                 double* energy, double* edge_zz, void* stream);
 size_t qt_static_scratch_bytes(void);
 
+/* Failure-detection hooks (host-side fault injection; no device fault).
+ * qt_plan_set_wait_limit sets how many polls a persistent-queue dependency
+ * wait makes before it gives up (default 4194304; each poll sleeps ~0.1 us).
+ * qt_plan_inject_stall(plan, 1) makes the next uploads give the dependency of
+ * the last queued task that has one a tile count that is never reached, so
+ * its waiters run out: the call then ends with every warp stopped and
+ * qt_plan_check returns QT_ETIMEOUT; the CUDA context stays usable.
+ * qt_plan_inject_stall(plan, 0) restores the plan. */
+qt_status qt_plan_set_wait_limit(qt_plan* plan, int32_t polls);
+qt_status qt_plan_inject_stall(qt_plan* plan, int32_t enable);
+
 void qt_plan_free(qt_plan* plan);
 
 /* One-shot energy (and gradient if grad != NULL) with HOST pointers: plans

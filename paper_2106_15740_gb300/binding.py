@@ -29,7 +29,7 @@ EXPORTS = [
     "qt_plan_edge_widths", "qt_plan_energy", "qt_plan_check", "qt_plan_energy_host",
     "qt_plan_free", "qt_energy_workspace_size", "qt_energy", "qt_last_error",
     "qt_plan_set_profiling", "qt_plan_kernel_times", "qt_plan_energy_static",
-    "qt_static_scratch_bytes",
+    "qt_static_scratch_bytes", "qt_plan_set_wait_limit", "qt_plan_inject_stall",
 ]
 
 
@@ -81,6 +81,8 @@ def lib():
             "qt_plan_set_profiling": [vp, i32],
             "qt_plan_kernel_times": [vp, C.POINTER(C.c_float), i32, pi32],
             "qt_plan_energy_static": [vp, vp, vp, vp, vp, vp],
+            "qt_plan_set_wait_limit": [vp, i32],
+            "qt_plan_inject_stall": [vp, i32],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -243,6 +245,14 @@ def qt_plan_energy_static(plan, gamma_ptr, beta_ptr, energy_ptr, edge_zz_ptr, st
 
 def qt_static_scratch_bytes():
     return lib().qt_static_scratch_bytes()
+
+
+def qt_plan_set_wait_limit(plan, polls):
+    _check(lib().qt_plan_set_wait_limit(plan, int(polls)))
+
+
+def qt_plan_inject_stall(plan, enable):
+    _check(lib().qt_plan_inject_stall(plan, int(bool(enable))))
 
 
 def qt_plan_free(plan):

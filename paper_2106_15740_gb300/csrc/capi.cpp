@@ -290,6 +290,30 @@ qt_status qt_plan_kernel_times(qt_plan* plan, float* ms, int32_t cap, int32_t* n
   return plan_kernel_times(&plan->P, ms, cap, n);
 }
 
+qt_status qt_plan_set_wait_limit(qt_plan* plan, int32_t polls) {
+  if (!plan || polls < 1) return fail(QT_EINVAL, "plan is NULL or polls < 1");
+  plan->P.spin_limit = polls;
+  return QT_OK;
+}
+
+qt_status qt_plan_inject_stall(qt_plan* plan, int32_t enable) {
+  if (!plan) return fail(QT_EINVAL, "plan is NULL");
+  Plan& P = plan->P;
+  P.stall_step = -1;
+  if (enable) {
+    for (size_t t = P.tasks.size(); t-- > 0;) {
+      const int32_t dep = P.buckets[P.tasks[t].bucket].dep;
+      if (dep >= 0) {
+        P.stall_step = dep;
+        break;
+      }
+    }
+    if (P.stall_step < 0) return fail(QT_ESTATE, "no queued task waits on another (persistent plan needed)");
+  }
+  P.bound_ws = nullptr;  // upload again with (or without) the stall
+  return QT_OK;
+}
+
 void qt_plan_free(qt_plan* plan) { delete plan; }
 
 qt_status qt_energy_workspace_size(const qt_graph* g, int32_t p, int32_t B, qt_dtype dtype, int32_t gradient,

@@ -19,6 +19,7 @@
 #include "engine.h"
 
 #include <algorithm>
+#include <cstddef>
 #include <cstring>
 #include <map>
 #include <queue>
@@ -436,6 +437,8 @@ qt_status compile_plan(Plan* P) {
   o = align256(o + sizeof(double) * 4 * (size_t)B * p);
   L.dz = o;
   if (grad) o = align256(o + sizeof(double) * 2 * (size_t)n_edges * B * 2 * p);
+  L.gpart = o;
+  if (grad) o = align256(o + sizeof(double) * 2 * (size_t)P->leaf.size() * B * kDevMaxLeaves);
   L.data = o;
   o = align256(o + (size_t)es * (size_t)P->data_elems);
   L.total = o;
@@ -473,6 +476,13 @@ qt_status run_plan(Plan* P, const double* gamma, const double* beta, double* ene
     if (!P->buckets.empty())
       QT_CUDA(cudaMemcpyAsync(base + L.buckets, P->buckets.data(), sizeof(DevBucket) * P->buckets.size(),
                               cudaMemcpyHostToDevice, s));
+    if (P->stall_step >= 0 && P->stall_step < (int32_t)P->buckets.size()) {
+      // failure-detection hook: a tile count that no warp will ever reach
+      const int32_t unreachable = P->buckets[P->stall_step].ntask + 1;
+      QT_CUDA(cudaMemcpyAsync(base + L.buckets + sizeof(DevBucket) * P->stall_step + offsetof(DevBucket, ntask),
+                              &unreachable, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+      QT_CUDA(cudaStreamSynchronize(s));
+    }
     if (!P->tasks.empty())
       QT_CUDA(cudaMemcpyAsync(base + L.tasks, P->tasks.data(), sizeof(DevTask) * P->tasks.size(),
                               cudaMemcpyHostToDevice, s));
@@ -532,9 +542,9 @@ qt_status run_plan(Plan* P, const double* gamma, const double* beta, double* ene
   QT_CUDA(launch_energy(dtype, data, (const int64_t*)(base + L.scal_off), (const int32_t*)(base + L.scal_begin),
                         (int32_t)P->edges.size(), B, energy, edge_zz, s));
   if (grad)
-    QT_CUDA(launch_gradient(dtype, (const DevLeafFactor*)(base + L.leaf), (const int32_t*)(base + L.leaf_first),
-                            (int32_t)P->edges.size(), P->lbar_shift, trig, P->p, B, data, (double*)(base + L.dz),
-                            grad, s));
+    QT_CUDA(launch_gradient(dtype, (const DevLeafFactor*)(base + L.leaf), (int32_t)P->leaf.size(),
+                            (const int32_t*)(base + L.leaf_first), (int32_t)P->edges.size(), P->lbar_shift, trig,
+                            P->p, B, data, (double*)(base + L.gpart), (double*)(base + L.dz), grad, s));
   return QT_OK;
 }
 

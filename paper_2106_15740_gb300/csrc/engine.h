@@ -17,7 +17,7 @@ namespace qt {
 
 struct WsLayout {
   size_t ctrl = 0, done = 0, buckets = 0, tasks = 0, leaf = 0, leaf_first = 0, scal_off = 0, scal_begin = 0;
-  size_t angles = 0, results = 0, trig = 0, dz = 0, data = 0, total = 0;
+  size_t angles = 0, results = 0, trig = 0, dz = 0, gpart = 0, data = 0, total = 0;
 };
 
 struct Plan {
@@ -46,6 +46,9 @@ struct Plan {
 
   // statistics
   double alg_bytes = 0.0, flops = 0.0;
+
+  // failure-detection hook: step whose uploaded tile count is made unreachable
+  int32_t stall_step = -1;
 
   // state
   const void* bound_ws = nullptr;

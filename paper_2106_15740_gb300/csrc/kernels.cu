@@ -243,28 +243,24 @@ __device__ __forceinline__ double2 leaf_deriv(uint32_t w, uint32_t z, const doub
   return v;
 }
 
-// dZ_e/dtheta for every edge e, angle set b and angle theta (0..p-1: gamma,
-// p..2p-1: beta): sum over the edge's leaf factors F and their leaves l that
-// carry theta of sum_z Lbar_F[z] * dl(z) * prod_{l' != l} l'(z).  FP64.
+// Per leaf factor F and angle set b: for every leaf l of F that carries an
+// angle, sum_z Lbar_F[z] * dl(z) * prod_{l' != l} l'(z) (FP64), written to
+// part[(f * B + b) * kDevMaxLeaves + l] (zero for leaves without an angle).
 template <class Real>
-__global__ void leafgrad_kernel(const DevLeafFactor* __restrict__ lf, const int32_t* __restrict__ leaf_first,
-                                int32_t n_edges, int64_t lbar_shift, const double* __restrict__ trig, int32_t p,
-                                int32_t B, const Real* __restrict__ data, double* __restrict__ dz) {
+__global__ void leafgrad_kernel(const DevLeafFactor* __restrict__ lf, int32_t n_lf, int64_t lbar_shift,
+                                const double* __restrict__ trig, int32_t p, int32_t B,
+                                const Real* __restrict__ data, double2* __restrict__ part) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t n = (int64_t)n_edges * B * 2 * p;
-  if (idx >= n) return;
-  const int32_t th = (int32_t)(idx % (2 * p));
-  const int32_t b = (int32_t)((idx / (2 * p)) % B);
-  const int32_t e = (int32_t)(idx / ((int64_t)2 * p * B));
-  const uint32_t want_kind = th < p ? 1u : 2u;
-  const uint32_t want_layer = (uint32_t)(th < p ? th + 1 : th - p + 1);
-  double ar = 0.0, ai = 0.0;
-  for (int32_t f = leaf_first[e]; f < leaf_first[e + 1]; ++f) {
-    const DevLeafFactor F = lf[f];
-    for (int32_t l = 0; l < F.n_leaves; ++l) {
-      const uint32_t w = F.leaf[l];
-      if ((w & 3u) != want_kind || (w >> 16) != want_layer) continue;
-      const double* tr = trig + ((int64_t)b * p + (int64_t)want_layer - 1) * 4;
+  if (idx >= (int64_t)n_lf * B) return;
+  const int32_t f = (int32_t)(idx / B), b = (int32_t)(idx % B);
+  const DevLeafFactor F = lf[f];
+  for (int32_t l = 0; l < kDevMaxLeaves; ++l) {
+    double ar = 0.0, ai = 0.0;
+    const uint32_t w = l < F.n_leaves ? F.leaf[l] : 0u;
+    const uint32_t kind = w & 3u;
+    if (l < F.n_leaves && (kind == 1u || kind == 2u)) {
+      const int32_t layer = (int32_t)(w >> 16);
+      const double* tr = trig + ((int64_t)b * p + layer - 1) * 4;
       for (uint32_t z = 0; z < (1u << F.rank); ++z) {
         double2 t = leaf_deriv(w, z, tr);
         for (int32_t l2 = 0; l2 < F.n_leaves; ++l2) {
@@ -279,6 +275,33 @@ __global__ void leafgrad_kernel(const DevLeafFactor* __restrict__ lf, const int3
         ar += gr * t.x - gi * t.y;
         ai += gr * t.y + gi * t.x;
       }
+    }
+    part[idx * kDevMaxLeaves + l] = make_double2(ar, ai);
+  }
+}
+
+// dZ_e/dtheta for every edge e, angle set b and angle theta (0..p-1: gamma,
+// p..2p-1: beta): the per-leaf parts of the edge's factors whose leaf carries
+// theta, summed in a fixed order.
+__global__ void edgegrad_kernel(const DevLeafFactor* __restrict__ lf, const int32_t* __restrict__ leaf_first,
+                                int32_t n_edges, int32_t p, int32_t B, const double2* __restrict__ part,
+                                double* __restrict__ dz) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n_edges * B * 2 * p) return;
+  const int32_t th = (int32_t)(idx % (2 * p));
+  const int32_t b = (int32_t)((idx / (2 * p)) % B);
+  const int32_t e = (int32_t)(idx / ((int64_t)2 * p * B));
+  const uint32_t want_kind = th < p ? 1u : 2u;
+  const uint32_t want_layer = (uint32_t)(th < p ? th + 1 : th - p + 1);
+  double ar = 0.0, ai = 0.0;
+  for (int32_t f = leaf_first[e]; f < leaf_first[e + 1]; ++f) {
+    const int32_t nl = lf[f].n_leaves;
+    for (int32_t l = 0; l < nl; ++l) {
+      const uint32_t w = lf[f].leaf[l];
+      if ((w & 3u) != want_kind || (w >> 16) != want_layer) continue;
+      const double2 v = part[((int64_t)f * B + b) * kDevMaxLeaves + l];
+      ar += v.x;
+      ai += v.y;
     }
   }
   dz[2 * idx] = ar;
@@ -432,17 +455,20 @@ cudaError_t launch_energy(int dtype, const void* data, const int64_t* scal_off, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_gradient(int dtype, const DevLeafFactor* lf, const int32_t* leaf_first, int32_t n_edges,
-                            int64_t lbar_shift, const double* trig, int32_t p, int32_t B, const void* data, double* dz,
-                            double* grad, cudaStream_t s) {
-  const int64_t n = (int64_t)n_edges * B * 2 * p;
-  const int64_t blocks = (n + 127) / 128;
-  if (dtype == QT_C64)
-    dev::leafgrad_kernel<float><<<(int)blocks, 128, 0, s>>>(lf, leaf_first, n_edges, lbar_shift, trig, p, B,
-                                                            (const float*)data, dz);
-  else
-    dev::leafgrad_kernel<double><<<(int)blocks, 128, 0, s>>>(lf, leaf_first, n_edges, lbar_shift, trig, p, B,
-                                                             (const double*)data, dz);
+cudaError_t launch_gradient(int dtype, const DevLeafFactor* lf, int32_t n_lf, const int32_t* leaf_first,
+                            int32_t n_edges, int64_t lbar_shift, const double* trig, int32_t p, int32_t B,
+                            const void* data, double* part, double* dz, double* grad, cudaStream_t s) {
+  const int64_t n1 = (int64_t)n_lf * B;
+  if (n1 > 0) {
+    if (dtype == QT_C64)
+      dev::leafgrad_kernel<float><<<(int)((n1 + 127) / 128), 128, 0, s>>>(lf, n_lf, lbar_shift, trig, p, B,
+                                                                        (const float*)data, (double2*)part);
+    else
+      dev::leafgrad_kernel<double><<<(int)((n1 + 127) / 128), 128, 0, s>>>(lf, n_lf, lbar_shift, trig, p, B,
+                                                                         (const double*)data, (double2*)part);
+  }
+  const int64_t n2 = (int64_t)n_edges * B * 2 * p;
+  dev::edgegrad_kernel<<<(int)((n2 + 127) / 128), 128, 0, s>>>(lf, leaf_first, n_edges, p, B, (const double2*)part, dz);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   dev::gradreduce_kernel<<<(B * 2 * p + 127) / 128, 128, 0, s>>>(dz, n_edges, p, B, grad);

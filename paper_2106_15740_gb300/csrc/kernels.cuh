@@ -513,6 +513,30 @@ __device__ __forceinline__ void tile_adjred(WarpTile* w, Real* __restrict__ data
     }
   }
   // lane sums -> per-vector sums (lanes rip * Bv + v share vector v)
+  if ((g.Bv & (g.Bv - 1)) == 0) {
+    // Bv a power of two: RP * Bv = 32, so a butterfly over the lane bits at
+    // and above Bv adds the RP lanes of each vector; lanes < Bv keep the sums.
+#pragma unroll
+    for (int v = 0; v < VB; ++v) {
+      for (int off = 16; off >= g.Bv; off >>= 1) {
+        s0.c[v].x += __shfl_xor_sync(0xffffffffu, s0.c[v].x, off);
+        s0.c[v].y += __shfl_xor_sync(0xffffffffu, s0.c[v].y, off);
+        s1.c[v].x += __shfl_xor_sync(0xffffffffu, s1.c[v].x, off);
+        s1.c[v].y += __shfl_xor_sync(0xffffffffu, s1.c[v].y, off);
+      }
+    }
+    if (lane < g.Bv) {
+#pragma unroll
+      for (int v = 0; v < VB; ++v) {
+        const int64_t e0 = PAIR ? d.out_off + 2 * (int64_t)kt
+                                : d.out_off + (int64_t)(2 * kt) * B + (int64_t)(v0 * VB + v);
+        const int64_t e1 = PAIR ? e0 + 1 : e0 + B;
+        if (QT_RANGE_OK(e0, 1, 2, -1)) atomic_add_cx<Real>(data, e0, s0.c[v]);
+        if (QT_RANGE_OK(e1, 1, 2, -1)) atomic_add_cx<Real>(data, e1, s1.c[v]);
+      }
+    }
+    return;
+  }
   Real* red = RedBuf<Real>::get(w);
   const int per = 4 / (int)(sizeof(Real) / 4);  // Real slots per lane: 4 floats or 2 doubles
 #pragma unroll

@@ -23,8 +23,8 @@ cudaError_t persistent_occupancy(int dtype, bool grad, int32_t B, int* blocks_pe
 cudaError_t launch_energy(int dtype, const void* data, const int64_t* scal_off, const int32_t* scal_begin,
                           int32_t n_edges, int32_t B, double* energy, double* edge_zz, cudaStream_t s);
 
-cudaError_t launch_gradient(int dtype, const DevLeafFactor* lf, const int32_t* leaf_first, int32_t n_edges,
-                            int64_t lbar_shift, const double* trig, int32_t p, int32_t B, const void* data, double* dz,
-                            double* grad, cudaStream_t s);
+cudaError_t launch_gradient(int dtype, const DevLeafFactor* lf, int32_t n_lf, const int32_t* leaf_first,
+                            int32_t n_edges, int64_t lbar_shift, const double* trig, int32_t p, int32_t B,
+                            const void* data, double* part, double* dz, double* grad, cudaStream_t s);
 
 }  // namespace qt

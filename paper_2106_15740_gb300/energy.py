@@ -107,6 +107,41 @@ class EnergyPlan:
             pass
 
 
+def autotune(n_vertices, edges, p, batch=1, dtype="c64", gradient=False, device="cuda:0", reps=3,
+             lane_items=None, group_rows=(0, 1 << 20), max_workspace=0, edge_range=None, gamma=None, beta=None):
+    """Pick the warp-tile size and bucket grouping of a persistent plan by
+    timing each candidate on the device (CUDA events around `reps` calls after
+    two warm-ups).  Returns (best_options, {candidate: ms}).  Angles default
+    to zeros (the work does not depend on their values)."""
+    device = torch.device(device)
+    if lane_items is None:
+        lane_items = (16, 32, 64) if batch >= 16 else (8, 16, 32)
+    g = torch.zeros((batch, p), dtype=torch.float64, device=device) if gamma is None else gamma
+    b = torch.zeros((batch, p), dtype=torch.float64, device=device) if beta is None else beta
+    timings = {}
+    for li in lane_items:
+        for gr in group_rows:
+            plan = EnergyPlan(n_vertices, edges, p, batch=batch, dtype=dtype, mode="persistent",
+                              gradient=gradient, device=device, lane_items=li, group_rows=gr,
+                              max_workspace=max_workspace, edge_range=edge_range)
+            for _ in range(2):
+                plan.energy(g, b, grad=gradient)
+            plan.check()
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0.record()
+            for _ in range(reps):
+                plan.energy(g, b, grad=gradient)
+            t1.record()
+            torch.cuda.synchronize(device)
+            plan.check()
+            timings[(li, gr)] = t0.elapsed_time(t1) / reps
+            plan.close()
+            del plan
+            torch.cuda.empty_cache()
+    li, gr = min(timings, key=timings.get)
+    return dict(lane_items=li, group_rows=gr), timings
+
+
 def contract_edge(n_vertices, edges, p, gamma, beta, edge, dtype="c128", device="cuda:0"):
     """<Z_j Z_k> of one edge through qt_build_lightcone / qt_order / qt_contract.
     Returns (value, width)."""

@@ -125,3 +125,31 @@ def test_workspace_grows_with_batch_and_precision(qtlib):
             sizes[(B, dt)] = qb.qt_energy_workspace_size(n, edges, p, B, dt, 0)
     assert sizes[(8, qb.QT_C64)] > sizes[(1, qb.QT_C64)]
     assert sizes[(8, qb.QT_C128)] > sizes[(8, qb.QT_C64)]
+
+
+def test_stall_hook_needs_a_waiting_task(qtlib):
+    """Per-bucket plans have no queue, so there is nothing to stall."""
+    from paper_2106_15740_gb300 import binding as qb
+    n, edges, p, g, b = workload("n16_p1")
+    opt = qb.qt_plan_options_default()
+    plan = qb.qt_plan_create(n, edges, p, opt)
+    try:
+        with pytest.raises(qb.QTError) as ei:
+            qb.qt_plan_inject_stall(plan, 1)
+        assert ei.value.status == qb.QT_ESTATE
+        qb.qt_plan_inject_stall(plan, 0)
+        with pytest.raises(qb.QTError):
+            qb.qt_plan_set_wait_limit(plan, 0)
+    finally:
+        qb.qt_plan_free(plan)
+
+
+def test_gradient_plans_need_the_persistent_queue(qtlib):
+    from paper_2106_15740_gb300 import binding as qb
+    n, edges, p, g, b = workload("n16_p1")
+    opt = qb.qt_plan_options_default()
+    opt.gradient = 1
+    opt.mode = qb.QT_MODE_PER_BUCKET
+    with pytest.raises(qb.QTError) as ei:
+        qb.qt_plan_create(n, edges, p, opt)
+    assert ei.value.status == qb.QT_EINVAL
