@@ -349,8 +349,9 @@ qt_status compile_plan(Plan* P) {
         // atomic scatter, whose contention is then at most 32 per element
         d.kind = kStepAdjRed;
         d.in[n + 1] = input_record(all & ~tmask, 0, 0);  // complement record
-        d.n_rows = (int64_t)1 << __builtin_popcount(all & ~tmask);
         d.tgt_bits = __builtin_popcount(tmask);
+        d.comp_bits = __builtin_popcount(all & ~tmask);
+        d.n_rows = (int64_t)1 << (d.tgt_bits + d.comp_bits);  // = 2^out_rank
       }
       P->buckets.push_back(d);
     }

@@ -176,16 +176,9 @@ __global__ void __launch_bounds__(256, 4) persistent_kernel(const DevBucket* __r
         break;
       }
 #endif
-      int64_t tile = task.tile < 0 ? 0 : task.tile;
-      uint32_t kt = 0;
-      if (GRAD && w->d.kind == kStepAdjRed) {  // tile = kt * chunks + chunk
-        const int64_t chunks = (w->d.n_rows + g.R - 1) / g.R;
-        kt = (uint32_t)(tile / chunks);
-        tile -= (int64_t)kt * chunks;
-      }
-      const int64_t r0 = tile * g.R;
+      const int64_t r0 = task.tile < 0 ? 0 : (int64_t)task.tile * g.R;
       const int64_t r1 = r0 + g.R < w->d.n_rows ? r0 + g.R : w->d.n_rows;
-      warp_tile<Real, VB, PAIR, true, GRAD>(w, data, g, r0, r1, lane, ctrl, b, kt);
+      warp_tile<Real, VB, PAIR, true, GRAD>(w, data, g, r0, r1, lane, ctrl, b);
       __syncwarp();  // the next bucket of a group reads what this one wrote
     }
     __threadfence();

@@ -193,6 +193,7 @@ __device__ __forceinline__ void load_bucket(DevBucket* dst, const DevBucket* src
     dst->kind = src->kind;
     dst->aflags = src->aflags;
     dst->tgt_bits = src->tgt_bits;
+    dst->comp_bits = src->comp_bits;
   }
 }
 
@@ -463,18 +464,82 @@ template <> struct RedBuf<double> {
   static __device__ __forceinline__ double* get(WarpTile* w) { return &w->redd[0][0]; }
 };
 
-// Reduction adjoint step (kStepAdjRed) for target row kt: the lane sums its
-// items (completions c in [r0, r1)) of Gbar[y] * prod_{factors} at x = 0, 1,
-// the warp adds the lanes of each vector of angle sets, and one atomic add
-// per target element goes to rows (kt << 1) | x.  Needs Bv <= 32.
+// Reduction adjoint step (kStepAdjRed).  The tile's rows q = kt * 2^comp_bits
+// + c run over target rows kt and their completions c; since 2^comp_bits >=
+// 32 >= RP, all lanes of a pass share kt, which changes every
+// 2^comp_bits / RP passes.  Lanes sum Gbar[y] * prod_{factors} at x = 0, 1
+// while kt stays fixed; at each change the lanes of each vector of angle sets
+// are added (shuffle butterfly when Bv is a power of two, else through shared
+// memory) and one atomic add per target element goes to rows (kt << 1) | x.
+template <class Real, int VB, bool PAIR>
+__device__ __forceinline__ void flush_target(WarpTile* w, Real* __restrict__ data, const TileGeom& g, uint32_t kt,
+                                             Pack<Real, VB>& s0, Pack<Real, VB>& s1, int lane, int rip, int v0,
+                                             bool lane_on, DevCtrl* ctrl, int dbg_bucket) {
+  (void)ctrl;
+  (void)dbg_bucket;
+  const DevBucket& d = w->d;
+  const int B = g.B;
+  if ((g.Bv & (g.Bv - 1)) == 0) {  // RP * Bv = 32: butterfly over the lane bits >= Bv
+#pragma unroll
+    for (int v = 0; v < VB; ++v) {
+      for (int off = 16; off >= g.Bv; off >>= 1) {
+        s0.c[v].x += __shfl_xor_sync(0xffffffffu, s0.c[v].x, off);
+        s0.c[v].y += __shfl_xor_sync(0xffffffffu, s0.c[v].y, off);
+        s1.c[v].x += __shfl_xor_sync(0xffffffffu, s1.c[v].x, off);
+        s1.c[v].y += __shfl_xor_sync(0xffffffffu, s1.c[v].y, off);
+      }
+    }
+  } else {
+    Real* red = RedBuf<Real>::get(w);
+    const int per = 4 / (int)(sizeof(Real) / 4);
+#pragma unroll
+    for (int v = 0; v < VB; ++v) {
+      for (int x = 0; x < 2; ++x) {
+        typename Cx<Real>::T& sv = x == 0 ? s0.c[v] : s1.c[v];
+        __syncwarp();
+        red[lane * per + 0] = sv.x;
+        red[lane * per + 1] = sv.y;
+        __syncwarp();
+        if (lane_on && rip == 0) {
+          typename Cx<Real>::T t;
+          t.x = 0;
+          t.y = 0;
+          for (int r = 0; r < g.RP; ++r) {
+            t.x += red[(r * g.Bv + v0) * per + 0];
+            t.y += red[(r * g.Bv + v0) * per + 1];
+          }
+          sv = t;
+        }
+      }
+    }
+    __syncwarp();
+  }
+  if (lane_on && rip == 0) {
+#pragma unroll
+    for (int v = 0; v < VB; ++v) {
+      const int64_t e0 = PAIR ? d.out_off + 2 * (int64_t)kt
+                              : d.out_off + (int64_t)(2 * kt) * B + (int64_t)(v0 * VB + v);
+      const int64_t e1 = PAIR ? e0 + 1 : e0 + B;
+      if (QT_RANGE_OK(e0, 1, 2, -1)) atomic_add_cx<Real>(data, e0, s0.c[v]);
+      if (QT_RANGE_OK(e1, 1, 2, -1)) atomic_add_cx<Real>(data, e1, s1.c[v]);
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < VB; ++v) {
+    s0.c[v].x = 0;
+    s0.c[v].y = 0;
+    s1.c[v] = s0.c[v];
+  }
+}
+
 template <class Real, int VB, bool PAIR, bool CG, int U>
 __device__ __forceinline__ void tile_adjred(WarpTile* w, Real* __restrict__ data, const TileGeom& g, int64_t r0,
-                                            int64_t r1, uint32_t kt, int lane, int rip, int v0, bool lane_on,
-                                            DevCtrl* ctrl, int dbg_bucket) {
+                                            int64_t r1, int lane, int rip, int v0, bool lane_on, DevCtrl* ctrl,
+                                            int dbg_bucket) {
   const DevBucket& d = w->d;
   const int n_in = d.n_in;
-  const int Q = g.P * g.VC;
-  const int B = g.B;
+  const int Q = g.P * g.VC;  // VC == 1 here (Bv <= 32)
+  const int seg = (1 << d.comp_bits) / g.RP < Q ? (1 << d.comp_bits) / g.RP : Q;  // passes per target row
   Pack<Real, VB> s0, s1;
 #pragma unroll
   for (int v = 0; v < VB; ++v) {
@@ -504,94 +569,22 @@ __device__ __forceinline__ void tile_adjred(WarpTile* w, Real* __restrict__ data
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      if (!it.ok[u]) continue;
+      const int q = q0 + u;
+      if (q < Q) {
+        if (it.ok[u]) {
 #pragma unroll
-      for (int v = 0; v < VB; ++v) {
-        s0.c[v] = cadd<Real>(s0.c[v], p0[u].c[v]);
-        s1.c[v] = cadd<Real>(s1.c[v], p1[u].c[v]);
-      }
-    }
-  }
-  // lane sums -> per-vector sums (lanes rip * Bv + v share vector v)
-  if ((g.Bv & (g.Bv - 1)) == 0) {
-    // Bv a power of two: RP * Bv = 32, so a butterfly over the lane bits at
-    // and above Bv adds the RP lanes of each vector; lanes < Bv keep the sums.
-#pragma unroll
-    for (int v = 0; v < VB; ++v) {
-      for (int off = 16; off >= g.Bv; off >>= 1) {
-        s0.c[v].x += __shfl_xor_sync(0xffffffffu, s0.c[v].x, off);
-        s0.c[v].y += __shfl_xor_sync(0xffffffffu, s0.c[v].y, off);
-        s1.c[v].x += __shfl_xor_sync(0xffffffffu, s1.c[v].x, off);
-        s1.c[v].y += __shfl_xor_sync(0xffffffffu, s1.c[v].y, off);
-      }
-    }
-    if (lane < g.Bv) {
-#pragma unroll
-      for (int v = 0; v < VB; ++v) {
-        const int64_t e0 = PAIR ? d.out_off + 2 * (int64_t)kt
-                                : d.out_off + (int64_t)(2 * kt) * B + (int64_t)(v0 * VB + v);
-        const int64_t e1 = PAIR ? e0 + 1 : e0 + B;
-        if (QT_RANGE_OK(e0, 1, 2, -1)) atomic_add_cx<Real>(data, e0, s0.c[v]);
-        if (QT_RANGE_OK(e1, 1, 2, -1)) atomic_add_cx<Real>(data, e1, s1.c[v]);
-      }
-    }
-    return;
-  }
-  Real* red = RedBuf<Real>::get(w);
-  const int per = 4 / (int)(sizeof(Real) / 4);  // Real slots per lane: 4 floats or 2 doubles
-#pragma unroll
-  for (int v = 0; v < VB; ++v) {
-    __syncwarp();
-    red[lane * per + 0] = s0.c[v].x;
-    red[lane * per + 1] = s0.c[v].y;
-    if (per == 4) {
-      red[lane * per + 2] = s1.c[v].x;
-      red[lane * per + 3] = s1.c[v].y;
-    }
-    __syncwarp();
-    if (lane_on && rip == 0) {
-      typename Cx<Real>::T t0, t1;
-      t0.x = 0;
-      t0.y = 0;
-      t1 = t0;
-      for (int r = 0; r < g.RP; ++r) {
-        const int l = r * g.Bv + v0;
-        t0.x += red[l * per + 0];
-        t0.y += red[l * per + 1];
-        if (per == 4) {
-          t1.x += red[l * per + 2];
-          t1.y += red[l * per + 3];
+          for (int v = 0; v < VB; ++v) {
+            s0.c[v] = cadd<Real>(s0.c[v], p0[u].c[v]);
+            s1.c[v] = cadd<Real>(s1.c[v], p1[u].c[v]);
+          }
+        }
+        if ((q + 1) % seg == 0 || q + 1 == Q) {  // end of a target row's passes (warp-uniform)
+          const uint32_t kt = (uint32_t)((r0 + (int64_t)q * g.RP) >> d.comp_bits);
+          flush_target<Real, VB, PAIR>(w, data, g, kt, s0, s1, lane, rip, v0, lane_on, ctrl, dbg_bucket);
         }
       }
-      const int64_t e0 = PAIR ? d.out_off + 2 * (int64_t)kt
-                              : d.out_off + (int64_t)(2 * kt) * B + (int64_t)(v0 * VB + v);
-      if (QT_RANGE_OK(e0, 1, 2, -1)) atomic_add_cx<Real>(data, e0, t0);
-      if (per == 4) {
-        const int64_t e1 = PAIR ? e0 + 1 : e0 + B;
-        if (QT_RANGE_OK(e1, 1, 2, -1)) atomic_add_cx<Real>(data, e1, t1);
-      }
-    }
-    if (per == 2) {  // complex128: second pass for x = 1
-      __syncwarp();
-      red[lane * per + 0] = s1.c[v].x;
-      red[lane * per + 1] = s1.c[v].y;
-      __syncwarp();
-      if (lane_on && rip == 0) {
-        typename Cx<Real>::T t1;
-        t1.x = 0;
-        t1.y = 0;
-        for (int r = 0; r < g.RP; ++r) {
-          const int l = r * g.Bv + v0;
-          t1.x += red[l * per + 0];
-          t1.y += red[l * per + 1];
-        }
-        const int64_t e1 = PAIR ? d.out_off + 2 * (int64_t)kt + 1
-                                : d.out_off + (int64_t)(2 * kt + 1) * B + (int64_t)(v0 * VB + v);
-        if (QT_RANGE_OK(e1, 1, 2, -1)) atomic_add_cx<Real>(data, e1, t1);
-      }
     }
   }
-  __syncwarp();
 }
 
 // One warp evaluates output rows [r0, r1) of the bucket in w->d (all B angle
@@ -600,18 +593,18 @@ __device__ __forceinline__ void tile_adjred(WarpTile* w, Real* __restrict__ data
 // w->lpart.  Per item an input row is one table read plus one add.
 template <class Real, int VB, bool PAIR, bool CG, bool GRAD = false>
 __device__ __forceinline__ void warp_tile(WarpTile* w, Real* __restrict__ data, const TileGeom& g, int64_t r0,
-                                          int64_t r1, int lane, DevCtrl* ctrl = nullptr, int dbg_bucket = -1,
-                                          uint32_t kt = 0) {
+                                          int64_t r1, int lane, DevCtrl* ctrl = nullptr, int dbg_bucket = -1) {
   const DevBucket& d = w->d;
   const int n_rec = d.kind == kStepAdj ? d.n_in + 1 : d.n_in;
   int rip, v0;
   bool lane_on;
   lane_slot(g, lane, &rip, &v0, &lane_on);
   const int P = g.P;
-  if (GRAD && d.kind == kStepAdjRed) {  // rows are completions: y = pdep(kt, mask_t) | pdep(c, ~mask_t)
-    const uint32_t yt = pdep_in(kt, d.in[d.n_in]);
+  if (GRAD && d.kind == kStepAdjRed) {  // row q = kt * 2^comp_bits + c: y = pdep(kt, mask_t) | pdep(c, ~mask_t)
+    const uint32_t cmask = (1u << d.comp_bits) - 1u;
     for (int pp = lane; pp < P; pp += 32) {
-      const uint32_t yp = yt | pdep_in((uint32_t)(r0 + (int64_t)pp * g.RP), d.in[d.n_in + 1]);
+      const uint32_t q = (uint32_t)(r0 + (int64_t)pp * g.RP);
+      const uint32_t yp = pdep_in(q >> d.comp_bits, d.in[d.n_in]) | pdep_in(q & cmask, d.in[d.n_in + 1]);
       for (int i = 0; i < d.n_in; ++i) w->tab[i][pp] = pext_in(yp, d.in[i]);
     }
   } else {
@@ -626,7 +619,7 @@ __device__ __forceinline__ void warp_tile(WarpTile* w, Real* __restrict__ data, 
   else if (d.kind == kStepAdj)
     tile_adjoint<Real, VB, PAIR, CG, 2>(w, data, g, r0, r1, lane, rip, v0, lane_on, ctrl, dbg_bucket);
   else if (d.kind == kStepAdjRed)
-    tile_adjred<Real, VB, PAIR, CG, 2>(w, data, g, r0, r1, kt, lane, rip, v0, lane_on, ctrl, dbg_bucket);
+    tile_adjred<Real, VB, PAIR, CG, 2>(w, data, g, r0, r1, lane, rip, v0, lane_on, ctrl, dbg_bucket);
   else
     tile_zero<Real, VB, PAIR, 2>(w, data, g, r0, r1, rip, v0, lane_on);
 }

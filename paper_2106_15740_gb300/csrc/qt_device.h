@@ -57,12 +57,13 @@ struct TileGeom {
 //              in[n_in] describes the target (mask and runs; off = out_off).
 //   kStepZero: clear n_rows x B elements at out_off (an atomic target).
 //   kStepAdjRed: the adjoint of a target t that lacks some of the bucket's
-//              variables, as a reduction: each warp tile fixes one target row
-//              k_t (of 2^tgt_bits) and sums over a chunk of the n_rows
-//              completions (values of the missing variables, bits of the
-//              complement mask), y = pdep(k_t, mask_t) | pdep(c, ~mask_t);
-//              one atomic add per target element per tile.  in[n_in] is the
-//              target record, in[n_in + 1] the complement record.
+//              variables, as a reduction over the combined space of target
+//              rows k_t (2^tgt_bits) and completions c (2^comp_bits values of
+//              the missing variables, bits of the complement mask), row index
+//              k_t * 2^comp_bits + c, y = pdep(k_t, mask_t) | pdep(c, ~mask_t);
+//              lanes sum while k_t stays fixed and add one atomic per target
+//              element at each change of k_t.  in[n_in] is the target record,
+//              in[n_in + 1] the complement record.
 constexpr int32_t kStepFwd = 0, kStepAdj = 1, kStepZero = 2, kStepAdjRed = 3;
 constexpr int32_t kAdjFull = 1, kAdjUnitG = 2;
 
@@ -76,16 +77,12 @@ struct DevBucket {
   int32_t kind;                // kStep*
   int32_t aflags;              // kAdj* bits (kStepAdj)
   int32_t tgt_bits;            // kStepAdjRed: target rows 2^tgt_bits (times x = 0, 1)
-  int32_t pad_;
+  int32_t comp_bits;           // kStepAdjRed: completions per target row 2^comp_bits (>= 5)
   DevInput in[kDevMaxIn];
 };
 
-// Warp tiles of a step: target rows x chunks of n_rows (kStepAdjRed), else
-// chunks of n_rows.
-inline int64_t step_tiles(const DevBucket& d, int64_t R) {
-  const int64_t chunks = (d.n_rows + R - 1) / R;
-  return d.kind == kStepAdjRed ? (chunks << d.tgt_bits) : chunks;
-}
+// Warp tiles of a step: chunks of R of its n_rows.
+inline int64_t step_tiles(const DevBucket& d, int64_t R) { return (d.n_rows + R - 1) / R; }
 
 // Leaf factor: product of the leaves of one bucket over the union of their
 // variables, materialised per angle set.  A leaf is packed as
