@@ -142,7 +142,9 @@ typedef struct {
   int32_t edge_begin;     /* plan the edges [edge_begin, edge_end) of the graph; */
   int32_t edge_end;       /* edge_end <= 0 means all edges from edge_begin on.  Energies and
                              gradients then cover only those edges (a partial sum) */
-  int32_t reserved_;
+  int32_t slice;          /* 1: an edge whose width is above max_width is sliced instead of
+                             rejected -- variables are fixed, one at a time, until the rest of
+                             the network fits, and the 2^s restricted networks are summed */
 } qt_plan_options;
 
 /* Fill `opt` with defaults: batch 1, QT_C128, QT_MODE_PER_BUCKET, no gradient,
@@ -161,8 +163,13 @@ qt_status qt_plan_workspace_size(const qt_plan* plan, size_t* bytes);
 qt_status qt_plan_stats(const qt_plan* plan, int32_t* n_edges, int32_t* max_width,
                         int64_t* n_buckets, double* alg_bytes, double* flops);
 
-/* Per-edge widths (n_edges entries, host array). */
+/* Per-edge widths (n_edges entries, host array); for a sliced edge, the width
+ * of its restricted networks. */
 qt_status qt_plan_edge_widths(const qt_plan* plan, int32_t* widths);
+
+/* Per-edge number of sliced variables s (the edge is evaluated as 2^s
+ * restricted networks; 0 for an edge that fits the width budget). */
+qt_status qt_plan_edge_slices(const qt_plan* plan, int32_t* slices);
 
 /* Evaluate the plan with DEVICE pointers, asynchronously on `stream`:
  *   gamma, beta : [B][p] float64 angles

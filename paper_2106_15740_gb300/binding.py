@@ -29,7 +29,7 @@ EXPORTS = [
     "qt_plan_edge_widths", "qt_plan_energy", "qt_plan_check", "qt_plan_energy_host",
     "qt_plan_free", "qt_energy_workspace_size", "qt_energy", "qt_last_error",
     "qt_plan_set_profiling", "qt_plan_kernel_times", "qt_plan_energy_static",
-    "qt_static_scratch_bytes", "qt_plan_set_wait_limit", "qt_plan_inject_stall",
+    "qt_static_scratch_bytes", "qt_plan_set_wait_limit", "qt_plan_inject_stall", "qt_plan_edge_slices",
 ]
 
 
@@ -47,7 +47,7 @@ class qt_plan_options(C.Structure):
     _fields_ = [("batch", C.c_int32), ("dtype", C.c_int32), ("mode", C.c_int32),
                 ("gradient", C.c_int32), ("max_width", C.c_int32), ("lane_items", C.c_int32),
                 ("max_workspace", C.c_int64), ("group_rows", C.c_int32), ("edge_begin", C.c_int32),
-                ("edge_end", C.c_int32), ("reserved_", C.c_int32)]
+                ("edge_end", C.c_int32), ("slice", C.c_int32)]
 
 
 _lib = None
@@ -73,6 +73,7 @@ def lib():
             "qt_plan_workspace_size": [vp, C.POINTER(sz)],
             "qt_plan_stats": [vp, pi32, pi32, C.POINTER(i64), pd, pd],
             "qt_plan_edge_widths": [vp, pi32],
+            "qt_plan_edge_slices": [vp, pi32],
             "qt_plan_energy": [vp, vp, vp, vp, vp, vp, vp, sz, vp],
             "qt_plan_check": [vp, vp],
             "qt_plan_energy_host": [vp, pd, pd, pd, pd, pd, vp, sz, vp],
@@ -203,6 +204,12 @@ def qt_plan_edge_widths(plan, n_edges):
     w = np.zeros(n_edges, dtype=np.int32)
     _check(lib().qt_plan_edge_widths(plan, w.ctypes.data_as(C.POINTER(C.c_int32))))
     return w
+
+
+def qt_plan_edge_slices(plan, n_edges):
+    sl = np.zeros(n_edges, dtype=np.int32)
+    _check(lib().qt_plan_edge_slices(plan, sl.ctypes.data_as(C.POINTER(C.c_int32))))
+    return sl
 
 
 def qt_plan_energy(plan, gamma_ptr, beta_ptr, energy_ptr, edge_zz_ptr, grad_ptr, ws_ptr, ws_bytes, stream):

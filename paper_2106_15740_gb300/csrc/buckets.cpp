@@ -41,15 +41,28 @@ qt_status make_edge_plan(const Network& net, const std::vector<int32_t>& order, 
     std::vector<int32_t> vars;   // sorted by elimination position
   };
   std::vector<std::vector<Item>> pending(n);
+  std::vector<int32_t> constants;  // tensors with every slot fixed by slicing
   for (int32_t t = 0; t < (int32_t)net.tensors.size(); ++t) {
     const Tensor& T = net.tensors[t];
     Item it{t, true, {}};
-    for (int32_t r = 0; r < T.rank; ++r) it.vars.push_back(T.v[r]);
+    int32_t free_slots = 0;
+    for (int32_t r = 0; r < T.rank; ++r)
+      if (T.fix[r] < 0) {
+        it.vars.push_back(T.v[r]);
+        ++free_slots;
+      }
+    if (free_slots == 0) {
+      constants.push_back(t);
+      continue;
+    }
     std::sort(it.vars.begin(), it.vars.end(), by_pos);
     it.vars.erase(std::unique(it.vars.begin(), it.vars.end()), it.vars.end());
-    if ((int32_t)it.vars.size() != T.rank) return fail(QT_EINVAL, "tensor repeats a variable");
+    if ((int32_t)it.vars.size() != free_slots) return fail(QT_EINVAL, "tensor repeats a variable");
     pending[pos[it.vars[0]]].push_back(std::move(it));
   }
+  if (n == 0) return fail(QT_EINVAL, "network has no free variable");
+  // a constant multiplies the whole network: fold it into the first bucket's leaf factor
+  for (int32_t t : constants) pending[0].push_back(Item{t, true, {}});
 
   ep->edge = net.edge;
   ep->width = 0;
@@ -61,7 +74,7 @@ qt_status make_edge_plan(const Network& net, const std::vector<int32_t>& order, 
     bk.var = v;
     std::vector<Item>& items = pending[i];
     if (items.empty()) return fail(QT_EINVAL, "variable " + std::to_string(v) + " appears in no tensor");
-    std::vector<int32_t> U;
+    std::vector<int32_t> U{v};
     for (auto& it : items) U.insert(U.end(), it.vars.begin(), it.vars.end());
     std::sort(U.begin(), U.end(), by_pos);
     U.erase(std::unique(U.begin(), U.end()), U.end());
@@ -90,7 +103,10 @@ qt_status make_edge_plan(const Network& net, const std::vector<int32_t>& order, 
       bk.in_rank.push_back((int32_t)it.vars.size());
       ep->buckets[it.src].consumer = i;
     }
-    if (!leaf_vars.empty()) {
+    bool any_leaf = false;
+    for (auto& it : items) any_leaf |= it.leaf;
+    if (any_leaf) {
+      leaf_vars.push_back(v);  // the leaf factor always carries the eliminated variable (bit 0)
       std::sort(leaf_vars.begin(), leaf_vars.end(), by_pos);
       leaf_vars.erase(std::unique(leaf_vars.begin(), leaf_vars.end()), leaf_vars.end());
       bk.leaf_rank = (int32_t)leaf_vars.size();
@@ -105,7 +121,11 @@ qt_status make_edge_plan(const Network& net, const std::vector<int32_t>& order, 
         L.rank = T.rank;
         for (int32_t r = 0; r < 2; ++r) {
           L.bit[r] = -1;
-          if (r < T.rank)
+          L.fix[r] = -1;
+          if (r >= T.rank) continue;
+          if (T.fix[r] >= 0)
+            L.fix[r] = T.fix[r];
+          else
             L.bit[r] = (int8_t)(std::find(leaf_vars.begin(), leaf_vars.end(), T.v[r]) - leaf_vars.begin());
         }
         bk.leaves.push_back(L);

@@ -24,23 +24,57 @@ static qt_status check_angles(const double* a, int64_t n, const char* name) {
 }
 
 // Build, order and bucket-plan every edge network of a graph.
-static qt_status plan_edges(const Graph& G, int32_t p, int32_t max_width, int32_t e0, int32_t e1, Plan* P) {
+// Build, order and bucket-plan every edge network of a graph.  An edge above
+// the width budget is rejected, or, with slicing, fixed variables are chosen
+// until the rest fits and its 2^s restricted networks are planned (one order
+// for all of them: they share the structure).
+static constexpr int32_t kMaxSlices = 20;
+
+static qt_status plan_edges(const Graph& G, int32_t p, int32_t max_width, bool slice, int32_t e0, int32_t e1,
+                            Plan* P) {
   P->edges.clear();
   P->widths.clear();
+  P->slices.clear();
+  P->net_first.assign(1, 0);
   for (int32_t e = e0; e < e1; ++e) {
     Network net;
     build_lightcone(G, p, e, &net);
     std::vector<int32_t> order;
-    const int32_t w = min_fill_order(net, &order);
-    if (w > max_width)
-      return fail(QT_EWIDTH, "edge " + std::to_string(e) + " has contraction width " + std::to_string(w) +
-                                 " above the budget " + std::to_string(max_width));
-    EdgePlan ep;
-    qt_status st = make_edge_plan(net, order, &ep);
-    if (st != QT_OK) return st;
-    P->widths.push_back(ep.width);
-    P->edges.push_back(std::move(ep));
+    int32_t w = min_fill_order(net, &order);
+    std::vector<int32_t> sliced;
+    if (w > max_width) {
+      if (!slice)
+        return fail(QT_EWIDTH, "edge " + std::to_string(e) + " has contraction width " + std::to_string(w) +
+                                   " above the budget " + std::to_string(max_width));
+      w = choose_slices(net, max_width, kMaxSlices, &sliced);
+      if (w > max_width)
+        return fail(QT_EWIDTH, "edge " + std::to_string(e) + " needs more than " + std::to_string(kMaxSlices) +
+                                   " sliced variables to reach width " + std::to_string(max_width));
+      Network red;
+      restrict_network(net, sliced, 0u, &red);
+      min_fill_order(red, &order);
+    }
+    const uint32_t n_slices = 1u << sliced.size();
+    for (uint32_t a = 0; a < n_slices; ++a) {
+      EdgePlan ep;
+      qt_status st;
+      if (sliced.empty()) {
+        st = make_edge_plan(net, order, &ep);
+      } else {
+        Network r;
+        restrict_network(net, sliced, a, &r);
+        st = make_edge_plan(r, order, &ep);
+      }
+      if (st != QT_OK) return st;
+      ep.edge = e;
+      ep.slices = (int32_t)sliced.size();
+      P->edges.push_back(std::move(ep));
+    }
+    P->widths.push_back(w);
+    P->slices.push_back((int32_t)sliced.size());
+    P->net_first.push_back((int32_t)P->edges.size());
   }
+  P->n_orig = e1 - e0;
   return QT_OK;
 }
 
@@ -118,7 +152,10 @@ static qt_status contract_plan(const qt_network* net, const int32_t* order, qt_d
   P->p = net->net.p;
   P->elem_bytes = dtype == QT_C64 ? 8 : 16;
   P->widths = {ep.width};
+  P->slices = {0};
   P->edges.push_back(std::move(ep));
+  P->n_orig = 1;
+  P->net_first = {0, 1};
   return compile_plan(P);
 }
 
@@ -163,7 +200,7 @@ void qt_plan_options_default(qt_plan_options* opt) {
   opt->group_rows = 0;
   opt->edge_begin = 0;
   opt->edge_end = 0;
-  opt->reserved_ = 0;
+  opt->slice = 0;
 }
 
 qt_status qt_plan_create(const qt_graph* g, int32_t p, const qt_plan_options* opt, qt_plan** out) {
@@ -193,7 +230,7 @@ qt_status qt_plan_create(const qt_graph* g, int32_t p, const qt_plan_options* op
     } else {
       h->P.opt.edge_begin = o.edge_begin;
       h->P.opt.edge_end = e1;
-      st = plan_edges(h->P.G, p, o.max_width, o.edge_begin, e1, &h->P);
+      st = plan_edges(h->P.G, p, o.max_width, o.slice != 0, o.edge_begin, e1, &h->P);
     }
   }
   if (st == QT_OK) st = compile_plan(&h->P);
@@ -215,7 +252,7 @@ qt_status qt_plan_stats(const qt_plan* plan, int32_t* n_edges, int32_t* max_widt
                         double* alg_bytes, double* flops) {
   if (!plan) return fail(QT_EINVAL, "plan is NULL");
   const Plan& P = plan->P;
-  if (n_edges) *n_edges = (int32_t)P.edges.size();
+  if (n_edges) *n_edges = P.n_orig;
   if (max_width) {
     int32_t w = 0;
     for (int32_t x : P.widths) w = std::max(w, x);
@@ -230,6 +267,12 @@ qt_status qt_plan_stats(const qt_plan* plan, int32_t* n_edges, int32_t* max_widt
 qt_status qt_plan_edge_widths(const qt_plan* plan, int32_t* widths) {
   if (!plan || !widths) return fail(QT_EINVAL, "plan or widths is NULL");
   std::copy(plan->P.widths.begin(), plan->P.widths.end(), widths);
+  return QT_OK;
+}
+
+qt_status qt_plan_edge_slices(const qt_plan* plan, int32_t* slices) {
+  if (!plan || !slices) return fail(QT_EINVAL, "plan or slices is NULL");
+  std::copy(plan->P.slices.begin(), plan->P.slices.end(), slices);
   return QT_OK;
 }
 
@@ -248,7 +291,7 @@ qt_status qt_plan_energy_host(qt_plan* plan, const double* gamma, const double* 
                               double* edge_zz, double* grad, void* workspace, size_t ws_bytes, void* stream) {
   if (!plan) return fail(QT_EINVAL, "plan is NULL");
   Plan& P = plan->P;
-  const int32_t B = P.opt.batch, p = P.p, ne = (int32_t)P.edges.size();
+  const int32_t B = P.opt.batch, p = P.p, ne = P.n_orig;
   qt_status st;
   if ((st = check_angles(gamma, (int64_t)B * p, "gamma")) != QT_OK) return st;
   if ((st = check_angles(beta, (int64_t)B * p, "beta")) != QT_OK) return st;

@@ -132,8 +132,7 @@ qt_status compile_plan(Plan* P) {
   for (int32_t e = 0; e < n_edges; ++e) {
     const EdgePlan& ep = P->edges[e];
     const int32_t nb = (int32_t)ep.buckets.size();
-    if (grad && ep.scalars.size() != 1)
-      return fail(QT_EINVAL, "gradient plans need one connected network per edge");
+
     Arena arena;
     out_off[e].assign(nb, 0);
     leaf_off[e].assign(nb, -1);
@@ -167,6 +166,21 @@ qt_status compile_plan(Plan* P) {
     if (grad) {
       Arena aarena;
       gbar_off[e].assign(nb, -1);
+      if (ep.scalars.size() > 1) {
+        // a network that split into components: Gbar of each scalar result is
+        // the product of the others, a rank-0 adjoint step into a 2-row buffer
+        for (int32_t sb : ep.scalars) {
+          gbar_off[e][sb] = aarena.alloc(align_el(2 * (int64_t)B));
+          AdjStep st;
+          st.bucket = sb;
+          st.input = -2;  // scalar adjoint
+          st.target = gbar_off[e][sb];
+          st.leaf = false;
+          st.full = true;
+          st.zero_rank = 0;
+          adj[e].push_back(st);
+        }
+      }
       for (int32_t b = nb - 1; b >= 0; --b) {
         const Bucket& bk = ep.buckets[b];
         if ((int32_t)bk.in_src.size() + (bk.out_rank > 0 ? 1 : 0) + 1 > kDevMaxIn)
@@ -201,6 +215,7 @@ qt_status compile_plan(Plan* P) {
             if (j != k && bk.in_src[j] >= 0) P->alg_bytes += (double)B * es * (double)((int64_t)1 << bk.in_rank[j]);
         }
         if (bk.out_rank > 0) aarena.release(gbar_off[e][b], align_el(((int64_t)1 << bk.out_rank) * B));
+        else if (gbar_off[e][b] >= 0) aarena.release(gbar_off[e][b], align_el(2 * (int64_t)B));
       }
       region[e] = fwd_peak[e] + aarena.peak;
     }
@@ -266,7 +281,7 @@ qt_status compile_plan(Plan* P) {
   P->buckets.clear();
   P->edge_first.assign(n_edges + 1, 0);
   P->leaf.clear();
-  P->leaf_first.assign(n_edges + 1, 0);
+  P->leaf_first.assign(P->n_orig + 1, 0);
   P->scal_off.clear();
   P->scal_begin.assign(n_edges + 1, 0);
   for (int32_t e = 0; e < n_edges; ++e) {
@@ -276,7 +291,6 @@ qt_status compile_plan(Plan* P) {
       return ep.buckets[b].out_rank == 0 ? scal_base + out_off[e][b] : rbase + out_off[e][b];
     };
     P->edge_first[e] = (int32_t)P->buckets.size();
-    P->leaf_first[e] = (int32_t)P->leaf.size();
     std::vector<std::vector<DevInput>> fwd_in(ep.buckets.size());
     for (int32_t i = 0; i < (int32_t)ep.buckets.size(); ++i) {
       const Bucket& bk = ep.buckets[i];
@@ -304,7 +318,10 @@ qt_status compile_plan(Plan* P) {
             const LeafRef& Lr = bk.leaves[l];
             lf.leaf[l] = (uint32_t)Lr.kind | (uint32_t)Lr.conj << 2 | (uint32_t)Lr.rank << 3 |
                          (uint32_t)(Lr.bit[0] < 0 ? 0 : Lr.bit[0]) << 5 |
-                         (uint32_t)(Lr.bit[1] < 0 ? 0 : Lr.bit[1]) << 10 | (uint32_t)Lr.layer << 16;
+                         (uint32_t)(Lr.bit[1] < 0 ? 0 : Lr.bit[1]) << 10 |
+                         (uint32_t)(Lr.fix[0] >= 0) << 15 | (uint32_t)(Lr.fix[0] > 0) << 16 |
+                         (uint32_t)(Lr.fix[1] >= 0) << 17 | (uint32_t)(Lr.fix[1] > 0) << 18 |
+                         (uint32_t)Lr.layer << 19;
           }
           P->leaf.push_back(lf);
         }
@@ -318,6 +335,23 @@ qt_status compile_plan(Plan* P) {
       std::memset(&d, 0, sizeof(d));
       d.dep = -1;
       d.ntask = 1;
+      if (st.input == -2) {  // scalar adjoint: product of the network's other scalar results
+        d.kind = kStepAdj;
+        d.out_rank = 0;
+        d.n_rows = 1;
+        d.out_off = rbase + fwd_peak[e] + st.target;
+        d.aflags = kAdjFull;
+        int32_t n = 0;
+        for (int32_t sb : ep.scalars)
+          if (sb != st.bucket) {
+            if (n + 1 >= kDevMaxIn) return fail(QT_EINVAL, "too many network components for the gradient");
+            d.in[n++] = input_record(0u, scal_base + out_off[e][sb], kInNoPair);
+          }
+        d.in[n] = input_record(0u, d.out_off, 0);
+        d.n_in = n;
+        P->buckets.push_back(d);
+        continue;
+      }
       if (st.input < 0) {
         d.kind = kStepZero;
         d.out_rank = st.zero_rank;
@@ -333,7 +367,7 @@ qt_status compile_plan(Plan* P) {
       d.aflags = st.full ? kAdjFull : 0;
       const uint32_t all = bk.out_rank ? (1u << bk.out_rank) - 1u : 0u;
       int32_t n = 0;
-      if (bk.out_rank > 0) {
+      if (gbar_off[e][st.bucket] >= 0) {  // rank > 0, or a scalar of a multi-component network
         d.in[n++] = input_record(all, rbase + fwd_peak[e] + gbar_off[e][st.bucket], kInNoPair);
       } else {
         d.aflags |= kAdjUnitG;
@@ -359,7 +393,17 @@ qt_status compile_plan(Plan* P) {
     P->scal_begin[e + 1] = (int32_t)P->scal_off.size();
   }
   P->edge_first[n_edges] = (int32_t)P->buckets.size();
-  P->leaf_first[n_edges] = (int32_t)P->leaf.size();
+  // leaf factors of each planned graph edge (its networks are consecutive)
+  {
+    std::vector<int32_t> net_leaf(n_edges + 1, 0);
+    int32_t count = 0;
+    for (int32_t e = 0; e < n_edges; ++e) {
+      net_leaf[e] = count;
+      for (const Bucket& bk : P->edges[e].buckets) count += bk.leaf_rank > 0 ? 1 : 0;
+    }
+    net_leaf[n_edges] = count;
+    for (int32_t o = 0; o <= P->n_orig; ++o) P->leaf_first[o] = net_leaf[P->net_first[o]];
+  }
 
   // ---- persistent queue: each edge's steps form a chain; slots round-robin ----
   P->tasks.clear();
@@ -430,14 +474,16 @@ qt_status compile_plan(Plan* P) {
   o = align256(o + sizeof(int64_t) * P->scal_off.size());
   L.scal_begin = o;
   o = align256(o + sizeof(int32_t) * P->scal_begin.size());
+  L.net_first = o;
+  o = align256(o + sizeof(int32_t) * P->net_first.size());
   L.angles = o;
   o = align256(o + sizeof(double) * 2 * (size_t)B * p);
   L.results = o;
-  o = align256(o + sizeof(double) * ((size_t)B + (size_t)n_edges * B * 2 + (size_t)B * 2 * p));
+  o = align256(o + sizeof(double) * ((size_t)B + (size_t)P->n_orig * B * 2 + (size_t)B * 2 * p));
   L.trig = o;
   o = align256(o + sizeof(double) * 4 * (size_t)B * p);
   L.dz = o;
-  if (grad) o = align256(o + sizeof(double) * 2 * (size_t)n_edges * B * 2 * p);
+  if (grad) o = align256(o + sizeof(double) * 2 * (size_t)P->n_orig * B * 2 * p);
   L.gpart = o;
   if (grad) o = align256(o + sizeof(double) * 2 * (size_t)P->leaf.size() * B * kDevMaxLeaves);
   L.data = o;
@@ -498,6 +544,8 @@ qt_status run_plan(Plan* P, const double* gamma, const double* beta, double* ene
                               cudaMemcpyHostToDevice, s));
     QT_CUDA(cudaMemcpyAsync(base + L.scal_begin, P->scal_begin.data(), sizeof(int32_t) * P->scal_begin.size(),
                             cudaMemcpyHostToDevice, s));
+    QT_CUDA(cudaMemcpyAsync(base + L.net_first, P->net_first.data(), sizeof(int32_t) * P->net_first.size(),
+                            cudaMemcpyHostToDevice, s));
     QT_CUDA(cudaStreamSynchronize(s));  // host vectors may change after return
     P->bound_ws = ws;
     P->device = dev;
@@ -541,10 +589,10 @@ qt_status run_plan(Plan* P, const double* gamma, const double* beta, double* ene
   }
   if (ev_stop) QT_CUDA(cudaEventRecord(ev_stop, s));
   QT_CUDA(launch_energy(dtype, data, (const int64_t*)(base + L.scal_off), (const int32_t*)(base + L.scal_begin),
-                        (int32_t)P->edges.size(), B, energy, edge_zz, s));
+                        (const int32_t*)(base + L.net_first), P->n_orig, B, energy, edge_zz, s));
   if (grad)
     QT_CUDA(launch_gradient(dtype, (const DevLeafFactor*)(base + L.leaf), (int32_t)P->leaf.size(),
-                            (const int32_t*)(base + L.leaf_first), (int32_t)P->edges.size(), P->lbar_shift, trig,
+                            (const int32_t*)(base + L.leaf_first), P->n_orig, P->lbar_shift, trig,
                             P->p, B, data, (double*)(base + L.gpart), (double*)(base + L.dz), grad, s));
   return QT_OK;
 }

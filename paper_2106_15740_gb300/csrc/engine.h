@@ -16,7 +16,8 @@ struct qt_network {
 namespace qt {
 
 struct WsLayout {
-  size_t ctrl = 0, done = 0, buckets = 0, tasks = 0, leaf = 0, leaf_first = 0, scal_off = 0, scal_begin = 0;
+  size_t ctrl = 0, done = 0, buckets = 0, tasks = 0, leaf = 0, leaf_first = 0, scal_off = 0, scal_begin = 0,
+         net_first = 0;
   size_t angles = 0, results = 0, trig = 0, dz = 0, gpart = 0, data = 0, total = 0;
 };
 
@@ -25,8 +26,11 @@ struct Plan {
   int32_t p = 0;
   qt_plan_options opt{};
   int32_t elem_bytes = 16;
-  std::vector<EdgePlan> edges;
-  std::vector<int32_t> widths;
+  std::vector<EdgePlan> edges;             // networks: one per edge, or 2^s per sliced edge
+  std::vector<int32_t> widths;             // per planned graph edge
+  std::vector<int32_t> slices;             // per planned graph edge: sliced variables s
+  int32_t n_orig = 0;                      // planned graph edges
+  std::vector<int32_t> net_first;          // first network of each planned edge (n_orig + 1)
 
   // device images (uploaded into the workspace)
   std::vector<DevBucket> buckets;          // steps of all edges (forward, then adjoint), concatenated

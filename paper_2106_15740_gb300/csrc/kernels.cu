@@ -27,11 +27,21 @@ __global__ void trig_kernel(const double* __restrict__ gamma, const double* __re
 //   MIX_q: cos b if new == old else -i sin b
 //   OBS  : +1 for bit 0, -1 for bit 1
 // conj = 1 takes the complex conjugate (bra half of the network).
+// Fields of a packed leaf (qt_device.h): layer, and the bit of slot 0 / 1 at
+// leaf-factor index z (a fixed slot gives its fixed value).
+__device__ __forceinline__ int32_t leaf_layer(uint32_t w) { return (int32_t)((w >> 19) & 127u); }
+__device__ __forceinline__ uint32_t leaf_bit0(uint32_t w, uint32_t z) {
+  return (w >> 15) & 1u ? (w >> 16) & 1u : (z >> ((w >> 5) & 31u)) & 1u;
+}
+__device__ __forceinline__ uint32_t leaf_bit1(uint32_t w, uint32_t z) {
+  return (w >> 17) & 1u ? (w >> 18) & 1u : (z >> ((w >> 10) & 31u)) & 1u;
+}
+
 template <class Real>
 __device__ __forceinline__ typename Cx<Real>::T leaf_value(uint32_t w, uint32_t z, const double* tr) {
   const uint32_t kind = w & 3u, conj = (w >> 2) & 1u;
-  const uint32_t b0 = (z >> ((w >> 5) & 31u)) & 1u;
-  const uint32_t b1 = (z >> ((w >> 10) & 31u)) & 1u;
+  const uint32_t b0 = leaf_bit0(w, z);
+  const uint32_t b1 = leaf_bit1(w, z);
   typename Cx<Real>::T v;
   if (kind == 0u) {
     v.x = (Real)0.70710678118654752440;
@@ -72,7 +82,7 @@ __global__ void leaf_factor_kernel(const DevLeafFactor* __restrict__ lf, int32_t
       acc.y = 0;
       for (int32_t l = 0; l < F.n_leaves; ++l) {
         const uint32_t w = F.leaf[l];
-        const int32_t layer = (int32_t)(w >> 16);
+        const int32_t layer = leaf_layer(w);
         const double* tr = trig + ((int64_t)b * p + (layer > 0 ? layer - 1 : 0)) * 4;
         acc = cmul<Real>(acc, leaf_value<Real>(w, z, tr));
       }
@@ -193,19 +203,26 @@ __global__ void __launch_bounds__(256, 4) persistent_kernel(const DevBucket* __r
 // FP64, and E = sum_e (1 - Re <Z_j Z_k>_e) / 2 in a fixed order.
 template <class Real>
 __global__ void energy_kernel(const Real* __restrict__ data, const int64_t* __restrict__ scal_off,
-                              const int32_t* __restrict__ scal_begin, int32_t n_edges, int32_t B,
-                              double* __restrict__ energy, double* __restrict__ edge_zz) {
+                              const int32_t* __restrict__ scal_begin, const int32_t* __restrict__ net_first,
+                              int32_t n_edges, int32_t B, double* __restrict__ energy, double* __restrict__ edge_zz) {
   const int32_t b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
   double E = 0.0;
   for (int32_t e = 0; e < n_edges; ++e) {
-    double zr = 1.0, zi = 0.0;
-    for (int32_t s = scal_begin[e]; s < scal_begin[e + 1]; ++s) {
-      const int64_t o = scal_off[s] + b;
-      const double vr = (double)data[2 * o], vi = (double)data[2 * o + 1];
-      const double nr = zr * vr - zi * vi;
-      zi = zr * vi + zi * vr;
-      zr = nr;
+    // <Z_j Z_k> = sum over the edge's networks (2^s slices) of the product of
+    // each network's scalar results
+    double zr = 0.0, zi = 0.0;
+    for (int32_t k = net_first[e]; k < net_first[e + 1]; ++k) {
+      double nr = 1.0, ni = 0.0;
+      for (int32_t s = scal_begin[k]; s < scal_begin[k + 1]; ++s) {
+        const int64_t o = scal_off[s] + b;
+        const double vr = (double)data[2 * o], vi = (double)data[2 * o + 1];
+        const double tr = nr * vr - ni * vi;
+        ni = nr * vi + ni * vr;
+        nr = tr;
+      }
+      zr += nr;
+      zi += ni;
     }
     if (edge_zz) {
       edge_zz[((int64_t)e * B + b) * 2 + 0] = zr;
@@ -222,8 +239,8 @@ __global__ void energy_kernel(const Real* __restrict__ data, const int64_t* __re
 //   MIX: d/db cos b = -sin b;  d/db (-i sin b) = -i cos b; conjugate for the bra
 __device__ __forceinline__ double2 leaf_deriv(uint32_t w, uint32_t z, const double* tr) {
   const uint32_t kind = w & 3u, conj = (w >> 2) & 1u;
-  const uint32_t b0 = (z >> ((w >> 5) & 31u)) & 1u;
-  const uint32_t b1 = (z >> ((w >> 10) & 31u)) & 1u;
+  const uint32_t b0 = leaf_bit0(w, z);
+  const uint32_t b1 = leaf_bit1(w, z);
   double2 v = make_double2(0.0, 0.0);
   if (kind == 1u) {
     const double s = (b0 == b1) ? 1.0 : -1.0;
@@ -252,14 +269,14 @@ __global__ void leafgrad_kernel(const DevLeafFactor* __restrict__ lf, int32_t n_
     const uint32_t w = l < F.n_leaves ? F.leaf[l] : 0u;
     const uint32_t kind = w & 3u;
     if (l < F.n_leaves && (kind == 1u || kind == 2u)) {
-      const int32_t layer = (int32_t)(w >> 16);
+      const int32_t layer = leaf_layer(w);
       const double* tr = trig + ((int64_t)b * p + layer - 1) * 4;
       for (uint32_t z = 0; z < (1u << F.rank); ++z) {
         double2 t = leaf_deriv(w, z, tr);
         for (int32_t l2 = 0; l2 < F.n_leaves; ++l2) {
           if (l2 == l) continue;
           const uint32_t w2 = F.leaf[l2];
-          const int32_t layer2 = (int32_t)(w2 >> 16);
+          const int32_t layer2 = leaf_layer(w2);
           const double* tr2 = trig + ((int64_t)b * p + (layer2 > 0 ? layer2 - 1 : 0)) * 4;
           t = cmul<double>(t, leaf_value<double>(w2, z, tr2));
         }
@@ -291,7 +308,7 @@ __global__ void edgegrad_kernel(const DevLeafFactor* __restrict__ lf, const int3
     const int32_t nl = lf[f].n_leaves;
     for (int32_t l = 0; l < nl; ++l) {
       const uint32_t w = lf[f].leaf[l];
-      if ((w & 3u) != want_kind || (w >> 16) != want_layer) continue;
+      if ((w & 3u) != want_kind || (uint32_t)leaf_layer(w) != want_layer) continue;
       const double2 v = part[((int64_t)f * B + b) * kDevMaxLeaves + l];
       ar += v.x;
       ai += v.y;
@@ -437,14 +454,15 @@ cudaError_t persistent_occupancy(int dtype, bool grad, int32_t B, int* blocks_pe
 }
 
 cudaError_t launch_energy(int dtype, const void* data, const int64_t* scal_off, const int32_t* scal_begin,
-                          int32_t n_edges, int32_t B, double* energy, double* edge_zz, cudaStream_t s) {
+                          const int32_t* net_first, int32_t n_edges, int32_t B, double* energy, double* edge_zz,
+                          cudaStream_t s) {
   const int32_t grid = (B + 127) / 128;
   if (dtype == QT_C64)
-    dev::energy_kernel<float><<<grid, 128, 0, s>>>((const float*)data, scal_off, scal_begin, n_edges, B,
+    dev::energy_kernel<float><<<grid, 128, 0, s>>>((const float*)data, scal_off, scal_begin, net_first, n_edges, B,
                                                    energy, edge_zz);
   else
-    dev::energy_kernel<double><<<grid, 128, 0, s>>>((const double*)data, scal_off, scal_begin, n_edges, B,
-                                                    energy, edge_zz);
+    dev::energy_kernel<double><<<grid, 128, 0, s>>>((const double*)data, scal_off, scal_begin, net_first, n_edges,
+                                                    B, energy, edge_zz);
   return cudaGetLastError();
 }
 

@@ -21,7 +21,8 @@ cudaError_t launch_persistent(int dtype, bool grad, const DevBucket* buckets, co
                               void* data, int64_t data_elems, int32_t grid, int32_t spin_limit, cudaStream_t s);
 cudaError_t persistent_occupancy(int dtype, bool grad, int32_t B, int* blocks_per_sm);
 cudaError_t launch_energy(int dtype, const void* data, const int64_t* scal_off, const int32_t* scal_begin,
-                          int32_t n_edges, int32_t B, double* energy, double* edge_zz, cudaStream_t s);
+                          const int32_t* net_first, int32_t n_edges, int32_t B, double* energy, double* edge_zz,
+                          cudaStream_t s);
 
 cudaError_t launch_gradient(int dtype, const DevLeafFactor* lf, int32_t n_lf, const int32_t* leaf_first,
                             int32_t n_edges, int64_t lbar_shift, const double* trig, int32_t p, int32_t B,

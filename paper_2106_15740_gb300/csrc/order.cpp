@@ -64,7 +64,7 @@ int32_t min_fill_order(const Network& net, std::vector<int32_t>* order) {
   const int32_t n = net.n_vars;
   BitGraph G(n);
   for (const Tensor& t : net.tensors)
-    if (t.rank == 2 && t.v[0] != t.v[1]) {
+    if (t.rank == 2 && t.v[0] >= 0 && t.v[1] >= 0 && t.v[0] != t.v[1]) {  // both slots free
       G.set(t.v[0], t.v[1]);
       G.set(t.v[1], t.v[0]);
     }

@@ -86,7 +86,9 @@ inline int64_t step_tiles(const DevBucket& d, int64_t R) { return (d.n_rows + R 
 
 // Leaf factor: product of the leaves of one bucket over the union of their
 // variables, materialised per angle set.  A leaf is packed as
-// kind | conj << 2 | rank << 3 | bit0 << 5 | bit1 << 10 | layer << 16.
+// kind | conj << 2 | rank << 3 | bit0 << 5 | bit1 << 10 | fixed0 << 15 |
+// value0 << 16 | fixed1 << 17 | value1 << 18 | layer << 19, where slot r reads
+// bit `bit r` of the factor's index unless slicing fixed it to `value r`.
 struct DevLeafFactor {
   int64_t off;
   int32_t rank;

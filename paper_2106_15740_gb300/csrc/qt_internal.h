@@ -28,10 +28,11 @@ qt_status make_graph(const qt_graph* g, Graph* out);
 // of its layer; the network stores structure only.
 struct Tensor {
   int8_t kind;      // qt_tensor_kind
-  int8_t rank;      // 1 or 2
+  int8_t rank;      // 1 or 2 index slots
   int8_t conj;      // 1 for the bra copy (elementwise complex conjugate)
   int8_t layer;     // 1..p for ZZ/MIX, 0 for PLUS, p for OBS
-  int32_t v[2];     // variable ids; MIX: v[0] = new, v[1] = old
+  int32_t v[2];     // variable ids; MIX: v[0] = new, v[1] = old (-1 for a fixed slot)
+  int8_t fix[2] = {-1, -1};  // slot fixed to 0 or 1 by slicing (-1: free)
 };
 
 struct Network {
@@ -49,6 +50,14 @@ void build_lightcone(const Graph& g, int32_t p, int32_t edge, Network* net);
 // Greedy min-fill over the interaction graph; returns the width.
 int32_t min_fill_order(const Network& net, std::vector<int32_t>* order);
 
+// Slicing: the network with the variables `sliced` fixed to the bits of
+// `assignment` (bit i for sliced[i]); the other variables keep their order
+// and are renumbered 0.. in it.
+void restrict_network(const Network& net, const std::vector<int32_t>& sliced, uint32_t assignment, Network* out);
+// Choose variables to fix until the min-fill width of the rest is at most
+// w_max (at most max_slices); returns the width reached.
+int32_t choose_slices(const Network& net, int32_t w_max, int32_t max_slices, std::vector<int32_t>* sliced);
+
 // ----------------------------------------------------------------- plan ----
 constexpr int kMaxIn = 8;        // inputs per bucket (intermediates + one leaf factor)
 constexpr int kMaxLeafRank = 10; // variables of one leaf factor
@@ -58,7 +67,8 @@ constexpr int kMaxLeaves = 16;   // leaves folded into one leaf factor
 // bit positions of its variables inside the leaf factor's index.
 struct LeafRef {
   int8_t kind, layer, conj, rank;
-  int8_t bit[2];
+  int8_t bit[2];   // position of a free slot's variable in the leaf factor
+  int8_t fix[2];   // fixed value of a sliced slot, -1 if free
 };
 
 // One bucket of bucket elimination (§Tensor network contraction): the
@@ -78,6 +88,7 @@ struct Bucket {
 
 struct EdgePlan {
   int32_t edge = -1;
+  int32_t slices = 0;                // sliced variables of the edge (this network is one of 2^slices)
   int32_t width = 0;
   std::vector<Bucket> buckets;
   std::vector<int32_t> scalars;      // buckets whose result has rank 0

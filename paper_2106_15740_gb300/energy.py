@@ -30,14 +30,14 @@ class EnergyPlan:
 
     def __init__(self, n_vertices, edges, p, batch=1, dtype="c128", mode="persistent",
                  max_workspace=0, max_width=0, device="cuda:0", gradient=False, lane_items=0,
-                 group_rows=0, edge_range=None):
+                 group_rows=0, edge_range=None, slice=False):
         self.n_vertices, self.p, self.batch = int(n_vertices), int(p), int(batch)
         self.edges = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
         self.device = torch.device(device)
         self.edge_range = (0, len(self.edges)) if edge_range is None else tuple(int(x) for x in edge_range)
         self.options = dict(batch=batch, dtype=dtype, mode=mode, max_workspace=max_workspace,
                             max_width=max_width, gradient=gradient, lane_items=lane_items,
-                            group_rows=group_rows, edge_range=self.edge_range)
+                            group_rows=group_rows, edge_range=self.edge_range, slice=slice)
         opt = qb.qt_plan_options_default()
         opt.batch = self.batch
         opt.dtype = DTYPES[dtype]
@@ -48,10 +48,12 @@ class EnergyPlan:
         opt.lane_items = int(lane_items)
         opt.group_rows = int(group_rows)
         opt.edge_begin, opt.edge_end = self.edge_range
+        opt.slice = int(bool(slice))
         self.plan = qb.qt_plan_create(self.n_vertices, self.edges, self.p, opt)
         self.ws_bytes = qb.qt_plan_workspace_size(self.plan)
         self.stats = qb.qt_plan_stats(self.plan)
         self.widths = qb.qt_plan_edge_widths(self.plan, self.n_edges)
+        self.slices = qb.qt_plan_edge_slices(self.plan, self.n_edges)
         self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
 
     @property

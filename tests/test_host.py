@@ -153,3 +153,33 @@ def test_gradient_plans_need_the_persistent_queue(qtlib):
     with pytest.raises(qb.QTError) as ei:
         qb.qt_plan_create(n, edges, p, opt)
     assert ei.value.status == qb.QT_EINVAL
+
+
+@pytest.mark.parametrize("name,max_width", [("n100_p3", 10), ("n60_p4", 23)])
+def test_slicing_meets_the_width_budget(qtlib, name, max_width):
+    """Without slicing a budget below an edge's width is an error; with it,
+    exactly the edges above the budget get sliced variables and every planned
+    width is within the budget."""
+    from paper_2106_15740_gb300 import binding as qb
+    n, edges, p, g, b = workload(name)
+    opt = qb.qt_plan_options_default()
+    plan = qb.qt_plan_create(n, edges, p, opt)
+    w0 = qb.qt_plan_edge_widths(plan, len(edges))
+    assert list(qb.qt_plan_edge_slices(plan, len(edges))) == [0] * len(edges)
+    qb.qt_plan_free(plan)
+    opt.max_width = max_width
+    with pytest.raises(qb.QTError) as ei:
+        qb.qt_plan_create(n, edges, p, opt)
+    assert ei.value.status == qb.QT_EWIDTH
+    opt.slice = 1
+    plan = qb.qt_plan_create(n, edges, p, opt)
+    try:
+        w = qb.qt_plan_edge_widths(plan, len(edges))
+        s = qb.qt_plan_edge_slices(plan, len(edges))
+        st = qb.qt_plan_stats(plan)
+    finally:
+        qb.qt_plan_free(plan)
+    assert st["n_edges"] == len(edges) and st["max_width"] <= max_width
+    assert (w <= max_width).all()
+    np.testing.assert_array_equal(s > 0, w0 > max_width)
+    np.testing.assert_array_equal(w[w0 <= max_width], w0[w0 <= max_width])
