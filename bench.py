@@ -230,12 +230,13 @@ def run_ours(args):
 
     n, edges, p, _, _ = workload(WORKLOAD["name"])
     B = WORKLOAD["batch"]
-    profile_only = (WORKLOAD["name"], B) != ("n100_p4", 64) or "edge_range" in WORKLOAD or "lane_items" in WORKLOAD
+    profile_only = ((WORKLOAD["name"], B) != ("n100_p4", 64) or "edge_range" in WORKLOAD or "lane_items" in WORKLOAD
+                    or "chunk_tiles" in WORKLOAD)
     gamma, beta = random_angles(B, p, 1002 + 7919 * rank)
     t_plan = time.perf_counter()
     plan = EnergyPlan(n, edges, p, batch=B, dtype=WORKLOAD["dtype"], mode="persistent", device=dev,
                       edge_range=WORKLOAD.get("edge_range"), lane_items=WORKLOAD.get("lane_items", 0),
-                      group_rows=WORKLOAD.get("group_rows", 0))
+                      group_rows=WORKLOAD.get("group_rows", 0), chunk_tiles=WORKLOAD.get("chunk_tiles", 0))
     t_plan = time.perf_counter() - t_plan
     g = torch.tensor(gamma, device=dev)
     b = torch.tensor(beta, device=dev)
@@ -338,6 +339,7 @@ def main():
     ap.add_argument("--edges", default=None, help="profiling only: edge range a:b of the graph")
     ap.add_argument("--lane-items", type=int, default=0, help="profiling only: warp tile items per lane")
     ap.add_argument("--group-rows", type=int, default=0, help="profiling only: grouping threshold")
+    ap.add_argument("--chunk-tiles", type=int, default=0, help="profiling only: warp tiles per queue claim")
     args = ap.parse_args()
     if args.edges:
         a, b = (int(x) for x in args.edges.split(":"))
@@ -345,6 +347,8 @@ def main():
         args.no_cpu_baseline = True
     if args.lane_items or args.group_rows:
         WORKLOAD["lane_items"], WORKLOAD["group_rows"] = args.lane_items, args.group_rows
+    if args.chunk_tiles:
+        WORKLOAD["chunk_tiles"] = args.chunk_tiles
         args.no_cpu_baseline = True
     for key in ("batch", "workload", "dtype"):
         val = getattr(args, key)

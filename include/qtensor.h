@@ -134,7 +134,8 @@ typedef struct {
   int32_t dtype;          /* qt_dtype */
   int32_t mode;           /* qt_mode */
   int32_t gradient;       /* 1: plan also computes dE/dgamma, dE/dbeta (adjoint sweep) */
-  int32_t max_width;      /* width budget; an edge above it fails with QT_EWIDTH (<=0: 31) */
+  int32_t max_width;      /* width budget; an edge above it fails with QT_EWIDTH unless sliced
+                             (<=0: 31) */
   int32_t lane_items;     /* work items per lane in one warp tile: 8, 16, 32 or 64 (<=0: by batch) */
   int64_t max_workspace;  /* cap on workspace bytes (<=0: no cap); sets edge concurrency */
   int32_t group_rows;     /* persistent mode: consecutive buckets of one edge with at most this many
@@ -145,6 +146,8 @@ typedef struct {
   int32_t slice;          /* 1: an edge whose width is above max_width is sliced instead of
                              rejected -- variables are fixed, one at a time, until the rest of
                              the network fits, and the 2^s restricted networks are summed */
+  int32_t chunk_tiles;    /* persistent mode: warp tiles per queue task (<=0: one, or more for the
+                             widest steps when the queue would pass 2^27 tasks) */
 } qt_plan_options;
 
 /* Fill `opt` with defaults: batch 1, QT_C128, QT_MODE_PER_BUCKET, no gradient,

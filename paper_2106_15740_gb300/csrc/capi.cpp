@@ -46,13 +46,10 @@ static qt_status plan_edges(const Graph& G, int32_t p, int32_t max_width, bool s
       if (!slice)
         return fail(QT_EWIDTH, "edge " + std::to_string(e) + " has contraction width " + std::to_string(w) +
                                    " above the budget " + std::to_string(max_width));
-      w = choose_slices(net, max_width, kMaxSlices, &sliced);
+      w = choose_slices(net, max_width, kMaxSlices, &sliced, &order);
       if (w > max_width)
         return fail(QT_EWIDTH, "edge " + std::to_string(e) + " needs more than " + std::to_string(kMaxSlices) +
                                    " sliced variables to reach width " + std::to_string(max_width));
-      Network red;
-      restrict_network(net, sliced, 0u, &red);
-      min_fill_order(red, &order);
     }
     const uint32_t n_slices = 1u << sliced.size();
     for (uint32_t a = 0; a < n_slices; ++a) {
@@ -201,6 +198,7 @@ void qt_plan_options_default(qt_plan_options* opt) {
   opt->edge_begin = 0;
   opt->edge_end = 0;
   opt->slice = 0;
+  opt->chunk_tiles = 0;
 }
 
 qt_status qt_plan_create(const qt_graph* g, int32_t p, const qt_plan_options* opt, qt_plan** out) {

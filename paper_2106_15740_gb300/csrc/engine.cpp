@@ -90,6 +90,8 @@ void fill_runs(uint32_t mask, DevInput* in) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 constexpr int32_t kMaxGroup = 4096;  // buckets in one single-tile group task
+constexpr int64_t kMaxTasks = (int64_t)1 << 27;  // queue length the automatic chunk sizes aim for
+constexpr int64_t kMinChunks = 8192;             // chunks per wide step, at least (about 1.7 per resident warp)
 
 }  // namespace
 
@@ -412,6 +414,24 @@ qt_status compile_plan(Plan* P) {
   int64_t group_rows = P->opt.group_rows == 0 ? 4 * (int64_t)geom.RP : (int64_t)P->opt.group_rows;
   if (group_rows > geom.R) group_rows = geom.R;
   if (persistent) {
+    // A step is split into chunks of `span` warp tiles, one queue task each:
+    // chunk_tiles if set; else one tile per chunk while the queue stays
+    // within kMaxTasks, fewer chunks per wide step (down to kMinChunks) when
+    // it would not.
+    int64_t cap = (int64_t)1 << 18;
+    if (P->opt.chunk_tiles <= 0)
+      for (;;) {
+        int64_t total = 0;
+        for (const DevBucket& d : P->buckets) total += std::min(step_tiles(d, geom.R), cap);
+        if (total <= kMaxTasks || cap <= kMinChunks) break;
+        cap >>= 1;
+      }
+    for (DevBucket& d : P->buckets) {
+      const int64_t nt = step_tiles(d, geom.R);
+      const int64_t span = P->opt.chunk_tiles > 0 ? P->opt.chunk_tiles : (nt + cap - 1) / cap;
+      d.span = (int32_t)std::min<int64_t>(std::max<int64_t>(span, 1), INT32_MAX);
+      if ((nt + d.span - 1) / d.span > INT32_MAX / 2) return fail(QT_EWIDTH, "step too large for the task queue");
+    }
     const int32_t S = P->n_slots;
     std::vector<size_t> ei(S, 0);
     std::vector<int32_t> bi(S, 0), prev(S, -1);
@@ -425,16 +445,16 @@ qt_status compile_plan(Plan* P) {
         const int32_t ns_e = P->edge_first[e + 1] - P->edge_first[e];
         const int32_t gb = P->edge_first[e] + bi[s];
         DevBucket& d = P->buckets[gb];
-        const int64_t nt = step_tiles(d, geom.R);
-        if (nt > INT32_MAX / 2) return fail(QT_EWIDTH, "bucket too large for the task queue");
+        const int64_t nt = (step_tiles(d, geom.R) + d.span - 1) / d.span;  // chunks of this step
         d.dep = prev[s];
-        if (nt == 1 && d.n_rows <= group_rows) {
+        if (step_tiles(d, geom.R) == 1 && d.n_rows <= group_rows) {
           int32_t k = 1;
           while (bi[s] + k < ns_e && k < kMaxGroup && P->buckets[gb + k].n_rows <= group_rows &&
                  step_tiles(P->buckets[gb + k], geom.R) == 1)
             ++k;
           for (int32_t j = 0; j < k; ++j) {
             P->buckets[gb + j].ntask = 1;
+            P->buckets[gb + j].span = 1;
             if (j > 0) P->buckets[gb + j].dep = -1;
           }
           P->tasks.push_back(DevTask{gb, -k});
@@ -442,10 +462,10 @@ qt_status compile_plan(Plan* P) {
           bi[s] += k - 1;
         } else {
           d.ntask = (int32_t)nt;
-          for (int32_t t = 0; t < d.ntask; ++t) P->tasks.push_back(DevTask{gb, t});
+          for (int32_t c = 0; c < d.ntask; ++c) P->tasks.push_back(DevTask{gb, c});
           prev[s] = gb;
         }
-        if ((int64_t)P->tasks.size() > INT32_MAX / 2) return fail(QT_EWIDTH, "task queue too long");
+        if ((int64_t)P->tasks.size() > INT32_MAX / 2) return fail(QT_ENOMEM, "task queue too long");
         if (++bi[s] == ns_e) {
           bi[s] = 0;
           ++ei[s];

@@ -118,8 +118,9 @@ __device__ __forceinline__ int32_t ld_acquire(const int32_t* p) {
   return v;
 }
 
-// Persistent queue, one task = one warp tile or one group of single-tile
-// buckets.  Each warp takes tasks in queue order (lane 0: atomicAdd on the
+// Persistent queue, one task = one chunk of a bucket's warp tiles (one tile,
+// or `span` consecutive tiles for the widest buckets of a very long queue) or
+// one group of single-tile buckets.  Each warp takes tasks in queue order (lane 0: atomicAdd on the
 // queue head, issued one task ahead so its latency overlaps a tile), waits
 // until the task's bucket's predecessor in its edge chain has all its tiles
 // done, evaluates the tile(s) and counts the bucket's tile done.  Every
@@ -166,7 +167,7 @@ __global__ void __launch_bounds__(256, 4) persistent_kernel(const DevBucket* __r
     failed = __shfl_sync(0xffffffffu, failed, 0);
     t_next = __shfl_sync(0xffffffffu, t_next, 0);
     if (failed) break;
-    const int32_t n_group = task.tile < 0 ? -task.tile : 1;
+    const int32_t n_group = task.chunk < 0 ? -task.chunk : 1;
     for (int32_t k = 0; k < n_group; ++k) {
       const int32_t b = task.bucket + k;
       if (b != cached) {  // uniform: every lane holds the same b and cached
@@ -186,10 +187,18 @@ __global__ void __launch_bounds__(256, 4) persistent_kernel(const DevBucket* __r
         break;
       }
 #endif
-      const int64_t r0 = task.tile < 0 ? 0 : (int64_t)task.tile * g.R;
-      const int64_t r1 = r0 + g.R < w->d.n_rows ? r0 + g.R : w->d.n_rows;
-      warp_tile<Real, VB, PAIR, true, GRAD>(w, data, g, r0, r1, lane, ctrl, b);
-      __syncwarp();  // the next bucket of a group reads what this one wrote
+      // a group runs the single tile of each of its steps; a chunk runs
+      // `span` consecutive tiles of one step
+      const int64_t n_rows = w->d.n_rows;
+      const int64_t span = task.chunk < 0 ? 1 : (int64_t)w->d.span;
+      const int64_t t0 = task.chunk < 0 ? 0 : (int64_t)task.chunk * span;
+      for (int64_t tt = t0; tt < t0 + span; ++tt) {
+        const int64_t r0 = tt * g.R;
+        if (r0 >= n_rows) break;
+        const int64_t r1 = r0 + g.R < n_rows ? r0 + g.R : n_rows;
+        warp_tile<Real, VB, PAIR, true, GRAD>(w, data, g, r0, r1, lane, ctrl, b);
+        __syncwarp();  // the next tile or step reuses the warp's tables and reads what this one wrote
+      }
     }
     __threadfence();
     __syncwarp();

@@ -73,11 +73,12 @@ struct DevBucket {
   int32_t out_rank;
   int32_t n_in;                // factors (for kStepAdj the target follows them)
   int32_t dep;                 // step that must be complete before this one (-1: none)
-  int32_t ntask;               // tiles of this step in the persistent queue
+  int32_t ntask;               // chunks of this step in the persistent queue (its done count)
   int32_t kind;                // kStep*
   int32_t aflags;              // kAdj* bits (kStepAdj)
   int32_t tgt_bits;            // kStepAdjRed: target rows 2^tgt_bits (times x = 0, 1)
   int32_t comp_bits;           // kStepAdjRed: completions per target row 2^comp_bits (>= 5)
+  int32_t span;                // warp tiles per queue task (chunk c covers tiles [c*span, (c+1)*span))
   DevInput in[kDevMaxIn];
 };
 
@@ -96,13 +97,14 @@ struct DevLeafFactor {
   uint32_t leaf[kDevMaxLeaves];
 };
 
-// Persistent-queue task.  tile >= 0: tile `tile` of bucket `bucket`.
-// tile < 0: a group of -tile consecutive buckets of one edge chain, starting
-// at `bucket`, each small enough for a single tile; one warp runs them in
-// order with no global synchronisation between them.
+// Persistent-queue task.  chunk >= 0: chunk `chunk` of step `bucket`, its
+// warp tiles [chunk * span, (chunk + 1) * span).  chunk < 0: a group of
+// -chunk consecutive steps of one edge chain, starting at `bucket`, each small
+// enough for a single tile; one warp runs them in order with no global
+// synchronisation between them.
 struct DevTask {
   int32_t bucket;
-  int32_t tile;
+  int32_t chunk;
 };
 
 // Control words at the start of the workspace.

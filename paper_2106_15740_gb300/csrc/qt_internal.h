@@ -54,9 +54,11 @@ int32_t min_fill_order(const Network& net, std::vector<int32_t>* order);
 // `assignment` (bit i for sliced[i]); the other variables keep their order
 // and are renumbered 0.. in it.
 void restrict_network(const Network& net, const std::vector<int32_t>& sliced, uint32_t assignment, Network* out);
-// Choose variables to fix until the min-fill width of the rest is at most
-// w_max (at most max_slices); returns the width reached.
-int32_t choose_slices(const Network& net, int32_t w_max, int32_t max_slices, std::vector<int32_t>* sliced);
+// Choose variables to fix until the width of the rest is at most w_max (at
+// most max_slices); returns the width reached and the elimination order of
+// the restricted networks (restricted variable ids).
+int32_t choose_slices(const Network& net, int32_t w_max, int32_t max_slices, std::vector<int32_t>* sliced,
+                      std::vector<int32_t>* order);
 
 // ----------------------------------------------------------------- plan ----
 constexpr int kMaxIn = 8;        // inputs per bucket (intermediates + one leaf factor)

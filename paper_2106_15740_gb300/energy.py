@@ -30,14 +30,15 @@ class EnergyPlan:
 
     def __init__(self, n_vertices, edges, p, batch=1, dtype="c128", mode="persistent",
                  max_workspace=0, max_width=0, device="cuda:0", gradient=False, lane_items=0,
-                 group_rows=0, edge_range=None, slice=False):
+                 group_rows=0, edge_range=None, slice=False, chunk_tiles=0):
         self.n_vertices, self.p, self.batch = int(n_vertices), int(p), int(batch)
         self.edges = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
         self.device = torch.device(device)
         self.edge_range = (0, len(self.edges)) if edge_range is None else tuple(int(x) for x in edge_range)
         self.options = dict(batch=batch, dtype=dtype, mode=mode, max_workspace=max_workspace,
                             max_width=max_width, gradient=gradient, lane_items=lane_items,
-                            group_rows=group_rows, edge_range=self.edge_range, slice=slice)
+                            group_rows=group_rows, edge_range=self.edge_range, slice=slice,
+                            chunk_tiles=chunk_tiles)
         opt = qb.qt_plan_options_default()
         opt.batch = self.batch
         opt.dtype = DTYPES[dtype]
@@ -49,6 +50,7 @@ class EnergyPlan:
         opt.group_rows = int(group_rows)
         opt.edge_begin, opt.edge_end = self.edge_range
         opt.slice = int(bool(slice))
+        opt.chunk_tiles = int(chunk_tiles)
         self.plan = qb.qt_plan_create(self.n_vertices, self.edges, self.p, opt)
         self.ws_bytes = qb.qt_plan_workspace_size(self.plan)
         self.stats = qb.qt_plan_stats(self.plan)
@@ -107,6 +109,42 @@ class EnergyPlan:
             self.close()
         except Exception:
             pass
+
+
+class QAOAEnergy(torch.autograd.Function):
+    """E(gamma, beta) of a gradient plan as an autograd function.
+
+    ``QAOAEnergy.apply(gamma, beta, plan)`` takes real float64 [B, p] CUDA
+    tensors and returns E[B].  When either angle tensor requires a gradient,
+    the forward call also runs the plan's adjoint bucket sweep (one call of
+    the library computes E and dE/dgamma, dE/dbeta for all B angle sets) and
+    keeps the gradient; backward scales it by grad_output.  Complex tensors
+    never reach autograd.
+    """
+
+    @staticmethod
+    def forward(ctx, gamma, beta, plan):
+        p = plan.p
+        if ctx.needs_input_grad[0] or ctx.needs_input_grad[1]:
+            if not plan.options["gradient"]:
+                raise qb.QTError(qb.QT_ESTATE, "angles require a gradient but the plan has no adjoint sweep")
+            e, g = plan.energy(gamma.detach(), beta.detach(), grad=True)
+            ctx.save_for_backward(g)
+        else:
+            e = plan.energy(gamma.detach(), beta.detach())
+        ctx.p = p
+        return e
+
+    @staticmethod
+    def backward(ctx, grad_energy):
+        (g,) = ctx.saved_tensors
+        go = grad_energy.reshape(-1, 1)
+        return go * g[:, :ctx.p], go * g[:, ctx.p:], None
+
+
+def qaoa_energy(plan, gamma, beta):
+    """E[B] for angle tensors [B, p]; differentiable through ``QAOAEnergy``."""
+    return QAOAEnergy.apply(gamma, beta, plan)
 
 
 def autotune(n_vertices, edges, p, batch=1, dtype="c64", gradient=False, device="cuda:0", reps=3,

@@ -117,3 +117,38 @@ def test_gradient_requires_gradient_plan():
     with pytest.raises(qb.QTError) as ei:
         plan.energy(torch.tensor(g, device="cuda:0"), torch.tensor(b, device="cuda:0"), grad=True)
     assert ei.value.status == qb.QT_ESTATE
+
+
+def test_autograd_function_matches_parameter_shift():
+    """QAOAEnergy through torch.autograd: the gradient of sum_k w_k E_k is
+    w_k times the parameter-shift gradient of angle set k."""
+    from paper_2106_15740_gb300.energy import qaoa_energy
+    n, p, B = 12, 2, 3
+    edges = random_regular_graph(n, 3, 11)
+    g, b = random_angles(B, p, 123)
+    plan = _grad_plan(n, edges, p, B, "c128")
+    gd = torch.tensor(g, device="cuda:0", requires_grad=True)
+    bd = torch.tensor(b, device="cuda:0", requires_grad=True)
+    w = torch.tensor([1.0, -2.0, 0.5], dtype=torch.float64, device="cuda:0")
+    e = qaoa_energy(plan, gd, bd)
+    (e * w).sum().backward()
+    plan.check()
+    for k in range(B):
+        dg, db = gr.param_shift_gradient(n, edges, g[k], b[k])
+        np.testing.assert_allclose(gd.grad[k].cpu().numpy(), w[k].item() * dg, atol=1e-9, rtol=0)
+        np.testing.assert_allclose(bd.grad[k].cpu().numpy(), w[k].item() * db, atol=1e-9, rtol=0)
+        assert abs(e[k].item() - sv.energy(n, edges, g[k], b[k])) < 1e-10 * len(edges)
+
+
+def test_autograd_function_without_gradient_plan():
+    """A forward-only plan serves angle tensors that need no gradient and
+    refuses those that do."""
+    from paper_2106_15740_gb300 import binding as qb
+    from paper_2106_15740_gb300.energy import EnergyPlan, qaoa_energy
+    n, edges, p, g, b = workload("n16_p1")
+    plan = EnergyPlan(n, edges, p, batch=1, dtype="c128", mode="persistent", device="cuda:0")
+    e = qaoa_energy(plan, torch.tensor(g, device="cuda:0"), torch.tensor(b, device="cuda:0"))
+    assert abs(e.item() - sv.energy(n, edges, g[0], b[0])) < 1e-10 * len(edges)
+    with pytest.raises(qb.QTError) as ei:
+        qaoa_energy(plan, torch.tensor(g, device="cuda:0", requires_grad=True), torch.tensor(b, device="cuda:0"))
+    assert ei.value.status == qb.QT_ESTATE
