@@ -170,6 +170,11 @@ qt_status qt_plan_stats(const qt_plan* plan, int32_t* n_edges, int32_t* max_widt
  * of its restricted networks. */
 qt_status qt_plan_edge_widths(const qt_plan* plan, int32_t* widths);
 
+/* Per-edge algorithmic bytes of one call (n_edges entries, host array): the
+ * plan's alg_bytes split by edge, summed over a sliced edge's networks.
+ * The cost model for splitting a graph's edges between GPUs. */
+qt_status qt_plan_edge_bytes(const qt_plan* plan, double* bytes);
+
 /* Per-edge number of sliced variables s (the edge is evaluated as 2^s
  * restricted networks; 0 for an edge that fits the width budget). */
 qt_status qt_plan_edge_slices(const qt_plan* plan, int32_t* slices);

@@ -30,6 +30,7 @@ EXPORTS = [
     "qt_plan_free", "qt_energy_workspace_size", "qt_energy", "qt_last_error",
     "qt_plan_set_profiling", "qt_plan_kernel_times", "qt_plan_energy_static",
     "qt_static_scratch_bytes", "qt_plan_set_wait_limit", "qt_plan_inject_stall", "qt_plan_edge_slices",
+    "qt_plan_edge_bytes",
 ]
 
 
@@ -75,6 +76,7 @@ def lib():
             "qt_plan_stats": [vp, pi32, pi32, C.POINTER(i64), pd, pd],
             "qt_plan_edge_widths": [vp, pi32],
             "qt_plan_edge_slices": [vp, pi32],
+            "qt_plan_edge_bytes": [vp, C.POINTER(C.c_double)],
             "qt_plan_energy": [vp, vp, vp, vp, vp, vp, vp, sz, vp],
             "qt_plan_check": [vp, vp],
             "qt_plan_energy_host": [vp, pd, pd, pd, pd, pd, vp, sz, vp],
@@ -211,6 +213,12 @@ def qt_plan_edge_slices(plan, n_edges):
     sl = np.zeros(n_edges, dtype=np.int32)
     _check(lib().qt_plan_edge_slices(plan, sl.ctypes.data_as(C.POINTER(C.c_int32))))
     return sl
+
+
+def qt_plan_edge_bytes(plan, n_edges):
+    by = np.zeros(n_edges, dtype=np.float64)
+    _check(lib().qt_plan_edge_bytes(plan, by.ctypes.data_as(C.POINTER(C.c_double))))
+    return by
 
 
 def qt_plan_energy(plan, gamma_ptr, beta_ptr, energy_ptr, edge_zz_ptr, grad_ptr, ws_ptr, ws_bytes, stream):

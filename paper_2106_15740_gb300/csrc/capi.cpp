@@ -268,6 +268,12 @@ qt_status qt_plan_edge_widths(const qt_plan* plan, int32_t* widths) {
   return QT_OK;
 }
 
+qt_status qt_plan_edge_bytes(const qt_plan* plan, double* bytes) {
+  if (!plan || !bytes) return fail(QT_EINVAL, "plan or bytes is NULL");
+  std::copy(plan->P.edge_bytes.begin(), plan->P.edge_bytes.end(), bytes);
+  return QT_OK;
+}
+
 qt_status qt_plan_edge_slices(const qt_plan* plan, int32_t* slices) {
   if (!plan || !slices) return fail(QT_EINVAL, "plan or slices is NULL");
   std::copy(plan->P.slices.begin(), plan->P.slices.end(), slices);

@@ -130,10 +130,12 @@ qt_status compile_plan(Plan* P) {
   std::vector<int64_t> region(n_edges), fwd_peak(n_edges), cost(n_edges);
   int64_t leaf_pool = 0, scal_pool = 0;
   P->alg_bytes = 0.0;
+  P->edge_bytes.assign(P->n_orig, 0.0);
   P->flops = 0.0;
   for (int32_t e = 0; e < n_edges; ++e) {
     const EdgePlan& ep = P->edges[e];
     const int32_t nb = (int32_t)ep.buckets.size();
+    const double bytes_before = P->alg_bytes;
 
     Arena arena;
     out_off[e].assign(nb, 0);
@@ -223,6 +225,7 @@ qt_status compile_plan(Plan* P) {
     }
     cost[e] = (int64_t)ebytes * (grad ? 3 : 1);
     P->alg_bytes += ebytes * (double)B * (double)es;
+    P->edge_bytes[ep.edge - P->opt.edge_begin] += P->alg_bytes - bytes_before;
   }
 
   // ---- region placement: per-bucket mode shares one; persistent uses slots ----

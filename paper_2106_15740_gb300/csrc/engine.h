@@ -50,6 +50,7 @@ struct Plan {
 
   // statistics
   double alg_bytes = 0.0, flops = 0.0;
+  std::vector<double> edge_bytes;          // per planned graph edge: algorithmic bytes of its networks
 
   // failure-detection hook: step whose uploaded tile count is made unreachable
   int32_t stall_step = -1;
