@@ -33,6 +33,29 @@ METRIC = "edge ⟨ZZ⟩ evals/sec + energy-grad evals/sec on 1 GB300; % HBM/tens
 WORKLOAD = dict(name="n100_p4", batch=64, dtype="c64")
 
 
+# DRAM traffic of one persistent-kernel launch on the 100-vertex p = 4 graph,
+# per angle set: dram__bytes_read.sum + dram__bytes_write.sum of one ncu
+# capture at B = 4 angle sets (18.49 GB; 9.02 GB at B = 2, so it grows in
+# proportion to B), scaled to the launch's B.  It holds for the kernel sources
+# with this digest only: after any change to them the traffic is reported as
+# null until the kernel is captured again.
+TRAFFIC_CAPTURE = {"sources_sha256_16": "d790be0bed269da2", "bytes_per_angle_set": 18494862336 / 4}
+
+
+def _kernel_digest():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "kernels.cuh", "qt_device.h"):
+        h.update((ROOT / "paper_2106_15740_gb300" / "csrc" / f).read_bytes())
+    return h.hexdigest()[:16]
+
+
+def _traffic(B, profile_only):
+    if profile_only or _kernel_digest() != TRAFFIC_CAPTURE["sources_sha256_16"]:
+        return None
+    return TRAFFIC_CAPTURE["bytes_per_angle_set"] * B
+
+
 def _peaks():
     p = ROOT / "MEASURED_PEAKS.json"
     if p.exists():
@@ -231,12 +254,15 @@ def run_ours(args):
     n, edges, p, _, _ = workload(WORKLOAD["name"])
     B = WORKLOAD["batch"]
     profile_only = ((WORKLOAD["name"], B) != ("n100_p4", 64) or "edge_range" in WORKLOAD or "lane_items" in WORKLOAD
-                    or "chunk_tiles" in WORKLOAD)
+                    or "chunk_tiles" in WORKLOAD or "gradient" in WORKLOAD or "max_width" in WORKLOAD)
+    grad = bool(WORKLOAD.get("gradient", False))
     gamma, beta = random_angles(B, p, 1002 + 7919 * rank)
     t_plan = time.perf_counter()
     plan = EnergyPlan(n, edges, p, batch=B, dtype=WORKLOAD["dtype"], mode="persistent", device=dev,
                       edge_range=WORKLOAD.get("edge_range"), lane_items=WORKLOAD.get("lane_items", 0),
-                      group_rows=WORKLOAD.get("group_rows", 0), chunk_tiles=WORKLOAD.get("chunk_tiles", 0))
+                      group_rows=WORKLOAD.get("group_rows", 0), chunk_tiles=WORKLOAD.get("chunk_tiles", 0),
+                      gradient=grad, max_width=WORKLOAD.get("max_width", 0), slice=WORKLOAD.get("slice", False),
+                      max_workspace=WORKLOAD.get("max_workspace", 0))
     t_plan = time.perf_counter() - t_plan
     g = torch.tensor(gamma, device=dev)
     b = torch.tensor(beta, device=dev)
@@ -244,7 +270,7 @@ def run_ours(args):
     units = plan.n_edges * B
 
     for _ in range(args.warmup):
-        plan.energy(g, b, out=out)
+        plan.energy(g, b, out=out, grad=grad)
     plan.check()
 
     qb.qt_plan_set_profiling(plan.plan, True)
@@ -258,7 +284,7 @@ def run_ours(args):
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
     for _ in range(args.steps):
-        plan.energy(g, b, out=out)
+        plan.energy(g, b, out=out, grad=grad)
     t1.record(stream)
     torch.cuda.synchronize(dev)
     if pg:
@@ -300,15 +326,17 @@ def run_ours(args):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": WORKLOAD["dtype"],
             "data": "synthetic",
-            "config": {"workload": "random 3-regular N=100 p=4 (seed 2), 150 edge lightcones x 64 angle sets, "
-                                   "complex64 + FP64 sums, persistent launch",
+            "config": {"workload": ("random 3-regular N=100 p=4 (seed 2), 150 edge lightcones x 64 angle sets, "
+                                    "complex64 + FP64 sums, persistent launch") if not profile_only else
+                                   f"profiling case {WORKLOAD}",
                        "n_vertices": n, "p": p, "edges": len(edges), "angle_sets_per_gpu": B,
                        "max_width": int(plan.stats["max_width"]), "buckets": plan.stats["n_buckets"],
                        "workspace_gb": round(plan.ws_bytes / 1e9, 2),
                        "l2": "working set larger than L2 (intermediates streamed through HBM every step)",
                        "plan_host_s": round(t_plan, 3)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "persistent_kernel<float,2,false>",
+                         "frac": achieved / peak, "traffic": _traffic(B, profile_only),
+                         "kernel": "persistent_kernel<float,2,false>",
                          "kernel_ms": kms, "alg_bytes_per_launch": alg, "peak_kind": peak_kind},
             "e2e": {"value": units * world / e2e_s, "unit": "edge_evals/s",
                     "h2d_bytes_per_step": int(2 * B * p * 8), "d2h_bytes_per_step": int(B * 8)},
@@ -339,7 +367,11 @@ def main():
     ap.add_argument("--edges", default=None, help="profiling only: edge range a:b of the graph")
     ap.add_argument("--lane-items", type=int, default=0, help="profiling only: warp tile items per lane")
     ap.add_argument("--group-rows", type=int, default=0, help="profiling only: grouping threshold")
-    ap.add_argument("--chunk-tiles", type=int, default=0, help="profiling only: warp tiles per queue claim")
+    ap.add_argument("--chunk-tiles", type=int, default=0, help="profiling only: warp tiles per queue task")
+    ap.add_argument("--gradient", action="store_true", help="profiling only: time the energy + adjoint gradient")
+    ap.add_argument("--max-width", type=int, default=0, help="profiling only: width budget")
+    ap.add_argument("--slice", action="store_true", help="profiling only: slice edges above the width budget")
+    ap.add_argument("--max-workspace-gb", type=float, default=0, help="profiling only: workspace cap")
     args = ap.parse_args()
     if args.edges:
         a, b = (int(x) for x in args.edges.split(":"))
@@ -350,6 +382,14 @@ def main():
     if args.chunk_tiles:
         WORKLOAD["chunk_tiles"] = args.chunk_tiles
         args.no_cpu_baseline = True
+    if args.gradient:
+        WORKLOAD["gradient"] = True
+        args.no_cpu_baseline = True
+    if args.max_width:
+        WORKLOAD["max_width"], WORKLOAD["slice"] = args.max_width, args.slice
+        args.no_cpu_baseline = True
+    if args.max_workspace_gb:
+        WORKLOAD["max_workspace"] = int(args.max_workspace_gb * (1 << 30))
     for key in ("batch", "workload", "dtype"):
         val = getattr(args, key)
         if val is not None:
