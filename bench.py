@@ -30,16 +30,21 @@ if str(ROOT) not in sys.path:
     sys.path.insert(0, str(ROOT))
 
 METRIC = "edge ⟨ZZ⟩ evals/sec + energy-grad evals/sec on 1 GB300; % HBM/tensor roofline"
-WORKLOAD = dict(name="n100_p4", batch=64, dtype="c64")
+WORKLOAD = dict(name="n100_p4", batch=64, dtype="c64", order_trials=100)
 
 
 # DRAM traffic of one persistent-kernel launch on the 100-vertex p = 4 graph,
 # per angle set: dram__bytes_read.sum + dram__bytes_write.sum of one ncu
-# capture at B = 4 angle sets (18.49 GB; 9.02 GB at B = 2, so it grows in
-# proportion to B), scaled to the launch's B.  It holds for the kernel sources
-# with this digest only: after any change to them the traffic is reported as
-# null until the kernel is captured again.
-TRAFFIC_CAPTURE = {"sources_sha256_16": "d790be0bed269da2", "bytes_per_angle_set": 18494862336 / 4}
+# capture at B = 4 angle sets, which grows in proportion to B (checked at
+# B = 2), scaled to the launch's B.  It holds only for the kernel sources with
+# this digest and for the plan with these algorithmic bytes per angle set (the
+# contraction order fixes the traffic): otherwise the traffic is reported as
+# null until that kernel and plan are captured again.
+TRAFFIC_CAPTURES = [
+    # greedy min-fill order
+    {"sources_sha256_16": "d790be0bed269da2", "alg_bytes_per_angle_set": 18702118912 / 4,
+     "bytes_per_angle_set": 18494862336 / 4},
+]
 
 
 def _kernel_digest():
@@ -50,10 +55,14 @@ def _kernel_digest():
     return h.hexdigest()[:16]
 
 
-def _traffic(B, profile_only):
-    if profile_only or _kernel_digest() != TRAFFIC_CAPTURE["sources_sha256_16"]:
+def _traffic(B, alg_bytes, profile_only):
+    if profile_only:
         return None
-    return TRAFFIC_CAPTURE["bytes_per_angle_set"] * B
+    digest = _kernel_digest()
+    for cap in TRAFFIC_CAPTURES:
+        if cap["sources_sha256_16"] == digest and abs(alg_bytes / B / cap["alg_bytes_per_angle_set"] - 1) < 1e-9:
+            return cap["bytes_per_angle_set"] * B
+    return None
 
 
 def _peaks():
@@ -196,6 +205,18 @@ def _time_calls(plan, g, b, grad, reps, torch):
     return t0.elapsed_time(t1) / reps
 
 
+def min_fill_comparison(n, edges, p, B, g, b, dev, torch):
+    """The same step with the plain greedy min-fill order (more bytes)."""
+    from paper_2106_15740_gb300.energy import EnergyPlan
+    plan = EnergyPlan(n, edges, p, batch=B, dtype=WORKLOAD["dtype"], mode="persistent", device=dev)
+    ms = _time_calls(plan, g, b, False, 5, torch)
+    out = {"value": len(edges) * B / (ms * 1e-3), "unit": "edge_evals/s", "ms_per_step": ms,
+           "alg_bytes_per_step": plan.stats["alg_bytes"], "max_width": int(plan.stats["max_width"]),
+           "achieved_gbs": plan.stats["alg_bytes"] / (ms * 1e-3) / 1e9}
+    plan.close()
+    return out
+
+
 def gradient_and_comparator(dev, torch):
     """Energy-gradient throughput on the 60-vertex p = 4 workload (8 angles,
     one angle set, complex64 adjoint sweep), and the plain per-edge complex128
@@ -206,8 +227,13 @@ def gradient_and_comparator(dev, torch):
     out = {}
     n, edges, p, g, b = workload("n60_p4")
     gd, bd = torch.tensor(g, device=dev), torch.tensor(b, device=dev)
-    plan = EnergyPlan(n, edges, p, batch=1, dtype="c64", mode="persistent", gradient=True, device=dev)
+    plan = EnergyPlan(n, edges, p, batch=1, dtype="c64", mode="persistent", gradient=True, device=dev,
+                      order_trials=WORKLOAD.get("order_trials", 0))
     ms_grad = _time_calls(plan, gd, bd, True, 5, torch)
+    grad_alg = plan.stats["alg_bytes"]
+    plan.close()
+    plan = EnergyPlan(n, edges, p, batch=1, dtype="c64", mode="persistent", gradient=True, device=dev)
+    ms_grad_mf = _time_calls(plan, gd, bd, True, 3, torch)
     plan.close()
     plan = EnergyPlan(n, edges, p, batch=1, dtype="c128", mode="per_bucket", device=dev)
     ms_loop = _time_calls(plan, gd, bd, False, 3, torch)
@@ -216,6 +242,9 @@ def gradient_and_comparator(dev, torch):
                    "ms_per_eval": ms_grad, "dtype": "c64",
                    "workload": "random 3-regular N=60 p=4 (seed 3), 90 edge lightcones, dE/dgamma and dE/dbeta "
                                "(8 angles) by the adjoint bucket sweep, one angle set",
+                   "ordering": f"searched, {WORKLOAD.get('order_trials', 0)} trials per edge",
+                   "alg_bytes_per_eval": grad_alg, "achieved_gbs": grad_alg / (ms_grad * 1e-3) / 1e9,
+                   "min_fill_order_ms_per_eval": ms_grad_mf,
                    "per_edge_c128_forward_ms": ms_loop,
                    "speedup_vs_per_edge_c128_forward": ms_loop / ms_grad}
     n, edges, p, g, b = workload("n100_p4", batch=1)
@@ -254,7 +283,8 @@ def run_ours(args):
     n, edges, p, _, _ = workload(WORKLOAD["name"])
     B = WORKLOAD["batch"]
     profile_only = ((WORKLOAD["name"], B) != ("n100_p4", 64) or "edge_range" in WORKLOAD or "lane_items" in WORKLOAD
-                    or "chunk_tiles" in WORKLOAD or "gradient" in WORKLOAD or "max_width" in WORKLOAD)
+                    or "chunk_tiles" in WORKLOAD or "gradient" in WORKLOAD or "max_width" in WORKLOAD
+                    or "profile_order" in WORKLOAD)
     grad = bool(WORKLOAD.get("gradient", False))
     gamma, beta = random_angles(B, p, 1002 + 7919 * rank)
     t_plan = time.perf_counter()
@@ -262,7 +292,7 @@ def run_ours(args):
                       edge_range=WORKLOAD.get("edge_range"), lane_items=WORKLOAD.get("lane_items", 0),
                       group_rows=WORKLOAD.get("group_rows", 0), chunk_tiles=WORKLOAD.get("chunk_tiles", 0),
                       gradient=grad, max_width=WORKLOAD.get("max_width", 0), slice=WORKLOAD.get("slice", False),
-                      max_workspace=WORKLOAD.get("max_workspace", 0))
+                      max_workspace=WORKLOAD.get("max_workspace", 0), order_trials=WORKLOAD.get("order_trials", 0))
     t_plan = time.perf_counter() - t_plan
     g = torch.tensor(gamma, device=dev)
     b = torch.tensor(beta, device=dev)
@@ -329,13 +359,17 @@ def run_ours(args):
             "config": {"workload": ("random 3-regular N=100 p=4 (seed 2), 150 edge lightcones x 64 angle sets, "
                                     "complex64 + FP64 sums, persistent launch") if not profile_only else
                                    f"profiling case {WORKLOAD}",
+                       "ordering": (f"per edge the cheapest of greedy min-fill and {WORKLOAD.get('order_trials', 0)} "
+                                    "seeded randomised greedy orders (seed 0, tau 1), no wider than min-fill"
+                                    if WORKLOAD.get("order_trials", 0) else "greedy min-fill"),
+                       "alg_bytes_per_step": alg,
                        "n_vertices": n, "p": p, "edges": len(edges), "angle_sets_per_gpu": B,
                        "max_width": int(plan.stats["max_width"]), "buckets": plan.stats["n_buckets"],
                        "workspace_gb": round(plan.ws_bytes / 1e9, 2),
                        "l2": "working set larger than L2 (intermediates streamed through HBM every step)",
                        "plan_host_s": round(t_plan, 3)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": _traffic(B, profile_only),
+                         "frac": achieved / peak, "traffic": _traffic(B, alg, profile_only),
                          "kernel": "persistent_kernel<float,2,false>",
                          "kernel_ms": kms, "alg_bytes_per_launch": alg, "peak_kind": peak_kind},
             "e2e": {"value": units * world / e2e_s, "unit": "edge_evals/s",
@@ -345,6 +379,8 @@ def run_ours(args):
         }
         if profile_only:
             res["profile_only"] = f"{WORKLOAD} (not the bench workload)"
+        if not profile_only and WORKLOAD.get("order_trials", 0):
+            res["min_fill_order"] = min_fill_comparison(n, edges, p, B, g, b, dev, torch)
         if not args.no_cpu_baseline:
             res.update(gradient_and_comparator(dev, torch))
             res["per_edge_c128_loop"]["speedup_of_value"] = res["value"] / res["per_edge_c128_loop"]["edge_evals_per_s"]
@@ -372,6 +408,8 @@ def main():
     ap.add_argument("--max-width", type=int, default=0, help="profiling only: width budget")
     ap.add_argument("--slice", action="store_true", help="profiling only: slice edges above the width budget")
     ap.add_argument("--max-workspace-gb", type=float, default=0, help="profiling only: workspace cap")
+    ap.add_argument("--order-trials", type=int, default=None,
+                    help="profiling only: randomised greedy orders per edge (0: min-fill)")
     args = ap.parse_args()
     if args.edges:
         a, b = (int(x) for x in args.edges.split(":"))
@@ -387,6 +425,10 @@ def main():
         args.no_cpu_baseline = True
     if args.max_width:
         WORKLOAD["max_width"], WORKLOAD["slice"] = args.max_width, args.slice
+        args.no_cpu_baseline = True
+    if args.order_trials is not None:
+        WORKLOAD["order_trials"] = args.order_trials
+        WORKLOAD["profile_order"] = True
         args.no_cpu_baseline = True
     if args.max_workspace_gb:
         WORKLOAD["max_workspace"] = int(args.max_workspace_gb * (1 << 30))

@@ -148,6 +148,13 @@ typedef struct {
                              the network fits, and the 2^s restricted networks are summed */
   int32_t chunk_tiles;    /* persistent mode: warp tiles per queue task (<=0: one, or more for the
                              widest steps when the queue would pass 2^27 tasks) */
+  int32_t order_trials;   /* 0: greedy min-fill order.  n > 0: also n seeded randomised greedy
+                             orders per edge (§Results orders with a randomised greedy, rgreedy);
+                             the one with the fewest bucket elements that is no wider than
+                             min-fill is kept.  Values are unchanged (up to rounding order) */
+  int32_t order_seed;     /* seed of the randomised orders (with the edge index) */
+  double order_tau;       /* temperature: the next variable is drawn with probability
+                             proportional to exp(-(fill - min fill) / order_tau) (<=0: 1) */
 } qt_plan_options;
 
 /* Fill `opt` with defaults: batch 1, QT_C128, QT_MODE_PER_BUCKET, no gradient,

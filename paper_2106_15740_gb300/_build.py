@@ -72,7 +72,7 @@ def build(verbose: bool = False, force: bool = False) -> Path:
     if failed:
         raise RuntimeError("compilation failed: " + ", ".join(failed))
     if force or jobs or _stale(LIB, objs):
-        cmd = [nvcc, *ARCH, "-shared", "-o", str(LIB), *map(str, objs), "-cudart", "static"]
+        cmd = [nvcc, *ARCH, "-shared", "-o", str(LIB), *map(str, objs), "-cudart", "static", "-lpthread"]
         res = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
         if res.returncode:
             sys.stderr.write(res.stdout.decode(errors="replace"))

@@ -49,7 +49,8 @@ class qt_plan_options(C.Structure):
                 ("gradient", C.c_int32), ("max_width", C.c_int32), ("lane_items", C.c_int32),
                 ("max_workspace", C.c_int64), ("group_rows", C.c_int32), ("edge_begin", C.c_int32),
                 ("edge_end", C.c_int32), ("slice", C.c_int32),
-                ("chunk_tiles", C.c_int32)]
+                ("chunk_tiles", C.c_int32), ("order_trials", C.c_int32), ("order_seed", C.c_int32),
+                ("order_tau", C.c_double)]
 
 
 _lib = None

@@ -1,7 +1,10 @@
 // extern "C" entry points declared in include/qtensor.h.  Argument checks,
 // handle management and error reporting; the work is in network.cpp,
 // order.cpp, buckets.cpp, engine.cpp and the CUDA kernels.
+#include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <thread>
 #include <new>
 
 #include "engine.h"
@@ -23,55 +26,100 @@ static qt_status check_angles(const double* a, int64_t n, const char* name) {
   return QT_OK;
 }
 
-// Build, order and bucket-plan every edge network of a graph.
-// Build, order and bucket-plan every edge network of a graph.  An edge above
-// the width budget is rejected, or, with slicing, fixed variables are chosen
-// until the rest fits and its 2^s restricted networks are planned (one order
-// for all of them: they share the structure).
+// Build, order and bucket-plan every edge network of a graph.  The order is
+// greedy min-fill, or the cheapest of min-fill and `order_trials` seeded
+// randomised greedy orders that are no wider.  An edge above the width budget
+// is rejected, or, with slicing, fixed variables are chosen until the rest
+// fits and its 2^s restricted networks are planned (one order for all of
+// them: they share the structure).  Edges are planned on host threads.
 static constexpr int32_t kMaxSlices = 20;
 
-static qt_status plan_edges(const Graph& G, int32_t p, int32_t max_width, bool slice, int32_t e0, int32_t e1,
-                            Plan* P) {
+struct EdgeResult {
+  std::vector<EdgePlan> nets;
+  int32_t width = 0, n_sliced = 0;
+  qt_status st = QT_OK;
+  std::string msg;
+};
+
+static void plan_one_edge(const Graph& G, int32_t p, int32_t e, const qt_plan_options& o, EdgeResult* r) {
+  Network net;
+  build_lightcone(G, p, e, &net);
+  const uint64_t seed = ((uint64_t)(uint32_t)o.order_seed << 32) ^ (uint64_t)(uint32_t)e;
+  const double tau = o.order_tau > 0 ? o.order_tau : 1.0;
+  std::vector<int32_t> order;
+  int32_t w = o.order_trials > 0 ? search_order(net, o.order_trials, tau, seed, 0, &order)
+                                 : min_fill_order(net, &order);
+  std::vector<int32_t> sliced;
+  if (w > o.max_width) {
+    if (!o.slice) {
+      r->st = QT_EWIDTH;
+      r->msg = "edge " + std::to_string(e) + " has contraction width " + std::to_string(w) + " above the budget " +
+               std::to_string(o.max_width);
+      return;
+    }
+    const std::vector<int32_t> base = order;
+    w = choose_slices(net, o.max_width, kMaxSlices, base, o.order_trials, tau, seed, &sliced, &order);
+    if (w > o.max_width) {
+      r->st = QT_EWIDTH;
+      r->msg = "edge " + std::to_string(e) + " needs more than " + std::to_string(kMaxSlices) +
+               " sliced variables to reach width " + std::to_string(o.max_width);
+      return;
+    }
+  }
+  const uint32_t n_slices = 1u << sliced.size();
+  r->nets.reserve(n_slices);
+  for (uint32_t a = 0; a < n_slices; ++a) {
+    EdgePlan ep;
+    qt_status st;
+    if (sliced.empty()) {
+      st = make_edge_plan(net, order, &ep);
+    } else {
+      Network rn;
+      restrict_network(net, sliced, a, &rn);
+      st = make_edge_plan(rn, order, &ep);
+    }
+    if (st != QT_OK) {
+      r->st = st;
+      r->msg = g_last_error;  // this thread's message
+      return;
+    }
+    ep.edge = e;
+    ep.slices = (int32_t)sliced.size();
+    r->nets.push_back(std::move(ep));
+  }
+  r->width = w;
+  r->n_sliced = (int32_t)sliced.size();
+}
+
+static qt_status plan_edges(const Graph& G, int32_t p, const qt_plan_options& o, int32_t e0, int32_t e1, Plan* P) {
+  const int32_t m = e1 - e0;
+  std::vector<EdgeResult> res(m);
+  const int32_t hw = (int32_t)std::max(1u, std::thread::hardware_concurrency());
+  const int32_t n_threads = std::min({hw, m, 64});
+  std::atomic<int32_t> next{0};
+  auto worker = [&]() {
+    for (int32_t k = next.fetch_add(1); k < m; k = next.fetch_add(1)) plan_one_edge(G, p, e0 + k, o, &res[k]);
+  };
+  if (n_threads <= 1) {
+    worker();
+  } else {
+    std::vector<std::thread> pool;
+    for (int32_t t = 0; t < n_threads; ++t) pool.emplace_back(worker);
+    for (auto& t : pool) t.join();
+  }
   P->edges.clear();
   P->widths.clear();
   P->slices.clear();
   P->net_first.assign(1, 0);
-  for (int32_t e = e0; e < e1; ++e) {
-    Network net;
-    build_lightcone(G, p, e, &net);
-    std::vector<int32_t> order;
-    int32_t w = min_fill_order(net, &order);
-    std::vector<int32_t> sliced;
-    if (w > max_width) {
-      if (!slice)
-        return fail(QT_EWIDTH, "edge " + std::to_string(e) + " has contraction width " + std::to_string(w) +
-                                   " above the budget " + std::to_string(max_width));
-      w = choose_slices(net, max_width, kMaxSlices, &sliced, &order);
-      if (w > max_width)
-        return fail(QT_EWIDTH, "edge " + std::to_string(e) + " needs more than " + std::to_string(kMaxSlices) +
-                                   " sliced variables to reach width " + std::to_string(max_width));
-    }
-    const uint32_t n_slices = 1u << sliced.size();
-    for (uint32_t a = 0; a < n_slices; ++a) {
-      EdgePlan ep;
-      qt_status st;
-      if (sliced.empty()) {
-        st = make_edge_plan(net, order, &ep);
-      } else {
-        Network r;
-        restrict_network(net, sliced, a, &r);
-        st = make_edge_plan(r, order, &ep);
-      }
-      if (st != QT_OK) return st;
-      ep.edge = e;
-      ep.slices = (int32_t)sliced.size();
-      P->edges.push_back(std::move(ep));
-    }
-    P->widths.push_back(w);
-    P->slices.push_back((int32_t)sliced.size());
+  for (int32_t k = 0; k < m; ++k) {
+    EdgeResult& r = res[k];
+    if (r.st != QT_OK) return fail(r.st, r.msg);
+    for (EdgePlan& ep : r.nets) P->edges.push_back(std::move(ep));
+    P->widths.push_back(r.width);
+    P->slices.push_back(r.n_sliced);
     P->net_first.push_back((int32_t)P->edges.size());
   }
-  P->n_orig = e1 - e0;
+  P->n_orig = m;
   return QT_OK;
 }
 
@@ -199,6 +247,9 @@ void qt_plan_options_default(qt_plan_options* opt) {
   opt->edge_end = 0;
   opt->slice = 0;
   opt->chunk_tiles = 0;
+  opt->order_trials = 0;
+  opt->order_seed = 0;
+  opt->order_tau = 1.0;
 }
 
 qt_status qt_plan_create(const qt_graph* g, int32_t p, const qt_plan_options* opt, qt_plan** out) {
@@ -214,6 +265,8 @@ qt_status qt_plan_create(const qt_graph* g, int32_t p, const qt_plan_options* op
   if (o.lane_items > 0 && o.lane_items != 8 && o.lane_items != 16 && o.lane_items != 32 && o.lane_items != 64)
     return fail(QT_EINVAL, "lane_items must be 8, 16, 32 or 64");
   if (o.lane_items <= 0) o.lane_items = o.batch >= 16 ? 32 : 16;
+  if (o.order_trials < 0 || o.order_trials > 100000) return fail(QT_EINVAL, "order_trials must be in [0, 100000]");
+  if (!(o.order_tau >= 0.0) || !std::isfinite(o.order_tau)) return fail(QT_EINVAL, "order_tau must be finite and >= 0");
   qt_plan* h = new (std::nothrow) qt_plan;
   if (!h) return fail(QT_ENOMEM, "host allocation failed");
   qt_status st = make_graph(g, &h->P.G);
@@ -228,7 +281,7 @@ qt_status qt_plan_create(const qt_graph* g, int32_t p, const qt_plan_options* op
     } else {
       h->P.opt.edge_begin = o.edge_begin;
       h->P.opt.edge_end = e1;
-      st = plan_edges(h->P.G, p, o.max_width, o.slice != 0, o.edge_begin, e1, &h->P);
+      st = plan_edges(h->P.G, p, o, o.edge_begin, e1, &h->P);
     }
   }
   if (st == QT_OK) st = compile_plan(&h->P);

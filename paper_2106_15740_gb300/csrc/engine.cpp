@@ -131,6 +131,9 @@ qt_status compile_plan(Plan* P) {
   int64_t leaf_pool = 0, scal_pool = 0;
   P->alg_bytes = 0.0;
   P->edge_bytes.assign(P->n_orig, 0.0);
+  std::vector<int32_t> orig_of(n_edges, 0);  // planned graph edge of each network
+  for (int32_t o = 0; o < P->n_orig; ++o)
+    for (int32_t k = P->net_first[o]; k < P->net_first[o + 1]; ++k) orig_of[k] = o;
   P->flops = 0.0;
   for (int32_t e = 0; e < n_edges; ++e) {
     const EdgePlan& ep = P->edges[e];
@@ -225,7 +228,7 @@ qt_status compile_plan(Plan* P) {
     }
     cost[e] = (int64_t)ebytes * (grad ? 3 : 1);
     P->alg_bytes += ebytes * (double)B * (double)es;
-    P->edge_bytes[ep.edge - P->opt.edge_begin] += P->alg_bytes - bytes_before;
+    P->edge_bytes[orig_of[e]] += P->alg_bytes - bytes_before;
   }
 
   // ---- region placement: per-bucket mode shares one; persistent uses slots ----

@@ -12,6 +12,7 @@
 // neighbours of the eliminated variable and their neighbours can change
 // fill-in, so only those are recounted.
 #include <algorithm>
+#include <cmath>
 
 #include "qt_internal.h"
 
@@ -60,7 +61,11 @@ struct BitGraph {
 
 }  // namespace
 
-int32_t min_fill_order(const Network& net, std::vector<int32_t>* order) {
+// Eliminate every variable of `net` in the order `pick` chooses from the
+// current (fill, degree, alive) arrays; returns the width and the cost
+// sum_b 2^{|U_b|} (elements the bucket steps touch, up to a factor).
+template <class Pick>
+static int32_t greedy_eliminate(const Network& net, Pick pick, std::vector<int32_t>* order, double* cost) {
   const int32_t n = net.n_vars;
   BitGraph G(n);
   for (const Tensor& t : net.tensors)
@@ -78,19 +83,15 @@ int32_t min_fill_order(const Network& net, std::vector<int32_t>* order) {
   order->clear();
   order->reserve(n);
   int32_t width = 0;
+  double c = 0.0;
   std::vector<int32_t> nb, touched;
   std::vector<char> mark(n, 0);
   for (int32_t step = 0; step < n; ++step) {
-    int32_t best = -1;
-    for (int32_t v = 0; v < n; ++v) {
-      if (!alive[v]) continue;
-      if (best < 0 || fill[v] < fill[best] || (fill[v] == fill[best] && deg[v] < deg[best]))
-        best = v;  // ascending scan keeps the smallest id on full ties
-    }
-    const int32_t v = best;
+    const int32_t v = pick(step, fill, deg, alive);
     nb.clear();
     G.for_each(v, [&](int32_t a) { nb.push_back(a); });
     width = std::max(width, (int32_t)nb.size());
+    c += std::ldexp(1.0, (int)nb.size() + 1);
     for (int32_t a : nb) {
       G.clear(a, v);
       for (int32_t b : nb)
@@ -113,7 +114,84 @@ int32_t min_fill_order(const Network& net, std::vector<int32_t>* order) {
       deg[u] = G.degree(u);
     }
   }
+  if (cost) *cost = c;
   return width;
+}
+
+int32_t min_fill_order(const Network& net, std::vector<int32_t>* order, double* cost) {
+  auto pick = [](int32_t, const std::vector<int64_t>& fill, const std::vector<int32_t>& deg,
+                 const std::vector<char>& alive) {
+    int32_t best = -1;
+    for (int32_t v = 0; v < (int32_t)fill.size(); ++v) {
+      if (!alive[v]) continue;
+      if (best < 0 || fill[v] < fill[best] || (fill[v] == fill[best] && deg[v] < deg[best]))
+        best = v;  // ascending scan keeps the smallest id on full ties
+    }
+    return best;
+  };
+  return greedy_eliminate(net, pick, order, cost);
+}
+
+// SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
+// generators", 2014): a counter-based generator, so a trial's draws depend
+// only on (seed, trial, step).
+static uint64_t splitmix64(uint64_t x) {
+  x += 0x9e3779b97f4a7c15ull;
+  x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+  x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+  return x ^ (x >> 31);
+}
+
+int32_t random_greedy_order(const Network& net, double tau, uint64_t seed, uint64_t trial,
+                            std::vector<int32_t>* order, double* cost) {
+  std::vector<double> wgt;
+  auto pick = [&](int32_t step, const std::vector<int64_t>& fill, const std::vector<int32_t>& deg,
+                  const std::vector<char>& alive) {
+    // weight exp(-(f_v - f_min) / tau) with f = fill-in + degree / (n + 1)
+    // (the degree breaks ties between equal fill-ins)
+    const int32_t n = (int32_t)fill.size();
+    double fmin = INFINITY;
+    for (int32_t v = 0; v < n; ++v)
+      if (alive[v]) fmin = std::min(fmin, (double)fill[v] + (double)deg[v] / (n + 1));
+    wgt.assign(n, 0.0);
+    double total = 0.0;
+    for (int32_t v = 0; v < n; ++v) {
+      if (!alive[v]) continue;
+      const double f = (double)fill[v] + (double)deg[v] / (n + 1);
+      const double x = (f - fmin) / tau;
+      wgt[v] = x > 40.0 ? 0.0 : std::exp(-x);
+      total += wgt[v];
+    }
+    const uint64_t r = splitmix64(splitmix64(splitmix64(seed) ^ trial) ^ (uint64_t)step);
+    double u = (double)(r >> 11) * 0x1.0p-53 * total;
+    int32_t last = -1;
+    for (int32_t v = 0; v < n; ++v) {
+      if (wgt[v] <= 0.0) continue;
+      last = v;
+      if (u < wgt[v]) return v;
+      u -= wgt[v];
+    }
+    return last;  // rounding left u just above the total
+  };
+  return greedy_eliminate(net, pick, order, cost);
+}
+
+int32_t search_order(const Network& net, int32_t trials, double tau, uint64_t seed, int32_t w_cap,
+                     std::vector<int32_t>* order, double* cost) {
+  double best_cost = 0.0;
+  int32_t best_w = min_fill_order(net, order, &best_cost);
+  std::vector<int32_t> cand;
+  for (int32_t t = 0; t < trials; ++t) {
+    double c = 0.0;
+    const int32_t w = random_greedy_order(net, tau, seed, (uint64_t)t, &cand, &c);
+    if (w <= std::max(w_cap, best_w) && (c < best_cost || (c == best_cost && w < best_w))) {
+      best_cost = c;
+      best_w = w;
+      order->swap(cand);
+    }
+  }
+  if (cost) *cost = best_cost;
+  return best_w;
 }
 
 }  // namespace qt

@@ -47,17 +47,31 @@ struct Network {
 void build_lightcone(const Graph& g, int32_t p, int32_t edge, Network* net);
 
 // ---------------------------------------------------------------- order ----
-// Greedy min-fill over the interaction graph; returns the width.
-int32_t min_fill_order(const Network& net, std::vector<int32_t>* order);
+// Greedy min-fill over the interaction graph; returns the width (and, if
+// `cost` is given, sum_b 2^{|U_b|} over the buckets of the order).
+int32_t min_fill_order(const Network& net, std::vector<int32_t>* order, double* cost = nullptr);
+// One seeded randomised greedy order: each step draws the next variable
+// with probability proportional to exp(-(f_v - f_min) / tau) (f: fill-in,
+// degree as tie-break).  Returns the width and the cost as above.
+int32_t random_greedy_order(const Network& net, double tau, uint64_t seed, uint64_t trial,
+                            std::vector<int32_t>* order, double* cost = nullptr);
+// Min-fill plus `trials` randomised orders: the cheapest whose width is at
+// most max(w_cap, min-fill width).  Returns its width.
+int32_t search_order(const Network& net, int32_t trials, double tau, uint64_t seed, int32_t w_cap,
+                     std::vector<int32_t>* order, double* cost = nullptr);
 
 // Slicing: the network with the variables `sliced` fixed to the bits of
 // `assignment` (bit i for sliced[i]); the other variables keep their order
 // and are renumbered 0.. in it.
 void restrict_network(const Network& net, const std::vector<int32_t>& sliced, uint32_t assignment, Network* out);
 // Choose variables to fix until the width of the rest is at most w_max (at
-// most max_slices); returns the width reached and the elimination order of
-// the restricted networks (restricted variable ids).
-int32_t choose_slices(const Network& net, int32_t w_max, int32_t max_slices, std::vector<int32_t>* sliced,
+// most max_slices), keeping the order `base` of the whole network; returns
+// the width reached and the elimination order of the restricted networks
+// (restricted variable ids): `base` restricted, or a fresh order of the
+// restricted network (min-fill, or searched with `trials` randomised orders)
+// when that is cheaper.
+int32_t choose_slices(const Network& net, int32_t w_max, int32_t max_slices, const std::vector<int32_t>& base,
+                      int32_t trials, double tau, uint64_t seed, std::vector<int32_t>* sliced,
                       std::vector<int32_t>* order);
 
 // ----------------------------------------------------------------- plan ----

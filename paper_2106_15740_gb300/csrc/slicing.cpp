@@ -86,17 +86,18 @@ double order_cost(const std::vector<std::vector<int32_t>>& sets, const std::vect
 
 }  // namespace
 
-// Width guard.  The min-fill order of the whole network is kept and
-// variables are fixed one at a time: fixing x removes it from every bucket
+// Width guard.  The order of the whole network is kept and variables are
+// fixed one at a time: fixing x removes it from every bucket
 // set that holds it, so the width can only go down.  Each step fixes the
 // variable held by the most widest bucket results (ties: the largest drop in
-// total bucket elements).  The restricted network's own min-fill order is
-// then tried as well; the cheaper of the two orders is returned.
-int32_t choose_slices(const Network& net, int32_t w_max, int32_t max_slices, std::vector<int32_t>* sliced,
+// total bucket elements).  The restricted network's own order (min-fill, or
+// the order search) is then tried as well; the cheaper of the two orders is
+// returned.
+int32_t choose_slices(const Network& net, int32_t w_max, int32_t max_slices, const std::vector<int32_t>& base,
+                      int32_t trials, double tau, uint64_t seed, std::vector<int32_t>* sliced,
                       std::vector<int32_t>* order_out) {
   sliced->clear();
-  std::vector<int32_t> order;
-  min_fill_order(net, &order);
+  const std::vector<int32_t>& order = base;
   const auto sets = bucket_sets(net, order);
   std::vector<char> in_s(net.n_vars, 0);
   auto width_now = [&]() {
@@ -147,7 +148,8 @@ int32_t choose_slices(const Network& net, int32_t w_max, int32_t max_slices, std
   Network red;
   restrict_network(net, *sliced, 0u, &red);
   std::vector<int32_t> reorder;
-  const int32_t w2 = min_fill_order(red, &reorder);
+  const int32_t w2 = trials > 0 ? search_order(red, trials, tau, seed ^ 0x5bd1e995ull, w_max, &reorder)
+                                : min_fill_order(red, &reorder);
   if (w2 <= std::max(w, w_max)) {
     std::vector<char> none(red.n_vars, 0);
     const double c1 = order_cost(bucket_sets(red, *order_out), none);

@@ -30,7 +30,8 @@ class EnergyPlan:
 
     def __init__(self, n_vertices, edges, p, batch=1, dtype="c128", mode="persistent",
                  max_workspace=0, max_width=0, device="cuda:0", gradient=False, lane_items=0,
-                 group_rows=0, edge_range=None, slice=False, chunk_tiles=0):
+                 group_rows=0, edge_range=None, slice=False, chunk_tiles=0, order_trials=0, order_seed=0,
+                 order_tau=1.0):
         self.n_vertices, self.p, self.batch = int(n_vertices), int(p), int(batch)
         self.edges = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
         self.device = torch.device(device)
@@ -38,7 +39,8 @@ class EnergyPlan:
         self.options = dict(batch=batch, dtype=dtype, mode=mode, max_workspace=max_workspace,
                             max_width=max_width, gradient=gradient, lane_items=lane_items,
                             group_rows=group_rows, edge_range=self.edge_range, slice=slice,
-                            chunk_tiles=chunk_tiles)
+                            chunk_tiles=chunk_tiles, order_trials=order_trials, order_seed=order_seed,
+                            order_tau=order_tau)
         opt = qb.qt_plan_options_default()
         opt.batch = self.batch
         opt.dtype = DTYPES[dtype]
@@ -51,6 +53,9 @@ class EnergyPlan:
         opt.edge_begin, opt.edge_end = self.edge_range
         opt.slice = int(bool(slice))
         opt.chunk_tiles = int(chunk_tiles)
+        opt.order_trials = int(order_trials)
+        opt.order_seed = int(order_seed)
+        opt.order_tau = float(order_tau)
         self.plan = qb.qt_plan_create(self.n_vertices, self.edges, self.p, opt)
         self.ws_bytes = qb.qt_plan_workspace_size(self.plan)
         self.stats = qb.qt_plan_stats(self.plan)

@@ -152,3 +152,16 @@ def test_autograd_function_without_gradient_plan():
     with pytest.raises(qb.QTError) as ei:
         qaoa_energy(plan, torch.tensor(g, device="cuda:0", requires_grad=True), torch.tensor(b, device="cuda:0"))
     assert ei.value.status == qb.QT_ESTATE
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_gradient_with_searched_orders_matches_parameter_shift(dtype):
+    n, p, B = 14, 3, 2
+    edges = random_regular_graph(n, 3, 6)
+    g, b = random_angles(B, p, 76)
+    plan = _grad_plan(n, edges, p, B, dtype, order_trials=20, order_seed=5)
+    e, grad = _run(plan, g, b)
+    for k in range(B):
+        ref = np.concatenate(gr.param_shift_gradient(n, edges, g[k], b[k]))
+        tol = 1e-9 if dtype == "c128" else 2e-5 * max(1.0, np.abs(ref).max())
+        np.testing.assert_allclose(grad[k], ref, atol=tol, rtol=0)

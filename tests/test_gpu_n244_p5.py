@@ -74,3 +74,18 @@ def test_sliced_edges_match_complex128_at_another_budget(sliced_run):
         zz = zz.cpu().numpy()[0, 0]
         assert abs(r["zz"][e, 0, 0] - zz[0]) < 2e-5 and abs(zz[1]) < 1e-10
         plan.close()
+
+
+def test_searched_order_plan_agrees_with_min_fill_plan(sliced_run):
+    """With the order search the graph needs far fewer sliced edges; every
+    edge's <ZZ> agrees with the min-fill sliced plan."""
+    from paper_2106_15740_gb300.energy import EnergyPlan
+    r = sliced_run
+    plan = EnergyPlan(r["n"], r["edges"], r["p"], batch=1, dtype="c64", mode="persistent", max_width=30, slice=True,
+                      order_trials=20, max_workspace=64 << 30, device="cuda:0")
+    assert (plan.widths <= 30).all() and plan.slices.sum() < r["slices"].sum()
+    gd, bd = torch.tensor(r["g"], device="cuda:0"), torch.tensor(r["b"], device="cuda:0")
+    e, zz = plan.energy(gd, bd, edge_zz=True)
+    plan.check()
+    np.testing.assert_allclose(zz.cpu().numpy()[:, 0, 0], r["zz"][:, 0, 0], atol=4e-5, rtol=0)
+    plan.close()

@@ -207,3 +207,20 @@ def test_workspace_too_small_is_an_error():
         qb.qt_plan_energy(plan.plan, gd.data_ptr(), bd.data_ptr(), out.data_ptr(), 0, 0,
                           plan.workspace.data_ptr(), plan.ws_bytes - 1, torch.cuda.current_stream().cuda_stream)
     assert ei.value.status == qb.QT_ENOMEM
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_searched_orders_match_oracle_on_n100_p3(dtype):
+    """Plans contracted in randomised greedy orders (not min-fill) give the
+    same per-edge values: all 150 edges against the oracle."""
+    from paper_2106_15740_gb300.energy import EnergyPlan
+    n, edges, p, g, b = workload("n100_p3", batch=1)
+    plan = EnergyPlan(n, edges, p, batch=1, dtype=dtype, mode="persistent", order_trials=30, order_seed=11,
+                      device="cuda:0")
+    e, zz = plan.energy(torch.tensor(g, device="cuda:0"), torch.tensor(b, device="cuda:0"), edge_zz=True)
+    plan.check()
+    zz = zz.cpu().numpy()[:, 0, :]
+    tol = 1e-10 if dtype == "c128" else 1e-5
+    for ei in range(len(edges)):
+        ref = lc.lightcone_zz(n, edges, p, g[0], b[0], ei)[0]
+        assert abs(zz[ei, 0] - ref.real) <= tol and abs(zz[ei, 1] - ref.imag) <= tol

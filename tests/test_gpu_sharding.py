@@ -54,5 +54,6 @@ def test_sharded_energy_single_rank_equals_plan():
     sh.check()
     ref = EnergyPlan(n, edges, p, batch=2, dtype="c128", mode="persistent", gradient=True, device="cuda:0")
     e0, g0 = ref.energy(gd, bd, grad=True)
-    np.testing.assert_array_equal(e.cpu().numpy(), e0.cpu().numpy())
-    np.testing.assert_array_equal(gr.cpu().numpy(), g0.cpu().numpy())
+    # the reverse sweep accumulates with atomics: equal up to rounding order
+    np.testing.assert_allclose(e.cpu().numpy(), e0.cpu().numpy(), atol=1e-12, rtol=0)
+    np.testing.assert_allclose(gr.cpu().numpy(), g0.cpu().numpy(), atol=1e-10, rtol=0)

@@ -183,3 +183,63 @@ def test_slicing_meets_the_width_budget(qtlib, name, max_width):
     assert (w <= max_width).all()
     np.testing.assert_array_equal(s > 0, w0 > max_width)
     np.testing.assert_array_equal(w[w0 <= max_width], w0[w0 <= max_width])
+
+
+def _plan_stats(name, batch=4, **kw):
+    from paper_2106_15740_gb300 import binding as qb
+    n, edges, p, g, b = workload(name)
+    opt = qb.qt_plan_options_default()
+    opt.batch = batch
+    opt.dtype = qb.QT_C64
+    for k, v in kw.items():
+        setattr(opt, k, v)
+    plan = qb.qt_plan_create(n, edges, p, opt)
+    try:
+        return qb.qt_plan_stats(plan), qb.qt_plan_edge_widths(plan, len(edges)), qb.qt_plan_edge_bytes(plan, len(edges))
+    finally:
+        qb.qt_plan_free(plan)
+
+
+def test_order_search_is_never_wider_or_costlier_than_min_fill(qtlib):
+    """The randomised greedy search keeps min-fill among its candidates and
+    only accepts orders no wider, so per edge the width never grows and the
+    planned bytes fall on the wide 100-vertex p = 4 graph."""
+    st0, w0, c0 = _plan_stats("n100_p4")
+    st1, w1, c1 = _plan_stats("n100_p4", order_trials=30, order_seed=3)
+    assert (w1 <= w0).all()
+    assert st1["alg_bytes"] < 0.6 * st0["alg_bytes"]
+    assert st1["n_edges"] == st0["n_edges"] == 150
+
+
+def test_order_search_is_deterministic_per_seed(qtlib):
+    from paper_2106_15740_gb300 import binding as qb
+    a = _plan_stats("n60_p4", order_trials=10, order_seed=7)
+    b = _plan_stats("n60_p4", order_trials=10, order_seed=7)
+    c = _plan_stats("n60_p4", order_trials=10, order_seed=8)
+    np.testing.assert_array_equal(a[2], b[2])
+    assert a[0]["alg_bytes"] == b[0]["alg_bytes"]
+    assert not np.array_equal(a[2], c[2])
+    opt = qb.qt_plan_options_default()
+    n, edges, p, g, bb = workload("n16_p1")
+    for bad in (dict(order_trials=-1), dict(order_tau=float("nan"))):
+        o = qb.qt_plan_options_default()
+        for k, v in bad.items():
+            setattr(o, k, v)
+        with pytest.raises(qb.QTError) as ei:
+            qb.qt_plan_create(n, edges, p, o)
+        assert ei.value.status == qb.QT_EINVAL
+
+
+def test_single_network_workspace_for_every_edge(qtlib):
+    """The single-network path plans one network whose graph edge id is not
+    its index in the plan."""
+    from paper_2106_15740_gb300 import binding as qb
+    n, edges, p, g, b = workload("n100_p3")
+    for e in (0, 1, 77, 149):
+        net = qb.qt_build_lightcone(n, edges, p, g[0], b[0], e)
+        try:
+            order, _ = qb.qt_order(net)
+            for dt in (qb.QT_C64, qb.QT_C128):
+                assert qb.qt_contract_workspace_size(net, order, dt) > 0
+        finally:
+            qb.qt_network_free(net)
