@@ -99,11 +99,19 @@ def _oracle_pool():
     return mp.get_context("spawn").Pool(cores), cores
 
 
-def cpu_baseline(budget_s=12.0):
-    """The oracle on host cores over a bounded sample of the workload."""
+def cpu_baseline(budget_s=12.0, gpu_zz=None):
+    """The oracle on host cores over a bounded sample of the workload.  With
+    the GPU's per-edge values gpu_zz[edge, angle set] (real parts) it also
+    returns the largest |GPU - oracle| over a seeded sample of pairs."""
     pool, cores = _oracle_pool()
+    err = None
     try:
         pool.map(_oracle_eval, _oracle_sample(cores, 1))  # warm the workers
+        if gpu_zz is not None:
+            chk = _oracle_sample(2 * cores, 7)
+            vals = pool.map(_oracle_eval, chk)
+            err = {"pairs": len(chk), "max_abs_dzz": max(abs(float(gpu_zz[e, k]) - v) for (_, e, k), v in zip(chk, vals)),
+                   "what": "complex64 bench path vs the FP64 oracle, seeded (edge, angle-set) sample"}
         n_items = cores * 6
         t0 = time.perf_counter()
         done = 0
@@ -115,7 +123,7 @@ def cpu_baseline(budget_s=12.0):
         pool.terminate()
     return {"value": done / dt, "unit": "edge_evals/s", "cores": cores, "kind": "oracle",
             "sample": f"{done} seeded (edge, angle-set) pairs of the N=100 p=4 workload, "
-                      f"FP64 naive bucket elimination, {cores} worker processes x 1 thread"}
+                      f"FP64 naive bucket elimination, {cores} worker processes x 1 thread"}, err
 
 
 def run_reference(args):
@@ -217,6 +225,19 @@ def min_fill_comparison(n, edges, p, B, g, b, dev, torch):
     return out
 
 
+def load_path_comparison(n, edges, p, B, g, b, dev, torch):
+    """The bench step with the operands staged in shared memory (bulk-copy ring)."""
+    from paper_2106_15740_gb300.energy import EnergyPlan
+    plan = EnergyPlan(n, edges, p, batch=B, dtype=WORKLOAD["dtype"], mode="persistent", device=dev,
+                      order_trials=WORKLOAD.get("order_trials", 0), load_path="staged")
+    ms = _time_calls(plan, g, b, False, 5, torch)
+    out = {"value": len(edges) * B / (ms * 1e-3), "unit": "edge_evals/s", "ms_per_step": ms,
+           "achieved_gbs": plan.stats["alg_bytes"] / (ms * 1e-3) / 1e9,
+           "what": "same plan, forward operands staged in shared memory by bulk copies (direct calls)"}
+    plan.close()
+    return out
+
+
 def gradient_and_comparator(dev, torch):
     """Energy-gradient throughput on the 60-vertex p = 4 workload (8 angles,
     one angle set, complex64 adjoint sweep), and the plain per-edge complex128
@@ -284,7 +305,8 @@ def run_ours(args):
     B = WORKLOAD["batch"]
     profile_only = ((WORKLOAD["name"], B) != ("n100_p4", 64) or "edge_range" in WORKLOAD or "lane_items" in WORKLOAD
                     or "chunk_tiles" in WORKLOAD or "gradient" in WORKLOAD or "max_width" in WORKLOAD
-                    or "profile_order" in WORKLOAD)
+                    or "profile_order" in WORKLOAD
+                    or "load_path" in WORKLOAD)
     grad = bool(WORKLOAD.get("gradient", False))
     gamma, beta = random_angles(B, p, 1002 + 7919 * rank)
     t_plan = time.perf_counter()
@@ -292,19 +314,21 @@ def run_ours(args):
                       edge_range=WORKLOAD.get("edge_range"), lane_items=WORKLOAD.get("lane_items", 0),
                       group_rows=WORKLOAD.get("group_rows", 0), chunk_tiles=WORKLOAD.get("chunk_tiles", 0),
                       gradient=grad, max_width=WORKLOAD.get("max_width", 0), slice=WORKLOAD.get("slice", False),
-                      max_workspace=WORKLOAD.get("max_workspace", 0), order_trials=WORKLOAD.get("order_trials", 0))
+                      max_workspace=WORKLOAD.get("max_workspace", 0), order_trials=WORKLOAD.get("order_trials", 0),
+                      load_path=WORKLOAD.get("load_path", "registers"))
     t_plan = time.perf_counter() - t_plan
     g = torch.tensor(gamma, device=dev)
     b = torch.tensor(beta, device=dev)
     out = torch.empty(B, dtype=torch.float64, device=dev)
     units = plan.n_edges * B
 
+    # One step = one replay of the evaluation captured as a CUDA graph.
+    step = plan.capture(grad=grad)
+    step(g, b)
     for _ in range(args.warmup):
-        plan.energy(g, b, out=out, grad=grad)
+        step.replay()
     plan.check()
 
-    qb.qt_plan_set_profiling(plan.plan, True)
-    qb.qt_plan_kernel_times(plan.plan)
     stream = torch.cuda.current_stream(dev)
     if pg:
         pg.barrier()
@@ -314,14 +338,27 @@ def run_ours(args):
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
     for _ in range(args.steps):
-        plan.energy(g, b, out=out, grad=grad)
+        step.replay()
     t1.record(stream)
     torch.cuda.synchronize(dev)
     if pg:
         pg.barrier()
-    clk = clocks.stop() if clocks else None
     plan.check()
     ms = t0.elapsed_time(t1) / args.steps
+
+    # Kernel time of the persistent launch: the same K steps as direct calls
+    # with the library's profiling events around the bucket launch (events
+    # on the launching stream), right after the graph-timed steps.
+    qb.qt_plan_set_profiling(plan.plan, True)
+    qb.qt_plan_kernel_times(plan.plan)
+    t0.record(stream)
+    for _ in range(args.steps):
+        plan.energy(g, b, out=out, grad=grad)
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop() if clocks else None
+    plan.check()
+    ms_direct = t0.elapsed_time(t1) / args.steps
     kernel_ms = qb.qt_plan_kernel_times(plan.plan)
     qb.qt_plan_set_profiling(plan.plan, False)
     if pg:
@@ -370,21 +407,30 @@ def run_ours(args):
                        "plan_host_s": round(t_plan, 3)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": _traffic(B, alg, profile_only),
-                         "kernel": "persistent_kernel<float,2,false>",
-                         "kernel_ms": kms, "alg_bytes_per_launch": alg, "peak_kind": peak_kind},
+                         "kernel": "persistent_kernel<float,2,false,false,%s>" % (
+                             "true" if WORKLOAD.get("load_path") == "staged" else "false"),
+                         "kernel_ms": kms, "kernel_ms_from": "CUDA events around the persistent launch over "
+                                                             "K direct calls after the graph-timed steps", "alg_bytes_per_launch": alg, "peak_kind": peak_kind},
             "e2e": {"value": units * world / e2e_s, "unit": "edge_evals/s",
                     "h2d_bytes_per_step": int(2 * B * p * 8), "d2h_bytes_per_step": int(B * 8)},
-            "gpu_launches": 4 * args.steps,
+            "gpu_launches": (7 if grad else 4) * args.steps,
+            "step_form": {"timed": "K replays of one CUDA graph holding the evaluation "
+                                   "(angle table, leaf factors, persistent launch, FP64 energy sum)",
+                          "ms_per_step_direct_calls": ms_direct},
             "clocks": clk,
         }
         if profile_only:
             res["profile_only"] = f"{WORKLOAD} (not the bench workload)"
         if not profile_only and WORKLOAD.get("order_trials", 0):
             res["min_fill_order"] = min_fill_comparison(n, edges, p, B, g, b, dev, torch)
+        if not profile_only:
+            res["staged_loads"] = load_path_comparison(n, edges, p, B, g, b, dev, torch)
         if not args.no_cpu_baseline:
             res.update(gradient_and_comparator(dev, torch))
             res["per_edge_c128_loop"]["speedup_of_value"] = res["value"] / res["per_edge_c128_loop"]["edge_evals_per_s"]
-            res["cpu_baseline"] = cpu_baseline()
+            _, zz = plan.energy(g, b, edge_zz=True)
+            plan.check()
+            res["cpu_baseline"], res["error_vs_oracle"] = cpu_baseline(gpu_zz=zz[:, :, 0].cpu().numpy())
         print(json.dumps(res))
     if pg:
         pg.destroy_process_group()
@@ -408,6 +454,8 @@ def main():
     ap.add_argument("--max-width", type=int, default=0, help="profiling only: width budget")
     ap.add_argument("--slice", action="store_true", help="profiling only: slice edges above the width budget")
     ap.add_argument("--max-workspace-gb", type=float, default=0, help="profiling only: workspace cap")
+    ap.add_argument("--load-path", default=None, choices=["staged", "registers"],
+                    help="profiling only: operand path of the persistent kernel")
     ap.add_argument("--order-trials", type=int, default=None,
                     help="profiling only: randomised greedy orders per edge (0: min-fill)")
     args = ap.parse_args()
@@ -429,6 +477,9 @@ def main():
     if args.order_trials is not None:
         WORKLOAD["order_trials"] = args.order_trials
         WORKLOAD["profile_order"] = True
+        args.no_cpu_baseline = True
+    if args.load_path is not None:
+        WORKLOAD["load_path"] = args.load_path
         args.no_cpu_baseline = True
     if args.max_workspace_gb:
         WORKLOAD["max_workspace"] = int(args.max_workspace_gb * (1 << 30))

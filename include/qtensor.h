@@ -155,6 +155,13 @@ typedef struct {
   int32_t order_seed;     /* seed of the randomised orders (with the edge index) */
   double order_tau;       /* temperature: the next variable is drawn with probability
                              proportional to exp(-(fill - min fill) / order_tau) (<=0: 1) */
+  int32_t load_path;      /* persistent mode: 0 (default) loads every operand into registers;
+                             1 stages the operands of forward steps in shared memory several
+                             rows ahead -- row-wide tiles (B >= 17 angle-set vectors) through
+                             a bulk-copy (TMA) ring with one mbarrier per slot, narrower tiles
+                             through a per-lane cp.async ring -- where the tile shape allows
+                             it (complex64 with B even or B = 1, complex128).  Both give
+                             bit-identical results */
 } qt_plan_options;
 
 /* Fill `opt` with defaults: batch 1, QT_C128, QT_MODE_PER_BUCKET, no gradient,
@@ -247,6 +254,22 @@ size_t qt_static_scratch_bytes(void);
  * qt_plan_inject_stall(plan, 0) restores the plan. */
 qt_status qt_plan_set_wait_limit(qt_plan* plan, int32_t polls);
 qt_status qt_plan_inject_stall(qt_plan* plan, int32_t enable);
+
+/* Queue tracing (measurement; the paper has no counterpart).  With a trace
+ * buffer set, every persistent launch of the plan writes, for each queue
+ * task t, four uint64 words at trace[4 t .. 4 t + 3]: the device clock
+ * (%globaltimer, ns) when a warp claimed the task, when the task's dependency
+ * was found complete, and when its tiles were done, then the SM index << 16 |
+ * warp index in the block.  `trace` is device memory of at least
+ * qt_plan_trace_size() bytes, owned by the caller and left set until it is
+ * replaced or cleared with NULL; QT_ESTATE for a per-bucket plan.  Each task
+ * is one entry of qt_plan_tasks(): its step and chunk (chunk < 0: a group of
+ * -chunk single-tile steps starting at that step), with the step's output
+ * rank, edge (index into the plan's edge range) and fan-in. */
+qt_status qt_plan_trace_size(const qt_plan* plan, size_t* bytes);
+qt_status qt_plan_set_trace(qt_plan* plan, void* trace, size_t bytes);
+qt_status qt_plan_tasks(const qt_plan* plan, int32_t* n_tasks, int32_t* step, int32_t* chunk,
+                        int32_t* out_rank, int32_t* edge, int32_t* n_in);
 
 void qt_plan_free(qt_plan* plan);
 

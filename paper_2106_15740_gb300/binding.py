@@ -30,7 +30,7 @@ EXPORTS = [
     "qt_plan_free", "qt_energy_workspace_size", "qt_energy", "qt_last_error",
     "qt_plan_set_profiling", "qt_plan_kernel_times", "qt_plan_energy_static",
     "qt_static_scratch_bytes", "qt_plan_set_wait_limit", "qt_plan_inject_stall", "qt_plan_edge_slices",
-    "qt_plan_edge_bytes",
+    "qt_plan_edge_bytes", "qt_plan_trace_size", "qt_plan_set_trace", "qt_plan_tasks",
 ]
 
 
@@ -50,7 +50,7 @@ class qt_plan_options(C.Structure):
                 ("max_workspace", C.c_int64), ("group_rows", C.c_int32), ("edge_begin", C.c_int32),
                 ("edge_end", C.c_int32), ("slice", C.c_int32),
                 ("chunk_tiles", C.c_int32), ("order_trials", C.c_int32), ("order_seed", C.c_int32),
-                ("order_tau", C.c_double)]
+                ("order_tau", C.c_double), ("load_path", C.c_int32)]
 
 
 _lib = None
@@ -88,6 +88,9 @@ def lib():
             "qt_plan_energy_static": [vp, vp, vp, vp, vp, vp],
             "qt_plan_set_wait_limit": [vp, i32],
             "qt_plan_inject_stall": [vp, i32],
+            "qt_plan_trace_size": [vp, C.POINTER(sz)],
+            "qt_plan_set_trace": [vp, vp, sz],
+            "qt_plan_tasks": [vp, pi32, pi32, pi32, pi32, pi32, pi32],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -124,6 +127,10 @@ def _dptr(a):
 
 def _as_pd(a):
     return a.ctypes.data_as(C.POINTER(C.c_double)) if a is not None else None
+
+
+def _as_pi32(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int32)) if a is not None else None
 
 
 # ------------------------------------------------------------------ network
@@ -270,6 +277,25 @@ def qt_plan_set_wait_limit(plan, polls):
 
 def qt_plan_inject_stall(plan, enable):
     _check(lib().qt_plan_inject_stall(plan, int(bool(enable))))
+
+
+def qt_plan_trace_size(plan):
+    n = C.c_size_t()
+    _check(lib().qt_plan_trace_size(plan, C.byref(n)))
+    return n.value
+
+
+def qt_plan_set_trace(plan, trace_ptr, nbytes):
+    _check(lib().qt_plan_set_trace(plan, trace_ptr or None, int(nbytes)))
+
+
+def qt_plan_tasks(plan):
+    """Queue tasks as a dict of int32 arrays: step, chunk, out_rank, edge, n_in."""
+    n = C.c_int32()
+    _check(lib().qt_plan_tasks(plan, C.byref(n), None, None, None, None, None))
+    cols = {k: np.empty(n.value, dtype=np.int32) for k in ("step", "chunk", "out_rank", "edge", "n_in")}
+    _check(lib().qt_plan_tasks(plan, C.byref(n), *(_as_pi32(cols[k]) for k in ("step", "chunk", "out_rank", "edge", "n_in"))))
+    return cols
 
 
 def qt_plan_free(plan):

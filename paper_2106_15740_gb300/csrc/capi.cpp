@@ -250,6 +250,7 @@ void qt_plan_options_default(qt_plan_options* opt) {
   opt->order_trials = 0;
   opt->order_seed = 0;
   opt->order_tau = 1.0;
+  opt->load_path = 0;
 }
 
 qt_status qt_plan_create(const qt_graph* g, int32_t p, const qt_plan_options* opt, qt_plan** out) {
@@ -267,6 +268,7 @@ qt_status qt_plan_create(const qt_graph* g, int32_t p, const qt_plan_options* op
   if (o.lane_items <= 0) o.lane_items = o.batch >= 16 ? 32 : 16;
   if (o.order_trials < 0 || o.order_trials > 100000) return fail(QT_EINVAL, "order_trials must be in [0, 100000]");
   if (!(o.order_tau >= 0.0) || !std::isfinite(o.order_tau)) return fail(QT_EINVAL, "order_tau must be finite and >= 0");
+  if (o.load_path != 0 && o.load_path != 1) return fail(QT_EINVAL, "load_path must be 0 or 1");
   qt_plan* h = new (std::nothrow) qt_plan;
   if (!h) return fail(QT_ENOMEM, "host allocation failed");
   qt_status st = make_graph(g, &h->P.G);
@@ -388,6 +390,52 @@ qt_status qt_plan_set_profiling(qt_plan* plan, int32_t on) {
 qt_status qt_plan_kernel_times(qt_plan* plan, float* ms, int32_t cap, int32_t* n) {
   if (!plan || (!ms && cap > 0)) return fail(QT_EINVAL, "plan or ms is NULL");
   return plan_kernel_times(&plan->P, ms, cap, n);
+}
+
+qt_status qt_plan_trace_size(const qt_plan* plan, size_t* bytes) {
+  if (!plan || !bytes) return fail(QT_EINVAL, "NULL argument");
+  *bytes = sizeof(unsigned long long) * 4 * plan->P.tasks.size();
+  return QT_OK;
+}
+
+qt_status qt_plan_set_trace(qt_plan* plan, void* trace, size_t bytes) {
+  if (!plan) return fail(QT_EINVAL, "plan is NULL");
+  Plan& P = plan->P;
+  if (!trace) {
+    P.trace = nullptr;
+    return QT_OK;
+  }
+  if (P.opt.mode != QT_MODE_PERSISTENT) return fail(QT_ESTATE, "tracing needs a persistent plan");
+  if (((uintptr_t)trace & 7u) != 0) return fail(QT_EINVAL, "trace buffer is not 8-byte aligned");
+  if (bytes < sizeof(unsigned long long) * 4 * P.tasks.size())
+    return fail(QT_ENOMEM, "trace buffer holds " + std::to_string(bytes) + " bytes, the queue needs " +
+                               std::to_string(sizeof(unsigned long long) * 4 * P.tasks.size()));
+  P.trace = (unsigned long long*)trace;
+  return QT_OK;
+}
+
+qt_status qt_plan_tasks(const qt_plan* plan, int32_t* n_tasks, int32_t* step, int32_t* chunk, int32_t* out_rank,
+                        int32_t* edge, int32_t* n_in) {
+  if (!plan || !n_tasks) return fail(QT_EINVAL, "NULL argument");
+  const Plan& P = plan->P;
+  *n_tasks = (int32_t)P.tasks.size();
+  const int32_t n_net = (int32_t)P.edge_first.size() - 1;
+  std::vector<int32_t> step_edge(P.buckets.size(), 0);
+  for (int32_t k = 0; k < n_net; ++k) {
+    // network k belongs to the planned edge whose network range holds it
+    int32_t e = 0;
+    while (e + 1 < (int32_t)P.net_first.size() - 1 && P.net_first[e + 1] <= k) ++e;
+    for (int32_t b = P.edge_first[k]; b < P.edge_first[k + 1]; ++b) step_edge[b] = e;
+  }
+  for (size_t t = 0; t < P.tasks.size(); ++t) {
+    const DevTask& T = P.tasks[t];
+    if (step) step[t] = T.bucket;
+    if (chunk) chunk[t] = T.chunk;
+    if (out_rank) out_rank[t] = P.buckets[T.bucket].out_rank;
+    if (edge) edge[t] = step_edge[T.bucket];
+    if (n_in) n_in[t] = P.buckets[T.bucket].n_in;
+  }
+  return QT_OK;
 }
 
 qt_status qt_plan_set_wait_limit(qt_plan* plan, int32_t polls) {

@@ -480,6 +480,14 @@ qt_status compile_plan(Plan* P) {
     }
   }
 
+  // The bulk-copy ring reads each operand row pair with one 16-byte-aligned
+  // copy: every forward input must start on a 16-byte boundary.
+  P->bulk_ok = true;
+  for (const DevBucket& d : P->buckets)
+    if (d.kind == kStepFwd)
+      for (int32_t i = 0; i < d.n_in; ++i)
+        if ((d.in[i].off * (int64_t)es) % 16 != 0) P->bulk_ok = false;
+
   // Workspace layout.
   WsLayout& L = P->ws;
   const int32_t p = P->p;
@@ -600,13 +608,13 @@ qt_status run_plan(Plan* P, const double* gamma, const double* beta, double* ene
   }
   if (P->opt.mode == QT_MODE_PERSISTENT) {
     int per_sm = 0;
-    QT_CUDA(persistent_occupancy(dtype, P->opt.gradient != 0, B, &per_sm));
+    QT_CUDA(persistent_occupancy(dtype, P->opt.gradient != 0, P->opt.load_path == 1, B, &per_sm));
     int n_sm = 0;
     QT_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
     const int32_t grid = std::max(1, per_sm) * n_sm;
-    QT_CUDA(launch_persistent(dtype, P->opt.gradient != 0, dbk, (const DevTask*)(base + L.tasks), (int32_t)P->tasks.size(),
+    QT_CUDA(launch_persistent(dtype, P->opt.gradient != 0, P->opt.load_path == 1, dbk, (const DevTask*)(base + L.tasks), (int32_t)P->tasks.size(),
                               (DevCtrl*)(base + L.ctrl), (int32_t*)(base + L.done), B, P->opt.lane_items, data,
-                              P->data_elems, grid, P->spin_limit, s));
+                              P->data_elems, grid, P->spin_limit, P->bulk_ok, P->trace, s));
   } else {
     int n_sm = 0;
     QT_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));

@@ -52,6 +52,12 @@ struct Plan {
   double alg_bytes = 0.0, flops = 0.0;
   std::vector<double> edge_bytes;          // per planned graph edge: algorithmic bytes of its networks
 
+  // every forward-step input starts on a 16-byte boundary (bulk-copy ring usable)
+  bool bulk_ok = false;
+
+  // queue trace buffer (device, 4 x uint64 per task) or null
+  unsigned long long* trace = nullptr;
+
   // failure-detection hook: step whose uploaded tile count is made unreachable
   int32_t stall_step = -1;
 

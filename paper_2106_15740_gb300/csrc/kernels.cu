@@ -112,6 +112,17 @@ __global__ void __launch_bounds__(256, 4) bucket_kernel(const DevBucket d, Real*
   }
 }
 
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long v;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(v));
+  return v;
+}
+__device__ __forceinline__ uint32_t smid() {
+  uint32_t v;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(v));
+  return v;
+}
+
 __device__ __forceinline__ int32_t ld_acquire(const int32_t* p) {
   int32_t v;
   asm volatile("ld.acquire.gpu.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -130,14 +141,29 @@ __device__ __forceinline__ int32_t ld_acquire(const int32_t* p) {
 // records QT_ETIMEOUT in the control word and no warp takes a task after that.
 // Consecutive tiles of one bucket on a warp reuse its record and skip the
 // wait (done counters only grow).
-template <class Real, int VB, bool PAIR, bool GRAD>
-__global__ void __launch_bounds__(256, 4) persistent_kernel(const DevBucket* __restrict__ buckets,
+//
+// STAGED: forward steps move their operands through a per-warp cp.async ring
+// in dynamic shared memory (kRingBytesPerWarp per warp, see kernels.cuh);
+// otherwise every load goes to registers.
+template <class Real, int VB, bool PAIR, bool GRAD, bool STAGED>
+__global__ void __launch_bounds__(256, STAGED ? 2 : 4) persistent_kernel(const DevBucket* __restrict__ buckets,
                                                             const DevTask* __restrict__ tasks, int32_t n_tasks,
                                                             DevCtrl* ctrl, int32_t* done, Real* __restrict__ data,
-                                                            const TileGeom g, int32_t spin_limit) {
+                                                            const TileGeom g, int32_t spin_limit,
+                                                            unsigned long long* __restrict__ trace) {
   __shared__ WarpTile tiles[8];
+  extern __shared__ uint4 ring_all[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   WarpTile* w = &tiles[wid];
+  uint4* ring = STAGED ? ring_all + (size_t)wid * kRingUnits * 32 : nullptr;
+  uint32_t phase = 0;  // bulk-copy ring: parity each slot waits for next
+  if (STAGED) {
+    if (lane == 0) {
+      for (int k = 0; k < kBulkSlots; ++k) mbar_init(&w->mbar[k], 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+  }
   // Lane 0 makes every scheduling decision; the warp acts on broadcasts.
   int32_t t = 0, cached = -1;  // cached: bucket whose record and lane parts are in *w
   if (lane == 0) t = atomicAdd(&ctrl->head, 1);
@@ -145,6 +171,7 @@ __global__ void __launch_bounds__(256, 4) persistent_kernel(const DevBucket* __r
   while (t < n_tasks) {
     int32_t t_next = n_tasks, failed = 0;
     const DevTask task = tasks[t];
+    if (trace != nullptr && lane == 0) w->trace_t[0] = globaltimer();
     if (lane == 0) {
       if (*((volatile int32_t*)&ctrl->status) == 0) t_next = atomicAdd(&ctrl->head, 1);
       if (task.bucket != cached) {
@@ -167,6 +194,7 @@ __global__ void __launch_bounds__(256, 4) persistent_kernel(const DevBucket* __r
     failed = __shfl_sync(0xffffffffu, failed, 0);
     t_next = __shfl_sync(0xffffffffu, t_next, 0);
     if (failed) break;
+    if (trace != nullptr && lane == 0) w->trace_t[1] = globaltimer();
     const int32_t n_group = task.chunk < 0 ? -task.chunk : 1;
     for (int32_t k = 0; k < n_group; ++k) {
       const int32_t b = task.bucket + k;
@@ -196,13 +224,20 @@ __global__ void __launch_bounds__(256, 4) persistent_kernel(const DevBucket* __r
         const int64_t r0 = tt * g.R;
         if (r0 >= n_rows) break;
         const int64_t r1 = r0 + g.R < n_rows ? r0 + g.R : n_rows;
-        warp_tile<Real, VB, PAIR, true, GRAD>(w, data, g, r0, r1, lane, ctrl, b);
+        warp_tile<Real, VB, PAIR, true, GRAD>(w, data, g, r0, r1, lane, ctrl, b, ring, &phase);
         __syncwarp();  // the next tile or step reuses the warp's tables and reads what this one wrote
       }
     }
     __threadfence();
     __syncwarp();
     if (lane == 0) atomicAdd(done + task.bucket + n_group - 1, 1);
+    if (trace != nullptr && lane == 0) {
+      unsigned long long* r = trace + 4 * (int64_t)t;
+      r[0] = w->trace_t[0];
+      r[1] = w->trace_t[1];
+      r[2] = globaltimer();
+      r[3] = ((unsigned long long)smid() << 16) | (unsigned long long)wid;
+    }
     t = t_next;
   }
 }
@@ -380,6 +415,8 @@ TileGeom tile_geom(int dtype, int32_t B, int32_t lane_items) {
   while (P * 2 * g.VC <= cap) P *= 2;
   g.P = P;
   g.R = P * g.RP;
+  g.bulk = 0;
+  g.wait_limit = 1 << 22;
   g.data_elems = 0;
   return g;
 }
@@ -409,57 +446,64 @@ cudaError_t launch_bucket(int dtype, const DevBucket& d, int32_t B, int32_t lane
   return cudaGetLastError();
 }
 
-template <bool GRAD>
-static cudaError_t launch_persistent_t(int dtype, const DevBucket* buckets, const DevTask* tasks, int32_t n_tasks,
-                                       DevCtrl* ctrl, int32_t* done, void* data, const TileGeom& g, int32_t B,
-                                       int32_t grid, int32_t spin_limit, cudaStream_t s) {
-  const int vb = vector_width(dtype, B);
-  const bool pair = (B == 1);
-  if (dtype == QT_C64) {
-    if (pair)
-      dev::persistent_kernel<float, 1, true, GRAD><<<grid, 256, 0, s>>>(buckets, tasks, n_tasks, ctrl, done,
-                                                                        (float*)data, g, spin_limit);
-    else if (vb == 2)
-      dev::persistent_kernel<float, 2, false, GRAD><<<grid, 256, 0, s>>>(buckets, tasks, n_tasks, ctrl, done,
-                                                                         (float*)data, g, spin_limit);
-    else
-      dev::persistent_kernel<float, 1, false, GRAD><<<grid, 256, 0, s>>>(buckets, tasks, n_tasks, ctrl, done,
-                                                                         (float*)data, g, spin_limit);
-  } else {
-    if (pair)
-      dev::persistent_kernel<double, 1, true, GRAD><<<grid, 256, 0, s>>>(buckets, tasks, n_tasks, ctrl, done,
-                                                                         (double*)data, g, spin_limit);
-    else
-      dev::persistent_kernel<double, 1, false, GRAD><<<grid, 256, 0, s>>>(buckets, tasks, n_tasks, ctrl, done,
-                                                                          (double*)data, g, spin_limit);
-  }
-  return cudaGetLastError();
+// The staged form exists for every tile shape whose operand pieces are 16
+// bytes (complex64 with B even or B = 1, complex128); complex64 with an odd
+// B >= 3 keeps the register path.
+bool staged_supported(int dtype, int32_t B) { return !(dtype == QT_C64 && B > 1 && B % 2 == 1); }
+
+template <class Real, int VB, bool PAIR, bool GRAD, bool ST>
+static const void* pk_fn() {
+  return (const void*)dev::persistent_kernel<Real, VB, PAIR, GRAD, ST>;
 }
 
-cudaError_t launch_persistent(int dtype, bool grad, const DevBucket* buckets, const DevTask* tasks,
-                              int32_t n_tasks, DevCtrl* ctrl, int32_t* done, int32_t B, int32_t lane_items,
-                              void* data, int64_t data_elems, int32_t grid, int32_t spin_limit, cudaStream_t s) {
-  TileGeom g = tile_geom(dtype, B, lane_items);
-  g.data_elems = data_elems;
-  return grad ? launch_persistent_t<true>(dtype, buckets, tasks, n_tasks, ctrl, done, data, g, B, grid, spin_limit, s)
-              : launch_persistent_t<false>(dtype, buckets, tasks, n_tasks, ctrl, done, data, g, B, grid, spin_limit, s);
-}
-
-template <bool GRAD>
-static const void* persistent_fn(int dtype, int32_t B) {
+template <bool GRAD, bool ST>
+static const void* persistent_fn_t(int dtype, int32_t B) {
   const int vb = vector_width(dtype, B);
   const bool pair = (B == 1);
   if (dtype == QT_C64)
-    return pair ? (const void*)dev::persistent_kernel<float, 1, true, GRAD>
-                : (vb == 2 ? (const void*)dev::persistent_kernel<float, 2, false, GRAD>
-                           : (const void*)dev::persistent_kernel<float, 1, false, GRAD>);
-  return pair ? (const void*)dev::persistent_kernel<double, 1, true, GRAD>
-              : (const void*)dev::persistent_kernel<double, 1, false, GRAD>;
+    return pair ? pk_fn<float, 1, true, GRAD, ST>()
+                : (vb == 2 ? pk_fn<float, 2, false, GRAD, ST>() : pk_fn<float, 1, false, GRAD, false>());
+  return pair ? pk_fn<double, 1, true, GRAD, ST>() : pk_fn<double, 1, false, GRAD, ST>();
 }
 
-cudaError_t persistent_occupancy(int dtype, bool grad, int32_t B, int* blocks_per_sm) {
-  const void* fn = grad ? persistent_fn<true>(dtype, B) : persistent_fn<false>(dtype, B);
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, 256, 0);
+static const void* persistent_fn(int dtype, bool grad, bool staged, int32_t B) {
+  if (staged && !staged_supported(dtype, B)) staged = false;
+  if (grad) return staged ? persistent_fn_t<true, true>(dtype, B) : persistent_fn_t<true, false>(dtype, B);
+  return staged ? persistent_fn_t<false, true>(dtype, B) : persistent_fn_t<false, false>(dtype, B);
+}
+
+// Dynamic shared memory of a persistent launch (the staged ring of 8 warps).
+static int persistent_smem(int dtype, bool staged, int32_t B) {
+  return staged && staged_supported(dtype, B) ? 8 * dev::kRingBytesPerWarp : 0;
+}
+
+cudaError_t launch_persistent(int dtype, bool grad, bool staged, const DevBucket* buckets, const DevTask* tasks,
+                              int32_t n_tasks, DevCtrl* ctrl, int32_t* done, int32_t B, int32_t lane_items,
+                              void* data, int64_t data_elems, int32_t grid, int32_t spin_limit,
+                              bool bulk, unsigned long long* trace, cudaStream_t s) {
+  TileGeom g = tile_geom(dtype, B, lane_items);
+  g.data_elems = data_elems;
+  g.bulk = bulk ? 1 : 0;
+  g.wait_limit = 1 << 22;
+  const void* fn = persistent_fn(dtype, grad, staged, B);
+  const int smem = persistent_smem(dtype, staged, B);
+  if (smem > 0) {
+    const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+  }
+  void* args[] = {(void*)&buckets, (void*)&tasks, (void*)&n_tasks, (void*)&ctrl, (void*)&done, (void*)&data,
+                  (void*)&g, (void*)&spin_limit, (void*)&trace};
+  return cudaLaunchKernel(fn, dim3(grid), dim3(256), args, (size_t)smem, s);
+}
+
+cudaError_t persistent_occupancy(int dtype, bool grad, bool staged, int32_t B, int* blocks_per_sm) {
+  const void* fn = persistent_fn(dtype, grad, staged, B);
+  const int smem = persistent_smem(dtype, staged, B);
+  if (smem > 0) {
+    const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, 256, (size_t)smem);
 }
 
 cudaError_t launch_energy(int dtype, const void* data, const int64_t* scal_off, const int32_t* scal_begin,

@@ -167,12 +167,16 @@ __device__ __forceinline__ bool qt_in_range(DevCtrl* ctrl, int64_t lo, int64_t s
 
 // Per-warp shared state of one tile: the bucket record and the pass table
 // tab[i][p] = pext(r0 + p * RP, mask_i).
+constexpr int kBulkSlots = 8;  // mbarriers (ring slots) of a warp's bulk-copy ring
+
 struct WarpTile {
   DevBucket d;
   uint32_t tab[kDevMaxIn][kLaneItems];
   uint32_t lpart[kDevMaxIn][32];  // pext(i_lane, mask) per input and lane
   float redf[32][4];              // per-lane partial sums of a reduction step (complex64)
   double redd[32][2];             // the same for complex128
+  unsigned long long mbar[kBulkSlots];  // bulk-copy ring: one transaction barrier per slot
+  unsigned long long trace_t[2];        // queue trace: claim and ready clock of the current task
 };
 
 // Copy a bucket record into the warp's shared slot with typed member
@@ -375,6 +379,280 @@ __device__ __forceinline__ void tile_items(WarpTile* w, Real* __restrict__ data,
       if (QT_RANGE_OK(so, VB, 2, -1)) stv<Real, VB>(data, so, o);
     }
   }
+}
+
+// ------------------------------------------------ shared-memory staged path --
+//
+// The register path above keeps at most 2 items' loads of one input in flight
+// per lane and waits on each input in turn.  The staged path moves the
+// operand rows through a per-warp ring in shared memory with cp.async: every
+// lane copies the 16-byte pieces of all inputs of its item q + S - 1 while it
+// multiplies item q, so S items' loads (all inputs) are in flight per lane
+// without holding registers.  Each lane reads back only what it copied, so
+// the ring needs no barrier: cp.async.wait_group makes a lane's own copies
+// visible to it.  Slot q % S is refilled for item q + S only after item q's
+// products were taken, one loop iteration earlier.
+//
+// Ring: kRingUnits 16-byte units per lane, unit j of lane l at ring[j * 32 + l]
+// (a warp's access to one unit is 512 contiguous bytes, conflict-free).
+// An item of a bucket with n_in inputs uses n_in * UPI units (UPI = 16-byte
+// pieces per input and item: the x = 0 and x = 1 rows of a [2^r][B] tensor
+// for B >= 2, or the adjacent pair of a B = 1 tensor); S = kRingUnits / units
+// rounded down to a power of two, at least 2.
+constexpr int kRingUnits = 16;
+constexpr int kRingBytesPerWarp = kRingUnits * 32 * 16;
+
+__device__ __forceinline__ void cp_async16(uint4* smem, const void* gmem, bool via_l1) {
+  const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+  if (via_l1)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// 16-byte pieces per input and item (0: this tile shape has no staged form).
+template <class Real, int VB, bool PAIR> struct StageUnits { static constexpr int value = 0; };
+template <> struct StageUnits<float, 2, false> { static constexpr int value = 2; };   // two 16-B rows
+template <> struct StageUnits<double, 1, false> { static constexpr int value = 2; };  // two double2 rows
+template <> struct StageUnits<float, 1, true> { static constexpr int value = 1; };    // one float4 pair
+template <> struct StageUnits<double, 1, true> { static constexpr int value = 2; };   // two double2
+
+template <class Real, int VB, bool PAIR, int S>
+__device__ __forceinline__ void stage_issue(const WarpTile* w, uint4* ring, const Real* __restrict__ data,
+                                            const TileGeom& g, int q, int Q, int64_t r0, int64_t r1, int lane,
+                                            int rip, int v0, bool lane_on, DevCtrl* ctrl, int dbg_bucket) {
+  (void)ctrl;
+  (void)dbg_bucket;
+  constexpr int UPI = StageUnits<Real, VB, PAIR>::value;
+  constexpr int SLOT = kRingUnits / S;
+  const DevBucket& d = w->d;
+  const ItemSet<1> it = make_items<1>(g, q, Q, r0, r1, rip, v0, lane_on);
+  if (it.ok[0]) {
+    uint4* slot = ring + (q % S) * SLOT * 32 + lane;
+    for (int i = 0; i < d.n_in; ++i) {
+      const uint32_t k = w->tab[i][it.pp[0]] + w->lpart[i][lane];
+      const bool leaf = d.in[i].flags & kInLeaf;
+      // element index of the x = 0 piece; the x = 1 piece is B elements on
+      // (rows 2k, 2k + 1 of a [2^r][B] tensor) or, for a B = 1 pair, adjacent
+      const int64_t e0 = PAIR ? d.in[i].off + 2 * (int64_t)k
+                              : d.in[i].off + (int64_t)(2 * k) * g.B + (int64_t)(it.vv[0] * VB);
+      if (QT_RANGE_OK(e0, PAIR ? 2 : g.B + VB, 1, i)) {
+        cp_async16(slot + (i * UPI) * 32, data + 2 * e0, leaf);
+        if (UPI == 2) cp_async16(slot + (i * UPI + 1) * 32, data + 2 * (PAIR ? e0 + 1 : e0 + g.B), leaf);
+      }
+    }
+  }
+  cp_async_commit();
+}
+
+// Forward items of one tile through the ring, S items ahead.
+template <class Real, int VB, bool PAIR, int S>
+__device__ __forceinline__ void tile_items_staged(WarpTile* w, uint4* ring, Real* __restrict__ data,
+                                                  const TileGeom& g, int64_t r0, int64_t r1, int lane, int rip,
+                                                  int v0, bool lane_on, DevCtrl* ctrl, int dbg_bucket) {
+  constexpr int UPI = StageUnits<Real, VB, PAIR>::value;
+  constexpr int SLOT = kRingUnits / S;
+  using C = typename Cx<Real>::T;
+  const DevBucket& d = w->d;
+  const int n_in = d.n_in;
+  const int Q = g.P * g.VC;
+#pragma unroll
+  for (int q = 0; q < S - 1; ++q) {
+    if (q < Q)
+      stage_issue<Real, VB, PAIR, S>(w, ring, data, g, q, Q, r0, r1, lane, rip, v0, lane_on, ctrl, dbg_bucket);
+    else
+      cp_async_commit();
+  }
+  for (int q = 0; q < Q; ++q) {
+    if (q + S - 1 < Q)
+      stage_issue<Real, VB, PAIR, S>(w, ring, data, g, q + S - 1, Q, r0, r1, lane, rip, v0, lane_on, ctrl,
+                                     dbg_bucket);
+    else
+      cp_async_commit();
+    cp_async_wait<S - 1>();  // this lane's copies of item q have landed
+    const ItemSet<1> it = make_items<1>(g, q, Q, r0, r1, rip, v0, lane_on);
+    if (!it.ok[0]) continue;
+    const uint4* slot = ring + (q % S) * SLOT * 32 + lane;
+    Pack<Real, VB> p0, p1;
+    for (int i = 0; i < n_in; ++i) {
+      Pack<Real, VB> a0, a1;
+      if (PAIR) {
+        const uint4 u0 = slot[(i * UPI) * 32];
+        if (UPI == 1) {  // complex64 pair: x = 0 in .x/.y, x = 1 in .z/.w
+          a0.c[0] = *reinterpret_cast<const C*>(&u0.x);
+          a1.c[0] = *reinterpret_cast<const C*>(&u0.z);
+        } else {
+          const uint4 u1 = slot[(i * UPI + 1) * 32];
+          a0.c[0] = *reinterpret_cast<const C*>(&u0);
+          a1.c[0] = *reinterpret_cast<const C*>(&u1);
+        }
+      } else {
+        const uint4 u0 = slot[(i * UPI) * 32];
+        const uint4 u1 = slot[(i * UPI + 1) * 32];
+        a0 = *reinterpret_cast<const Pack<Real, VB>*>(&u0);
+        a1 = *reinterpret_cast<const Pack<Real, VB>*>(&u1);
+      }
+      if (i == 0) {
+        p0 = a0;
+        p1 = a1;
+      } else {
+        pmul<Real, VB>(p0, a0);
+        pmul<Real, VB>(p1, a1);
+      }
+    }
+    Pack<Real, VB> o;
+#pragma unroll
+    for (int v = 0; v < VB; ++v) o.c[v] = cadd<Real>(p0.c[v], p1.c[v]);
+    const int64_t so = PAIR ? d.out_off + (int64_t)it.y[0]
+                            : d.out_off + (int64_t)it.y[0] * g.B + (int64_t)(it.vv[0] * VB);
+    if (QT_RANGE_OK(so, VB, 2, -1)) stv<Real, VB>(data, so, o);
+  }
+  cp_async_wait<0>();  // nothing of this tile stays in flight into the next one
+}
+
+// ------------------------------------------------ wide-row bulk-copy path --
+//
+// For row-wide tiles (RP = 1: one output row per pass, B >= 17 vectors, so
+// every lane of the warp works on the same row y) all operand addresses of a
+// row are warp-uniform: input i needs rows 2k and 2k + 1 (x = 0, 1) of its
+// [2^r][B] array, k = tab[i][y - r0], which are 2 * B contiguous complex
+// numbers.  Lane 0 brings that pair into a ring slot of shared memory with
+// one cp.async.bulk (the TMA engine's 1-D copy) per input, completing on the
+// slot's mbarrier; all lanes wait on the barrier's phase, read their vectors
+// of angle sets from shared memory, multiply, add over x and store the
+// output row.  A slot holds one row's operands (n_in * 2 * B * sizeof(cx));
+// with S slots, S - 1 rows are in flight while one is multiplied.  A slot is
+// refilled only after every lane has read it into registers (__syncwarp).
+// The ring's phases persist across tiles in `phase` (bit s = parity that
+// slot s waits for next); every fill issued in a tile is consumed in it.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* mb, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mb)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* mb, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mb)), "r"(bytes) : "memory");
+}
+// One bounded wait for the phase with parity `parity` of *mb; false if it
+// did not complete within `limit` probes.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* mb, uint32_t parity, int32_t limit) {
+  const uint32_t a = smem_u32(mb);
+  for (int32_t it = 0; it < limit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Global -> shared bulk copy of `bytes` (multiple of 16; both addresses
+// 16-byte aligned) completing `bytes` transactions on *mb.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, unsigned long long* mb) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(mb))
+      : "memory");
+}
+
+// Wide-row forward tile through the bulk-copy ring (kRingBytesPerWarp bytes
+// of this warp at `ring`); returns false (nothing done) when fewer than two
+// slots of the bucket's size fit.
+template <class Real, int VB>
+__device__ __forceinline__ bool tile_rows_bulk(WarpTile* w, unsigned char* ring, uint32_t& phase,
+                                               Real* __restrict__ data, const TileGeom& g, int64_t r0, int64_t r1,
+                                               int lane, DevCtrl* ctrl, int32_t wait_limit) {
+  using C = typename Cx<Real>::T;
+  const DevBucket& d = w->d;
+  const int n_in = d.n_in;
+  const uint32_t rowb = (uint32_t)g.B * (uint32_t)sizeof(C);  // bytes of one row of B complex numbers
+  const uint32_t pairb = 2u * rowb;
+  const uint32_t slotb = (uint32_t)n_in * pairb;
+  int S = (int)((uint32_t)kRingBytesPerWarp / slotb);
+  if (S > kBulkSlots) S = kBulkSlots;
+  if (S < 2) return false;
+  const int nrows = (int)(r1 - r0);
+  if (lane == 0) {
+    fence_proxy_async_smem();  // the previous tile's reads of the ring come first
+    for (int q = 0; q < S && q < nrows; ++q) {
+      unsigned long long* mb = &w->mbar[q];
+      unsigned char* dst = ring + (uint32_t)q * slotb;
+      mbar_expect_tx(mb, slotb);
+      for (int i = 0; i < n_in; ++i)
+        bulk_g2s(dst + (uint32_t)i * pairb, data + 2 * (d.in[i].off + (int64_t)(2 * w->tab[i][q]) * g.B), pairb, mb);
+    }
+  }
+  for (int q = 0; q < nrows; ++q) {
+    const int s = q % S;
+    if (!mbar_wait(&w->mbar[s], (phase >> s) & 1u, wait_limit)) {
+      if (lane == 0) atomicCAS(&ctrl->status, 0, (int32_t)QT_ETIMEOUT);
+    }
+    phase ^= 1u << s;
+    const unsigned char* src = ring + (uint32_t)s * slotb;
+    const int64_t y = r0 + q;
+    for (int vc = 0; vc < g.VC; ++vc) {
+      const int vv = lane + 32 * vc;
+      if (vv >= g.Bv) continue;
+      const uint32_t lo = (uint32_t)vv * VB * (uint32_t)sizeof(C);
+      Pack<Real, VB> p0, p1;
+      for (int i = 0; i < n_in; ++i) {
+        const unsigned char* base = src + (uint32_t)i * pairb + lo;
+        const Pack<Real, VB> a0 = *reinterpret_cast<const Pack<Real, VB>*>(base);
+        const Pack<Real, VB> a1 = *reinterpret_cast<const Pack<Real, VB>*>(base + rowb);
+        if (i == 0) {
+          p0 = a0;
+          p1 = a1;
+        } else {
+          pmul<Real, VB>(p0, a0);
+          pmul<Real, VB>(p1, a1);
+        }
+      }
+      Pack<Real, VB> o;
+#pragma unroll
+      for (int v = 0; v < VB; ++v) o.c[v] = cadd<Real>(p0.c[v], p1.c[v]);
+      stv<Real, VB>(data, d.out_off + y * g.B + (int64_t)vv * VB, o);
+    }
+    __syncwarp();  // every lane has read slot s
+    if (lane == 0 && q + S < nrows) {
+      unsigned long long* mb = &w->mbar[s];
+      unsigned char* dst = ring + (uint32_t)s * slotb;
+      mbar_expect_tx(mb, slotb);
+      for (int i = 0; i < n_in; ++i)
+        bulk_g2s(dst + (uint32_t)i * pairb,
+                 data + 2 * (d.in[i].off + (int64_t)(2 * w->tab[i][q + S]) * g.B), pairb, mb);
+    }
+  }
+  return true;
+}
+
+// Staged forward tile if the tile shape and the bucket's fan-in allow it;
+// returns false (nothing done) otherwise.
+template <class Real, int VB, bool PAIR>
+__device__ __forceinline__ bool try_tile_staged(WarpTile* w, uint4* ring, Real* __restrict__ data,
+                                                const TileGeom& g, int64_t r0, int64_t r1, int lane, int rip,
+                                                int v0, bool lane_on, DevCtrl* ctrl, int dbg_bucket) {
+  constexpr int UPI = StageUnits<Real, VB, PAIR>::value;
+  if (UPI == 0 || ring == nullptr) return false;
+  const int units = w->d.n_in * (UPI > 0 ? UPI : 1);
+  if (units <= kRingUnits / 8)
+    tile_items_staged<Real, VB, PAIR, 8>(w, ring, data, g, r0, r1, lane, rip, v0, lane_on, ctrl, dbg_bucket);
+  else if (units <= kRingUnits / 4)
+    tile_items_staged<Real, VB, PAIR, 4>(w, ring, data, g, r0, r1, lane, rip, v0, lane_on, ctrl, dbg_bucket);
+  else if (units <= kRingUnits / 2)
+    tile_items_staged<Real, VB, PAIR, 2>(w, ring, data, g, r0, r1, lane, rip, v0, lane_on, ctrl, dbg_bucket);
+  else
+    return false;
+  return true;
 }
 
 template <class Real>
@@ -594,7 +872,8 @@ __device__ __forceinline__ void tile_adjred(WarpTile* w, Real* __restrict__ data
 // w->lpart.  Per item an input row is one table read plus one add.
 template <class Real, int VB, bool PAIR, bool CG, bool GRAD = false>
 __device__ __forceinline__ void warp_tile(WarpTile* w, Real* __restrict__ data, const TileGeom& g, int64_t r0,
-                                          int64_t r1, int lane, DevCtrl* ctrl = nullptr, int dbg_bucket = -1) {
+                                          int64_t r1, int lane, DevCtrl* ctrl = nullptr, int dbg_bucket = -1,
+                                          uint4* ring = nullptr, uint32_t* phase = nullptr) {
   const DevBucket& d = w->d;
   const int n_rec = d.kind == kStepAdj ? d.n_in + 1 : d.n_in;
   int rip, v0;
@@ -615,14 +894,23 @@ __device__ __forceinline__ void warp_tile(WarpTile* w, Real* __restrict__ data, 
     }
   }
   __syncwarp();
-  if (!GRAD || d.kind == kStepFwd)
-    tile_items<Real, VB, PAIR, CG, 2, 0>(w, data, g, r0, r1, lane, rip, v0, lane_on, ctrl, dbg_bucket);
-  else if (d.kind == kStepAdj)
+  if (!GRAD || d.kind == kStepFwd) {
+    // staged plans: row-wide tiles through the bulk-copy ring, narrower ones
+    // through the per-lane cp.async ring; the register path otherwise
+    bool done = false;
+    if (!PAIR && StageUnits<Real, VB, PAIR>::value > 0 && ring != nullptr && g.bulk && g.RP == 1)
+      done = tile_rows_bulk<Real, VB>(w, reinterpret_cast<unsigned char*>(ring), *phase, data, g, r0, r1, lane, ctrl,
+                                      g.wait_limit);
+    else if (g.RP > 1)
+      done = try_tile_staged<Real, VB, PAIR>(w, ring, data, g, r0, r1, lane, rip, v0, lane_on, ctrl, dbg_bucket);
+    if (!done) tile_items<Real, VB, PAIR, CG, 2, 0>(w, data, g, r0, r1, lane, rip, v0, lane_on, ctrl, dbg_bucket);
+  } else if (d.kind == kStepAdj) {
     tile_adjoint<Real, VB, PAIR, CG, 2>(w, data, g, r0, r1, lane, rip, v0, lane_on, ctrl, dbg_bucket);
-  else if (d.kind == kStepAdjRed)
+  } else if (d.kind == kStepAdjRed) {
     tile_adjred<Real, VB, PAIR, CG, 2>(w, data, g, r0, r1, lane, rip, v0, lane_on, ctrl, dbg_bucket);
-  else
+  } else {
     tile_zero<Real, VB, PAIR, 2>(w, data, g, r0, r1, rip, v0, lane_on);
+  }
 }
 
 }  // namespace dev

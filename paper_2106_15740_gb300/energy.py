@@ -14,6 +14,7 @@ from . import binding as qb
 
 DTYPES = {"c128": qb.QT_C128, "c64": qb.QT_C64}
 MODES = {"per_bucket": qb.QT_MODE_PER_BUCKET, "persistent": qb.QT_MODE_PERSISTENT}
+LOAD_PATHS = {"registers": 0, "staged": 1}
 
 
 def _stream_handle(device):
@@ -31,7 +32,7 @@ class EnergyPlan:
     def __init__(self, n_vertices, edges, p, batch=1, dtype="c128", mode="persistent",
                  max_workspace=0, max_width=0, device="cuda:0", gradient=False, lane_items=0,
                  group_rows=0, edge_range=None, slice=False, chunk_tiles=0, order_trials=0, order_seed=0,
-                 order_tau=1.0):
+                 order_tau=1.0, load_path="registers"):
         self.n_vertices, self.p, self.batch = int(n_vertices), int(p), int(batch)
         self.edges = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
         self.device = torch.device(device)
@@ -40,7 +41,7 @@ class EnergyPlan:
                             max_width=max_width, gradient=gradient, lane_items=lane_items,
                             group_rows=group_rows, edge_range=self.edge_range, slice=slice,
                             chunk_tiles=chunk_tiles, order_trials=order_trials, order_seed=order_seed,
-                            order_tau=order_tau)
+                            order_tau=order_tau, load_path=load_path)
         opt = qb.qt_plan_options_default()
         opt.batch = self.batch
         opt.dtype = DTYPES[dtype]
@@ -56,6 +57,7 @@ class EnergyPlan:
         opt.order_trials = int(order_trials)
         opt.order_seed = int(order_seed)
         opt.order_tau = float(order_tau)
+        opt.load_path = LOAD_PATHS[load_path]
         self.plan = qb.qt_plan_create(self.n_vertices, self.edges, self.p, opt)
         self.ws_bytes = qb.qt_plan_workspace_size(self.plan)
         self.stats = qb.qt_plan_stats(self.plan)
@@ -91,6 +93,26 @@ class EnergyPlan:
         """Synchronise and raise if a device-side wait timed out."""
         qb.qt_plan_check(self.plan, _stream_handle(self.device))
 
+    def trace(self, gamma, beta, grad=False):
+        """Evaluate once with queue tracing on and return (trace, tasks):
+        trace is a uint64 array [n_tasks, 4] of (claimed, ready, done) device
+        clock readings in ns and (SM << 16 | warp); tasks the queue entries
+        (``binding.qt_plan_tasks``).  Persistent plans only."""
+        n = qb.qt_plan_trace_size(self.plan)
+        buf = torch.zeros(max(n, 8), dtype=torch.uint8, device=self.device)
+        qb.qt_plan_set_trace(self.plan, buf.data_ptr(), n)
+        try:
+            self.energy(gamma, beta, grad=grad)
+            self.check()
+        finally:
+            qb.qt_plan_set_trace(self.plan, 0, 0)
+        tr = buf[:n].cpu().numpy().view(np.uint64).reshape(-1, 4)
+        return tr, qb.qt_plan_tasks(self.plan)
+
+    def capture(self, edge_zz=False, grad=False):
+        """Capture one evaluation of this plan as a CUDA graph (``CapturedEnergy``)."""
+        return CapturedEnergy(self, edge_zz=edge_zz, grad=grad)
+
     def energy_host(self, gamma, beta, edge_zz=False, grad=False):
         B, p = self.batch, self.p
         ga = np.ascontiguousarray(np.asarray(gamma, dtype=np.float64).reshape(B, p))
@@ -114,6 +136,47 @@ class EnergyPlan:
             self.close()
         except Exception:
             pass
+
+
+class CapturedEnergy:
+    """One plan evaluation (angle table, leaf factors, the persistent bucket
+    launch, the FP64 energy sum and, for gradient plans, the leaf-gradient
+    kernels) captured once as a CUDA graph and replayed per call.
+
+    The graph reads the angles from static device tensors and writes static
+    outputs, so ``__call__`` copies the new angles in, replays the graph on
+    the current stream and returns the static outputs (overwritten by the
+    next replay; clone them to keep them).  A first direct call, outside the
+    capture, binds the plan to its workspace (that call uploads the plan's
+    descriptors and synchronises, which a capture cannot hold).
+    """
+
+    def __init__(self, plan, edge_zz=False, grad=False):
+        self.plan = plan
+        dev = plan.device
+        B, p = plan.batch, plan.p
+        self.gamma = torch.zeros((B, p), dtype=torch.float64, device=dev)
+        self.beta = torch.zeros((B, p), dtype=torch.float64, device=dev)
+        self.kw = dict(edge_zz=edge_zz, grad=grad)
+        plan.energy(self.gamma, self.beta, **self.kw)
+        plan.check()
+        self.graph = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(self.graph, stream=side, capture_error_mode="thread_local"):
+                self.outputs = plan.energy(self.gamma, self.beta, **self.kw)
+        torch.cuda.current_stream(dev).wait_stream(side)
+
+    def replay(self):
+        """Replay the captured evaluation on the static angle tensors."""
+        self.graph.replay()
+        return self.outputs
+
+    def __call__(self, gamma, beta):
+        self.gamma.copy_(gamma)
+        self.beta.copy_(beta)
+        return self.replay()
 
 
 class QAOAEnergy(torch.autograd.Function):

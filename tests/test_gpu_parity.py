@@ -122,6 +122,26 @@ def test_persistent_equals_per_bucket_bitwise():
     assert np.array_equal(out[0], out[1])
 
 
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("batch", [1, 2, 3, 64])
+def test_staged_loads_equal_register_loads_bitwise(dtype, batch):
+    """The shared-memory staged operand path and the register path multiply
+    the same operands in the same order, so every edge value is identical;
+    fan-ins above the ring's capacity and odd complex64 batches fall back to
+    registers inside the same launch.  Also checked against the oracle."""
+    n, edges, p, g, b = workload("n100_p3", batch=batch)
+    out = {}
+    for path in ("staged", "registers"):
+        plan = _plan(n, edges, p, batch, dtype, "persistent", load_path=path, order_trials=4)
+        out[path] = _run(plan, g, b)
+        plan.close()
+    assert np.array_equal(out["staged"][1], out["registers"][1])
+    assert np.array_equal(out["staged"][0], out["registers"][0])
+    sel = [0, 75, 149]
+    ref = _oracle_zz(n, edges, p, g[batch - 1], b[batch - 1], sel)
+    np.testing.assert_allclose(out["staged"][1][sel, batch - 1, 0], ref.real, atol=TOL[dtype], rtol=0)
+
+
 @pytest.mark.parametrize("batch", [2, 3, 5, 8])
 def test_batch_shapes(batch):
     """Even batches use the 2-wide complex64 vectors, odd ones the scalar path."""
