@@ -156,12 +156,13 @@ typedef struct {
   double order_tau;       /* temperature: the next variable is drawn with probability
                              proportional to exp(-(fill - min fill) / order_tau) (<=0: 1) */
   int32_t load_path;      /* persistent mode: 0 (default) loads every operand into registers;
-                             1 stages the operands of forward steps in shared memory several
-                             rows ahead -- row-wide tiles (B >= 17 angle-set vectors) through
-                             a bulk-copy (TMA) ring with one mbarrier per slot, narrower tiles
-                             through a per-lane cp.async ring -- where the tile shape allows
-                             it (complex64 with B even or B = 1, complex128).  Both give
-                             bit-identical results */
+                             1 stages the intermediate operands of forward steps in a per-warp
+                             shared-memory ring several rows ahead: lane 0 brings each operand
+                             row pair with one bulk copy (TMA) completing on the slot's
+                             mbarrier, and a bucket's leaf-factor rows stay in registers.
+                             Staging applies to row-wide tiles of 16-byte vectors (complex64
+                             with even B in [34, 64], complex128 with B in [17, 32]); other
+                             batches keep the register path.  Both give bit-identical results */
 } qt_plan_options;
 
 /* Fill `opt` with defaults: batch 1, QT_C128, QT_MODE_PER_BUCKET, no gradient,

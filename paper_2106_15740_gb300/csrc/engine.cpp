@@ -608,13 +608,13 @@ qt_status run_plan(Plan* P, const double* gamma, const double* beta, double* ene
   }
   if (P->opt.mode == QT_MODE_PERSISTENT) {
     int per_sm = 0;
-    QT_CUDA(persistent_occupancy(dtype, P->opt.gradient != 0, P->opt.load_path == 1, B, &per_sm));
+    QT_CUDA(persistent_occupancy(dtype, P->opt.gradient != 0, P->opt.load_path, P->bulk_ok, B, &per_sm));
     int n_sm = 0;
     QT_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
     const int32_t grid = std::max(1, per_sm) * n_sm;
-    QT_CUDA(launch_persistent(dtype, P->opt.gradient != 0, P->opt.load_path == 1, dbk, (const DevTask*)(base + L.tasks), (int32_t)P->tasks.size(),
+    QT_CUDA(launch_persistent(dtype, P->opt.gradient != 0, P->opt.load_path, P->bulk_ok, dbk, (const DevTask*)(base + L.tasks), (int32_t)P->tasks.size(),
                               (DevCtrl*)(base + L.ctrl), (int32_t*)(base + L.done), B, P->opt.lane_items, data,
-                              P->data_elems, grid, P->spin_limit, P->bulk_ok, P->trace, s));
+                              P->data_elems, grid, P->spin_limit, P->trace, s));
   } else {
     int n_sm = 0;
     QT_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));

@@ -142,11 +142,12 @@ __device__ __forceinline__ int32_t ld_acquire(const int32_t* p) {
 // Consecutive tiles of one bucket on a warp reuse its record and skip the
 // wait (done counters only grow).
 //
-// STAGED: forward steps move their operands through a per-warp cp.async ring
-// in dynamic shared memory (kRingBytesPerWarp per warp, see kernels.cuh);
-// otherwise every load goes to registers.
-template <class Real, int VB, bool PAIR, bool GRAD, bool STAGED>
-__global__ void __launch_bounds__(256, STAGED ? 2 : 4) persistent_kernel(const DevBucket* __restrict__ buckets,
+// STAGE (the plan's load path): 0 every operand load goes to registers;
+// 1 forward steps of row-wide tiles move their intermediate operands through
+// a per-warp bulk-copy ring in dynamic shared memory (kRingBytesPerWarp per
+// warp, see kernels.cuh).
+template <class Real, int VB, bool PAIR, bool GRAD, int STAGE>
+__global__ void __launch_bounds__(256, STAGE ? 2 : 4) persistent_kernel(const DevBucket* __restrict__ buckets,
                                                             const DevTask* __restrict__ tasks, int32_t n_tasks,
                                                             DevCtrl* ctrl, int32_t* done, Real* __restrict__ data,
                                                             const TileGeom g, int32_t spin_limit,
@@ -155,9 +156,9 @@ __global__ void __launch_bounds__(256, STAGED ? 2 : 4) persistent_kernel(const D
   extern __shared__ uint4 ring_all[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   WarpTile* w = &tiles[wid];
-  uint4* ring = STAGED ? ring_all + (size_t)wid * kRingUnits * 32 : nullptr;
+  uint4* ring = STAGE ? ring_all + (size_t)wid * (kRingBytesPerWarp / 16) : nullptr;
   uint32_t phase = 0;  // bulk-copy ring: parity each slot waits for next
-  if (STAGED) {
+  if (STAGE != 0) {
     if (lane == 0) {
       for (int k = 0; k < kBulkSlots; ++k) mbar_init(&w->mbar[k], 1);
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -224,7 +225,7 @@ __global__ void __launch_bounds__(256, STAGED ? 2 : 4) persistent_kernel(const D
         const int64_t r0 = tt * g.R;
         if (r0 >= n_rows) break;
         const int64_t r1 = r0 + g.R < n_rows ? r0 + g.R : n_rows;
-        warp_tile<Real, VB, PAIR, true, GRAD>(w, data, g, r0, r1, lane, ctrl, b, ring, &phase);
+        warp_tile<Real, VB, PAIR, true, GRAD, STAGE>(w, data, g, r0, r1, lane, ctrl, b, ring, &phase);
         __syncwarp();  // the next tile or step reuses the warp's tables and reads what this one wrote
       }
     }
@@ -415,7 +416,6 @@ TileGeom tile_geom(int dtype, int32_t B, int32_t lane_items) {
   while (P * 2 * g.VC <= cap) P *= 2;
   g.P = P;
   g.R = P * g.RP;
-  g.bulk = 0;
   g.wait_limit = 1 << 22;
   g.data_elems = 0;
   return g;
@@ -446,47 +446,55 @@ cudaError_t launch_bucket(int dtype, const DevBucket& d, int32_t B, int32_t lane
   return cudaGetLastError();
 }
 
-// The staged form exists for every tile shape whose operand pieces are 16
-// bytes (complex64 with B even or B = 1, complex128); complex64 with an odd
-// B >= 3 keeps the register path.
-bool staged_supported(int dtype, int32_t B) { return !(dtype == QT_C64 && B > 1 && B % 2 == 1); }
+// Staged kernels exist for row-wide tiles of 16-byte vectors: one row per
+// pass and one vector chunk per row (complex64 with even B in [34, 64],
+// complex128 with B in [17, 32]); other shapes keep the register path.
+bool staged_supported(int dtype, int32_t B) {
+  if (B <= 1 || !(dtype == QT_C128 || vector_width(dtype, B) == 2)) return false;
+  const TileGeom g = tile_geom(dtype, B, 0);
+  return g.RP == 1 && g.VC == 1;
+}
 
-template <class Real, int VB, bool PAIR, bool GRAD, bool ST>
+template <class Real, int VB, bool PAIR, bool GRAD, int ST>
 static const void* pk_fn() {
   return (const void*)dev::persistent_kernel<Real, VB, PAIR, GRAD, ST>;
 }
 
-template <bool GRAD, bool ST>
+template <bool GRAD, int ST>
 static const void* persistent_fn_t(int dtype, int32_t B) {
   const int vb = vector_width(dtype, B);
   const bool pair = (B == 1);
   if (dtype == QT_C64)
-    return pair ? pk_fn<float, 1, true, GRAD, ST>()
-                : (vb == 2 ? pk_fn<float, 2, false, GRAD, ST>() : pk_fn<float, 1, false, GRAD, false>());
-  return pair ? pk_fn<double, 1, true, GRAD, ST>() : pk_fn<double, 1, false, GRAD, ST>();
+    return pair ? pk_fn<float, 1, true, GRAD, 0>()
+                : (vb == 2 ? pk_fn<float, 2, false, GRAD, ST>() : pk_fn<float, 1, false, GRAD, 0>());
+  return pair ? pk_fn<double, 1, true, GRAD, 0>() : pk_fn<double, 1, false, GRAD, ST>();
 }
 
-static const void* persistent_fn(int dtype, bool grad, bool staged, int32_t B) {
-  if (staged && !staged_supported(dtype, B)) staged = false;
-  if (grad) return staged ? persistent_fn_t<true, true>(dtype, B) : persistent_fn_t<true, false>(dtype, B);
-  return staged ? persistent_fn_t<false, true>(dtype, B) : persistent_fn_t<false, false>(dtype, B);
+template <bool GRAD>
+static const void* persistent_fn_g(int dtype, int stage, int32_t B) {
+  return stage != 0 ? persistent_fn_t<GRAD, 1>(dtype, B) : persistent_fn_t<GRAD, 0>(dtype, B);
+}
+
+static const void* persistent_fn(int dtype, bool grad, int stage, int32_t B) {
+  if (!staged_supported(dtype, B)) stage = 0;
+  return grad ? persistent_fn_g<true>(dtype, stage, B) : persistent_fn_g<false>(dtype, stage, B);
 }
 
 // Dynamic shared memory of a persistent launch (the staged ring of 8 warps).
-static int persistent_smem(int dtype, bool staged, int32_t B) {
-  return staged && staged_supported(dtype, B) ? 8 * dev::kRingBytesPerWarp : 0;
+static int persistent_smem(int dtype, int stage, int32_t B) {
+  return stage != 0 && staged_supported(dtype, B) ? 8 * dev::kRingBytesPerWarp : 0;
 }
 
-cudaError_t launch_persistent(int dtype, bool grad, bool staged, const DevBucket* buckets, const DevTask* tasks,
-                              int32_t n_tasks, DevCtrl* ctrl, int32_t* done, int32_t B, int32_t lane_items,
-                              void* data, int64_t data_elems, int32_t grid, int32_t spin_limit,
-                              bool bulk, unsigned long long* trace, cudaStream_t s) {
+cudaError_t launch_persistent(int dtype, bool grad, int32_t load_path, bool bulk_ok, const DevBucket* buckets,
+                              const DevTask* tasks, int32_t n_tasks, DevCtrl* ctrl, int32_t* done, int32_t B,
+                              int32_t lane_items, void* data, int64_t data_elems, int32_t grid, int32_t spin_limit,
+                              unsigned long long* trace, cudaStream_t s) {
   TileGeom g = tile_geom(dtype, B, lane_items);
   g.data_elems = data_elems;
-  g.bulk = bulk ? 1 : 0;
   g.wait_limit = 1 << 22;
-  const void* fn = persistent_fn(dtype, grad, staged, B);
-  const int smem = persistent_smem(dtype, staged, B);
+  const int stage = load_path != 0 && bulk_ok ? 1 : 0;
+  const void* fn = persistent_fn(dtype, grad, stage, B);
+  const int smem = persistent_smem(dtype, stage, B);
   if (smem > 0) {
     const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
@@ -496,9 +504,11 @@ cudaError_t launch_persistent(int dtype, bool grad, bool staged, const DevBucket
   return cudaLaunchKernel(fn, dim3(grid), dim3(256), args, (size_t)smem, s);
 }
 
-cudaError_t persistent_occupancy(int dtype, bool grad, bool staged, int32_t B, int* blocks_per_sm) {
-  const void* fn = persistent_fn(dtype, grad, staged, B);
-  const int smem = persistent_smem(dtype, staged, B);
+cudaError_t persistent_occupancy(int dtype, bool grad, int32_t load_path, bool bulk_ok, int32_t B,
+                                 int* blocks_per_sm) {
+  const int stage = load_path != 0 && bulk_ok ? 1 : 0;
+  const void* fn = persistent_fn(dtype, grad, stage, B);
+  const int smem = persistent_smem(dtype, stage, B);
   if (smem > 0) {
     const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;

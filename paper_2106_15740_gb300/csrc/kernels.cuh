@@ -383,137 +383,19 @@ __device__ __forceinline__ void tile_items(WarpTile* w, Real* __restrict__ data,
 
 // ------------------------------------------------ shared-memory staged path --
 //
-// The register path above keeps at most 2 items' loads of one input in flight
-// per lane and waits on each input in turn.  The staged path moves the
-// operand rows through a per-warp ring in shared memory with cp.async: every
-// lane copies the 16-byte pieces of all inputs of its item q + S - 1 while it
-// multiplies item q, so S items' loads (all inputs) are in flight per lane
-// without holding registers.  Each lane reads back only what it copied, so
-// the ring needs no barrier: cp.async.wait_group makes a lane's own copies
-// visible to it.  Slot q % S is refilled for item q + S only after item q's
-// products were taken, one loop iteration earlier.
-//
-// Ring: kRingUnits 16-byte units per lane, unit j of lane l at ring[j * 32 + l]
-// (a warp's access to one unit is 512 contiguous bytes, conflict-free).
-// An item of a bucket with n_in inputs uses n_in * UPI units (UPI = 16-byte
-// pieces per input and item: the x = 0 and x = 1 rows of a [2^r][B] tensor
-// for B >= 2, or the adjacent pair of a B = 1 tensor); S = kRingUnits / units
-// rounded down to a power of two, at least 2.
-constexpr int kRingUnits = 16;
-constexpr int kRingBytesPerWarp = kRingUnits * 32 * 16;
+// The register path above keeps at most 2 rows' loads of one input in flight
+// per lane and waits on each input in turn.  The staged path (plan option
+// load_path 1) applies to row-wide tiles (RP = 1, VC = 1: B >= 17 angle-set
+// vectors, each lane one vector of the same row) and moves the intermediate
+// operand rows through a per-warp ring in shared memory (kRingBytesPerWarp
+// bytes of dynamic shared memory per warp), several rows ahead of the row
+// being multiplied.
+constexpr int kRingBytesPerWarp = 8192;
 
-__device__ __forceinline__ void cp_async16(uint4* smem, const void* gmem, bool via_l1) {
-  const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
-  if (via_l1)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-  else
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
-// 16-byte pieces per input and item (0: this tile shape has no staged form).
-template <class Real, int VB, bool PAIR> struct StageUnits { static constexpr int value = 0; };
-template <> struct StageUnits<float, 2, false> { static constexpr int value = 2; };   // two 16-B rows
-template <> struct StageUnits<double, 1, false> { static constexpr int value = 2; };  // two double2 rows
-template <> struct StageUnits<float, 1, true> { static constexpr int value = 1; };    // one float4 pair
-template <> struct StageUnits<double, 1, true> { static constexpr int value = 2; };   // two double2
-
-template <class Real, int VB, bool PAIR, int S>
-__device__ __forceinline__ void stage_issue(const WarpTile* w, uint4* ring, const Real* __restrict__ data,
-                                            const TileGeom& g, int q, int Q, int64_t r0, int64_t r1, int lane,
-                                            int rip, int v0, bool lane_on, DevCtrl* ctrl, int dbg_bucket) {
-  (void)ctrl;
-  (void)dbg_bucket;
-  constexpr int UPI = StageUnits<Real, VB, PAIR>::value;
-  constexpr int SLOT = kRingUnits / S;
-  const DevBucket& d = w->d;
-  const ItemSet<1> it = make_items<1>(g, q, Q, r0, r1, rip, v0, lane_on);
-  if (it.ok[0]) {
-    uint4* slot = ring + (q % S) * SLOT * 32 + lane;
-    for (int i = 0; i < d.n_in; ++i) {
-      const uint32_t k = w->tab[i][it.pp[0]] + w->lpart[i][lane];
-      const bool leaf = d.in[i].flags & kInLeaf;
-      // element index of the x = 0 piece; the x = 1 piece is B elements on
-      // (rows 2k, 2k + 1 of a [2^r][B] tensor) or, for a B = 1 pair, adjacent
-      const int64_t e0 = PAIR ? d.in[i].off + 2 * (int64_t)k
-                              : d.in[i].off + (int64_t)(2 * k) * g.B + (int64_t)(it.vv[0] * VB);
-      if (QT_RANGE_OK(e0, PAIR ? 2 : g.B + VB, 1, i)) {
-        cp_async16(slot + (i * UPI) * 32, data + 2 * e0, leaf);
-        if (UPI == 2) cp_async16(slot + (i * UPI + 1) * 32, data + 2 * (PAIR ? e0 + 1 : e0 + g.B), leaf);
-      }
-    }
-  }
-  cp_async_commit();
-}
-
-// Forward items of one tile through the ring, S items ahead.
-template <class Real, int VB, bool PAIR, int S>
-__device__ __forceinline__ void tile_items_staged(WarpTile* w, uint4* ring, Real* __restrict__ data,
-                                                  const TileGeom& g, int64_t r0, int64_t r1, int lane, int rip,
-                                                  int v0, bool lane_on, DevCtrl* ctrl, int dbg_bucket) {
-  constexpr int UPI = StageUnits<Real, VB, PAIR>::value;
-  constexpr int SLOT = kRingUnits / S;
-  using C = typename Cx<Real>::T;
-  const DevBucket& d = w->d;
-  const int n_in = d.n_in;
-  const int Q = g.P * g.VC;
-#pragma unroll
-  for (int q = 0; q < S - 1; ++q) {
-    if (q < Q)
-      stage_issue<Real, VB, PAIR, S>(w, ring, data, g, q, Q, r0, r1, lane, rip, v0, lane_on, ctrl, dbg_bucket);
-    else
-      cp_async_commit();
-  }
-  for (int q = 0; q < Q; ++q) {
-    if (q + S - 1 < Q)
-      stage_issue<Real, VB, PAIR, S>(w, ring, data, g, q + S - 1, Q, r0, r1, lane, rip, v0, lane_on, ctrl,
-                                     dbg_bucket);
-    else
-      cp_async_commit();
-    cp_async_wait<S - 1>();  // this lane's copies of item q have landed
-    const ItemSet<1> it = make_items<1>(g, q, Q, r0, r1, rip, v0, lane_on);
-    if (!it.ok[0]) continue;
-    const uint4* slot = ring + (q % S) * SLOT * 32 + lane;
-    Pack<Real, VB> p0, p1;
-    for (int i = 0; i < n_in; ++i) {
-      Pack<Real, VB> a0, a1;
-      if (PAIR) {
-        const uint4 u0 = slot[(i * UPI) * 32];
-        if (UPI == 1) {  // complex64 pair: x = 0 in .x/.y, x = 1 in .z/.w
-          a0.c[0] = *reinterpret_cast<const C*>(&u0.x);
-          a1.c[0] = *reinterpret_cast<const C*>(&u0.z);
-        } else {
-          const uint4 u1 = slot[(i * UPI + 1) * 32];
-          a0.c[0] = *reinterpret_cast<const C*>(&u0);
-          a1.c[0] = *reinterpret_cast<const C*>(&u1);
-        }
-      } else {
-        const uint4 u0 = slot[(i * UPI) * 32];
-        const uint4 u1 = slot[(i * UPI + 1) * 32];
-        a0 = *reinterpret_cast<const Pack<Real, VB>*>(&u0);
-        a1 = *reinterpret_cast<const Pack<Real, VB>*>(&u1);
-      }
-      if (i == 0) {
-        p0 = a0;
-        p1 = a1;
-      } else {
-        pmul<Real, VB>(p0, a0);
-        pmul<Real, VB>(p1, a1);
-      }
-    }
-    Pack<Real, VB> o;
-#pragma unroll
-    for (int v = 0; v < VB; ++v) o.c[v] = cadd<Real>(p0.c[v], p1.c[v]);
-    const int64_t so = PAIR ? d.out_off + (int64_t)it.y[0]
-                            : d.out_off + (int64_t)it.y[0] * g.B + (int64_t)(it.vv[0] * VB);
-    if (QT_RANGE_OK(so, VB, 2, -1)) stv<Real, VB>(data, so, o);
-  }
-  cp_async_wait<0>();  // nothing of this tile stays in flight into the next one
-}
+// Tile shapes with a staged form: 16-byte vectors of angle sets.
+template <class Real, int VB> struct Stageable { static constexpr bool value = false; };
+template <> struct Stageable<float, 2> { static constexpr bool value = true; };
+template <> struct Stageable<double, 1> { static constexpr bool value = true; };
 
 // ------------------------------------------------ wide-row bulk-copy path --
 //
@@ -565,93 +447,139 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
-// Wide-row forward tile through the bulk-copy ring (kRingBytesPerWarp bytes
-// of this warp at `ring`); returns false (nothing done) when fewer than two
-// slots of the bucket's size fit.
+// Leaf handling shared by the row-wide staged tiles.  A bucket's leaf
+// factor (at most one input) is small and its row changes slowly with y:
+// over the R rows of a tile it takes 2^m values, m = number of its mask bits
+// below log2(R), and for m = 1 those are rows k0 and k0 + 1 (pext keeps the
+// order of the bits), k0 = pext(r0).  With m <= 1 every lane keeps its vector
+// of both leaf rows (x = 0, 1) in registers for the whole tile.  Returns
+// false when the bucket has several leaf inputs or m > 1.
+__device__ __forceinline__ bool row_leaf(const DevBucket& d, const TileGeom& g, int* il, int* n_int,
+                                         uint32_t* leaf_bit) {
+  *il = -1;
+  *n_int = 0;
+  *leaf_bit = 0;
+  for (int i = 0; i < d.n_in; ++i) {
+    if (d.in[i].flags & kInLeaf) {
+      if (*il >= 0) return false;
+      *il = i;
+    } else {
+      ++*n_int;
+    }
+  }
+  if (*il >= 0) {
+    const uint32_t lm = d.in[*il].mask & ((uint32_t)g.R - 1u);  // r0 is a multiple of R
+    if (lm & (lm - 1u)) return false;
+    *leaf_bit = lm;
+  }
+  return true;
+}
+
+template <class Real, int VB>
+__device__ __forceinline__ void row_leaf_load(const WarpTile* w, const Real* __restrict__ data, const TileGeom& g,
+                                              int il, uint32_t leaf_bit, int vv, Pack<Real, VB> (&lf)[2][2]) {
+  if (il < 0) return;
+  const DevBucket& d = w->d;
+  const uint32_t k0 = w->tab[il][0];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    if (j == 1 && leaf_bit == 0) continue;
+    const int64_t e0 = d.in[il].off + (int64_t)(2 * (k0 + (uint32_t)j)) * g.B + (int64_t)vv * VB;
+    lf[j][0] = ldv<Real, VB, false>(data, e0);
+    lf[j][1] = ldv<Real, VB, false>(data, e0 + g.B);
+  }
+}
+
+// Wide-row forward tile (RP = 1, VC = 1) through the bulk-copy ring
+// (kRingBytesPerWarp bytes of this warp at `ring`): lane 0 brings each
+// intermediate's row pair of a row into the row's slot with one
+// cp.async.bulk, completing on the slot's mbarrier; the leaf stays in
+// registers (row_leaf).  Products in input order: bit-identical to the
+// register path.  Returns false (nothing done) when the shape does not fit.
 template <class Real, int VB>
 __device__ __forceinline__ bool tile_rows_bulk(WarpTile* w, unsigned char* ring, uint32_t& phase,
                                                Real* __restrict__ data, const TileGeom& g, int64_t r0, int64_t r1,
                                                int lane, DevCtrl* ctrl, int32_t wait_limit) {
   using C = typename Cx<Real>::T;
+  using PK = Pack<Real, VB>;
   const DevBucket& d = w->d;
   const int n_in = d.n_in;
+  int il, n_int;
+  uint32_t leaf_bit;
+  if (!row_leaf(d, g, &il, &n_int, &leaf_bit)) return false;
   const uint32_t rowb = (uint32_t)g.B * (uint32_t)sizeof(C);  // bytes of one row of B complex numbers
   const uint32_t pairb = 2u * rowb;
-  const uint32_t slotb = (uint32_t)n_in * pairb;
+  const uint32_t slotb = (uint32_t)(n_int > 0 ? n_int : 1) * pairb;
   int S = (int)((uint32_t)kRingBytesPerWarp / slotb);
   if (S > kBulkSlots) S = kBulkSlots;
   if (S < 2) return false;
   const int nrows = (int)(r1 - r0);
-  if (lane == 0) {
+  const int vv = lane < g.Bv ? lane : 0;  // idle lanes compute vector 0 and do not store
+  PK lf[2][2];
+  row_leaf_load<Real, VB>(w, data, g, il, leaf_bit, vv, lf);
+  if (lane == 0 && n_int > 0) {
     fence_proxy_async_smem();  // the previous tile's reads of the ring come first
     for (int q = 0; q < S && q < nrows; ++q) {
       unsigned long long* mb = &w->mbar[q];
       unsigned char* dst = ring + (uint32_t)q * slotb;
       mbar_expect_tx(mb, slotb);
-      for (int i = 0; i < n_in; ++i)
-        bulk_g2s(dst + (uint32_t)i * pairb, data + 2 * (d.in[i].off + (int64_t)(2 * w->tab[i][q]) * g.B), pairb, mb);
+      for (int i = 0, j = 0; i < n_in; ++i) {
+        if (i == il) continue;
+        bulk_g2s(dst + (uint32_t)j * pairb, data + 2 * (d.in[i].off + (int64_t)(2 * w->tab[i][q]) * g.B), pairb, mb);
+        ++j;
+      }
     }
   }
+  const uint32_t lo = (uint32_t)vv * VB * (uint32_t)sizeof(C);
   for (int q = 0; q < nrows; ++q) {
     const int s = q % S;
-    if (!mbar_wait(&w->mbar[s], (phase >> s) & 1u, wait_limit)) {
-      if (lane == 0) atomicCAS(&ctrl->status, 0, (int32_t)QT_ETIMEOUT);
-    }
-    phase ^= 1u << s;
-    const unsigned char* src = ring + (uint32_t)s * slotb;
-    const int64_t y = r0 + q;
-    for (int vc = 0; vc < g.VC; ++vc) {
-      const int vv = lane + 32 * vc;
-      if (vv >= g.Bv) continue;
-      const uint32_t lo = (uint32_t)vv * VB * (uint32_t)sizeof(C);
-      Pack<Real, VB> p0, p1;
-      for (int i = 0; i < n_in; ++i) {
-        const unsigned char* base = src + (uint32_t)i * pairb + lo;
-        const Pack<Real, VB> a0 = *reinterpret_cast<const Pack<Real, VB>*>(base);
-        const Pack<Real, VB> a1 = *reinterpret_cast<const Pack<Real, VB>*>(base + rowb);
-        if (i == 0) {
-          p0 = a0;
-          p1 = a1;
-        } else {
-          pmul<Real, VB>(p0, a0);
-          pmul<Real, VB>(p1, a1);
-        }
+    if (n_int > 0) {
+      if (!mbar_wait(&w->mbar[s], (phase >> s) & 1u, wait_limit)) {
+        if (lane == 0) atomicCAS(&ctrl->status, 0, (int32_t)QT_ETIMEOUT);
       }
-      Pack<Real, VB> o;
+      phase ^= 1u << s;
+    }
+    const unsigned char* src = ring + (uint32_t)s * slotb + lo;
+    const int64_t y = r0 + q;
+    const bool hi = ((uint32_t)y & leaf_bit) != 0;
+    PK p0, p1;
+    for (int i = 0, j = 0; i < n_in; ++i) {
+      PK a0, a1;
+      if (i == il) {
+        a0 = hi ? lf[1][0] : lf[0][0];
+        a1 = hi ? lf[1][1] : lf[0][1];
+      } else {
+        a0 = *reinterpret_cast<const PK*>(src + (uint32_t)j * pairb);
+        a1 = *reinterpret_cast<const PK*>(src + (uint32_t)j * pairb + rowb);
+        ++j;
+      }
+      if (i == 0) {
+        p0 = a0;
+        p1 = a1;
+      } else {
+        pmul<Real, VB>(p0, a0);
+        pmul<Real, VB>(p1, a1);
+      }
+    }
+    if (lane < g.Bv) {
+      PK o;
 #pragma unroll
       for (int v = 0; v < VB; ++v) o.c[v] = cadd<Real>(p0.c[v], p1.c[v]);
       stv<Real, VB>(data, d.out_off + y * g.B + (int64_t)vv * VB, o);
     }
     __syncwarp();  // every lane has read slot s
-    if (lane == 0 && q + S < nrows) {
+    if (lane == 0 && n_int > 0 && q + S < nrows) {
       unsigned long long* mb = &w->mbar[s];
       unsigned char* dst = ring + (uint32_t)s * slotb;
       mbar_expect_tx(mb, slotb);
-      for (int i = 0; i < n_in; ++i)
-        bulk_g2s(dst + (uint32_t)i * pairb,
-                 data + 2 * (d.in[i].off + (int64_t)(2 * w->tab[i][q + S]) * g.B), pairb, mb);
+      for (int i = 0, j = 0; i < n_in; ++i) {
+        if (i == il) continue;
+        bulk_g2s(dst + (uint32_t)j * pairb, data + 2 * (d.in[i].off + (int64_t)(2 * w->tab[i][q + S]) * g.B), pairb,
+                 mb);
+        ++j;
+      }
     }
   }
-  return true;
-}
-
-// Staged forward tile if the tile shape and the bucket's fan-in allow it;
-// returns false (nothing done) otherwise.
-template <class Real, int VB, bool PAIR>
-__device__ __forceinline__ bool try_tile_staged(WarpTile* w, uint4* ring, Real* __restrict__ data,
-                                                const TileGeom& g, int64_t r0, int64_t r1, int lane, int rip,
-                                                int v0, bool lane_on, DevCtrl* ctrl, int dbg_bucket) {
-  constexpr int UPI = StageUnits<Real, VB, PAIR>::value;
-  if (UPI == 0 || ring == nullptr) return false;
-  const int units = w->d.n_in * (UPI > 0 ? UPI : 1);
-  if (units <= kRingUnits / 8)
-    tile_items_staged<Real, VB, PAIR, 8>(w, ring, data, g, r0, r1, lane, rip, v0, lane_on, ctrl, dbg_bucket);
-  else if (units <= kRingUnits / 4)
-    tile_items_staged<Real, VB, PAIR, 4>(w, ring, data, g, r0, r1, lane, rip, v0, lane_on, ctrl, dbg_bucket);
-  else if (units <= kRingUnits / 2)
-    tile_items_staged<Real, VB, PAIR, 2>(w, ring, data, g, r0, r1, lane, rip, v0, lane_on, ctrl, dbg_bucket);
-  else
-    return false;
   return true;
 }
 
@@ -870,7 +798,7 @@ __device__ __forceinline__ void tile_adjred(WarpTile* w, Real* __restrict__ data
 // sets).  r0 is a multiple of g.R.  The pass table tab[i][p] =
 // pext(r0 + p * RP, mask_i) is built here; the lane parts must already be in
 // w->lpart.  Per item an input row is one table read plus one add.
-template <class Real, int VB, bool PAIR, bool CG, bool GRAD = false>
+template <class Real, int VB, bool PAIR, bool CG, bool GRAD = false, int STAGE = 0>
 __device__ __forceinline__ void warp_tile(WarpTile* w, Real* __restrict__ data, const TileGeom& g, int64_t r0,
                                           int64_t r1, int lane, DevCtrl* ctrl = nullptr, int dbg_bucket = -1,
                                           uint4* ring = nullptr, uint32_t* phase = nullptr) {
@@ -898,11 +826,9 @@ __device__ __forceinline__ void warp_tile(WarpTile* w, Real* __restrict__ data, 
     // staged plans: row-wide tiles through the bulk-copy ring, narrower ones
     // through the per-lane cp.async ring; the register path otherwise
     bool done = false;
-    if (!PAIR && StageUnits<Real, VB, PAIR>::value > 0 && ring != nullptr && g.bulk && g.RP == 1)
+    if (STAGE != 0 && !PAIR && Stageable<Real, VB>::value && g.RP == 1 && g.VC == 1)
       done = tile_rows_bulk<Real, VB>(w, reinterpret_cast<unsigned char*>(ring), *phase, data, g, r0, r1, lane, ctrl,
                                       g.wait_limit);
-    else if (g.RP > 1)
-      done = try_tile_staged<Real, VB, PAIR>(w, ring, data, g, r0, r1, lane, rip, v0, lane_on, ctrl, dbg_bucket);
     if (!done) tile_items<Real, VB, PAIR, CG, 2, 0>(w, data, g, r0, r1, lane, rip, v0, lane_on, ctrl, dbg_bucket);
   } else if (d.kind == kStepAdj) {
     tile_adjoint<Real, VB, PAIR, CG, 2>(w, data, g, r0, r1, lane, rip, v0, lane_on, ctrl, dbg_bucket);

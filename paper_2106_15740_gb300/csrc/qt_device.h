@@ -41,13 +41,9 @@ constexpr int32_t kInNoPair = 2;  // one row per output row (no eliminated-varia
 //   Bv >  32: RP = 1; VC = ceil(Bv / 32) vector chunks per row
 //   P = passes per tile (power of two), P * VC <= kLaneItems
 constexpr int kLaneItems = 64;
-//   bulk = forward steps of row-wide tiles (RP = 1) on the staged path use
-//        the bulk-copy ring (every operand offset even, so each row pair is
-//        16-byte aligned); 0 keeps the per-lane cp.async ring
 //   wait_limit = probes of one bounded wait on a ring barrier
 struct TileGeom {
   int32_t B, Bv, RP, VC, P, R;
-  int32_t bulk;
   int32_t wait_limit;
   int64_t data_elems;  // size of the data region, for the QT_DEVICE_CHECKS build
 };

@@ -125,10 +125,11 @@ def test_persistent_equals_per_bucket_bitwise():
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 @pytest.mark.parametrize("batch", [1, 2, 3, 64])
 def test_staged_loads_equal_register_loads_bitwise(dtype, batch):
-    """The shared-memory staged operand path and the register path multiply
-    the same operands in the same order, so every edge value is identical;
-    fan-ins above the ring's capacity and odd complex64 batches fall back to
-    registers inside the same launch.  Also checked against the oracle."""
+    """The shared-memory staged operand path (bulk-copy ring, row-wide tiles)
+    and the register path multiply the same operands in the same order, so
+    every edge value is identical; buckets whose operands do not fit the ring
+    and batches without a staged form use registers in the same launch.  Also
+    checked against the oracle."""
     n, edges, p, g, b = workload("n100_p3", batch=batch)
     out = {}
     for path in ("staged", "registers"):
