@@ -163,6 +163,13 @@ typedef struct {
                              Staging applies to row-wide tiles of 16-byte vectors (complex64
                              with even B in [34, 64], complex128 with B in [17, 32]); other
                              batches keep the register path.  Both give bit-identical results */
+  int64_t checkpoint_bytes; /* gradient plans: 0 (default) keeps every forward intermediate of a
+                             network for the reverse sweep.  > 0 cuts each network's bucket order
+                             into segments whose intermediates hold at most this many bytes;
+                             only intermediates consumed in a later segment (and those of the
+                             last segment) are kept, and the reverse sweep re-runs a segment's
+                             forward steps before its adjoint steps (less memory, more traffic;
+                             results equal up to rounding order) */
 } qt_plan_options;
 
 /* Fill `opt` with defaults: batch 1, QT_C128, QT_MODE_PER_BUCKET, no gradient,

@@ -50,7 +50,7 @@ class qt_plan_options(C.Structure):
                 ("max_workspace", C.c_int64), ("group_rows", C.c_int32), ("edge_begin", C.c_int32),
                 ("edge_end", C.c_int32), ("slice", C.c_int32),
                 ("chunk_tiles", C.c_int32), ("order_trials", C.c_int32), ("order_seed", C.c_int32),
-                ("order_tau", C.c_double), ("load_path", C.c_int32)]
+                ("order_tau", C.c_double), ("load_path", C.c_int32), ("checkpoint_bytes", C.c_int64)]
 
 
 _lib = None

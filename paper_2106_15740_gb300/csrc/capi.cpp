@@ -251,6 +251,7 @@ void qt_plan_options_default(qt_plan_options* opt) {
   opt->order_seed = 0;
   opt->order_tau = 1.0;
   opt->load_path = 0;
+  opt->checkpoint_bytes = 0;
 }
 
 qt_status qt_plan_create(const qt_graph* g, int32_t p, const qt_plan_options* opt, qt_plan** out) {
@@ -269,6 +270,7 @@ qt_status qt_plan_create(const qt_graph* g, int32_t p, const qt_plan_options* op
   if (o.order_trials < 0 || o.order_trials > 100000) return fail(QT_EINVAL, "order_trials must be in [0, 100000]");
   if (!(o.order_tau >= 0.0) || !std::isfinite(o.order_tau)) return fail(QT_EINVAL, "order_tau must be finite and >= 0");
   if (o.load_path != 0 && o.load_path != 1) return fail(QT_EINVAL, "load_path must be 0 or 1");
+  if (o.checkpoint_bytes < 0) return fail(QT_EINVAL, "checkpoint_bytes must be >= 0");
   qt_plan* h = new (std::nothrow) qt_plan;
   if (!h) return fail(QT_ENOMEM, "host allocation failed");
   qt_status st = make_graph(g, &h->P.G);

@@ -105,6 +105,155 @@ static DevInput input_record(uint32_t mask, int64_t off, int32_t flags) {
   return in;
 }
 
+// One step of a gradient network in execution order: forward steps, then,
+// per checkpoint segment from the last to the first, the forward steps of
+// the segment that are re-run and the segment's adjoint steps.
+struct GradOp {
+  int32_t kind = kStepFwd;   // kStepFwd, kStepAdj, kStepZero
+  int32_t bucket = -1;
+  int32_t input = -1;        // kStepAdj: input of the bucket; -2: scalar adjoint of a multi-component network
+  bool recompute = false;    // kStepFwd: a re-run in the reverse sweep
+  int64_t out = 0;           // arena offset of the output / target (leaf target: its leaf-pool offset)
+  bool leaf = false, full = false;
+  int32_t zero_rank = 0;
+  int64_t gbar = -1;         // kStepAdj: arena offset of the bucket's output adjoint (-1: none)
+  std::vector<int64_t> loc;  // arena offset of each intermediate input (-1 for the leaf factor)
+};
+
+// Reverse-mode plan of one network with checkpointing.  The bucket order is
+// cut into segments whose produced intermediates hold at most `budget`
+// elements (one segment if budget <= 0).  A forward intermediate is kept
+// through the forward pass if its consumer lies in a later segment or it
+// belongs to the last segment; the others are freed when consumed and the
+// reverse sweep re-runs their forward steps just before their segment's
+// adjoint steps.  Every tensor shares one first-fit arena in execution order
+// (an output is allocated before its step's inputs are released); a forward
+// tensor is released once its consumer's adjoint steps are done, an output
+// adjoint once its bucket's adjoint steps are done.  Returns the arena peak;
+// *recompute_bytes gets the extra forward traffic (elements x B).
+static int64_t plan_gradient_network(const EdgePlan& ep, int64_t B, int64_t budget, int64_t al,
+                                     const std::vector<int64_t>& leaf_off, std::vector<GradOp>* ops,
+                                     std::vector<int64_t>* fwd_loc, double* recompute_elems) {
+  auto align_el = [&](int64_t x) { return (x + al - 1) / al * al; };
+  const int32_t nb = (int32_t)ep.buckets.size();
+  auto size_of = [&](int32_t i) {
+    const int32_t r = ep.buckets[i].out_rank;
+    return r > 0 ? align_el(((int64_t)1 << r) * B) : (int64_t)0;
+  };
+  std::vector<int32_t> seg(nb, 0);
+  int32_t nseg = 1;
+  if (budget > 0) {
+    int64_t acc = 0;
+    int32_t cur = 0;
+    for (int32_t i = 0; i < nb; ++i) {
+      if (acc > 0 && acc + size_of(i) > budget) {
+        ++cur;
+        acc = 0;
+      }
+      seg[i] = cur;
+      acc += size_of(i);
+    }
+    nseg = cur + 1;
+  }
+  auto kept = [&](int32_t c) {
+    const int32_t con = ep.buckets[c].consumer;
+    return seg[c] == nseg - 1 || (con >= 0 && seg[con] > seg[c]);
+  };
+  Arena A;
+  std::vector<int64_t> loc(nb, -1), gbar(nb, -1);
+  fwd_loc->assign(nb, -1);
+  *recompute_elems = 0.0;
+  auto fwd_op = [&](int32_t i, bool re) {
+    const Bucket& bk = ep.buckets[i];
+    GradOp op;
+    op.kind = kStepFwd;
+    op.bucket = i;
+    op.recompute = re;
+    if (bk.out_rank > 0) {
+      loc[i] = A.alloc(size_of(i));
+      op.out = loc[i];
+    }
+    for (size_t k = 0; k < bk.in_src.size(); ++k) op.loc.push_back(bk.in_src[k] >= 0 ? loc[bk.in_src[k]] : -1);
+    ops->push_back(op);
+    if (re) {
+      double el = (double)((int64_t)1 << bk.out_rank);
+      for (size_t k = 0; k < bk.in_src.size(); ++k)
+        if (bk.in_src[k] >= 0) el += (double)((int64_t)1 << bk.in_rank[k]);
+      *recompute_elems += el * (double)B;
+    }
+  };
+  // forward pass
+  for (int32_t i = 0; i < nb; ++i) {
+    fwd_op(i, false);
+    (*fwd_loc)[i] = loc[i];
+    for (int32_t c : ep.buckets[i].in_src)
+      if (c >= 0 && !kept(c)) {
+        A.release(loc[c], size_of(c));
+        loc[c] = -1;
+      }
+  }
+  // output adjoints of the scalar results of a network that split into
+  // components: the product of the other scalars (rank-0 adjoint steps)
+  if (ep.scalars.size() > 1)
+    for (int32_t sb : ep.scalars) {
+      gbar[sb] = A.alloc(align_el(2 * B));
+      GradOp op;
+      op.kind = kStepAdj;
+      op.bucket = sb;
+      op.input = -2;
+      op.out = gbar[sb];
+      op.full = true;
+      ops->push_back(op);
+    }
+  // reverse sweep, segment by segment
+  for (int32_t k = nseg - 1; k >= 0; --k) {
+    if (k != nseg - 1)
+      for (int32_t c = 0; c < nb; ++c)
+        if (seg[c] == k && ep.buckets[c].out_rank > 0 && loc[c] < 0) fwd_op(c, true);
+    for (int32_t b = nb - 1; b >= 0; --b) {
+      if (seg[b] != k) continue;
+      const Bucket& bk = ep.buckets[b];
+      const uint32_t all = bk.out_rank ? ((1u << bk.out_rank) - 1u) : 0u;
+      std::vector<int64_t> in_loc;
+      for (int32_t c : bk.in_src) in_loc.push_back(c >= 0 ? loc[c] : -1);
+      for (size_t kk = 0; kk < bk.in_src.size(); ++kk) {
+        GradOp op;
+        op.kind = kStepAdj;
+        op.bucket = b;
+        op.input = (int32_t)kk;
+        op.full = bk.in_mask[kk] == all;
+        op.gbar = gbar[b];
+        op.loc = in_loc;
+        const int32_t t = bk.in_src[kk];
+        if (t >= 0) {
+          gbar[t] = A.alloc(size_of(t));
+          op.out = gbar[t];
+          if (!op.full) {
+            GradOp z;
+            z.kind = kStepZero;
+            z.bucket = b;
+            z.out = gbar[t];
+            z.zero_rank = ep.buckets[t].out_rank;
+            ops->push_back(z);
+          }
+        } else {
+          op.leaf = true;
+          op.out = leaf_off[b];
+        }
+        ops->push_back(op);
+      }
+      if (gbar[b] >= 0) A.release(gbar[b], bk.out_rank > 0 ? size_of(b) : align_el(2 * B));
+      gbar[b] = -1;
+      for (int32_t c : bk.in_src)
+        if (c >= 0) {
+          A.release(loc[c], size_of(c));
+          loc[c] = -1;
+        }
+    }
+  }
+  return A.peak;
+}
+
 qt_status compile_plan(Plan* P) {
   const int32_t B = P->opt.batch;
   const int32_t es = P->elem_bytes;
@@ -116,18 +265,13 @@ qt_status compile_plan(Plan* P) {
   if (grad && !persistent) return fail(QT_EINVAL, "gradient plans need QT_MODE_PERSISTENT");
 
   // ---- per-edge memory plans (offsets relative to the edge's region) ----
-  // Forward intermediates: first-fit with free-on-consume, or kept for the
-  // adjoint sweep in gradient plans.  Adjoint buffers follow the forward
-  // arena in the same region, first-fit with free-after-use.
-  struct AdjStep {
-    int32_t bucket, input;  // kStepAdj: bucket b, input k; kStepZero: input < 0
-    int64_t target;         // target offset (region-relative, or leaf-adjoint pool index)
-    bool leaf, full;
-    int32_t zero_rank;
-  };
-  std::vector<std::vector<int64_t>> out_off(n_edges), leaf_off(n_edges), gbar_off(n_edges);
-  std::vector<std::vector<AdjStep>> adj(n_edges);
-  std::vector<int64_t> region(n_edges), fwd_peak(n_edges), cost(n_edges);
+  // Forward intermediates: first-fit with free-on-consume.  Gradient plans
+  // lay out the forward pass, the checkpoint re-runs and the adjoint buffers
+  // of a network in one first-fit arena in execution order
+  // (plan_gradient_network).
+  std::vector<std::vector<int64_t>> out_off(n_edges), leaf_off(n_edges);
+  std::vector<std::vector<GradOp>> gops(n_edges);
+  std::vector<int64_t> region(n_edges), cost(n_edges);
   int64_t leaf_pool = 0, scal_pool = 0;
   P->alg_bytes = 0.0;
   P->edge_bytes.assign(P->n_orig, 0.0);
@@ -168,63 +312,26 @@ qt_status compile_plan(Plan* P) {
       const double nin = (double)bk.in_src.size();
       P->flops += (double)B * (double)rows * (2.0 * 6.0 * (nin - 1.0) + 2.0);
     }
-    fwd_peak[e] = arena.peak;
     region[e] = arena.peak;
     if (grad) {
-      Arena aarena;
-      gbar_off[e].assign(nb, -1);
-      if (ep.scalars.size() > 1) {
-        // a network that split into components: Gbar of each scalar result is
-        // the product of the others, a rank-0 adjoint step into a 2-row buffer
-        for (int32_t sb : ep.scalars) {
-          gbar_off[e][sb] = aarena.alloc(align_el(2 * (int64_t)B));
-          AdjStep st;
-          st.bucket = sb;
-          st.input = -2;  // scalar adjoint
-          st.target = gbar_off[e][sb];
-          st.leaf = false;
-          st.full = true;
-          st.zero_rank = 0;
-          adj[e].push_back(st);
-        }
+      // reverse sweep (and checkpoint re-runs) in one arena with the forward
+      // pass; reverse traffic: per adjoint step Gbar and the other inputs
+      // read, the target written
+      double re_el = 0.0;
+      std::vector<int64_t> floc;
+      region[e] = plan_gradient_network(ep, B, P->opt.checkpoint_bytes / es, al, leaf_off[e], &gops[e], &floc,
+                                        &re_el);
+      for (int32_t i = 0; i < nb; ++i)
+        if (ep.buckets[i].out_rank > 0) out_off[e][i] = floc[i];
+      P->alg_bytes += re_el * (double)es;
+      for (const GradOp& op : gops[e]) {
+        if (op.kind != kStepAdj || op.input < 0) continue;
+        const Bucket& bk = ep.buckets[op.bucket];
+        P->alg_bytes += (double)B * es * (double)(((int64_t)1 << bk.out_rank) + ((int64_t)1 << bk.in_rank[op.input]));
+        for (size_t j = 0; j < bk.in_src.size(); ++j)
+          if ((int32_t)j != op.input && bk.in_src[j] >= 0)
+            P->alg_bytes += (double)B * es * (double)((int64_t)1 << bk.in_rank[j]);
       }
-      for (int32_t b = nb - 1; b >= 0; --b) {
-        const Bucket& bk = ep.buckets[b];
-        if ((int32_t)bk.in_src.size() + (bk.out_rank > 0 ? 1 : 0) + 1 > kDevMaxIn)
-          return fail(QT_EINVAL, "bucket fan-in above the gradient limit");
-        const uint32_t all = bk.out_rank ? ((bk.out_rank == 32) ? 0xffffffffu : ((1u << bk.out_rank) - 1u)) : 0u;
-        for (size_t k = 0; k < bk.in_src.size(); ++k) {
-          AdjStep st;
-          st.bucket = b;
-          st.input = (int32_t)k;
-          st.full = bk.in_mask[k] == all;
-          st.zero_rank = 0;
-          if (bk.in_src[k] >= 0) {
-            const int32_t t = bk.in_src[k];
-            const Bucket& tb = ep.buckets[t];
-            gbar_off[e][t] = aarena.alloc(align_el(((int64_t)1 << tb.out_rank) * B));
-            st.leaf = false;
-            st.target = gbar_off[e][t];
-            if (!st.full) {
-              AdjStep z = st;
-              z.input = -1;
-              z.zero_rank = tb.out_rank;
-              adj[e].push_back(z);
-            }
-          } else {
-            st.leaf = true;
-            st.target = leaf_off[e][b];
-          }
-          adj[e].push_back(st);
-          // reverse sweep traffic: Gbar and the other inputs read, the target written
-          P->alg_bytes += (double)B * es * (double)(((int64_t)1 << bk.out_rank) + ((int64_t)1 << bk.in_rank[k]));
-          for (size_t j = 0; j < bk.in_src.size(); ++j)
-            if (j != k && bk.in_src[j] >= 0) P->alg_bytes += (double)B * es * (double)((int64_t)1 << bk.in_rank[j]);
-        }
-        if (bk.out_rank > 0) aarena.release(gbar_off[e][b], align_el(((int64_t)1 << bk.out_rank) * B));
-        else if (gbar_off[e][b] >= 0) aarena.release(gbar_off[e][b], align_el(2 * (int64_t)B));
-      }
-      region[e] = fwd_peak[e] + aarena.peak;
     }
     cost[e] = (int64_t)ebytes * (grad ? 3 : 1);
     P->alg_bytes += ebytes * (double)B * (double)es;
@@ -295,63 +402,75 @@ qt_status compile_plan(Plan* P) {
   for (int32_t e = 0; e < n_edges; ++e) {
     const EdgePlan& ep = P->edges[e];
     const int64_t rbase = arena_base + edge_base[e];
-    auto fwd_loc = [&](int32_t b) {
-      return ep.buckets[b].out_rank == 0 ? scal_base + out_off[e][b] : rbase + out_off[e][b];
-    };
     P->edge_first[e] = (int32_t)P->buckets.size();
-    std::vector<std::vector<DevInput>> fwd_in(ep.buckets.size());
-    for (int32_t i = 0; i < (int32_t)ep.buckets.size(); ++i) {
+    auto leaf_record = [&](int32_t i) {
+      const Bucket& bk = ep.buckets[i];
+      DevLeafFactor lf;
+      std::memset(&lf, 0, sizeof(lf));
+      lf.off = leaf_off[e][i];
+      lf.rank = bk.leaf_rank;
+      lf.n_leaves = (int32_t)bk.leaves.size();
+      for (int32_t l = 0; l < lf.n_leaves; ++l) {
+        const LeafRef& Lr = bk.leaves[l];
+        lf.leaf[l] = (uint32_t)Lr.kind | (uint32_t)Lr.conj << 2 | (uint32_t)Lr.rank << 3 |
+                     (uint32_t)(Lr.bit[0] < 0 ? 0 : Lr.bit[0]) << 5 | (uint32_t)(Lr.bit[1] < 0 ? 0 : Lr.bit[1]) << 10 |
+                     (uint32_t)(Lr.fix[0] >= 0) << 15 | (uint32_t)(Lr.fix[0] > 0) << 16 |
+                     (uint32_t)(Lr.fix[1] >= 0) << 17 | (uint32_t)(Lr.fix[1] > 0) << 18 | (uint32_t)Lr.layer << 19;
+      }
+      P->leaf.push_back(lf);
+    };
+    // input k of bucket i with the intermediate at arena offset `at`
+    auto in_record = [&](int32_t i, int32_t k, int64_t at) {
+      const Bucket& bk = ep.buckets[i];
+      return bk.in_src[k] >= 0 ? input_record(bk.in_mask[k], rbase + at, 0)
+                               : input_record(bk.in_mask[k], leaf_off[e][i], kInLeaf);
+    };
+    // forward step of bucket i (output at arena offset `out`, inputs at loc)
+    auto fwd_record = [&](int32_t i, int64_t out, const std::vector<int64_t>& loc) {
       const Bucket& bk = ep.buckets[i];
       DevBucket d;
       std::memset(&d, 0, sizeof(d));
       d.kind = kStepFwd;
       d.out_rank = bk.out_rank;
       d.n_rows = (int64_t)1 << bk.out_rank;
-      d.out_off = fwd_loc(i);
+      d.out_off = bk.out_rank == 0 ? scal_base + out_off[e][i] : rbase + out;
       d.n_in = (int32_t)bk.in_src.size();
       d.dep = -1;
       d.ntask = 1;
-      for (int32_t k = 0; k < d.n_in; ++k) {
-        const int32_t src = bk.in_src[k];
-        if (src >= 0) {
-          d.in[k] = input_record(bk.in_mask[k], fwd_loc(src), 0);
-        } else {
-          d.in[k] = input_record(bk.in_mask[k], leaf_off[e][i], kInLeaf);
-          DevLeafFactor lf;
-          std::memset(&lf, 0, sizeof(lf));
-          lf.off = leaf_off[e][i];
-          lf.rank = bk.leaf_rank;
-          lf.n_leaves = (int32_t)bk.leaves.size();
-          for (int32_t l = 0; l < lf.n_leaves; ++l) {
-            const LeafRef& Lr = bk.leaves[l];
-            lf.leaf[l] = (uint32_t)Lr.kind | (uint32_t)Lr.conj << 2 | (uint32_t)Lr.rank << 3 |
-                         (uint32_t)(Lr.bit[0] < 0 ? 0 : Lr.bit[0]) << 5 |
-                         (uint32_t)(Lr.bit[1] < 0 ? 0 : Lr.bit[1]) << 10 |
-                         (uint32_t)(Lr.fix[0] >= 0) << 15 | (uint32_t)(Lr.fix[0] > 0) << 16 |
-                         (uint32_t)(Lr.fix[1] >= 0) << 17 | (uint32_t)(Lr.fix[1] > 0) << 18 |
-                         (uint32_t)Lr.layer << 19;
-          }
-          P->leaf.push_back(lf);
-        }
-        fwd_in[i].push_back(d.in[k]);
+      for (int32_t k = 0; k < d.n_in; ++k) d.in[k] = in_record(i, k, loc[k]);
+      return d;
+    };
+    if (!grad) {
+      for (int32_t i = 0; i < (int32_t)ep.buckets.size(); ++i) {
+        const Bucket& bk = ep.buckets[i];
+        std::vector<int64_t> loc;
+        for (int32_t c : bk.in_src) loc.push_back(c >= 0 ? out_off[e][c] : -1);
+        P->buckets.push_back(fwd_record(i, out_off[e][i], loc));
+        if (bk.leaf_rank > 0) leaf_record(i);
       }
-      P->buckets.push_back(d);
     }
-    for (const AdjStep& st : adj[e]) {
-      const Bucket& bk = ep.buckets[st.bucket];
+    for (const GradOp& op : gops[e]) {
+      const Bucket& bk = ep.buckets[op.bucket];
+      for (size_t k = 0; k < op.loc.size(); ++k)  // every intermediate operand is resident
+        if (bk.in_src[k] >= 0 && op.loc[k] < 0) return fail(QT_EINVAL, "internal: gradient plan reads a released tensor");
+      if (op.kind == kStepFwd) {
+        P->buckets.push_back(fwd_record(op.bucket, op.out, op.loc));
+        if (!op.recompute && bk.leaf_rank > 0) leaf_record(op.bucket);
+        continue;
+      }
       DevBucket d;
       std::memset(&d, 0, sizeof(d));
       d.dep = -1;
       d.ntask = 1;
-      if (st.input == -2) {  // scalar adjoint: product of the network's other scalar results
+      if (op.input == -2) {  // scalar adjoint: product of the network's other scalar results
         d.kind = kStepAdj;
         d.out_rank = 0;
         d.n_rows = 1;
-        d.out_off = rbase + fwd_peak[e] + st.target;
+        d.out_off = rbase + op.out;
         d.aflags = kAdjFull;
         int32_t n = 0;
         for (int32_t sb : ep.scalars)
-          if (sb != st.bucket) {
+          if (sb != op.bucket) {
             if (n + 1 >= kDevMaxIn) return fail(QT_EINVAL, "too many network components for the gradient");
             d.in[n++] = input_record(0u, scal_base + out_off[e][sb], kInNoPair);
           }
@@ -360,32 +479,34 @@ qt_status compile_plan(Plan* P) {
         P->buckets.push_back(d);
         continue;
       }
-      if (st.input < 0) {
+      if (op.kind == kStepZero) {
         d.kind = kStepZero;
-        d.out_rank = st.zero_rank;
-        d.n_rows = (int64_t)1 << st.zero_rank;
-        d.out_off = rbase + fwd_peak[e] + st.target;
+        d.out_rank = op.zero_rank;
+        d.n_rows = (int64_t)1 << op.zero_rank;
+        d.out_off = rbase + op.out;
         P->buckets.push_back(d);
         continue;
       }
+      if ((int32_t)bk.in_src.size() + (bk.out_rank > 0 ? 1 : 0) + 1 > kDevMaxIn)
+        return fail(QT_EINVAL, "bucket fan-in above the gradient limit");
       d.kind = kStepAdj;
       d.out_rank = bk.out_rank;
       d.n_rows = (int64_t)1 << bk.out_rank;
-      d.out_off = st.leaf ? st.target + lbar_shift : rbase + fwd_peak[e] + st.target;
-      d.aflags = st.full ? kAdjFull : 0;
+      d.out_off = op.leaf ? op.out + lbar_shift : rbase + op.out;
+      d.aflags = op.full ? kAdjFull : 0;
       const uint32_t all = bk.out_rank ? (1u << bk.out_rank) - 1u : 0u;
       int32_t n = 0;
-      if (gbar_off[e][st.bucket] >= 0) {  // rank > 0, or a scalar of a multi-component network
-        d.in[n++] = input_record(all, rbase + fwd_peak[e] + gbar_off[e][st.bucket], kInNoPair);
+      if (op.gbar >= 0) {  // rank > 0, or a scalar of a multi-component network
+        d.in[n++] = input_record(all, rbase + op.gbar, kInNoPair);
       } else {
         d.aflags |= kAdjUnitG;
       }
       for (int32_t j = 0; j < (int32_t)bk.in_src.size(); ++j)
-        if (j != st.input) d.in[n++] = fwd_in[st.bucket][j];
-      const uint32_t tmask = bk.in_mask[st.input];
+        if (j != op.input) d.in[n++] = in_record(op.bucket, j, op.loc[j]);
+      const uint32_t tmask = bk.in_mask[op.input];
       d.in[n] = input_record(tmask, d.out_off, 0);  // target record
       d.n_in = n;
-      if (!st.full && __builtin_popcount(all & ~tmask) >= 5 && geom_bv <= 32 && n + 2 <= kDevMaxIn) {
+      if (!op.full && __builtin_popcount(all & ~tmask) >= 5 && geom_bv <= 32 && n + 2 <= kDevMaxIn) {
         // reduction form (32 or more completions per target element): one warp
         // tile per (target row, chunk of completions); smaller targets keep the
         // atomic scatter, whose contention is then at most 32 per element

@@ -165,3 +165,41 @@ def test_gradient_with_searched_orders_matches_parameter_shift(dtype):
         ref = np.concatenate(gr.param_shift_gradient(n, edges, g[k], b[k]))
         tol = 1e-9 if dtype == "c128" else 2e-5 * max(1.0, np.abs(ref).max())
         np.testing.assert_allclose(grad[k], ref, atol=tol, rtol=0)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("budget", [1 << 9, 1 << 12, 1 << 16])
+def test_checkpointed_gradient_matches_full_sweep_and_parameter_shift(dtype, budget):
+    """Checkpoint segments (forward steps re-run in the reverse sweep) give
+    the same E and gradient as keeping every intermediate, up to rounding
+    order, and match the exact parameter-shift gradient."""
+    n, p, B = 14, 3, 2
+    edges = random_regular_graph(n, 3, 11)
+    g, b = random_angles(B, p, 91)
+    full = _grad_plan(n, edges, p, B, dtype)
+    e0, g0 = _run(full, g, b)
+    full.close()
+    plan = _grad_plan(n, edges, p, B, dtype, checkpoint_bytes=budget)
+    assert plan.stats["alg_bytes"] > 0
+    e1, g1 = _run(plan, g, b)
+    plan.close()
+    tol = 1e-12 if dtype == "c128" else 1e-5
+    np.testing.assert_allclose(e1, e0, atol=tol * len(edges), rtol=0)
+    np.testing.assert_allclose(g1, g0, atol=tol * max(1.0, np.abs(g0).max()), rtol=0)
+    for k in range(B):
+        ref = np.concatenate(gr.param_shift_gradient(n, edges, g[k], b[k]))
+        np.testing.assert_allclose(g1[k], ref, atol=1e-9 if dtype == "c128" else 2e-5 * max(1.0, np.abs(ref).max()),
+                                   rtol=0)
+
+
+def test_checkpointed_gradient_on_n60_p4_edges():
+    """A larger checkpointed plan (10 edges of the 60-vertex p = 4 graph,
+    complex128) against the unsegmented sweep."""
+    n, edges, p, g, b = workload("n60_p4")
+    out = []
+    for cb in (0, 1 << 22):
+        plan = _grad_plan(n, edges, p, 1, "c128", edge_range=(0, 10), checkpoint_bytes=cb)
+        out.append(_run(plan, g, b))
+        plan.close()
+    np.testing.assert_allclose(out[1][0], out[0][0], atol=1e-11, rtol=0)
+    np.testing.assert_allclose(out[1][1], out[0][1], atol=1e-11, rtol=0)

@@ -243,3 +243,26 @@ def test_single_network_workspace_for_every_edge(qtlib):
                 assert qb.qt_contract_workspace_size(net, order, dt) > 0
         finally:
             qb.qt_network_free(net)
+
+
+def test_checkpoint_segments_add_recompute_traffic(qtlib):
+    """Gradient plans with a checkpoint budget re-run forward steps: more
+    steps and algorithmic bytes than the unsegmented plan; a budget larger
+    than every network keeps the unsegmented plan."""
+    from paper_2106_15740_gb300 import binding as qb
+    n, edges, p, _, _ = workload("n100_p3")
+    stats = {}
+    for cb in (0, 1 << 40, 1 << 12):
+        opt = qb.qt_plan_options_default()
+        opt.batch, opt.dtype, opt.mode, opt.gradient = 1, qb.QT_C64, qb.QT_MODE_PERSISTENT, 1
+        opt.checkpoint_bytes = cb
+        pl = qb.qt_plan_create(n, np.asarray(edges, np.int32), p, opt)
+        stats[cb] = (qb.qt_plan_stats(pl), qb.qt_plan_workspace_size(pl))
+        qb.qt_plan_free(pl)
+    assert stats[1 << 40] == stats[0]
+    assert stats[1 << 12][0]["n_buckets"] > stats[0][0]["n_buckets"]
+    assert stats[1 << 12][0]["alg_bytes"] > stats[0][0]["alg_bytes"]
+    opt = qb.qt_plan_options_default()
+    opt.checkpoint_bytes = -1
+    with pytest.raises(qb.QTError):
+        qb.qt_plan_create(n, np.asarray(edges, np.int32), p, opt)
