@@ -181,10 +181,11 @@ qt_status qt_plan_create(const qt_graph* g, int32_t p, const qt_plan_options* op
 /* Workspace bytes the plan needs (device memory, 256-byte aligned base). */
 qt_status qt_plan_workspace_size(const qt_plan* plan, size_t* bytes);
 
-/* Plan statistics: number of edges, maximum width over edges, total buckets,
- * algorithmic bytes moved by the bucket kernels per call (inputs that are
- * intermediates and leaf factors read once, outputs written once, times B and
- * the element size) and real FLOPs per call. */
+/* Plan statistics: number of edges, maximum width over edges, total steps
+ * (forward, re-run and adjoint), algorithmic bytes moved by the bucket kernels
+ * per call (every intermediate input read once per step that reads it, every
+ * output written once, times B and the element size; leaf factors of rank
+ * <= 10 are not counted) and real FLOPs per call. */
 qt_status qt_plan_stats(const qt_plan* plan, int32_t* n_edges, int32_t* max_width,
                         int64_t* n_buckets, double* alg_bytes, double* flops);
 
