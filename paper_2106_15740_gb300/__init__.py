@@ -7,6 +7,8 @@ on hand-written CUDA kernels.
 
 * ``binding``  -- ctypes binding of the C ABI (include/qtensor.h), same names.
 * ``energy``   -- torch-facing helpers: device workspace, streams, plans.
+* ``optimize`` -- multi-start angle optimisation driven by the adjoint gradient.
+* ``sharding`` -- splitting a graph's edges between ranks.
 """
 from . import binding  # noqa: F401
 from .binding import QTError  # noqa: F401
