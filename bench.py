@@ -280,6 +280,42 @@ def gradient_and_comparator(dev, torch):
     return out
 
 
+def amplitude_measure(dev, torch):
+    """Single-amplitude cost on the paper's benchmark shape (§Results: one
+    amplitude of the full circuit of a random 3-regular graph, 40 vertices,
+    p = 3, the depth the paper reaches on a 4 GB laptop with ZZ and diagonal
+    gates): 8 seeded bitstrings, one angle set, complex128 (the paper's
+    precision) and complex64, searched orders."""
+    import numpy as np
+    from paper_2106_15740_gb300.amplitude import AmplitudePlan
+    from workloads import random_angles, random_regular_graph
+    n, p = 40, 3
+    edges = random_regular_graph(n, 3, 0)
+    g, b = random_angles(1, p, 1000)
+    bits = np.random.default_rng(7).integers(0, 2, (8, n)).astype(np.uint8)
+    gd, bd = torch.tensor(g, device=dev), torch.tensor(b, device=dev)
+    out = {"workload": "random 3-regular N=40 p=3 (seed 0), 8 bitstrings x 1 angle set, full-circuit ket networks, "
+                       "100 order trials per bitstring"}
+    for dtype in ("c128", "c64"):
+        plan = AmplitudePlan(n, edges, p, bits, batch=1, dtype=dtype, order_trials=100, device=dev)
+        for _ in range(2):
+            plan.amplitudes(gd, bd)
+        plan.check()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for _ in range(5):
+            plan.amplitudes(gd, bd)
+        t1.record()
+        torch.cuda.synchronize()
+        plan.check()
+        ms = t0.elapsed_time(t1) / 5
+        out[dtype] = {"amplitudes_per_s": 8 / (ms * 1e-3), "ms_per_call": ms, "max_width": int(max(plan.widths)),
+                      "alg_bytes_per_call": plan.stats["alg_bytes"],
+                      "achieved_gbs": plan.stats["alg_bytes"] / (ms * 1e-3) / 1e9}
+        plan.close()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -427,6 +463,7 @@ def run_ours(args):
             res["staged_loads"] = load_path_comparison(n, edges, p, B, g, b, dev, torch)
         if not args.no_cpu_baseline:
             res.update(gradient_and_comparator(dev, torch))
+            res["single_amplitude"] = amplitude_measure(dev, torch)
             res["per_edge_c128_loop"]["speedup_of_value"] = res["value"] / res["per_edge_c128_loop"]["edge_evals_per_s"]
             _, zz = plan.energy(g, b, edge_zz=True)
             plan.check()

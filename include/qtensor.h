@@ -264,6 +264,23 @@ size_t qt_static_scratch_bytes(void);
 qt_status qt_plan_set_wait_limit(qt_plan* plan, int32_t polls);
 qt_status qt_plan_inject_stall(qt_plan* plan, int32_t enable);
 
+/* Single amplitudes (§Results: the paper benchmarks the cost of one amplitude
+ * <x| U(gamma, beta) |+>^n of the full QAOA circuit).  Plans one ket network
+ * per bitstring over all qubits -- |+> leaves, the diagonal ZZ phases on the
+ * qubits' current indices (§Diagonal gate simplification), the mixers -- with
+ * each qubit's output index fixed to its bit, ordered, sliced and contracted
+ * like the edge networks (same options; gradient must be 0).  bits is a host
+ * array [n_strings][n_vertices] of 0/1 bytes (qubit u = byte u).  The plan is
+ * evaluated with qt_plan_amplitudes, whose amp output is a DEVICE array
+ * [n_strings][B][2] (re, im) written asynchronously on `stream` (qt_plan_check
+ * reports device failures); the per-edge calls reject amplitude plans with
+ * QT_ESTATE and qt_plan_amplitudes rejects edge plans.  qt_plan_edge_widths /
+ * _slices / _bytes report per bitstring. */
+qt_status qt_amplitude_plan_create(const qt_graph* g, int32_t p, const uint8_t* bits, int32_t n_strings,
+                                   const qt_plan_options* opt, qt_plan** out);
+qt_status qt_plan_amplitudes(qt_plan* plan, const double* gamma, const double* beta, double* amp,
+                             void* workspace, size_t ws_bytes, void* stream);
+
 /* Queue tracing (measurement; the paper has no counterpart).  With a trace
  * buffer set, every persistent launch of the plan writes, for each queue
  * task t, four uint64 words at trace[4 t .. 4 t + 3]: the device clock

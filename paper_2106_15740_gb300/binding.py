@@ -31,6 +31,7 @@ EXPORTS = [
     "qt_plan_set_profiling", "qt_plan_kernel_times", "qt_plan_energy_static",
     "qt_static_scratch_bytes", "qt_plan_set_wait_limit", "qt_plan_inject_stall", "qt_plan_edge_slices",
     "qt_plan_edge_bytes", "qt_plan_trace_size", "qt_plan_set_trace", "qt_plan_tasks",
+    "qt_amplitude_plan_create", "qt_plan_amplitudes",
 ]
 
 
@@ -89,6 +90,9 @@ def lib():
             "qt_plan_set_wait_limit": [vp, i32],
             "qt_plan_inject_stall": [vp, i32],
             "qt_plan_trace_size": [vp, C.POINTER(sz)],
+            "qt_amplitude_plan_create": [C.POINTER(qt_graph), i32, C.POINTER(C.c_uint8), i32,
+                                         C.POINTER(qt_plan_options), C.POINTER(vp)],
+            "qt_plan_amplitudes": [vp, vp, vp, vp, vp, sz, vp],
             "qt_plan_set_trace": [vp, vp, sz],
             "qt_plan_tasks": [vp, pi32, pi32, pi32, pi32, pi32, pi32],
         }
@@ -196,6 +200,20 @@ def qt_plan_create(n_vertices, edges, p, opt):
     h = C.c_void_p()
     _check(lib().qt_plan_create(C.byref(g), int(p), C.byref(opt), C.byref(h)))
     return h
+
+
+def qt_amplitude_plan_create(n_vertices, edges, p, bits, opt):
+    """bits: uint8 array [n_strings, n_vertices] of 0/1."""
+    bits = np.ascontiguousarray(np.asarray(bits, dtype=np.uint8).reshape(-1, int(n_vertices)))
+    g, keep = _graph(n_vertices, edges)
+    out = C.c_void_p()
+    _check(lib().qt_amplitude_plan_create(C.byref(g), int(p), bits.ctypes.data_as(C.POINTER(C.c_uint8)),
+                                          bits.shape[0], C.byref(opt), C.byref(out)))
+    return out
+
+
+def qt_plan_amplitudes(plan, gamma_ptr, beta_ptr, amp_ptr, ws_ptr, ws_bytes, stream):
+    _check(lib().qt_plan_amplitudes(plan, gamma_ptr, beta_ptr, amp_ptr, ws_ptr, ws_bytes, stream))
 
 
 def qt_plan_workspace_size(plan):

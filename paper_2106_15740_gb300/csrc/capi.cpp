@@ -4,8 +4,9 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
-#include <thread>
+#include <functional>
 #include <new>
+#include <thread>
 
 #include "engine.h"
 #include "kernels_api.h"
@@ -41,9 +42,13 @@ struct EdgeResult {
   std::string msg;
 };
 
-static void plan_one_edge(const Graph& G, int32_t p, int32_t e, const qt_plan_options& o, EdgeResult* r) {
+// Builds the network of unit e (an edge lightcone, or a bitstring's amplitude).
+using NetBuilder = std::function<void(int32_t, Network*)>;
+
+static void plan_one_edge(const NetBuilder& build, const char* unit, int32_t e, const qt_plan_options& o,
+                          EdgeResult* r) {
   Network net;
-  build_lightcone(G, p, e, &net);
+  build(e, &net);
   const uint64_t seed = ((uint64_t)(uint32_t)o.order_seed << 32) ^ (uint64_t)(uint32_t)e;
   const double tau = o.order_tau > 0 ? o.order_tau : 1.0;
   std::vector<int32_t> order;
@@ -53,15 +58,15 @@ static void plan_one_edge(const Graph& G, int32_t p, int32_t e, const qt_plan_op
   if (w > o.max_width) {
     if (!o.slice) {
       r->st = QT_EWIDTH;
-      r->msg = "edge " + std::to_string(e) + " has contraction width " + std::to_string(w) + " above the budget " +
-               std::to_string(o.max_width);
+      r->msg = std::string(unit) + " " + std::to_string(e) + " has contraction width " + std::to_string(w) +
+               " above the budget " + std::to_string(o.max_width);
       return;
     }
     const std::vector<int32_t> base = order;
     w = choose_slices(net, o.max_width, kMaxSlices, base, o.order_trials, tau, seed, &sliced, &order);
     if (w > o.max_width) {
       r->st = QT_EWIDTH;
-      r->msg = "edge " + std::to_string(e) + " needs more than " + std::to_string(kMaxSlices) +
+      r->msg = std::string(unit) + " " + std::to_string(e) + " needs more than " + std::to_string(kMaxSlices) +
                " sliced variables to reach width " + std::to_string(o.max_width);
       return;
     }
@@ -91,14 +96,15 @@ static void plan_one_edge(const Graph& G, int32_t p, int32_t e, const qt_plan_op
   r->n_sliced = (int32_t)sliced.size();
 }
 
-static qt_status plan_edges(const Graph& G, int32_t p, const qt_plan_options& o, int32_t e0, int32_t e1, Plan* P) {
+static qt_status plan_units(const NetBuilder& build, const char* unit, const qt_plan_options& o, int32_t e0,
+                            int32_t e1, Plan* P) {
   const int32_t m = e1 - e0;
   std::vector<EdgeResult> res(m);
   const int32_t hw = (int32_t)std::max(1u, std::thread::hardware_concurrency());
   const int32_t n_threads = std::min({hw, m, 64});
   std::atomic<int32_t> next{0};
   auto worker = [&]() {
-    for (int32_t k = next.fetch_add(1); k < m; k = next.fetch_add(1)) plan_one_edge(G, p, e0 + k, o, &res[k]);
+    for (int32_t k = next.fetch_add(1); k < m; k = next.fetch_add(1)) plan_one_edge(build, unit, e0 + k, o, &res[k]);
   };
   if (n_threads <= 1) {
     worker();
@@ -254,9 +260,7 @@ void qt_plan_options_default(qt_plan_options* opt) {
   opt->checkpoint_bytes = 0;
 }
 
-qt_status qt_plan_create(const qt_graph* g, int32_t p, const qt_plan_options* opt, qt_plan** out) {
-  if (!out) return fail(QT_EINVAL, "out is NULL");
-  if (p < 1 || p > 64) return fail(QT_EINVAL, "p must be in [1, 64]");
+static qt_status check_options(const qt_plan_options* opt, qt_plan_options* out) {
   qt_plan_options o;
   qt_plan_options_default(&o);
   if (opt) o = *opt;
@@ -271,6 +275,16 @@ qt_status qt_plan_create(const qt_graph* g, int32_t p, const qt_plan_options* op
   if (!(o.order_tau >= 0.0) || !std::isfinite(o.order_tau)) return fail(QT_EINVAL, "order_tau must be finite and >= 0");
   if (o.load_path != 0 && o.load_path != 1) return fail(QT_EINVAL, "load_path must be 0 or 1");
   if (o.checkpoint_bytes < 0) return fail(QT_EINVAL, "checkpoint_bytes must be >= 0");
+  *out = o;
+  return QT_OK;
+}
+
+qt_status qt_plan_create(const qt_graph* g, int32_t p, const qt_plan_options* opt, qt_plan** out) {
+  if (!out) return fail(QT_EINVAL, "out is NULL");
+  if (p < 1 || p > 64) return fail(QT_EINVAL, "p must be in [1, 64]");
+  qt_plan_options o;
+  qt_status st0 = check_options(opt, &o);
+  if (st0 != QT_OK) return st0;
   qt_plan* h = new (std::nothrow) qt_plan;
   if (!h) return fail(QT_ENOMEM, "host allocation failed");
   qt_status st = make_graph(g, &h->P.G);
@@ -285,7 +299,9 @@ qt_status qt_plan_create(const qt_graph* g, int32_t p, const qt_plan_options* op
     } else {
       h->P.opt.edge_begin = o.edge_begin;
       h->P.opt.edge_end = e1;
-      st = plan_edges(h->P.G, p, o, o.edge_begin, e1, &h->P);
+      const Graph& G = h->P.G;
+      st = plan_units([&](int32_t e, Network* net) { build_lightcone(G, p, e, net); }, "edge", o, o.edge_begin, e1,
+                      &h->P);
     }
   }
   if (st == QT_OK) st = compile_plan(&h->P);
@@ -295,6 +311,52 @@ qt_status qt_plan_create(const qt_graph* g, int32_t p, const qt_plan_options* op
   }
   *out = h;
   return QT_OK;
+}
+
+qt_status qt_amplitude_plan_create(const qt_graph* g, int32_t p, const uint8_t* bits, int32_t n_strings,
+                                   const qt_plan_options* opt, qt_plan** out) {
+  if (!out) return fail(QT_EINVAL, "out is NULL");
+  if (p < 1 || p > 64) return fail(QT_EINVAL, "p must be in [1, 64]");
+  if (!bits || n_strings < 1) return fail(QT_EINVAL, "bitstrings are NULL or empty");
+  qt_plan_options o;
+  qt_status st = check_options(opt, &o);
+  if (st != QT_OK) return st;
+  if (o.gradient) return fail(QT_EINVAL, "amplitude plans have no gradient");
+  qt_plan* h = new (std::nothrow) qt_plan;
+  if (!h) return fail(QT_ENOMEM, "host allocation failed");
+  st = make_graph(g, &h->P.G);
+  if (st == QT_OK) {
+    const int32_t n = h->P.G.n;
+    for (int64_t i = 0; i < (int64_t)n_strings * n && st == QT_OK; ++i)
+      if (bits[i] > 1) st = fail(QT_EINVAL, "bitstring bytes must be 0 or 1");
+  }
+  if (st == QT_OK) {
+    h->P.p = p;
+    h->P.opt = o;
+    h->P.opt.edge_begin = 0;
+    h->P.opt.edge_end = n_strings;
+    h->P.elem_bytes = o.dtype == QT_C64 ? 8 : 16;
+    h->P.amplitude = true;
+    const Graph& G = h->P.G;
+    std::vector<uint8_t> x(bits, bits + (size_t)n_strings * G.n);
+    st = plan_units([&](int32_t s, Network* net) { build_amplitude_network(G, p, x.data() + (size_t)s * G.n, s, net); },
+                    "bitstring", o, 0, n_strings, &h->P);
+  }
+  if (st == QT_OK) st = compile_plan(&h->P);
+  if (st != QT_OK) {
+    delete h;
+    return st;
+  }
+  *out = h;
+  return QT_OK;
+}
+
+qt_status qt_plan_amplitudes(qt_plan* plan, const double* gamma, const double* beta, double* amp, void* workspace,
+                             size_t ws_bytes, void* stream) {
+  if (!plan) return fail(QT_EINVAL, "plan is NULL");
+  if (!plan->P.amplitude) return fail(QT_ESTATE, "not an amplitude plan (use qt_plan_energy)");
+  if (!amp) return fail(QT_EINVAL, "amp is NULL");
+  return run_plan(&plan->P, gamma, beta, nullptr, amp, nullptr, workspace, ws_bytes, stream);
 }
 
 qt_status qt_plan_workspace_size(const qt_plan* plan, size_t* bytes) {
@@ -340,6 +402,7 @@ qt_status qt_plan_edge_slices(const qt_plan* plan, int32_t* slices) {
 qt_status qt_plan_energy(qt_plan* plan, const double* gamma, const double* beta, double* energy, double* edge_zz,
                          double* grad, void* workspace, size_t ws_bytes, void* stream) {
   if (!plan) return fail(QT_EINVAL, "plan is NULL");
+  if (plan->P.amplitude) return fail(QT_ESTATE, "amplitude plan: use qt_plan_amplitudes");
   return run_plan(&plan->P, gamma, beta, energy, edge_zz, grad, workspace, ws_bytes, stream);
 }
 
@@ -351,6 +414,7 @@ qt_status qt_plan_check(qt_plan* plan, void* stream) {
 qt_status qt_plan_energy_host(qt_plan* plan, const double* gamma, const double* beta, double* energy,
                               double* edge_zz, double* grad, void* workspace, size_t ws_bytes, void* stream) {
   if (!plan) return fail(QT_EINVAL, "plan is NULL");
+  if (plan->P.amplitude) return fail(QT_ESTATE, "amplitude plan: use qt_plan_amplitudes");
   Plan& P = plan->P;
   const int32_t B = P.opt.batch, p = P.p, ne = P.n_orig;
   qt_status st;

@@ -52,6 +52,9 @@ struct Plan {
   double alg_bytes = 0.0, flops = 0.0;
   std::vector<double> edge_bytes;          // per planned graph edge: algorithmic bytes of its networks
 
+  // the plan's units are bitstrings of single amplitudes, not edges
+  bool amplitude = false;
+
   // every forward-step input starts on a 16-byte boundary (bulk-copy ring usable)
   bool bulk_ok = false;
 

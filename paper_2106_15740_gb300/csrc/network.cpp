@@ -105,4 +105,39 @@ void build_lightcone(const Graph& g, int32_t p, int32_t edge, Network* net) {
   add(QT_T_OBS, (int8_t)p, 0, ket(k, top[k]), -1);
 }
 
+// Single amplitude <x| U(gamma, beta) |+>^n (§Results: the paper's benchmark
+// is one amplitude of the full circuit; §Diagonal gate simplification applies
+// as above).  Every qubit takes part.  Qubit u carries ket variables
+// v_u^0 .. v_u^{p-1} (canonical ids: qubits ascending, u * p + l); its output
+// variable v_u^p is projected on bit x_u, so it is no variable at all: the
+// last mixer's `new` slot is fixed to x_u.  Tensors: |+> on v_u^0, the
+// diagonal ZZ_q on (v_a^{q-1}, v_b^{q-1}) for every edge, MIX_q on
+// (v_u^q, v_u^{q-1}).  No bra copy and no observable.
+void build_amplitude_network(const Graph& g, int32_t p, const uint8_t* bits, int32_t index, Network* net) {
+  auto var = [&](int32_t u, int32_t l) { return u * p + l; };
+  net->p = p;
+  net->edge = index;
+  net->n_vars = g.n * p;
+  net->tensors.clear();
+  auto add = [&](int8_t kind, int8_t layer, int32_t a, int32_t b) {
+    Tensor t;
+    t.kind = kind;
+    t.layer = layer;
+    t.conj = 0;
+    t.rank = b < 0 && kind != QT_T_MIX ? 1 : 2;
+    t.v[0] = a;
+    t.v[1] = b;
+    net->tensors.push_back(t);
+    return &net->tensors.back();
+  };
+  for (int32_t u = 0; u < g.n; ++u) add(QT_T_PLUS, 0, var(u, 0), -1);
+  for (int32_t q = 1; q <= p; ++q) {
+    for (size_t e = 0; e < g.eu.size(); ++e) add(QT_T_ZZ, (int8_t)q, var(g.eu[e], q - 1), var(g.ev[e], q - 1));
+    for (int32_t u = 0; u < g.n; ++u) {
+      Tensor* t = add(QT_T_MIX, (int8_t)q, q < p ? var(u, q) : -1, var(u, q - 1));
+      if (q == p) t->fix[0] = (int8_t)(bits[u] ? 1 : 0);
+    }
+  }
+}
+
 }  // namespace qt

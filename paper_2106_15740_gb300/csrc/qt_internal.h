@@ -45,6 +45,9 @@ struct Network {
 
 // Build the reverse-lightcone network of edge `edge` (structure only).
 void build_lightcone(const Graph& g, int32_t p, int32_t edge, Network* net);
+// Build the ket network of the single amplitude <x|psi> of the full circuit,
+// x given as one byte (0 or 1) per qubit; `index` labels the network.
+void build_amplitude_network(const Graph& g, int32_t p, const uint8_t* bits, int32_t index, Network* net);
 
 // ---------------------------------------------------------------- order ----
 // Greedy min-fill over the interaction graph; returns the width (and, if

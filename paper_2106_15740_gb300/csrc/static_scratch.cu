@@ -65,6 +65,7 @@ extern "C" qt_status qt_plan_energy_static(qt_plan* plan, const double* gamma, c
   using namespace qt;
   if (!plan) return fail(QT_EINVAL, "plan is NULL");
   Plan& P = plan->P;
+  if (P.amplitude) return fail(QT_ESTATE, "amplitude plan: use qt_plan_amplitudes");
   if (P.ws.total > kStaticScratchBytes)
     return fail(QT_ENOMEM, "plan needs " + std::to_string(P.ws.total) + " bytes of scratch; the static scratch holds " +
                                std::to_string(kStaticScratchBytes) + " bytes (use qt_plan_energy with a workspace)");

@@ -266,3 +266,29 @@ def test_checkpoint_segments_add_recompute_traffic(qtlib):
     opt.checkpoint_bytes = -1
     with pytest.raises(qb.QTError):
         qb.qt_plan_create(n, np.asarray(edges, np.int32), p, opt)
+
+
+def test_amplitude_plans_validate_and_size(qtlib):
+    """Amplitude networks: one per bitstring, no gradient, 0/1 bytes only;
+    on a 40-vertex p = 3 graph the searched order is narrower than min-fill."""
+    from paper_2106_15740_gb300 import binding as qb
+    n, p = 40, 3
+    edges = random_regular_graph(n, 3, 53)
+    bits = np.zeros((2, n), dtype=np.uint8)
+    widths = {}
+    for trials in (0, 50):
+        opt = qb.qt_plan_options_default()
+        opt.mode, opt.order_trials = qb.QT_MODE_PERSISTENT, trials
+        pl = qb.qt_amplitude_plan_create(n, edges, p, bits, opt)
+        widths[trials] = list(qb.qt_plan_edge_widths(pl, 2))
+        assert qb.qt_plan_stats(pl)["n_edges"] == 2
+        qb.qt_plan_free(pl)
+    assert max(widths[50]) <= max(widths[0])
+    opt = qb.qt_plan_options_default()
+    bad = bits.copy()
+    bad[0, 3] = 2
+    with pytest.raises(qb.QTError):
+        qb.qt_amplitude_plan_create(n, edges, p, bad, opt)
+    opt.gradient, opt.mode = 1, qb.QT_MODE_PERSISTENT
+    with pytest.raises(qb.QTError):
+        qb.qt_amplitude_plan_create(n, edges, p, bits, opt)
