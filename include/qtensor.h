@@ -281,6 +281,24 @@ qt_status qt_amplitude_plan_create(const qt_graph* g, int32_t p, const uint8_t* 
 qt_status qt_plan_amplitudes(qt_plan* plan, const double* gamma, const double* beta, double* amp,
                              void* workspace, size_t ws_bytes, void* stream);
 
+/* Representation cost study (§Results, Fig. diag_costs and diag_costs_vs_n:
+ * the contraction cost of one amplitude <0...0|psi> of a QAOA circuit with
+ * and without the gate simplifications).  Host only, no device memory.  For
+ * representation `rep` (qt_representation) the amplitude's interaction graph
+ * is ordered by greedy min-fill, or by the cheapest of min-fill and
+ * `order_trials` seeded randomised greedy orders (seed `seed`); *n_vars gets
+ * the free variables, *width the contraction width (largest bucket result
+ * rank) and *log2_cost log2 of sum_b 2^{|U_b|}, the paper's FLOP measure up
+ * to a constant factor.  QT_EINVAL for a bad graph, p or rep. */
+typedef enum {
+  QT_REP_DEFAULT = 0,     /* CNOT-Z-CNOT ZZ gates and H-Z-H mixers, every gate with new indices */
+  QT_REP_DIAGONAL = 1,    /* the same gates, diagonal gates (and CNOT controls) keep their index */
+  QT_REP_ZZ = 2,          /* ZZ and X mixer gates, both with new indices */
+  QT_REP_ZZ_DIAGONAL = 3  /* ZZ gates keep both indices (the energy and amplitude networks) */
+} qt_representation;
+qt_status qt_representation_cost(const qt_graph* g, int32_t p, int32_t rep, int32_t order_trials, int32_t seed,
+                                 int32_t* n_vars, int32_t* width, double* log2_cost);
+
 /* Queue tracing (measurement; the paper has no counterpart).  With a trace
  * buffer set, every persistent launch of the plan writes, for each queue
  * task t, four uint64 words at trace[4 t .. 4 t + 3]: the device clock

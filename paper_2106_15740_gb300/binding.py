@@ -18,6 +18,7 @@ LIB_PATH = Path(__file__).resolve().parent / "libqtensor_gb300.so"
 QT_OK, QT_EINVAL, QT_ENOMEM, QT_EWIDTH, QT_ECUDA, QT_ETIMEOUT, QT_ESTATE = range(7)
 QT_C128, QT_C64 = 0, 1
 QT_MODE_PER_BUCKET, QT_MODE_PERSISTENT = 0, 1
+QT_REP_DEFAULT, QT_REP_DIAGONAL, QT_REP_ZZ, QT_REP_ZZ_DIAGONAL = range(4)
 STATUS_NAMES = {0: "QT_OK", 1: "QT_EINVAL", 2: "QT_ENOMEM", 3: "QT_EWIDTH", 4: "QT_ECUDA",
                 5: "QT_ETIMEOUT", 6: "QT_ESTATE"}
 
@@ -31,7 +32,7 @@ EXPORTS = [
     "qt_plan_set_profiling", "qt_plan_kernel_times", "qt_plan_energy_static",
     "qt_static_scratch_bytes", "qt_plan_set_wait_limit", "qt_plan_inject_stall", "qt_plan_edge_slices",
     "qt_plan_edge_bytes", "qt_plan_trace_size", "qt_plan_set_trace", "qt_plan_tasks",
-    "qt_amplitude_plan_create", "qt_plan_amplitudes",
+    "qt_amplitude_plan_create", "qt_plan_amplitudes", "qt_representation_cost",
 ]
 
 
@@ -93,6 +94,7 @@ def lib():
             "qt_amplitude_plan_create": [C.POINTER(qt_graph), i32, C.POINTER(C.c_uint8), i32,
                                          C.POINTER(qt_plan_options), C.POINTER(vp)],
             "qt_plan_amplitudes": [vp, vp, vp, vp, vp, sz, vp],
+            "qt_representation_cost": [C.POINTER(qt_graph), i32, i32, i32, i32, pi32, pi32, pd],
             "qt_plan_set_trace": [vp, vp, sz],
             "qt_plan_tasks": [vp, pi32, pi32, pi32, pi32, pi32, pi32],
         }
@@ -214,6 +216,15 @@ def qt_amplitude_plan_create(n_vertices, edges, p, bits, opt):
 
 def qt_plan_amplitudes(plan, gamma_ptr, beta_ptr, amp_ptr, ws_ptr, ws_bytes, stream):
     _check(lib().qt_plan_amplitudes(plan, gamma_ptr, beta_ptr, amp_ptr, ws_ptr, ws_bytes, stream))
+
+
+def qt_representation_cost(n_vertices, edges, p, rep, order_trials=0, seed=0):
+    """(n_vars, width, log2 cost) of the amplitude network in representation rep."""
+    g, keep = _graph(n_vertices, edges)
+    nv, w, c = C.c_int32(), C.c_int32(), C.c_double()
+    _check(lib().qt_representation_cost(C.byref(g), int(p), int(rep), int(order_trials), int(seed), C.byref(nv),
+                                        C.byref(w), C.byref(c)))
+    return nv.value, w.value, c.value
 
 
 def qt_plan_workspace_size(plan):

@@ -351,6 +351,27 @@ qt_status qt_amplitude_plan_create(const qt_graph* g, int32_t p, const uint8_t* 
   return QT_OK;
 }
 
+qt_status qt_representation_cost(const qt_graph* g, int32_t p, int32_t rep, int32_t order_trials, int32_t seed,
+                                 int32_t* n_vars, int32_t* width, double* log2_cost) {
+  if (p < 1 || p > 64) return fail(QT_EINVAL, "p must be in [1, 64]");
+  if (rep < QT_REP_DEFAULT || rep > QT_REP_ZZ_DIAGONAL) return fail(QT_EINVAL, "unknown representation");
+  if (order_trials < 0 || order_trials > 100000) return fail(QT_EINVAL, "order_trials must be in [0, 100000]");
+  Graph G;
+  qt_status st = make_graph(g, &G);
+  if (st != QT_OK) return st;
+  Network net;
+  build_representation_network(G, p, rep, &net);
+  std::vector<int32_t> order;
+  double cost = 0.0;
+  const int32_t w = order_trials > 0 ? search_order(net, order_trials, 1.0, (uint64_t)(uint32_t)seed << 32, 0, &order,
+                                                    &cost)
+                                     : min_fill_order(net, &order, &cost);
+  if (n_vars) *n_vars = net.n_vars;
+  if (width) *width = w;
+  if (log2_cost) *log2_cost = std::log2(cost);
+  return QT_OK;
+}
+
 qt_status qt_plan_amplitudes(qt_plan* plan, const double* gamma, const double* beta, double* amp, void* workspace,
                              size_t ws_bytes, void* stream) {
   if (!plan) return fail(QT_EINVAL, "plan is NULL");

@@ -140,4 +140,111 @@ void build_amplitude_network(const Graph& g, int32_t p, const uint8_t* bits, int
   }
 }
 
+// Interaction structure of the amplitude <0...0| U(gamma, beta) |+>^n in one
+// of the four gate representations that §Results compares (structure only:
+// every gate is a clique on its variables, written as pairwise rank-2
+// tensors, which is the same interaction graph, so the result serves the
+// ordering code and its cost, not a contraction).  A gate opens a new
+// variable for every qubit index it does not keep; an index a diagonal gate
+// keeps (§Diagonal gate simplification) is shared.
+//   QT_REP_DEFAULT:     ZZ(gamma) = CNOT (I x Z^{2 gamma}) CNOT, mixer = H Z^{2 beta} H
+//                       (Fig. 1), every gate with new output indices
+//   QT_REP_DIAGONAL:    the same gates; Z rotations keep their index, and a
+//                       CNOT keeps its control index (it is diagonal in it)
+//   QT_REP_ZZ:          ZZ(gamma) as one two-qubit gate and the mixer as one
+//                       X^{2 beta} gate, both with new output indices
+//   QT_REP_ZZ_DIAGONAL: ZZ(gamma) keeps both indices (the hot path's network)
+// Each qubit's output index is projected on 0 and so is no variable.
+void build_representation_network(const Graph& g, int32_t p, int32_t rep, Network* net) {
+  std::vector<std::vector<int32_t>> cliques;
+  std::vector<int32_t> cur(g.n), owner;
+  int32_t nv = 0;
+  for (int32_t u = 0; u < g.n; ++u) {
+    cur[u] = nv++;
+    owner.push_back(u);
+    cliques.push_back({cur[u]});  // |+>
+  }
+  auto fresh = [&](int32_t u) {
+    owner.push_back(u);
+    return cur[u] = nv++;
+  };
+  const bool diag = rep == QT_REP_DIAGONAL || rep == QT_REP_ZZ_DIAGONAL;
+  for (int32_t q = 1; q <= p; ++q) {
+    for (size_t e = 0; e < g.eu.size(); ++e) {
+      const int32_t a = g.eu[e], b = g.ev[e];
+      if (rep == QT_REP_ZZ_DIAGONAL) {
+        cliques.push_back({cur[a], cur[b]});
+      } else if (rep == QT_REP_ZZ) {
+        const int32_t a0 = cur[a], b0 = cur[b];
+        cliques.push_back({a0, b0, fresh(a), fresh(b)});
+      } else {
+        for (int32_t half = 0; half < 2; ++half) {  // CNOT, Z^{2 gamma} on the target, CNOT
+          const int32_t a0 = cur[a], b0 = cur[b];
+          if (diag)
+            cliques.push_back({a0, b0, fresh(b)});
+          else
+            cliques.push_back({a0, b0, fresh(a), fresh(b)});
+          if (half == 0) {
+            if (diag)
+              cliques.push_back({cur[b]});
+            else {
+              const int32_t t0 = cur[b];
+              cliques.push_back({t0, fresh(b)});
+            }
+          }
+        }
+      }
+    }
+    for (int32_t u = 0; u < g.n; ++u) {
+      if (rep == QT_REP_ZZ || rep == QT_REP_ZZ_DIAGONAL) {
+        const int32_t u0 = cur[u];
+        cliques.push_back({u0, fresh(u)});
+      } else {  // H, Z^{2 beta}, H
+        int32_t u0 = cur[u];
+        cliques.push_back({u0, fresh(u)});
+        if (diag)
+          cliques.push_back({cur[u]});
+        else {
+          u0 = cur[u];
+          cliques.push_back({u0, fresh(u)});
+        }
+        u0 = cur[u];
+        cliques.push_back({u0, fresh(u)});
+      }
+    }
+  }
+  // project the outputs: drop each qubit's last variable; number the rest
+  // canonically, qubits ascending and each qubit's variables in the order
+  // its gates opened them (for ZZ + diagonal: the amplitude network's ids)
+  std::vector<int32_t> keep, remap(nv, -1);
+  std::vector<char> dropped(nv, 0);
+  for (int32_t u = 0; u < g.n; ++u) dropped[cur[u]] = 1;
+  for (int32_t v = 0; v < nv; ++v)
+    if (!dropped[v]) keep.push_back(v);
+  std::stable_sort(keep.begin(), keep.end(), [&](int32_t a, int32_t b) { return owner[a] < owner[b]; });
+  const int32_t m = (int32_t)keep.size();
+  for (int32_t i = 0; i < m; ++i) remap[keep[i]] = i;
+  net->p = p;
+  net->edge = -1;
+  net->n_vars = m;
+  net->tensors.clear();
+  for (const auto& c : cliques) {
+    std::vector<int32_t> vs;
+    for (int32_t v : c)
+      if (remap[v] >= 0) vs.push_back(remap[v]);
+    for (size_t i = 0; i < vs.size(); ++i)
+      for (size_t j = i; j < vs.size(); ++j) {
+        if (i == j && vs.size() > 1) continue;
+        Tensor t;
+        t.kind = QT_T_ZZ;
+        t.layer = 0;
+        t.conj = 0;
+        t.rank = i == j ? 1 : 2;
+        t.v[0] = vs[i];
+        t.v[1] = i == j ? -1 : vs[j];
+        net->tensors.push_back(t);
+      }
+  }
+}
+
 }  // namespace qt

@@ -48,6 +48,9 @@ void build_lightcone(const Graph& g, int32_t p, int32_t edge, Network* net);
 // Build the ket network of the single amplitude <x|psi> of the full circuit,
 // x given as one byte (0 or 1) per qubit; `index` labels the network.
 void build_amplitude_network(const Graph& g, int32_t p, const uint8_t* bits, int32_t index, Network* net);
+// Interaction structure (pairwise cliques) of the amplitude <0...0|psi> in
+// one of the qt_representation gate representations (ordering cost only).
+void build_representation_network(const Graph& g, int32_t p, int32_t rep, Network* net);
 
 // ---------------------------------------------------------------- order ----
 // Greedy min-fill over the interaction graph; returns the width (and, if

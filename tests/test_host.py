@@ -292,3 +292,46 @@ def test_amplitude_plans_validate_and_size(qtlib):
     opt.gradient, opt.mode = 1, qb.QT_MODE_PERSISTENT
     with pytest.raises(qb.QTError):
         qb.qt_amplitude_plan_create(n, edges, p, bits, opt)
+
+
+@pytest.mark.parametrize("n,p", [(20, 1), (20, 3), (40, 2)])
+def test_representation_variable_counts(qtlib, n, p):
+    """Free variables of the amplitude network per representation (outputs
+    projected): ZZ+diagonal n p; ZZ adds two per ZZ gate; diagonal keeps the
+    Z rotations and CNOT controls but opens one index per CNOT target and
+    per Hadamard; default opens one per gate index."""
+    from paper_2106_15740_gb300 import binding as qb
+    edges = random_regular_graph(n, 3, 1)
+    m = len(edges)
+    expect = {qb.QT_REP_ZZ_DIAGONAL: n * p, qb.QT_REP_ZZ: n * p + 2 * m * p,
+              qb.QT_REP_DIAGONAL: p * (2 * n + 2 * m), qb.QT_REP_DEFAULT: p * (3 * n + 5 * m)}
+    for rep, nv in expect.items():
+        assert qb.qt_representation_cost(n, edges, p, rep)[0] == nv
+
+
+def test_zz_diagonal_representation_is_the_amplitude_network(qtlib):
+    """The cost study's ZZ + diagonal structure is the interaction graph of the
+    amplitude plans: same min-fill width."""
+    from paper_2106_15740_gb300 import binding as qb
+    for n, p, seed in ((30, 2, 3), (40, 3, 4)):
+        edges = random_regular_graph(n, 3, seed)
+        _, w, _ = qb.qt_representation_cost(n, edges, p, qb.QT_REP_ZZ_DIAGONAL)
+        opt = qb.qt_plan_options_default()
+        opt.mode = qb.QT_MODE_PERSISTENT
+        pl = qb.qt_amplitude_plan_create(n, edges, p, np.zeros((1, n), np.uint8), opt)
+        assert int(qb.qt_plan_edge_widths(pl, 1)[0]) == w
+        qb.qt_plan_free(pl)
+
+
+def test_simplifications_lower_width_and_cost_at_depth(qtlib):
+    """At p = 3 on 40 vertices the diagonal and ZZ simplifications cut the
+    width and cost by orders of magnitude (the paper's Table 1 regime)."""
+    from paper_2106_15740_gb300 import binding as qb
+    from paper_2106_15740_gb300.cost_study import LAPTOP_BYTES, fits
+    edges = random_regular_graph(40, 3, 0)
+    r = {rep: qb.qt_representation_cost(40, edges, 3, rep, 10, 0) for rep in range(4)}
+    assert r[qb.QT_REP_ZZ_DIAGONAL][1] <= r[qb.QT_REP_DIAGONAL][1] < r[qb.QT_REP_DEFAULT][1]
+    assert r[qb.QT_REP_DEFAULT][2] - r[qb.QT_REP_ZZ_DIAGONAL][2] >= 10  # >= 1000x fewer FLOPs
+    assert fits(r[qb.QT_REP_ZZ_DIAGONAL][1], LAPTOP_BYTES) and not fits(r[qb.QT_REP_DEFAULT][1], LAPTOP_BYTES)
+    with pytest.raises(qb.QTError):
+        qb.qt_representation_cost(40, edges, 3, 7)
