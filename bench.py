@@ -41,9 +41,9 @@ WORKLOAD = dict(name="n100_p4", batch=64, dtype="c64", order_trials=100)
 # contraction order fixes the traffic): otherwise the traffic is reported as
 # null until that kernel and plan are captured again.
 TRAFFIC_CAPTURES = [
-    # greedy min-fill order
-    {"sources_sha256_16": "d790be0bed269da2", "alg_bytes_per_angle_set": 18702118912 / 4,
-     "bytes_per_angle_set": 18494862336 / 4},
+    # orders searched per edge (100 trials), the bench plan; register load path
+    {"sources_sha256_16": "1de256cd8adf133e", "alg_bytes_per_angle_set": 5170666432 / 4,
+     "bytes_per_angle_set": (2160890368 + 2468238080) / 4},
 ]
 
 
@@ -244,7 +244,7 @@ def gradient_and_comparator(dev, torch):
     contraction (one kernel launch per bucket, edge after edge, one angle set
     at a time) on the gradient workload and on the bench workload."""
     from paper_2106_15740_gb300.energy import EnergyPlan
-    from workloads import workload
+    from workloads import random_angles, workload
     out = {}
     n, edges, p, g, b = workload("n60_p4")
     gd, bd = torch.tensor(g, device=dev), torch.tensor(b, device=dev)
@@ -259,7 +259,14 @@ def gradient_and_comparator(dev, torch):
     plan = EnergyPlan(n, edges, p, batch=1, dtype="c128", mode="per_bucket", device=dev)
     ms_loop = _time_calls(plan, gd, bd, False, 3, torch)
     plan.close()
+    gb, bb = random_angles(16, p, 1003)
+    plan = EnergyPlan(n, edges, p, batch=16, dtype="c64", mode="persistent", gradient=True, device=dev,
+                      order_trials=WORKLOAD.get("order_trials", 0))
+    ms_grad16 = _time_calls(plan, torch.tensor(gb, device=dev), torch.tensor(bb, device=dev), True, 3, torch)
+    plan.close()
     out["grad"] = {"metric": "energy-grad evals/sec", "value": 1e3 / ms_grad, "unit": "grad_evals/s",
+                   "batched_16": {"value": 16e3 / ms_grad16, "ms_per_call": ms_grad16,
+                                  "what": "16 angle sets per call (a multi-start optimiser's batch)"},
                    "ms_per_eval": ms_grad, "dtype": "c64",
                    "workload": "random 3-regular N=60 p=4 (seed 3), 90 edge lightcones, dE/dgamma and dE/dbeta "
                                "(8 angles) by the adjoint bucket sweep, one angle set",
@@ -345,6 +352,15 @@ def run_ours(args):
                     or "load_path" in WORKLOAD)
     grad = bool(WORKLOAD.get("gradient", False))
     gamma, beta = random_angles(B, p, 1002 + 7919 * rank)
+    tuned = None
+    if not profile_only:
+        # tile size and grouping picked on this device, before the timed region
+        from paper_2106_15740_gb300.energy import autotune
+        best, timings = autotune(n, edges, p, batch=B, dtype=WORKLOAD["dtype"], device=dev, reps=3,
+                                 lane_items=(16, 32, 64), group_rows=(0,),
+                                 order_trials=WORKLOAD.get("order_trials", 0))
+        WORKLOAD["lane_items"], WORKLOAD["group_rows"] = best["lane_items"], best["group_rows"]
+        tuned = {"choice": best, "ms_per_candidate": {f"lane_items={k[0]}": round(v, 3) for k, v in timings.items()}}
     t_plan = time.perf_counter()
     plan = EnergyPlan(n, edges, p, batch=B, dtype=WORKLOAD["dtype"], mode="persistent", device=dev,
                       edge_range=WORKLOAD.get("edge_range"), lane_items=WORKLOAD.get("lane_items", 0),
@@ -455,6 +471,8 @@ def run_ours(args):
                           "ms_per_step_direct_calls": ms_direct},
             "clocks": clk,
         }
+        if tuned:
+            res["autotune"] = tuned
         if profile_only:
             res["profile_only"] = f"{WORKLOAD} (not the bench workload)"
         if not profile_only and WORKLOAD.get("order_trials", 0):

@@ -218,11 +218,13 @@ def qaoa_energy(plan, gamma, beta):
 
 
 def autotune(n_vertices, edges, p, batch=1, dtype="c64", gradient=False, device="cuda:0", reps=3,
-             lane_items=None, group_rows=(0, 1 << 20), max_workspace=0, edge_range=None, gamma=None, beta=None):
+             lane_items=None, group_rows=(0, 1 << 20), max_workspace=0, edge_range=None, gamma=None, beta=None,
+             **plan_options):
     """Pick the warp-tile size and bucket grouping of a persistent plan by
     timing each candidate on the device (CUDA events around `reps` calls after
     two warm-ups).  Returns (best_options, {candidate: ms}).  Angles default
-    to zeros (the work does not depend on their values)."""
+    to zeros (the work does not depend on their values).  Further keyword
+    arguments (order_trials, load_path, ...) go to every candidate plan."""
     device = torch.device(device)
     if lane_items is None:
         lane_items = (16, 32, 64) if batch >= 16 else (8, 16, 32)
@@ -233,7 +235,7 @@ def autotune(n_vertices, edges, p, batch=1, dtype="c64", gradient=False, device=
         for gr in group_rows:
             plan = EnergyPlan(n_vertices, edges, p, batch=batch, dtype=dtype, mode="persistent",
                               gradient=gradient, device=device, lane_items=li, group_rows=gr,
-                              max_workspace=max_workspace, edge_range=edge_range)
+                              max_workspace=max_workspace, edge_range=edge_range, **plan_options)
             for _ in range(2):
                 plan.energy(g, b, grad=gradient)
             plan.check()
