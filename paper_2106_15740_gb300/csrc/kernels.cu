@@ -142,12 +142,13 @@ __device__ __forceinline__ int32_t ld_acquire(const int32_t* p) {
 // Consecutive tiles of one bucket on a warp reuse its record and skip the
 // wait (done counters only grow).
 //
-// STAGE (the plan's load path): 0 every operand load goes to registers;
-// 1 forward steps of row-wide tiles move their intermediate operands through
-// a per-warp bulk-copy ring in dynamic shared memory (kRingBytesPerWarp per
-// warp, see kernels.cuh).
+// STAGE: 0 generic register path; 1 forward steps of row-wide tiles move
+// their intermediate operands through a per-warp bulk-copy ring in dynamic
+// shared memory (kRingBytesPerWarp per warp, see kernels.cuh; the plan's
+// load_path 1); 2 row-wide plans on the register path: every forward tile
+// takes tile_rows_regs and the generic forward tile is not compiled in.
 template <class Real, int VB, bool PAIR, bool GRAD, int STAGE>
-__global__ void __launch_bounds__(256, STAGE ? 2 : 4) persistent_kernel(const DevBucket* __restrict__ buckets,
+__global__ void __launch_bounds__(256, STAGE == 1 ? 2 : 4) persistent_kernel(const DevBucket* __restrict__ buckets,
                                                             const DevTask* __restrict__ tasks, int32_t n_tasks,
                                                             DevCtrl* ctrl, int32_t* done, Real* __restrict__ data,
                                                             const TileGeom g, int32_t spin_limit,
@@ -156,9 +157,9 @@ __global__ void __launch_bounds__(256, STAGE ? 2 : 4) persistent_kernel(const De
   extern __shared__ uint4 ring_all[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   WarpTile* w = &tiles[wid];
-  uint4* ring = STAGE ? ring_all + (size_t)wid * (kRingBytesPerWarp / 16) : nullptr;
+  uint4* ring = STAGE == 1 ? ring_all + (size_t)wid * (kRingBytesPerWarp / 16) : nullptr;
   uint32_t phase = 0;  // bulk-copy ring: parity each slot waits for next
-  if (STAGE != 0) {
+  if (STAGE == 1) {
     if (lane == 0) {
       for (int k = 0; k < kBulkSlots; ++k) mbar_init(&w->mbar[k], 1);
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -472,7 +473,16 @@ static const void* persistent_fn_t(int dtype, int32_t B) {
 
 template <bool GRAD>
 static const void* persistent_fn_g(int dtype, int stage, int32_t B) {
-  return stage != 0 ? persistent_fn_t<GRAD, 1>(dtype, B) : persistent_fn_t<GRAD, 0>(dtype, B);
+  if (stage == 1) return persistent_fn_t<GRAD, 1>(dtype, B);
+  if (stage == 2) return persistent_fn_t<GRAD, 2>(dtype, B);
+  return persistent_fn_t<GRAD, 0>(dtype, B);
+}
+
+// Kernel variant of a launch: the staged ring (load path 1), else the lean
+// row path for row-wide tile shapes, else the generic register path.
+static int persistent_stage(int dtype, int32_t load_path, bool bulk_ok, int32_t B) {
+  if (!staged_supported(dtype, B)) return 0;
+  return load_path != 0 && bulk_ok ? 1 : 2;
 }
 
 static const void* persistent_fn(int dtype, bool grad, int stage, int32_t B) {
@@ -482,7 +492,7 @@ static const void* persistent_fn(int dtype, bool grad, int stage, int32_t B) {
 
 // Dynamic shared memory of a persistent launch (the staged ring of 8 warps).
 static int persistent_smem(int dtype, int stage, int32_t B) {
-  return stage != 0 && staged_supported(dtype, B) ? 8 * dev::kRingBytesPerWarp : 0;
+  return stage == 1 && staged_supported(dtype, B) ? 8 * dev::kRingBytesPerWarp : 0;
 }
 
 cudaError_t launch_persistent(int dtype, bool grad, int32_t load_path, bool bulk_ok, const DevBucket* buckets,
@@ -492,7 +502,7 @@ cudaError_t launch_persistent(int dtype, bool grad, int32_t load_path, bool bulk
   TileGeom g = tile_geom(dtype, B, lane_items);
   g.data_elems = data_elems;
   g.wait_limit = 1 << 22;
-  const int stage = load_path != 0 && bulk_ok ? 1 : 0;
+  const int stage = persistent_stage(dtype, load_path, bulk_ok, B);
   const void* fn = persistent_fn(dtype, grad, stage, B);
   const int smem = persistent_smem(dtype, stage, B);
   if (smem > 0) {
@@ -506,7 +516,7 @@ cudaError_t launch_persistent(int dtype, bool grad, int32_t load_path, bool bulk
 
 cudaError_t persistent_occupancy(int dtype, bool grad, int32_t load_path, bool bulk_ok, int32_t B,
                                  int* blocks_per_sm) {
-  const int stage = load_path != 0 && bulk_ok ? 1 : 0;
+  const int stage = persistent_stage(dtype, load_path, bulk_ok, B);
   const void* fn = persistent_fn(dtype, grad, stage, B);
   const int smem = persistent_smem(dtype, stage, B);
   if (smem > 0) {

@@ -381,6 +381,58 @@ __device__ __forceinline__ void tile_items(WarpTile* w, Real* __restrict__ data,
   }
 }
 
+// Row-wide forward tile on the register path (RP = 1, VC = 1: every lane of
+// the warp works on the same output row, lane l on vector l).  The same loads
+// and products as tile_items, two rows per iteration, with the row's operand
+// rows read straight from the pass table (the lane part is 0) and no
+// per-item bookkeeping; bit-identical to tile_items.
+template <class Real, int VB>
+__device__ __forceinline__ void tile_rows_regs(WarpTile* w, Real* __restrict__ data, const TileGeom& g, int64_t r0,
+                                               int64_t r1, int lane) {
+  using PK = Pack<Real, VB>;
+  const DevBucket& d = w->d;
+  const int n_in = d.n_in;
+  const int nrows = (int)(r1 - r0);
+  const bool on = lane < g.Bv;
+  const int64_t B = g.B;
+  const int64_t lo = (int64_t)(on ? lane : 0) * VB;  // idle lanes read vector 0 and store nothing
+  for (int q = 0; q < nrows; q += 2) {
+    const int qb = q + 1 < nrows ? q + 1 : q;
+    PK p0[2], p1[2];
+    for (int i = 0; i < n_in; ++i) {
+      const bool leaf = d.in[i].flags & kInLeaf;
+      const int64_t base = d.in[i].off + lo;
+      const int64_t e0 = base + (int64_t)(2 * w->tab[i][q]) * B;
+      const int64_t e1 = base + (int64_t)(2 * w->tab[i][qb]) * B;
+      const PK a00 = ldv_in<Real, VB, true>(data, e0, leaf);
+      const PK a01 = ldv_in<Real, VB, true>(data, e0 + B, leaf);
+      const PK a10 = ldv_in<Real, VB, true>(data, e1, leaf);
+      const PK a11 = ldv_in<Real, VB, true>(data, e1 + B, leaf);
+      if (i == 0) {
+        p0[0] = a00;
+        p1[0] = a01;
+        p0[1] = a10;
+        p1[1] = a11;
+      } else {
+        pmul<Real, VB>(p0[0], a00);
+        pmul<Real, VB>(p1[0], a01);
+        pmul<Real, VB>(p0[1], a10);
+        pmul<Real, VB>(p1[1], a11);
+      }
+    }
+    if (on) {
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        if (u == 1 && qb == q) break;
+        PK o;
+#pragma unroll
+        for (int v = 0; v < VB; ++v) o.c[v] = cadd<Real>(p0[u].c[v], p1[u].c[v]);
+        stv<Real, VB>(data, d.out_off + (r0 + q + u) * B + lo, o);
+      }
+    }
+  }
+}
+
 // ------------------------------------------------ shared-memory staged path --
 //
 // The register path above keeps at most 2 rows' loads of one input in flight
@@ -823,12 +875,22 @@ __device__ __forceinline__ void warp_tile(WarpTile* w, Real* __restrict__ data, 
   }
   __syncwarp();
   if (!GRAD || d.kind == kStepFwd) {
-    // staged plans: row-wide tiles through the bulk-copy ring, narrower ones
-    // through the per-lane cp.async ring; the register path otherwise
+    // STAGE 1: row-wide tiles through the bulk-copy ring (the register path
+    // for buckets the ring cannot hold); STAGE 2: every forward tile of a
+    // row-wide plan on the lean row path (the launcher picks STAGE 2 only for
+    // that shape; any other shape is reported, not computed); STAGE 0: the
+    // generic register path
     bool done = false;
-    if (STAGE != 0 && !PAIR && Stageable<Real, VB>::value && g.RP == 1 && g.VC == 1)
+    if (STAGE == 1 && !PAIR && Stageable<Real, VB>::value && g.RP == 1 && g.VC == 1)
       done = tile_rows_bulk<Real, VB>(w, reinterpret_cast<unsigned char*>(ring), *phase, data, g, r0, r1, lane, ctrl,
                                       g.wait_limit);
+    if (STAGE == 2) {
+      if (g.RP == 1 && g.VC == 1)
+        tile_rows_regs<Real, VB>(w, data, g, r0, r1, lane);
+      else if (lane == 0 && ctrl != nullptr)
+        atomicCAS(&ctrl->status, 0, (int32_t)QT_EINVAL);
+      done = true;
+    }
     if (!done) tile_items<Real, VB, PAIR, CG, 2, 0>(w, data, g, r0, r1, lane, rip, v0, lane_on, ctrl, dbg_bucket);
   } else if (d.kind == kStepAdj) {
     tile_adjoint<Real, VB, PAIR, CG, 2>(w, data, g, r0, r1, lane, rip, v0, lane_on, ctrl, dbg_bucket);
