@@ -574,10 +574,13 @@ qt_status compile_plan(Plan* P) {
         DevBucket& d = P->buckets[gb];
         const int64_t nt = (step_tiles(d, geom.R) + d.span - 1) / d.span;  // chunks of this step
         d.dep = prev[s];
-        if (step_tiles(d, geom.R) == 1 && d.n_rows <= group_rows) {
+        // consecutive tiny forward steps of a chain run on one warp; reverse-sweep
+        // steps are not grouped (a warp running hundreds of them back to back
+        // left the rest of the GPU waiting on its chain)
+        if (d.kind == kStepFwd && step_tiles(d, geom.R) == 1 && d.n_rows <= group_rows) {
           int32_t k = 1;
-          while (bi[s] + k < ns_e && k < kMaxGroup && P->buckets[gb + k].n_rows <= group_rows &&
-                 step_tiles(P->buckets[gb + k], geom.R) == 1)
+          while (bi[s] + k < ns_e && k < kMaxGroup && P->buckets[gb + k].kind == kStepFwd &&
+                 P->buckets[gb + k].n_rows <= group_rows && step_tiles(P->buckets[gb + k], geom.R) == 1)
             ++k;
           for (int32_t j = 0; j < k; ++j) {
             P->buckets[gb + j].ntask = 1;

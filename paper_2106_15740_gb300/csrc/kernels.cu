@@ -302,38 +302,54 @@ __device__ __forceinline__ double2 leaf_deriv(uint32_t w, uint32_t z, const doub
 // Per leaf factor F and angle set b: for every leaf l of F that carries an
 // angle, sum_z Lbar_F[z] * dl(z) * prod_{l' != l} l'(z) (FP64), written to
 // part[(f * B + b) * kDevMaxLeaves + l] (zero for leaves without an angle).
+// One warp per (F, b); lanes split the 2^rank index values z.  For each z the
+// products over the other leaves come from a prefix pass (Lbar times the
+// leaves before l) and a suffix pass (the leaves after l), so a z costs
+// O(n_leaves) instead of O(n_leaves^2); each leaf's sum is reduced over the
+// warp with shuffles.
 template <class Real>
 __global__ void leafgrad_kernel(const DevLeafFactor* __restrict__ lf, int32_t n_lf, int64_t lbar_shift,
                                 const double* __restrict__ trig, int32_t p, int32_t B,
                                 const Real* __restrict__ data, double2* __restrict__ part) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)n_lf * B) return;
-  const int32_t f = (int32_t)(idx / B), b = (int32_t)(idx % B);
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= (int64_t)n_lf * B) return;
+  const int32_t f = (int32_t)(warp / B), b = (int32_t)(warp % B);
   const DevLeafFactor F = lf[f];
-  for (int32_t l = 0; l < kDevMaxLeaves; ++l) {
-    double ar = 0.0, ai = 0.0;
-    const uint32_t w = l < F.n_leaves ? F.leaf[l] : 0u;
-    const uint32_t kind = w & 3u;
-    if (l < F.n_leaves && (kind == 1u || kind == 2u)) {
+  const int32_t n = F.n_leaves;
+  double2 acc[kDevMaxLeaves], pre[kDevMaxLeaves], val[kDevMaxLeaves];
+  for (int32_t l = 0; l < kDevMaxLeaves; ++l) acc[l] = make_double2(0.0, 0.0);
+  for (uint32_t z = (uint32_t)lane; z < (1u << F.rank); z += 32u) {
+    const int64_t o = F.off + lbar_shift + (int64_t)z * B + b;
+    double2 run = make_double2((double)data[2 * o], (double)data[2 * o + 1]);  // Lbar_F[z]
+    for (int32_t l = 0; l < n; ++l) {  // prefix: Lbar times the leaves before l
+      const uint32_t w = F.leaf[l];
       const int32_t layer = leaf_layer(w);
-      const double* tr = trig + ((int64_t)b * p + layer - 1) * 4;
-      for (uint32_t z = 0; z < (1u << F.rank); ++z) {
-        double2 t = leaf_deriv(w, z, tr);
-        for (int32_t l2 = 0; l2 < F.n_leaves; ++l2) {
-          if (l2 == l) continue;
-          const uint32_t w2 = F.leaf[l2];
-          const int32_t layer2 = leaf_layer(w2);
-          const double* tr2 = trig + ((int64_t)b * p + (layer2 > 0 ? layer2 - 1 : 0)) * 4;
-          t = cmul<double>(t, leaf_value<double>(w2, z, tr2));
-        }
-        const int64_t o = F.off + lbar_shift + (int64_t)z * B + b;
-        const double gr = (double)data[2 * o], gi = (double)data[2 * o + 1];
-        ar += gr * t.x - gi * t.y;
-        ai += gr * t.y + gi * t.x;
-      }
+      val[l] = leaf_value<double>(w, z, trig + ((int64_t)b * p + (layer > 0 ? layer - 1 : 0)) * 4);
+      pre[l] = run;
+      run = cmul<double>(run, val[l]);
     }
-    part[idx * kDevMaxLeaves + l] = make_double2(ar, ai);
+    double2 suf = make_double2(1.0, 0.0);  // the leaves after l
+    for (int32_t l = n - 1; l >= 0; --l) {
+      const uint32_t w = F.leaf[l];
+      const uint32_t kind = w & 3u;
+      if (kind == 1u || kind == 2u) {
+        const double2 d = leaf_deriv(w, z, trig + ((int64_t)b * p + leaf_layer(w) - 1) * 4);
+        const double2 t = cmul<double>(cmul<double>(pre[l], d), suf);
+        acc[l].x += t.x;
+        acc[l].y += t.y;
+      }
+      suf = cmul<double>(suf, val[l]);
+    }
   }
+  for (int32_t l = 0; l < n; ++l)
+    for (int off = 16; off > 0; off >>= 1) {
+      acc[l].x += __shfl_xor_sync(0xffffffffu, acc[l].x, off);
+      acc[l].y += __shfl_xor_sync(0xffffffffu, acc[l].y, off);
+    }
+  if (lane == 0)
+    for (int32_t l = 0; l < kDevMaxLeaves; ++l)
+      part[warp * kDevMaxLeaves + l] = l < n ? acc[l] : make_double2(0.0, 0.0);
 }
 
 // dZ_e/dtheta for every edge e, angle set b and angle theta (0..p-1: gamma,
@@ -545,11 +561,11 @@ cudaError_t launch_gradient(int dtype, const DevLeafFactor* lf, int32_t n_lf, co
   const int64_t n1 = (int64_t)n_lf * B;
   if (n1 > 0) {
     if (dtype == QT_C64)
-      dev::leafgrad_kernel<float><<<(int)((n1 + 127) / 128), 128, 0, s>>>(lf, n_lf, lbar_shift, trig, p, B,
-                                                                        (const float*)data, (double2*)part);
+      dev::leafgrad_kernel<float><<<(int)((n1 * 32 + 127) / 128), 128, 0, s>>>(lf, n_lf, lbar_shift, trig, p, B,
+                                                                             (const float*)data, (double2*)part);
     else
-      dev::leafgrad_kernel<double><<<(int)((n1 + 127) / 128), 128, 0, s>>>(lf, n_lf, lbar_shift, trig, p, B,
-                                                                         (const double*)data, (double2*)part);
+      dev::leafgrad_kernel<double><<<(int)((n1 * 32 + 127) / 128), 128, 0, s>>>(lf, n_lf, lbar_shift, trig, p, B,
+                                                                              (const double*)data, (double2*)part);
   }
   const int64_t n2 = (int64_t)n_edges * B * 2 * p;
   dev::edgegrad_kernel<<<(int)((n2 + 127) / 128), 128, 0, s>>>(lf, leaf_first, n_edges, p, B, (const double2*)part, dz);
