@@ -454,6 +454,7 @@ def run_ours(args):
                        "alg_bytes_per_step": alg,
                        "n_vertices": n, "p": p, "edges": len(edges), "angle_sets_per_gpu": B,
                        "max_width": int(plan.stats["max_width"]), "buckets": plan.stats["n_buckets"],
+                       "width_histogram": {int(w): int(c) for w, c in zip(*np.unique(plan.widths, return_counts=True))},
                        "workspace_gb": round(plan.ws_bytes / 1e9, 2),
                        "l2": "working set larger than L2 (intermediates streamed through HBM every step)",
                        "plan_host_s": round(t_plan, 3)},

@@ -245,3 +245,47 @@ def test_searched_orders_match_oracle_on_n100_p3(dtype):
     for ei in range(len(edges)):
         ref = lc.lightcone_zz(n, edges, p, g[0], b[0], ei)[0]
         assert abs(zz[ei, 0] - ref.real) <= tol and abs(zz[ei, 1] - ref.imag) <= tol
+
+
+def test_tree_like_lightcones_give_equal_values():
+    """Edges whose radius-p neighbourhood is a tree have isomorphic lightcone
+    networks, so their <Z_j Z_k> must agree (to rounding: their orders and
+    variable ids differ); at p = 1 they also equal the triangle-free closed
+    form sin(4b) sin(2g) cos^2(2g) of a 3-regular graph."""
+    from oracle import closed_form as cf
+    from oracle.lightcone import reverse_lightcone
+    for p, B in ((1, 2), (2, 2)):
+        n = 100
+        edges = random_regular_graph(n, 3, 17)
+        g, b = random_angles(B, p, 18)
+        tree = 2 * (2 ** (p + 1) - 1)
+        like = [e for e in range(len(edges)) if len(reverse_lightcone(n, edges, p, e)[0]) == tree]
+        assert len(like) >= 10
+        plan = _plan(n, edges, p, B, "c128", "persistent")
+        _, zz = _run(plan, g, b)
+        plan.close()
+        for k in range(B):
+            vals = zz[like, k, 0]
+            assert vals.max() - vals.min() <= 1e-12
+            if p == 1:
+                assert abs(vals[0] - cf.p1_zz(n, edges, like[0], g[k][0], b[k][0])) <= 1e-12
+
+
+@pytest.mark.parametrize("n", [3, 4, 5, 6, 7, 8])
+def test_tiny_graph_sweep_against_state_vector(n):
+    """Every small random graph shape (G(n, 1/2), seeded) at p = 1..3, both
+    precisions, both modes."""
+    for seed in (1, 2):
+        edges = erdos_renyi_graph(n, 0.5, 100 * n + seed)
+        if len(edges) == 0:
+            continue
+        for p in (1, 2, 3):
+            g, b = random_angles(2, p, 7 * n + p + seed)
+            refs = [sv.edge_zz(n, edges, g[k], b[k]) for k in range(2)]
+            for dtype in ("c128", "c64"):
+                for mode in ("per_bucket", "persistent"):
+                    plan = _plan(n, edges, p, 2, dtype, mode)
+                    _, zz = _run(plan, g, b)
+                    plan.close()
+                    for k in range(2):
+                        np.testing.assert_allclose(zz[:, k, 0], refs[k], atol=TOL[dtype], rtol=0)
