@@ -38,10 +38,9 @@ __device__ __forceinline__ uint32_t leaf_bit1(uint32_t w, uint32_t z) {
 }
 
 template <class Real>
-__device__ __forceinline__ typename Cx<Real>::T leaf_value(uint32_t w, uint32_t z, const double* tr) {
+__device__ __forceinline__ typename Cx<Real>::T leaf_value_bits(uint32_t w, uint32_t b0, uint32_t b1,
+                                                                const double* tr) {
   const uint32_t kind = w & 3u, conj = (w >> 2) & 1u;
-  const uint32_t b0 = leaf_bit0(w, z);
-  const uint32_t b1 = leaf_bit1(w, z);
   typename Cx<Real>::T v;
   if (kind == 0u) {
     v.x = (Real)0.70710678118654752440;
@@ -64,6 +63,57 @@ __device__ __forceinline__ typename Cx<Real>::T leaf_value(uint32_t w, uint32_t 
   }
   if (conj) v.y = -v.y;
   return v;
+}
+
+template <class Real>
+__device__ __forceinline__ typename Cx<Real>::T leaf_value(uint32_t w, uint32_t z, const double* tr) {
+  return leaf_value_bits<Real>(w, leaf_bit0(w, z), leaf_bit1(w, z), tr);
+}
+
+// Leaf factors for up to LeafTabB<Real> angle sets: one block per factor.
+// Each leaf takes at most 4 values (its two slot bits) per angle set; the
+// block tabulates them in 32 KB of shared memory once, then every element of
+// the factor is the product, in leaf order, of one table entry per leaf --
+// the same values multiplied in the same order as leaf_factor_kernel.
+template <class Real> struct LeafTabB { static constexpr int value = 32768 / (kDevMaxLeaves * 4 * 2 * (int)sizeof(Real)); };
+
+template <class Real>
+__global__ void leaf_factor_tab_kernel(const DevLeafFactor* __restrict__ lf, int32_t n_lf,
+                                       const double* __restrict__ trig, int32_t p, int32_t B,
+                                       Real* __restrict__ data) {
+  using C = typename Cx<Real>::T;
+  __shared__ C tab[kDevMaxLeaves][4][LeafTabB<Real>::value];
+  __shared__ uint32_t words[kDevMaxLeaves];
+  for (int32_t f = blockIdx.x; f < n_lf; f += gridDim.x) {
+    const DevLeafFactor& F = lf[f];
+    const int32_t nl = F.n_leaves;
+    __syncthreads();  // the previous factor's readers are done with the table
+    for (int32_t i = threadIdx.x; i < nl * 4 * B; i += blockDim.x) {
+      const int32_t l = i / (4 * B), c = (i / B) & 3, b = i % B;
+      const uint32_t w = F.leaf[l];
+      const int32_t layer = leaf_layer(w);
+      // a fixed slot reads its fixed value whatever the combination says
+      const uint32_t b0 = (w >> 15) & 1u ? (w >> 16) & 1u : (uint32_t)(c & 1);
+      const uint32_t b1 = (w >> 17) & 1u ? (w >> 18) & 1u : (uint32_t)(c >> 1);
+      tab[l][c][b] = leaf_value_bits<Real>(w, b0, b1, trig + ((int64_t)b * p + (layer > 0 ? layer - 1 : 0)) * 4);
+    }
+    if (threadIdx.x < nl) words[threadIdx.x] = F.leaf[threadIdx.x];
+    __syncthreads();
+    const int32_t n = (1 << F.rank) * B;
+    for (int32_t idx = threadIdx.x; idx < n; idx += blockDim.x) {
+      const uint32_t z = idx / B;
+      const int32_t b = idx - (int32_t)z * B;
+      C acc;
+      acc.x = 1;
+      acc.y = 0;
+      for (int32_t l = 0; l < nl; ++l) {
+        const uint32_t w = words[l];
+        const uint32_t c = ((z >> ((w >> 5) & 31u)) & 1u) | (((z >> ((w >> 10) & 31u)) & 1u) << 1);
+        acc = cmul<Real>(acc, tab[l][c][b]);
+      }
+      reinterpret_cast<C*>(data)[F.off + idx] = acc;
+    }
+  }
 }
 
 template <class Real>
@@ -246,15 +296,18 @@ __global__ void __launch_bounds__(256, STAGE == 1 ? 2 : 4) persistent_kernel(con
 
 // Final step (§QAOA algorithm, E = sum_k E_k): per angle set, the value of
 // each edge network is the product of its scalar bucket results, taken in
-// FP64, and E = sum_e (1 - Re <Z_j Z_k>_e) / 2 in a fixed order.
+// FP64, and E = sum_e (1 - Re <Z_j Z_k>_e) / 2 in a fixed order.  One warp per
+// angle set: lane l sums the edges l, l + 32, ... in order, then a fixed
+// butterfly adds the 32 partial sums.
 template <class Real>
 __global__ void energy_kernel(const Real* __restrict__ data, const int64_t* __restrict__ scal_off,
                               const int32_t* __restrict__ scal_begin, const int32_t* __restrict__ net_first,
                               int32_t n_edges, int32_t B, double* __restrict__ energy, double* __restrict__ edge_zz) {
-  const int32_t b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= B) return;
+  const int32_t b = (int32_t)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (b >= B) return;  // whole warps leave together
   double E = 0.0;
-  for (int32_t e = 0; e < n_edges; ++e) {
+  for (int32_t e = lane; e < n_edges; e += 32) {
     // <Z_j Z_k> = sum over the edge's networks (2^s slices) of the product of
     // each network's scalar results
     double zr = 0.0, zi = 0.0;
@@ -276,7 +329,8 @@ __global__ void energy_kernel(const Real* __restrict__ data, const int64_t* __re
     }
     E += 0.5 * (1.0 - zr);
   }
-  if (energy) energy[b] = E;
+  for (int off = 16; off > 0; off >>= 1) E += __shfl_xor_sync(0xffffffffu, E, off);
+  if (energy && lane == 0) energy[b] = E;
 }
 
 // Derivative of one leaf value with respect to its own angle (the ZZ angle
@@ -404,6 +458,15 @@ cudaError_t launch_trig(const double* gamma, const double* beta, int32_t p, int3
 cudaError_t launch_leaf_factors(int dtype, const DevLeafFactor* lf, int32_t n_lf, const double* trig,
                                 int32_t p, int32_t B, void* data, cudaStream_t s) {
   if (n_lf == 0) return cudaSuccess;
+  const int32_t tab_b = dtype == QT_C64 ? dev::LeafTabB<float>::value : dev::LeafTabB<double>::value;
+  if (B <= tab_b) {
+    const int32_t grid = n_lf < 65535 ? n_lf : 65535;
+    if (dtype == QT_C64)
+      dev::leaf_factor_tab_kernel<float><<<grid, 256, 0, s>>>(lf, n_lf, trig, p, B, (float*)data);
+    else
+      dev::leaf_factor_tab_kernel<double><<<grid, 256, 0, s>>>(lf, n_lf, trig, p, B, (double*)data);
+    return cudaGetLastError();
+  }
   const int32_t grid = n_lf < 152 * 16 ? n_lf : 152 * 16;
   if (dtype == QT_C64)
     dev::leaf_factor_kernel<float><<<grid, 128, 0, s>>>(lf, n_lf, trig, p, B, (float*)data);
@@ -545,7 +608,7 @@ cudaError_t persistent_occupancy(int dtype, bool grad, int32_t load_path, bool b
 cudaError_t launch_energy(int dtype, const void* data, const int64_t* scal_off, const int32_t* scal_begin,
                           const int32_t* net_first, int32_t n_edges, int32_t B, double* energy, double* edge_zz,
                           cudaStream_t s) {
-  const int32_t grid = (B + 127) / 128;
+  const int32_t grid = (B + 3) / 4;  // 4 warps (angle sets) per block
   if (dtype == QT_C64)
     dev::energy_kernel<float><<<grid, 128, 0, s>>>((const float*)data, scal_off, scal_begin, net_first, n_edges, B,
                                                    energy, edge_zz);
