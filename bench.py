@@ -42,8 +42,8 @@ WORKLOAD = dict(name="n100_p4", batch=64, dtype="c64", order_trials=100)
 # null until that kernel and plan are captured again.
 TRAFFIC_CAPTURES = [
     # orders searched per edge (100 trials), the bench plan; register load path (lean row tile)
-    {"sources_sha256_16": "59835d19a0f22d12", "alg_bytes_per_angle_set": 5170666432 / 4,
-     "bytes_per_angle_set": (2160084736 + 2472047872) / 4},
+    {"sources_sha256_16": "471f7b1c1c3aeddd", "alg_bytes_per_angle_set": 5170666432 / 4,
+     "bytes_per_angle_set": (2153464576 + 2471153920) / 4},
 ]
 
 
