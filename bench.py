@@ -357,10 +357,11 @@ def run_ours(args):
         # tile size and grouping picked on this device, before the timed region
         from paper_2106_15740_gb300.energy import autotune
         best, timings = autotune(n, edges, p, batch=B, dtype=WORKLOAD["dtype"], device=dev, reps=3,
-                                 lane_items=(16, 32, 64), group_rows=(0,),
+                                 lane_items=(16, 32, 64), group_rows=(0, 32),
                                  order_trials=WORKLOAD.get("order_trials", 0))
         WORKLOAD["lane_items"], WORKLOAD["group_rows"] = best["lane_items"], best["group_rows"]
-        tuned = {"choice": best, "ms_per_candidate": {f"lane_items={k[0]}": round(v, 3) for k, v in timings.items()}}
+        tuned = {"choice": best,
+                 "ms_per_candidate": {f"lane_items={k[0]},group_rows={k[1]}": round(v, 3) for k, v in timings.items()}}
     t_plan = time.perf_counter()
     plan = EnergyPlan(n, edges, p, batch=B, dtype=WORKLOAD["dtype"], mode="persistent", device=dev,
                       edge_range=WORKLOAD.get("edge_range"), lane_items=WORKLOAD.get("lane_items", 0),
