@@ -544,10 +544,11 @@ template <bool GRAD, int ST>
 static const void* persistent_fn_t(int dtype, int32_t B) {
   const int vb = vector_width(dtype, B);
   const bool pair = (B == 1);
+  constexpr int PST = ST == 2 ? 2 : 0;  // one-angle-set plans: lean pair path or generic
   if (dtype == QT_C64)
-    return pair ? pk_fn<float, 1, true, GRAD, 0>()
+    return pair ? pk_fn<float, 1, true, GRAD, PST>()
                 : (vb == 2 ? pk_fn<float, 2, false, GRAD, ST>() : pk_fn<float, 1, false, GRAD, 0>());
-  return pair ? pk_fn<double, 1, true, GRAD, 0>() : pk_fn<double, 1, false, GRAD, ST>();
+  return pair ? pk_fn<double, 1, true, GRAD, PST>() : pk_fn<double, 1, false, GRAD, ST>();
 }
 
 template <bool GRAD>
@@ -557,15 +558,17 @@ static const void* persistent_fn_g(int dtype, int stage, int32_t B) {
   return persistent_fn_t<GRAD, 0>(dtype, B);
 }
 
-// Kernel variant of a launch: the staged ring (load path 1), else the lean
-// row path for row-wide tile shapes, else the generic register path.
+// Kernel variant of a launch: the lean pair path for one angle set, the
+// staged ring (load path 1) or the lean row path for row-wide tile shapes,
+// else the generic register path.
 static int persistent_stage(int dtype, int32_t load_path, bool bulk_ok, int32_t B) {
+  if (B == 1) return 2;  // one angle set: the lean pair path
   if (!staged_supported(dtype, B)) return 0;
   return load_path != 0 && bulk_ok ? 1 : 2;
 }
 
 static const void* persistent_fn(int dtype, bool grad, int stage, int32_t B) {
-  if (!staged_supported(dtype, B)) stage = 0;
+  if (!staged_supported(dtype, B) && !(B == 1 && stage == 2)) stage = 0;
   return grad ? persistent_fn_g<true>(dtype, stage, B) : persistent_fn_g<false>(dtype, stage, B);
 }
 

@@ -435,6 +435,58 @@ __device__ __forceinline__ void tile_rows_regs(WarpTile* w, Real* __restrict__ d
   }
 }
 
+// Forward tile of the one-angle-set layout on the register path (PAIR: B = 1,
+// rows x = 0, 1 of an input adjacent; RP = 32 rows per pass, lane l on row
+// r0 + pass * 32 + l).  The same loads and products as tile_items, two passes
+// per iteration, without its per-item bookkeeping; bit-identical to it.
+template <class Real>
+__device__ __forceinline__ void tile_pairs_regs(WarpTile* w, Real* __restrict__ data, const TileGeom& g, int64_t r0,
+                                                int64_t r1, int lane) {
+  using P1 = Pack<Real, 1>;
+  const DevBucket& d = w->d;
+  const int n_in = d.n_in;
+  for (int pp = 0; pp < g.P && r0 + (int64_t)pp * 32 < r1; pp += 2) {
+    const int64_t ya = r0 + (int64_t)pp * 32 + lane, yb = ya + 32;
+    const bool oka = ya < r1, okb = pp + 1 < g.P && yb < r1;
+    P1 p0[2], p1[2];
+#pragma unroll 1
+    for (int i = 0; i < n_in; ++i) {
+      const bool leaf = d.in[i].flags & kInLeaf;
+      const uint32_t lp = w->lpart[i][lane];
+      const uint32_t ka = oka ? w->tab[i][pp] + lp : 0u;  // idle items read row 0 and store nothing
+      const uint32_t kb = okb ? w->tab[i][pp + 1] + lp : 0u;
+      const Pack<Real, 2> qa = ldpair_in<Real, true>(data, d.in[i].off + 2 * (int64_t)ka, leaf);
+      const Pack<Real, 2> qb = ldpair_in<Real, true>(data, d.in[i].off + 2 * (int64_t)kb, leaf);
+      P1 a00, a01, a10, a11;
+      a00.c[0] = qa.c[0];
+      a01.c[0] = qa.c[1];
+      a10.c[0] = qb.c[0];
+      a11.c[0] = qb.c[1];
+      if (i == 0) {
+        p0[0] = a00;
+        p1[0] = a01;
+        p0[1] = a10;
+        p1[1] = a11;
+      } else {
+        pmul<Real, 1>(p0[0], a00);
+        pmul<Real, 1>(p1[0], a01);
+        pmul<Real, 1>(p0[1], a10);
+        pmul<Real, 1>(p1[1], a11);
+      }
+    }
+    if (oka) {
+      P1 o;
+      o.c[0] = cadd<Real>(p0[0].c[0], p1[0].c[0]);
+      stv<Real, 1>(data, d.out_off + ya, o);
+    }
+    if (okb) {
+      P1 o;
+      o.c[0] = cadd<Real>(p0[1].c[0], p1[1].c[0]);
+      stv<Real, 1>(data, d.out_off + yb, o);
+    }
+  }
+}
+
 // ------------------------------------------------ shared-memory staged path --
 //
 // The register path above keeps at most 2 rows' loads of one input in flight
@@ -879,15 +931,17 @@ __device__ __forceinline__ void warp_tile(WarpTile* w, Real* __restrict__ data, 
   if (!GRAD || d.kind == kStepFwd) {
     // STAGE 1: row-wide tiles through the bulk-copy ring (the register path
     // for buckets the ring cannot hold); STAGE 2: every forward tile of a
-    // row-wide plan on the lean row path (the launcher picks STAGE 2 only for
-    // that shape; any other shape is reported, not computed); STAGE 0: the
-    // generic register path
+    // row-wide or one-angle-set plan on the lean row / pair path (the launcher
+    // picks STAGE 2 only for those shapes; any other shape is reported, not
+    // computed); STAGE 0: the generic register path
     bool done = false;
     if (STAGE == 1 && !PAIR && Stageable<Real, VB>::value && g.RP == 1 && g.VC == 1)
       done = tile_rows_bulk<Real, VB>(w, reinterpret_cast<unsigned char*>(ring), *phase, data, g, r0, r1, lane, ctrl,
                                       g.wait_limit);
     if (STAGE == 2) {
-      if (g.RP == 1 && g.VC == 1)
+      if (PAIR && g.RP == 32 && g.VC == 1)
+        tile_pairs_regs<Real>(w, data, g, r0, r1, lane);
+      else if (!PAIR && g.RP == 1 && g.VC == 1)
         tile_rows_regs<Real, VB>(w, data, g, r0, r1, lane);
       else if (lane == 0 && ctrl != nullptr)
         atomicCAS(&ctrl->status, 0, (int32_t)QT_EINVAL);
