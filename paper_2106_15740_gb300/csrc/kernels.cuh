@@ -487,6 +487,133 @@ __device__ __forceinline__ void tile_pairs_regs(WarpTile* w, Real* __restrict__ 
   }
 }
 
+template <class Real>
+__device__ __forceinline__ void atomic_add_cx(Real* data, int64_t e, typename Cx<Real>::T v) {
+  atomicAdd(data + 2 * e, v.x);
+  atomicAdd(data + 2 * e + 1, v.y);
+}
+
+// Adjoint step (kStepAdj) on the lean paths: the same factors, products,
+// target rows and stores or atomic adds as tile_adjoint, two rows per
+// iteration, addressed straight from the pass table.  Factors flagged
+// kInNoPair (the output adjoint) give one value for x = 0 and x = 1.
+// One angle set (PAIR, 32 rows per pass, lane l on row r0 + pass * 32 + l):
+template <class Real>
+__device__ __forceinline__ void tile_adjoint_pairs(WarpTile* w, Real* __restrict__ data, const TileGeom& g,
+                                                   int64_t r0, int64_t r1, int lane) {
+  using P1 = Pack<Real, 1>;
+  const DevBucket& d = w->d;
+  const int n_in = d.n_in;
+  const bool full = d.aflags & kAdjFull;
+  const uint32_t lp_t = w->lpart[n_in][lane];
+  for (int pp = 0; pp < g.P && r0 + (int64_t)pp * 32 < r1; pp += 2) {
+    const int64_t ya = r0 + (int64_t)pp * 32 + lane, yb = ya + 32;
+    const bool ok[2] = {ya < r1, pp + 1 < g.P && yb < r1};
+    P1 p0[2], p1[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      p0[u].c[0].x = 1;
+      p0[u].c[0].y = 0;
+      p1[u] = p0[u];
+    }
+#pragma unroll 1
+    for (int i = 0; i < n_in; ++i) {
+      const int32_t fl = d.in[i].flags;
+      const bool leaf = fl & kInLeaf;
+      const uint32_t lp = w->lpart[i][lane];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const uint32_t k = ok[u] ? w->tab[i][pp + u] + lp : 0u;  // idle items read row 0
+        P1 a0, a1;
+        if (fl & kInNoPair) {
+          a0 = ldv_in<Real, 1, true>(data, d.in[i].off + (int64_t)k, leaf);
+          a1 = a0;
+        } else {
+          const Pack<Real, 2> q = ldpair_in<Real, true>(data, d.in[i].off + 2 * (int64_t)k, leaf);
+          a0.c[0] = q.c[0];
+          a1.c[0] = q.c[1];
+        }
+        pmul<Real, 1>(p0[u], a0);
+        pmul<Real, 1>(p1[u], a1);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (!ok[u]) continue;
+      const int64_t e0 = d.out_off + 2 * (int64_t)(w->tab[n_in][pp + u] + lp_t);
+      if (full) {
+        stv<Real, 1>(data, e0, p0[u]);
+        stv<Real, 1>(data, e0 + 1, p1[u]);
+      } else {
+        atomic_add_cx<Real>(data, e0, p0[u].c[0]);
+        atomic_add_cx<Real>(data, e0 + 1, p1[u].c[0]);
+      }
+    }
+  }
+}
+
+// Row-wide tiles (RP = 1, VC = 1: every lane on the same output row):
+template <class Real, int VB>
+__device__ __forceinline__ void tile_adjoint_rows(WarpTile* w, Real* __restrict__ data, const TileGeom& g,
+                                                  int64_t r0, int64_t r1, int lane) {
+  using PK = Pack<Real, VB>;
+  const DevBucket& d = w->d;
+  const int n_in = d.n_in;
+  const int nrows = (int)(r1 - r0);
+  const bool full = d.aflags & kAdjFull;
+  const bool on = lane < g.Bv;
+  const int64_t B = g.B;
+  const int64_t lo = (int64_t)(on ? lane : 0) * VB;
+  for (int q = 0; q < nrows; q += 2) {
+    const int qq[2] = {q, q + 1 < nrows ? q + 1 : q};
+    PK p0[2], p1[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int v = 0; v < VB; ++v) {
+        p0[u].c[v].x = 1;
+        p0[u].c[v].y = 0;
+        p1[u].c[v] = p0[u].c[v];
+      }
+#pragma unroll 1
+    for (int i = 0; i < n_in; ++i) {
+      const int32_t fl = d.in[i].flags;
+      const bool leaf = fl & kInLeaf;
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const uint32_t k = w->tab[i][qq[u]];
+        PK a0, a1;
+        if (fl & kInNoPair) {
+          a0 = ldv_in<Real, VB, true>(data, d.in[i].off + (int64_t)k * B + lo, leaf);
+          a1 = a0;
+        } else {
+          const int64_t e = d.in[i].off + (int64_t)(2 * k) * B + lo;
+          a0 = ldv_in<Real, VB, true>(data, e, leaf);
+          a1 = ldv_in<Real, VB, true>(data, e + B, leaf);
+        }
+        pmul<Real, VB>(p0[u], a0);
+        pmul<Real, VB>(p1[u], a1);
+      }
+    }
+    if (!on) continue;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (u == 1 && qq[1] == q) break;
+      const int64_t e0 = d.out_off + (int64_t)(2 * w->tab[n_in][qq[u]]) * B + lo;
+      if (full) {
+        stv<Real, VB>(data, e0, p0[u]);
+        stv<Real, VB>(data, e0 + B, p1[u]);
+      } else {
+#pragma unroll
+        for (int v = 0; v < VB; ++v) {
+          atomic_add_cx<Real>(data, e0 + v, p0[u].c[v]);
+          atomic_add_cx<Real>(data, e0 + B + v, p1[u].c[v]);
+        }
+      }
+    }
+  }
+}
+
 // ------------------------------------------------ shared-memory staged path --
 //
 // The register path above keeps at most 2 rows' loads of one input in flight
@@ -689,11 +816,6 @@ __device__ __forceinline__ bool tile_rows_bulk(WarpTile* w, unsigned char* ring,
   return true;
 }
 
-template <class Real>
-__device__ __forceinline__ void atomic_add_cx(Real* data, int64_t e, typename Cx<Real>::T v) {
-  atomicAdd(data + 2 * e, v.x);
-  atomicAdd(data + 2 * e + 1, v.y);
-}
 
 // Adjoint step (kStepAdj): for each item (row y, vector), the product of the
 // factors at x = 0 and x = 1 goes to the target rows (k_t << 1) | x,
@@ -949,7 +1071,12 @@ __device__ __forceinline__ void warp_tile(WarpTile* w, Real* __restrict__ data, 
     }
     if (!done) tile_items<Real, VB, PAIR, CG, 2, 0>(w, data, g, r0, r1, lane, rip, v0, lane_on, ctrl, dbg_bucket);
   } else if (d.kind == kStepAdj) {
-    tile_adjoint<Real, VB, PAIR, CG, 2>(w, data, g, r0, r1, lane, rip, v0, lane_on, ctrl, dbg_bucket);
+    if (STAGE == 2 && PAIR && g.RP == 32 && g.VC == 1)
+      tile_adjoint_pairs<Real>(w, data, g, r0, r1, lane);
+    else if (STAGE == 2 && !PAIR && g.RP == 1 && g.VC == 1)
+      tile_adjoint_rows<Real, VB>(w, data, g, r0, r1, lane);
+    else
+      tile_adjoint<Real, VB, PAIR, CG, 2>(w, data, g, r0, r1, lane, rip, v0, lane_on, ctrl, dbg_bucket);
   } else if (d.kind == kStepAdjRed) {
     tile_adjred<Real, VB, PAIR, CG, 2>(w, data, g, r0, r1, lane, rip, v0, lane_on, ctrl, dbg_bucket);
   } else {
