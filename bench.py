@@ -238,6 +238,21 @@ def load_path_comparison(n, edges, p, B, g, b, dev, torch):
     return out
 
 
+def chain_comparison(n, edges, p, B, g, b, dev, torch):
+    """The bench step with every step of a workspace slot chained to the one
+    before it (chain_steps), instead of waiting only for its tree dependencies."""
+    from paper_2106_15740_gb300.energy import EnergyPlan
+    plan = EnergyPlan(n, edges, p, batch=B, dtype=WORKLOAD["dtype"], mode="persistent", device=dev,
+                      order_trials=WORKLOAD.get("order_trials", 0), lane_items=WORKLOAD.get("lane_items", 0),
+                      group_rows=WORKLOAD.get("group_rows", 0), chain_steps=True)
+    ms = _time_calls(plan, g, b, False, 5, torch)
+    out = {"value": len(edges) * B / (ms * 1e-3), "unit": "edge_evals/s", "ms_per_step": ms,
+           "achieved_gbs": plan.stats["alg_bytes"] / (ms * 1e-3) / 1e9,
+           "what": "same plan and tile, each step waits for the step before it on its slot (direct calls)"}
+    plan.close()
+    return out
+
+
 def gradient_and_comparator(dev, torch):
     """Energy-gradient throughput on the 60-vertex p = 4 workload (8 angles,
     one angle set, complex64 adjoint sweep), and the plain per-edge complex128
@@ -349,7 +364,7 @@ def run_ours(args):
     profile_only = ((WORKLOAD["name"], B) != ("n100_p4", 64) or "edge_range" in WORKLOAD or "lane_items" in WORKLOAD
                     or "chunk_tiles" in WORKLOAD or "gradient" in WORKLOAD or "max_width" in WORKLOAD
                     or "profile_order" in WORKLOAD
-                    or "load_path" in WORKLOAD)
+                    or "load_path" in WORKLOAD or "chain_steps" in WORKLOAD)
     grad = bool(WORKLOAD.get("gradient", False))
     gamma, beta = random_angles(B, p, 1002 + 7919 * rank)
     tuned = None
@@ -357,7 +372,7 @@ def run_ours(args):
         # tile size and grouping picked on this device, before the timed region
         from paper_2106_15740_gb300.energy import autotune
         best, timings = autotune(n, edges, p, batch=B, dtype=WORKLOAD["dtype"], device=dev, reps=3,
-                                 lane_items=(16, 32, 64), group_rows=(0, 32),
+                                 lane_items=(16, 32, 64), group_rows=(0, -1, 32),
                                  order_trials=WORKLOAD.get("order_trials", 0))
         WORKLOAD["lane_items"], WORKLOAD["group_rows"] = best["lane_items"], best["group_rows"]
         tuned = {"choice": best,
@@ -368,7 +383,8 @@ def run_ours(args):
                       group_rows=WORKLOAD.get("group_rows", 0), chunk_tiles=WORKLOAD.get("chunk_tiles", 0),
                       gradient=grad, max_width=WORKLOAD.get("max_width", 0), slice=WORKLOAD.get("slice", False),
                       max_workspace=WORKLOAD.get("max_workspace", 0), order_trials=WORKLOAD.get("order_trials", 0),
-                      load_path=WORKLOAD.get("load_path", "registers"))
+                      load_path=WORKLOAD.get("load_path", "registers"),
+                      chain_steps=WORKLOAD.get("chain_steps", False))
     t_plan = time.perf_counter() - t_plan
     g = torch.tensor(gamma, device=dev)
     b = torch.tensor(beta, device=dev)
@@ -481,6 +497,7 @@ def run_ours(args):
             res["min_fill_order"] = min_fill_comparison(n, edges, p, B, g, b, dev, torch)
         if not profile_only:
             res["staged_loads"] = load_path_comparison(n, edges, p, B, g, b, dev, torch)
+            res["chained_steps"] = chain_comparison(n, edges, p, B, g, b, dev, torch)
         if not args.no_cpu_baseline:
             res.update(gradient_and_comparator(dev, torch))
             res["single_amplitude"] = amplitude_measure(dev, torch)
@@ -513,6 +530,8 @@ def main():
     ap.add_argument("--max-workspace-gb", type=float, default=0, help="profiling only: workspace cap")
     ap.add_argument("--load-path", default=None, choices=["staged", "registers"],
                     help="profiling only: operand path of the persistent kernel")
+    ap.add_argument("--chain-steps", action="store_true",
+                    help="profiling only: chain every step of a workspace slot to the one before it")
     ap.add_argument("--order-trials", type=int, default=None,
                     help="profiling only: randomised greedy orders per edge (0: min-fill)")
     args = ap.parse_args()
@@ -537,6 +556,9 @@ def main():
         args.no_cpu_baseline = True
     if args.load_path is not None:
         WORKLOAD["load_path"] = args.load_path
+        args.no_cpu_baseline = True
+    if args.chain_steps:
+        WORKLOAD["chain_steps"] = True
         args.no_cpu_baseline = True
     if args.max_workspace_gb:
         WORKLOAD["max_workspace"] = int(args.max_workspace_gb * (1 << 30))

@@ -31,7 +31,7 @@ EXPORTS = [
     "qt_plan_free", "qt_energy_workspace_size", "qt_energy", "qt_last_error",
     "qt_plan_set_profiling", "qt_plan_kernel_times", "qt_plan_energy_static",
     "qt_static_scratch_bytes", "qt_plan_set_wait_limit", "qt_plan_inject_stall", "qt_plan_edge_slices",
-    "qt_plan_edge_bytes", "qt_plan_trace_size", "qt_plan_set_trace", "qt_plan_tasks",
+    "qt_plan_edge_bytes", "qt_plan_trace_size", "qt_plan_set_trace", "qt_plan_tasks", "qt_plan_schedule",
     "qt_amplitude_plan_create", "qt_plan_amplitudes", "qt_representation_cost",
 ]
 
@@ -52,7 +52,8 @@ class qt_plan_options(C.Structure):
                 ("max_workspace", C.c_int64), ("group_rows", C.c_int32), ("edge_begin", C.c_int32),
                 ("edge_end", C.c_int32), ("slice", C.c_int32),
                 ("chunk_tiles", C.c_int32), ("order_trials", C.c_int32), ("order_seed", C.c_int32),
-                ("order_tau", C.c_double), ("load_path", C.c_int32), ("checkpoint_bytes", C.c_int64)]
+                ("order_tau", C.c_double), ("load_path", C.c_int32), ("checkpoint_bytes", C.c_int64),
+                ("chain_steps", C.c_int32)]
 
 
 _lib = None
@@ -97,6 +98,8 @@ def lib():
             "qt_representation_cost": [C.POINTER(qt_graph), i32, i32, i32, i32, pi32, pi32, pd],
             "qt_plan_set_trace": [vp, vp, sz],
             "qt_plan_tasks": [vp, pi32, pi32, pi32, pi32, pi32, pi32],
+            "qt_plan_schedule": [vp, pi32, pi32, pi32, pi32, pi32, pi32, pi32, pi32, pi32,
+                                 C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -325,6 +328,28 @@ def qt_plan_tasks(plan):
     cols = {k: np.empty(n.value, dtype=np.int32) for k in ("step", "chunk", "out_rank", "edge", "n_in")}
     _check(lib().qt_plan_tasks(plan, C.byref(n), *(_as_pi32(cols[k]) for k in ("step", "chunk", "out_rank", "edge", "n_in"))))
     return cols
+
+
+def qt_plan_schedule(plan):
+    """Schedule of a forward persistent plan as a dict of arrays (see the C
+    header): dep_first, dep_count, deps, in_first, src, unit, write_lo, write_hi."""
+    ns, nd, nr = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(lib().qt_plan_schedule(plan, C.byref(ns), C.byref(nd), C.byref(nr), *([None] * 9)))
+    n = ns.value
+    out = {k: np.empty(n, dtype=np.int32) for k in ("dep_first", "dep_count", "unit")}
+    out["deps"] = np.empty(max(nd.value, 1), dtype=np.int32)
+    out["in_first"] = np.empty(n + 1, dtype=np.int32)
+    out["src"] = np.empty(max(nr.value, 1), dtype=np.int32)
+    out["write_lo"] = np.empty(n, dtype=np.int64)
+    out["write_hi"] = np.empty(n, dtype=np.int64)
+    p64 = lambda a: a.ctypes.data_as(C.POINTER(C.c_int64))
+    _check(lib().qt_plan_schedule(plan, C.byref(ns), C.byref(nd), C.byref(nr), _as_pi32(out["dep_first"]),
+                                  _as_pi32(out["dep_count"]), _as_pi32(out["deps"]), _as_pi32(out["in_first"]),
+                                  _as_pi32(out["src"]), _as_pi32(out["unit"]), p64(out["write_lo"]),
+                                  p64(out["write_hi"])))
+    out["deps"] = out["deps"][:nd.value]
+    out["src"] = out["src"][:nr.value]
+    return out
 
 
 def qt_plan_free(plan):

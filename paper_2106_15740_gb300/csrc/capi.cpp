@@ -258,6 +258,7 @@ void qt_plan_options_default(qt_plan_options* opt) {
   opt->order_tau = 1.0;
   opt->load_path = 0;
   opt->checkpoint_bytes = 0;
+  opt->chain_steps = 0;
 }
 
 static qt_status check_options(const qt_plan_options* opt, qt_plan_options* out) {
@@ -275,6 +276,7 @@ static qt_status check_options(const qt_plan_options* opt, qt_plan_options* out)
   if (!(o.order_tau >= 0.0) || !std::isfinite(o.order_tau)) return fail(QT_EINVAL, "order_tau must be finite and >= 0");
   if (o.load_path != 0 && o.load_path != 1) return fail(QT_EINVAL, "load_path must be 0 or 1");
   if (o.checkpoint_bytes < 0) return fail(QT_EINVAL, "checkpoint_bytes must be >= 0");
+  if (o.chain_steps != 0 && o.chain_steps != 1) return fail(QT_EINVAL, "chain_steps must be 0 or 1");
   *out = o;
   return QT_OK;
 }
@@ -525,6 +527,40 @@ qt_status qt_plan_tasks(const qt_plan* plan, int32_t* n_tasks, int32_t* step, in
   return QT_OK;
 }
 
+qt_status qt_plan_schedule(const qt_plan* plan, int32_t* n_steps, int32_t* n_deps, int32_t* n_reads,
+                           int32_t* dep_first, int32_t* dep_count, int32_t* deps, int32_t* in_first, int32_t* src,
+                           int32_t* unit, int64_t* write_lo, int64_t* write_hi) {
+  if (!plan || !n_steps || !n_deps || !n_reads) return fail(QT_EINVAL, "NULL argument");
+  const Plan& P = plan->P;
+  if (P.opt.mode != QT_MODE_PERSISTENT || P.opt.gradient)
+    return fail(QT_ESTATE, "the schedule is reported for forward persistent plans");
+  const int32_t ns = (int32_t)P.buckets.size();
+  int32_t nr = 0;
+  for (const DevBucket& d : P.buckets)
+    for (int32_t k = 0; k < d.n_in; ++k) nr += d.in[k].src >= 0 ? 1 : 0;
+  *n_steps = ns;
+  *n_deps = (int32_t)P.deps.size();
+  *n_reads = nr;
+  if (!dep_first || !dep_count || !deps || !in_first || !src || !unit || !write_lo || !write_hi) return QT_OK;
+  for (int32_t s = 0; s < ns; ++s) unit[s] = s;
+  for (const DevTask& t : P.tasks)
+    for (int32_t k = 1; k < -t.chunk; ++k) unit[t.bucket + k] = t.bucket;
+  int32_t r = 0;
+  for (int32_t s = 0; s < ns; ++s) {
+    const DevBucket& d = P.buckets[s];
+    dep_first[s] = d.dep;
+    dep_count[s] = unit[s] == s ? d.n_dep : 0;
+    in_first[s] = r;
+    for (int32_t k = 0; k < d.n_in; ++k)
+      if (d.in[k].src >= 0) src[r++] = d.in[k].src;
+    write_lo[s] = d.out_off;
+    write_hi[s] = d.out_off + d.n_rows * (int64_t)P.opt.batch;
+  }
+  in_first[ns] = r;
+  std::copy(P.deps.begin(), P.deps.end(), deps);
+  return QT_OK;
+}
+
 qt_status qt_plan_set_wait_limit(qt_plan* plan, int32_t polls) {
   if (!plan || polls < 1) return fail(QT_EINVAL, "plan is NULL or polls < 1");
   plan->P.spin_limit = polls;
@@ -537,9 +573,9 @@ qt_status qt_plan_inject_stall(qt_plan* plan, int32_t enable) {
   P.stall_step = -1;
   if (enable) {
     for (size_t t = P.tasks.size(); t-- > 0;) {
-      const int32_t dep = P.buckets[P.tasks[t].bucket].dep;
-      if (dep >= 0) {
-        P.stall_step = dep;
+      const DevBucket& d = P.buckets[P.tasks[t].bucket];
+      if (d.n_dep > 0) {
+        P.stall_step = P.deps[d.dep];
         break;
       }
     }

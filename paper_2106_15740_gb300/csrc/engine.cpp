@@ -2,7 +2,7 @@
 //
 // compile_plan turns the bucket plans of every edge network into device
 // records (qt_device.h) and lays out the workspace:
-//   [ctrl | done counters | buckets | tasks | leaf factors | scalar table |
+//   [ctrl | done counters | buckets | tasks | dependency lists | leaf factors | scalar table |
 //    angles | results | trig table | data]
 // data = [leaf-factor pool | scalar results | intermediate arenas].
 // Intermediates of one edge live in an arena planned by first-fit with
@@ -13,9 +13,10 @@
 // QT_MODE_PER_BUCKET launches one kernel per bucket, edge after edge, all
 // edges sharing one arena.  QT_MODE_PERSISTENT issues one persistent launch
 // over a queue of bucket tiles; edges are spread over "slots" (one arena
-// each), buckets of one slot form a chain (each waits for the previous one),
-// and the queue interleaves the slots round-robin so independent work fills
-// the GPU while a chain waits.
+// each).  A queued step waits for the steps it reads and for the readers of
+// the arena space it overwrites (gradient plans: for the step before it on
+// its slot), and the queue interleaves the slots round-robin so independent
+// work fills the GPU while a step waits.
 #include "engine.h"
 
 #include <algorithm>
@@ -102,6 +103,7 @@ static DevInput input_record(uint32_t mask, int64_t off, int32_t flags) {
   fill_runs(mask, &in);
   in.off = off;
   in.flags = flags;
+  in.src = -1;
   return in;
 }
 
@@ -119,6 +121,89 @@ struct GradOp {
   int64_t gbar = -1;         // kStepAdj: arena offset of the bucket's output adjoint (-1: none)
   std::vector<int64_t> loc;  // arena offset of each intermediate input (-1 for the leaf factor)
 };
+
+// Steps of one forward network that must be complete before bucket i runs
+// (indices within the network).  Bucket elimination forms a tree: bucket i
+// reads only the outputs of the buckets in its in_src, so it waits for those
+// and not for the whole order before it.  Memory adds the rest: the arena
+// hands out space in the elimination order (output allocated before the
+// step's inputs are released), so bucket i's output may overwrite an
+// intermediate that an earlier bucket read; i then also waits for that
+// reader.  The arena is replayed in order with, per element range, the last
+// step that read it; a write also overtakes the range's earlier writer,
+// whose reader it waits for.  Entries that another entry already depends on
+// (transitively) are dropped.  `off` holds the arena offsets of the outputs;
+// outputs of rank 0 live outside the arena.  *sinks gets the buckets whose
+// output no later bucket reads.  False if the offsets contradict the order
+// (a live intermediate overwritten).
+static bool forward_deps(const EdgePlan& ep, const std::vector<int64_t>& off, int64_t B, int64_t al,
+                         std::vector<std::vector<int32_t>>* deps, std::vector<int32_t>* sinks) {
+  const int32_t nb = (int32_t)ep.buckets.size();
+  auto size_of = [&](int32_t i) { return ((((int64_t)1 << ep.buckets[i].out_rank) * B) + al - 1) / al * al; };
+  std::vector<int32_t> reader(nb, -1);
+  for (int32_t i = 0; i < nb; ++i)
+    for (int32_t c : ep.buckets[i].in_src)
+      if (c >= 0) reader[c] = i;
+  sinks->clear();
+  for (int32_t i = 0; i < nb; ++i)
+    if (reader[i] < 0) sinks->push_back(i);
+  // released ranges: start -> (end, step that read it last); disjoint
+  std::map<int64_t, std::pair<int64_t, int32_t>> dead;
+  const int32_t W = (nb + 63) / 64;
+  std::vector<uint64_t> anc((size_t)nb * W, 0);  // bit d of row i: i depends on d (transitively)
+  deps->assign(nb, {});
+  std::vector<int32_t> raw;
+  for (int32_t i = 0; i < nb; ++i) {
+    const Bucket& bk = ep.buckets[i];
+    raw.clear();
+    for (int32_t c : bk.in_src)
+      if (c >= 0) raw.push_back(c);
+    if (bk.out_rank > 0) {
+      const int64_t a0 = off[i], a1 = a0 + size_of(i);
+      auto it = dead.upper_bound(a0);
+      if (it != dead.begin()) --it;
+      while (it != dead.end() && it->first < a1) {
+        const int64_t b0 = it->first, b1 = it->second.first;
+        const int32_t r = it->second.second;
+        if (b1 <= a0) {
+          ++it;
+          continue;
+        }
+        raw.push_back(r);
+        it = dead.erase(it);
+        if (b0 < a0) dead[b0] = {a0, r};  // keep the parts outside [a0, a1)
+        if (b1 > a1) dead[a1] = {b1, r};
+      }
+    }
+    for (int32_t c : bk.in_src) {
+      if (c < 0 || ep.buckets[c].out_rank == 0) continue;
+      const int64_t b0 = off[c], b1 = b0 + size_of(c);
+      auto it = dead.lower_bound(b0);  // a live range cannot already be marked released
+      if (it != dead.end() && it->first < b1) return false;
+      if (it != dead.begin() && std::prev(it)->second.first > b0) return false;
+      dead[b0] = {b1, i};
+    }
+    std::sort(raw.begin(), raw.end());
+    raw.erase(std::unique(raw.begin(), raw.end()), raw.end());
+    uint64_t* ai = &anc[(size_t)i * W];
+    for (int32_t d : raw) {
+      if (d >= i) return false;
+      const uint64_t* ad = &anc[(size_t)d * W];
+      for (int32_t w = 0; w < W; ++w) ai[w] |= ad[w];
+    }
+    for (int32_t d : raw) {
+      bool implied = false;
+      for (int32_t d2 : raw)
+        if (d2 != d && ((anc[(size_t)d2 * W + (d >> 6)] >> (d & 63)) & 1u)) {
+          implied = true;
+          break;
+        }
+      if (!implied) (*deps)[i].push_back(d);
+      ai[d >> 6] |= (uint64_t)1 << (d & 63);
+    }
+  }
+  return true;
+}
 
 // Reverse-mode plan of one network with checkpointing.  The bucket order is
 // cut into segments whose produced intermediates hold at most `budget`
@@ -392,6 +477,10 @@ qt_status compile_plan(Plan* P) {
   P->lbar_elems = grad ? leaf_pool : 0;
 
   // ---- device records: per edge, forward steps then adjoint steps ----
+  // forward plans: per step its dependencies inside its network (global step
+  // indices), per network the steps no other step of it reads
+  std::vector<std::vector<int32_t>> fdeps;
+  std::vector<std::vector<int32_t>> net_sinks(n_edges);
   const int32_t geom_bv = tile_geom(P->opt.dtype, B, P->opt.lane_items).Bv;
   P->buckets.clear();
   P->edge_first.assign(n_edges + 1, 0);
@@ -441,13 +530,24 @@ qt_status compile_plan(Plan* P) {
       return d;
     };
     if (!grad) {
+      const int32_t g0 = (int32_t)P->buckets.size();
       for (int32_t i = 0; i < (int32_t)ep.buckets.size(); ++i) {
         const Bucket& bk = ep.buckets[i];
         std::vector<int64_t> loc;
         for (int32_t c : bk.in_src) loc.push_back(c >= 0 ? out_off[e][c] : -1);
         P->buckets.push_back(fwd_record(i, out_off[e][i], loc));
+        for (int32_t k = 0; k < (int32_t)bk.in_src.size(); ++k)
+          if (bk.in_src[k] >= 0) P->buckets.back().in[k].src = g0 + bk.in_src[k];
         if (bk.leaf_rank > 0) leaf_record(i);
       }
+      std::vector<std::vector<int32_t>> ld;
+      std::vector<int32_t> sk;
+      if (!forward_deps(ep, out_off[e], B, al, &ld, &sk))
+        return fail(QT_EINVAL, "internal: arena offsets contradict the bucket order");
+      fdeps.resize(P->buckets.size());
+      for (int32_t i = 0; i < (int32_t)ld.size(); ++i)
+        for (int32_t d : ld[i]) fdeps[g0 + i].push_back(g0 + d);
+      for (int32_t i : sk) net_sinks[e].push_back(g0 + i);
     }
     for (const GradOp& op : gops[e]) {
       const Bucket& bk = ep.buckets[op.bucket];
@@ -560,8 +660,24 @@ qt_status compile_plan(Plan* P) {
       if ((nt + d.span - 1) / d.span > INT32_MAX / 2) return fail(QT_EWIDTH, "step too large for the task queue");
     }
     const int32_t S = P->n_slots;
+    // Dependencies: gradient plans (and chain_steps) chain each step of a
+    // slot to the one queued before it.  Forward plans take the tree order of
+    // forward_deps; a step with no dependency inside its network waits for
+    // the sinks of the network the slot ran before (whose arena it reuses).
+    // The done counter of a grouped step is its group's last step (`rep`).
+    const bool chain = grad || P->opt.chain_steps != 0;
+    std::vector<int32_t> rep(P->buckets.size());
+    for (size_t b = 0; b < rep.size(); ++b) rep[b] = (int32_t)b;
+    std::vector<std::vector<int32_t>> prev_sinks(S);
+    P->deps.clear();
+    std::vector<int32_t> dl;
+    auto add_deps = [&](int32_t s, int32_t b, int32_t self) {
+      const std::vector<int32_t>& own = chain || fdeps[b].empty() ? prev_sinks[s] : fdeps[b];
+      for (int32_t x : own)
+        if (rep[x] != self) dl.push_back(rep[x]);
+    };
     std::vector<size_t> ei(S, 0);
-    std::vector<int32_t> bi(S, 0), prev(S, -1);
+    std::vector<int32_t> bi(S, 0);
     bool any = true;
     while (any) {
       any = false;
@@ -573,32 +689,43 @@ qt_status compile_plan(Plan* P) {
         const int32_t gb = P->edge_first[e] + bi[s];
         DevBucket& d = P->buckets[gb];
         const int64_t nt = (step_tiles(d, geom.R) + d.span - 1) / d.span;  // chunks of this step
-        d.dep = prev[s];
-        // consecutive tiny forward steps of a chain run on one warp; reverse-sweep
+        dl.clear();
+        // consecutive tiny forward steps of a network run on one warp; reverse-sweep
         // steps are not grouped (a warp running hundreds of them back to back
         // left the rest of the GPU waiting on its chain)
+        int32_t last = gb;
         if (d.kind == kStepFwd && step_tiles(d, geom.R) == 1 && d.n_rows <= group_rows) {
           int32_t k = 1;
           while (bi[s] + k < ns_e && k < kMaxGroup && P->buckets[gb + k].kind == kStepFwd &&
                  P->buckets[gb + k].n_rows <= group_rows && step_tiles(P->buckets[gb + k], geom.R) == 1)
             ++k;
+          last = gb + k - 1;
           for (int32_t j = 0; j < k; ++j) {
             P->buckets[gb + j].ntask = 1;
             P->buckets[gb + j].span = 1;
-            if (j > 0) P->buckets[gb + j].dep = -1;
+            P->buckets[gb + j].dep = 0;
+            P->buckets[gb + j].n_dep = 0;
+            rep[gb + j] = last;
           }
+          for (int32_t j = 0; j < (chain ? 1 : k); ++j) add_deps(s, gb + j, last);
           P->tasks.push_back(DevTask{gb, -k});
-          prev[s] = gb + k - 1;
           bi[s] += k - 1;
         } else {
           d.ntask = (int32_t)nt;
+          add_deps(s, gb, gb);
           for (int32_t c = 0; c < d.ntask; ++c) P->tasks.push_back(DevTask{gb, c});
-          prev[s] = gb;
         }
+        std::sort(dl.begin(), dl.end());
+        dl.erase(std::unique(dl.begin(), dl.end()), dl.end());
+        P->buckets[gb].dep = (int32_t)P->deps.size();
+        P->buckets[gb].n_dep = (int32_t)dl.size();
+        P->deps.insert(P->deps.end(), dl.begin(), dl.end());
+        if (chain) prev_sinks[s].assign(1, last);
         if ((int64_t)P->tasks.size() > INT32_MAX / 2) return fail(QT_ENOMEM, "task queue too long");
         if (++bi[s] == ns_e) {
           bi[s] = 0;
           ++ei[s];
+          if (!chain) prev_sinks[s] = net_sinks[e];
         }
       }
     }
@@ -624,6 +751,8 @@ qt_status compile_plan(Plan* P) {
   o = align256(o + sizeof(DevBucket) * P->buckets.size());
   L.tasks = o;
   o = align256(o + sizeof(DevTask) * P->tasks.size());
+  L.deps = o;
+  o = align256(o + sizeof(int32_t) * P->deps.size());
   L.leaf = o;
   o = align256(o + sizeof(DevLeafFactor) * P->leaf.size());
   L.leaf_first = o;
@@ -691,6 +820,9 @@ qt_status run_plan(Plan* P, const double* gamma, const double* beta, double* ene
     if (!P->tasks.empty())
       QT_CUDA(cudaMemcpyAsync(base + L.tasks, P->tasks.data(), sizeof(DevTask) * P->tasks.size(),
                               cudaMemcpyHostToDevice, s));
+    if (!P->deps.empty())
+      QT_CUDA(cudaMemcpyAsync(base + L.deps, P->deps.data(), sizeof(int32_t) * P->deps.size(),
+                              cudaMemcpyHostToDevice, s));
     if (!P->leaf.empty())
       QT_CUDA(cudaMemcpyAsync(base + L.leaf, P->leaf.data(), sizeof(DevLeafFactor) * P->leaf.size(),
                               cudaMemcpyHostToDevice, s));
@@ -738,7 +870,7 @@ qt_status run_plan(Plan* P, const double* gamma, const double* beta, double* ene
     const int32_t grid = std::max(1, per_sm) * n_sm;
     QT_CUDA(launch_persistent(dtype, P->opt.gradient != 0, P->opt.load_path, P->bulk_ok, dbk, (const DevTask*)(base + L.tasks), (int32_t)P->tasks.size(),
                               (DevCtrl*)(base + L.ctrl), (int32_t*)(base + L.done), B, P->opt.lane_items, data,
-                              P->data_elems, grid, P->spin_limit, P->trace, s));
+                              P->data_elems, grid, P->spin_limit, (const int32_t*)(base + L.deps), P->trace, s));
   } else {
     int n_sm = 0;
     QT_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));

@@ -16,7 +16,7 @@ struct qt_network {
 namespace qt {
 
 struct WsLayout {
-  size_t ctrl = 0, done = 0, buckets = 0, tasks = 0, leaf = 0, leaf_first = 0, scal_off = 0, scal_begin = 0,
+  size_t ctrl = 0, done = 0, buckets = 0, tasks = 0, deps = 0, leaf = 0, leaf_first = 0, scal_off = 0, scal_begin = 0,
          net_first = 0;
   size_t angles = 0, results = 0, trig = 0, dz = 0, gpart = 0, data = 0, total = 0;
 };
@@ -40,6 +40,7 @@ struct Plan {
   int64_t lbar_shift = 0;                  // leaf-adjoint element = leaf element + lbar_shift
   int64_t lbar_elems = 0;
   std::vector<DevTask> tasks;
+  std::vector<int32_t> deps;               // dependency lists of the queued steps (DevBucket dep, n_dep)
   std::vector<int64_t> scal_off;           // element offsets of scalar results
   std::vector<int32_t> scal_begin;         // CSR over edges
   int64_t tile_items = 0;                  // output rows per warp tile

@@ -202,6 +202,7 @@ __global__ void __launch_bounds__(256, STAGE == 1 ? 2 : 4) persistent_kernel(con
                                                             const DevTask* __restrict__ tasks, int32_t n_tasks,
                                                             DevCtrl* ctrl, int32_t* done, Real* __restrict__ data,
                                                             const TileGeom g, int32_t spin_limit,
+                                                            const int32_t* __restrict__ deps,
                                                             unsigned long long* __restrict__ trace) {
   __shared__ WarpTile tiles[8];
   extern __shared__ uint4 ring_all[];
@@ -224,26 +225,27 @@ __global__ void __launch_bounds__(256, STAGE == 1 ? 2 : 4) persistent_kernel(con
     int32_t t_next = n_tasks, failed = 0;
     const DevTask task = tasks[t];
     if (trace != nullptr && lane == 0) w->trace_t[0] = globaltimer();
-    if (lane == 0) {
-      if (*((volatile int32_t*)&ctrl->status) == 0) t_next = atomicAdd(&ctrl->head, 1);
-      if (task.bucket != cached) {
-        const int32_t dep = buckets[task.bucket].dep;
-        if (dep >= 0) {
-          const int32_t need = buckets[dep].ntask;
-          int32_t polls = 0;
-          while (ld_acquire(done + dep) < need) {
-            ++polls;
-            if (polls > spin_limit || ((polls & 63) == 0 && *((volatile int32_t*)&ctrl->status) != 0)) {
-              if (atomicCAS(&ctrl->status, 0, (int32_t)QT_ETIMEOUT) == 0) ctrl->spins = dep;
-              failed = 1;
-              break;
-            }
-            __nanosleep(100);
+    if (lane == 0 && *((volatile int32_t*)&ctrl->status) == 0) t_next = atomicAdd(&ctrl->head, 1);
+    if (task.bucket != cached) {  // uniform; a warp that ran a chunk of this step already saw its inputs
+      // lane q waits for the dependencies q, q + 32, ... of the step (each poll bounded)
+      const int32_t nd = buckets[task.bucket].n_dep, d0 = buckets[task.bucket].dep;
+      for (int32_t q = lane; q < nd && !failed; q += 32) {
+        const int32_t dep = deps[d0 + q];
+        const int32_t need = buckets[dep].ntask;
+        int32_t polls = 0;
+        while (ld_acquire(done + dep) < need) {
+          ++polls;
+          if (polls > spin_limit || ((polls & 63) == 0 && *((volatile int32_t*)&ctrl->status) != 0)) {
+            if (atomicCAS(&ctrl->status, 0, (int32_t)QT_ETIMEOUT) == 0) ctrl->spins = dep;
+            failed = 1;
+            break;
           }
+          __nanosleep(100);
         }
       }
+      __syncwarp();  // every lane's acquire before any lane reads the inputs
     }
-    failed = __shfl_sync(0xffffffffu, failed, 0);
+    failed = __any_sync(0xffffffffu, failed);
     t_next = __shfl_sync(0xffffffffu, t_next, 0);
     if (failed) break;
     if (trace != nullptr && lane == 0) w->trace_t[1] = globaltimer();
@@ -580,7 +582,7 @@ static int persistent_smem(int dtype, int stage, int32_t B) {
 cudaError_t launch_persistent(int dtype, bool grad, int32_t load_path, bool bulk_ok, const DevBucket* buckets,
                               const DevTask* tasks, int32_t n_tasks, DevCtrl* ctrl, int32_t* done, int32_t B,
                               int32_t lane_items, void* data, int64_t data_elems, int32_t grid, int32_t spin_limit,
-                              unsigned long long* trace, cudaStream_t s) {
+                              const int32_t* deps, unsigned long long* trace, cudaStream_t s) {
   TileGeom g = tile_geom(dtype, B, lane_items);
   g.data_elems = data_elems;
   g.wait_limit = 1 << 22;
@@ -592,7 +594,7 @@ cudaError_t launch_persistent(int dtype, bool grad, int32_t load_path, bool bulk
     if (e != cudaSuccess) return e;
   }
   void* args[] = {(void*)&buckets, (void*)&tasks, (void*)&n_tasks, (void*)&ctrl, (void*)&done, (void*)&data,
-                  (void*)&g, (void*)&spin_limit, (void*)&trace};
+                  (void*)&g, (void*)&spin_limit, (void*)&deps, (void*)&trace};
   return cudaLaunchKernel(fn, dim3(grid), dim3(256), args, (size_t)smem, s);
 }
 

@@ -199,6 +199,7 @@ __device__ __forceinline__ void load_bucket(DevBucket* dst, const DevBucket* src
     dst->tgt_bits = src->tgt_bits;
     dst->comp_bits = src->comp_bits;
     dst->span = src->span;
+    dst->n_dep = src->n_dep;
   }
 }
 

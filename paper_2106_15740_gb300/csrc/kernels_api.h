@@ -20,7 +20,7 @@ bool staged_supported(int dtype, int32_t B);
 cudaError_t launch_persistent(int dtype, bool grad, int32_t load_path, bool bulk_ok, const DevBucket* buckets,
                               const DevTask* tasks, int32_t n_tasks, DevCtrl* ctrl, int32_t* done, int32_t B,
                               int32_t lane_items, void* data, int64_t data_elems, int32_t grid, int32_t spin_limit,
-                              unsigned long long* trace, cudaStream_t s);
+                              const int32_t* deps, unsigned long long* trace, cudaStream_t s);
 cudaError_t persistent_occupancy(int dtype, bool grad, int32_t load_path, bool bulk_ok, int32_t B,
                                  int* blocks_per_sm);
 cudaError_t launch_energy(int dtype, const void* data, const int64_t* scal_off, const int32_t* scal_begin,

@@ -25,7 +25,8 @@ struct DevInput {
   int32_t nruns;
   uint32_t run[kDevMaxRuns];   // src | len << 8 | dst << 16
   int32_t flags;               // kIn* bits below
-  int32_t pad;
+  int32_t src;                 // forward plans: the step that writes this input (-1: leaf factor or
+                               // not recorded); host-side schedule checks only
 };
 constexpr int32_t kInLeaf = 1;    // written before the launch, read through L1
 constexpr int32_t kInNoPair = 2;  // one row per output row (no eliminated-variable bit): an adjoint
@@ -74,13 +75,15 @@ struct DevBucket {
   int64_t n_rows;              // rows iterated: 2^out_rank of the bucket
   int32_t out_rank;
   int32_t n_in;                // factors (for kStepAdj the target follows them)
-  int32_t dep;                 // step that must be complete before this one (-1: none)
+  int32_t dep;                 // first entry of the step's list in the plan's dependency array
   int32_t ntask;               // chunks of this step in the persistent queue (its done count)
   int32_t kind;                // kStep*
   int32_t aflags;              // kAdj* bits (kStepAdj)
   int32_t tgt_bits;            // kStepAdjRed: target rows 2^tgt_bits (times x = 0, 1)
   int32_t comp_bits;           // kStepAdjRed: completions per target row 2^comp_bits (>= 5)
   int32_t span;                // warp tiles per queue task (chunk c covers tiles [c*span, (c+1)*span))
+  int32_t n_dep;               // steps that must be complete before a task of this one starts:
+                               // deps[dep .. dep + n_dep) (done count of each = its ntask)
   DevInput in[kDevMaxIn];
 };
 

@@ -217,6 +217,35 @@ def test_workspace_cap_limits_concurrency():
     assert np.array_equal(_run(full, g, b)[1], _run(capped, g, b)[1])
 
 
+@pytest.mark.parametrize("dtype,batch,cap", [("c64", 64, 1), ("c64", 4, 4), ("c128", 1, 4), ("c128", 3, 1)])
+def test_tree_schedule_equals_chain_bitwise(dtype, batch, cap):
+    """Steps that wait only for their tree dependencies (and the readers of
+    the workspace they overwrite) compute every value with the same operands
+    in the same order as the chained schedule: identical bits.  A workspace
+    cap (cap > 1) puts several networks on one slot.  Also checked against
+    the oracle."""
+    n, edges, p, g, b = workload("n100_p3", batch=batch)
+    out = {}
+    ws = None
+    for chain in (True, False):
+        plan = _plan(n, edges, p, batch, dtype, "persistent", order_trials=4, chain_steps=chain,
+                     max_workspace=0 if ws is None or cap == 1 else ws // cap)
+        if ws is None and cap > 1:
+            ws = plan.ws_bytes
+            plan.close()
+            plan = _plan(n, edges, p, batch, dtype, "persistent", order_trials=4, chain_steps=chain,
+                         max_workspace=ws // cap)
+        for _ in range(3):  # repeated launches: a race would show as a changing bit
+            out.setdefault(chain, []).append(_run(plan, g, b))
+        plan.close()
+    for r in out[True] + out[False]:
+        assert np.array_equal(r[1], out[True][0][1])
+        assert np.array_equal(r[0], out[True][0][0])
+    sel = [0, 75, 149]
+    ref = _oracle_zz(n, edges, p, g[batch - 1], b[batch - 1], sel)
+    np.testing.assert_allclose(out[False][0][1][sel, batch - 1, 0], ref.real, atol=TOL[dtype], rtol=0)
+
+
 def test_workspace_too_small_is_an_error():
     from paper_2106_15740_gb300 import binding as qb
     n, edges, p, g, b = workload("n16_p1")

@@ -1,0 +1,219 @@
+"""The persistent queue's dependency graph, checked on the host (no GPU).
+
+A forward plan lets a step start once the steps whose outputs it reads and
+the readers of the workspace it overwrites are done (bucket elimination forms
+a tree, §Tensor network contraction), instead of chaining every step of a
+workspace slot.  That is only safe if every two steps that touch the same
+workspace elements, one of them writing, are ordered by the graph in queue
+order.  These tests take the schedule the library reports
+(``qt_plan_schedule``: each step's written element range, the steps it reads,
+its dependency list) and check exactly that, pair by pair, together with:
+every dependency lies earlier in the queue (a persistent kernel whose warps
+claim tasks in queue order cannot then wait forever); every read sees the
+write of the step it names, with no other write to those elements between
+them in queue order; and the tree order is shorter than the chain.
+"""
+import numpy as np
+import pytest
+
+from workloads import random_regular_graph
+
+
+def _plan(n, edges, p, B=4, chain=0, group_rows=0, max_workspace=0, order_trials=0, dtype=None):
+    from paper_2106_15740_gb300 import binding as qb
+    opt = qb.qt_plan_options_default()
+    opt.batch = B
+    opt.dtype = qb.QT_C64 if dtype is None else dtype
+    opt.mode = qb.QT_MODE_PERSISTENT
+    opt.chain_steps = chain
+    opt.group_rows = group_rows
+    opt.max_workspace = max_workspace
+    opt.order_trials = order_trials
+    return qb.qt_plan_create(n, edges, p, opt)
+
+
+def _schedule(plan):
+    from paper_2106_15740_gb300 import binding as qb
+    sch = qb.qt_plan_schedule(plan)
+    tasks = qb.qt_plan_tasks(plan)
+    return sch, tasks
+
+
+def check_schedule(sch, tasks):
+    """Asserts the schedule is race-free; returns (units, longest dependency
+    path in units, ordered conflicting pairs, of them between two edges' networks)."""
+    unit = sch["unit"]
+    n = len(unit)
+    # queue position of each unit (first task that runs it)
+    qpos = np.full(n, -1, dtype=np.int64)
+    for t, s in enumerate(tasks["step"]):
+        if qpos[s] < 0:
+            qpos[s] = t
+    units = np.nonzero(unit == np.arange(n))[0]
+    assert (qpos[units] >= 0).all()
+    order = units[np.argsort(qpos[units], kind="stable")]
+    # ancestors of each unit (python ints as bitsets over unit ranks), in queue order
+    rank = {int(u): i for i, u in enumerate(order)}
+    anc = [0] * len(order)
+    depth = [0] * len(order)
+    for i, u in enumerate(order):
+        d0, dc = int(sch["dep_first"][u]), int(sch["dep_count"][u])
+        a, dp = 0, 0
+        for d in sch["deps"][d0:d0 + dc]:
+            du = int(unit[d])
+            # a dependency is the last step of its unit (its done counter)
+            assert du != u
+            last = du + int((unit[du:] == du).sum()) - 1
+            assert int(d) == last, "a dependency must name the last step of its group"
+            j = rank[du]
+            assert j < i, "dependency later in the queue than the step waiting for it"
+            a |= anc[j] | (1 << j)
+            dp = max(dp, depth[j] + 1)
+        anc[i] = a
+        depth[i] = dp
+    step_rank = np.array([rank[int(u)] for u in unit])
+    # position of each step in execution order: units by queue order, a group's steps in order
+    pos = step_rank.astype(np.int64) * n + (np.arange(n) - unit)
+
+    lo, hi = sch["write_lo"], sch["write_hi"]
+    assert (hi > lo).all()
+    # access list: (lo, hi, step, is_write)
+    acc_lo, acc_hi, acc_step, acc_w = [lo], [hi], [np.arange(n)], [np.ones(n, bool)]
+    reads_of = []
+    for s in range(n):
+        srcs = sch["src"][sch["in_first"][s]:sch["in_first"][s + 1]]
+        reads_of.append(srcs)
+        for a in srcs:
+            # a step never reads what it writes
+            assert hi[a] <= lo[s] or hi[s] <= lo[a]
+    rs = np.repeat(np.arange(n), np.diff(sch["in_first"]))
+    acc_lo.append(lo[sch["src"]]); acc_hi.append(hi[sch["src"]]); acc_step.append(rs)
+    acc_w.append(np.zeros(len(rs), bool))
+    L, H, S, Wr = (np.concatenate(x) for x in (acc_lo, acc_hi, acc_step, acc_w))
+    # all overlapping pairs with a write, by a sweep over start points
+    o = np.argsort(L, kind="stable")
+    L, H, S, Wr = L[o], H[o], S[o], Wr[o]
+    step_edge = np.zeros(n, dtype=np.int64)
+    for t, s in enumerate(tasks["step"]):
+        k = -int(tasks["chunk"][t]) if tasks["chunk"][t] < 0 else 1
+        step_edge[s:s + k] = tasks["edge"][t]
+    pairs = cross = 0
+    for i in range(len(L)):
+        j = i + 1 + np.nonzero(L[i + 1:np.searchsorted(L, H[i], "left")] < H[i])[0]
+        j = j[(S[j] != S[i]) & (Wr[j] | Wr[i])]
+        for k in j:
+            a, b = int(S[i]), int(S[k])
+            if pos[a] > pos[b]:
+                a, b = b, a
+            if unit[a] == unit[b]:
+                continue  # one warp runs a group's steps in order
+            ra, rb = int(step_rank[a]), int(step_rank[b])
+            assert (anc[rb] >> ra) & 1, f"steps {a} and {b} touch the same elements unordered"
+            pairs += 1
+            cross += int(step_edge[a] != step_edge[b])
+    # every read sees its source's write: no write to those elements between them
+    wo = np.argsort(pos)
+    for s in range(n):
+        for a in reads_of[s]:
+            between = wo[(pos[wo] > pos[a]) & (pos[wo] < pos[s])]
+            clash = between[(lo[between] < hi[a]) & (hi[between] > lo[a])]
+            assert len(clash) == 0, f"step {s} reads {a} after {clash[:3]} overwrote it"
+    return len(order), max(depth) + 1, pairs, cross
+
+
+@pytest.mark.parametrize("group_rows", [0, -1, 1 << 20])
+def test_tree_schedule_is_race_free(qtlib, group_rows):
+    n = 16
+    edges = random_regular_graph(n, 3, 31)
+    plan = _plan(n, edges, 2, group_rows=group_rows)
+    from paper_2106_15740_gb300 import binding as qb
+    try:
+        units, depth, pairs, cross = check_schedule(*_schedule(plan))
+    finally:
+        qb.qt_plan_free(plan)
+    assert cross == 0  # one slot per network: nothing shared between edges
+    if group_rows <= 0:  # (with every step grouped, each network is a single task)
+        assert pairs > 0 and depth < units
+
+
+def test_tree_schedule_with_shared_slots_is_race_free(qtlib):
+    """A workspace cap puts several networks on one slot: a network's first
+    steps then reuse the arena of the network before it."""
+    from paper_2106_15740_gb300 import binding as qb
+    n = 16
+    edges = random_regular_graph(n, 3, 32)
+    full = _plan(n, edges, 3)
+    ws = qb.qt_plan_workspace_size(full)
+    qb.qt_plan_free(full)
+    plan = _plan(n, edges, 3, max_workspace=ws // 3)
+    try:
+        units, depth, pairs, cross = check_schedule(*_schedule(plan))
+    finally:
+        qb.qt_plan_free(plan)
+    assert cross > 0  # networks of one slot reuse each other's arena
+    assert pairs > 0 and depth < units
+
+
+def test_chain_schedule_is_one_path_per_slot(qtlib):
+    from paper_2106_15740_gb300 import binding as qb
+    n = 12
+    edges = random_regular_graph(n, 3, 33)
+    plan = _plan(n, edges, 2, chain=1, group_rows=-1)
+    try:
+        sch, tasks = _schedule(plan)
+        units, depth, _, _ = check_schedule(sch, tasks)
+    finally:
+        qb.qt_plan_free(plan)
+    assert (sch["dep_count"] <= 1).all()
+    # one path per slot: each network's steps all lie on its slot's path
+    per_edge = np.bincount(tasks["edge"][tasks["chunk"] <= 0])
+    assert depth >= per_edge.max()
+
+
+def test_tree_schedule_of_searched_orders_is_race_free(qtlib):
+    """Randomised greedy orders and complex128 (other arena sizes)."""
+    from paper_2106_15740_gb300 import binding as qb
+    n = 20
+    edges = random_regular_graph(n, 3, 34)
+    plan = _plan(n, edges, 2, B=3, order_trials=8, dtype=qb.QT_C128)
+    try:
+        units, depth, pairs, _ = check_schedule(*_schedule(plan))
+    finally:
+        qb.qt_plan_free(plan)
+    assert pairs > 0 and depth < units
+
+
+def test_schedule_rejects_gradient_plans(qtlib):
+    from paper_2106_15740_gb300 import binding as qb
+    n = 8
+    edges = random_regular_graph(n, 3, 35)
+    opt = qb.qt_plan_options_default()
+    opt.batch = 2
+    opt.mode = qb.QT_MODE_PERSISTENT
+    opt.gradient = 1
+    plan = qb.qt_plan_create(n, edges, 1, opt)
+    try:
+        with pytest.raises(Exception):
+            qb.qt_plan_schedule(plan)
+    finally:
+        qb.qt_plan_free(plan)
+
+
+def test_checker_finds_a_dropped_dependency(qtlib):
+    """The check itself: remove the dependencies of one step that reads
+    another task's output and the pair is reported unordered."""
+    from paper_2106_15740_gb300 import binding as qb
+    n = 12
+    edges = random_regular_graph(n, 3, 36)
+    plan = _plan(n, edges, 2, group_rows=-1)
+    try:
+        sch, tasks = _schedule(plan)
+    finally:
+        qb.qt_plan_free(plan)
+    check_schedule(sch, tasks)
+    s = next(s for s in range(len(sch["unit"])) if sch["in_first"][s + 1] > sch["in_first"][s])
+    bad = dict(sch)
+    bad["dep_count"] = sch["dep_count"].copy()
+    bad["dep_count"][s] = 0
+    with pytest.raises(AssertionError, match="unordered"):
+        check_schedule(bad, tasks)
