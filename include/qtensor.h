@@ -137,7 +137,10 @@ typedef struct {
   int32_t max_width;      /* width budget; an edge above it fails with QT_EWIDTH unless sliced
                              (<=0: 31) */
   int32_t lane_items;     /* work items per lane in one warp tile: 8, 16, 32 or 64 (<=0: by batch) */
-  int64_t max_workspace;  /* cap on workspace bytes (<=0: no cap); sets edge concurrency */
+  int64_t max_workspace;  /* cap on the bytes of the workspace's data region -- intermediates,
+                             leaf factors, scalars -- (<=0: no cap); sets edge concurrency.  The
+                             step descriptors and the task queue (bytes per queued task, not
+                             set by concurrency) come on top */
   int32_t group_rows;     /* persistent mode: consecutive buckets of one edge with at most this many
                              rows run back to back in one task (0: by batch, <0: never) */
   int32_t edge_begin;     /* plan the edges [edge_begin, edge_end) of the graph; */
@@ -171,13 +174,16 @@ typedef struct {
                              forward steps before its adjoint steps (less memory, more traffic;
                              results equal up to rounding order) */
   int32_t chain_steps;    /* persistent mode: 0 (default) a queued step waits only for the steps
-                             whose outputs it reads (bucket elimination forms a tree) and for
-                             the readers of the workspace its output reuses, so independent
-                             buckets of a network run at the same time; a network's first steps
-                             wait for the previous network on the same workspace slot.  1: every
+                             that last wrote what it reads (bucket elimination forms a tree: the
+                             buckets that produced its inputs) and for the last writer and the
+                             readers of the workspace it writes, which the arena may reuse --
+                             also across the networks that share a workspace slot.  Independent
+                             buckets then run at the same time; an adjoint step of a gradient
+                             plan likewise waits for its bucket's output adjoint, its other
+                             operands and the users of the space its target reuses.  1: every
                              step waits for the step planned before it on its slot (one chain
-                             per slot).  Gradient plans always chain.  Results are bit-identical
-                             either way */
+                             per slot).  Energies are bit-identical either way; gradients agree
+                             up to the order of the atomic additions some adjoint steps make */
 } qt_plan_options;
 
 /* Fill `opt` with defaults: batch 1, QT_C128, QT_MODE_PER_BUCKET, no gradient,
@@ -323,25 +329,26 @@ qt_status qt_plan_set_trace(qt_plan* plan, void* trace, size_t bytes);
 qt_status qt_plan_tasks(const qt_plan* plan, int32_t* n_tasks, int32_t* step, int32_t* chunk,
                         int32_t* out_rank, int32_t* edge, int32_t* n_in);
 
-/* Schedule of a forward persistent plan, for checking on the host that
- * steps which touch the same workspace elements are ordered (§bucket
- * elimination: a bucket reads the tensors earlier buckets produced).  Step s
- * (0 <= s < n_steps, the order the plan lists them) writes data elements
- * [write_lo[s], write_hi[s]) (complex elements of the plan's dtype from the
- * data base) and reads the outputs of the steps src[in_first[s] ..
- * in_first[s + 1]) (leaf factors are written before the launch and only read:
- * not listed).  The queue runs steps in tasks: unit[s] is the first step of
- * the task group that runs s (s itself unless single-tile steps are grouped;
- * a group runs its steps in order on one warp; the chunks of one step write
- * disjoint rows).  A task of unit u starts once every step in
- * deps[dep_first[u] .. dep_first[u] + dep_count[u]) is complete (dep_count is
- * 0 for the other steps of a group).  Arrays may be NULL to ask only for
- * n_steps, n_deps and n_reads; otherwise in_first holds n_steps + 1 entries,
- * deps n_deps, src n_reads and the others n_steps.  QT_ESTATE for a gradient
- * or per-bucket plan. */
-qt_status qt_plan_schedule(const qt_plan* plan, int32_t* n_steps, int32_t* n_deps, int32_t* n_reads,
-                           int32_t* dep_first, int32_t* dep_count, int32_t* deps, int32_t* in_first,
-                           int32_t* src, int32_t* unit, int64_t* write_lo, int64_t* write_hi);
+/* Schedule of a persistent plan, for checking on the host that steps which
+ * touch the same workspace elements are ordered (§bucket elimination: a
+ * bucket reads the tensors earlier buckets produced; the adjoint sweep reads
+ * them again).  Step s (0 <= s < n_steps, the order the plan lists them)
+ * touches the data elements [acc_lo[a], acc_hi[a]) for a in acc_first[s] ..
+ * acc_first[s + 1] (complex elements of the plan's dtype from the data base),
+ * writing them if acc_write[a] (an accumulation counts as a write) and
+ * reading them otherwise; leaf factors, written before the launch and only
+ * read, are not listed.  The queue runs steps in tasks: unit[s] is the first
+ * step of the task group that runs s (s itself unless single-tile steps are
+ * grouped; a group runs its steps in order on one warp; the chunks of one
+ * step write disjoint rows).  A task of unit u starts once every step in
+ * deps[dep_first[u] .. dep_first[u] + dep_count[u]) is complete (dep_count
+ * is 0 for the other steps of a group).  Arrays may be NULL to ask only for
+ * n_steps, n_deps and n_access; otherwise acc_first holds n_steps + 1
+ * entries, deps n_deps, acc_lo, acc_hi and acc_write n_access, and the
+ * others n_steps.  QT_ESTATE for a per-bucket plan. */
+qt_status qt_plan_schedule(const qt_plan* plan, int32_t* n_steps, int32_t* n_deps, int32_t* n_access,
+                           int32_t* dep_first, int32_t* dep_count, int32_t* deps, int32_t* acc_first,
+                           int64_t* acc_lo, int64_t* acc_hi, int32_t* acc_write, int32_t* unit);
 
 void qt_plan_free(qt_plan* plan);
 

@@ -98,8 +98,8 @@ def lib():
             "qt_representation_cost": [C.POINTER(qt_graph), i32, i32, i32, i32, pi32, pi32, pd],
             "qt_plan_set_trace": [vp, vp, sz],
             "qt_plan_tasks": [vp, pi32, pi32, pi32, pi32, pi32, pi32],
-            "qt_plan_schedule": [vp, pi32, pi32, pi32, pi32, pi32, pi32, pi32, pi32, pi32,
-                                 C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
+            "qt_plan_schedule": [vp, pi32, pi32, pi32, pi32, pi32, pi32, pi32,
+                                 C.POINTER(C.c_int64), C.POINTER(C.c_int64), pi32, pi32],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -331,24 +331,24 @@ def qt_plan_tasks(plan):
 
 
 def qt_plan_schedule(plan):
-    """Schedule of a forward persistent plan as a dict of arrays (see the C
-    header): dep_first, dep_count, deps, in_first, src, unit, write_lo, write_hi."""
-    ns, nd, nr = C.c_int32(), C.c_int32(), C.c_int32()
-    _check(lib().qt_plan_schedule(plan, C.byref(ns), C.byref(nd), C.byref(nr), *([None] * 9)))
+    """Schedule of a persistent plan as a dict of arrays (see the C header):
+    dep_first, dep_count, deps, acc_first, acc_lo, acc_hi, acc_write, unit."""
+    ns, nd, na = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(lib().qt_plan_schedule(plan, C.byref(ns), C.byref(nd), C.byref(na), *([None] * 9)))
     n = ns.value
     out = {k: np.empty(n, dtype=np.int32) for k in ("dep_first", "dep_count", "unit")}
     out["deps"] = np.empty(max(nd.value, 1), dtype=np.int32)
-    out["in_first"] = np.empty(n + 1, dtype=np.int32)
-    out["src"] = np.empty(max(nr.value, 1), dtype=np.int32)
-    out["write_lo"] = np.empty(n, dtype=np.int64)
-    out["write_hi"] = np.empty(n, dtype=np.int64)
+    out["acc_first"] = np.empty(n + 1, dtype=np.int32)
+    out["acc_lo"] = np.empty(max(na.value, 1), dtype=np.int64)
+    out["acc_hi"] = np.empty(max(na.value, 1), dtype=np.int64)
+    out["acc_write"] = np.empty(max(na.value, 1), dtype=np.int32)
     p64 = lambda a: a.ctypes.data_as(C.POINTER(C.c_int64))
-    _check(lib().qt_plan_schedule(plan, C.byref(ns), C.byref(nd), C.byref(nr), _as_pi32(out["dep_first"]),
-                                  _as_pi32(out["dep_count"]), _as_pi32(out["deps"]), _as_pi32(out["in_first"]),
-                                  _as_pi32(out["src"]), _as_pi32(out["unit"]), p64(out["write_lo"]),
-                                  p64(out["write_hi"])))
-    out["deps"] = out["deps"][:nd.value]
-    out["src"] = out["src"][:nr.value]
+    _check(lib().qt_plan_schedule(plan, C.byref(ns), C.byref(nd), C.byref(na), _as_pi32(out["dep_first"]),
+                                  _as_pi32(out["dep_count"]), _as_pi32(out["deps"]), _as_pi32(out["acc_first"]),
+                                  p64(out["acc_lo"]), p64(out["acc_hi"]), _as_pi32(out["acc_write"]),
+                                  _as_pi32(out["unit"])))
+    for k, m in (("deps", nd.value), ("acc_lo", na.value), ("acc_hi", na.value), ("acc_write", na.value)):
+        out[k] = out[k][:m]
     return out
 
 

@@ -527,37 +527,29 @@ qt_status qt_plan_tasks(const qt_plan* plan, int32_t* n_tasks, int32_t* step, in
   return QT_OK;
 }
 
-qt_status qt_plan_schedule(const qt_plan* plan, int32_t* n_steps, int32_t* n_deps, int32_t* n_reads,
-                           int32_t* dep_first, int32_t* dep_count, int32_t* deps, int32_t* in_first, int32_t* src,
-                           int32_t* unit, int64_t* write_lo, int64_t* write_hi) {
-  if (!plan || !n_steps || !n_deps || !n_reads) return fail(QT_EINVAL, "NULL argument");
+qt_status qt_plan_schedule(const qt_plan* plan, int32_t* n_steps, int32_t* n_deps, int32_t* n_access,
+                           int32_t* dep_first, int32_t* dep_count, int32_t* deps, int32_t* acc_first,
+                           int64_t* acc_lo, int64_t* acc_hi, int32_t* acc_write, int32_t* unit) {
+  if (!plan || !n_steps || !n_deps || !n_access) return fail(QT_EINVAL, "NULL argument");
   const Plan& P = plan->P;
-  if (P.opt.mode != QT_MODE_PERSISTENT || P.opt.gradient)
-    return fail(QT_ESTATE, "the schedule is reported for forward persistent plans");
+  if (P.opt.mode != QT_MODE_PERSISTENT) return fail(QT_ESTATE, "the schedule is reported for persistent plans");
   const int32_t ns = (int32_t)P.buckets.size();
-  int32_t nr = 0;
-  for (const DevBucket& d : P.buckets)
-    for (int32_t k = 0; k < d.n_in; ++k) nr += d.in[k].src >= 0 ? 1 : 0;
   *n_steps = ns;
   *n_deps = (int32_t)P.deps.size();
-  *n_reads = nr;
-  if (!dep_first || !dep_count || !deps || !in_first || !src || !unit || !write_lo || !write_hi) return QT_OK;
+  *n_access = (int32_t)P.acc_lo.size();
+  if (!dep_first || !dep_count || !deps || !acc_first || !acc_lo || !acc_hi || !acc_write || !unit) return QT_OK;
   for (int32_t s = 0; s < ns; ++s) unit[s] = s;
   for (const DevTask& t : P.tasks)
     for (int32_t k = 1; k < -t.chunk; ++k) unit[t.bucket + k] = t.bucket;
-  int32_t r = 0;
   for (int32_t s = 0; s < ns; ++s) {
-    const DevBucket& d = P.buckets[s];
-    dep_first[s] = d.dep;
-    dep_count[s] = unit[s] == s ? d.n_dep : 0;
-    in_first[s] = r;
-    for (int32_t k = 0; k < d.n_in; ++k)
-      if (d.in[k].src >= 0) src[r++] = d.in[k].src;
-    write_lo[s] = d.out_off;
-    write_hi[s] = d.out_off + d.n_rows * (int64_t)P.opt.batch;
+    dep_first[s] = P.buckets[s].dep;
+    dep_count[s] = unit[s] == s ? P.buckets[s].n_dep : 0;
   }
-  in_first[ns] = r;
   std::copy(P.deps.begin(), P.deps.end(), deps);
+  std::copy(P.acc_first.begin(), P.acc_first.end(), acc_first);
+  std::copy(P.acc_lo.begin(), P.acc_lo.end(), acc_lo);
+  std::copy(P.acc_hi.begin(), P.acc_hi.end(), acc_hi);
+  for (size_t a = 0; a < P.acc_w.size(); ++a) acc_write[a] = P.acc_w[a];
   return QT_OK;
 }
 

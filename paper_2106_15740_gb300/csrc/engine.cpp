@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <cstddef>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <queue>
 
@@ -103,7 +104,6 @@ static DevInput input_record(uint32_t mask, int64_t off, int32_t flags) {
   fill_runs(mask, &in);
   in.off = off;
   in.flags = flags;
-  in.src = -1;
   return in;
 }
 
@@ -122,87 +122,100 @@ struct GradOp {
   std::vector<int64_t> loc;  // arena offset of each intermediate input (-1 for the leaf factor)
 };
 
-// Steps of one forward network that must be complete before bucket i runs
-// (indices within the network).  Bucket elimination forms a tree: bucket i
-// reads only the outputs of the buckets in its in_src, so it waits for those
-// and not for the whole order before it.  Memory adds the rest: the arena
-// hands out space in the elimination order (output allocated before the
-// step's inputs are released), so bucket i's output may overwrite an
-// intermediate that an earlier bucket read; i then also waits for that
-// reader.  The arena is replayed in order with, per element range, the last
-// step that read it; a write also overtakes the range's earlier writer,
-// whose reader it waits for.  Entries that another entry already depends on
-// (transitively) are dropped.  `off` holds the arena offsets of the outputs;
-// outputs of rank 0 live outside the arena.  *sinks gets the buckets whose
-// output no later bucket reads.  False if the offsets contradict the order
-// (a live intermediate overwritten).
-static bool forward_deps(const EdgePlan& ep, const std::vector<int64_t>& off, int64_t B, int64_t al,
-                         std::vector<std::vector<int32_t>>* deps, std::vector<int32_t>* sinks) {
-  const int32_t nb = (int32_t)ep.buckets.size();
-  auto size_of = [&](int32_t i) { return ((((int64_t)1 << ep.buckets[i].out_rank) * B) + al - 1) / al * al; };
-  std::vector<int32_t> reader(nb, -1);
-  for (int32_t i = 0; i < nb; ++i)
-    for (int32_t c : ep.buckets[i].in_src)
-      if (c >= 0) reader[c] = i;
-  sinks->clear();
-  for (int32_t i = 0; i < nb; ++i)
-    if (reader[i] < 0) sinks->push_back(i);
-  // released ranges: start -> (end, step that read it last); disjoint
-  std::map<int64_t, std::pair<int64_t, int32_t>> dead;
-  const int32_t W = (nb + 63) / 64;
-  std::vector<uint64_t> anc((size_t)nb * W, 0);  // bit d of row i: i depends on d (transitively)
-  deps->assign(nb, {});
+// Dependencies of the steps of one workspace slot from the data elements
+// they touch.  The slot runs its networks one after another, each network's
+// steps in plan order (`nets`: global step ranges); that order is correct
+// run sequentially, and a step may start early as long as it keeps every
+// conflicting access in that order: it waits for the last writer of what it
+// reads (bucket elimination: the buckets that produced its inputs) and for
+// the last writer and all readers since of what it writes (the arena reuses
+// released space).  An accumulating write (atomic adds) counts as a write.
+// Within a network, entries that another entry already depends on
+// (transitively) are dropped; entries in earlier networks of the slot are
+// kept as found.  deps[s] gets global step indices, all earlier in the slot.
+static void access_deps(const Plan& P, const std::vector<std::pair<int32_t, int32_t>>& nets,
+                        std::vector<std::vector<int32_t>>* deps) {
+  struct Seg {
+    int64_t end;
+    int32_t writer;
+    std::vector<int32_t> readers;
+  };
+  std::map<int64_t, Seg> mem;  // disjoint segments of touched elements
+  // split so that a segment boundary falls at x (x inside a segment)
+  auto split = [&](int64_t x) {
+    auto it = mem.upper_bound(x);
+    if (it == mem.begin()) return;
+    --it;
+    if (it->first < x && it->second.end > x) {
+      Seg tail = it->second;
+      it->second.end = x;
+      mem.emplace(x, std::move(tail));
+    }
+  };
+  // visit the segments covering [lo, hi), creating untouched ones
+  auto cover = [&](int64_t lo, int64_t hi, const std::function<void(Seg&)>& f) {
+    split(lo);
+    split(hi);
+    int64_t x = lo;
+    auto it = mem.lower_bound(lo);
+    while (x < hi) {
+      if (it == mem.end() || it->first > x) {
+        const int64_t e = it == mem.end() ? hi : std::min(hi, it->first);
+        it = mem.emplace_hint(it, x, Seg{e, -1, {}});
+      }
+      f(it->second);
+      x = it->second.end;
+      ++it;
+    }
+  };
   std::vector<int32_t> raw;
-  for (int32_t i = 0; i < nb; ++i) {
-    const Bucket& bk = ep.buckets[i];
-    raw.clear();
-    for (int32_t c : bk.in_src)
-      if (c >= 0) raw.push_back(c);
-    if (bk.out_rank > 0) {
-      const int64_t a0 = off[i], a1 = a0 + size_of(i);
-      auto it = dead.upper_bound(a0);
-      if (it != dead.begin()) --it;
-      while (it != dead.end() && it->first < a1) {
-        const int64_t b0 = it->first, b1 = it->second.first;
-        const int32_t r = it->second.second;
-        if (b1 <= a0) {
-          ++it;
-          continue;
+  std::vector<uint64_t> anc;
+  for (const auto& nr : nets) {
+    const int32_t s0 = nr.first, n = nr.second - nr.first, W = (n + 63) / 64;
+    anc.assign((size_t)n * W, 0);
+    for (int32_t s = s0; s < s0 + n; ++s) {
+      raw.clear();
+      const int32_t a0 = P.acc_first[s], a1 = P.acc_first[s + 1];
+      for (int32_t a = a0; a < a1; ++a)
+        cover(P.acc_lo[a], P.acc_hi[a], [&](Seg& g) {
+          if (g.writer >= 0) raw.push_back(g.writer);
+          if (P.acc_w[a]) raw.insert(raw.end(), g.readers.begin(), g.readers.end());
+        });
+      for (int32_t a = a0; a < a1; ++a)  // reads first: a write by the same step supersedes them
+        if (!P.acc_w[a]) cover(P.acc_lo[a], P.acc_hi[a], [&](Seg& g) { g.readers.push_back(s); });
+      for (int32_t a = a0; a < a1; ++a)
+        if (P.acc_w[a])
+          cover(P.acc_lo[a], P.acc_hi[a], [&](Seg& g) {
+            g.writer = s;
+            g.readers.clear();
+          });
+      std::sort(raw.begin(), raw.end());
+      raw.erase(std::unique(raw.begin(), raw.end()), raw.end());
+      raw.erase(std::remove(raw.begin(), raw.end(), s), raw.end());
+      // the slot runs its networks in its own order, so an earlier network's
+      // steps may have larger indices: "inside" means within [s0, s0 + n)
+      auto inside = [&](int32_t d) { return d >= s0 && d < s0 + n; };
+      uint64_t* ai = &anc[(size_t)(s - s0) * W];
+      for (int32_t d : raw)
+        if (inside(d)) {
+          const uint64_t* ad = &anc[(size_t)(d - s0) * W];
+          for (int32_t w = 0; w < W; ++w) ai[w] |= ad[w];
         }
-        raw.push_back(r);
-        it = dead.erase(it);
-        if (b0 < a0) dead[b0] = {a0, r};  // keep the parts outside [a0, a1)
-        if (b1 > a1) dead[a1] = {b1, r};
+      std::vector<int32_t>& out = (*deps)[s];
+      out.clear();
+      for (int32_t d : raw) {
+        bool implied = false;
+        if (inside(d))
+          for (int32_t d2 : raw)
+            if (d2 != d && inside(d2) && ((anc[(size_t)(d2 - s0) * W + ((d - s0) >> 6)] >> ((d - s0) & 63)) & 1u)) {
+              implied = true;
+              break;
+            }
+        if (!implied) out.push_back(d);
+        if (inside(d)) ai[(d - s0) >> 6] |= (uint64_t)1 << ((d - s0) & 63);
       }
     }
-    for (int32_t c : bk.in_src) {
-      if (c < 0 || ep.buckets[c].out_rank == 0) continue;
-      const int64_t b0 = off[c], b1 = b0 + size_of(c);
-      auto it = dead.lower_bound(b0);  // a live range cannot already be marked released
-      if (it != dead.end() && it->first < b1) return false;
-      if (it != dead.begin() && std::prev(it)->second.first > b0) return false;
-      dead[b0] = {b1, i};
-    }
-    std::sort(raw.begin(), raw.end());
-    raw.erase(std::unique(raw.begin(), raw.end()), raw.end());
-    uint64_t* ai = &anc[(size_t)i * W];
-    for (int32_t d : raw) {
-      if (d >= i) return false;
-      const uint64_t* ad = &anc[(size_t)d * W];
-      for (int32_t w = 0; w < W; ++w) ai[w] |= ad[w];
-    }
-    for (int32_t d : raw) {
-      bool implied = false;
-      for (int32_t d2 : raw)
-        if (d2 != d && ((anc[(size_t)d2 * W + (d >> 6)] >> (d & 63)) & 1u)) {
-          implied = true;
-          break;
-        }
-      if (!implied) (*deps)[i].push_back(d);
-      ai[d >> 6] |= (uint64_t)1 << (d & 63);
-    }
   }
-  return true;
 }
 
 // Reverse-mode plan of one network with checkpointing.  The bucket order is
@@ -477,10 +490,18 @@ qt_status compile_plan(Plan* P) {
   P->lbar_elems = grad ? leaf_pool : 0;
 
   // ---- device records: per edge, forward steps then adjoint steps ----
-  // forward plans: per step its dependencies inside its network (global step
-  // indices), per network the steps no other step of it reads
-  std::vector<std::vector<int32_t>> fdeps;
-  std::vector<std::vector<int32_t>> net_sinks(n_edges);
+  // Each record also lists the data elements it touches (acc_*), from which
+  // the persistent queue derives its dependencies.
+  P->acc_first.assign(1, 0);
+  P->acc_lo.clear();
+  P->acc_hi.clear();
+  P->acc_w.clear();
+  auto touch = [&](int64_t lo, int64_t n, bool w) {
+    P->acc_lo.push_back(lo);
+    P->acc_hi.push_back(lo + n);
+    P->acc_w.push_back(w ? 1 : 0);
+  };
+  auto step_done = [&]() { P->acc_first.push_back((int32_t)P->acc_lo.size()); };
   const int32_t geom_bv = tile_geom(P->opt.dtype, B, P->opt.lane_items).Bv;
   P->buckets.clear();
   P->edge_first.assign(n_edges + 1, 0);
@@ -529,32 +550,31 @@ qt_status compile_plan(Plan* P) {
       for (int32_t k = 0; k < d.n_in; ++k) d.in[k] = in_record(i, k, loc[k]);
       return d;
     };
+    // intermediates of the network: elements of the output of bucket c
+    auto tensor_el = [&](int32_t c) { return ((int64_t)1 << ep.buckets[c].out_rank) * B; };
+    auto fwd_push = [&](int32_t i, int64_t out, const std::vector<int64_t>& loc) {
+      const Bucket& bk = ep.buckets[i];
+      P->buckets.push_back(fwd_record(i, out, loc));
+      for (size_t k = 0; k < bk.in_src.size(); ++k)
+        if (bk.in_src[k] >= 0) touch(rbase + loc[k], tensor_el(bk.in_src[k]), false);
+      touch(P->buckets.back().out_off, P->buckets.back().n_rows * B, true);
+      step_done();
+    };
     if (!grad) {
-      const int32_t g0 = (int32_t)P->buckets.size();
       for (int32_t i = 0; i < (int32_t)ep.buckets.size(); ++i) {
         const Bucket& bk = ep.buckets[i];
         std::vector<int64_t> loc;
         for (int32_t c : bk.in_src) loc.push_back(c >= 0 ? out_off[e][c] : -1);
-        P->buckets.push_back(fwd_record(i, out_off[e][i], loc));
-        for (int32_t k = 0; k < (int32_t)bk.in_src.size(); ++k)
-          if (bk.in_src[k] >= 0) P->buckets.back().in[k].src = g0 + bk.in_src[k];
+        fwd_push(i, out_off[e][i], loc);
         if (bk.leaf_rank > 0) leaf_record(i);
       }
-      std::vector<std::vector<int32_t>> ld;
-      std::vector<int32_t> sk;
-      if (!forward_deps(ep, out_off[e], B, al, &ld, &sk))
-        return fail(QT_EINVAL, "internal: arena offsets contradict the bucket order");
-      fdeps.resize(P->buckets.size());
-      for (int32_t i = 0; i < (int32_t)ld.size(); ++i)
-        for (int32_t d : ld[i]) fdeps[g0 + i].push_back(g0 + d);
-      for (int32_t i : sk) net_sinks[e].push_back(g0 + i);
     }
     for (const GradOp& op : gops[e]) {
       const Bucket& bk = ep.buckets[op.bucket];
       for (size_t k = 0; k < op.loc.size(); ++k)  // every intermediate operand is resident
         if (bk.in_src[k] >= 0 && op.loc[k] < 0) return fail(QT_EINVAL, "internal: gradient plan reads a released tensor");
       if (op.kind == kStepFwd) {
-        P->buckets.push_back(fwd_record(op.bucket, op.out, op.loc));
+        fwd_push(op.bucket, op.out, op.loc);
         if (!op.recompute && bk.leaf_rank > 0) leaf_record(op.bucket);
         continue;
       }
@@ -577,6 +597,10 @@ qt_status compile_plan(Plan* P) {
         d.in[n] = input_record(0u, d.out_off, 0);
         d.n_in = n;
         P->buckets.push_back(d);
+        for (int32_t sb : ep.scalars)
+          if (sb != op.bucket) touch(scal_base + out_off[e][sb], B, false);
+        touch(d.out_off, 2 * B, true);
+        step_done();
         continue;
       }
       if (op.kind == kStepZero) {
@@ -585,6 +609,8 @@ qt_status compile_plan(Plan* P) {
         d.n_rows = (int64_t)1 << op.zero_rank;
         d.out_off = rbase + op.out;
         P->buckets.push_back(d);
+        touch(d.out_off, d.n_rows * B, true);
+        step_done();
         continue;
       }
       if ((int32_t)bk.in_src.size() + (bk.out_rank > 0 ? 1 : 0) + 1 > kDevMaxIn)
@@ -617,6 +643,12 @@ qt_status compile_plan(Plan* P) {
         d.n_rows = (int64_t)1 << (d.tgt_bits + d.comp_bits);  // = 2^out_rank
       }
       P->buckets.push_back(d);
+      if (op.gbar >= 0) touch(rbase + op.gbar, bk.out_rank > 0 ? tensor_el(op.bucket) : 2 * B, false);
+      for (int32_t j = 0; j < (int32_t)bk.in_src.size(); ++j)
+        if (j != op.input && bk.in_src[j] >= 0) touch(rbase + op.loc[j], tensor_el(bk.in_src[j]), false);
+      const int32_t t = bk.in_src[op.input];
+      touch(d.out_off, t >= 0 ? tensor_el(t) : ((int64_t)1 << bk.leaf_rank) * B, true);
+      step_done();
     }
     for (int32_t sb : ep.scalars) P->scal_off.push_back(scal_base + out_off[e][sb]);
     P->scal_begin[e + 1] = (int32_t)P->scal_off.size();
@@ -660,20 +692,29 @@ qt_status compile_plan(Plan* P) {
       if ((nt + d.span - 1) / d.span > INT32_MAX / 2) return fail(QT_EWIDTH, "step too large for the task queue");
     }
     const int32_t S = P->n_slots;
-    // Dependencies: gradient plans (and chain_steps) chain each step of a
-    // slot to the one queued before it.  Forward plans take the tree order of
-    // forward_deps; a step with no dependency inside its network waits for
-    // the sinks of the network the slot ran before (whose arena it reuses).
-    // The done counter of a grouped step is its group's last step (`rep`).
-    const bool chain = grad || P->opt.chain_steps != 0;
+    // Dependencies: with chain_steps each step of a slot waits for the task
+    // queued before it; otherwise for what access_deps finds from the
+    // elements the slot's steps touch.  The done counter of a grouped step is
+    // its group's last step (`rep`).
+    const bool chain = P->opt.chain_steps != 0;
+    std::vector<std::vector<int32_t>> sdeps(P->buckets.size());
+    if (!chain)
+      for (int32_t s = 0; s < S; ++s) {
+        std::vector<std::pair<int32_t, int32_t>> nets;
+        for (int32_t e : slot_edges[s]) nets.push_back({P->edge_first[e], P->edge_first[e + 1]});
+        access_deps(*P, nets, &sdeps);
+      }
     std::vector<int32_t> rep(P->buckets.size());
     for (size_t b = 0; b < rep.size(); ++b) rep[b] = (int32_t)b;
-    std::vector<std::vector<int32_t>> prev_sinks(S);
+    std::vector<int32_t> prev_last(S, -1);
     P->deps.clear();
     std::vector<int32_t> dl;
     auto add_deps = [&](int32_t s, int32_t b, int32_t self) {
-      const std::vector<int32_t>& own = chain || fdeps[b].empty() ? prev_sinks[s] : fdeps[b];
-      for (int32_t x : own)
+      if (chain) {
+        if (prev_last[s] >= 0) dl.push_back(prev_last[s]);
+        return;
+      }
+      for (int32_t x : sdeps[b])
         if (rep[x] != self) dl.push_back(rep[x]);
     };
     std::vector<size_t> ei(S, 0);
@@ -720,12 +761,11 @@ qt_status compile_plan(Plan* P) {
         P->buckets[gb].dep = (int32_t)P->deps.size();
         P->buckets[gb].n_dep = (int32_t)dl.size();
         P->deps.insert(P->deps.end(), dl.begin(), dl.end());
-        if (chain) prev_sinks[s].assign(1, last);
+        prev_last[s] = last;
         if ((int64_t)P->tasks.size() > INT32_MAX / 2) return fail(QT_ENOMEM, "task queue too long");
         if (++bi[s] == ns_e) {
           bi[s] = 0;
           ++ei[s];
-          if (!chain) prev_sinks[s] = net_sinks[e];
         }
       }
     }

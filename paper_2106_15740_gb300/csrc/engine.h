@@ -41,6 +41,11 @@ struct Plan {
   int64_t lbar_elems = 0;
   std::vector<DevTask> tasks;
   std::vector<int32_t> deps;               // dependency lists of the queued steps (DevBucket dep, n_dep)
+  // data elements each step touches: ranges acc_first[s] .. acc_first[s + 1] of
+  // [acc_lo, acc_hi), acc_w = 1 for a write (or an accumulation)
+  std::vector<int32_t> acc_first;
+  std::vector<int64_t> acc_lo, acc_hi;
+  std::vector<uint8_t> acc_w;
   std::vector<int64_t> scal_off;           // element offsets of scalar results
   std::vector<int32_t> scal_begin;         // CSR over edges
   int64_t tile_items = 0;                  // output rows per warp tile

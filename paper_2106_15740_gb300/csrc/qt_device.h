@@ -25,8 +25,7 @@ struct DevInput {
   int32_t nruns;
   uint32_t run[kDevMaxRuns];   // src | len << 8 | dst << 16
   int32_t flags;               // kIn* bits below
-  int32_t src;                 // forward plans: the step that writes this input (-1: leaf factor or
-                               // not recorded); host-side schedule checks only
+  int32_t pad;
 };
 constexpr int32_t kInLeaf = 1;    // written before the launch, read through L1
 constexpr int32_t kInNoPair = 2;  // one row per output row (no eliminated-variable bit): an adjoint

@@ -203,3 +203,41 @@ def test_checkpointed_gradient_on_n60_p4_edges():
         plan.close()
     np.testing.assert_allclose(out[1][0], out[0][0], atol=1e-11, rtol=0)
     np.testing.assert_allclose(out[1][1], out[0][1], atol=1e-11, rtol=0)
+
+
+@pytest.mark.parametrize("dtype,B,checkpoint,cap", [("c128", 1, 0, 1), ("c128", 2, 1 << 12, 2), ("c64", 64, 0, 1),
+                                                    ("c64", 3, 0, 2)])
+def test_tree_schedule_gradient_equals_chain(dtype, B, checkpoint, cap):
+    """Adjoint steps that wait only for what they read and for the users of
+    the space they reuse give the chained schedule's E and gradient: E
+    bit for bit, the gradient up to the order of the atomic additions of
+    accumulating adjoint steps.  cap = 2 halves the data region so that
+    networks share a workspace slot.  Repeated launches check that nothing
+    changes from run to run beyond that order; one angle set is checked
+    against the exact parameter-shift gradient."""
+    n, p = 14, 3
+    edges = random_regular_graph(n, 3, 12)
+    g, b = random_angles(B, p, 93)
+    out = {}
+    data = None
+    for chain in (True, False):
+        kw = dict(checkpoint_bytes=checkpoint, chain_steps=chain)
+        if cap > 1:
+            if data is None:
+                from paper_2106_15740_gb300 import binding as qb
+                probe = _grad_plan(n, edges, p, B, dtype, checkpoint_bytes=checkpoint)
+                data = int(qb.qt_plan_schedule(probe.plan)["acc_hi"].max()) * (16 if dtype == "c128" else 8)
+                probe.close()
+            kw["max_workspace"] = data * 2 // 3
+        plan = _grad_plan(n, edges, p, B, dtype, **kw)
+        out[chain] = [_run(plan, g, b) for _ in range(3)]
+        plan.close()
+    e0, g0 = out[True][0]
+    tol = 1e-12 if dtype == "c128" else 2e-6
+    for e, gg in out[True] + out[False]:
+        assert np.array_equal(e, e0)
+        np.testing.assert_allclose(gg, g0, atol=tol * max(1.0, np.abs(g0).max()), rtol=0)
+    k = B - 1
+    ref = np.concatenate(gr.param_shift_gradient(n, edges, g[k], b[k]))
+    np.testing.assert_allclose(out[False][0][1][k], ref,
+                               atol=1e-9 if dtype == "c128" else 2e-5 * max(1.0, np.abs(ref).max()), rtol=0)

@@ -1,17 +1,16 @@
 """The persistent queue's dependency graph, checked on the host (no GPU).
 
-A forward plan lets a step start once the steps whose outputs it reads and
-the readers of the workspace it overwrites are done (bucket elimination forms
-a tree, §Tensor network contraction), instead of chaining every step of a
-workspace slot.  That is only safe if every two steps that touch the same
-workspace elements, one of them writing, are ordered by the graph in queue
-order.  These tests take the schedule the library reports
-(``qt_plan_schedule``: each step's written element range, the steps it reads,
-its dependency list) and check exactly that, pair by pair, together with:
-every dependency lies earlier in the queue (a persistent kernel whose warps
-claim tasks in queue order cannot then wait forever); every read sees the
-write of the step it names, with no other write to those elements between
-them in queue order; and the tree order is shorter than the chain.
+A persistent plan lets a step start once the steps that last wrote what it
+reads, and the last writer and readers of what it writes, are done (bucket
+elimination forms a tree, §Tensor network contraction; the arena reuses
+released space), instead of chaining every step of a workspace slot.  That is
+only safe if every two steps that touch the same workspace elements, one of
+them writing, are ordered by the dependency graph as they are in queue order.
+These tests take the schedule the library reports (``qt_plan_schedule``: the
+element ranges each step reads and writes, its dependency list) and check
+exactly that, pair by pair, together with: every dependency lies earlier in
+the queue (a persistent kernel whose warps claim tasks in queue order cannot
+then wait forever), and the dependency paths are shorter than the chain.
 """
 import numpy as np
 import pytest
@@ -30,6 +29,12 @@ def _plan(n, edges, p, B=4, chain=0, group_rows=0, max_workspace=0, order_trials
     opt.max_workspace = max_workspace
     opt.order_trials = order_trials
     return qb.qt_plan_create(n, edges, p, opt)
+
+
+def _data_bytes(plan, es=8):
+    """Bytes of a plan's data region up to the last element any step touches."""
+    from paper_2106_15740_gb300 import binding as qb
+    return int(qb.qt_plan_schedule(plan)["acc_hi"].max()) * es
 
 
 def _schedule(plan):
@@ -75,28 +80,18 @@ def check_schedule(sch, tasks):
     # position of each step in execution order: units by queue order, a group's steps in order
     pos = step_rank.astype(np.int64) * n + (np.arange(n) - unit)
 
-    lo, hi = sch["write_lo"], sch["write_hi"]
-    assert (hi > lo).all()
-    # access list: (lo, hi, step, is_write)
-    acc_lo, acc_hi, acc_step, acc_w = [lo], [hi], [np.arange(n)], [np.ones(n, bool)]
-    reads_of = []
-    for s in range(n):
-        srcs = sch["src"][sch["in_first"][s]:sch["in_first"][s + 1]]
-        reads_of.append(srcs)
-        for a in srcs:
-            # a step never reads what it writes
-            assert hi[a] <= lo[s] or hi[s] <= lo[a]
-    rs = np.repeat(np.arange(n), np.diff(sch["in_first"]))
-    acc_lo.append(lo[sch["src"]]); acc_hi.append(hi[sch["src"]]); acc_step.append(rs)
-    acc_w.append(np.zeros(len(rs), bool))
-    L, H, S, Wr = (np.concatenate(x) for x in (acc_lo, acc_hi, acc_step, acc_w))
-    # all overlapping pairs with a write, by a sweep over start points
+    # every access as (lo, hi, step, is_write)
+    af = sch["acc_first"]
+    S = np.repeat(np.arange(n), np.diff(af))
+    L, H, Wr = sch["acc_lo"], sch["acc_hi"], sch["acc_write"].astype(bool)
+    assert len(S) == len(L) and (H > L).all()
     o = np.argsort(L, kind="stable")
     L, H, S, Wr = L[o], H[o], S[o], Wr[o]
     step_edge = np.zeros(n, dtype=np.int64)
     for t, s in enumerate(tasks["step"]):
         k = -int(tasks["chunk"][t]) if tasks["chunk"][t] < 0 else 1
         step_edge[s:s + k] = tasks["edge"][t]
+    # all overlapping pairs of two steps, one of them writing, by a sweep over start points
     pairs = cross = 0
     for i in range(len(L)):
         j = i + 1 + np.nonzero(L[i + 1:np.searchsorted(L, H[i], "left")] < H[i])[0]
@@ -111,13 +106,6 @@ def check_schedule(sch, tasks):
             assert (anc[rb] >> ra) & 1, f"steps {a} and {b} touch the same elements unordered"
             pairs += 1
             cross += int(step_edge[a] != step_edge[b])
-    # every read sees its source's write: no write to those elements between them
-    wo = np.argsort(pos)
-    for s in range(n):
-        for a in reads_of[s]:
-            between = wo[(pos[wo] > pos[a]) & (pos[wo] < pos[s])]
-            clash = between[(lo[between] < hi[a]) & (hi[between] > lo[a])]
-            assert len(clash) == 0, f"step {s} reads {a} after {clash[:3]} overwrote it"
     return len(order), max(depth) + 1, pairs, cross
 
 
@@ -143,9 +131,9 @@ def test_tree_schedule_with_shared_slots_is_race_free(qtlib):
     n = 16
     edges = random_regular_graph(n, 3, 32)
     full = _plan(n, edges, 3)
-    ws = qb.qt_plan_workspace_size(full)
+    data = _data_bytes(full)
     qb.qt_plan_free(full)
-    plan = _plan(n, edges, 3, max_workspace=ws // 3)
+    plan = _plan(n, edges, 3, max_workspace=data // 3)
     try:
         units, depth, pairs, cross = check_schedule(*_schedule(plan))
     finally:
@@ -183,17 +171,47 @@ def test_tree_schedule_of_searched_orders_is_race_free(qtlib):
     assert pairs > 0 and depth < units
 
 
-def test_schedule_rejects_gradient_plans(qtlib):
+@pytest.mark.parametrize("checkpoint", [False, True])
+def test_gradient_schedule_is_race_free(qtlib, checkpoint):
+    """The adjoint sweep reads the forward intermediates again, writes output
+    adjoints (zeroed first where it accumulates them) and reuses the arena;
+    with checkpointing it also re-runs forward steps.  Several networks share
+    a slot under a workspace cap."""
+    from paper_2106_15740_gb300 import binding as qb
+    n = 14
+    edges = random_regular_graph(n, 3, 35)
+
+    def grad_plan(cap, ckpt):
+        opt = qb.qt_plan_options_default()
+        opt.batch = 2
+        opt.dtype = qb.QT_C64
+        opt.mode = qb.QT_MODE_PERSISTENT
+        opt.gradient = 1
+        opt.max_workspace = cap
+        opt.checkpoint_bytes = ckpt
+        return qb.qt_plan_create(n, edges, 2, opt)
+
+    full = grad_plan(0, 0)
+    data = _data_bytes(full)
+    qb.qt_plan_free(full)
+    plan = grad_plan(data * 2 // 3, 4096 if checkpoint else 0)
+    try:
+        units, depth, pairs, cross = check_schedule(*_schedule(plan))
+    finally:
+        qb.qt_plan_free(plan)
+    assert pairs > 0 and cross > 0 and depth < units
+
+
+def test_schedule_rejects_per_bucket_plans(qtlib):
     from paper_2106_15740_gb300 import binding as qb
     n = 8
-    edges = random_regular_graph(n, 3, 35)
+    edges = random_regular_graph(n, 3, 37)
     opt = qb.qt_plan_options_default()
     opt.batch = 2
-    opt.mode = qb.QT_MODE_PERSISTENT
-    opt.gradient = 1
+    opt.mode = qb.QT_MODE_PER_BUCKET
     plan = qb.qt_plan_create(n, edges, 1, opt)
     try:
-        with pytest.raises(Exception):
+        with pytest.raises(qb.QTError):
             qb.qt_plan_schedule(plan)
     finally:
         qb.qt_plan_free(plan)
@@ -211,7 +229,9 @@ def test_checker_finds_a_dropped_dependency(qtlib):
     finally:
         qb.qt_plan_free(plan)
     check_schedule(sch, tasks)
-    s = next(s for s in range(len(sch["unit"])) if sch["in_first"][s + 1] > sch["in_first"][s])
+    # a step that reads an intermediate (it has a read access) and waits for something
+    s = next(s for s in range(len(sch["unit"]))
+             if sch["dep_count"][s] > 0 and not sch["acc_write"][sch["acc_first"][s]:sch["acc_first"][s + 1]].all())
     bad = dict(sch)
     bad["dep_count"] = sch["dep_count"].copy()
     bad["dep_count"][s] = 0
