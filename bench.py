@@ -41,9 +41,10 @@ WORKLOAD = dict(name="n100_p4", batch=64, dtype="c64", order_trials=100)
 # contraction order fixes the traffic): otherwise the traffic is reported as
 # null until that kernel and plan are captured again.
 TRAFFIC_CAPTURES = [
-    # orders searched per edge (100 trials), the bench plan; register load path (lean row tile)
-    {"sources_sha256_16": "471f7b1c1c3aeddd", "alg_bytes_per_angle_set": 5170666432 / 4,
-     "bytes_per_angle_set": (2153464576 + 2471153920) / 4},
+    # orders searched per edge (100 trials), the bench plan; register load path (lean row
+    # tile); steps wait for the dependencies found from the elements they touch
+    {"sources_sha256_16": "63c2243c03f50613", "alg_bytes_per_angle_set": 5170666432 / 4,
+     "bytes_per_angle_set": (2184769024 + 2472729344) / 4},
 ]
 
 
