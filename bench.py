@@ -37,14 +37,18 @@ WORKLOAD = dict(name="n100_p4", batch=64, dtype="c64", order_trials=100)
 # per angle set: dram__bytes_read.sum + dram__bytes_write.sum of one ncu
 # capture at B = 4 angle sets, which grows in proportion to B (checked at
 # B = 2), scaled to the launch's B.  It holds only for the kernel sources with
-# this digest and for the plan with these algorithmic bytes per angle set (the
-# contraction order fixes the traffic): otherwise the traffic is reported as
-# null until that kernel and plan are captured again.
+# this digest, for the plan with these algorithmic bytes per angle set (the
+# contraction order fixes the traffic) and for this queue order (which sets
+# what shares L2): otherwise the traffic is reported as null until that kernel
+# and plan are captured again.
 TRAFFIC_CAPTURES = [
     # orders searched per edge (100 trials), the bench plan; register load path (lean row
-    # tile); steps wait for the dependencies found from the elements they touch
+    # tile); steps wait for the dependencies found from the elements they touch; the queue
+    # takes the longest remaining dependency path first (the default) or the slots round-robin
     {"sources_sha256_16": "63c2243c03f50613", "alg_bytes_per_angle_set": 5170666432 / 4,
-     "bytes_per_angle_set": (2184769024 + 2472729344) / 4},
+     "queue_order": "critical_path", "bytes_per_angle_set": (2308382464 + 2503696896) / 4},
+    {"sources_sha256_16": "63c2243c03f50613", "alg_bytes_per_angle_set": 5170666432 / 4,
+     "queue_order": "round_robin", "bytes_per_angle_set": (2184769024 + 2472729344) / 4},
 ]
 
 
@@ -60,8 +64,10 @@ def _traffic(B, alg_bytes, profile_only):
     if profile_only:
         return None
     digest = _kernel_digest()
+    order = WORKLOAD.get("queue_order", "critical_path")
     for cap in TRAFFIC_CAPTURES:
-        if cap["sources_sha256_16"] == digest and abs(alg_bytes / B / cap["alg_bytes_per_angle_set"] - 1) < 1e-9:
+        if (cap["sources_sha256_16"] == digest and cap["queue_order"] == order
+                and abs(alg_bytes / B / cap["alg_bytes_per_angle_set"] - 1) < 1e-9):
             return cap["bytes_per_angle_set"] * B
     return None
 
@@ -254,6 +260,21 @@ def chain_comparison(n, edges, p, B, g, b, dev, torch):
     return out
 
 
+def round_robin_comparison(n, edges, p, B, g, b, dev, torch):
+    """The bench step with the queue taken round-robin over the workspace
+    slots, step by step, instead of longest remaining path first."""
+    from paper_2106_15740_gb300.energy import EnergyPlan
+    plan = EnergyPlan(n, edges, p, batch=B, dtype=WORKLOAD["dtype"], mode="persistent", device=dev,
+                      order_trials=WORKLOAD.get("order_trials", 0), lane_items=WORKLOAD.get("lane_items", 0),
+                      group_rows=WORKLOAD.get("group_rows", 0), queue_order="round_robin")
+    ms = _time_calls(plan, g, b, False, 5, torch)
+    out = {"value": len(edges) * B / (ms * 1e-3), "unit": "edge_evals/s", "ms_per_step": ms,
+           "achieved_gbs": plan.stats["alg_bytes"] / (ms * 1e-3) / 1e9,
+           "what": "same plan and tile, queue round-robin over slots step by step (direct calls)"}
+    plan.close()
+    return out
+
+
 def gradient_and_comparator(dev, torch):
     """Energy-gradient throughput on the 60-vertex p = 4 workload (8 angles,
     one angle set, complex64 adjoint sweep), and the plain per-edge complex128
@@ -365,7 +386,7 @@ def run_ours(args):
     profile_only = ((WORKLOAD["name"], B) != ("n100_p4", 64) or "edge_range" in WORKLOAD or "lane_items" in WORKLOAD
                     or "chunk_tiles" in WORKLOAD or "gradient" in WORKLOAD or "max_width" in WORKLOAD
                     or "profile_order" in WORKLOAD
-                    or "load_path" in WORKLOAD or "chain_steps" in WORKLOAD)
+                    or "load_path" in WORKLOAD or "chain_steps" in WORKLOAD or "queue_order" in WORKLOAD)
     grad = bool(WORKLOAD.get("gradient", False))
     gamma, beta = random_angles(B, p, 1002 + 7919 * rank)
     tuned = None
@@ -385,7 +406,8 @@ def run_ours(args):
                       gradient=grad, max_width=WORKLOAD.get("max_width", 0), slice=WORKLOAD.get("slice", False),
                       max_workspace=WORKLOAD.get("max_workspace", 0), order_trials=WORKLOAD.get("order_trials", 0),
                       load_path=WORKLOAD.get("load_path", "registers"),
-                      chain_steps=WORKLOAD.get("chain_steps", False))
+                      chain_steps=WORKLOAD.get("chain_steps", False),
+                      queue_order=WORKLOAD.get("queue_order", "critical_path"))
     t_plan = time.perf_counter() - t_plan
     g = torch.tensor(gamma, device=dev)
     b = torch.tensor(beta, device=dev)
@@ -499,6 +521,7 @@ def run_ours(args):
         if not profile_only:
             res["staged_loads"] = load_path_comparison(n, edges, p, B, g, b, dev, torch)
             res["chained_steps"] = chain_comparison(n, edges, p, B, g, b, dev, torch)
+            res["round_robin_queue"] = round_robin_comparison(n, edges, p, B, g, b, dev, torch)
         if not args.no_cpu_baseline:
             res.update(gradient_and_comparator(dev, torch))
             res["single_amplitude"] = amplitude_measure(dev, torch)
@@ -533,6 +556,8 @@ def main():
                     help="profiling only: operand path of the persistent kernel")
     ap.add_argument("--chain-steps", action="store_true",
                     help="profiling only: chain every step of a workspace slot to the one before it")
+    ap.add_argument("--queue-order", default=None, choices=["round_robin", "critical_path"],
+                    help="profiling only: order of the persistent queue")
     ap.add_argument("--order-trials", type=int, default=None,
                     help="profiling only: randomised greedy orders per edge (0: min-fill)")
     args = ap.parse_args()
@@ -560,6 +585,9 @@ def main():
         args.no_cpu_baseline = True
     if args.chain_steps:
         WORKLOAD["chain_steps"] = True
+        args.no_cpu_baseline = True
+    if args.queue_order is not None:
+        WORKLOAD["queue_order"] = args.queue_order
         args.no_cpu_baseline = True
     if args.max_workspace_gb:
         WORKLOAD["max_workspace"] = int(args.max_workspace_gb * (1 << 30))

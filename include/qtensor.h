@@ -184,6 +184,11 @@ typedef struct {
                              step waits for the step planned before it on its slot (one chain
                              per slot).  Energies are bit-identical either way; gradients agree
                              up to the order of the atomic additions some adjoint steps make */
+  int32_t queue_order;    /* persistent mode: 1 (default) the queue takes first the tasks with
+                             the longest remaining dependency path (estimated time through their
+                             dependents to the end of their slot), which starts long paths
+                             early; 0 it takes the slots round-robin, step by step.  Results are
+                             bit-identical either way */
 } qt_plan_options;
 
 /* Fill `opt` with defaults: batch 1, QT_C128, QT_MODE_PER_BUCKET, no gradient,

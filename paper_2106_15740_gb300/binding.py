@@ -53,7 +53,7 @@ class qt_plan_options(C.Structure):
                 ("edge_end", C.c_int32), ("slice", C.c_int32),
                 ("chunk_tiles", C.c_int32), ("order_trials", C.c_int32), ("order_seed", C.c_int32),
                 ("order_tau", C.c_double), ("load_path", C.c_int32), ("checkpoint_bytes", C.c_int64),
-                ("chain_steps", C.c_int32)]
+                ("chain_steps", C.c_int32), ("queue_order", C.c_int32)]
 
 
 _lib = None

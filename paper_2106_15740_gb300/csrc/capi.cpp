@@ -259,6 +259,7 @@ void qt_plan_options_default(qt_plan_options* opt) {
   opt->load_path = 0;
   opt->checkpoint_bytes = 0;
   opt->chain_steps = 0;
+  opt->queue_order = 1;
 }
 
 static qt_status check_options(const qt_plan_options* opt, qt_plan_options* out) {
@@ -277,6 +278,7 @@ static qt_status check_options(const qt_plan_options* opt, qt_plan_options* out)
   if (o.load_path != 0 && o.load_path != 1) return fail(QT_EINVAL, "load_path must be 0 or 1");
   if (o.checkpoint_bytes < 0) return fail(QT_EINVAL, "checkpoint_bytes must be >= 0");
   if (o.chain_steps != 0 && o.chain_steps != 1) return fail(QT_EINVAL, "chain_steps must be 0 or 1");
+  if (o.queue_order != 0 && o.queue_order != 1) return fail(QT_EINVAL, "queue_order must be 0 or 1");
   *out = o;
   return QT_OK;
 }

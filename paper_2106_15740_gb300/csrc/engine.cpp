@@ -769,6 +769,48 @@ qt_status compile_plan(Plan* P) {
         }
       }
     }
+    if (P->opt.queue_order == 1) {
+      // List scheduling: the units (a step's chunks, or a group) whose
+      // remaining dependency path -- estimated time through their dependents
+      // to the end of the slot -- is longest go first.  A dependency's path
+      // is longer than each of its dependents', so it stays earlier in the
+      // queue.  Estimated time of a task: 4 + 0.6 per warp pass over its
+      // rows (RP rows a pass; in microseconds, from queue traces), times the
+      // rounds its chunks need on about 4096 warps.
+      std::vector<int64_t> ustart;
+      for (int64_t t = 0; t < (int64_t)P->tasks.size(); ++t)
+        if (t == 0 || P->tasks[t].bucket != P->tasks[t - 1].bucket) ustart.push_back(t);
+      const int64_t nu = (int64_t)ustart.size();
+      ustart.push_back((int64_t)P->tasks.size());
+      std::vector<int32_t> unit_of(P->buckets.size(), -1);
+      std::vector<double> w(nu, 0.0), path(nu, 0.0), below(nu, 0.0);
+      for (int64_t u = 0; u < nu; ++u) {
+        const DevTask& t = P->tasks[ustart[u]];
+        const int32_t k = t.chunk < 0 ? -t.chunk : 1;
+        for (int32_t j = 0; j < k; ++j) {
+          const DevBucket& d = P->buckets[t.bucket + j];
+          unit_of[t.bucket + j] = (int32_t)u;
+          const int64_t rows = std::min<int64_t>(d.n_rows, (int64_t)d.span * geom.R);
+          const double passes = (double)((rows + geom.RP - 1) / geom.RP);
+          w[u] += (4.0 + 0.6 * passes) * (double)((d.ntask + 4095) / 4096);
+        }
+      }
+      for (int64_t u = nu - 1; u >= 0; --u) {
+        path[u] = w[u] + below[u];
+        const DevBucket& d = P->buckets[P->tasks[ustart[u]].bucket];
+        for (int32_t q = 0; q < d.n_dep; ++q) {
+          const int32_t v = unit_of[P->deps[d.dep + q]];
+          below[v] = std::max(below[v], path[u]);
+        }
+      }
+      std::vector<int64_t> order(nu);
+      for (int64_t u = 0; u < nu; ++u) order[u] = u;
+      std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return path[a] > path[b]; });
+      std::vector<DevTask> sorted;
+      sorted.reserve(P->tasks.size());
+      for (int64_t u : order) sorted.insert(sorted.end(), P->tasks.begin() + ustart[u], P->tasks.begin() + ustart[u + 1]);
+      P->tasks.swap(sorted);
+    }
   }
 
   // The bulk-copy ring reads each operand row pair with one 16-byte-aligned

@@ -14,6 +14,7 @@ from . import binding as qb
 
 DTYPES = {"c128": qb.QT_C128, "c64": qb.QT_C64}
 MODES = {"per_bucket": qb.QT_MODE_PER_BUCKET, "persistent": qb.QT_MODE_PERSISTENT}
+QUEUE_ORDERS = {"round_robin": 0, "critical_path": 1}
 LOAD_PATHS = {"registers": 0, "staged": 1}
 
 
@@ -32,7 +33,8 @@ class EnergyPlan:
     def __init__(self, n_vertices, edges, p, batch=1, dtype="c128", mode="persistent",
                  max_workspace=0, max_width=0, device="cuda:0", gradient=False, lane_items=0,
                  group_rows=0, edge_range=None, slice=False, chunk_tiles=0, order_trials=0, order_seed=0,
-                 order_tau=1.0, load_path="registers", checkpoint_bytes=0, chain_steps=False):
+                 order_tau=1.0, load_path="registers", checkpoint_bytes=0, chain_steps=False,
+                 queue_order="critical_path"):
         self.n_vertices, self.p, self.batch = int(n_vertices), int(p), int(batch)
         self.edges = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
         self.device = torch.device(device)
@@ -42,7 +44,8 @@ class EnergyPlan:
                             group_rows=group_rows, edge_range=self.edge_range, slice=slice,
                             chunk_tiles=chunk_tiles, order_trials=order_trials, order_seed=order_seed,
                             order_tau=order_tau, load_path=load_path,
-                            checkpoint_bytes=checkpoint_bytes, chain_steps=chain_steps)
+                            checkpoint_bytes=checkpoint_bytes, chain_steps=chain_steps,
+                            queue_order=queue_order)
         opt = qb.qt_plan_options_default()
         opt.batch = self.batch
         opt.dtype = DTYPES[dtype]
@@ -61,6 +64,7 @@ class EnergyPlan:
         opt.load_path = LOAD_PATHS[load_path]
         opt.checkpoint_bytes = int(checkpoint_bytes)
         opt.chain_steps = int(bool(chain_steps))
+        opt.queue_order = QUEUE_ORDERS[queue_order]
         self.plan = qb.qt_plan_create(self.n_vertices, self.edges, self.p, opt)
         self.ws_bytes = qb.qt_plan_workspace_size(self.plan)
         self.stats = qb.qt_plan_stats(self.plan)

@@ -18,7 +18,7 @@ import pytest
 from workloads import random_regular_graph
 
 
-def _plan(n, edges, p, B=4, chain=0, group_rows=0, max_workspace=0, order_trials=0, dtype=None):
+def _plan(n, edges, p, B=4, chain=0, group_rows=0, max_workspace=0, order_trials=0, dtype=None, queue_order=1):
     from paper_2106_15740_gb300 import binding as qb
     opt = qb.qt_plan_options_default()
     opt.batch = B
@@ -28,6 +28,7 @@ def _plan(n, edges, p, B=4, chain=0, group_rows=0, max_workspace=0, order_trials
     opt.group_rows = group_rows
     opt.max_workspace = max_workspace
     opt.order_trials = order_trials
+    opt.queue_order = queue_order
     return qb.qt_plan_create(n, edges, p, opt)
 
 
@@ -109,11 +110,12 @@ def check_schedule(sch, tasks):
     return len(order), max(depth) + 1, pairs, cross
 
 
+@pytest.mark.parametrize("queue_order", [0, 1])
 @pytest.mark.parametrize("group_rows", [0, -1, 1 << 20])
-def test_tree_schedule_is_race_free(qtlib, group_rows):
+def test_tree_schedule_is_race_free(qtlib, group_rows, queue_order):
     n = 16
     edges = random_regular_graph(n, 3, 31)
-    plan = _plan(n, edges, 2, group_rows=group_rows)
+    plan = _plan(n, edges, 2, group_rows=group_rows, queue_order=queue_order)
     from paper_2106_15740_gb300 import binding as qb
     try:
         units, depth, pairs, cross = check_schedule(*_schedule(plan))
@@ -124,7 +126,8 @@ def test_tree_schedule_is_race_free(qtlib, group_rows):
         assert pairs > 0 and depth < units
 
 
-def test_tree_schedule_with_shared_slots_is_race_free(qtlib):
+@pytest.mark.parametrize("queue_order", [0, 1])
+def test_tree_schedule_with_shared_slots_is_race_free(qtlib, queue_order):
     """A workspace cap puts several networks on one slot: a network's first
     steps then reuse the arena of the network before it."""
     from paper_2106_15740_gb300 import binding as qb
@@ -133,7 +136,7 @@ def test_tree_schedule_with_shared_slots_is_race_free(qtlib):
     full = _plan(n, edges, 3)
     data = _data_bytes(full)
     qb.qt_plan_free(full)
-    plan = _plan(n, edges, 3, max_workspace=data // 3)
+    plan = _plan(n, edges, 3, max_workspace=data // 3, queue_order=queue_order)
     try:
         units, depth, pairs, cross = check_schedule(*_schedule(plan))
     finally:
@@ -142,11 +145,12 @@ def test_tree_schedule_with_shared_slots_is_race_free(qtlib):
     assert pairs > 0 and depth < units
 
 
-def test_chain_schedule_is_one_path_per_slot(qtlib):
+@pytest.mark.parametrize("queue_order", [0, 1])
+def test_chain_schedule_is_one_path_per_slot(qtlib, queue_order):
     from paper_2106_15740_gb300 import binding as qb
     n = 12
     edges = random_regular_graph(n, 3, 33)
-    plan = _plan(n, edges, 2, chain=1, group_rows=-1)
+    plan = _plan(n, edges, 2, chain=1, group_rows=-1, queue_order=queue_order)
     try:
         sch, tasks = _schedule(plan)
         units, depth, _, _ = check_schedule(sch, tasks)
@@ -171,8 +175,9 @@ def test_tree_schedule_of_searched_orders_is_race_free(qtlib):
     assert pairs > 0 and depth < units
 
 
+@pytest.mark.parametrize("queue_order", [0, 1])
 @pytest.mark.parametrize("checkpoint", [False, True])
-def test_gradient_schedule_is_race_free(qtlib, checkpoint):
+def test_gradient_schedule_is_race_free(qtlib, checkpoint, queue_order):
     """The adjoint sweep reads the forward intermediates again, writes output
     adjoints (zeroed first where it accumulates them) and reuses the arena;
     with checkpointing it also re-runs forward steps.  Several networks share
@@ -189,6 +194,7 @@ def test_gradient_schedule_is_race_free(qtlib, checkpoint):
         opt.gradient = 1
         opt.max_workspace = cap
         opt.checkpoint_bytes = ckpt
+        opt.queue_order = queue_order
         return qb.qt_plan_create(n, edges, 2, opt)
 
     full = grad_plan(0, 0)
