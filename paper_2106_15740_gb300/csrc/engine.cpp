@@ -666,7 +666,7 @@ qt_status compile_plan(Plan* P) {
     for (int32_t o = 0; o <= P->n_orig; ++o) P->leaf_first[o] = net_leaf[P->net_first[o]];
   }
 
-  // ---- persistent queue: each edge's steps form a chain; slots round-robin ----
+  // ---- persistent queue: chunks and groups, dependency lists, queue order ----
   P->tasks.clear();
   const TileGeom geom = tile_geom(P->opt.dtype, B, P->opt.lane_items);
   P->tile_items = geom.R;

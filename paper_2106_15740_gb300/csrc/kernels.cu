@@ -183,8 +183,9 @@ __device__ __forceinline__ int32_t ld_acquire(const int32_t* p) {
 // or `span` consecutive tiles for the widest buckets of a very long queue) or
 // one group of single-tile buckets.  Each warp takes tasks in queue order (lane 0: atomicAdd on the
 // queue head, issued one task ahead so its latency overlaps a tile), waits
-// until the task's bucket's predecessor in its edge chain has all its tiles
-// done, evaluates the tile(s) and counts the bucket's tile done.  Every
+// until every step on its step's dependency list has all its tiles done
+// (lane q polls the entries q, q + 32, ...), evaluates the tile(s) and counts
+// the bucket's tile done.  Every
 // awaited tile comes earlier in the queue and is held by a running warp that
 // only waits on still earlier tiles, so every wait ends.  Waits are bounded:
 // after `spin_limit` polls (or as soon as another warp has failed) the warp

@@ -48,7 +48,7 @@ struct TileGeom {
   int64_t data_elems;  // size of the data region, for the QT_DEVICE_CHECKS build
 };
 
-// Step kinds of an edge chain.
+// Step kinds of a network's steps.
 //   kStepFwd : bucket product-sum, out[y] = sum_x prod_i in_i[(pext(y) << 1) | x]
 //   kStepAdj : adjoint of one input t of a bucket (reverse sweep): for every
 //              output row y of the bucket, c_x = Gbar[y] * prod_{i != t} in_i
@@ -103,7 +103,7 @@ struct DevLeafFactor {
 
 // Persistent-queue task.  chunk >= 0: chunk `chunk` of step `bucket`, its
 // warp tiles [chunk * span, (chunk + 1) * span).  chunk < 0: a group of
-// -chunk consecutive steps of one edge chain, starting at `bucket`, each small
+// -chunk consecutive steps of one network, starting at `bucket`, each small
 // enough for a single tile; one warp runs them in order with no global
 // synchronisation between them.
 struct DevTask {
