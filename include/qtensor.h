@@ -142,7 +142,8 @@ typedef struct {
                              step descriptors and the task queue (bytes per queued task, not
                              set by concurrency) come on top */
   int32_t group_rows;     /* persistent mode: consecutive buckets of one edge with at most this many
-                             rows run back to back in one task (0: by batch, <0: never) */
+                             rows run back to back in one task (<0: never; 0: by batch -- never
+                             for B = 1, else up to 4 warp passes of rows) */
   int32_t edge_begin;     /* plan the edges [edge_begin, edge_end) of the graph; */
   int32_t edge_end;       /* edge_end <= 0 means all edges from edge_begin on.  Energies and
                              gradients then cover only those edges (a partial sum) */

@@ -670,7 +670,11 @@ qt_status compile_plan(Plan* P) {
   P->tasks.clear();
   const TileGeom geom = tile_geom(P->opt.dtype, B, P->opt.lane_items);
   P->tile_items = geom.R;
-  int64_t group_rows = P->opt.group_rows == 0 ? 4 * (int64_t)geom.RP : (int64_t)P->opt.group_rows;
+  // By batch: one angle set never groups (its tiny steps are independent more
+  // often than not and run side by side instead); larger batches group steps
+  // of up to 4 passes, which saves the per-task overhead of their many tiny
+  // adjoint-sweep steps.
+  int64_t group_rows = P->opt.group_rows != 0 ? (int64_t)P->opt.group_rows : (B == 1 ? -1 : 4 * (int64_t)geom.RP);
   if (group_rows > geom.R) group_rows = geom.R;
   if (persistent) {
     // A step is split into chunks of `span` warp tiles, one queue task each:
