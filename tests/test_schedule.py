@@ -243,3 +243,33 @@ def test_checker_finds_a_dropped_dependency(qtlib):
     bad["dep_count"][s] = 0
     with pytest.raises(AssertionError, match="unordered"):
         check_schedule(bad, tasks)
+
+
+def test_default_grouping_by_batch(qtlib):
+    """group_rows = 0: one angle set runs every step as its own task (its
+    tiny steps run side by side); larger batches group tiny consecutive
+    forward steps."""
+    from paper_2106_15740_gb300 import binding as qb
+    n = 16
+    edges = random_regular_graph(n, 3, 38)
+    for B, grouped in ((1, False), (4, True), (64, True)):
+        plan = _plan(n, edges, 3, B=B)
+        try:
+            tasks = qb.qt_plan_tasks(plan)
+        finally:
+            qb.qt_plan_free(plan)
+        assert bool((tasks["chunk"] < 0).any()) == grouped, B
+
+
+@pytest.mark.parametrize("field,value", [("chain_steps", 2), ("chain_steps", -1), ("queue_order", 2),
+                                         ("queue_order", -1)])
+def test_schedule_options_are_validated(qtlib, field, value):
+    from paper_2106_15740_gb300 import binding as qb
+    opt = qb.qt_plan_options_default()
+    assert opt.chain_steps == 0 and opt.queue_order == 1
+    opt.batch = 2
+    opt.mode = qb.QT_MODE_PERSISTENT
+    setattr(opt, field, value)
+    with pytest.raises(qb.QTError) as ei:
+        qb.qt_plan_create(8, random_regular_graph(8, 3, 39), 1, opt)
+    assert ei.value.status == qb.QT_EINVAL
