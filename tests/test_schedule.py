@@ -273,3 +273,43 @@ def test_schedule_options_are_validated(qtlib, field, value):
     with pytest.raises(qb.QTError) as ei:
         qb.qt_plan_create(8, random_regular_graph(8, 3, 39), 1, opt)
     assert ei.value.status == qb.QT_EINVAL
+
+
+def test_sliced_gradient_schedule_is_race_free(qtlib):
+    """Sliced networks (2^s restricted copies per edge, some falling apart
+    into components whose scalar adjoints read the other scalars) under the
+    dependency lists."""
+    from paper_2106_15740_gb300 import binding as qb
+    n = 12
+    edges = random_regular_graph(n, 3, 40)
+    opt = qb.qt_plan_options_default()
+    opt.batch = 2
+    opt.dtype = qb.QT_C64
+    opt.mode = qb.QT_MODE_PERSISTENT
+    opt.gradient = 1
+    opt.max_width = 5
+    opt.slice = 1
+    plan = qb.qt_plan_create(n, edges, 2, opt)
+    try:
+        assert qb.qt_plan_edge_slices(plan, len(edges)).max() > 0
+        units, depth, pairs, _ = check_schedule(*_schedule(plan))
+    finally:
+        qb.qt_plan_free(plan)
+    assert pairs > 0 and depth < units
+
+
+def test_amplitude_schedule_is_race_free(qtlib):
+    from paper_2106_15740_gb300 import binding as qb
+    n = 14
+    edges = random_regular_graph(n, 3, 41)
+    bits = np.random.default_rng(5).integers(0, 2, size=(6, n))
+    opt = qb.qt_plan_options_default()
+    opt.batch = 1
+    opt.dtype = qb.QT_C128
+    opt.mode = qb.QT_MODE_PERSISTENT
+    plan = qb.qt_amplitude_plan_create(n, edges, 2, bits, opt)
+    try:
+        units, depth, pairs, _ = check_schedule(*_schedule(plan))
+    finally:
+        qb.qt_plan_free(plan)
+    assert pairs > 0 and depth < units
