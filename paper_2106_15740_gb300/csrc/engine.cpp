@@ -804,7 +804,7 @@ qt_status compile_plan(Plan* P) {
         const DevBucket& d = P->buckets[P->tasks[ustart[u]].bucket];
         for (int32_t q = 0; q < d.n_dep; ++q) {
           const int32_t v = unit_of[P->deps[d.dep + q]];
-          below[v] = std::max(below[v], path[u]);
+          if (v >= 0) below[v] = std::max(below[v], path[u]);  // every queued step has a unit
         }
       }
       std::vector<int64_t> order(nu);
