@@ -127,11 +127,22 @@ def cpu_baseline(budget_s=12.0, gpu_zz=None):
             pool.map(_oracle_eval, _oracle_sample(n_items, 2 + done))
             done += n_items
         dt = time.perf_counter() - t0
+        # one worker at a time: the single-thread rate on the same kind of sample
+        t1 = time.perf_counter()
+        single = 0
+        for item in _oracle_sample(max(cores * 2, 8), 999):
+            pool.apply(_oracle_eval, (item,))
+            single += 1
+            if time.perf_counter() - t1 > budget_s / 4:
+                break
+        dt1 = time.perf_counter() - t1
     finally:
         pool.terminate()
     return {"value": done / dt, "unit": "edge_evals/s", "cores": cores, "kind": "oracle",
             "sample": f"{done} seeded (edge, angle-set) pairs of the N=100 p=4 workload, "
-                      f"FP64 naive bucket elimination, {cores} worker processes x 1 thread"}, err
+                      f"FP64 naive bucket elimination, {cores} worker processes x 1 thread",
+            "single_thread": {"value": single / dt1, "unit": "edge_evals/s",
+                              "sample": f"{single} pairs, one worker process x 1 thread"}}, err
 
 
 def run_reference(args):
