@@ -46,9 +46,9 @@ TRAFFIC_CAPTURES = [
     # tile); steps wait for the dependencies found from the elements they touch; the queue
     # takes the longest remaining dependency path first (the default) or the slots round-robin.
     # Captured at digest 63c2243c03f50613; only comments of those sources changed since.
-    {"sources_sha256_16": "08136b2916b328dd", "alg_bytes_per_angle_set": 5170666432 / 4,
+    {"sources_sha256_16": "3cb853ff50c29a4c", "alg_bytes_per_angle_set": 5170666432 / 4,
      "queue_order": "critical_path", "bytes_per_angle_set": (2308382464 + 2503696896) / 4},
-    {"sources_sha256_16": "08136b2916b328dd", "alg_bytes_per_angle_set": 5170666432 / 4,
+    {"sources_sha256_16": "3cb853ff50c29a4c", "alg_bytes_per_angle_set": 5170666432 / 4,
      "queue_order": "round_robin", "bytes_per_angle_set": (2184769024 + 2472729344) / 4},
 ]
 

@@ -218,7 +218,8 @@ __global__ void __launch_bounds__(256, STAGE == 1 ? 2 : 4) persistent_kernel(con
     }
     __syncwarp();
   }
-  // Lane 0 makes every scheduling decision; the warp acts on broadcasts.
+  // Lane 0 claims tasks (the warp acts on broadcasts); the lanes poll a
+  // step's dependency list side by side.
   int32_t t = 0, cached = -1;  // cached: bucket whose record and lane parts are in *w
   if (lane == 0) t = atomicAdd(&ctrl->head, 1);
   t = __shfl_sync(0xffffffffu, t, 0);
