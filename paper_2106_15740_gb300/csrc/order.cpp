@@ -1,6 +1,6 @@
 // Greedy min-fill elimination order (§Tensor network contraction: the order
 // in which variables are summed out sets the size of the largest intermediate
-// and so the cost, §Results "contraction width").
+// and so the cost; §Results calls its rank the contraction width).
 //
 // Interaction graph: one vertex per variable, a clique on the variables of
 // every tensor.  Step: pick the alive variable with the smallest
