@@ -313,3 +313,45 @@ def test_amplitude_schedule_is_race_free(qtlib):
     finally:
         qb.qt_plan_free(plan)
     assert pairs > 0 and depth < units
+
+
+def test_schedule_sweep_of_random_configurations(qtlib):
+    """A seeded sweep over small plans: graph size and seed, depth, batch,
+    dtype, energy or gradient, checkpoint budget, workspace cap, queue order,
+    chained or dependency-list schedule and grouping.  Every schedule must
+    pass the check."""
+    from paper_2106_15740_gb300 import binding as qb
+    rng = np.random.default_rng(2106)
+    checked = 0
+    for trial in range(64):
+        n = int(rng.choice([6, 8, 10, 12]))
+        p = int(rng.integers(1, 3 if n > 8 else 4))
+        edges = random_regular_graph(n, 3, int(rng.integers(0, 1000)))
+        opt = qb.qt_plan_options_default()
+        opt.batch = int(rng.choice([1, 2, 3, 8, 64]))
+        opt.dtype = int(rng.choice([qb.QT_C64, qb.QT_C128]))
+        opt.mode = qb.QT_MODE_PERSISTENT
+        opt.gradient = int(rng.integers(0, 2))
+        opt.queue_order = int(rng.integers(0, 2))
+        opt.chain_steps = int(rng.random() < 0.2)
+        opt.group_rows = int(rng.choice([0, -1, 64]))
+        if opt.gradient and rng.integers(0, 2):
+            opt.checkpoint_bytes = int(rng.choice([1 << 10, 1 << 14]))
+        plan = qb.qt_plan_create(n, edges, p, opt)
+        data = _data_bytes(plan, 8 if opt.dtype == qb.QT_C64 else 16)
+        qb.qt_plan_free(plan)
+        if rng.integers(0, 2):  # several networks per workspace slot, if the cap allows
+            opt.max_workspace = data * 3 // 4
+            try:
+                plan = qb.qt_plan_create(n, edges, p, opt)
+            except qb.QTError:
+                opt.max_workspace = 0
+                plan = qb.qt_plan_create(n, edges, p, opt)
+        else:
+            plan = qb.qt_plan_create(n, edges, p, opt)
+        try:
+            check_schedule(*_schedule(plan))
+            checked += 1
+        finally:
+            qb.qt_plan_free(plan)
+    assert checked == 64
