@@ -13,10 +13,11 @@
 // QT_MODE_PER_BUCKET launches one kernel per bucket, edge after edge, all
 // edges sharing one arena.  QT_MODE_PERSISTENT issues one persistent launch
 // over a queue of bucket tiles; edges are spread over "slots" (one arena
-// each).  A queued step waits for the steps it reads and for the readers of
-// the arena space it overwrites (gradient plans: for the step before it on
-// its slot), and the queue interleaves the slots round-robin so independent
-// work fills the GPU while a step waits.
+// each).  A queued step waits for the last writer of what it reads and for
+// the last writer and readers of what it writes (access_deps; forward and
+// adjoint steps alike), and the queue takes first the tasks with the longest
+// remaining dependency path (or the slots round-robin), so independent work
+// fills the GPU while a step waits.
 #include "engine.h"
 
 #include <algorithm>
