@@ -223,7 +223,7 @@ def qaoa_energy(plan, gamma, beta):
 
 
 def autotune(n_vertices, edges, p, batch=1, dtype="c64", gradient=False, device="cuda:0", reps=3,
-             lane_items=None, group_rows=(0, 1 << 20), max_workspace=0, edge_range=None, gamma=None, beta=None,
+             lane_items=None, group_rows=(0, -1, 32), max_workspace=0, edge_range=None, gamma=None, beta=None,
              **plan_options):
     """Pick the warp-tile size and bucket grouping of a persistent plan by
     timing each candidate on the device (CUDA events around `reps` calls after
