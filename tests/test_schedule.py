@@ -355,3 +355,14 @@ def test_schedule_sweep_of_random_configurations(qtlib):
         finally:
             qb.qt_plan_free(plan)
     assert checked == 64
+
+
+def test_schedule_stats_module(qtlib):
+    from paper_2106_15740_gb300.schedule import compare
+    n = 16
+    edges = random_regular_graph(n, 3, 42)
+    res = compare(n, edges, 3, batch=4, group_rows=-1)
+    tree, chain = res["dependency lists"], res["chained"]
+    assert tree["units"] == chain["units"] > 0
+    assert chain["max_deps"] == 1 and tree["max_deps"] >= 1
+    assert tree["longest_path"] < chain["longest_path"]
