@@ -7,7 +7,9 @@ a group of tiny steps that one warp runs in order), the dependencies per
 unit, and the longest dependency path in units, which bounds how many steps
 one after another the launch must wait through.  With ``chain_steps`` every
 step of a workspace slot waits for the one before it, so the path is the
-length of a slot's step list.
+length of a slot's step list.  ``trace_stats`` summarises a queue trace taken
+on the device (``EnergyPlan.trace``): time working, waiting and idle, and the
+start-up phase before all warps are busy.
 
     python -m paper_2106_15740_gb300.schedule      # the bench and gradient workloads
 """
@@ -40,6 +42,48 @@ def schedule_stats(plan) -> dict:
             "deps_per_unit": float(len(sch["deps"])) / max(n_units, 1),
             "max_deps": int(sch["dep_count"].max()) if n_units else 0,
             "longest_path": max(depth.values()) if depth else 0}
+
+
+def trace_stats(trace, n_warps, bin_ns=200_000, busy_frac=0.9) -> dict:
+    """Summary of a queue trace (``EnergyPlan.trace``: per task the claim,
+    ready and done clock readings in ns).  A warp is *waiting* from claim to
+    ready (its task's dependencies) and *working* from ready to done.
+
+    Returns the span, the fractions of n_warps x span spent working, waiting
+    and idle, the per-bin averages of working and waiting warps, and
+    ``full_after_ns``: the end of the first bin in which at least busy_frac of
+    the warps work (the start-up phase before it), and ``tail_ns``: the time
+    from the last such bin's end to the end of the span."""
+    tr = np.asarray(trace, dtype=np.uint64)
+    claim, ready, done = (tr[:, i].astype(np.int64) for i in range(3))
+    t0 = claim.min()
+    claim, ready, done = claim - t0, ready - t0, done - t0
+    span = int(done.max())
+    nb = span // bin_ns + 1
+
+    def occupancy(a, b):
+        acc = np.zeros(nb + 1)
+        ba, bb = a // bin_ns, b // bin_ns
+        same = ba == bb
+        np.add.at(acc, ba[same], (b - a)[same])
+        d = ~same
+        np.add.at(acc, ba[d], (ba[d] + 1) * bin_ns - a[d])
+        np.add.at(acc, bb[d], b[d] - bb[d] * bin_ns)
+        for k in np.nonzero(d & (bb - ba > 1))[0]:  # bins fully covered
+            acc[ba[k] + 1:bb[k]] += bin_ns
+        return acc[:nb] / bin_ns
+
+    work = occupancy(ready, done)
+    wait = occupancy(claim, ready)
+    full = np.nonzero(work >= busy_frac * n_warps)[0]
+    total = float(n_warps) * span
+    return {"span_ns": span,
+            "work_frac": float((done - ready).sum()) / total,
+            "wait_frac": float((ready - claim).sum()) / total,
+            "idle_frac": 1.0 - float((done - claim).sum()) / total,
+            "working_warps": work, "waiting_warps": wait, "bin_ns": bin_ns,
+            "full_after_ns": int((full[0] + 1) * bin_ns) if len(full) else None,
+            "tail_ns": int(span - (full[-1] + 1) * bin_ns) if len(full) else None}
 
 
 def compare(n_vertices, edges, p, **options) -> dict:

@@ -366,3 +366,20 @@ def test_schedule_stats_module(qtlib):
     assert tree["units"] == chain["units"] > 0
     assert chain["max_deps"] == 1 and tree["max_deps"] >= 1
     assert tree["longest_path"] < chain["longest_path"]
+
+
+def test_trace_stats_on_a_synthetic_trace():
+    """Two warps, bins of 10 ns: warp 0 waits 0-10 and works 10-40; warp 1
+    works 0-20, then waits 20-25 and works 25-40."""
+    from paper_2106_15740_gb300.schedule import trace_stats
+    tr = np.array([[0, 10, 40, 0], [0, 0, 20, 1], [20, 25, 40, 1]], dtype=np.uint64) + np.array(
+        [100, 100, 100, 0], dtype=np.uint64)
+    st = trace_stats(tr, n_warps=2, bin_ns=10, busy_frac=1.0)
+    assert st["span_ns"] == 40
+    assert st["work_frac"] == pytest.approx((30 + 20 + 15) / 80)
+    assert st["wait_frac"] == pytest.approx((10 + 5) / 80)
+    assert st["idle_frac"] == pytest.approx(0.0)
+    # bins [0,10) .. [40,50): warp 0 works in bins 1-3; warp 1 in bins 0-1, half of 2, and 3
+    np.testing.assert_allclose(st["working_warps"], [1.0, 2.0, 1.5, 2.0, 0.0])
+    np.testing.assert_allclose(st["waiting_warps"], [1.0, 0.0, 0.5, 0.0, 0.0])
+    assert st["full_after_ns"] == 20 and st["tail_ns"] == 0
