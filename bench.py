@@ -421,6 +421,7 @@ def run_ours(args):
                       chain_steps=WORKLOAD.get("chain_steps", False),
                       queue_order=WORKLOAD.get("queue_order", "critical_path"))
     t_plan = time.perf_counter() - t_plan
+    from paper_2106_15740_gb300.schedule import bytes_by_rank
     g = torch.tensor(gamma, device=dev)
     b = torch.tensor(beta, device=dev)
     out = torch.empty(B, dtype=torch.float64, device=dev)
@@ -509,7 +510,8 @@ def run_ours(args):
                        "width_histogram": {int(w): int(c) for w, c in zip(*np.unique(plan.widths, return_counts=True))},
                        "workspace_gb": round(plan.ws_bytes / 1e9, 2),
                        "l2": "working set larger than L2 (intermediates streamed through HBM every step)",
-                       "plan_host_s": round(t_plan, 3)},
+                       "plan_host_s": round(t_plan, 3),
+                       "alg_bytes_by_result_rank": bytes_by_rank(plan.plan, B, 8 if WORKLOAD["dtype"] == "c64" else 16)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": _traffic(B, alg, profile_only),
                          "kernel": "persistent_kernel<float,2,false,false,%s>" % (

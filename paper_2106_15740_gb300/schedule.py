@@ -44,6 +44,31 @@ def schedule_stats(plan) -> dict:
             "longest_path": max(depth.values()) if depth else 0}
 
 
+def bytes_by_rank(plan, batch, elem_bytes, threshold=18) -> dict:
+    """Algorithmic bytes of a persistent plan split by the steps' result rank:
+    steps whose output has rank >= threshold stream their operands through
+    HBM; narrower ones work mostly out of L2.  A step's bytes are the
+    elements it reads and writes (its intermediate inputs and its output;
+    leaf factors are not counted) times elem_bytes, so that over all steps
+    they sum to the plan's algorithmic bytes (gradient plans add their
+    zeroing steps and scalar adjoints, which that count leaves out).  batch
+    is the plan's B (a
+    step's output holds 2^rank x B elements).  Returns {"rank>=t": bytes,
+    "rank<t": bytes}."""
+    sch = qb.qt_plan_schedule(plan)
+    af = sch["acc_first"]
+    n = len(sch["unit"])
+    step = np.repeat(np.arange(n), np.diff(af))
+    el = (sch["acc_hi"] - sch["acc_lo"]).astype(np.float64)
+    per_step = np.bincount(step, weights=el, minlength=n)
+    out_el = np.zeros(n)
+    w = sch["acc_write"].astype(bool)
+    np.maximum.at(out_el, step[w], el[w])
+    wide = out_el >= float(batch) * 2.0 ** threshold
+    return {f"rank>={threshold}": float(per_step[wide].sum() * elem_bytes),
+            f"rank<{threshold}": float(per_step[~wide].sum() * elem_bytes)}
+
+
 def trace_stats(trace, n_warps, bin_ns=200_000, busy_frac=0.9) -> dict:
     """Summary of a queue trace (``EnergyPlan.trace``: per task the claim,
     ready and done clock readings in ns).  A warp is *waiting* from claim to

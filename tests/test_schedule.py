@@ -383,3 +383,31 @@ def test_trace_stats_on_a_synthetic_trace():
     np.testing.assert_allclose(st["working_warps"], [1.0, 2.0, 1.5, 2.0, 0.0])
     np.testing.assert_allclose(st["waiting_warps"], [1.0, 0.0, 0.5, 0.0, 0.0])
     assert st["full_after_ns"] == 20 and st["tail_ns"] == 0
+
+
+@pytest.mark.parametrize("gradient", [0, 1])
+def test_bytes_by_rank_sums_to_the_plan_bytes(qtlib, gradient):
+    """The per-step element counts of the schedule, split at any rank, add
+    up to the plan's algorithmic bytes: exactly for forward plans; gradient
+    plans add their zeroing steps and scalar adjoints."""
+    from paper_2106_15740_gb300 import binding as qb
+    from paper_2106_15740_gb300.schedule import bytes_by_rank
+    n = 14
+    edges = random_regular_graph(n, 3, 43)
+    opt = qb.qt_plan_options_default()
+    opt.batch = 4
+    opt.dtype = qb.QT_C64
+    opt.mode = qb.QT_MODE_PERSISTENT
+    opt.gradient = gradient
+    plan = qb.qt_plan_create(n, edges, 3, opt)
+    try:
+        total = qb.qt_plan_stats(plan)["alg_bytes"]
+        sums = [sum(bytes_by_rank(plan, 4, 8, t).values()) for t in (2, 6, 10, 40)]
+        assert max(sums) == pytest.approx(min(sums), rel=1e-12)  # the split does not lose bytes
+        if gradient:  # plus the zeroing steps and scalar adjoints, not in the algorithmic count
+            assert total <= sums[0] <= 1.1 * total
+        else:
+            assert sums[0] == pytest.approx(total, rel=1e-12)
+        assert bytes_by_rank(plan, 4, 8, 40)["rank>=40"] == 0.0
+    finally:
+        qb.qt_plan_free(plan)
