@@ -222,6 +222,16 @@ qt_status qt_plan_edge_bytes(const qt_plan* plan, double* bytes);
  * restricted networks; 0 for an edge that fits the width budget). */
 qt_status qt_plan_edge_slices(const qt_plan* plan, int32_t* slices);
 
+/* Elimination order the plan contracts unit `unit` (0-based within the
+ * plan's edge range, or a bitstring of an amplitude plan) in (§Tensor network
+ * contraction: one bucket per variable, in this order).  Variable ids are the
+ * network's canonical ids (qt_build_lightcone); for a sliced unit they are
+ * the restricted network's ids (the fixed variables removed and the rest
+ * renumbered in order).  Call with order = NULL to get *n_vars; otherwise
+ * *n_vars holds the capacity of `order` on entry and the variable count on
+ * return.  QT_EINVAL for a unit out of range or a capacity too small. */
+qt_status qt_plan_edge_order(const qt_plan* plan, int32_t unit, int32_t* order, int32_t* n_vars);
+
 /* Evaluate the plan with DEVICE pointers, asynchronously on `stream`:
  *   gamma, beta : [B][p] float64 angles
  *   energy      : [B] float64, E = sum_e (1 - Re<Z_j Z_k>_e)/2
@@ -261,13 +271,17 @@ qt_status qt_plan_kernel_times(qt_plan* plan, float* ms, int32_t cap, int32_t* n
  * but the plan's scratch space lives in a device array of
  * qt_static_scratch_bytes() bytes built into the library (held on every device
  * that loads the library until exit) instead of a caller workspace.  gamma,
- * beta, energy ([B]) and edge_zz ([n_edges][B][2] or NULL) are device pointers;
- * the call is asynchronous on `stream`.  Allocates no device memory.  The
- * first call on a device looks up the array's address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture.
- * Every call re-uploads the plan's descriptors and clears its counters, since
- * all calls share the array; calls that overlap on the GPU race.  QT_ENOMEM
- * (with the sizes in the message) if the plan's workspace size is above
+ * beta, energy ([B]) and edge_zz ([n_edges][B][2] or NULL) are device pointers.
+ * Allocates no device memory.  The first call in a CUDA context of a device
+ * (its primary context, or a new one after a reset) looks up the array's
+ * address there (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  All calls share the array: the
+ * library remembers, per device and context, which plan's descriptors it
+ * holds.  A call whose plan is not that plan uploads its descriptors and
+ * waits for `stream` before it returns; a call with the same plan only clears
+ * the counters that must start at zero and is asynchronous on `stream`.
+ * Calls that overlap on the GPU race on the array.  QT_ENOMEM (with the sizes
+ * in the message) if the plan's workspace size is above
  * qt_static_scratch_bytes(). */
 qt_status qt_plan_energy_static(qt_plan* plan, const double* gamma, const double* beta,
                                 double* energy, double* edge_zz, void* stream);

@@ -32,7 +32,7 @@ EXPORTS = [
     "qt_plan_set_profiling", "qt_plan_kernel_times", "qt_plan_energy_static",
     "qt_static_scratch_bytes", "qt_plan_set_wait_limit", "qt_plan_inject_stall", "qt_plan_edge_slices",
     "qt_plan_edge_bytes", "qt_plan_trace_size", "qt_plan_set_trace", "qt_plan_tasks", "qt_plan_schedule",
-    "qt_amplitude_plan_create", "qt_plan_amplitudes", "qt_representation_cost",
+    "qt_amplitude_plan_create", "qt_plan_amplitudes", "qt_representation_cost", "qt_plan_edge_order",
 ]
 
 
@@ -80,6 +80,7 @@ def lib():
             "qt_plan_stats": [vp, pi32, pi32, C.POINTER(i64), pd, pd],
             "qt_plan_edge_widths": [vp, pi32],
             "qt_plan_edge_slices": [vp, pi32],
+            "qt_plan_edge_order": [vp, i32, pi32, pi32],
             "qt_plan_edge_bytes": [vp, C.POINTER(C.c_double)],
             "qt_plan_energy": [vp, vp, vp, vp, vp, vp, vp, sz, vp],
             "qt_plan_check": [vp, vp],
@@ -253,6 +254,14 @@ def qt_plan_edge_slices(plan, n_edges):
     sl = np.zeros(n_edges, dtype=np.int32)
     _check(lib().qt_plan_edge_slices(plan, sl.ctypes.data_as(C.POINTER(C.c_int32))))
     return sl
+
+
+def qt_plan_edge_order(plan, unit):
+    n = C.c_int32(0)
+    _check(lib().qt_plan_edge_order(plan, int(unit), None, C.byref(n)))
+    order = np.zeros(n.value, dtype=np.int32)
+    _check(lib().qt_plan_edge_order(plan, int(unit), order.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(n)))
+    return order
 
 
 def qt_plan_edge_bytes(plan, n_edges):

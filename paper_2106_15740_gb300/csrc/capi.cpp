@@ -424,6 +424,22 @@ qt_status qt_plan_edge_slices(const qt_plan* plan, int32_t* slices) {
   return QT_OK;
 }
 
+qt_status qt_plan_edge_order(const qt_plan* plan, int32_t unit, int32_t* order, int32_t* n_vars) {
+  if (!plan || !n_vars) return fail(QT_EINVAL, "plan or n_vars is NULL");
+  const Plan& P = plan->P;
+  if (unit < 0 || unit >= P.n_orig) return fail(QT_EINVAL, "unit " + std::to_string(unit) + " out of range");
+  const EdgePlan& ep = P.edges[P.net_first[unit]];
+  const int32_t n = (int32_t)ep.buckets.size();
+  if (order) {
+    if (*n_vars < n)
+      return fail(QT_EINVAL, "order holds " + std::to_string(*n_vars) + " entries, the network has " +
+                                 std::to_string(n) + " variables");
+    for (int32_t i = 0; i < n; ++i) order[i] = ep.buckets[i].var;
+  }
+  *n_vars = n;
+  return QT_OK;
+}
+
 qt_status qt_plan_energy(qt_plan* plan, const double* gamma, const double* beta, double* energy, double* edge_zz,
                          double* grad, void* workspace, size_t ws_bytes, void* stream) {
   if (!plan) return fail(QT_EINVAL, "plan is NULL");
