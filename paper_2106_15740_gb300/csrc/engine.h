@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <utility>
 #include <vector>
 
@@ -21,7 +22,14 @@ struct WsLayout {
   size_t angles = 0, results = 0, trig = 0, dz = 0, gpart = 0, data = 0, total = 0;
 };
 
+// Process-wide serial number of plans (never reused, unlike their addresses).
+inline uint64_t next_plan_uid() {
+  static std::atomic<uint64_t> counter{0};
+  return ++counter;
+}
+
 struct Plan {
+  uint64_t uid = next_plan_uid();
   Graph G;
   int32_t p = 0;
   qt_plan_options opt{};

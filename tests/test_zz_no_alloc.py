@@ -6,8 +6,10 @@ all device allocations): the plan's scratch space lives in a device array
 built into the library instead of a caller workspace.  This test compares
 it, through the C ABI, with the workspace entry point qt_plan_energy on two
 calls in a row (the second with other angles, so stale contents of the
-shared array would show), within the complex128 tolerance of the parity
-tests.  The file name makes pytest collect it last.
+shared array would show; the second call reuses the descriptors the first
+one uploaded), and on calls that alternate between two plans (each switch
+uploads the other plan's descriptors again), within the complex128
+tolerance of the parity tests.  The file name makes pytest collect it last.
 """
 import numpy as np
 import pytest
@@ -62,6 +64,39 @@ def test_static_scratch_matches_workspace_call_twice():
             np.testing.assert_allclose(zz_st.cpu().numpy(), zz_ref.cpu().numpy(), atol=TOL, rtol=0)
     finally:
         qb.qt_plan_free(plan)
+
+
+def _compare(qb, plan, n_edges, p, seed):
+    stream = torch.cuda.current_stream().cuda_stream
+    ws_bytes = qb.qt_plan_workspace_size(plan)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda:0")
+    g, b = random_angles(2, p, seed)
+    gd = torch.tensor(g, device="cuda:0")
+    bd = torch.tensor(b, device="cuda:0")
+    e_ref = torch.empty(2, dtype=torch.float64, device="cuda:0")
+    zz_ref = torch.empty((n_edges, 2, 2), dtype=torch.float64, device="cuda:0")
+    qb.qt_plan_energy(plan, gd.data_ptr(), bd.data_ptr(), e_ref.data_ptr(), zz_ref.data_ptr(), 0,
+                      ws.data_ptr(), ws_bytes, stream)
+    e_st = torch.full((2,), np.nan, dtype=torch.float64, device="cuda:0")
+    zz_st = torch.full((n_edges, 2, 2), np.nan, dtype=torch.float64, device="cuda:0")
+    qb.qt_plan_energy_static(plan, gd.data_ptr(), bd.data_ptr(), e_st.data_ptr(), zz_st.data_ptr(), stream)
+    qb.qt_plan_check(plan, stream)
+    np.testing.assert_allclose(e_st.cpu().numpy(), e_ref.cpu().numpy(), atol=TOL * n_edges, rtol=0)
+    np.testing.assert_allclose(zz_st.cpu().numpy(), zz_ref.cpu().numpy(), atol=TOL, rtol=0)
+
+
+def test_static_scratch_alternating_plans():
+    """Plans A, B, A, B: every switch must bring the other plan's
+    descriptors back into the shared array."""
+    from paper_2106_15740_gb300 import binding as qb
+    a, na, pa = _plan("n100_p3", 2, qb.QT_C128, qb.QT_MODE_PERSISTENT)
+    b, nb, pb = _plan("n16_p1", 2, qb.QT_C128, qb.QT_MODE_PERSISTENT)
+    try:
+        for k, (plan, n_edges, p) in enumerate([(a, na, pa), (b, nb, pb), (a, na, pa), (b, nb, pb)]):
+            _compare(qb, plan, n_edges, p, 40 + k)
+    finally:
+        qb.qt_plan_free(a)
+        qb.qt_plan_free(b)
 
 
 def test_static_scratch_rejects_plans_above_its_size():
