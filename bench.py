@@ -22,6 +22,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 from pathlib import Path
 
@@ -212,6 +213,10 @@ class ClockSampler:
             for nm, v in zip(names, f[5:9]):
                 if v.lower() == "active":
                     reasons.add(nm)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
         sm.sort()
         return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
                 "samples": len(sm)}
@@ -438,7 +443,8 @@ def run_ours(args):
     if pg:
         pg.barrier()
     torch.cuda.synchronize(dev)
-    clocks = ClockSampler(local, str(ROOT / "gpurun_out" / f"clocks_rank{rank}.csv")) if rank == 0 else None
+    clocks = ClockSampler(local, os.path.join(tempfile.gettempdir(), f"qt_bench_clocks_{os.getpid()}.csv")) \
+        if rank == 0 else None
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
@@ -610,7 +616,6 @@ def main():
         if val is not None:
             WORKLOAD["name" if key == "workload" else key] = val
             args.no_cpu_baseline = True
-    (ROOT / "gpurun_out").mkdir(exist_ok=True)
     if args.impl == "reference":
         run_reference(args)
     else:
