@@ -108,19 +108,31 @@ def _oracle_pool():
     return mp.get_context("spawn").Pool(cores), cores
 
 
-def cpu_baseline(budget_s=12.0, gpu_zz=None):
+ERROR_ANGLE_SETS = (0, 21, 42, 63)
+
+
+def cpu_baseline(budget_s=12.0, gpu_zz=None, gpu_e=None):
     """The oracle on host cores over a bounded sample of the workload.  With
-    the GPU's per-edge values gpu_zz[edge, angle set] (real parts) it also
-    returns the largest |GPU - oracle| over a seeded sample of pairs."""
+    the GPU's per-edge values gpu_zz[edge, angle set] (real parts) and
+    energies gpu_e[angle set] it also returns the errors against the oracle
+    on every edge of ERROR_ANGLE_SETS: the largest per-edge |d<ZZ>| and the
+    full-graph |dE| of each of those angle sets."""
     pool, cores = _oracle_pool()
     err = None
     try:
         pool.map(_oracle_eval, _oracle_sample(cores, 1))  # warm the workers
         if gpu_zz is not None:
-            chk = _oracle_sample(2 * cores, 7)
-            vals = pool.map(_oracle_eval, chk)
-            err = {"pairs": len(chk), "max_abs_dzz": max(abs(float(gpu_zz[e, k]) - v) for (_, e, k), v in zip(chk, vals)),
-                   "what": "complex64 bench path vs the FP64 oracle, seeded (edge, angle-set) sample"}
+            n_edges = gpu_zz.shape[0]
+            chk = [(WORKLOAD["name"], e, k) for k in ERROR_ANGLE_SETS for e in range(n_edges)]
+            vals = pool.map(_oracle_eval, chk, chunksize=8)
+            ref = {(e, k): v for (_, e, k), v in zip(chk, vals)}
+            d_e = {k: float(gpu_e[k]) - sum(0.5 * (1.0 - ref[(e, k)]) for e in range(n_edges)) for k in ERROR_ANGLE_SETS}
+            err = {"pairs": len(chk),
+                   "max_abs_dzz": max(abs(float(gpu_zz[e, k]) - v) for (e, k), v in ref.items()),
+                   "abs_dE": {str(k): abs(v) for k, v in d_e.items()},
+                   "max_abs_dE": max(abs(v) for v in d_e.values()),
+                   "what": "complex64 bench path (the timed plan) vs the FP64 oracle: every edge of angle sets "
+                           + ", ".join(map(str, ERROR_ANGLE_SETS)) + "; E over all 150 edges"}
         n_items = cores * 6
         t0 = time.perf_counter()
         done = 0
@@ -222,11 +234,17 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def _time_calls(plan, g, b, grad, reps, torch):
-    """Mean device time (ms) of `reps` plan evaluations after two warm-ups."""
+def _time_calls(plan, g, b, grad, reps, torch, kernel=False):
+    """Mean device time (ms) of `reps` plan evaluations after two warm-ups;
+    with kernel=True also the mean time of the persistent bucket launch
+    alone (the library's events around it, on the launching stream)."""
+    from paper_2106_15740_gb300 import binding as qb
     for _ in range(2):
         plan.energy(g, b, grad=grad)
     plan.check()
+    if kernel:
+        qb.qt_plan_set_profiling(plan.plan, True)
+        qb.qt_plan_kernel_times(plan.plan)
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0.record()
     for _ in range(reps):
@@ -234,7 +252,18 @@ def _time_calls(plan, g, b, grad, reps, torch):
     t1.record()
     torch.cuda.synchronize()
     plan.check()
-    return t0.elapsed_time(t1) / reps
+    ms = t0.elapsed_time(t1) / reps
+    if not kernel:
+        return ms
+    k = qb.qt_plan_kernel_times(plan.plan)
+    qb.qt_plan_set_profiling(plan.plan, False)
+    return ms, sum(k) / max(1, len(k))
+
+
+def _roofline(alg_bytes, kernel_ms, peak, peak_kind, kernel):
+    achieved = alg_bytes / (kernel_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "kernel": kernel, "kernel_ms": kernel_ms, "alg_bytes_per_launch": alg_bytes, "peak_kind": peak_kind}
 
 
 def min_fill_comparison(n, edges, p, B, g, b, dev, torch):
@@ -245,19 +274,6 @@ def min_fill_comparison(n, edges, p, B, g, b, dev, torch):
     out = {"value": len(edges) * B / (ms * 1e-3), "unit": "edge_evals/s", "ms_per_step": ms,
            "alg_bytes_per_step": plan.stats["alg_bytes"], "max_width": int(plan.stats["max_width"]),
            "achieved_gbs": plan.stats["alg_bytes"] / (ms * 1e-3) / 1e9}
-    plan.close()
-    return out
-
-
-def load_path_comparison(n, edges, p, B, g, b, dev, torch):
-    """The bench step with the operands staged in shared memory (bulk-copy ring)."""
-    from paper_2106_15740_gb300.energy import EnergyPlan
-    plan = EnergyPlan(n, edges, p, batch=B, dtype=WORKLOAD["dtype"], mode="persistent", device=dev,
-                      order_trials=WORKLOAD.get("order_trials", 0), load_path="staged")
-    ms = _time_calls(plan, g, b, False, 5, torch)
-    out = {"value": len(edges) * B / (ms * 1e-3), "unit": "edge_evals/s", "ms_per_step": ms,
-           "achieved_gbs": plan.stats["alg_bytes"] / (ms * 1e-3) / 1e9,
-           "what": "same plan, forward operands staged in shared memory by bulk copies (direct calls)"}
     plan.close()
     return out
 
@@ -294,19 +310,24 @@ def round_robin_comparison(n, edges, p, B, g, b, dev, torch):
 
 def gradient_and_comparator(dev, torch):
     """Energy-gradient throughput on the 60-vertex p = 4 workload (8 angles,
-    one angle set, complex64 adjoint sweep), and the plain per-edge complex128
-    contraction (one kernel launch per bucket, edge after edge, one angle set
-    at a time) on the gradient workload and on the bench workload."""
+    one angle set, adjoint sweep) in complex64 and complex128, and the plain
+    per-edge complex128 contraction (one kernel launch per bucket, edge after
+    edge, one angle set at a time) on the gradient workload and on the bench
+    workload (all 64 angle sets of one bench step, measured)."""
     from paper_2106_15740_gb300.energy import EnergyPlan
     from workloads import random_angles, workload
+    peak, peak_kind = _peaks()
     out = {}
     n, edges, p, g, b = workload("n60_p4")
     gd, bd = torch.tensor(g, device=dev), torch.tensor(b, device=dev)
-    plan = EnergyPlan(n, edges, p, batch=1, dtype="c64", mode="persistent", gradient=True, device=dev,
-                      order_trials=WORKLOAD.get("order_trials", 0))
-    ms_grad = _time_calls(plan, gd, bd, True, 5, torch)
-    grad_alg = plan.stats["alg_bytes"]
-    plan.close()
+    res = {}
+    for dt in ("c64", "c128"):
+        plan = EnergyPlan(n, edges, p, batch=1, dtype=dt, mode="persistent", gradient=True, device=dev,
+                          order_trials=WORKLOAD.get("order_trials", 0))
+        ms, kms = _time_calls(plan, gd, bd, True, 5, torch, kernel=True)
+        _, gr = plan.energy(gd, bd, grad=True)
+        res[dt] = dict(ms=ms, kms=kms, alg=plan.stats["alg_bytes"], grad=gr.cpu().numpy()[0])
+        plan.close()
     plan = EnergyPlan(n, edges, p, batch=1, dtype="c64", mode="persistent", gradient=True, device=dev)
     ms_grad_mf = _time_calls(plan, gd, bd, True, 3, torch)
     plan.close()
@@ -318,26 +339,125 @@ def gradient_and_comparator(dev, torch):
                       order_trials=WORKLOAD.get("order_trials", 0))
     ms_grad16 = _time_calls(plan, torch.tensor(gb, device=dev), torch.tensor(bb, device=dev), True, 3, torch)
     plan.close()
-    out["grad"] = {"metric": "energy-grad evals/sec", "value": 1e3 / ms_grad, "unit": "grad_evals/s",
+    c64, c128 = res["c64"], res["c128"]
+    out["grad"] = {"metric": "energy-grad evals/sec", "value": 1e3 / c64["ms"], "unit": "grad_evals/s",
                    "batched_16": {"value": 16e3 / ms_grad16, "ms_per_call": ms_grad16,
                                   "what": "16 angle sets per call (a multi-start optimiser's batch)"},
-                   "ms_per_eval": ms_grad, "dtype": "c64",
+                   "ms_per_eval": c64["ms"], "dtype": "c64",
                    "workload": "random 3-regular N=60 p=4 (seed 3), 90 edge lightcones, dE/dgamma and dE/dbeta "
                                "(8 angles) by the adjoint bucket sweep, one angle set",
                    "ordering": f"searched, {WORKLOAD.get('order_trials', 0)} trials per edge",
-                   "alg_bytes_per_eval": grad_alg, "achieved_gbs": grad_alg / (ms_grad * 1e-3) / 1e9,
+                   "alg_bytes_per_eval": c64["alg"], "achieved_gbs": c64["alg"] / (c64["ms"] * 1e-3) / 1e9,
+                   "roofline": _roofline(c64["alg"], c64["kms"], peak, peak_kind,
+                                         "persistent_kernel<float,1,true,true,2>"),
+                   "c128": {"value": 1e3 / c128["ms"], "ms_per_eval": c128["ms"], "alg_bytes_per_eval": c128["alg"],
+                            "roofline": _roofline(c128["alg"], c128["kms"], peak, peak_kind,
+                                                  "persistent_kernel<double,1,true,true,2>")},
+                   "max_abs_dgrad_c64_vs_c128": float(abs(c64["grad"] - c128["grad"]).max()),
+                   "max_abs_grad": float(abs(c128["grad"]).max()),
                    "min_fill_order_ms_per_eval": ms_grad_mf,
                    "per_edge_c128_forward_ms": ms_loop,
-                   "speedup_vs_per_edge_c128_forward": ms_loop / ms_grad}
-    n, edges, p, g, b = workload("n100_p4", batch=1)
-    gd, bd = torch.tensor(g, device=dev), torch.tensor(b, device=dev)
+                   "speedup_vs_per_edge_c128_forward": ms_loop / c64["ms"]}
+    n, edges, p, g, b = workload("n100_p4", batch=64)
     plan = EnergyPlan(n, edges, p, batch=1, dtype="c128", mode="per_bucket", device=dev)
-    ms_one = _time_calls(plan, gd, bd, False, 2, torch)
+    gs = [torch.tensor(g[k:k + 1], device=dev) for k in range(64)]
+    bs = [torch.tensor(b[k:k + 1], device=dev) for k in range(64)]
+    plan.energy(gs[0], bs[0])
+    plan.check()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for k in range(64):
+        plan.energy(gs[k], bs[k])
+    t1.record()
+    torch.cuda.synchronize()
+    plan.check()
+    ms_step = t0.elapsed_time(t1)
     plan.close()
-    out["per_edge_c128_loop"] = {"ms_per_angle_set": ms_one, "ms_per_step_equivalent": 64 * ms_one,
-                                 "edge_evals_per_s": len(edges) / (ms_one * 1e-3),
+    out["per_edge_c128_loop"] = {"ms_per_step": ms_step, "ms_per_angle_set": ms_step / 64,
+                                 "edge_evals_per_s": 64 * len(edges) / (ms_step * 1e-3),
                                  "what": "same graph, complex128, one launch per bucket, edges one after "
-                                         "another, one angle set per call (64 calls = one bench step)"}
+                                         "another, one angle set per call: all 64 calls of one bench step, measured"}
+    return out
+
+
+def complex128_counterparts(dev, torch):
+    """The bench plan (150 edges x 64 angle sets, searched orders, one
+    persistent launch) in complex128, and the 100-vertex p = 3 graph (one
+    angle set) in both precisions: time, roofline, and the complex64
+    error against complex128."""
+    import numpy as np
+    from paper_2106_15740_gb300.energy import EnergyPlan
+    from workloads import workload
+    peak, peak_kind = _peaks()
+    out = {}
+    for name, B, trials in (("n100_p4", 64, WORKLOAD.get("order_trials", 0)), ("n100_p3", 1, 0)):
+        n, edges, p, g, b = workload(name, batch=B)
+        gd, bd = torch.tensor(g, device=dev), torch.tensor(b, device=dev)
+        r = {}
+        for dt in ("c64", "c128"):
+            plan = EnergyPlan(n, edges, p, batch=B, dtype=dt, mode="persistent", device=dev, order_trials=trials)
+            ms, kms = _time_calls(plan, gd, bd, False, 5, torch, kernel=True)
+            e, zz = plan.energy(gd, bd, edge_zz=True)
+            plan.check()
+            r[dt] = dict(ms=ms, kms=kms, alg=plan.stats["alg_bytes"], e=e.cpu().numpy(), zz=zz.cpu().numpy())
+            plan.close()
+        key = "n100_p4_b64" if B == 64 else "n100_p3_b1"
+        out[key] = {
+            "c128": {"value": len(edges) * B / (r["c128"]["ms"] * 1e-3), "unit": "edge_evals/s",
+                     "ms_per_call": r["c128"]["ms"],
+                     "roofline": _roofline(r["c128"]["alg"], r["c128"]["kms"], peak, peak_kind, "persistent_kernel<double,...>")},
+            "c64": {"value": len(edges) * B / (r["c64"]["ms"] * 1e-3), "unit": "edge_evals/s",
+                    "ms_per_call": r["c64"]["ms"],
+                    "roofline": _roofline(r["c64"]["alg"], r["c64"]["kms"], peak, peak_kind, "persistent_kernel<float,...>")},
+            "c64_vs_c128": {"max_abs_dzz": float(np.abs(r["c64"]["zz"][:, :, 0] - r["c128"]["zz"][:, :, 0]).max()),
+                            "max_abs_dE": float(np.abs(r["c64"]["e"] - r["c128"]["e"]).max())},
+            "workload": f"{name}, {len(edges)} edges x {B} angle sets, "
+                        + (f"searched orders ({trials} trials)" if trials else "min-fill orders")}
+    return out
+
+
+def large_config(dev, torch):
+    """The 244-vertex p = 5 graph (366 edges): searched orders (100 trials),
+    width budget 28 with slicing; energy and energy + gradient in complex64,
+    energy in complex128 for the error; one angle set."""
+    import numpy as np
+    from paper_2106_15740_gb300.energy import EnergyPlan
+    from workloads import workload
+    peak, peak_kind = _peaks()
+    n, edges, p, g, b = workload("n244_p5")
+    gd, bd = torch.tensor(g, device=dev), torch.tensor(b, device=dev)
+    kw = dict(batch=1, mode="persistent", device=dev, order_trials=100, max_width=28, slice=True,
+              max_workspace=100 << 30)
+    out = {"workload": "random 3-regular N=244 p=5 (seed 4), 366 edge lightcones, one angle set, searched orders "
+                       "(100 trials), width budget 28 (wider edges sliced)"}
+    plan = EnergyPlan(n, edges, p, dtype="c64", **kw)
+    ms, kms = _time_calls(plan, gd, bd, False, 3, torch, kernel=True)
+    e64, zz64 = plan.energy(gd, bd, edge_zz=True)
+    plan.check()
+    out["energy_c64"] = {"value": len(edges) / (ms * 1e-3), "unit": "edge_evals/s", "ms_per_call": ms,
+                         "max_width": int(plan.widths.max()), "sliced_edges": int((plan.slices > 0).sum()),
+                         "networks": int((2 ** plan.slices.astype(np.int64)).sum()),
+                         "roofline": _roofline(plan.stats["alg_bytes"], kms, peak, peak_kind, "persistent_kernel<float,1,true,false,2>")}
+    plan.close()
+    torch.cuda.empty_cache()
+    plan = EnergyPlan(n, edges, p, dtype="c64", gradient=True, **kw)
+    ms, kms = _time_calls(plan, gd, bd, True, 2, torch, kernel=True)
+    _, g64 = plan.energy(gd, bd, grad=True)
+    plan.check()
+    out["energy_grad_c64"] = {"value": 1e3 / ms, "unit": "grad_evals/s", "ms_per_call": ms,
+                              "roofline": _roofline(plan.stats["alg_bytes"], kms, peak, peak_kind,
+                                                    "persistent_kernel<float,1,true,true,2>")}
+    plan.close()
+    torch.cuda.empty_cache()
+    plan = EnergyPlan(n, edges, p, dtype="c128", **kw)
+    ms128 = _time_calls(plan, gd, bd, False, 1, torch)
+    e128, zz128 = plan.energy(gd, bd, edge_zz=True)
+    plan.check()
+    plan.close()
+    torch.cuda.empty_cache()
+    out["energy_c128_ms_per_call"] = ms128
+    out["c64_vs_c128"] = {"max_abs_dzz": float((zz64[:, 0, 0] - zz128[:, 0, 0]).abs().max()),
+                          "abs_dE": float((e64 - e128).abs().max())}
     return out
 
 
@@ -403,7 +523,7 @@ def run_ours(args):
     profile_only = ((WORKLOAD["name"], B) != ("n100_p4", 64) or "edge_range" in WORKLOAD or "lane_items" in WORKLOAD
                     or "chunk_tiles" in WORKLOAD or "gradient" in WORKLOAD or "max_width" in WORKLOAD
                     or "profile_order" in WORKLOAD
-                    or "load_path" in WORKLOAD or "chain_steps" in WORKLOAD or "queue_order" in WORKLOAD)
+                    or "chain_steps" in WORKLOAD or "queue_order" in WORKLOAD)
     grad = bool(WORKLOAD.get("gradient", False))
     gamma, beta = random_angles(B, p, 1002 + 7919 * rank)
     tuned = None
@@ -414,17 +534,24 @@ def run_ours(args):
                                  lane_items=(16, 32, 64), group_rows=(0, -1, 32),
                                  order_trials=WORKLOAD.get("order_trials", 0))
         WORKLOAD["lane_items"], WORKLOAD["group_rows"] = best["lane_items"], best["group_rows"]
+        # then the per-width schedule: warp tiles per queue task by band of output ranks
+        from paper_2106_15740_gb300.energy import autotune_bands
+        by_rank, band_ms = autotune_bands(n, edges, p, batch=B, dtype=WORKLOAD["dtype"], device=dev, reps=3,
+                                          order_trials=WORKLOAD.get("order_trials", 0),
+                                          lane_items=best["lane_items"], group_rows=best["group_rows"])
+        WORKLOAD["chunk_tiles_by_rank"] = by_rank
         tuned = {"choice": best,
-                 "ms_per_candidate": {f"lane_items={k[0]},group_rows={k[1]}": round(v, 3) for k, v in timings.items()}}
+                 "ms_per_candidate": {f"lane_items={k[0]},group_rows={k[1]}": round(v, 3) for k, v in timings.items()},
+                 "per_width_band": band_ms}
     t_plan = time.perf_counter()
     plan = EnergyPlan(n, edges, p, batch=B, dtype=WORKLOAD["dtype"], mode="persistent", device=dev,
                       edge_range=WORKLOAD.get("edge_range"), lane_items=WORKLOAD.get("lane_items", 0),
                       group_rows=WORKLOAD.get("group_rows", 0), chunk_tiles=WORKLOAD.get("chunk_tiles", 0),
                       gradient=grad, max_width=WORKLOAD.get("max_width", 0), slice=WORKLOAD.get("slice", False),
                       max_workspace=WORKLOAD.get("max_workspace", 0), order_trials=WORKLOAD.get("order_trials", 0),
-                      load_path=WORKLOAD.get("load_path", "registers"),
                       chain_steps=WORKLOAD.get("chain_steps", False),
-                      queue_order=WORKLOAD.get("queue_order", "critical_path"))
+                      queue_order=WORKLOAD.get("queue_order", "critical_path"),
+                      chunk_tiles_by_rank=WORKLOAD.get("chunk_tiles_by_rank"))
     t_plan = time.perf_counter() - t_plan
     from paper_2106_15740_gb300.schedule import bytes_by_rank
     g = torch.tensor(gamma, device=dev)
@@ -447,15 +574,19 @@ def run_ours(args):
         if rank == 0 else None
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     t0.record(stream)
-    for _ in range(args.steps):
+    marks[0].record(stream)
+    for i in range(args.steps):
         step.replay()
+        marks[i + 1].record(stream)
     t1.record(stream)
     torch.cuda.synchronize(dev)
     if pg:
         pg.barrier()
     plan.check()
     ms = t0.elapsed_time(t1) / args.steps
+    per_step = sorted(marks[i].elapsed_time(marks[i + 1]) for i in range(args.steps))
 
     # Kernel time of the persistent launch: the same K steps as direct calls
     # with the library's profiling events around the bucket launch (events
@@ -520,8 +651,7 @@ def run_ours(args):
                        "alg_bytes_by_result_rank": bytes_by_rank(plan.plan, B, 8 if WORKLOAD["dtype"] == "c64" else 16)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": _traffic(B, alg, profile_only),
-                         "kernel": "persistent_kernel<float,2,false,false,%s>" % (
-                             "true" if WORKLOAD.get("load_path") == "staged" else "false"),
+                         "kernel": "persistent_kernel<float,2,false,false,2>",
                          "kernel_ms": kms, "kernel_ms_from": "CUDA events around the persistent launch over "
                                                              "K direct calls after the graph-timed steps", "alg_bytes_per_launch": alg, "peak_kind": peak_kind},
             "e2e": {"value": units * world / e2e_s, "unit": "edge_evals/s",
@@ -530,6 +660,9 @@ def run_ours(args):
             "step_form": {"timed": "K replays of one CUDA graph holding the evaluation "
                                    "(angle table, leaf factors, persistent launch, FP64 energy sum)",
                           "ms_per_step_direct_calls": ms_direct},
+            "step_ms": {"mean": ms, "median": per_step[len(per_step) // 2], "min": per_step[0],
+                        "max": per_step[-1], "steps": len(per_step),
+                        "what": "CUDA events between consecutive graph replays of the timed region"},
             "clocks": clk,
         }
         if tuned:
@@ -539,16 +672,20 @@ def run_ours(args):
         if not profile_only and WORKLOAD.get("order_trials", 0):
             res["min_fill_order"] = min_fill_comparison(n, edges, p, B, g, b, dev, torch)
         if not profile_only:
-            res["staged_loads"] = load_path_comparison(n, edges, p, B, g, b, dev, torch)
             res["chained_steps"] = chain_comparison(n, edges, p, B, g, b, dev, torch)
             res["round_robin_queue"] = round_robin_comparison(n, edges, p, B, g, b, dev, torch)
         if not args.no_cpu_baseline:
+            e_gpu, zz = plan.energy(g, b, edge_zz=True)
+            plan.check()
+            zz_host, e_host = zz[:, :, 0].cpu().numpy(), e_gpu.cpu().numpy()
+            plan.close()
+            torch.cuda.empty_cache()
             res.update(gradient_and_comparator(dev, torch))
+            res["complex128"] = complex128_counterparts(dev, torch)
+            res["large"] = large_config(dev, torch)
             res["single_amplitude"] = amplitude_measure(dev, torch)
             res["per_edge_c128_loop"]["speedup_of_value"] = res["value"] / res["per_edge_c128_loop"]["edge_evals_per_s"]
-            _, zz = plan.energy(g, b, edge_zz=True)
-            plan.check()
-            res["cpu_baseline"], res["error_vs_oracle"] = cpu_baseline(gpu_zz=zz[:, :, 0].cpu().numpy())
+            res["cpu_baseline"], res["error_vs_oracle"] = cpu_baseline(gpu_zz=zz_host, gpu_e=e_host)
         print(json.dumps(res))
     if pg:
         pg.destroy_process_group()
@@ -572,8 +709,6 @@ def main():
     ap.add_argument("--max-width", type=int, default=0, help="profiling only: width budget")
     ap.add_argument("--slice", action="store_true", help="profiling only: slice edges above the width budget")
     ap.add_argument("--max-workspace-gb", type=float, default=0, help="profiling only: workspace cap")
-    ap.add_argument("--load-path", default=None, choices=["staged", "registers"],
-                    help="profiling only: operand path of the persistent kernel")
     ap.add_argument("--chain-steps", action="store_true",
                     help="profiling only: chain every step of a workspace slot to the one before it")
     ap.add_argument("--queue-order", default=None, choices=["round_robin", "critical_path"],
@@ -599,9 +734,6 @@ def main():
     if args.order_trials is not None:
         WORKLOAD["order_trials"] = args.order_trials
         WORKLOAD["profile_order"] = True
-        args.no_cpu_baseline = True
-    if args.load_path is not None:
-        WORKLOAD["load_path"] = args.load_path
         args.no_cpu_baseline = True
     if args.chain_steps:
         WORKLOAD["chain_steps"] = True

@@ -159,14 +159,6 @@ typedef struct {
   int32_t order_seed;     /* seed of the randomised orders (with the edge index) */
   double order_tau;       /* temperature: the next variable is drawn with probability
                              proportional to exp(-(fill - min fill) / order_tau) (<=0: 1) */
-  int32_t load_path;      /* persistent mode: 0 (default) loads every operand into registers;
-                             1 stages the intermediate operands of forward steps in a per-warp
-                             shared-memory ring several rows ahead: lane 0 brings each operand
-                             row pair with one bulk copy (TMA) completing on the slot's
-                             mbarrier, and a bucket's leaf-factor rows stay in registers.
-                             Staging applies to row-wide tiles of 16-byte vectors (complex64
-                             with even B in [34, 64], complex128 with B in [17, 32]); other
-                             batches keep the register path.  Both give bit-identical results */
   int64_t checkpoint_bytes; /* gradient plans: 0 (default) keeps every forward intermediate of a
                              network for the reverse sweep.  > 0 cuts each network's bucket order
                              into segments whose intermediates hold at most this many bytes;
@@ -190,6 +182,12 @@ typedef struct {
                              dependents to the end of their slot), which starts long paths
                              early; 0 it takes the slots round-robin, step by step.  Results are
                              bit-identical either way */
+  int32_t chunk_tiles_by_rank[32]; /* persistent mode, per-width schedule: a step whose output rank
+                             is r runs in queue tasks of chunk_tiles_by_rank[r] warp tiles when that
+                             is > 0 (at least as many as the queue-length rule asks for), else as
+                             chunk_tiles says.  The autotuner picks these per width band (§Results:
+                             the width of a step sets its cost).  Results are bit-identical for
+                             any choice */
 } qt_plan_options;
 
 /* Fill `opt` with defaults: batch 1, QT_C128, QT_MODE_PER_BUCKET, no gradient,
@@ -343,11 +341,14 @@ qt_status qt_representation_cost(const qt_graph* g, int32_t p, int32_t rep, int3
  * replaced or cleared with NULL; QT_ESTATE for a per-bucket plan.  Each task
  * is one entry of qt_plan_tasks(): its step and chunk (chunk < 0: a group of
  * -chunk single-tile steps starting at that step), with the step's output
- * rank, edge (index into the plan's edge range) and fan-in. */
+ * rank, edge (index into the plan's edge range), fan-in and kind (0 forward
+ * bucket step, 1 adjoint of one input, 2 clearing an accumulated adjoint,
+ * 3 adjoint of one input by reduction over its missing variables).  Output
+ * arrays may be NULL. */
 qt_status qt_plan_trace_size(const qt_plan* plan, size_t* bytes);
 qt_status qt_plan_set_trace(qt_plan* plan, void* trace, size_t bytes);
 qt_status qt_plan_tasks(const qt_plan* plan, int32_t* n_tasks, int32_t* step, int32_t* chunk,
-                        int32_t* out_rank, int32_t* edge, int32_t* n_in);
+                        int32_t* out_rank, int32_t* edge, int32_t* n_in, int32_t* kind);
 
 /* Schedule of a persistent plan, for checking on the host that steps which
  * touch the same workspace elements are ordered (§bucket elimination: a

@@ -52,8 +52,9 @@ class qt_plan_options(C.Structure):
                 ("max_workspace", C.c_int64), ("group_rows", C.c_int32), ("edge_begin", C.c_int32),
                 ("edge_end", C.c_int32), ("slice", C.c_int32),
                 ("chunk_tiles", C.c_int32), ("order_trials", C.c_int32), ("order_seed", C.c_int32),
-                ("order_tau", C.c_double), ("load_path", C.c_int32), ("checkpoint_bytes", C.c_int64),
-                ("chain_steps", C.c_int32), ("queue_order", C.c_int32)]
+                ("order_tau", C.c_double), ("checkpoint_bytes", C.c_int64),
+                ("chain_steps", C.c_int32), ("queue_order", C.c_int32),
+                ("chunk_tiles_by_rank", C.c_int32 * 32)]
 
 
 _lib = None
@@ -98,7 +99,7 @@ def lib():
             "qt_plan_amplitudes": [vp, vp, vp, vp, vp, sz, vp],
             "qt_representation_cost": [C.POINTER(qt_graph), i32, i32, i32, i32, pi32, pi32, pd],
             "qt_plan_set_trace": [vp, vp, sz],
-            "qt_plan_tasks": [vp, pi32, pi32, pi32, pi32, pi32, pi32],
+            "qt_plan_tasks": [vp, pi32, pi32, pi32, pi32, pi32, pi32, pi32],
             "qt_plan_schedule": [vp, pi32, pi32, pi32, pi32, pi32, pi32, pi32,
                                  C.POINTER(C.c_int64), C.POINTER(C.c_int64), pi32, pi32],
         }
@@ -331,11 +332,12 @@ def qt_plan_set_trace(plan, trace_ptr, nbytes):
 
 
 def qt_plan_tasks(plan):
-    """Queue tasks as a dict of int32 arrays: step, chunk, out_rank, edge, n_in."""
+    """Queue tasks as a dict of int32 arrays: step, chunk, out_rank, edge, n_in, kind."""
+    names = ("step", "chunk", "out_rank", "edge", "n_in", "kind")
     n = C.c_int32()
-    _check(lib().qt_plan_tasks(plan, C.byref(n), None, None, None, None, None))
-    cols = {k: np.empty(n.value, dtype=np.int32) for k in ("step", "chunk", "out_rank", "edge", "n_in")}
-    _check(lib().qt_plan_tasks(plan, C.byref(n), *(_as_pi32(cols[k]) for k in ("step", "chunk", "out_rank", "edge", "n_in"))))
+    _check(lib().qt_plan_tasks(plan, C.byref(n), None, None, None, None, None, None))
+    cols = {k: np.empty(n.value, dtype=np.int32) for k in names}
+    _check(lib().qt_plan_tasks(plan, C.byref(n), *(_as_pi32(cols[k]) for k in names)))
     return cols
 
 

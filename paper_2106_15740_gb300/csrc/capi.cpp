@@ -256,10 +256,10 @@ void qt_plan_options_default(qt_plan_options* opt) {
   opt->order_trials = 0;
   opt->order_seed = 0;
   opt->order_tau = 1.0;
-  opt->load_path = 0;
   opt->checkpoint_bytes = 0;
   opt->chain_steps = 0;
   opt->queue_order = 1;
+  for (int32_t r = 0; r < 32; ++r) opt->chunk_tiles_by_rank[r] = 0;
 }
 
 static qt_status check_options(const qt_plan_options* opt, qt_plan_options* out) {
@@ -275,10 +275,12 @@ static qt_status check_options(const qt_plan_options* opt, qt_plan_options* out)
   if (o.lane_items <= 0) o.lane_items = o.batch >= 16 ? 32 : 16;
   if (o.order_trials < 0 || o.order_trials > 100000) return fail(QT_EINVAL, "order_trials must be in [0, 100000]");
   if (!(o.order_tau >= 0.0) || !std::isfinite(o.order_tau)) return fail(QT_EINVAL, "order_tau must be finite and >= 0");
-  if (o.load_path != 0 && o.load_path != 1) return fail(QT_EINVAL, "load_path must be 0 or 1");
   if (o.checkpoint_bytes < 0) return fail(QT_EINVAL, "checkpoint_bytes must be >= 0");
   if (o.chain_steps != 0 && o.chain_steps != 1) return fail(QT_EINVAL, "chain_steps must be 0 or 1");
   if (o.queue_order != 0 && o.queue_order != 1) return fail(QT_EINVAL, "queue_order must be 0 or 1");
+  for (int32_t r = 0; r < 32; ++r)
+    if (o.chunk_tiles_by_rank[r] < 0 || o.chunk_tiles_by_rank[r] > (1 << 20))
+      return fail(QT_EINVAL, "chunk_tiles_by_rank entries must be in [0, 2^20]");
   *out = o;
   return QT_OK;
 }
@@ -522,7 +524,7 @@ qt_status qt_plan_set_trace(qt_plan* plan, void* trace, size_t bytes) {
 }
 
 qt_status qt_plan_tasks(const qt_plan* plan, int32_t* n_tasks, int32_t* step, int32_t* chunk, int32_t* out_rank,
-                        int32_t* edge, int32_t* n_in) {
+                        int32_t* edge, int32_t* n_in, int32_t* kind) {
   if (!plan || !n_tasks) return fail(QT_EINVAL, "NULL argument");
   const Plan& P = plan->P;
   *n_tasks = (int32_t)P.tasks.size();
@@ -541,6 +543,7 @@ qt_status qt_plan_tasks(const qt_plan* plan, int32_t* n_tasks, int32_t* step, in
     if (out_rank) out_rank[t] = P.buckets[T.bucket].out_rank;
     if (edge) edge[t] = step_edge[T.bucket];
     if (n_in) n_in[t] = P.buckets[T.bucket].n_in;
+    if (kind) kind[t] = P.buckets[T.bucket].kind;
   }
   return QT_OK;
 }

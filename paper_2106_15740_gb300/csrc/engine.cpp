@@ -3,7 +3,7 @@
 // compile_plan turns the bucket plans of every edge network into device
 // records (qt_device.h) and lays out the workspace:
 //   [ctrl | done counters | buckets | tasks | dependency lists | leaf factors | scalar table |
-//    angles | results | trig table | data]
+//    network leaf counts | angles | results | trig table | data]
 // data = [leaf-factor pool | scalar results | intermediate arenas].
 // Intermediates of one edge live in an arena planned by first-fit with
 // free-on-consume: a bucket's output is allocated before its inputs are
@@ -521,6 +521,7 @@ qt_status compile_plan(Plan* P) {
       lf.off = leaf_off[e][i];
       lf.rank = bk.leaf_rank;
       lf.n_leaves = (int32_t)bk.leaves.size();
+      lf.net = e;
       for (int32_t l = 0; l < lf.n_leaves; ++l) {
         const LeafRef& Lr = bk.leaves[l];
         lf.leaf[l] = (uint32_t)Lr.kind | (uint32_t)Lr.conj << 2 | (uint32_t)Lr.rank << 3 |
@@ -655,6 +656,20 @@ qt_status compile_plan(Plan* P) {
     P->scal_begin[e + 1] = (int32_t)P->scal_off.size();
   }
   P->edge_first[n_edges] = (int32_t)P->buckets.size();
+  // leaf counts of each network: ZZ and mixer leaves per layer, |+> leaves
+  // (the norm of the stored gates is divided out per network on the device)
+  {
+    const int32_t stride = 2 * P->p + 1;
+    P->net_counts.assign((size_t)n_edges * stride, 0);
+    for (int32_t e = 0; e < n_edges; ++e)
+      for (const Bucket& bk : P->edges[e].buckets)
+        for (const LeafRef& L : bk.leaves) {
+          int32_t* c = &P->net_counts[(size_t)e * stride];
+          if (L.kind == QT_T_ZZ && L.layer >= 1 && L.layer <= P->p) ++c[L.layer - 1];
+          else if (L.kind == QT_T_MIX && L.layer >= 1 && L.layer <= P->p) ++c[P->p + L.layer - 1];
+          else if (L.kind == QT_T_PLUS) ++c[2 * P->p];
+        }
+  }
   // leaf factors of each planned graph edge (its networks are consecutive)
   {
     std::vector<int32_t> net_leaf(n_edges + 1, 0);
@@ -692,7 +707,9 @@ qt_status compile_plan(Plan* P) {
       }
     for (DevBucket& d : P->buckets) {
       const int64_t nt = step_tiles(d, geom.R);
-      const int64_t span = P->opt.chunk_tiles > 0 ? P->opt.chunk_tiles : (nt + cap - 1) / cap;
+      int64_t span = P->opt.chunk_tiles > 0 ? P->opt.chunk_tiles : (nt + cap - 1) / cap;
+      const int32_t by_rank = d.out_rank >= 0 && d.out_rank < 32 ? P->opt.chunk_tiles_by_rank[d.out_rank] : 0;
+      if (by_rank > 0) span = std::max<int64_t>(by_rank, (nt + cap - 1) / cap);
       d.span = (int32_t)std::min<int64_t>(std::max<int64_t>(span, 1), INT32_MAX);
       if ((nt + d.span - 1) / d.span > INT32_MAX / 2) return fail(QT_EWIDTH, "step too large for the task queue");
     }
@@ -818,14 +835,6 @@ qt_status compile_plan(Plan* P) {
     }
   }
 
-  // The bulk-copy ring reads each operand row pair with one 16-byte-aligned
-  // copy: every forward input must start on a 16-byte boundary.
-  P->bulk_ok = true;
-  for (const DevBucket& d : P->buckets)
-    if (d.kind == kStepFwd)
-      for (int32_t i = 0; i < d.n_in; ++i)
-        if ((d.in[i].off * (int64_t)es) % 16 != 0) P->bulk_ok = false;
-
   // Workspace layout.
   WsLayout& L = P->ws;
   const int32_t p = P->p;
@@ -850,12 +859,14 @@ qt_status compile_plan(Plan* P) {
   o = align256(o + sizeof(int32_t) * P->scal_begin.size());
   L.net_first = o;
   o = align256(o + sizeof(int32_t) * P->net_first.size());
+  L.counts = o;
+  o = align256(o + sizeof(int32_t) * P->net_counts.size());
   L.angles = o;
   o = align256(o + sizeof(double) * 2 * (size_t)B * p);
   L.results = o;
   o = align256(o + sizeof(double) * ((size_t)B + (size_t)P->n_orig * B * 2 + (size_t)B * 2 * p));
   L.trig = o;
-  o = align256(o + sizeof(double) * 4 * (size_t)B * p);
+  o = align256(o + sizeof(double) * kTrigStride * (size_t)B * p);
   L.dz = o;
   if (grad) o = align256(o + sizeof(double) * 2 * (size_t)P->n_orig * B * 2 * p);
   L.gpart = o;
@@ -923,6 +934,9 @@ qt_status run_plan(Plan* P, const double* gamma, const double* beta, double* ene
                             cudaMemcpyHostToDevice, s));
     QT_CUDA(cudaMemcpyAsync(base + L.net_first, P->net_first.data(), sizeof(int32_t) * P->net_first.size(),
                             cudaMemcpyHostToDevice, s));
+    if (!P->net_counts.empty())
+      QT_CUDA(cudaMemcpyAsync(base + L.counts, P->net_counts.data(), sizeof(int32_t) * P->net_counts.size(),
+                              cudaMemcpyHostToDevice, s));
     QT_CUDA(cudaStreamSynchronize(s));  // host vectors may change after return
     P->bound_ws = ws;
     P->device = dev;
@@ -933,7 +947,7 @@ qt_status run_plan(Plan* P, const double* gamma, const double* beta, double* ene
   if (P->lbar_elems > 0)  // leaf-factor adjoints are accumulated with atomics
     QT_CUDA(cudaMemsetAsync(base + L.data + (size_t)P->elem_bytes * P->lbar_shift, 0,
                             (size_t)P->elem_bytes * P->lbar_elems, s));
-  QT_CUDA(launch_trig(gamma, beta, P->p, B, trig, s));
+  QT_CUDA(launch_trig(dtype, gamma, beta, P->p, B, trig, s));
   QT_CUDA(launch_leaf_factors(dtype, (const DevLeafFactor*)(base + L.leaf), (int32_t)P->leaf.size(), trig, P->p,
                               B, data, s));
   const DevBucket* dbk = (const DevBucket*)(base + L.buckets);
@@ -951,11 +965,11 @@ qt_status run_plan(Plan* P, const double* gamma, const double* beta, double* ene
   }
   if (P->opt.mode == QT_MODE_PERSISTENT) {
     int per_sm = 0;
-    QT_CUDA(persistent_occupancy(dtype, P->opt.gradient != 0, P->opt.load_path, P->bulk_ok, B, &per_sm));
+    QT_CUDA(persistent_occupancy(dtype, P->opt.gradient != 0, B, &per_sm));
     int n_sm = 0;
     QT_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
     const int32_t grid = std::max(1, per_sm) * n_sm;
-    QT_CUDA(launch_persistent(dtype, P->opt.gradient != 0, P->opt.load_path, P->bulk_ok, dbk, (const DevTask*)(base + L.tasks), (int32_t)P->tasks.size(),
+    QT_CUDA(launch_persistent(dtype, P->opt.gradient != 0, dbk, (const DevTask*)(base + L.tasks), (int32_t)P->tasks.size(),
                               (DevCtrl*)(base + L.ctrl), (int32_t*)(base + L.done), B, P->opt.lane_items, data,
                               P->data_elems, grid, P->spin_limit, (const int32_t*)(base + L.deps), P->trace, s));
   } else {
@@ -966,11 +980,13 @@ qt_status run_plan(Plan* P, const double* gamma, const double* beta, double* ene
   }
   if (ev_stop) QT_CUDA(cudaEventRecord(ev_stop, s));
   QT_CUDA(launch_energy(dtype, data, (const int64_t*)(base + L.scal_off), (const int32_t*)(base + L.scal_begin),
-                        (const int32_t*)(base + L.net_first), P->n_orig, B, energy, edge_zz, s));
+                        (const int32_t*)(base + L.net_first), (const int32_t*)(base + L.counts), trig, P->p,
+                        P->n_orig, B, energy, edge_zz, s));
   if (grad)
     QT_CUDA(launch_gradient(dtype, (const DevLeafFactor*)(base + L.leaf), (int32_t)P->leaf.size(),
                             (const int32_t*)(base + L.leaf_first), P->n_orig, P->lbar_shift, trig,
-                            P->p, B, data, (double*)(base + L.gpart), (double*)(base + L.dz), grad, s));
+                            (const int32_t*)(base + L.counts), P->p, B, data, (double*)(base + L.gpart),
+                            (double*)(base + L.dz), grad, s));
   return QT_OK;
 }
 

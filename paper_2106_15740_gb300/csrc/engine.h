@@ -18,7 +18,7 @@ namespace qt {
 
 struct WsLayout {
   size_t ctrl = 0, done = 0, buckets = 0, tasks = 0, deps = 0, leaf = 0, leaf_first = 0, scal_off = 0, scal_begin = 0,
-         net_first = 0;
+         net_first = 0, counts = 0;
   size_t angles = 0, results = 0, trig = 0, dz = 0, gpart = 0, data = 0, total = 0;
 };
 
@@ -56,6 +56,7 @@ struct Plan {
   std::vector<uint8_t> acc_w;
   std::vector<int64_t> scal_off;           // element offsets of scalar results
   std::vector<int32_t> scal_begin;         // CSR over edges
+  std::vector<int32_t> net_counts;         // per network: ZZ and mixer leaves per layer, |+> leaves (2p + 1)
   int64_t tile_items = 0;                  // output rows per warp tile
   int32_t spin_limit = 1 << 22;            // polls of a bounded dependency wait
   int32_t n_slots = 0;
@@ -68,9 +69,6 @@ struct Plan {
 
   // the plan's units are bitstrings of single amplitudes, not edges
   bool amplitude = false;
-
-  // every forward-step input starts on a 16-byte boundary (bulk-copy ring usable)
-  bool bulk_ok = false;
 
   // queue trace buffer (device, 4 x uint64 per task) or null
   unsigned long long* trace = nullptr;

@@ -6,18 +6,95 @@
 namespace qt {
 namespace dev {
 
-// Angle table: trig[(b * p + q) * 4 + {0,1,2,3}] = cos g, sin g, cos b, sin b.
+// Angle table (qt_device.h, kTrigStride doubles per angle set and layer):
+// the cos and sin values the ZZ and mixer leaves take, and log r of each.
+//
+// complex128: the FP64 cos and sin, log r = 0.
+// complex64: every leaf is stored as a float pair (c, s), and any such pair
+// is exactly r (cos t', sin t') with r = |(c, s)| and t' = atan2(s, c): a
+// stored gate (ZZ phase or mixer) is r times the exact gate at the angle t'.
+// The pair is chosen to put t' as close to t as the float grid allows: the
+// larger of |cos t|, |sin t| is stepped over the floats within kUnitSearch
+// ulps of its rounded value, the other component is the float nearest to
+// the same ratio, and the candidate with the smallest angle |t' - t| (from
+// the cross and dot products with (cos t, sin t), in FP64) wins.  Nearest
+// rounding of both leaves up to about 4e-8 rad of angle error and a norm
+// error of the same size; the search brings the angle error under about
+// 1.5e-8 rad at every angle (less where the two components' grids do not
+// step together), and the norm error is divided out per network in FP64
+// (energy_kernel and leafgrad_kernel, with the network's leaf counts).
+constexpr int kUnitSearch = 48;
+
+__device__ __forceinline__ float step_ulps(float x, int k) { return __int_as_float(__float_as_int(x) + k); }
+
+__device__ void unit_pair_f32(double t, double* c_out, double* s_out, double* log_r) {
+  double st, ct;
+  sincos(t, &st, &ct);
+  const bool cbig = fabs(ct) >= fabs(st);
+  const double big = cbig ? ct : st, small = cbig ? st : ct;
+  const double ratio = small / big;
+  const float b0 = (float)big;  // |big| >= 1/sqrt(2): stepping its bits never crosses zero
+  float bb = b0, sb = (float)small;
+  double best = -1.0;
+  for (int j = 0; j <= 2 * kUnitSearch; ++j) {  // k = 0, 1, -1, 2, -2, ...: ties keep the nearest
+    const int k = (j & 1) ? (j + 1) / 2 : -(j / 2);
+    const float bk = step_ulps(b0, k);
+    const float sk = (float)((double)bk * ratio);
+    const double cross = (double)sk * big - (double)bk * small;
+    const double dot = (double)bk * big + (double)sk * small;
+    const double err = fabs(cross / dot) + 1e-12 * (double)abs(k);  // near-ties go to the nearest float
+    if (best < 0.0 || err < best) {
+      best = err;
+      bb = bk;
+      sb = sk;
+    }
+  }
+  const double c = cbig ? (double)bb : (double)sb, s = cbig ? (double)sb : (double)bb;
+  *c_out = c;
+  *s_out = s;
+  *log_r = 0.5 * log(c * c + s * s);
+}
+
+template <class Real>
 __global__ void trig_kernel(const double* __restrict__ gamma, const double* __restrict__ beta, int32_t p,
                             int32_t B, double* __restrict__ trig) {
   const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= B * p) return;
-  double sg, cg, sb, cb;
-  sincos(gamma[i], &sg, &cg);
-  sincos(beta[i], &sb, &cb);
-  trig[4 * i + 0] = cg;
-  trig[4 * i + 1] = sg;
-  trig[4 * i + 2] = cb;
-  trig[4 * i + 3] = sb;
+  double* t = trig + (int64_t)kTrigStride * i;
+  if (sizeof(Real) == sizeof(double)) {
+    double sg, cg, sb, cb;
+    sincos(gamma[i], &sg, &cg);
+    sincos(beta[i], &sb, &cb);
+    t[0] = cg;
+    t[1] = sg;
+    t[2] = cb;
+    t[3] = sb;
+    t[4] = 0.0;
+    t[5] = 0.0;
+  } else {
+    unit_pair_f32(gamma[i], &t[0], &t[1], &t[4]);
+    unit_pair_f32(beta[i], &t[2], &t[3], &t[5]);
+  }
+}
+
+// |+> amplitude 1/sqrt(2) as the leaves store it, and log of its ratio to
+// the exact value (the |+> part of a network's norm correction).
+template <class Real> __device__ __forceinline__ double plus_amp() { return (double)(Real)0.70710678118654752440; }
+template <class Real> __device__ __forceinline__ double log_r_plus() {
+  return sizeof(Real) == sizeof(double) ? 0.0 : log(plus_amp<Real>() * 1.41421356237309504880);
+}
+
+// log of the stored-gate norm product of network k at angle set b (0 for
+// complex128): sum over its leaves of log r.
+__device__ __forceinline__ double network_log_r(const int32_t* __restrict__ counts, int32_t k, int32_t b, int32_t p,
+                                                const double* __restrict__ trig, double lr_plus) {
+  const int32_t* c = counts + (int64_t)k * (2 * p + 1);
+  double acc = (double)c[2 * p] * lr_plus;
+  for (int32_t q = 0; q < p; ++q) {
+    const double* t = trig + ((int64_t)b * p + q) * kTrigStride;
+    acc += (double)c[q] * t[4] + (double)c[p + q] * t[5];
+  }
+  return acc;
 }
 
 // Value of one leaf at its index bits (§Diagonal gate simplification and
@@ -37,45 +114,106 @@ __device__ __forceinline__ uint32_t leaf_bit1(uint32_t w, uint32_t z) {
   return (w >> 17) & 1u ? (w >> 18) & 1u : (z >> ((w >> 10) & 31u)) & 1u;
 }
 
+// The leaf's value as it is stored for precision Real (the ZZ and mixer
+// values come from the angle table, already Real-exact; the |+> amplitude
+// is rounded to Real), returned in FP64 so that products of leaves are
+// taken in FP64 and rounded to Real once.
 template <class Real>
-__device__ __forceinline__ typename Cx<Real>::T leaf_value_bits(uint32_t w, uint32_t b0, uint32_t b1,
-                                                                const double* tr) {
+__device__ __forceinline__ double2 leaf_value_bits(uint32_t w, uint32_t b0, uint32_t b1, const double* tr) {
   const uint32_t kind = w & 3u, conj = (w >> 2) & 1u;
-  typename Cx<Real>::T v;
+  double2 v;
   if (kind == 0u) {
-    v.x = (Real)0.70710678118654752440;
-    v.y = 0;
+    v.x = plus_amp<Real>();
+    v.y = 0.0;
   } else if (kind == 1u) {
-    const Real s = (b0 == b1) ? (Real)1 : (Real)-1;
-    v.x = (Real)tr[0];
-    v.y = -s * (Real)tr[1];
+    const double s = (b0 == b1) ? 1.0 : -1.0;
+    v.x = tr[0];
+    v.y = -s * tr[1];
   } else if (kind == 2u) {
     if (b0 == b1) {
-      v.x = (Real)tr[2];
-      v.y = 0;
+      v.x = tr[2];
+      v.y = 0.0;
     } else {
-      v.x = 0;
-      v.y = -(Real)tr[3];
+      v.x = 0.0;
+      v.y = -tr[3];
     }
   } else {
-    v.x = b0 ? (Real)-1 : (Real)1;
-    v.y = 0;
+    v.x = b0 ? -1.0 : 1.0;
+    v.y = 0.0;
   }
   if (conj) v.y = -v.y;
   return v;
 }
 
 template <class Real>
-__device__ __forceinline__ typename Cx<Real>::T leaf_value(uint32_t w, uint32_t z, const double* tr) {
+__device__ __forceinline__ double2 leaf_value(uint32_t w, uint32_t z, const double* tr) {
   return leaf_value_bits<Real>(w, leaf_bit0(w, z), leaf_bit1(w, z), tr);
 }
 
+// Product of Real-exact leaf values, accumulated without rounding error worth
+// speaking of and rounded to Real once.  complex128: FP64 products.
+// complex64: FP64 arithmetic is scarce on this GPU (a small fraction of the
+// FP32 rate), so the running product is kept as an unevaluated sum of two
+// floats per component (hi + lo, about 48 significant bits) and each leaf,
+// an exact float, is multiplied in with error-free transformations on the
+// FP32 pipes (the product's rounding error from an FMA, the sum's from the
+// two-sum identity).
+template <class Real> struct LeafAcc;
+template <> struct LeafAcc<double> {
+  double2 v = make_double2(1.0, 0.0);
+  __device__ __forceinline__ void mul(double2 l) { v = cmul<double>(v, l); }
+  __device__ __forceinline__ double2 rounded() const { return v; }
+};
+__device__ __forceinline__ void two_prod(float a, float b, float* p, float* e) {
+  *p = a * b;
+  *e = fmaf(a, b, -*p);
+}
+__device__ __forceinline__ void two_sum(float a, float b, float* s, float* e) {
+  *s = a + b;
+  const float bb = *s - a;
+  *e = (a - (*s - bb)) + (b - bb);
+}
+template <> struct LeafAcc<float> {
+  float rh = 1.f, rl = 0.f, ih = 0.f, il = 0.f;  // re = rh + rl, im = ih + il
+  __device__ __forceinline__ void mul(double2 l) {
+    const float lr = (float)l.x, li = (float)l.y;  // exact: leaves are stored as floats
+    float p1, e1, p2, e2, p3, e3, p4, e4;
+    two_prod(rh, lr, &p1, &e1);
+    two_prod(ih, li, &p2, &e2);
+    two_prod(rh, li, &p3, &e3);
+    two_prod(ih, lr, &p4, &e4);
+    float s, t;
+    two_sum(p1, -p2, &s, &t);  // re = rh lr - ih li + (lo parts)
+    t += (e1 - e2) + (rl * lr - il * li);
+    const float nrh = s + t, nrl = t - (nrh - s);
+    two_sum(p3, p4, &s, &t);   // im = rh li + ih lr + (lo parts)
+    t += (e3 + e4) + (rl * li + il * lr);
+    const float nih = s + t, nil = t - (nih - s);
+    rh = nrh;
+    rl = nrl;
+    ih = nih;
+    il = nil;
+  }
+  // hi is the float nearest to hi + lo (each update renormalises the pair)
+  __device__ __forceinline__ float2 rounded() const { return make_float2(rh, ih); }
+};
+
 // Leaf factors for up to LeafTabB<Real> angle sets: one block per factor.
 // Each leaf takes at most 4 values (its two slot bits) per angle set; the
-// block tabulates them in 32 KB of shared memory once, then every element of
-// the factor is the product, in leaf order, of one table entry per leaf --
-// the same values multiplied in the same order as leaf_factor_kernel.
+// block tabulates them in 32 KB of shared memory once (the stored values are
+// Real-exact, so the table holds them in Real), then every element of the
+// factor is the product, in leaf order, of one table entry per leaf
+// (LeafAcc: rounded to Real once) -- the same values multiplied in the same
+// order as leaf_factor_kernel.
 template <class Real> struct LeafTabB { static constexpr int value = 32768 / (kDevMaxLeaves * 4 * 2 * (int)sizeof(Real)); };
+
+template <class Real>
+__device__ __forceinline__ typename Cx<Real>::T to_real(double2 v) {
+  typename Cx<Real>::T r;
+  r.x = (Real)v.x;
+  r.y = (Real)v.y;
+  return r;
+}
 
 template <class Real>
 __global__ void leaf_factor_tab_kernel(const DevLeafFactor* __restrict__ lf, int32_t n_lf,
@@ -95,7 +233,8 @@ __global__ void leaf_factor_tab_kernel(const DevLeafFactor* __restrict__ lf, int
       // a fixed slot reads its fixed value whatever the combination says
       const uint32_t b0 = (w >> 15) & 1u ? (w >> 16) & 1u : (uint32_t)(c & 1);
       const uint32_t b1 = (w >> 17) & 1u ? (w >> 18) & 1u : (uint32_t)(c >> 1);
-      tab[l][c][b] = leaf_value_bits<Real>(w, b0, b1, trig + ((int64_t)b * p + (layer > 0 ? layer - 1 : 0)) * 4);
+      tab[l][c][b] = to_real<Real>(
+          leaf_value_bits<Real>(w, b0, b1, trig + ((int64_t)b * p + (layer > 0 ? layer - 1 : 0)) * kTrigStride));
     }
     if (threadIdx.x < nl) words[threadIdx.x] = F.leaf[threadIdx.x];
     __syncthreads();
@@ -103,15 +242,14 @@ __global__ void leaf_factor_tab_kernel(const DevLeafFactor* __restrict__ lf, int
     for (int32_t idx = threadIdx.x; idx < n; idx += blockDim.x) {
       const uint32_t z = idx / B;
       const int32_t b = idx - (int32_t)z * B;
-      C acc;
-      acc.x = 1;
-      acc.y = 0;
+      LeafAcc<Real> acc;
       for (int32_t l = 0; l < nl; ++l) {
         const uint32_t w = words[l];
         const uint32_t c = ((z >> ((w >> 5) & 31u)) & 1u) | (((z >> ((w >> 10) & 31u)) & 1u) << 1);
-        acc = cmul<Real>(acc, tab[l][c][b]);
+        const C t = tab[l][c][b];
+        acc.mul(make_double2((double)t.x, (double)t.y));
       }
-      reinterpret_cast<C*>(data)[F.off + idx] = acc;
+      reinterpret_cast<C*>(data)[F.off + idx] = acc.rounded();
     }
   }
 }
@@ -127,16 +265,14 @@ __global__ void leaf_factor_kernel(const DevLeafFactor* __restrict__ lf, int32_t
     for (int32_t idx = threadIdx.x; idx < n; idx += blockDim.x) {
       const uint32_t z = idx / B;
       const int32_t b = idx - (int32_t)z * B;
-      C acc;
-      acc.x = 1;
-      acc.y = 0;
+      LeafAcc<Real> acc;
       for (int32_t l = 0; l < F.n_leaves; ++l) {
         const uint32_t w = F.leaf[l];
         const int32_t layer = leaf_layer(w);
-        const double* tr = trig + ((int64_t)b * p + (layer > 0 ? layer - 1 : 0)) * 4;
-        acc = cmul<Real>(acc, leaf_value<Real>(w, z, tr));
+        const double* tr = trig + ((int64_t)b * p + (layer > 0 ? layer - 1 : 0)) * kTrigStride;
+        acc.mul(leaf_value<Real>(w, z, tr));
       }
-      reinterpret_cast<C*>(data)[F.off + idx] = acc;
+      reinterpret_cast<C*>(data)[F.off + idx] = acc.rounded();
     }
   }
 }
@@ -193,31 +329,19 @@ __device__ __forceinline__ int32_t ld_acquire(const int32_t* p) {
 // Consecutive tiles of one bucket on a warp reuse its record and skip the
 // wait (done counters only grow).
 //
-// STAGE: 0 generic register path; 1 forward steps of row-wide tiles move
-// their intermediate operands through a per-warp bulk-copy ring in dynamic
-// shared memory (kRingBytesPerWarp per warp, see kernels.cuh; the plan's
-// load_path 1); 2 row-wide plans on the register path: every forward tile
-// takes tile_rows_regs and the generic forward tile is not compiled in.
+// STAGE: 0 generic register path; 2 row-wide and one-angle-set plans on the
+// lean register tiles: every forward tile takes tile_rows_regs or
+// tile_pairs_regs and the generic forward tile is not compiled in.
 template <class Real, int VB, bool PAIR, bool GRAD, int STAGE>
-__global__ void __launch_bounds__(256, STAGE == 1 ? 2 : 4) persistent_kernel(const DevBucket* __restrict__ buckets,
+__global__ void __launch_bounds__(256, 4) persistent_kernel(const DevBucket* __restrict__ buckets,
                                                             const DevTask* __restrict__ tasks, int32_t n_tasks,
                                                             DevCtrl* ctrl, int32_t* done, Real* __restrict__ data,
                                                             const TileGeom g, int32_t spin_limit,
                                                             const int32_t* __restrict__ deps,
                                                             unsigned long long* __restrict__ trace) {
   __shared__ WarpTile tiles[8];
-  extern __shared__ uint4 ring_all[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   WarpTile* w = &tiles[wid];
-  uint4* ring = STAGE == 1 ? ring_all + (size_t)wid * (kRingBytesPerWarp / 16) : nullptr;
-  uint32_t phase = 0;  // bulk-copy ring: parity each slot waits for next
-  if (STAGE == 1) {
-    if (lane == 0) {
-      for (int k = 0; k < kBulkSlots; ++k) mbar_init(&w->mbar[k], 1);
-      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncwarp();
-  }
   // Lane 0 claims tasks (the warp acts on broadcasts); the lanes poll a
   // step's dependency list side by side.
   int32_t t = 0, cached = -1;  // cached: bucket whose record and lane parts are in *w
@@ -280,7 +404,7 @@ __global__ void __launch_bounds__(256, STAGE == 1 ? 2 : 4) persistent_kernel(con
         const int64_t r0 = tt * g.R;
         if (r0 >= n_rows) break;
         const int64_t r1 = r0 + g.R < n_rows ? r0 + g.R : n_rows;
-        warp_tile<Real, VB, PAIR, true, GRAD, STAGE>(w, data, g, r0, r1, lane, ctrl, b, ring, &phase);
+        warp_tile<Real, VB, PAIR, true, GRAD, STAGE>(w, data, g, r0, r1, lane, ctrl, b);
         __syncwarp();  // the next tile or step reuses the warp's tables and reads what this one wrote
       }
     }
@@ -300,16 +424,19 @@ __global__ void __launch_bounds__(256, STAGE == 1 ? 2 : 4) persistent_kernel(con
 
 // Final step (§QAOA algorithm, E = sum_k E_k): per angle set, the value of
 // each edge network is the product of its scalar bucket results, taken in
-// FP64, and E = sum_e (1 - Re <Z_j Z_k>_e) / 2 in a fixed order.  One warp per
-// angle set: lane l sums the edges l, l + 32, ... in order, then a fixed
-// butterfly adds the 32 partial sums.
+// FP64 and divided by the network's stored-gate norm product (complex64:
+// exp(network_log_r); 1 for complex128), and E = sum_e (1 - Re <Z_j Z_k>_e)
+// / 2 in a fixed order.  One warp per angle set: lane l sums the edges l,
+// l + 32, ... in order, then a fixed butterfly adds the 32 partial sums.
 template <class Real>
 __global__ void energy_kernel(const Real* __restrict__ data, const int64_t* __restrict__ scal_off,
                               const int32_t* __restrict__ scal_begin, const int32_t* __restrict__ net_first,
+                              const int32_t* __restrict__ counts, const double* __restrict__ trig, int32_t p,
                               int32_t n_edges, int32_t B, double* __restrict__ energy, double* __restrict__ edge_zz) {
   const int32_t b = (int32_t)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (b >= B) return;  // whole warps leave together
+  const double lr_plus = log_r_plus<Real>();
   double E = 0.0;
   for (int32_t e = lane; e < n_edges; e += 32) {
     // <Z_j Z_k> = sum over the edge's networks (2^s slices) of the product of
@@ -323,6 +450,11 @@ __global__ void energy_kernel(const Real* __restrict__ data, const int64_t* __re
         const double tr = nr * vr - ni * vi;
         ni = nr * vi + ni * vr;
         nr = tr;
+      }
+      if (sizeof(Real) != sizeof(double)) {
+        const double corr = exp(-network_log_r(counts, k, b, p, trig, lr_plus));
+        nr *= corr;
+        ni *= corr;
       }
       zr += nr;
       zi += ni;
@@ -365,10 +497,14 @@ __device__ __forceinline__ double2 leaf_deriv(uint32_t w, uint32_t z, const doub
 // leaves before l) and a suffix pass (the leaves after l), so a z costs
 // O(n_leaves) instead of O(n_leaves^2); each leaf's sum is reduced over the
 // warp with shuffles.
+//
+// The parts are divided by the factor's network's stored-gate norm product
+// (complex64, see trig_kernel): to first order that is the derivative of the
+// exact network at the stored angles.
 template <class Real>
 __global__ void leafgrad_kernel(const DevLeafFactor* __restrict__ lf, int32_t n_lf, int64_t lbar_shift,
-                                const double* __restrict__ trig, int32_t p, int32_t B,
-                                const Real* __restrict__ data, double2* __restrict__ part) {
+                                const double* __restrict__ trig, const int32_t* __restrict__ counts, int32_t p,
+                                int32_t B, const Real* __restrict__ data, double2* __restrict__ part) {
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= (int64_t)n_lf * B) return;
@@ -383,7 +519,7 @@ __global__ void leafgrad_kernel(const DevLeafFactor* __restrict__ lf, int32_t n_
     for (int32_t l = 0; l < n; ++l) {  // prefix: Lbar times the leaves before l
       const uint32_t w = F.leaf[l];
       const int32_t layer = leaf_layer(w);
-      val[l] = leaf_value<double>(w, z, trig + ((int64_t)b * p + (layer > 0 ? layer - 1 : 0)) * 4);
+      val[l] = leaf_value<Real>(w, z, trig + ((int64_t)b * p + (layer > 0 ? layer - 1 : 0)) * kTrigStride);
       pre[l] = run;
       run = cmul<double>(run, val[l]);
     }
@@ -392,7 +528,7 @@ __global__ void leafgrad_kernel(const DevLeafFactor* __restrict__ lf, int32_t n_
       const uint32_t w = F.leaf[l];
       const uint32_t kind = w & 3u;
       if (kind == 1u || kind == 2u) {
-        const double2 d = leaf_deriv(w, z, trig + ((int64_t)b * p + leaf_layer(w) - 1) * 4);
+        const double2 d = leaf_deriv(w, z, trig + ((int64_t)b * p + leaf_layer(w) - 1) * kTrigStride);
         const double2 t = cmul<double>(cmul<double>(pre[l], d), suf);
         acc[l].x += t.x;
         acc[l].y += t.y;
@@ -405,9 +541,11 @@ __global__ void leafgrad_kernel(const DevLeafFactor* __restrict__ lf, int32_t n_
       acc[l].x += __shfl_xor_sync(0xffffffffu, acc[l].x, off);
       acc[l].y += __shfl_xor_sync(0xffffffffu, acc[l].y, off);
     }
+  const double corr = sizeof(Real) == sizeof(double) ? 1.0
+                                                     : exp(-network_log_r(counts, F.net, b, p, trig, log_r_plus<Real>()));
   if (lane == 0)
     for (int32_t l = 0; l < kDevMaxLeaves; ++l)
-      part[warp * kDevMaxLeaves + l] = l < n ? acc[l] : make_double2(0.0, 0.0);
+      part[warp * kDevMaxLeaves + l] = l < n ? make_double2(acc[l].x * corr, acc[l].y * corr) : make_double2(0.0, 0.0);
 }
 
 // dZ_e/dtheta for every edge e, angle set b and angle theta (0..p-1: gamma,
@@ -452,10 +590,13 @@ __global__ void gradreduce_kernel(const double* __restrict__ dz, int32_t n_edges
 
 // ------------------------------------------------------------- launchers ---
 
-cudaError_t launch_trig(const double* gamma, const double* beta, int32_t p, int32_t B, double* trig,
+cudaError_t launch_trig(int dtype, const double* gamma, const double* beta, int32_t p, int32_t B, double* trig,
                         cudaStream_t s) {
   const int32_t n = B * p;
-  dev::trig_kernel<<<(n + 127) / 128, 128, 0, s>>>(gamma, beta, p, B, trig);
+  if (dtype == QT_C64)
+    dev::trig_kernel<float><<<(n + 127) / 128, 128, 0, s>>>(gamma, beta, p, B, trig);
+  else
+    dev::trig_kernel<double><<<(n + 127) / 128, 128, 0, s>>>(gamma, beta, p, B, trig);
   return cudaGetLastError();
 }
 
@@ -530,10 +671,11 @@ cudaError_t launch_bucket(int dtype, const DevBucket& d, int32_t B, int32_t lane
   return cudaGetLastError();
 }
 
-// Staged kernels exist for row-wide tiles of 16-byte vectors: one row per
-// pass and one vector chunk per row (complex64 with even B in [34, 64],
-// complex128 with B in [17, 32]); other shapes keep the register path.
-bool staged_supported(int dtype, int32_t B) {
+// Row-wide tile shapes (one output row per pass, one vector chunk per row:
+// complex64 with even B in [34, 64], complex128 with B in [17, 32]) take the
+// lean row tile; one angle set takes the lean pair tile; other batches the
+// generic register tile.
+bool row_wide(int dtype, int32_t B) {
   if (B <= 1 || !(dtype == QT_C128 || vector_width(dtype, B) == 2)) return false;
   const TileGeom g = tile_geom(dtype, B, 0);
   return g.RP == 1 && g.VC == 1;
@@ -544,98 +686,66 @@ static const void* pk_fn() {
   return (const void*)dev::persistent_kernel<Real, VB, PAIR, GRAD, ST>;
 }
 
-template <bool GRAD, int ST>
-static const void* persistent_fn_t(int dtype, int32_t B) {
-  const int vb = vector_width(dtype, B);
-  const bool pair = (B == 1);
-  constexpr int PST = ST == 2 ? 2 : 0;  // one-angle-set plans: lean pair path or generic
-  if (dtype == QT_C64)
-    return pair ? pk_fn<float, 1, true, GRAD, PST>()
-                : (vb == 2 ? pk_fn<float, 2, false, GRAD, ST>() : pk_fn<float, 1, false, GRAD, 0>());
-  return pair ? pk_fn<double, 1, true, GRAD, PST>() : pk_fn<double, 1, false, GRAD, ST>();
-}
-
+// Kernel variant of a launch: the lean pair tile (one angle set), the lean
+// row tile (row-wide shapes), else the generic register tile.
 template <bool GRAD>
-static const void* persistent_fn_g(int dtype, int stage, int32_t B) {
-  if (stage == 1) return persistent_fn_t<GRAD, 1>(dtype, B);
-  if (stage == 2) return persistent_fn_t<GRAD, 2>(dtype, B);
-  return persistent_fn_t<GRAD, 0>(dtype, B);
+static const void* persistent_fn_g(int dtype, int32_t B) {
+  const bool pair = (B == 1);
+  const bool lean = pair || row_wide(dtype, B);
+  if (dtype == QT_C64) {
+    if (pair) return pk_fn<float, 1, true, GRAD, 2>();
+    if (vector_width(dtype, B) == 2) return lean ? pk_fn<float, 2, false, GRAD, 2>() : pk_fn<float, 2, false, GRAD, 0>();
+    return pk_fn<float, 1, false, GRAD, 0>();
+  }
+  if (pair) return pk_fn<double, 1, true, GRAD, 2>();
+  return lean ? pk_fn<double, 1, false, GRAD, 2>() : pk_fn<double, 1, false, GRAD, 0>();
 }
 
-// Kernel variant of a launch: the lean pair path for one angle set, the
-// staged ring (load path 1) or the lean row path for row-wide tile shapes,
-// else the generic register path.
-static int persistent_stage(int dtype, int32_t load_path, bool bulk_ok, int32_t B) {
-  if (B == 1) return 2;  // one angle set: the lean pair path
-  if (!staged_supported(dtype, B)) return 0;
-  return load_path != 0 && bulk_ok ? 1 : 2;
+static const void* persistent_fn(int dtype, bool grad, int32_t B) {
+  return grad ? persistent_fn_g<true>(dtype, B) : persistent_fn_g<false>(dtype, B);
 }
 
-static const void* persistent_fn(int dtype, bool grad, int stage, int32_t B) {
-  if (!staged_supported(dtype, B) && !(B == 1 && stage == 2)) stage = 0;
-  return grad ? persistent_fn_g<true>(dtype, stage, B) : persistent_fn_g<false>(dtype, stage, B);
-}
-
-// Dynamic shared memory of a persistent launch (the staged ring of 8 warps).
-static int persistent_smem(int dtype, int stage, int32_t B) {
-  return stage == 1 && staged_supported(dtype, B) ? 8 * dev::kRingBytesPerWarp : 0;
-}
-
-cudaError_t launch_persistent(int dtype, bool grad, int32_t load_path, bool bulk_ok, const DevBucket* buckets,
-                              const DevTask* tasks, int32_t n_tasks, DevCtrl* ctrl, int32_t* done, int32_t B,
-                              int32_t lane_items, void* data, int64_t data_elems, int32_t grid, int32_t spin_limit,
-                              const int32_t* deps, unsigned long long* trace, cudaStream_t s) {
+cudaError_t launch_persistent(int dtype, bool grad, const DevBucket* buckets, const DevTask* tasks, int32_t n_tasks,
+                              DevCtrl* ctrl, int32_t* done, int32_t B, int32_t lane_items, void* data,
+                              int64_t data_elems, int32_t grid, int32_t spin_limit, const int32_t* deps,
+                              unsigned long long* trace, cudaStream_t s) {
   TileGeom g = tile_geom(dtype, B, lane_items);
   g.data_elems = data_elems;
   g.wait_limit = 1 << 22;
-  const int stage = persistent_stage(dtype, load_path, bulk_ok, B);
-  const void* fn = persistent_fn(dtype, grad, stage, B);
-  const int smem = persistent_smem(dtype, stage, B);
-  if (smem > 0) {
-    const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-  }
+  const void* fn = persistent_fn(dtype, grad, B);
   void* args[] = {(void*)&buckets, (void*)&tasks, (void*)&n_tasks, (void*)&ctrl, (void*)&done, (void*)&data,
                   (void*)&g, (void*)&spin_limit, (void*)&deps, (void*)&trace};
-  return cudaLaunchKernel(fn, dim3(grid), dim3(256), args, (size_t)smem, s);
+  return cudaLaunchKernel(fn, dim3(grid), dim3(256), args, 0, s);
 }
 
-cudaError_t persistent_occupancy(int dtype, bool grad, int32_t load_path, bool bulk_ok, int32_t B,
-                                 int* blocks_per_sm) {
-  const int stage = persistent_stage(dtype, load_path, bulk_ok, B);
-  const void* fn = persistent_fn(dtype, grad, stage, B);
-  const int smem = persistent_smem(dtype, stage, B);
-  if (smem > 0) {
-    const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-  }
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, 256, (size_t)smem);
+cudaError_t persistent_occupancy(int dtype, bool grad, int32_t B, int* blocks_per_sm) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, persistent_fn(dtype, grad, B), 256, 0);
 }
 
 cudaError_t launch_energy(int dtype, const void* data, const int64_t* scal_off, const int32_t* scal_begin,
-                          const int32_t* net_first, int32_t n_edges, int32_t B, double* energy, double* edge_zz,
-                          cudaStream_t s) {
+                          const int32_t* net_first, const int32_t* counts, const double* trig, int32_t p,
+                          int32_t n_edges, int32_t B, double* energy, double* edge_zz, cudaStream_t s) {
   const int32_t grid = (B + 3) / 4;  // 4 warps (angle sets) per block
   if (dtype == QT_C64)
-    dev::energy_kernel<float><<<grid, 128, 0, s>>>((const float*)data, scal_off, scal_begin, net_first, n_edges, B,
-                                                   energy, edge_zz);
+    dev::energy_kernel<float><<<grid, 128, 0, s>>>((const float*)data, scal_off, scal_begin, net_first, counts, trig,
+                                                   p, n_edges, B, energy, edge_zz);
   else
-    dev::energy_kernel<double><<<grid, 128, 0, s>>>((const double*)data, scal_off, scal_begin, net_first, n_edges,
-                                                    B, energy, edge_zz);
+    dev::energy_kernel<double><<<grid, 128, 0, s>>>((const double*)data, scal_off, scal_begin, net_first, counts,
+                                                    trig, p, n_edges, B, energy, edge_zz);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gradient(int dtype, const DevLeafFactor* lf, int32_t n_lf, const int32_t* leaf_first,
-                            int32_t n_edges, int64_t lbar_shift, const double* trig, int32_t p, int32_t B,
-                            const void* data, double* part, double* dz, double* grad, cudaStream_t s) {
+                            int32_t n_edges, int64_t lbar_shift, const double* trig, const int32_t* counts, int32_t p,
+                            int32_t B, const void* data, double* part, double* dz, double* grad, cudaStream_t s) {
   const int64_t n1 = (int64_t)n_lf * B;
   if (n1 > 0) {
     if (dtype == QT_C64)
-      dev::leafgrad_kernel<float><<<(int)((n1 * 32 + 127) / 128), 128, 0, s>>>(lf, n_lf, lbar_shift, trig, p, B,
-                                                                             (const float*)data, (double2*)part);
+      dev::leafgrad_kernel<float><<<(int)((n1 * 32 + 127) / 128), 128, 0, s>>>(
+          lf, n_lf, lbar_shift, trig, counts, p, B, (const float*)data, (double2*)part);
     else
-      dev::leafgrad_kernel<double><<<(int)((n1 * 32 + 127) / 128), 128, 0, s>>>(lf, n_lf, lbar_shift, trig, p, B,
-                                                                              (const double*)data, (double2*)part);
+      dev::leafgrad_kernel<double><<<(int)((n1 * 32 + 127) / 128), 128, 0, s>>>(
+          lf, n_lf, lbar_shift, trig, counts, p, B, (const double*)data, (double2*)part);
   }
   const int64_t n2 = (int64_t)n_edges * B * 2 * p;
   dev::edgegrad_kernel<<<(int)((n2 + 127) / 128), 128, 0, s>>>(lf, leaf_first, n_edges, p, B, (const double2*)part, dz);

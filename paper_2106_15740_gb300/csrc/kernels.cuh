@@ -167,7 +167,6 @@ __device__ __forceinline__ bool qt_in_range(DevCtrl* ctrl, int64_t lo, int64_t s
 
 // Per-warp shared state of one tile: the bucket record and the pass table
 // tab[i][p] = pext(r0 + p * RP, mask_i).
-constexpr int kBulkSlots = 8;  // mbarriers (ring slots) of a warp's bulk-copy ring
 
 struct WarpTile {
   DevBucket d;
@@ -175,7 +174,6 @@ struct WarpTile {
   uint32_t lpart[kDevMaxIn][32];  // pext(i_lane, mask) per input and lane
   float redf[32][4];              // per-lane partial sums of a reduction step (complex64)
   double redd[32][2];             // the same for complex128
-  unsigned long long mbar[kBulkSlots];  // bulk-copy ring: one transaction barrier per slot
   unsigned long long trace_t[2];        // queue trace: claim and ready clock of the current task
 };
 
@@ -615,209 +613,6 @@ __device__ __forceinline__ void tile_adjoint_rows(WarpTile* w, Real* __restrict_
   }
 }
 
-// ------------------------------------------------ shared-memory staged path --
-//
-// The register path above keeps at most 2 rows' loads of one input in flight
-// per lane and waits on each input in turn.  The staged path (plan option
-// load_path 1) applies to row-wide tiles (RP = 1, VC = 1: B >= 17 angle-set
-// vectors, each lane one vector of the same row) and moves the intermediate
-// operand rows through a per-warp ring in shared memory (kRingBytesPerWarp
-// bytes of dynamic shared memory per warp), several rows ahead of the row
-// being multiplied.
-constexpr int kRingBytesPerWarp = 8192;
-
-// Tile shapes with a staged form: 16-byte vectors of angle sets.
-template <class Real, int VB> struct Stageable { static constexpr bool value = false; };
-template <> struct Stageable<float, 2> { static constexpr bool value = true; };
-template <> struct Stageable<double, 1> { static constexpr bool value = true; };
-
-// ------------------------------------------------ wide-row bulk-copy path --
-//
-// For row-wide tiles (RP = 1: one output row per pass, B >= 17 vectors, so
-// every lane of the warp works on the same row y) all operand addresses of a
-// row are warp-uniform: input i needs rows 2k and 2k + 1 (x = 0, 1) of its
-// [2^r][B] array, k = tab[i][y - r0], which are 2 * B contiguous complex
-// numbers.  Lane 0 brings that pair into a ring slot of shared memory with
-// one cp.async.bulk (the TMA engine's 1-D copy) per input, completing on the
-// slot's mbarrier; all lanes wait on the barrier's phase, read their vectors
-// of angle sets from shared memory, multiply, add over x and store the
-// output row.  A slot holds one row's operands (n_in * 2 * B * sizeof(cx));
-// with S slots, S - 1 rows are in flight while one is multiplied.  A slot is
-// refilled only after every lane has read it into registers (__syncwarp).
-// The ring's phases persist across tiles in `phase` (bit s = parity that
-// slot s waits for next); every fill issued in a tile is consumed in it.
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(unsigned long long* mb, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mb)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* mb, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mb)), "r"(bytes) : "memory");
-}
-// One bounded wait for the phase with parity `parity` of *mb; false if it
-// did not complete within `limit` probes.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* mb, uint32_t parity, int32_t limit) {
-  const uint32_t a = smem_u32(mb);
-  for (int32_t it = 0; it < limit; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-// Global -> shared bulk copy of `bytes` (multiple of 16; both addresses
-// 16-byte aligned) completing `bytes` transactions on *mb.
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, unsigned long long* mb) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(mb))
-      : "memory");
-}
-
-// Leaf handling shared by the row-wide staged tiles.  A bucket's leaf
-// factor (at most one input) is small and its row changes slowly with y:
-// over the R rows of a tile it takes 2^m values, m = number of its mask bits
-// below log2(R), and for m = 1 those are rows k0 and k0 + 1 (pext keeps the
-// order of the bits), k0 = pext(r0).  With m <= 1 every lane keeps its vector
-// of both leaf rows (x = 0, 1) in registers for the whole tile.  Returns
-// false when the bucket has several leaf inputs or m > 1.
-__device__ __forceinline__ bool row_leaf(const DevBucket& d, const TileGeom& g, int* il, int* n_int,
-                                         uint32_t* leaf_bit) {
-  *il = -1;
-  *n_int = 0;
-  *leaf_bit = 0;
-  for (int i = 0; i < d.n_in; ++i) {
-    if (d.in[i].flags & kInLeaf) {
-      if (*il >= 0) return false;
-      *il = i;
-    } else {
-      ++*n_int;
-    }
-  }
-  if (*il >= 0) {
-    const uint32_t lm = d.in[*il].mask & ((uint32_t)g.R - 1u);  // r0 is a multiple of R
-    if (lm & (lm - 1u)) return false;
-    *leaf_bit = lm;
-  }
-  return true;
-}
-
-template <class Real, int VB>
-__device__ __forceinline__ void row_leaf_load(const WarpTile* w, const Real* __restrict__ data, const TileGeom& g,
-                                              int il, uint32_t leaf_bit, int vv, Pack<Real, VB> (&lf)[2][2]) {
-  if (il < 0) return;
-  const DevBucket& d = w->d;
-  const uint32_t k0 = w->tab[il][0];
-#pragma unroll
-  for (int j = 0; j < 2; ++j) {
-    if (j == 1 && leaf_bit == 0) continue;
-    const int64_t e0 = d.in[il].off + (int64_t)(2 * (k0 + (uint32_t)j)) * g.B + (int64_t)vv * VB;
-    lf[j][0] = ldv<Real, VB, false>(data, e0);
-    lf[j][1] = ldv<Real, VB, false>(data, e0 + g.B);
-  }
-}
-
-// Wide-row forward tile (RP = 1, VC = 1) through the bulk-copy ring
-// (kRingBytesPerWarp bytes of this warp at `ring`): lane 0 brings each
-// intermediate's row pair of a row into the row's slot with one
-// cp.async.bulk, completing on the slot's mbarrier; the leaf stays in
-// registers (row_leaf).  Products in input order: bit-identical to the
-// register path.  Returns false (nothing done) when the shape does not fit.
-template <class Real, int VB>
-__device__ __forceinline__ bool tile_rows_bulk(WarpTile* w, unsigned char* ring, uint32_t& phase,
-                                               Real* __restrict__ data, const TileGeom& g, int64_t r0, int64_t r1,
-                                               int lane, DevCtrl* ctrl, int32_t wait_limit) {
-  using C = typename Cx<Real>::T;
-  using PK = Pack<Real, VB>;
-  const DevBucket& d = w->d;
-  const int n_in = d.n_in;
-  int il, n_int;
-  uint32_t leaf_bit;
-  if (!row_leaf(d, g, &il, &n_int, &leaf_bit)) return false;
-  const uint32_t rowb = (uint32_t)g.B * (uint32_t)sizeof(C);  // bytes of one row of B complex numbers
-  const uint32_t pairb = 2u * rowb;
-  const uint32_t slotb = (uint32_t)(n_int > 0 ? n_int : 1) * pairb;
-  int S = (int)((uint32_t)kRingBytesPerWarp / slotb);
-  if (S > kBulkSlots) S = kBulkSlots;
-  if (S < 2) return false;
-  const int nrows = (int)(r1 - r0);
-  const int vv = lane < g.Bv ? lane : 0;  // idle lanes compute vector 0 and do not store
-  PK lf[2][2];
-  row_leaf_load<Real, VB>(w, data, g, il, leaf_bit, vv, lf);
-  if (lane == 0 && n_int > 0) {
-    fence_proxy_async_smem();  // the previous tile's reads of the ring come first
-    for (int q = 0; q < S && q < nrows; ++q) {
-      unsigned long long* mb = &w->mbar[q];
-      unsigned char* dst = ring + (uint32_t)q * slotb;
-      mbar_expect_tx(mb, slotb);
-      for (int i = 0, j = 0; i < n_in; ++i) {
-        if (i == il) continue;
-        bulk_g2s(dst + (uint32_t)j * pairb, data + 2 * (d.in[i].off + (int64_t)(2 * w->tab[i][q]) * g.B), pairb, mb);
-        ++j;
-      }
-    }
-  }
-  const uint32_t lo = (uint32_t)vv * VB * (uint32_t)sizeof(C);
-  for (int q = 0; q < nrows; ++q) {
-    const int s = q % S;
-    if (n_int > 0) {
-      if (!mbar_wait(&w->mbar[s], (phase >> s) & 1u, wait_limit)) {
-        if (lane == 0) atomicCAS(&ctrl->status, 0, (int32_t)QT_ETIMEOUT);
-      }
-      phase ^= 1u << s;
-    }
-    const unsigned char* src = ring + (uint32_t)s * slotb + lo;
-    const int64_t y = r0 + q;
-    const bool hi = ((uint32_t)y & leaf_bit) != 0;
-    PK p0, p1;
-    for (int i = 0, j = 0; i < n_in; ++i) {
-      PK a0, a1;
-      if (i == il) {
-        a0 = hi ? lf[1][0] : lf[0][0];
-        a1 = hi ? lf[1][1] : lf[0][1];
-      } else {
-        a0 = *reinterpret_cast<const PK*>(src + (uint32_t)j * pairb);
-        a1 = *reinterpret_cast<const PK*>(src + (uint32_t)j * pairb + rowb);
-        ++j;
-      }
-      if (i == 0) {
-        p0 = a0;
-        p1 = a1;
-      } else {
-        pmul<Real, VB>(p0, a0);
-        pmul<Real, VB>(p1, a1);
-      }
-    }
-    if (lane < g.Bv) {
-      PK o;
-#pragma unroll
-      for (int v = 0; v < VB; ++v) o.c[v] = cadd<Real>(p0.c[v], p1.c[v]);
-      stv<Real, VB>(data, d.out_off + y * g.B + (int64_t)vv * VB, o);
-    }
-    __syncwarp();  // every lane has read slot s
-    if (lane == 0 && n_int > 0 && q + S < nrows) {
-      unsigned long long* mb = &w->mbar[s];
-      unsigned char* dst = ring + (uint32_t)s * slotb;
-      mbar_expect_tx(mb, slotb);
-      for (int i = 0, j = 0; i < n_in; ++i) {
-        if (i == il) continue;
-        bulk_g2s(dst + (uint32_t)j * pairb, data + 2 * (d.in[i].off + (int64_t)(2 * w->tab[i][q + S]) * g.B), pairb,
-                 mb);
-        ++j;
-      }
-    }
-  }
-  return true;
-}
-
-
 // Adjoint step (kStepAdj): for each item (row y, vector), the product of the
 // factors at x = 0 and x = 1 goes to the target rows (k_t << 1) | x,
 // k_t = pext(y, mask_t).
@@ -1029,8 +824,7 @@ __device__ __forceinline__ void tile_adjred(WarpTile* w, Real* __restrict__ data
 // w->lpart.  Per item an input row is one table read plus one add.
 template <class Real, int VB, bool PAIR, bool CG, bool GRAD = false, int STAGE = 0>
 __device__ __forceinline__ void warp_tile(WarpTile* w, Real* __restrict__ data, const TileGeom& g, int64_t r0,
-                                          int64_t r1, int lane, DevCtrl* ctrl = nullptr, int dbg_bucket = -1,
-                                          uint4* ring = nullptr, uint32_t* phase = nullptr) {
+                                          int64_t r1, int lane, DevCtrl* ctrl = nullptr, int dbg_bucket = -1) {
   const DevBucket& d = w->d;
   const int n_rec = d.kind == kStepAdj ? d.n_in + 1 : d.n_in;
   int rip, v0;
@@ -1052,15 +846,11 @@ __device__ __forceinline__ void warp_tile(WarpTile* w, Real* __restrict__ data, 
   }
   __syncwarp();
   if (!GRAD || d.kind == kStepFwd) {
-    // STAGE 1: row-wide tiles through the bulk-copy ring (the register path
-    // for buckets the ring cannot hold); STAGE 2: every forward tile of a
-    // row-wide or one-angle-set plan on the lean row / pair path (the launcher
-    // picks STAGE 2 only for those shapes; any other shape is reported, not
-    // computed); STAGE 0: the generic register path
+    // STAGE 2: every forward tile of a row-wide or one-angle-set plan on the
+    // lean row / pair path (the launcher picks STAGE 2 only for those
+    // shapes; any other shape is reported, not computed); STAGE 0: the
+    // generic register path
     bool done = false;
-    if (STAGE == 1 && !PAIR && Stageable<Real, VB>::value && g.RP == 1 && g.VC == 1)
-      done = tile_rows_bulk<Real, VB>(w, reinterpret_cast<unsigned char*>(ring), *phase, data, g, r0, r1, lane, ctrl,
-                                      g.wait_limit);
     if (STAGE == 2) {
       if (PAIR && g.RP == 32 && g.VC == 1)
         tile_pairs_regs<Real>(w, data, g, r0, r1, lane);

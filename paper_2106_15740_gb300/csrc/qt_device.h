@@ -98,8 +98,22 @@ struct DevLeafFactor {
   int64_t off;
   int32_t rank;
   int32_t n_leaves;
+  int32_t net;                 // network the factor belongs to (its leaf-count row)
+  int32_t pad;
   uint32_t leaf[kDevMaxLeaves];
 };
+
+// Angle table: per angle set b and layer q, kTrigStride doubles at
+// trig[(b * p + q) * kTrigStride]: cos g, sin g, cos b, sin b (the values the
+// leaves take), log r_g, log r_b (see trig_kernel: each stored gate is
+// r times the exact gate at a nearby angle; complex128 plans have r = 1).
+constexpr int kTrigStride = 6;
+
+// Leaf counts of network k: 2p + 1 int32 at counts[k * (2p + 1)]: ZZ leaves
+// of layers 1..p, mixer leaves of layers 1..p, |+> leaves (ket and bra
+// copies all counted).  A network built from stored gates r x exact gate is
+// prod r^count times the exact network: energy_kernel and leafgrad_kernel
+// divide that product out in FP64.
 
 // Persistent-queue task.  chunk >= 0: chunk `chunk` of step `bucket`, its
 // warp tiles [chunk * span, (chunk + 1) * span).  chunk < 0: a group of

@@ -15,7 +15,6 @@ from . import binding as qb
 DTYPES = {"c128": qb.QT_C128, "c64": qb.QT_C64}
 MODES = {"per_bucket": qb.QT_MODE_PER_BUCKET, "persistent": qb.QT_MODE_PERSISTENT}
 QUEUE_ORDERS = {"round_robin": 0, "critical_path": 1}
-LOAD_PATHS = {"registers": 0, "staged": 1}
 
 
 def _stream_handle(device):
@@ -33,8 +32,8 @@ class EnergyPlan:
     def __init__(self, n_vertices, edges, p, batch=1, dtype="c128", mode="persistent",
                  max_workspace=0, max_width=0, device="cuda:0", gradient=False, lane_items=0,
                  group_rows=0, edge_range=None, slice=False, chunk_tiles=0, order_trials=0, order_seed=0,
-                 order_tau=1.0, load_path="registers", checkpoint_bytes=0, chain_steps=False,
-                 queue_order="critical_path"):
+                 order_tau=1.0, checkpoint_bytes=0, chain_steps=False,
+                 queue_order="critical_path", chunk_tiles_by_rank=None):
         self.n_vertices, self.p, self.batch = int(n_vertices), int(p), int(batch)
         self.edges = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
         self.device = torch.device(device)
@@ -43,9 +42,9 @@ class EnergyPlan:
                             max_width=max_width, gradient=gradient, lane_items=lane_items,
                             group_rows=group_rows, edge_range=self.edge_range, slice=slice,
                             chunk_tiles=chunk_tiles, order_trials=order_trials, order_seed=order_seed,
-                            order_tau=order_tau, load_path=load_path,
+                            order_tau=order_tau,
                             checkpoint_bytes=checkpoint_bytes, chain_steps=chain_steps,
-                            queue_order=queue_order)
+                            queue_order=queue_order, chunk_tiles_by_rank=chunk_tiles_by_rank)
         opt = qb.qt_plan_options_default()
         opt.batch = self.batch
         opt.dtype = DTYPES[dtype]
@@ -61,10 +60,11 @@ class EnergyPlan:
         opt.order_trials = int(order_trials)
         opt.order_seed = int(order_seed)
         opt.order_tau = float(order_tau)
-        opt.load_path = LOAD_PATHS[load_path]
         opt.checkpoint_bytes = int(checkpoint_bytes)
         opt.chain_steps = int(bool(chain_steps))
         opt.queue_order = QUEUE_ORDERS[queue_order]
+        for r, t in (chunk_tiles_by_rank or {}).items():  # {output rank: warp tiles per queue task}
+            opt.chunk_tiles_by_rank[int(r)] = int(t)
         self.plan = qb.qt_plan_create(self.n_vertices, self.edges, self.p, opt)
         self.ws_bytes = qb.qt_plan_workspace_size(self.plan)
         self.stats = qb.qt_plan_stats(self.plan)
@@ -229,7 +229,7 @@ def autotune(n_vertices, edges, p, batch=1, dtype="c64", gradient=False, device=
     timing each candidate on the device (CUDA events around `reps` calls after
     two warm-ups).  Returns (best_options, {candidate: ms}).  Angles default
     to zeros (the work does not depend on their values).  Further keyword
-    arguments (order_trials, load_path, ...) go to every candidate plan."""
+    arguments (order_trials, chain_steps, ...) go to every candidate plan."""
     device = torch.device(device)
     if lane_items is None:
         lane_items = (16, 32, 64) if batch >= 16 else (8, 16, 32)
@@ -257,6 +257,64 @@ def autotune(n_vertices, edges, p, batch=1, dtype="c64", gradient=False, device=
             torch.cuda.empty_cache()
     li, gr = min(timings, key=timings.get)
     return dict(lane_items=li, group_rows=gr), timings
+
+
+WIDTH_BANDS = ((18, 31), (14, 17), (0, 13))
+
+
+def autotune_bands(n_vertices, edges, p, batch=1, dtype="c64", gradient=False, device="cuda:0", reps=3,
+                   spans=(1, 2, 4), bands=WIDTH_BANDS, gamma=None, beta=None, **plan_options):
+    """Per-width schedule: for each band of output ranks, the number of warp
+    tiles one queue task takes (``chunk_tiles_by_rank``), picked by timing on
+    the device with the other plan options fixed.  Bands are tuned one after
+    another (the widest first, where most bytes move), each keeping the best
+    choice of those before it; span 1 everywhere (the plan default) is the
+    first candidate, so the result is never slower than it as timed.
+    Returns ({rank: tiles}, {band: {"tiles_per_task": span, "ms_per_candidate": {span: ms}}})."""
+    device = torch.device(device)
+    g = torch.zeros((batch, p), dtype=torch.float64, device=device) if gamma is None else gamma
+    b = torch.zeros((batch, p), dtype=torch.float64, device=device) if beta is None else beta
+
+    def time_choice(choice):
+        plan = EnergyPlan(n_vertices, edges, p, batch=batch, dtype=dtype, mode="persistent", gradient=gradient,
+                          device=device, chunk_tiles_by_rank=choice, **plan_options)
+        for _ in range(2):
+            plan.energy(g, b, grad=gradient)
+        plan.check()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for _ in range(reps):
+            plan.energy(g, b, grad=gradient)
+        t1.record()
+        torch.cuda.synchronize(device)
+        plan.check()
+        ms = t0.elapsed_time(t1) / reps
+        plan.close()
+        del plan
+        torch.cuda.empty_cache()
+        return ms
+
+    choice = {}
+    timings = {}
+    base = time_choice({})
+    for lo, hi in bands:
+        band = f"rank {lo}-{hi}"
+        timings[band] = {1: base}
+        best_span, best_ms = 1, base
+        for sp in spans:
+            if sp == 1:
+                continue
+            trial = dict(choice)
+            trial.update({r: sp for r in range(lo, hi + 1)})
+            ms = time_choice(trial)
+            timings[band][sp] = ms
+            if ms < best_ms:
+                best_span, best_ms = sp, ms
+        if best_span != 1:
+            choice.update({r: best_span for r in range(lo, hi + 1)})
+        base = best_ms
+        timings[band] = {"tiles_per_task": best_span, "ms_per_candidate": timings[band]}
+    return choice, timings
 
 
 def contract_edge(n_vertices, edges, p, gamma, beta, edge, dtype="c128", device="cuda:0"):

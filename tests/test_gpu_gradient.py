@@ -7,8 +7,10 @@ of the complex128 GPU energy for the whole 60-vertex p = 4 graph.
 
 Tolerances: complex128 1e-9 absolute against the exact gradient (rounding of
 a few thousand FP64 products and sums); against finite differences the FD
-truncation error O(h^2 |E'''|) ~ 1e-8 dominates.  complex64: 2e-5 per unit of
-gradient scale (FP32 rounding, about 100 bucket steps of 2^-24 each).
+truncation error O(h^2 |E'''|) ~ 1e-8 dominates.  complex64: 1e-5 per unit of
+gradient scale (FP32 rounding, about 100 bucket steps of 2^-24 each; the
+stored gates' norm is divided out per network).  Energies: 1e-9 (complex128)
+and 1e-5 (complex64) for the whole graph.
 """
 import numpy as np
 import pytest
@@ -54,9 +56,9 @@ def test_gradient_matches_parameter_shift(dtype, n, p, B, seed):
         dg, db = gr.param_shift_gradient(n, edges, g[k], b[k])
         ref = np.concatenate([dg, db])
         scale = max(1.0, np.abs(ref).max())
-        tol = 1e-9 if dtype == "c128" else 2e-5 * scale
+        tol = 1e-9 if dtype == "c128" else 1e-5 * scale
         np.testing.assert_allclose(grad[k], ref, atol=tol, rtol=0)
-        assert abs(e[k] - sv.energy(n, edges, g[k], b[k])) <= (1e-10 if dtype == "c128" else 1e-5) * len(edges)
+        assert abs(e[k] - sv.energy(n, edges, g[k], b[k])) <= (1e-9 if dtype == "c128" else 1e-5)
 
 
 def test_gradient_plan_energy_equals_forward_plan():
@@ -105,7 +107,7 @@ def test_n60_p4_full_graph_vs_gpu_finite_differences(dtype):
 
     dg, db = gr.fd_gradient(energy, g[0], b[0], h=h)
     ref = np.concatenate([dg, db])
-    tol = 1e-7 if dtype == "c128" else 2e-5 * max(1.0, np.abs(ref).max())
+    tol = 1e-7 if dtype == "c128" else 1e-5 * max(1.0, np.abs(ref).max())
     np.testing.assert_allclose(grad[0], ref, atol=tol, rtol=0)
 
 
@@ -137,7 +139,7 @@ def test_autograd_function_matches_parameter_shift():
         dg, db = gr.param_shift_gradient(n, edges, g[k], b[k])
         np.testing.assert_allclose(gd.grad[k].cpu().numpy(), w[k].item() * dg, atol=1e-9, rtol=0)
         np.testing.assert_allclose(bd.grad[k].cpu().numpy(), w[k].item() * db, atol=1e-9, rtol=0)
-        assert abs(e[k].item() - sv.energy(n, edges, g[k], b[k])) < 1e-10 * len(edges)
+        assert abs(e[k].item() - sv.energy(n, edges, g[k], b[k])) < 1e-9
 
 
 def test_autograd_function_without_gradient_plan():
@@ -148,7 +150,7 @@ def test_autograd_function_without_gradient_plan():
     n, edges, p, g, b = workload("n16_p1")
     plan = EnergyPlan(n, edges, p, batch=1, dtype="c128", mode="persistent", device="cuda:0")
     e = qaoa_energy(plan, torch.tensor(g, device="cuda:0"), torch.tensor(b, device="cuda:0"))
-    assert abs(e.item() - sv.energy(n, edges, g[0], b[0])) < 1e-10 * len(edges)
+    assert abs(e.item() - sv.energy(n, edges, g[0], b[0])) < 1e-9
     with pytest.raises(qb.QTError) as ei:
         qaoa_energy(plan, torch.tensor(g, device="cuda:0", requires_grad=True), torch.tensor(b, device="cuda:0"))
     assert ei.value.status == qb.QT_ESTATE
@@ -163,7 +165,7 @@ def test_gradient_with_searched_orders_matches_parameter_shift(dtype):
     e, grad = _run(plan, g, b)
     for k in range(B):
         ref = np.concatenate(gr.param_shift_gradient(n, edges, g[k], b[k]))
-        tol = 1e-9 if dtype == "c128" else 2e-5 * max(1.0, np.abs(ref).max())
+        tol = 1e-9 if dtype == "c128" else 1e-5 * max(1.0, np.abs(ref).max())
         np.testing.assert_allclose(grad[k], ref, atol=tol, rtol=0)
 
 
@@ -184,11 +186,11 @@ def test_checkpointed_gradient_matches_full_sweep_and_parameter_shift(dtype, bud
     e1, g1 = _run(plan, g, b)
     plan.close()
     tol = 1e-12 if dtype == "c128" else 1e-5
-    np.testing.assert_allclose(e1, e0, atol=tol * len(edges), rtol=0)
+    np.testing.assert_allclose(e1, e0, atol=1e-10 if dtype == "c128" else 1e-5, rtol=0)
     np.testing.assert_allclose(g1, g0, atol=tol * max(1.0, np.abs(g0).max()), rtol=0)
     for k in range(B):
         ref = np.concatenate(gr.param_shift_gradient(n, edges, g[k], b[k]))
-        np.testing.assert_allclose(g1[k], ref, atol=1e-9 if dtype == "c128" else 2e-5 * max(1.0, np.abs(ref).max()),
+        np.testing.assert_allclose(g1[k], ref, atol=1e-9 if dtype == "c128" else 1e-5 * max(1.0, np.abs(ref).max()),
                                    rtol=0)
 
 
@@ -240,7 +242,7 @@ def test_tree_schedule_gradient_equals_chain(dtype, B, checkpoint, cap):
     k = B - 1
     ref = np.concatenate(gr.param_shift_gradient(n, edges, g[k], b[k]))
     np.testing.assert_allclose(out[False][0][1][k], ref,
-                               atol=1e-9 if dtype == "c128" else 2e-5 * max(1.0, np.abs(ref).max()), rtol=0)
+                               atol=1e-9 if dtype == "c128" else 1e-5 * max(1.0, np.abs(ref).max()), rtol=0)
 
 
 def test_n20_p2_gradient_vs_state_vector_differences():
@@ -256,7 +258,7 @@ def test_n20_p2_gradient_vs_state_vector_differences():
     plan = _grad_plan(n, edges, p, B, "c128")
     e, grad = _run(plan, g, b)
     plan.close()
-    assert abs(e[0] - sv.energy(n, edges, g[0], b[0])) <= 1e-10 * len(edges)
+    assert abs(e[0] - sv.energy(n, edges, g[0], b[0])) <= 1e-9
     dg, db = gr.fd_gradient(lambda gg, bb: sv.energy(n, edges, gg, bb), g[0], b[0])
     ref = np.concatenate([dg, db])
     np.testing.assert_allclose(grad[0], ref, atol=1e-7 * max(1.0, np.abs(ref).max()), rtol=0)

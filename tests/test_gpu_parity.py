@@ -2,7 +2,8 @@
 
 Tolerances (from the precision of each path): |d<Z_j Z_k>| <= 1e-10 for
 complex128 and <= 1e-5 for complex64 (FP32 products, one FP32 add per
-bucket, FP64 edge product and energy sum).
+bucket, FP64 edge product and energy sum); the whole graph's energy E to
+1e-9 (complex128) and 1e-5 (complex64).
 """
 import numpy as np
 import pytest
@@ -16,6 +17,7 @@ from workloads import complete_graph, erdos_renyi_graph, random_angles, random_r
 pytestmark = pytest.mark.gpu
 
 TOL = {"c128": 1e-10, "c64": 1e-5}
+TOL_E = {"c128": 1e-9, "c64": 1e-5}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -78,7 +80,7 @@ def test_n16_p1_all_edges_vs_statevector(mode, dtype):
         ref = sv.edge_zz(n, edges, g[k], b[k])
         np.testing.assert_allclose(zz[:, k, 0], ref, atol=TOL[dtype], rtol=0)
         np.testing.assert_allclose(zz[:, k, 1], 0, atol=TOL[dtype])
-        assert abs(e[k] - 0.5 * (len(edges) - ref.sum())) <= TOL[dtype] * len(edges)
+        assert abs(e[k] - 0.5 * (len(edges) - ref.sum())) <= TOL_E[dtype]
 
 
 @pytest.mark.parametrize("mode", ["per_bucket", "persistent"])
@@ -90,7 +92,7 @@ def test_n100_p3_all_edges_vs_oracle(mode, dtype):
     ref = _oracle_zz(n, edges, p, g[0], b[0])
     np.testing.assert_allclose(zz[:, 0, 0], ref.real, atol=TOL[dtype], rtol=0)
     np.testing.assert_allclose(zz[:, 0, 1], ref.imag, atol=TOL[dtype], rtol=0)
-    assert abs(e[0] - 0.5 * np.sum(1 - ref.real)) <= TOL[dtype] * len(edges)
+    assert abs(e[0] - 0.5 * np.sum(1 - ref.real)) <= TOL_E[dtype]
 
 
 def test_n100_p4_batched_c64_vs_oracle():
@@ -124,23 +126,17 @@ def test_persistent_equals_per_bucket_bitwise():
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 @pytest.mark.parametrize("batch", [1, 2, 3, 64])
-def test_staged_loads_equal_register_loads_bitwise(dtype, batch):
-    """The shared-memory staged operand path (bulk-copy ring, row-wide tiles)
-    and the register path multiply the same operands in the same order, so
-    every edge value is identical; buckets whose operands do not fit the ring
-    and batches without a staged form use registers in the same launch.  Also
-    checked against the oracle."""
+def test_lean_and_generic_tiles_agree_with_oracle(dtype, batch):
+    """Every batch shape of the persistent launch (the lean pair tile for one
+    angle set, the lean row tile for row-wide shapes, the generic tile
+    otherwise) with searched orders, against the oracle."""
     n, edges, p, g, b = workload("n100_p3", batch=batch)
-    out = {}
-    for path in ("staged", "registers"):
-        plan = _plan(n, edges, p, batch, dtype, "persistent", load_path=path, order_trials=4)
-        out[path] = _run(plan, g, b)
-        plan.close()
-    assert np.array_equal(out["staged"][1], out["registers"][1])
-    assert np.array_equal(out["staged"][0], out["registers"][0])
+    plan = _plan(n, edges, p, batch, dtype, "persistent", order_trials=4)
+    _, zz = _run(plan, g, b)
+    plan.close()
     sel = [0, 75, 149]
     ref = _oracle_zz(n, edges, p, g[batch - 1], b[batch - 1], sel)
-    np.testing.assert_allclose(out["staged"][1][sel, batch - 1, 0], ref.real, atol=TOL[dtype], rtol=0)
+    np.testing.assert_allclose(zz[sel, batch - 1, 0], ref.real, atol=TOL[dtype], rtol=0)
 
 
 @pytest.mark.parametrize("batch", [2, 3, 5, 8])
@@ -332,3 +328,17 @@ def test_critical_path_queue_order_equals_round_robin_bitwise(dtype, batch):
         plan.close()
     assert np.array_equal(out["round_robin"][1], out["critical_path"][1])
     assert np.array_equal(out["round_robin"][0], out["critical_path"][0])
+
+
+def test_per_width_chunks_are_bitwise_identical():
+    """Per-width schedules (warp tiles per queue task by output rank, as the
+    autotuner sets them) change which warp runs which rows, not the
+    arithmetic: every edge value is identical."""
+    n, edges, p, g, b = workload("n100_p3", batch=64)
+    out = []
+    for by_rank in (None, {r: 4 for r in range(10, 32)}, {r: 2 for r in range(32)}):
+        plan = _plan(n, edges, p, 64, "c64", "persistent", chunk_tiles_by_rank=by_rank)
+        out.append(_run(plan, g, b))
+        plan.close()
+    for e, zz in out[1:]:
+        assert np.array_equal(zz, out[0][1]) and np.array_equal(e, out[0][0])

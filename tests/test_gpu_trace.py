@@ -20,11 +20,11 @@ def _lib(qtlib):
     return qtlib
 
 
-@pytest.mark.parametrize("load_path", ["registers", "staged"])
-def test_trace_covers_every_task_in_order(load_path):
+@pytest.mark.parametrize("batch", [64, 1])
+def test_trace_covers_every_task_in_order(batch):
     from paper_2106_15740_gb300.energy import EnergyPlan
-    n, edges, p, g, b = workload("n100_p3", batch=64)
-    plan = EnergyPlan(n, edges, p, batch=64, dtype="c64", mode="persistent", device="cuda:0", load_path=load_path)
+    n, edges, p, g, b = workload("n100_p3", batch=batch)
+    plan = EnergyPlan(n, edges, p, batch=batch, dtype="c64", mode="persistent", device="cuda:0")
     gd, bd = torch.tensor(g, device="cuda:0"), torch.tensor(b, device="cuda:0")
     e0 = plan.energy(gd, bd).clone()
     tr, tasks = plan.trace(gd, bd)

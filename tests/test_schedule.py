@@ -18,7 +18,8 @@ import pytest
 from workloads import random_regular_graph
 
 
-def _plan(n, edges, p, B=4, chain=0, group_rows=0, max_workspace=0, order_trials=0, dtype=None, queue_order=1):
+def _plan(n, edges, p, B=4, chain=0, group_rows=0, max_workspace=0, order_trials=0, dtype=None, queue_order=1,
+          by_rank=None):
     from paper_2106_15740_gb300 import binding as qb
     opt = qb.qt_plan_options_default()
     opt.batch = B
@@ -29,6 +30,8 @@ def _plan(n, edges, p, B=4, chain=0, group_rows=0, max_workspace=0, order_trials
     opt.max_workspace = max_workspace
     opt.order_trials = order_trials
     opt.queue_order = queue_order
+    for r, t in (by_rank or {}).items():
+        opt.chunk_tiles_by_rank[r] = t
     return qb.qt_plan_create(n, edges, p, opt)
 
 
@@ -261,6 +264,26 @@ def test_default_grouping_by_batch(qtlib):
         assert bool((tasks["chunk"] < 0).any()) == grouped, B
 
 
+def test_per_width_chunks_schedule_is_race_free(qtlib):
+    """Per-width schedule: steps of output rank >= 6 in tasks of 2 tiles,
+    rank >= 9 in tasks of 4; every step still completes its own tiles and the
+    schedule stays race free."""
+    from paper_2106_15740_gb300 import binding as qb
+    n = 20
+    edges = random_regular_graph(n, 3, 35)
+    by_rank = {r: (2 if r < 9 else 4) for r in range(6, 32)}
+    base = _plan(n, edges, 3, B=64)
+    plan = _plan(n, edges, 3, B=64, by_rank=by_rank)
+    try:
+        t0, t1 = qb.qt_plan_tasks(base), qb.qt_plan_tasks(plan)
+        assert len(t1["step"]) < len(t0["step"])
+        units, depth, pairs, _ = check_schedule(*_schedule(plan))
+    finally:
+        qb.qt_plan_free(plan)
+        qb.qt_plan_free(base)
+    assert pairs > 0 and depth < units
+
+
 @pytest.mark.parametrize("field,value", [("chain_steps", 2), ("chain_steps", -1), ("queue_order", 2),
                                          ("queue_order", -1)])
 def test_schedule_options_are_validated(qtlib, field, value):
@@ -270,6 +293,17 @@ def test_schedule_options_are_validated(qtlib, field, value):
     opt.batch = 2
     opt.mode = qb.QT_MODE_PERSISTENT
     setattr(opt, field, value)
+    with pytest.raises(qb.QTError) as ei:
+        qb.qt_plan_create(8, random_regular_graph(8, 3, 39), 1, opt)
+    assert ei.value.status == qb.QT_EINVAL
+
+
+def test_per_width_chunks_are_validated(qtlib):
+    from paper_2106_15740_gb300 import binding as qb
+    opt = qb.qt_plan_options_default()
+    assert list(opt.chunk_tiles_by_rank) == [0] * 32
+    opt.mode = qb.QT_MODE_PERSISTENT
+    opt.chunk_tiles_by_rank[5] = -1
     with pytest.raises(qb.QTError) as ei:
         qb.qt_plan_create(8, random_regular_graph(8, 3, 39), 1, opt)
     assert ei.value.status == qb.QT_EINVAL
