@@ -436,52 +436,62 @@ __device__ __forceinline__ void tile_rows_regs(WarpTile* w, Real* __restrict__ d
 
 // Forward tile of the one-angle-set layout on the register path (PAIR: B = 1,
 // rows x = 0, 1 of an input adjacent; RP = 32 rows per pass, lane l on row
-// r0 + pass * 32 + l).  The same loads and products as tile_items, two passes
-// per iteration, without its per-item bookkeeping; bit-identical to it.
+// r0 + pass * 32 + l).  The same loads and products as tile_items,
+// PairPasses passes per iteration (each lane keeps that many rows' loads of an
+// input in flight: 4 in complex64, 2 in complex128, where 4 would spill at
+// the 64-register budget), without its per-item bookkeeping; bit-identical to
+// it.  Rows past
+// the step's end or the tile's passes read row 0 of each input (always inside
+// the input) and store nothing.
+template <class Real> struct PairPasses { static constexpr int value = sizeof(Real) == 4 ? 4 : 2; };
+template <class Real> struct AdjPairPasses { static constexpr int value = 2; };
+
 template <class Real>
 __device__ __forceinline__ void tile_pairs_regs(WarpTile* w, Real* __restrict__ data, const TileGeom& g, int64_t r0,
                                                 int64_t r1, int lane) {
   using P1 = Pack<Real, 1>;
+  constexpr int U = PairPasses<Real>::value;
   const DevBucket& d = w->d;
   const int n_in = d.n_in;
-  for (int pp = 0; pp < g.P && r0 + (int64_t)pp * 32 < r1; pp += 2) {
-    const int64_t ya = r0 + (int64_t)pp * 32 + lane, yb = ya + 32;
-    const bool oka = ya < r1, okb = pp + 1 < g.P && yb < r1;
-    P1 p0[2], p1[2];
+  for (int pp = 0; pp < g.P && r0 + (int64_t)pp * 32 < r1; pp += U) {
+    int64_t y[U];
+    bool ok[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      y[u] = r0 + (int64_t)(pp + u) * 32 + lane;
+      ok[u] = pp + u < g.P && y[u] < r1;
+    }
+    P1 p0[U], p1[U];
 #pragma unroll 1
     for (int i = 0; i < n_in; ++i) {
       const bool leaf = d.in[i].flags & kInLeaf;
       const uint32_t lp = w->lpart[i][lane];
-      const uint32_t ka = oka ? w->tab[i][pp] + lp : 0u;  // idle items read row 0 and store nothing
-      const uint32_t kb = okb ? w->tab[i][pp + 1] + lp : 0u;
-      const Pack<Real, 2> qa = ldpair_in<Real, true>(data, d.in[i].off + 2 * (int64_t)ka, leaf);
-      const Pack<Real, 2> qb = ldpair_in<Real, true>(data, d.in[i].off + 2 * (int64_t)kb, leaf);
-      P1 a00, a01, a10, a11;
-      a00.c[0] = qa.c[0];
-      a01.c[0] = qa.c[1];
-      a10.c[0] = qb.c[0];
-      a11.c[0] = qb.c[1];
-      if (i == 0) {
-        p0[0] = a00;
-        p1[0] = a01;
-        p0[1] = a10;
-        p1[1] = a11;
-      } else {
-        pmul<Real, 1>(p0[0], a00);
-        pmul<Real, 1>(p1[0], a01);
-        pmul<Real, 1>(p0[1], a10);
-        pmul<Real, 1>(p1[1], a11);
+      Pack<Real, 2> q[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const uint32_t k = ok[u] ? w->tab[i][pp + u] + lp : 0u;  // idle items read row 0 and store nothing
+        q[u] = ldpair_in<Real, true>(data, d.in[i].off + 2 * (int64_t)k, leaf);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        P1 a0, a1;
+        a0.c[0] = q[u].c[0];
+        a1.c[0] = q[u].c[1];
+        if (i == 0) {
+          p0[u] = a0;
+          p1[u] = a1;
+        } else {
+          pmul<Real, 1>(p0[u], a0);
+          pmul<Real, 1>(p1[u], a1);
+        }
       }
     }
-    if (oka) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (!ok[u]) continue;
       P1 o;
-      o.c[0] = cadd<Real>(p0[0].c[0], p1[0].c[0]);
-      stv<Real, 1>(data, d.out_off + ya, o);
-    }
-    if (okb) {
-      P1 o;
-      o.c[0] = cadd<Real>(p0[1].c[0], p1[1].c[0]);
-      stv<Real, 1>(data, d.out_off + yb, o);
+      o.c[0] = cadd<Real>(p0[u].c[0], p1[u].c[0]);
+      stv<Real, 1>(data, d.out_off + y[u], o);
     }
   }
 }
@@ -493,24 +503,27 @@ __device__ __forceinline__ void atomic_add_cx(Real* data, int64_t e, typename Cx
 }
 
 // Adjoint step (kStepAdj) on the lean paths: the same factors, products,
-// target rows and stores or atomic adds as tile_adjoint, two rows per
+// target rows and stores or atomic adds as tile_adjoint, several rows per
 // iteration, addressed straight from the pass table.  Factors flagged
 // kInNoPair (the output adjoint) give one value for x = 0 and x = 1.
-// One angle set (PAIR, 32 rows per pass, lane l on row r0 + pass * 32 + l):
+// One angle set (PAIR, 32 rows per pass, lane l on row r0 + pass * 32 + l,
+// AdjPairPasses passes per iteration):
 template <class Real>
 __device__ __forceinline__ void tile_adjoint_pairs(WarpTile* w, Real* __restrict__ data, const TileGeom& g,
                                                    int64_t r0, int64_t r1, int lane) {
   using P1 = Pack<Real, 1>;
+  constexpr int U = AdjPairPasses<Real>::value;
   const DevBucket& d = w->d;
   const int n_in = d.n_in;
   const bool full = d.aflags & kAdjFull;
   const uint32_t lp_t = w->lpart[n_in][lane];
-  for (int pp = 0; pp < g.P && r0 + (int64_t)pp * 32 < r1; pp += 2) {
-    const int64_t ya = r0 + (int64_t)pp * 32 + lane, yb = ya + 32;
-    const bool ok[2] = {ya < r1, pp + 1 < g.P && yb < r1};
-    P1 p0[2], p1[2];
+  for (int pp = 0; pp < g.P && r0 + (int64_t)pp * 32 < r1; pp += U) {
+    bool ok[U];
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
+    for (int u = 0; u < U; ++u) ok[u] = pp + u < g.P && r0 + (int64_t)(pp + u) * 32 + lane < r1;
+    P1 p0[U], p1[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
       p0[u].c[0].x = 1;
       p0[u].c[0].y = 0;
       p1[u] = p0[u];
@@ -520,24 +533,27 @@ __device__ __forceinline__ void tile_adjoint_pairs(WarpTile* w, Real* __restrict
       const int32_t fl = d.in[i].flags;
       const bool leaf = fl & kInLeaf;
       const uint32_t lp = w->lpart[i][lane];
+      P1 a0[U], a1[U];
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
+      for (int u = 0; u < U; ++u) {
         const uint32_t k = ok[u] ? w->tab[i][pp + u] + lp : 0u;  // idle items read row 0
-        P1 a0, a1;
         if (fl & kInNoPair) {
-          a0 = ldv_in<Real, 1, true>(data, d.in[i].off + (int64_t)k, leaf);
-          a1 = a0;
+          a0[u] = ldv_in<Real, 1, true>(data, d.in[i].off + (int64_t)k, leaf);
+          a1[u] = a0[u];
         } else {
           const Pack<Real, 2> q = ldpair_in<Real, true>(data, d.in[i].off + 2 * (int64_t)k, leaf);
-          a0.c[0] = q.c[0];
-          a1.c[0] = q.c[1];
+          a0[u].c[0] = q.c[0];
+          a1[u].c[0] = q.c[1];
         }
-        pmul<Real, 1>(p0[u], a0);
-        pmul<Real, 1>(p1[u], a1);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        pmul<Real, 1>(p0[u], a0[u]);
+        pmul<Real, 1>(p1[u], a1[u]);
       }
     }
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
+    for (int u = 0; u < U; ++u) {
       if (!ok[u]) continue;
       const int64_t e0 = d.out_off + 2 * (int64_t)(w->tab[n_in][pp + u] + lp_t);
       if (full) {
@@ -818,6 +834,92 @@ __device__ __forceinline__ void tile_adjred(WarpTile* w, Real* __restrict__ data
   }
 }
 
+// Reduction adjoint step (kStepAdjRed) of the one-angle-set layout (PAIR,
+// RP = 32: lane l on completion c = l of pass pp, all lanes of a pass on the
+// same target row kt, which changes every 2^comp_bits / 32 passes).  The same
+// loads, products, sums and atomic adds as tile_adjred, AdjRedPasses passes
+// per iteration (that many rows' loads of every factor in flight per lane),
+// without the generic tile's per-item bookkeeping.  The pass table and lane
+// parts are those warp_tile builds for the reduction order.
+template <class Real> struct AdjRedPasses { static constexpr int value = sizeof(Real) == 4 ? 4 : 2; };
+
+template <class Real>
+__device__ __forceinline__ void tile_adjred_pairs(WarpTile* w, Real* __restrict__ data, const TileGeom& g,
+                                                  int64_t r0, int64_t r1, int lane) {
+  using P1 = Pack<Real, 1>;
+  constexpr int U = AdjRedPasses<Real>::value;
+  const DevBucket& d = w->d;
+  const int n_in = d.n_in;
+  const int seg = (1 << d.comp_bits) / 32;  // passes per target row (>= 1)
+  P1 s0, s1;
+  s0.c[0].x = 0;
+  s0.c[0].y = 0;
+  s1 = s0;
+  for (int pp = 0; pp < g.P && r0 + (int64_t)pp * 32 < r1; pp += U) {
+    bool ok[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) ok[u] = pp + u < g.P && r0 + (int64_t)(pp + u) * 32 + lane < r1;
+    P1 p0[U], p1[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      p0[u].c[0].x = 1;
+      p0[u].c[0].y = 0;
+      p1[u] = p0[u];
+    }
+#pragma unroll 1
+    for (int i = 0; i < n_in; ++i) {
+      const int32_t fl = d.in[i].flags;
+      const bool leaf = fl & kInLeaf;
+      const uint32_t lp = w->lpart[i][lane];
+      P1 a0[U], a1[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const uint32_t k = ok[u] ? w->tab[i][pp + u] + lp : 0u;  // idle items read row 0
+        if (fl & kInNoPair) {
+          a0[u] = ldv_in<Real, 1, true>(data, d.in[i].off + (int64_t)k, leaf);
+          a1[u] = a0[u];
+        } else {
+          const Pack<Real, 2> q = ldpair_in<Real, true>(data, d.in[i].off + 2 * (int64_t)k, leaf);
+          a0[u].c[0] = q.c[0];
+          a1[u].c[0] = q.c[1];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        pmul<Real, 1>(p0[u], a0[u]);
+        pmul<Real, 1>(p1[u], a1[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int q = pp + u;
+      if (q >= g.P || r0 + (int64_t)q * 32 >= r1) break;  // warp-uniform: the tile's last pass is done
+      if (ok[u]) {
+        s0.c[0] = cadd<Real>(s0.c[0], p0[u].c[0]);
+        s1.c[0] = cadd<Real>(s1.c[0], p1[u].c[0]);
+      }
+      if ((q + 1) % seg == 0 || q + 1 == g.P || r0 + (int64_t)(q + 1) * 32 >= r1) {  // end of a target row's passes
+        const uint32_t kt = (uint32_t)((r0 + (int64_t)q * 32) >> d.comp_bits);
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+          s0.c[0].x += __shfl_xor_sync(0xffffffffu, s0.c[0].x, off);
+          s0.c[0].y += __shfl_xor_sync(0xffffffffu, s0.c[0].y, off);
+          s1.c[0].x += __shfl_xor_sync(0xffffffffu, s1.c[0].x, off);
+          s1.c[0].y += __shfl_xor_sync(0xffffffffu, s1.c[0].y, off);
+        }
+        if (lane == 0) {
+          const int64_t e0 = d.out_off + 2 * (int64_t)kt;
+          atomic_add_cx<Real>(data, e0, s0.c[0]);
+          atomic_add_cx<Real>(data, e0 + 1, s1.c[0]);
+        }
+        s0.c[0].x = 0;
+        s0.c[0].y = 0;
+        s1 = s0;
+      }
+    }
+  }
+}
+
 // One warp evaluates output rows [r0, r1) of the bucket in w->d (all B angle
 // sets).  r0 is a multiple of g.R.  The pass table tab[i][p] =
 // pext(r0 + p * RP, mask_i) is built here; the lane parts must already be in
@@ -869,7 +971,10 @@ __device__ __forceinline__ void warp_tile(WarpTile* w, Real* __restrict__ data, 
     else
       tile_adjoint<Real, VB, PAIR, CG, 2>(w, data, g, r0, r1, lane, rip, v0, lane_on, ctrl, dbg_bucket);
   } else if (d.kind == kStepAdjRed) {
-    tile_adjred<Real, VB, PAIR, CG, 2>(w, data, g, r0, r1, lane, rip, v0, lane_on, ctrl, dbg_bucket);
+    if (STAGE == 2 && PAIR && g.RP == 32 && g.VC == 1)
+      tile_adjred_pairs<Real>(w, data, g, r0, r1, lane);
+    else
+      tile_adjred<Real, VB, PAIR, CG, 2>(w, data, g, r0, r1, lane, rip, v0, lane_on, ctrl, dbg_bucket);
   } else {
     tile_zero<Real, VB, PAIR, 2>(w, data, g, r0, r1, rip, v0, lane_on);
   }
