@@ -320,10 +320,18 @@ def gradient_and_comparator(dev, torch):
     out = {}
     n, edges, p, g, b = workload("n60_p4")
     gd, bd = torch.tensor(g, device=dev), torch.tensor(b, device=dev)
+    # tile size, grouping and per-width schedule of the gradient plan, picked on this device
+    from paper_2106_15740_gb300.energy import autotune, autotune_bands
+    trials = WORKLOAD.get("order_trials", 0)
+    best, timings = autotune(n, edges, p, batch=1, dtype="c64", gradient=True, device=dev, reps=3,
+                             lane_items=(16, 32, 64), group_rows=(0, 32), order_trials=trials)
+    by_rank, band_ms = autotune_bands(n, edges, p, batch=1, dtype="c64", gradient=True, device=dev, reps=3,
+                                      order_trials=trials, **best)
+    tuned = dict(best, chunk_tiles_by_rank=by_rank)
     res = {}
     for dt in ("c64", "c128"):
         plan = EnergyPlan(n, edges, p, batch=1, dtype=dt, mode="persistent", gradient=True, device=dev,
-                          order_trials=WORKLOAD.get("order_trials", 0))
+                          order_trials=trials, **tuned)
         ms, kms = _time_calls(plan, gd, bd, True, 5, torch, kernel=True)
         _, gr = plan.energy(gd, bd, grad=True)
         res[dt] = dict(ms=ms, kms=kms, alg=plan.stats["alg_bytes"], grad=gr.cpu().numpy()[0])
@@ -347,6 +355,9 @@ def gradient_and_comparator(dev, torch):
                    "workload": "random 3-regular N=60 p=4 (seed 3), 90 edge lightcones, dE/dgamma and dE/dbeta "
                                "(8 angles) by the adjoint bucket sweep, one angle set",
                    "ordering": f"searched, {WORKLOAD.get('order_trials', 0)} trials per edge",
+                   "autotune": {"choice": best, "per_width_band": band_ms,
+                                "ms_per_candidate": {f"lane_items={k[0]},group_rows={k[1]}": round(v, 3)
+                                                     for k, v in timings.items()}},
                    "alg_bytes_per_eval": c64["alg"], "achieved_gbs": c64["alg"] / (c64["ms"] * 1e-3) / 1e9,
                    "roofline": _roofline(c64["alg"], c64["kms"], peak, peak_kind,
                                          "persistent_kernel<float,1,true,true,2>"),

@@ -771,12 +771,12 @@ qt_status compile_plan(Plan* P) {
             rep[gb + j] = last;
           }
           for (int32_t j = 0; j < (chain ? 1 : k); ++j) add_deps(s, gb + j, last);
-          P->tasks.push_back(DevTask{gb, -k});
+          P->tasks.push_back(DevTask{gb, -k, 0, 0});
           bi[s] += k - 1;
         } else {
           d.ntask = (int32_t)nt;
           add_deps(s, gb, gb);
-          for (int32_t c = 0; c < d.ntask; ++c) P->tasks.push_back(DevTask{gb, c});
+          for (int32_t c = 0; c < d.ntask; ++c) P->tasks.push_back(DevTask{gb, c, 0, 0});
         }
         std::sort(dl.begin(), dl.end());
         dl.erase(std::unique(dl.begin(), dl.end()), dl.end());
@@ -835,6 +835,15 @@ qt_status compile_plan(Plan* P) {
     }
   }
 
+  // Device images of the queue: each task carries its step's dependency list,
+  // each list entry the done count that completes the step it names.
+  for (DevTask& t : P->tasks) {
+    t.dep = P->buckets[t.bucket].dep;
+    t.n_dep = P->buckets[t.bucket].n_dep;
+  }
+  P->dev_deps.resize(P->deps.size());
+  for (size_t i = 0; i < P->deps.size(); ++i) P->dev_deps[i] = DevDep{P->deps[i], P->buckets[P->deps[i]].ntask};
+
   // Workspace layout.
   WsLayout& L = P->ws;
   const int32_t p = P->p;
@@ -848,7 +857,7 @@ qt_status compile_plan(Plan* P) {
   L.tasks = o;
   o = align256(o + sizeof(DevTask) * P->tasks.size());
   L.deps = o;
-  o = align256(o + sizeof(int32_t) * P->deps.size());
+  o = align256(o + sizeof(DevDep) * P->dev_deps.size());
   L.leaf = o;
   o = align256(o + sizeof(DevLeafFactor) * P->leaf.size());
   L.leaf_first = o;
@@ -908,19 +917,21 @@ qt_status run_plan(Plan* P, const double* gamma, const double* beta, double* ene
     if (!P->buckets.empty())
       QT_CUDA(cudaMemcpyAsync(base + L.buckets, P->buckets.data(), sizeof(DevBucket) * P->buckets.size(),
                               cudaMemcpyHostToDevice, s));
-    if (P->stall_step >= 0 && P->stall_step < (int32_t)P->buckets.size()) {
-      // failure-detection hook: a tile count that no warp will ever reach
-      const int32_t unreachable = P->buckets[P->stall_step].ntask + 1;
-      QT_CUDA(cudaMemcpyAsync(base + L.buckets + sizeof(DevBucket) * P->stall_step + offsetof(DevBucket, ntask),
-                              &unreachable, sizeof(int32_t), cudaMemcpyHostToDevice, s));
-      QT_CUDA(cudaStreamSynchronize(s));
-    }
     if (!P->tasks.empty())
       QT_CUDA(cudaMemcpyAsync(base + L.tasks, P->tasks.data(), sizeof(DevTask) * P->tasks.size(),
                               cudaMemcpyHostToDevice, s));
-    if (!P->deps.empty())
-      QT_CUDA(cudaMemcpyAsync(base + L.deps, P->deps.data(), sizeof(int32_t) * P->deps.size(),
-                              cudaMemcpyHostToDevice, s));
+    std::vector<DevDep> stalled;
+    const DevDep* deps_src = P->dev_deps.data();
+    if (P->stall_step >= 0 && P->stall_step < (int32_t)P->buckets.size()) {
+      // failure-detection hook: waiters of that step look for a done count that is never reached
+      stalled = P->dev_deps;
+      for (DevDep& d : stalled)
+        if (d.step == P->stall_step) d.need = P->buckets[P->stall_step].ntask + 1;
+      deps_src = stalled.data();
+    }
+    if (!P->dev_deps.empty())
+      QT_CUDA(cudaMemcpyAsync(base + L.deps, deps_src, sizeof(DevDep) * P->dev_deps.size(), cudaMemcpyHostToDevice,
+                              s));
     if (!P->leaf.empty())
       QT_CUDA(cudaMemcpyAsync(base + L.leaf, P->leaf.data(), sizeof(DevLeafFactor) * P->leaf.size(),
                               cudaMemcpyHostToDevice, s));
@@ -971,7 +982,7 @@ qt_status run_plan(Plan* P, const double* gamma, const double* beta, double* ene
     const int32_t grid = std::max(1, per_sm) * n_sm;
     QT_CUDA(launch_persistent(dtype, P->opt.gradient != 0, dbk, (const DevTask*)(base + L.tasks), (int32_t)P->tasks.size(),
                               (DevCtrl*)(base + L.ctrl), (int32_t*)(base + L.done), B, P->opt.lane_items, data,
-                              P->data_elems, grid, P->spin_limit, (const int32_t*)(base + L.deps), P->trace, s));
+                              P->data_elems, grid, P->spin_limit, (const DevDep*)(base + L.deps), P->trace, s));
   } else {
     int n_sm = 0;
     QT_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));

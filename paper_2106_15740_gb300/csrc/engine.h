@@ -49,6 +49,7 @@ struct Plan {
   int64_t lbar_elems = 0;
   std::vector<DevTask> tasks;
   std::vector<int32_t> deps;               // dependency lists of the queued steps (DevBucket dep, n_dep)
+  std::vector<DevDep> dev_deps;            // the same lists as the device reads them (step, done count)
   // data elements each step touches: ranges acc_first[s] .. acc_first[s + 1] of
   // [acc_lo, acc_hi), acc_w = 1 for a write (or an accumulation)
   std::vector<int32_t> acc_first;

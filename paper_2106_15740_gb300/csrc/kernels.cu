@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(256, 4) persistent_kernel(const DevBucket* __r
                                                             const DevTask* __restrict__ tasks, int32_t n_tasks,
                                                             DevCtrl* ctrl, int32_t* done, Real* __restrict__ data,
                                                             const TileGeom g, int32_t spin_limit,
-                                                            const int32_t* __restrict__ deps,
+                                                            const DevDep* __restrict__ deps,
                                                             unsigned long long* __restrict__ trace) {
   __shared__ WarpTile tiles[8];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -353,23 +353,31 @@ __global__ void __launch_bounds__(256, 4) persistent_kernel(const DevBucket* __r
     if (trace != nullptr && lane == 0) w->trace_t[0] = globaltimer();
     if (lane == 0 && *((volatile int32_t*)&ctrl->status) == 0) t_next = atomicAdd(&ctrl->head, 1);
     if (task.bucket != cached) {  // uniform; a warp that ran a chunk of this step already saw its inputs
-      // lane q waits for the dependencies q, q + 32, ... of the step (each poll bounded)
-      const int32_t nd = buckets[task.bucket].n_dep, d0 = buckets[task.bucket].dep;
+      // The task carries its step's dependency list; lane q waits for the
+      // entries q, q + 32, ... (each poll bounded).  The first entry's load
+      // and the copy of the step's record (static, written before the
+      // launch) are issued together, so the record arrives during the wait.
+      const int32_t nd = task.n_dep, d0 = task.dep;
+      DevDep dd{0, 0};
+      if (lane < nd) dd = deps[d0 + lane];
+      copy_bucket(&w->d, buckets + task.bucket, lane);
       for (int32_t q = lane; q < nd && !failed; q += 32) {
-        const int32_t dep = deps[d0 + q];
-        const int32_t need = buckets[dep].ntask;
+        if (q != lane) dd = deps[d0 + q];
         int32_t polls = 0;
-        while (ld_acquire(done + dep) < need) {
+        while (ld_acquire(done + dd.step) < dd.need) {
           ++polls;
           if (polls > spin_limit || ((polls & 63) == 0 && *((volatile int32_t*)&ctrl->status) != 0)) {
-            if (atomicCAS(&ctrl->status, 0, (int32_t)QT_ETIMEOUT) == 0) ctrl->spins = dep;
+            if (atomicCAS(&ctrl->status, 0, (int32_t)QT_ETIMEOUT) == 0) ctrl->spins = dd.step;
             failed = 1;
             break;
           }
           __nanosleep(100);
         }
       }
-      __syncwarp();  // every lane's acquire before any lane reads the inputs
+      __syncwarp();  // every lane's acquire (and record store) before any lane reads
+      lane_parts(w, g, lane);
+      __syncwarp();
+      cached = task.bucket;
     }
     failed = __any_sync(0xffffffffu, failed);
     t_next = __shfl_sync(0xffffffffu, t_next, 0);
@@ -707,7 +715,7 @@ static const void* persistent_fn(int dtype, bool grad, int32_t B) {
 
 cudaError_t launch_persistent(int dtype, bool grad, const DevBucket* buckets, const DevTask* tasks, int32_t n_tasks,
                               DevCtrl* ctrl, int32_t* done, int32_t B, int32_t lane_items, void* data,
-                              int64_t data_elems, int32_t grid, int32_t spin_limit, const int32_t* deps,
+                              int64_t data_elems, int32_t grid, int32_t spin_limit, const DevDep* deps,
                               unsigned long long* trace, cudaStream_t s) {
   TileGeom g = tile_geom(dtype, B, lane_items);
   g.data_elems = data_elems;

@@ -201,6 +201,28 @@ __device__ __forceinline__ void load_bucket(DevBucket* dst, const DevBucket* src
   }
 }
 
+// The same copy for every record slot: lanes 0 .. kDevMaxIn - 1 copy input
+// slot `lane` whatever the step's fan-in (the host zero-fills unused slots,
+// so the shared copy holds no stale entries), lane 31 the header.  It needs
+// no field of the record first, so its loads go out at once.
+__device__ __forceinline__ void copy_bucket(DevBucket* dst, const DevBucket* src, int lane) {
+  if (lane < kDevMaxIn) dst->in[lane] = src->in[lane];
+  if (lane == 31) {
+    dst->out_off = src->out_off;
+    dst->n_rows = src->n_rows;
+    dst->out_rank = src->out_rank;
+    dst->n_in = src->n_in;
+    dst->dep = src->dep;
+    dst->ntask = src->ntask;
+    dst->kind = src->kind;
+    dst->aflags = src->aflags;
+    dst->tgt_bits = src->tgt_bits;
+    dst->comp_bits = src->comp_bits;
+    dst->span = src->span;
+    dst->n_dep = src->n_dep;
+  }
+}
+
 template <class Real, bool CG>
 __device__ __forceinline__ Pack<Real, 2> ldpair_in(const Real* data, int64_t e, bool leaf) {
   return leaf ? ldpair<Real, false>(data, e) : ldpair<Real, CG>(data, e);

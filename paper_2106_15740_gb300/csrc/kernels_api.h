@@ -19,7 +19,7 @@ cudaError_t launch_bucket(int dtype, const DevBucket& d, int32_t B, int32_t lane
 bool row_wide(int dtype, int32_t B);
 cudaError_t launch_persistent(int dtype, bool grad, const DevBucket* buckets, const DevTask* tasks, int32_t n_tasks,
                               DevCtrl* ctrl, int32_t* done, int32_t B, int32_t lane_items, void* data,
-                              int64_t data_elems, int32_t grid, int32_t spin_limit, const int32_t* deps,
+                              int64_t data_elems, int32_t grid, int32_t spin_limit, const DevDep* deps,
                               unsigned long long* trace, cudaStream_t s);
 cudaError_t persistent_occupancy(int dtype, bool grad, int32_t B, int* blocks_per_sm);
 cudaError_t launch_energy(int dtype, const void* data, const int64_t* scal_off, const int32_t* scal_begin,

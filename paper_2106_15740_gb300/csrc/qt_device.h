@@ -115,7 +115,7 @@ constexpr int kTrigStride = 6;
 // prod r^count times the exact network: energy_kernel and leafgrad_kernel
 // divide that product out in FP64.
 
-// Persistent-queue task.  chunk >= 0: chunk `chunk` of step `bucket`, its
+// Persistent-queue task (16 bytes, one load).  chunk >= 0: chunk `chunk` of step `bucket`, its
 // warp tiles [chunk * span, (chunk + 1) * span).  chunk < 0: a group of
 // -chunk consecutive steps of one network, starting at `bucket`, each small
 // enough for a single tile; one warp runs them in order with no global
@@ -123,6 +123,15 @@ constexpr int kTrigStride = 6;
 struct DevTask {
   int32_t bucket;
   int32_t chunk;
+  int32_t dep;                 // the step's dependency list: deps[dep .. dep + n_dep) (a group:
+  int32_t n_dep;               // its first step's list; the others wait on nothing)
+};
+
+// One entry of a dependency list: the step waited for and the done count
+// that completes it (its number of queue tasks).
+struct DevDep {
+  int32_t step;
+  int32_t need;
 };
 
 // Control words at the start of the workspace.
