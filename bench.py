@@ -393,9 +393,9 @@ def gradient_and_comparator(dev, torch):
 
 def complex128_counterparts(dev, torch):
     """The bench plan (150 edges x 64 angle sets, searched orders, one
-    persistent launch) in complex128, and the 100-vertex p = 3 graph (one
-    angle set) in both precisions: time, roofline, and the complex64
-    error against complex128."""
+    persistent launch) in complex128 and in float pairs (c64x2), and the
+    100-vertex p = 3 graph (one angle set) in the three precisions: time,
+    roofline, and the complex64 and float-pair errors against complex128."""
     import numpy as np
     from paper_2106_15740_gb300.energy import EnergyPlan
     from workloads import workload
@@ -405,7 +405,7 @@ def complex128_counterparts(dev, torch):
         n, edges, p, g, b = workload(name, batch=B)
         gd, bd = torch.tensor(g, device=dev), torch.tensor(b, device=dev)
         r = {}
-        for dt in ("c64", "c128"):
+        for dt in ("c64", "c128", "c64x2"):
             plan = EnergyPlan(n, edges, p, batch=B, dtype=dt, mode="persistent", device=dev, order_trials=trials)
             ms, kms = _time_calls(plan, gd, bd, False, 5, torch, kernel=True)
             e, zz = plan.energy(gd, bd, edge_zz=True)
@@ -420,8 +420,14 @@ def complex128_counterparts(dev, torch):
             "c64": {"value": len(edges) * B / (r["c64"]["ms"] * 1e-3), "unit": "edge_evals/s",
                     "ms_per_call": r["c64"]["ms"],
                     "roofline": _roofline(r["c64"]["alg"], r["c64"]["kms"], peak, peak_kind, "persistent_kernel<float,...>")},
+            "c64x2": {"value": len(edges) * B / (r["c64x2"]["ms"] * 1e-3), "unit": "edge_evals/s",
+                      "ms_per_call": r["c64x2"]["ms"],
+                      "roofline": _roofline(r["c64x2"]["alg"], r["c64x2"]["kms"], peak, peak_kind,
+                                            "persistent_kernel<ff,...> (float pairs)")},
             "c64_vs_c128": {"max_abs_dzz": float(np.abs(r["c64"]["zz"][:, :, 0] - r["c128"]["zz"][:, :, 0]).max()),
                             "max_abs_dE": float(np.abs(r["c64"]["e"] - r["c128"]["e"]).max())},
+            "c64x2_vs_c128": {"max_abs_dzz": float(np.abs(r["c64x2"]["zz"][:, :, 0] - r["c128"]["zz"][:, :, 0]).max()),
+                              "max_abs_dE": float(np.abs(r["c64x2"]["e"] - r["c128"]["e"]).max())},
             "workload": f"{name}, {len(edges)} edges x {B} angle sets, "
                         + (f"searched orders ({trials} trials)" if trials else "min-fill orders")}
     return out
@@ -460,6 +466,15 @@ def large_config(dev, torch):
                                                     "persistent_kernel<float,1,true,true,2>")}
     plan.close()
     torch.cuda.empty_cache()
+    plan = EnergyPlan(n, edges, p, dtype="c64x2", **kw)
+    msx2, kmsx2 = _time_calls(plan, gd, bd, False, 1, torch, kernel=True)
+    ex2, zzx2 = plan.energy(gd, bd, edge_zz=True)
+    plan.check()
+    out["energy_c64x2"] = {"value": len(edges) / (msx2 * 1e-3), "unit": "edge_evals/s", "ms_per_call": msx2,
+                           "roofline": _roofline(plan.stats["alg_bytes"], kmsx2, peak, peak_kind,
+                                                 "persistent_kernel<ff,1,true,false,2> (float pairs)")}
+    plan.close()
+    torch.cuda.empty_cache()
     plan = EnergyPlan(n, edges, p, dtype="c128", **kw)
     ms128 = _time_calls(plan, gd, bd, False, 1, torch)
     e128, zz128 = plan.energy(gd, bd, edge_zz=True)
@@ -469,6 +484,8 @@ def large_config(dev, torch):
     out["energy_c128_ms_per_call"] = ms128
     out["c64_vs_c128"] = {"max_abs_dzz": float((zz64[:, 0, 0] - zz128[:, 0, 0]).abs().max()),
                           "abs_dE": float((e64 - e128).abs().max())}
+    out["c64x2_vs_c128"] = {"max_abs_dzz": float((zzx2[:, 0, 0] - zz128[:, 0, 0]).abs().max()),
+                            "abs_dE": float((ex2 - e128).abs().max())}
     return out
 
 

@@ -54,7 +54,13 @@ typedef enum {
 
 typedef enum {
   QT_C128 = 0,      /* complex128 storage and arithmetic */
-  QT_C64 = 1        /* complex64 storage, FP32 arithmetic; FP64 edge product and energy sum */
+  QT_C64 = 1,       /* complex64 storage, FP32 arithmetic; gates stored as float pairs whose
+                       norm is divided out per network, leaf products in float pairs, FP64
+                       network products and energy sums */
+  QT_C64X2 = 2      /* each real part and imaginary part an unevaluated sum of two floats
+                       (hi + lo, about 48 significant bits, 16 bytes per complex number) with
+                       error-free FP32 arithmetic: complex128-class results from the FP32 pipes.
+                       Energies and amplitudes only (gradient plans reject it) */
 } qt_dtype;
 
 typedef enum {

@@ -16,7 +16,7 @@ import numpy as np
 LIB_PATH = Path(__file__).resolve().parent / "libqtensor_gb300.so"
 
 QT_OK, QT_EINVAL, QT_ENOMEM, QT_EWIDTH, QT_ECUDA, QT_ETIMEOUT, QT_ESTATE = range(7)
-QT_C128, QT_C64 = 0, 1
+QT_C128, QT_C64, QT_C64X2 = 0, 1, 2
 QT_MODE_PER_BUCKET, QT_MODE_PERSISTENT = 0, 1
 QT_REP_DEFAULT, QT_REP_DIAGONAL, QT_REP_ZZ, QT_REP_ZZ_DIAGONAL = range(4)
 STATUS_NAMES = {0: "QT_OK", 1: "QT_EINVAL", 2: "QT_ENOMEM", 3: "QT_EWIDTH", 4: "QT_ECUDA",

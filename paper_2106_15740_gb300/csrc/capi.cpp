@@ -191,7 +191,7 @@ qt_status qt_order(const qt_network* net, int32_t* order, int32_t* n_vars, int32
 
 static qt_status contract_plan(const qt_network* net, const int32_t* order, qt_dtype dtype, Plan* P) {
   if (!net || !order) return fail(QT_EINVAL, "network or order is NULL");
-  if (dtype != QT_C128 && dtype != QT_C64) return fail(QT_EINVAL, "unknown dtype");
+  if (dtype != QT_C128 && dtype != QT_C64 && dtype != QT_C64X2) return fail(QT_EINVAL, "unknown dtype");
   std::vector<int32_t> o(order, order + net->net.n_vars);
   EdgePlan ep;
   qt_status st = make_edge_plan(net->net, o, &ep);
@@ -201,7 +201,7 @@ static qt_status contract_plan(const qt_network* net, const int32_t* order, qt_d
   P->opt.mode = QT_MODE_PER_BUCKET;
   P->opt.lane_items = 16;
   P->p = net->net.p;
-  P->elem_bytes = dtype == QT_C64 ? 8 : 16;
+  P->elem_bytes = dtype == QT_C64 ? 8 : 16;  // complex128 and float pairs: 16 bytes
   P->widths = {ep.width};
   P->slices = {0};
   P->edges.push_back(std::move(ep));
@@ -267,7 +267,9 @@ static qt_status check_options(const qt_plan_options* opt, qt_plan_options* out)
   qt_plan_options_default(&o);
   if (opt) o = *opt;
   if (o.batch < 1) return fail(QT_EINVAL, "batch must be >= 1");
-  if (o.dtype != QT_C128 && o.dtype != QT_C64) return fail(QT_EINVAL, "unknown dtype");
+  if (o.dtype != QT_C128 && o.dtype != QT_C64 && o.dtype != QT_C64X2) return fail(QT_EINVAL, "unknown dtype");
+  if (o.dtype == QT_C64X2 && o.gradient)
+    return fail(QT_EINVAL, "the float-pair precision (QT_C64X2) evaluates energies and amplitudes only");
   if (o.mode != QT_MODE_PER_BUCKET && o.mode != QT_MODE_PERSISTENT) return fail(QT_EINVAL, "unknown mode");
   if (o.max_width <= 0 || o.max_width > 31) o.max_width = 31;
   if (o.lane_items > 0 && o.lane_items != 8 && o.lane_items != 16 && o.lane_items != 32 && o.lane_items != 64)

@@ -197,6 +197,13 @@ template <> struct LeafAcc<float> {
   // hi is the float nearest to hi + lo (each update renormalises the pair)
   __device__ __forceinline__ float2 rounded() const { return make_float2(rh, ih); }
 };
+// Float pairs: the product of the leaves (each an FP64 value split into a
+// pair) in float-pair arithmetic.
+template <> struct LeafAcc<ff> {
+  ff2 v = ff2{ff(1.0f, 0.0f), ff(0.0f, 0.0f)};
+  __device__ __forceinline__ void mul(double2 l) { v = cmul<ff>(v, ff2{ff(l.x), ff(l.y)}); }
+  __device__ __forceinline__ ff2 rounded() const { return v; }
+};
 
 // Leaf factors for up to LeafTabB<Real> angle sets: one block per factor.
 // Each leaf takes at most 4 values (its two slot bits) per angle set; the
@@ -616,6 +623,8 @@ cudaError_t launch_leaf_factors(int dtype, const DevLeafFactor* lf, int32_t n_lf
     const int32_t grid = n_lf < 65535 ? n_lf : 65535;
     if (dtype == QT_C64)
       dev::leaf_factor_tab_kernel<float><<<grid, 256, 0, s>>>(lf, n_lf, trig, p, B, (float*)data);
+    else if (dtype == QT_C64X2)
+      dev::leaf_factor_tab_kernel<dev::ff><<<grid, 256, 0, s>>>(lf, n_lf, trig, p, B, (dev::ff*)data);
     else
       dev::leaf_factor_tab_kernel<double><<<grid, 256, 0, s>>>(lf, n_lf, trig, p, B, (double*)data);
     return cudaGetLastError();
@@ -623,6 +632,8 @@ cudaError_t launch_leaf_factors(int dtype, const DevLeafFactor* lf, int32_t n_lf
   const int32_t grid = n_lf < 152 * 16 ? n_lf : 152 * 16;
   if (dtype == QT_C64)
     dev::leaf_factor_kernel<float><<<grid, 128, 0, s>>>(lf, n_lf, trig, p, B, (float*)data);
+  else if (dtype == QT_C64X2)
+    dev::leaf_factor_kernel<dev::ff><<<grid, 128, 0, s>>>(lf, n_lf, trig, p, B, (dev::ff*)data);
   else
     dev::leaf_factor_kernel<double><<<grid, 128, 0, s>>>(lf, n_lf, trig, p, B, (double*)data);
   return cudaGetLastError();
@@ -670,6 +681,11 @@ cudaError_t launch_bucket(int dtype, const DevBucket& d, int32_t B, int32_t lane
       dev::bucket_kernel<float, 2, false><<<(int)blocks, 256, 0, s>>>(d, (float*)data, g, n_tiles);
     else
       dev::bucket_kernel<float, 1, false><<<(int)blocks, 256, 0, s>>>(d, (float*)data, g, n_tiles);
+  } else if (dtype == QT_C64X2) {
+    if (pair)
+      dev::bucket_kernel<dev::ff, 1, true><<<(int)blocks, 256, 0, s>>>(d, (dev::ff*)data, g, n_tiles);
+    else
+      dev::bucket_kernel<dev::ff, 1, false><<<(int)blocks, 256, 0, s>>>(d, (dev::ff*)data, g, n_tiles);
   } else {
     if (pair)
       dev::bucket_kernel<double, 1, true><<<(int)blocks, 256, 0, s>>>(d, (double*)data, g, n_tiles);
@@ -684,7 +700,7 @@ cudaError_t launch_bucket(int dtype, const DevBucket& d, int32_t B, int32_t lane
 // lean row tile; one angle set takes the lean pair tile; other batches the
 // generic register tile.
 bool row_wide(int dtype, int32_t B) {
-  if (B <= 1 || !(dtype == QT_C128 || vector_width(dtype, B) == 2)) return false;
+  if (B <= 1 || !(dtype == QT_C128 || dtype == QT_C64X2 || vector_width(dtype, B) == 2)) return false;
   const TileGeom g = tile_geom(dtype, B, 0);
   return g.RP == 1 && g.VC == 1;
 }
@@ -705,6 +721,14 @@ static const void* persistent_fn_g(int dtype, int32_t B) {
     if (vector_width(dtype, B) == 2) return lean ? pk_fn<float, 2, false, GRAD, 2>() : pk_fn<float, 2, false, GRAD, 0>();
     return pk_fn<float, 1, false, GRAD, 0>();
   }
+  if (dtype == QT_C64X2) {  // float pairs: energies and amplitudes only
+    if constexpr (GRAD) {
+      return nullptr;
+    } else {
+      if (pair) return pk_fn<dev::ff, 1, true, false, 2>();
+      return lean ? pk_fn<dev::ff, 1, false, false, 2>() : pk_fn<dev::ff, 1, false, false, 0>();
+    }
+  }
   if (pair) return pk_fn<double, 1, true, GRAD, 2>();
   return lean ? pk_fn<double, 1, false, GRAD, 2>() : pk_fn<double, 1, false, GRAD, 0>();
 }
@@ -721,13 +745,16 @@ cudaError_t launch_persistent(int dtype, bool grad, const DevBucket* buckets, co
   g.data_elems = data_elems;
   g.wait_limit = 1 << 22;
   const void* fn = persistent_fn(dtype, grad, B);
+  if (!fn) return cudaErrorInvalidValue;  // no such variant (float pairs have no adjoint sweep)
   void* args[] = {(void*)&buckets, (void*)&tasks, (void*)&n_tasks, (void*)&ctrl, (void*)&done, (void*)&data,
                   (void*)&g, (void*)&spin_limit, (void*)&deps, (void*)&trace};
   return cudaLaunchKernel(fn, dim3(grid), dim3(256), args, 0, s);
 }
 
 cudaError_t persistent_occupancy(int dtype, bool grad, int32_t B, int* blocks_per_sm) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, persistent_fn(dtype, grad, B), 256, 0);
+  const void* fn = persistent_fn(dtype, grad, B);
+  if (!fn) return cudaErrorInvalidValue;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, 256, 0);
 }
 
 cudaError_t launch_energy(int dtype, const void* data, const int64_t* scal_off, const int32_t* scal_begin,
@@ -737,6 +764,9 @@ cudaError_t launch_energy(int dtype, const void* data, const int64_t* scal_off, 
   if (dtype == QT_C64)
     dev::energy_kernel<float><<<grid, 128, 0, s>>>((const float*)data, scal_off, scal_begin, net_first, counts, trig,
                                                    p, n_edges, B, energy, edge_zz);
+  else if (dtype == QT_C64X2)
+    dev::energy_kernel<dev::ff><<<grid, 128, 0, s>>>((const dev::ff*)data, scal_off, scal_begin, net_first, counts,
+                                                     trig, p, n_edges, B, energy, edge_zz);
   else
     dev::energy_kernel<double><<<grid, 128, 0, s>>>((const double*)data, scal_off, scal_begin, net_first, counts,
                                                     trig, p, n_edges, B, energy, edge_zz);

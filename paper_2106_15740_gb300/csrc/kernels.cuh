@@ -24,15 +24,60 @@
 namespace qt {
 namespace dev {
 
+// A real number as an unevaluated sum of two floats, hi + lo with |lo| at
+// most half an ulp of hi: about 48 significant bits, all arithmetic on the
+// FP32 pipes (this GPU's FP64 rate is a small fraction of its FP32 rate).
+// Products use the FMA-exact product error (Dekker's two-product through a
+// fused multiply-add), sums Knuth's two-sum; each result is renormalised.
+// The relative error of a product or sum is a few units of 2^-46.
+struct ff {
+  float hi, lo;
+  ff() = default;
+  __device__ __forceinline__ ff(float h, float l) : hi(h), lo(l) {}
+  __device__ __forceinline__ ff(int v) : hi((float)v), lo(0.f) {}
+  __device__ __forceinline__ ff(double v) {
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+  }
+  __device__ __forceinline__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+
+__device__ __forceinline__ ff ff_renorm(float s, float e) {
+  const float h = s + e;
+  return ff(h, e - (h - s));
+}
+__device__ __forceinline__ ff operator+(ff a, ff b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  const float e = ((a.hi - (s - bb)) + (b.hi - bb)) + (a.lo + b.lo);
+  return ff_renorm(s, e);
+}
+__device__ __forceinline__ ff operator-(ff a) { return ff(-a.hi, -a.lo); }
+__device__ __forceinline__ ff operator*(ff a, ff b) {
+  const float p = a.hi * b.hi;
+  const float e = fmaf(a.hi, b.hi, -p) + fmaf(a.hi, b.lo, a.lo * b.hi);
+  return ff_renorm(p, e);
+}
+
+// a * b + c, fused where the type has a fused multiply-add
+__device__ __forceinline__ float fmad(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmad(double a, double b, double c) { return ::fma(a, b, c); }
+__device__ __forceinline__ ff fmad(ff a, ff b, ff c) { return a * b + c; }
+
+struct ff2 {
+  ff x, y;
+};
+
 template <class Real> struct Cx;
 template <> struct Cx<float> { using T = float2; };
 template <> struct Cx<double> { using T = double2; };
+template <> struct Cx<ff> { using T = ff2; };
 
 template <class Real>
 __device__ __forceinline__ typename Cx<Real>::T cmul(typename Cx<Real>::T a, typename Cx<Real>::T b) {
   typename Cx<Real>::T r;
-  r.x = fma(a.x, b.x, -a.y * b.y);
-  r.y = fma(a.x, b.y, a.y * b.x);
+  r.x = fmad(a.x, b.x, -a.y * b.y);
+  r.y = fmad(a.x, b.y, a.y * b.x);
   return r;
 }
 
@@ -99,6 +144,26 @@ template <> __device__ __forceinline__ void stv<float, 1>(float* d, int64_t e, c
 }
 template <> __device__ __forceinline__ void stv<double, 1>(double* d, int64_t e, const Pack<double, 1>& p) {
   *reinterpret_cast<double2*>(d + 2 * e) = p.c[0];
+}
+
+// Float pairs: one complex number is 16 bytes (re.hi, re.lo, im.hi, im.lo).
+__device__ __forceinline__ ff2 ff2_of(float4 v) { return ff2{ff(v.x, v.y), ff(v.z, v.w)}; }
+template <> __device__ __forceinline__ Pack<ff, 1> ldv<ff, 1, true>(const ff* d, int64_t e) {
+  return Pack<ff, 1>{{ff2_of(__ldcg(reinterpret_cast<const float4*>(d + 2 * e)))}};
+}
+template <> __device__ __forceinline__ Pack<ff, 1> ldv<ff, 1, false>(const ff* d, int64_t e) {
+  return Pack<ff, 1>{{ff2_of(*reinterpret_cast<const float4*>(d + 2 * e))}};
+}
+template <> __device__ __forceinline__ Pack<ff, 2> ldpair<ff, true>(const ff* d, int64_t e) {
+  return Pack<ff, 2>{{ff2_of(__ldcg(reinterpret_cast<const float4*>(d + 2 * e))),
+                      ff2_of(__ldcg(reinterpret_cast<const float4*>(d + 2 * e + 2)))}};
+}
+template <> __device__ __forceinline__ Pack<ff, 2> ldpair<ff, false>(const ff* d, int64_t e) {
+  return Pack<ff, 2>{{ff2_of(*reinterpret_cast<const float4*>(d + 2 * e)),
+                      ff2_of(*reinterpret_cast<const float4*>(d + 2 * e + 2))}};
+}
+template <> __device__ __forceinline__ void stv<ff, 1>(ff* d, int64_t e, const Pack<ff, 1>& p) {
+  *reinterpret_cast<float4*>(d + 2 * e) = make_float4(p.c[0].x.hi, p.c[0].x.lo, p.c[0].y.hi, p.c[0].y.lo);
 }
 
 // Input row index bits: pext(y, mask) from the precomputed runs.
@@ -969,7 +1034,7 @@ __device__ __forceinline__ void warp_tile(WarpTile* w, Real* __restrict__ data, 
     }
   }
   __syncwarp();
-  if (!GRAD || d.kind == kStepFwd) {
+  if (!GRAD || d.kind == kStepFwd) {  // (adjoint tiles below are compiled only into GRAD kernels)
     // STAGE 2: every forward tile of a row-wide or one-angle-set plan on the
     // lean row / pair path (the launcher picks STAGE 2 only for those
     // shapes; any other shape is reported, not computed); STAGE 0: the
@@ -985,20 +1050,24 @@ __device__ __forceinline__ void warp_tile(WarpTile* w, Real* __restrict__ data, 
       done = true;
     }
     if (!done) tile_items<Real, VB, PAIR, CG, 2, 0>(w, data, g, r0, r1, lane, rip, v0, lane_on, ctrl, dbg_bucket);
-  } else if (d.kind == kStepAdj) {
-    if (STAGE == 2 && PAIR && g.RP == 32 && g.VC == 1)
-      tile_adjoint_pairs<Real>(w, data, g, r0, r1, lane);
-    else if (STAGE == 2 && !PAIR && g.RP == 1 && g.VC == 1)
-      tile_adjoint_rows<Real, VB>(w, data, g, r0, r1, lane);
-    else
-      tile_adjoint<Real, VB, PAIR, CG, 2>(w, data, g, r0, r1, lane, rip, v0, lane_on, ctrl, dbg_bucket);
-  } else if (d.kind == kStepAdjRed) {
-    if (STAGE == 2 && PAIR && g.RP == 32 && g.VC == 1)
-      tile_adjred_pairs<Real>(w, data, g, r0, r1, lane);
-    else
-      tile_adjred<Real, VB, PAIR, CG, 2>(w, data, g, r0, r1, lane, rip, v0, lane_on, ctrl, dbg_bucket);
   } else {
-    tile_zero<Real, VB, PAIR, 2>(w, data, g, r0, r1, rip, v0, lane_on);
+    if constexpr (GRAD) {
+      if (d.kind == kStepAdj) {
+        if (STAGE == 2 && PAIR && g.RP == 32 && g.VC == 1)
+          tile_adjoint_pairs<Real>(w, data, g, r0, r1, lane);
+        else if (STAGE == 2 && !PAIR && g.RP == 1 && g.VC == 1)
+          tile_adjoint_rows<Real, VB>(w, data, g, r0, r1, lane);
+        else
+          tile_adjoint<Real, VB, PAIR, CG, 2>(w, data, g, r0, r1, lane, rip, v0, lane_on, ctrl, dbg_bucket);
+      } else if (d.kind == kStepAdjRed) {
+        if (STAGE == 2 && PAIR && g.RP == 32 && g.VC == 1)
+          tile_adjred_pairs<Real>(w, data, g, r0, r1, lane);
+        else
+          tile_adjred<Real, VB, PAIR, CG, 2>(w, data, g, r0, r1, lane, rip, v0, lane_on, ctrl, dbg_bucket);
+      } else {
+        tile_zero<Real, VB, PAIR, 2>(w, data, g, r0, r1, rip, v0, lane_on);
+      }
+    }
   }
 }
 

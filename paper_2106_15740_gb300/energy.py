@@ -12,7 +12,7 @@ import torch
 
 from . import binding as qb
 
-DTYPES = {"c128": qb.QT_C128, "c64": qb.QT_C64}
+DTYPES = {"c128": qb.QT_C128, "c64": qb.QT_C64, "c64x2": qb.QT_C64X2}
 MODES = {"per_bucket": qb.QT_MODE_PER_BUCKET, "persistent": qb.QT_MODE_PERSISTENT}
 QUEUE_ORDERS = {"round_robin": 0, "critical_path": 1}
 

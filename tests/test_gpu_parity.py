@@ -1,9 +1,10 @@
 """GPU parity: the CUDA path through the C ABI against the CPU oracle.
 
 Tolerances (from the precision of each path): |d<Z_j Z_k>| <= 1e-10 for
-complex128 and <= 1e-5 for complex64 (FP32 products, one FP32 add per
-bucket, FP64 edge product and energy sum); the whole graph's energy E to
-1e-9 (complex128) and 1e-5 (complex64).
+complex128 and for float pairs (c64x2, about 48 significant bits), <= 1e-5
+for complex64 (FP32 products, one FP32 add per bucket, FP64 edge product and
+energy sum); the whole graph's energy E to 1e-9 (complex128, float pairs)
+and 1e-5 (complex64).
 """
 import numpy as np
 import pytest
@@ -16,8 +17,8 @@ from workloads import complete_graph, erdos_renyi_graph, random_angles, random_r
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"c128": 1e-10, "c64": 1e-5}
-TOL_E = {"c128": 1e-9, "c64": 1e-5}
+TOL = {"c128": 1e-10, "c64": 1e-5, "c64x2": 1e-10}
+TOL_E = {"c128": 1e-9, "c64": 1e-5, "c64x2": 1e-9}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -71,7 +72,7 @@ def test_contract_p3_networks_c128():
 # ------------------------------------------------------------ energy plans --
 
 @pytest.mark.parametrize("mode", ["per_bucket", "persistent"])
-@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("dtype", ["c128", "c64", "c64x2"])
 def test_n16_p1_all_edges_vs_statevector(mode, dtype):
     n, edges, p, g, b = workload("n16_p1", batch=3)
     plan = _plan(n, edges, p, 3, dtype, mode)
@@ -84,7 +85,7 @@ def test_n16_p1_all_edges_vs_statevector(mode, dtype):
 
 
 @pytest.mark.parametrize("mode", ["per_bucket", "persistent"])
-@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("dtype", ["c128", "c64", "c64x2"])
 def test_n100_p3_all_edges_vs_oracle(mode, dtype):
     n, edges, p, g, b = workload("n100_p3")
     plan = _plan(n, edges, p, 1, dtype, mode)
@@ -124,8 +125,8 @@ def test_persistent_equals_per_bucket_bitwise():
     assert np.array_equal(out[0], out[1])
 
 
-@pytest.mark.parametrize("dtype", ["c128", "c64"])
-@pytest.mark.parametrize("batch", [1, 2, 3, 64])
+@pytest.mark.parametrize("dtype", ["c128", "c64", "c64x2"])
+@pytest.mark.parametrize("batch", [1, 2, 3, 32, 64])
 def test_lean_and_generic_tiles_agree_with_oracle(dtype, batch):
     """Every batch shape of the persistent launch (the lean pair tile for one
     angle set, the lean row tile for row-wide shapes, the generic tile
@@ -342,3 +343,17 @@ def test_per_width_chunks_are_bitwise_identical():
         plan.close()
     for e, zz in out[1:]:
         assert np.array_equal(zz, out[0][1]) and np.array_equal(e, out[0][0])
+
+
+def test_float_pairs_match_complex128_on_the_bench_workload():
+    """The float-pair precision on the bench workload (150 edges x 64 angle
+    sets, searched orders): every edge and energy against the complex128 plan
+    of the same orders, to 1e-10 per edge and 1e-9 per energy."""
+    n, edges, p, g, b = workload("n100_p4", batch=64)
+    out = {}
+    for dtype in ("c64x2", "c128"):
+        plan = _plan(n, edges, p, 64, dtype, "persistent", order_trials=100)
+        out[dtype] = _run(plan, g, b)
+        plan.close()
+    np.testing.assert_allclose(out["c64x2"][1], out["c128"][1], atol=1e-10, rtol=0)
+    np.testing.assert_allclose(out["c64x2"][0], out["c128"][0], atol=1e-9, rtol=0)
