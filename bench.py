@@ -728,7 +728,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=None, help="profiling only: angle sets per GPU")
     ap.add_argument("--workload", default=None, help="profiling only: named workload of workloads.py")
-    ap.add_argument("--dtype", default=None, choices=["c64", "c128"], help="profiling only")
+    ap.add_argument("--dtype", default=None, choices=["c64", "c128", "c64x2"], help="profiling only")
     ap.add_argument("--edges", default=None, help="profiling only: edge range a:b of the graph")
     ap.add_argument("--lane-items", type=int, default=0, help="profiling only: warp tile items per lane")
     ap.add_argument("--group-rows", type=int, default=0, help="profiling only: grouping threshold")
