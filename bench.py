@@ -43,14 +43,11 @@ WORKLOAD = dict(name="n100_p4", batch=64, dtype="c64", order_trials=100)
 # what shares L2): otherwise the traffic is reported as null until that kernel
 # and plan are captured again.
 TRAFFIC_CAPTURES = [
-    # orders searched per edge (100 trials), the bench plan; register load path (lean row
-    # tile); steps wait for the dependencies found from the elements they touch; the queue
-    # takes the longest remaining dependency path first (the default) or the slots round-robin.
-    # Captured at digest 63c2243c03f50613; only comments of those sources changed since.
-    {"sources_sha256_16": "3cb853ff50c29a4c", "alg_bytes_per_angle_set": 5170666432 / 4,
-     "queue_order": "critical_path", "bytes_per_angle_set": (2308382464 + 2503696896) / 4},
-    {"sources_sha256_16": "3cb853ff50c29a4c", "alg_bytes_per_angle_set": 5170666432 / 4,
-     "queue_order": "round_robin", "bytes_per_angle_set": (2184769024 + 2472729344) / 4},
+    # orders searched per edge (100 trials), the bench plan; the queue takes the longest
+    # remaining dependency path first (the default); fixed-fan-in row tile, task records
+    # carrying dependency lists (profiles/persistent_kernel_n100p4_b4_dram.md).
+    {"sources_sha256_16": "eccc125112799279", "alg_bytes_per_angle_set": 5170666432 / 4,
+     "queue_order": "critical_path", "bytes_per_angle_set": (2322033664 + 2500920320) / 4},
 ]
 
 

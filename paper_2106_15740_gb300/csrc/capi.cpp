@@ -274,10 +274,14 @@ static qt_status check_options(const qt_plan_options* opt, qt_plan_options* out)
   if (o.max_width <= 0 || o.max_width > 31) o.max_width = 31;
   if (o.lane_items > 0 && o.lane_items != 8 && o.lane_items != 16 && o.lane_items != 32 && o.lane_items != 64)
     return fail(QT_EINVAL, "lane_items must be 8, 16, 32 or 64");
-  // by batch: one angle set takes 32 passes of 32 rows per tile (measured on the 60-vertex p = 4
-  // graph: 16 passes 1.99 / 10.3 ms, 32 passes 1.72 / 9.10 ms, 64 passes 2.00 / 10.3 ms for the
-  // energy / energy + gradient); 2..15 angle sets 16 items, 16 or more 32
-  if (o.lane_items <= 0) o.lane_items = (o.batch >= 16 || o.batch == 1) ? 32 : 16;
+  // by batch: one angle set in a complex64 persistent plan takes 32 passes of 32 rows per tile
+  // (measured on the 60-vertex p = 4 graph: 16 passes 1.99 / 10.3 ms, 32 passes 1.72 / 9.10 ms,
+  // 64 passes 2.00 / 10.3 ms for the energy / energy + gradient); complex128 and float pairs, whose
+  // tiles take longer, and the per-bucket launches keep 16 (32 made them slower: per-bucket
+  // complex128 loop 19.4 -> 31.1 s per bench step, complex128 amplitudes 5.1 -> 6.3 ms);
+  // 2..15 angle sets 16 items, 16 or more 32
+  if (o.lane_items <= 0)
+    o.lane_items = (o.batch >= 16 || (o.batch == 1 && o.dtype == QT_C64 && o.mode == QT_MODE_PERSISTENT)) ? 32 : 16;
   if (o.order_trials < 0 || o.order_trials > 100000) return fail(QT_EINVAL, "order_trials must be in [0, 100000]");
   if (!(o.order_tau >= 0.0) || !std::isfinite(o.order_tau)) return fail(QT_EINVAL, "order_tau must be finite and >= 0");
   if (o.checkpoint_bytes < 0) return fail(QT_EINVAL, "checkpoint_bytes must be >= 0");

@@ -17,63 +17,92 @@ namespace dev {
 // larger of |cos t|, |sin t| is stepped over the floats within kUnitSearch
 // ulps of its rounded value, the other component is the float nearest to
 // the same ratio, and the candidate with the smallest angle |t' - t| (from
-// the cross and dot products with (cos t, sin t), in FP64) wins.  Nearest
+// its cross product with (cos t, sin t), in FP64) wins.  Nearest
 // rounding of both leaves up to about 4e-8 rad of angle error and a norm
 // error of the same size; the search brings the angle error under about
 // 1.5e-8 rad at every angle (less where the two components' grids do not
 // step together), and the norm error is divided out per network in FP64
 // (energy_kernel and leafgrad_kernel, with the network's leaf counts).
+// The search runs a warp per angle: FP64 arithmetic is scarce on this GPU
+// and a thread per angle took 0.22 ms of the bench step.
 constexpr int kUnitSearch = 48;
 
 __device__ __forceinline__ float step_ulps(float x, int k) { return __int_as_float(__float_as_int(x) + k); }
 
-__device__ void unit_pair_f32(double t, double* c_out, double* s_out, double* log_r) {
+// One warp searches the float pair of one angle t: lane l tries the
+// candidates j = l, l + 32, l + 64 (< 2 kUnitSearch + 1; candidate j steps the
+// larger component by k = 0, 1, -1, 2, -2, ... ulps), scoring |cross product|
+// with (cos t, sin t) (the angle error times the pair's length, which is 1 to
+// within 2e-6 on all candidates) plus 1e-12 |k|, so near-ties go to the nearest
+// float; a warp argmin (smallest score, then smallest j) picks the pair.
+__device__ void unit_pair_f32_warp(double t, int lane, double* c_out, double* s_out, double* log_r) {
   double st, ct;
   sincos(t, &st, &ct);
   const bool cbig = fabs(ct) >= fabs(st);
   const double big = cbig ? ct : st, small = cbig ? st : ct;
   const double ratio = small / big;
   const float b0 = (float)big;  // |big| >= 1/sqrt(2): stepping its bits never crosses zero
-  float bb = b0, sb = (float)small;
-  double best = -1.0;
-  for (int j = 0; j <= 2 * kUnitSearch; ++j) {  // k = 0, 1, -1, 2, -2, ...: ties keep the nearest
+  double best = 1e300;
+  int best_j = 1 << 30;
+  for (int j = lane; j <= 2 * kUnitSearch; j += 32) {
     const int k = (j & 1) ? (j + 1) / 2 : -(j / 2);
     const float bk = step_ulps(b0, k);
     const float sk = (float)((double)bk * ratio);
-    const double cross = (double)sk * big - (double)bk * small;
-    const double dot = (double)bk * big + (double)sk * small;
-    const double err = fabs(cross / dot) + 1e-12 * (double)abs(k);  // near-ties go to the nearest float
-    if (best < 0.0 || err < best) {
+    const double err = fabs(fma((double)sk, big, -(double)bk * small)) + 1e-12 * (double)abs(k);
+    if (err < best) {
       best = err;
-      bb = bk;
-      sb = sk;
+      best_j = j;
     }
   }
+  for (int off = 16; off >= 1; off >>= 1) {
+    const double ob = __shfl_xor_sync(0xffffffffu, best, off);
+    const int oj = __shfl_xor_sync(0xffffffffu, best_j, off);
+    if (ob < best || (ob == best && oj < best_j)) {
+      best = ob;
+      best_j = oj;
+    }
+  }
+  const int k = (best_j & 1) ? (best_j + 1) / 2 : -(best_j / 2);
+  const float bb = step_ulps(b0, k);
+  const float sb = (float)((double)bb * ratio);
   const double c = cbig ? (double)bb : (double)sb, s = cbig ? (double)sb : (double)bb;
   *c_out = c;
   *s_out = s;
   *log_r = 0.5 * log(c * c + s * s);
 }
 
-template <class Real>
-__global__ void trig_kernel(const double* __restrict__ gamma, const double* __restrict__ beta, int32_t p,
-                            int32_t B, double* __restrict__ trig) {
+// complex128 (and float pairs): one thread per (angle set, layer)
+__global__ void trig_kernel_f64(const double* __restrict__ gamma, const double* __restrict__ beta, int32_t p,
+                                int32_t B, double* __restrict__ trig) {
   const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= B * p) return;
   double* t = trig + (int64_t)kTrigStride * i;
-  if (sizeof(Real) == sizeof(double)) {
-    double sg, cg, sb, cb;
-    sincos(gamma[i], &sg, &cg);
-    sincos(beta[i], &sb, &cb);
-    t[0] = cg;
-    t[1] = sg;
-    t[2] = cb;
-    t[3] = sb;
-    t[4] = 0.0;
-    t[5] = 0.0;
-  } else {
-    unit_pair_f32(gamma[i], &t[0], &t[1], &t[4]);
-    unit_pair_f32(beta[i], &t[2], &t[3], &t[5]);
+  double sg, cg, sb, cb;
+  sincos(gamma[i], &sg, &cg);
+  sincos(beta[i], &sb, &cb);
+  t[0] = cg;
+  t[1] = sg;
+  t[2] = cb;
+  t[3] = sb;
+  t[4] = 0.0;
+  t[5] = 0.0;
+}
+
+// complex64: one warp per (angle set, layer, gamma or beta)
+__global__ void trig_kernel_f32(const double* __restrict__ gamma, const double* __restrict__ beta, int32_t p,
+                                int32_t B, double* __restrict__ trig) {
+  const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wg >= 2 * (int64_t)B * p) return;  // whole warps leave together
+  const int32_t i = (int32_t)(wg >> 1);
+  const bool is_beta = wg & 1;
+  double c, s, lr;
+  unit_pair_f32_warp(is_beta ? beta[i] : gamma[i], lane, &c, &s, &lr);
+  if (lane == 0) {
+    double* t = trig + (int64_t)kTrigStride * i;
+    t[is_beta ? 2 : 0] = c;
+    t[is_beta ? 3 : 1] = s;
+    t[is_beta ? 5 : 4] = lr;
   }
 }
 
@@ -514,7 +543,7 @@ __device__ __forceinline__ double2 leaf_deriv(uint32_t w, uint32_t z, const doub
 // warp with shuffles.
 //
 // The parts are divided by the factor's network's stored-gate norm product
-// (complex64, see trig_kernel): to first order that is the derivative of the
+// (complex64, see trig_kernel_f32): to first order that is the derivative of the
 // exact network at the stored angles.
 template <class Real>
 __global__ void leafgrad_kernel(const DevLeafFactor* __restrict__ lf, int32_t n_lf, int64_t lbar_shift,
@@ -608,10 +637,12 @@ __global__ void gradreduce_kernel(const double* __restrict__ dz, int32_t n_edges
 cudaError_t launch_trig(int dtype, const double* gamma, const double* beta, int32_t p, int32_t B, double* trig,
                         cudaStream_t s) {
   const int32_t n = B * p;
-  if (dtype == QT_C64)
-    dev::trig_kernel<float><<<(n + 127) / 128, 128, 0, s>>>(gamma, beta, p, B, trig);
-  else
-    dev::trig_kernel<double><<<(n + 127) / 128, 128, 0, s>>>(gamma, beta, p, B, trig);
+  if (dtype == QT_C64) {
+    const int64_t threads = (int64_t)n * 2 * 32;  // a warp per (angle set, layer, gamma or beta)
+    dev::trig_kernel_f32<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(gamma, beta, p, B, trig);
+  } else {
+    dev::trig_kernel_f64<<<(n + 127) / 128, 128, 0, s>>>(gamma, beta, p, B, trig);
+  }
   return cudaGetLastError();
 }
 

@@ -105,7 +105,7 @@ struct DevLeafFactor {
 
 // Angle table: per angle set b and layer q, kTrigStride doubles at
 // trig[(b * p + q) * kTrigStride]: cos g, sin g, cos b, sin b (the values the
-// leaves take), log r_g, log r_b (see trig_kernel: each stored gate is
+// leaves take), log r_g, log r_b (see trig_kernel_f32: each stored gate is
 // r times the exact gate at a nearby angle; complex128 plans have r = 1).
 constexpr int kTrigStride = 6;
 
