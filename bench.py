@@ -491,7 +491,7 @@ def amplitude_measure(dev, torch):
     amplitude of the full circuit of a random 3-regular graph, 40 vertices,
     p = 3, the depth the paper reaches on a 4 GB laptop with ZZ and diagonal
     gates): 8 seeded bitstrings, one angle set, complex128 (the paper's
-    precision) and complex64, searched orders."""
+    precision), float pairs and complex64, searched orders."""
     import numpy as np
     from paper_2106_15740_gb300.amplitude import AmplitudePlan
     from workloads import random_angles, random_regular_graph
@@ -502,7 +502,7 @@ def amplitude_measure(dev, torch):
     gd, bd = torch.tensor(g, device=dev), torch.tensor(b, device=dev)
     out = {"workload": "random 3-regular N=40 p=3 (seed 0), 8 bitstrings x 1 angle set, full-circuit ket networks, "
                        "100 order trials per bitstring"}
-    for dtype in ("c128", "c64"):
+    for dtype in ("c128", "c64x2", "c64"):
         plan = AmplitudePlan(n, edges, p, bits, batch=1, dtype=dtype, order_trials=100, device=dev)
         for _ in range(2):
             plan.amplitudes(gd, bd)

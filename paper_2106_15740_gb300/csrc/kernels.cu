@@ -726,14 +726,14 @@ cudaError_t launch_bucket(int dtype, const DevBucket& d, int32_t B, int32_t lane
   return cudaGetLastError();
 }
 
-// Row-wide tile shapes (one output row per pass, one vector chunk per row:
-// complex64 with even B in [34, 64], complex128 with B in [17, 32]) take the
-// lean row tile; one angle set takes the lean pair tile; other batches the
-// generic register tile.
+// Row-wide tile shapes (one output row per pass: complex64 with even B in
+// [34, 64], complex128 with B in [17, 32], float pairs with B in [17, 64], one
+// or two vector chunks per row) take the lean row tiles; one angle set takes
+// the lean pair tile; other batches the generic register tile.
 bool row_wide(int dtype, int32_t B) {
   if (B <= 1 || !(dtype == QT_C128 || dtype == QT_C64X2 || vector_width(dtype, B) == 2)) return false;
   const TileGeom g = tile_geom(dtype, B, 0);
-  return g.RP == 1 && g.VC == 1;
+  return g.RP == 1 && (g.VC == 1 || (g.VC == 2 && dtype == QT_C64X2));
 }
 
 template <class Real, int VB, bool PAIR, bool GRAD, int ST>
@@ -757,7 +757,8 @@ static const void* persistent_fn_g(int dtype, int32_t B) {
       return nullptr;
     } else {
       if (pair) return pk_fn<dev::ff, 1, true, false, 2>();
-      return lean ? pk_fn<dev::ff, 1, false, false, 2>() : pk_fn<dev::ff, 1, false, false, 0>();
+      if (!lean) return pk_fn<dev::ff, 1, false, false, 0>();
+      return tile_geom(dtype, B, 0).VC == 2 ? pk_fn<dev::ff, 1, false, false, 3>() : pk_fn<dev::ff, 1, false, false, 2>();
     }
   }
   if (pair) return pk_fn<double, 1, true, GRAD, 2>();

@@ -598,6 +598,60 @@ __device__ __forceinline__ void tile_rows_regs(WarpTile* w, Real* __restrict__ d
   }
 }
 
+// Row-wide forward tile with two vector chunks per row (RP = 1, VC = 2: 33 to
+// 64 vectors of angle sets, lane l on vectors l and l + 32 of the same output
+// row), one row per iteration: the same loads and products as tile_items,
+// bit-identical to it, with the operand rows read straight from the pass
+// table.  Used for float pairs at 33-64 angle sets (STAGE 3): 67.0 -> 57.9 ms
+// on the 100-vertex p = 4 graph at 64 angle sets.  Complex128 keeps the generic
+// tile there (this one made it slower, 129 -> 207 ms: its FP64 arithmetic sets
+// the pace, and one row per iteration exposes it), and so does complex64.
+template <class Real, int VB>
+__device__ __forceinline__ void tile_rows_vc2(WarpTile* w, Real* __restrict__ data, const TileGeom& g, int64_t r0,
+                                              int64_t r1, int lane) {
+  using PK = Pack<Real, VB>;
+  const DevBucket& d = w->d;
+  const int n_in = d.n_in;
+  const int nrows = (int)(r1 - r0);
+  const bool on1 = lane + 32 < g.Bv;  // (lane < Bv always: Bv > 32)
+  const int64_t B = g.B;
+  const int64_t lo0 = (int64_t)lane * VB;
+  const int64_t lo1 = (int64_t)(on1 ? lane + 32 : lane) * VB;  // idle chunk lanes reread chunk 0, store nothing
+  for (int q = 0; q < nrows; ++q) {
+    PK p0[2], p1[2];
+#pragma unroll 1
+    for (int i = 0; i < n_in; ++i) {
+      const bool leaf = d.in[i].flags & kInLeaf;
+      const int64_t e = d.in[i].off + (int64_t)(2 * w->tab[i][q]) * B;
+      const PK a00 = ldv_in<Real, VB, true>(data, e + lo0, leaf);
+      const PK a01 = ldv_in<Real, VB, true>(data, e + B + lo0, leaf);
+      const PK a10 = ldv_in<Real, VB, true>(data, e + lo1, leaf);
+      const PK a11 = ldv_in<Real, VB, true>(data, e + B + lo1, leaf);
+      if (i == 0) {
+        p0[0] = a00;
+        p1[0] = a01;
+        p0[1] = a10;
+        p1[1] = a11;
+      } else {
+        pmul<Real, VB>(p0[0], a00);
+        pmul<Real, VB>(p1[0], a01);
+        pmul<Real, VB>(p0[1], a10);
+        pmul<Real, VB>(p1[1], a11);
+      }
+    }
+    const int64_t row = d.out_off + (r0 + q) * B;
+    PK o;
+#pragma unroll
+    for (int v = 0; v < VB; ++v) o.c[v] = cadd<Real>(p0[0].c[v], p1[0].c[v]);
+    stv<Real, VB>(data, row + lo0, o);
+    if (on1) {
+#pragma unroll
+      for (int v = 0; v < VB; ++v) o.c[v] = cadd<Real>(p0[1].c[v], p1[1].c[v]);
+      stv<Real, VB>(data, row + lo1, o);
+    }
+  }
+}
+
 // Forward tile of the one-angle-set layout on the register path (PAIR: B = 1,
 // rows x = 0, 1 of an input adjacent; RP = 32 rows per pass, lane l on row
 // r0 + pass * 32 + l).  The same loads and products as tile_items,
@@ -1122,6 +1176,14 @@ __device__ __forceinline__ void warp_tile(WarpTile* w, Real* __restrict__ data, 
         tile_pairs_regs<Real>(w, data, g, r0, r1, lane);
       else if (!PAIR && g.RP == 1 && g.VC == 1)
         tile_rows_regs<Real, VB>(w, data, g, r0, r1, lane);
+      else if (lane == 0 && ctrl != nullptr)
+        atomicCAS(&ctrl->status, 0, (int32_t)QT_EINVAL);
+      done = true;
+    }
+    if (STAGE == 3) {  // float pairs with two vector chunks per row (a kernel of its own: compiled
+                       // into the STAGE 2 kernel, this tile raised that kernel's spills)
+      if (!PAIR && g.RP == 1 && g.VC == 2)
+        tile_rows_vc2<Real, VB>(w, data, g, r0, r1, lane);
       else if (lane == 0 && ctrl != nullptr)
         atomicCAS(&ctrl->status, 0, (int32_t)QT_EINVAL);
       done = true;
