@@ -48,6 +48,9 @@ TRAFFIC_CAPTURES = [
     # carrying dependency lists (profiles/persistent_kernel_n100p4_b4_dram.md).
     {"sources_sha256_16": "eccc125112799279", "alg_bytes_per_angle_set": 5170666432 / 4,
      "queue_order": "critical_path", "bytes_per_angle_set": (2322033664 + 2500920320) / 4},
+    # the same after the warp-per-angle table search and the float-pair two-chunk tile
+    {"sources_sha256_16": "cd11e675aaf9e03a", "alg_bytes_per_angle_set": 5170666432 / 4,
+     "queue_order": "critical_path", "bytes_per_angle_set": (2330160896 + 2504982528) / 4},
 ]
 
 
