@@ -639,10 +639,21 @@ qt_status compile_plan(Plan* P) {
         // tile per (target row, chunk of completions); smaller targets keep the
         // atomic scatter, whose contention is then at most 32 per element
         d.kind = kStepAdjRed;
-        d.in[n + 1] = input_record(all & ~tmask, 0, 0);  // complement record
-        d.tgt_bits = __builtin_popcount(tmask);
-        d.comp_bits = __builtin_popcount(all & ~tmask);
-        d.n_rows = (int64_t)1 << (d.tgt_bits + d.comp_bits);  // = 2^out_rank
+        if (B == 1 && n + 3 <= kDevMaxIn) {
+          // one angle set: lanes on the bucket's five lowest variables (bk.out_rank >= 5 here),
+          // the pass index on the completion bits above them, then the target bits
+          const uint32_t comp = all & ~tmask;
+          d.aflags |= kAdjRedLow;
+          d.in[n + 1] = input_record(comp & ~31u, 0, 0);
+          d.in[n + 2] = input_record(tmask & ~31u, 0, 0);
+          d.comp_bits = __builtin_popcount(comp & ~31u);
+          d.tgt_bits = __builtin_popcount(tmask & ~31u);
+        } else {
+          d.in[n + 1] = input_record(all & ~tmask, 0, 0);  // complement record
+          d.tgt_bits = __builtin_popcount(tmask);
+          d.comp_bits = __builtin_popcount(all & ~tmask);
+        }
+        d.n_rows = (int64_t)1 << bk.out_rank;
       }
       P->buckets.push_back(d);
       if (op.gbar >= 0) touch(rbase + op.gbar, bk.out_rank > 0 ? tensor_el(op.bucket) : 2 * B, false);

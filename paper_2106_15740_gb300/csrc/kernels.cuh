@@ -243,18 +243,19 @@ struct WarpTile {
 };
 
 // Copy a bucket record into the warp's shared slot with typed member
-// assignments (lane i < n_in copies input i, lane 31 the header), so every
-// later read of the slot sees the stores through its own type.  Call with
-// all 32 lanes; the caller synchronises the warp before reading the slot.
+// assignments (lane i < kDevMaxIn copies input slot i, lane 31 the header),
+// so every later read of the slot sees the stores through its own type.  Call
+// with all 32 lanes; the caller synchronises the warp before reading the
+// slot.  Every input slot is copied (the host zero-fills unused ones), so the
+// records a step reads past its factors (target, completion and chain
+// records) never come from an earlier step.
 __device__ __forceinline__ void load_bucket(DevBucket* dst, const DevBucket* src, int lane) {
-  const int n_in = src->n_in;
-  const int n_rec = src->kind == kStepAdj ? n_in + 1 : (src->kind == kStepAdjRed ? n_in + 2 : n_in);
-  if (lane < kDevMaxIn && lane < n_rec) dst->in[lane] = src->in[lane];
+  if (lane < kDevMaxIn) dst->in[lane] = src->in[lane];
   if (lane == 31) {
     dst->out_off = src->out_off;
     dst->n_rows = src->n_rows;
     dst->out_rank = src->out_rank;
-    dst->n_in = n_in;
+    dst->n_in = src->n_in;
     dst->dep = src->dep;
     dst->ntask = src->ntask;
     dst->kind = src->kind;
@@ -317,12 +318,13 @@ __device__ __forceinline__ void lane_parts(WarpTile* w, const TileGeom& g, int l
   int rip, v0;
   bool on;
   lane_slot(g, lane, &rip, &v0, &on);
-  if (w->d.kind == kStepAdjRed) {  // lanes index completions: part of y = pdep(i_lane, complement)
+  const bool red_low = w->d.kind == kStepAdjRed && (w->d.aflags & kAdjRedLow);
+  if (w->d.kind == kStepAdjRed && !red_low) {  // lanes index completions: part of y = pdep(i_lane, complement)
     const uint32_t ylane = pdep_in((uint32_t)rip, w->d.in[w->d.n_in + 1]);
     for (int i = 0; i < w->d.n_in; ++i) w->lpart[i][lane] = pext_in(ylane, w->d.in[i]);
     return;
   }
-  const int n_rec = w->d.kind == kStepAdj ? w->d.n_in + 1 : w->d.n_in;
+  const int n_rec = w->d.kind == kStepAdj || red_low ? w->d.n_in + 1 : w->d.n_in;
   for (int i = 0; i < n_rec; ++i) w->lpart[i][lane] = pext_in((uint32_t)rip, w->d.in[i]);
 }
 
@@ -720,6 +722,26 @@ __device__ __forceinline__ void atomic_add_cx(Real* data, int64_t e, typename Cx
   atomicAdd(data + 2 * e + 1, v.y);
 }
 
+// Atomic add of two adjacent complex numbers (elements e0, e0 + 1).  In
+// complex64 at an even e0 (the pair's 16 bytes aligned: every tensor starts
+// 256-byte aligned and a pair row at an even element) this is one 16-byte
+// vector atomic instead of four scalar ones.
+template <class Real>
+__device__ __forceinline__ void atomic_add_pair(Real* data, int64_t e0, typename Cx<Real>::T c0,
+                                                typename Cx<Real>::T c1) {
+  atomic_add_cx<Real>(data, e0, c0);
+  atomic_add_cx<Real>(data, e0 + 1, c1);
+}
+template <>
+__device__ __forceinline__ void atomic_add_pair<float>(float* data, int64_t e0, float2 c0, float2 c1) {
+  if ((e0 & 1) == 0) {
+    atomicAdd(reinterpret_cast<float4*>(data + 2 * e0), make_float4(c0.x, c0.y, c1.x, c1.y));
+  } else {
+    atomic_add_cx<float>(data, e0, c0);
+    atomic_add_cx<float>(data, e0 + 1, c1);
+  }
+}
+
 // Adjoint step (kStepAdj) on the lean paths: the same factors, products,
 // target rows and stores or atomic adds as tile_adjoint, several rows per
 // iteration, addressed straight from the pass table.  Factors flagged
@@ -778,8 +800,7 @@ __device__ __forceinline__ void tile_adjoint_pairs(WarpTile* w, Real* __restrict
         stv<Real, 1>(data, e0, p0[u]);
         stv<Real, 1>(data, e0 + 1, p1[u]);
       } else {
-        atomic_add_cx<Real>(data, e0, p0[u].c[0]);
-        atomic_add_cx<Real>(data, e0 + 1, p1[u].c[0]);
+        atomic_add_pair<Real>(data, e0, p0[u].c[0], p1[u].c[0]);
       }
     }
   }
@@ -836,6 +857,9 @@ __device__ __forceinline__ void tile_adjoint_rows(WarpTile* w, Real* __restrict_
       if (full) {
         stv<Real, VB>(data, e0, p0[u]);
         stv<Real, VB>(data, e0 + B, p1[u]);
+      } else if (VB == 2) {  // a lane's two angle sets are adjacent elements
+        atomic_add_pair<Real>(data, e0, p0[u].c[0], p0[u].c[VB - 1]);
+        atomic_add_pair<Real>(data, e0 + B, p1[u].c[0], p1[u].c[VB - 1]);
       } else {
 #pragma unroll
         for (int v = 0; v < VB; ++v) {
@@ -1002,6 +1026,10 @@ __device__ __forceinline__ void tile_adjred(WarpTile* w, Real* __restrict__ data
                                             int64_t r1, int lane, int rip, int v0, bool lane_on, DevCtrl* ctrl,
                                             int dbg_bucket) {
   const DevBucket& d = w->d;
+  if (d.aflags & kAdjRedLow) {  // the one-angle-set lane form: the pair tiles evaluate it, never this one
+    if (lane == 0 && ctrl != nullptr) atomicCAS(&ctrl->status, 0, (int32_t)QT_EINVAL);
+    return;
+  }
   const int n_in = d.n_in;
   const int Q = g.P * g.VC;  // VC == 1 here (Bv <= 32)
   const int seg = (1 << d.comp_bits) / g.RP < Q ? (1 << d.comp_bits) / g.RP : Q;  // passes per target row
@@ -1052,6 +1080,46 @@ __device__ __forceinline__ void tile_adjred(WarpTile* w, Real* __restrict__ data
   }
 }
 
+// End of a target group of a one-angle-set reduction step (pass q of the tile
+// at r0 is its last): the lanes' sums s0, s1 (x = 0, 1) are summed over the
+// lanes that share a target and added to the target's adjoint, and reset.
+// Lanes on completions (the default form): one target per group, lane 0 adds.
+// kAdjRedLow: lanes on the bucket's five lowest variables; a butterfly over
+// the lane bits that are completion bits, then every lane whose completion
+// bits are 0 adds its own target element (target row from the pass table).
+template <class Real>
+__device__ __forceinline__ void adjred_pairs_flush(const WarpTile* w, Real* __restrict__ data, int64_t r0, int q,
+                                                   int lane, Pack<Real, 1>& s0, Pack<Real, 1>& s1) {
+  const DevBucket& d = w->d;
+  if (d.aflags & kAdjRedLow) {
+    const uint32_t cl = ~d.in[d.n_in].mask & 31u;  // completion bits among the lane bits (warp-uniform)
+#pragma unroll
+    for (int b = 0; b < 5; ++b) {
+      if (!((cl >> b) & 1u)) continue;
+      s0.c[0].x += __shfl_xor_sync(0xffffffffu, s0.c[0].x, 1 << b);
+      s0.c[0].y += __shfl_xor_sync(0xffffffffu, s0.c[0].y, 1 << b);
+      s1.c[0].x += __shfl_xor_sync(0xffffffffu, s1.c[0].x, 1 << b);
+      s1.c[0].y += __shfl_xor_sync(0xffffffffu, s1.c[0].y, 1 << b);
+    }
+    if (((uint32_t)lane & cl) == 0u)
+      atomic_add_pair<Real>(data, d.out_off + 2 * (int64_t)(w->tab[d.n_in][q] + w->lpart[d.n_in][lane]), s0.c[0],
+                            s1.c[0]);
+  } else {
+    const uint32_t kt = (uint32_t)((r0 + (int64_t)q * 32) >> d.comp_bits);
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+      s0.c[0].x += __shfl_xor_sync(0xffffffffu, s0.c[0].x, off);
+      s0.c[0].y += __shfl_xor_sync(0xffffffffu, s0.c[0].y, off);
+      s1.c[0].x += __shfl_xor_sync(0xffffffffu, s1.c[0].x, off);
+      s1.c[0].y += __shfl_xor_sync(0xffffffffu, s1.c[0].y, off);
+    }
+    if (lane == 0) atomic_add_pair<Real>(data, d.out_off + 2 * (int64_t)kt, s0.c[0], s1.c[0]);
+  }
+  s0.c[0].x = 0;
+  s0.c[0].y = 0;
+  s1 = s0;
+}
+
 // Reduction adjoint step (kStepAdjRed) of the one-angle-set layout (PAIR,
 // RP = 32: lane l on completion c = l of pass pp, all lanes of a pass on the
 // same target row kt, which changes every 2^comp_bits / 32 passes).  The same
@@ -1068,7 +1136,7 @@ __device__ __forceinline__ void tile_adjred_pairs(WarpTile* w, Real* __restrict_
   constexpr int U = AdjRedPasses<Real>::value;
   const DevBucket& d = w->d;
   const int n_in = d.n_in;
-  const int seg = (1 << d.comp_bits) / 32;  // passes per target row (>= 1)
+  const int seg = (d.aflags & kAdjRedLow) ? 1 << d.comp_bits : (1 << d.comp_bits) / 32;  // passes per target group
   P1 s0, s1;
   s0.c[0].x = 0;
   s0.c[0].y = 0;
@@ -1116,24 +1184,130 @@ __device__ __forceinline__ void tile_adjred_pairs(WarpTile* w, Real* __restrict_
         s0.c[0] = cadd<Real>(s0.c[0], p0[u].c[0]);
         s1.c[0] = cadd<Real>(s1.c[0], p1[u].c[0]);
       }
-      if ((q + 1) % seg == 0 || q + 1 == g.P || r0 + (int64_t)(q + 1) * 32 >= r1) {  // end of a target row's passes
-        const uint32_t kt = (uint32_t)((r0 + (int64_t)q * 32) >> d.comp_bits);
+      if ((q + 1) % seg == 0 || q + 1 == g.P || r0 + (int64_t)(q + 1) * 32 >= r1)  // end of a target group's passes
+        adjred_pairs_flush<Real>(w, data, r0, q, lane, s0, s1);
+    }
+  }
+}
+
+// Adjoint steps of the one-angle-set layout with the factor count NF fixed at
+// compile time (2 to 4 factors: the output adjoint, then the bucket's other
+// inputs, each a pair of rows x = 0, 1).  The same loads, products and stores or atomic adds as
+// tile_adjoint_pairs and tile_adjred_pairs, but every factor's loads of U
+// passes are issued before the first product: U * NF loads in flight per lane
+// and one memory round trip per U passes, where the rolled factor loop makes
+// NF round trips.  AdjNfPasses keeps the loaded values within the 64-register
+// budget.
+template <class Real, int NF> struct AdjNfPasses {
+  static constexpr int value = sizeof(Real) == 4 ? 2 : (NF <= 2 ? 2 : 1);
+};
+
+template <class Real, int NF, int U>
+__device__ __forceinline__ void load_factors_nf(const WarpTile* w, const Real* __restrict__ data, int pp,
+                                                const bool (&ok)[U], const uint32_t (&lp)[NF],
+                                                Pack<Real, 1> (&p0)[U], Pack<Real, 1> (&p1)[U]) {
+  const DevBucket& d = w->d;
+  Pack<Real, 1> g0[U];  // factor 0, the output adjoint: one value for x = 0 and x = 1
+  Pack<Real, 2> q[NF - 1][U];
 #pragma unroll
-        for (int off = 16; off >= 1; off >>= 1) {
-          s0.c[0].x += __shfl_xor_sync(0xffffffffu, s0.c[0].x, off);
-          s0.c[0].y += __shfl_xor_sync(0xffffffffu, s0.c[0].y, off);
-          s1.c[0].x += __shfl_xor_sync(0xffffffffu, s1.c[0].x, off);
-          s1.c[0].y += __shfl_xor_sync(0xffffffffu, s1.c[0].y, off);
-        }
-        if (lane == 0) {
-          const int64_t e0 = d.out_off + 2 * (int64_t)kt;
-          atomic_add_cx<Real>(data, e0, s0.c[0]);
-          atomic_add_cx<Real>(data, e0 + 1, s1.c[0]);
-        }
-        s0.c[0].x = 0;
-        s0.c[0].y = 0;
-        s1 = s0;
+  for (int u = 0; u < U; ++u) {
+    const uint32_t k = ok[u] ? w->tab[0][pp + u] + lp[0] : 0u;  // idle items read row 0
+    g0[u] = ldv_in<Real, 1, true>(data, d.in[0].off + (int64_t)k, d.in[0].flags & kInLeaf);
+  }
+#pragma unroll
+  for (int i = 1; i < NF; ++i) {
+    const bool leaf = d.in[i].flags & kInLeaf;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint32_t k = ok[u] ? w->tab[i][pp + u] + lp[i] : 0u;
+      q[i - 1][u] = ldpair_in<Real, true>(data, d.in[i].off + 2 * (int64_t)k, leaf);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    p0[u] = g0[u];
+    p1[u] = g0[u];
+#pragma unroll
+    for (int i = 1; i < NF; ++i) {
+      Pack<Real, 1> a0, a1;
+      a0.c[0] = q[i - 1][u].c[0];
+      a1.c[0] = q[i - 1][u].c[1];
+      pmul<Real, 1>(p0[u], a0);
+      pmul<Real, 1>(p1[u], a1);
+    }
+  }
+}
+
+// Whether the adjoint step in w->d has the factor form of the NF tiles: the
+// output adjoint first (one value per output row), every other factor a pair.
+__device__ __forceinline__ bool adj_nf_form(const DevBucket& d) {
+  if (d.n_in < 2 || d.n_in > 4 || !(d.in[0].flags & kInNoPair)) return false;
+  for (int i = 1; i < d.n_in; ++i)
+    if (d.in[i].flags & kInNoPair) return false;
+  return true;
+}
+
+template <class Real, int NF>
+__device__ __forceinline__ void tile_adjoint_pairs_nf(WarpTile* w, Real* __restrict__ data, const TileGeom& g,
+                                                      int64_t r0, int64_t r1, int lane) {
+  using P1 = Pack<Real, 1>;
+  constexpr int U = AdjNfPasses<Real, NF>::value;
+  const DevBucket& d = w->d;
+  const bool full = d.aflags & kAdjFull;
+  const uint32_t lp_t = w->lpart[NF][lane];
+  uint32_t lp[NF];
+#pragma unroll
+  for (int i = 0; i < NF; ++i) lp[i] = w->lpart[i][lane];
+  for (int pp = 0; pp < g.P && r0 + (int64_t)pp * 32 < r1; pp += U) {
+    bool ok[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) ok[u] = pp + u < g.P && r0 + (int64_t)(pp + u) * 32 + lane < r1;
+    P1 p0[U], p1[U];
+    load_factors_nf<Real, NF, U>(w, data, pp, ok, lp, p0, p1);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (!ok[u]) continue;
+      const int64_t e0 = d.out_off + 2 * (int64_t)(w->tab[NF][pp + u] + lp_t);
+      if (full) {
+        stv<Real, 1>(data, e0, p0[u]);
+        stv<Real, 1>(data, e0 + 1, p1[u]);
+      } else {
+        atomic_add_pair<Real>(data, e0, p0[u].c[0], p1[u].c[0]);
       }
+    }
+  }
+}
+
+template <class Real, int NF>
+__device__ __forceinline__ void tile_adjred_pairs_nf(WarpTile* w, Real* __restrict__ data, const TileGeom& g,
+                                                     int64_t r0, int64_t r1, int lane) {
+  using P1 = Pack<Real, 1>;
+  constexpr int U = AdjNfPasses<Real, NF>::value;
+  const DevBucket& d = w->d;
+  const int seg = (d.aflags & kAdjRedLow) ? 1 << d.comp_bits : (1 << d.comp_bits) / 32;  // passes per target group
+  uint32_t lp[NF];
+#pragma unroll
+  for (int i = 0; i < NF; ++i) lp[i] = w->lpart[i][lane];
+  P1 s0, s1;
+  s0.c[0].x = 0;
+  s0.c[0].y = 0;
+  s1 = s0;
+  for (int pp = 0; pp < g.P && r0 + (int64_t)pp * 32 < r1; pp += U) {
+    bool ok[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) ok[u] = pp + u < g.P && r0 + (int64_t)(pp + u) * 32 + lane < r1;
+    P1 p0[U], p1[U];
+    load_factors_nf<Real, NF, U>(w, data, pp, ok, lp, p0, p1);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int q = pp + u;
+      if (q >= g.P || r0 + (int64_t)q * 32 >= r1) break;  // warp-uniform: the tile's last pass is done
+      if (ok[u]) {
+        s0.c[0] = cadd<Real>(s0.c[0], p0[u].c[0]);
+        s1.c[0] = cadd<Real>(s1.c[0], p1[u].c[0]);
+      }
+      if ((q + 1) % seg == 0 || q + 1 == g.P || r0 + (int64_t)(q + 1) * 32 >= r1)  // end of a target group's passes
+        adjred_pairs_flush<Real>(w, data, r0, q, lane, s0, s1);
     }
   }
 }
@@ -1151,7 +1325,14 @@ __device__ __forceinline__ void warp_tile(WarpTile* w, Real* __restrict__ data, 
   bool lane_on;
   lane_slot(g, lane, &rip, &v0, &lane_on);
   const int P = g.P;
-  if (GRAD && d.kind == kStepAdjRed) {  // row q = kt * 2^comp_bits + c: y = pdep(kt, mask_t) | pdep(c, ~mask_t)
+  if (GRAD && d.kind == kStepAdjRed && (d.aflags & kAdjRedLow)) {  // row q = (h << 5) | lane, RP = 32
+    const uint32_t hmask = (1u << d.comp_bits) - 1u;
+    for (int pp = lane; pp < P; pp += 32) {
+      const uint32_t h = (uint32_t)((r0 + (int64_t)pp * g.RP) >> 5);
+      const uint32_t yp = pdep_in(h & hmask, d.in[d.n_in + 1]) | pdep_in(h >> d.comp_bits, d.in[d.n_in + 2]);
+      for (int i = 0; i <= d.n_in; ++i) w->tab[i][pp] = pext_in(yp, d.in[i]);
+    }
+  } else if (GRAD && d.kind == kStepAdjRed) {  // row q = kt * 2^comp_bits + c: y = pdep(kt, mask_t) | pdep(c, ~mask_t)
     const uint32_t cmask = (1u << d.comp_bits) - 1u;
     for (int pp = lane; pp < P; pp += 32) {
       const uint32_t q = (uint32_t)(r0 + (int64_t)pp * g.RP);
@@ -1192,15 +1373,33 @@ __device__ __forceinline__ void warp_tile(WarpTile* w, Real* __restrict__ data, 
   } else {
     if constexpr (GRAD) {
       if (d.kind == kStepAdj) {
-        if (STAGE == 2 && PAIR && g.RP == 32 && g.VC == 1)
-          tile_adjoint_pairs<Real>(w, data, g, r0, r1, lane);
+        if (STAGE == 2 && PAIR && g.RP == 32 && g.VC == 1) {
+          const bool nf = adj_nf_form(d);
+          if (nf && d.n_in == 2)
+            tile_adjoint_pairs_nf<Real, 2>(w, data, g, r0, r1, lane);
+          else if (nf && d.n_in == 3)
+            tile_adjoint_pairs_nf<Real, 3>(w, data, g, r0, r1, lane);
+          else if (nf && d.n_in == 4)
+            tile_adjoint_pairs_nf<Real, 4>(w, data, g, r0, r1, lane);
+          else
+            tile_adjoint_pairs<Real>(w, data, g, r0, r1, lane);
+        }
         else if (STAGE == 2 && !PAIR && g.RP == 1 && g.VC == 1)
           tile_adjoint_rows<Real, VB>(w, data, g, r0, r1, lane);
         else
           tile_adjoint<Real, VB, PAIR, CG, 2>(w, data, g, r0, r1, lane, rip, v0, lane_on, ctrl, dbg_bucket);
       } else if (d.kind == kStepAdjRed) {
-        if (STAGE == 2 && PAIR && g.RP == 32 && g.VC == 1)
-          tile_adjred_pairs<Real>(w, data, g, r0, r1, lane);
+        if (STAGE == 2 && PAIR && g.RP == 32 && g.VC == 1) {
+          const bool nf = adj_nf_form(d);
+          if (nf && d.n_in == 2)
+            tile_adjred_pairs_nf<Real, 2>(w, data, g, r0, r1, lane);
+          else if (nf && d.n_in == 3)
+            tile_adjred_pairs_nf<Real, 3>(w, data, g, r0, r1, lane);
+          else if (nf && d.n_in == 4)
+            tile_adjred_pairs_nf<Real, 4>(w, data, g, r0, r1, lane);
+          else
+            tile_adjred_pairs<Real>(w, data, g, r0, r1, lane);
+        }
         else
           tile_adjred<Real, VB, PAIR, CG, 2>(w, data, g, r0, r1, lane, rip, v0, lane_on, ctrl, dbg_bucket);
       } else {

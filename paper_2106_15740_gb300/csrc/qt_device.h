@@ -66,8 +66,17 @@ struct TileGeom {
 //              lanes sum while k_t stays fixed and add one atomic per target
 //              element at each change of k_t.  in[n_in] is the target record,
 //              in[n_in + 1] the complement record.
+//              With kAdjRedLow (one angle set): the lanes take the bucket's
+//              five lowest variables instead, so a warp's loads of the output
+//              adjoint are contiguous.  Row q = (h << 5) | lane with the pass
+//              index h = k_h * 2^comp_bits + c_h, y = lane | pdep(c_h,
+//              in[n_in + 1].mask) | pdep(k_h, in[n_in + 2].mask): the
+//              completion and target bits above bit 4 (comp_bits and tgt_bits
+//              count them).  Lanes sum over the passes of one k_h, then over
+//              their completion bits (a butterfly), and the lanes whose
+//              completion bits are 0 add one atomic per target element.
 constexpr int32_t kStepFwd = 0, kStepAdj = 1, kStepZero = 2, kStepAdjRed = 3;
-constexpr int32_t kAdjFull = 1, kAdjUnitG = 2;
+constexpr int32_t kAdjFull = 1, kAdjUnitG = 2, kAdjRedLow = 4;
 
 struct DevBucket {
   int64_t out_off;             // element offset of the output
@@ -78,8 +87,8 @@ struct DevBucket {
   int32_t ntask;               // chunks of this step in the persistent queue (its done count)
   int32_t kind;                // kStep*
   int32_t aflags;              // kAdj* bits (kStepAdj)
-  int32_t tgt_bits;            // kStepAdjRed: target rows 2^tgt_bits (times x = 0, 1)
-  int32_t comp_bits;           // kStepAdjRed: completions per target row 2^comp_bits (>= 5)
+  int32_t tgt_bits;            // kStepAdjRed: target rows 2^tgt_bits (times x = 0, 1); kAdjRedLow: target bits above bit 4
+  int32_t comp_bits;           // kStepAdjRed: completions per target row 2^comp_bits (>= 5); kAdjRedLow: completion bits above bit 4
   int32_t span;                // warp tiles per queue task (chunk c covers tiles [c*span, (c+1)*span))
   int32_t n_dep;               // steps that must be complete before a task of this one starts:
                                // deps[dep .. dep + n_dep) (done count of each = its ntask)
