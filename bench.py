@@ -278,34 +278,43 @@ def min_fill_comparison(n, edges, p, B, g, b, dev, torch):
     return out
 
 
-def chain_comparison(n, edges, p, B, g, b, dev, torch):
-    """The bench step with every step of a workspace slot chained to the one
-    before it (chain_steps), instead of waiting only for its tree dependencies."""
+def _plan_variant(n, edges, p, B, g, b, dev, torch, what, **kw):
+    """The bench step's plan and tile with one planning option changed (direct calls)."""
     from paper_2106_15740_gb300.energy import EnergyPlan
     plan = EnergyPlan(n, edges, p, batch=B, dtype=WORKLOAD["dtype"], mode="persistent", device=dev,
                       order_trials=WORKLOAD.get("order_trials", 0), lane_items=WORKLOAD.get("lane_items", 0),
-                      group_rows=WORKLOAD.get("group_rows", 0), chain_steps=True)
+                      group_rows=WORKLOAD.get("group_rows", 0), **kw)
     ms = _time_calls(plan, g, b, False, 5, torch)
     out = {"value": len(edges) * B / (ms * 1e-3), "unit": "edge_evals/s", "ms_per_step": ms,
-           "achieved_gbs": plan.stats["alg_bytes"] / (ms * 1e-3) / 1e9,
-           "what": "same plan and tile, each step waits for the step before it on its slot (direct calls)"}
+           "alg_bytes_per_step": plan.stats["alg_bytes"],
+           "achieved_gbs": plan.stats["alg_bytes"] / (ms * 1e-3) / 1e9, "what": what}
     plan.close()
+    torch.cuda.empty_cache()
     return out
+
+
+def chain_comparison(n, edges, p, B, g, b, dev, torch):
+    """The bench step with every step of a workspace slot chained to the one
+    before it (chain_steps), instead of waiting only for its tree dependencies."""
+    return _plan_variant(n, edges, p, B, g, b, dev, torch,
+                         "same plan and tile, each step waits for the step before it on its slot (direct calls)",
+                         chain_steps=True)
 
 
 def round_robin_comparison(n, edges, p, B, g, b, dev, torch):
     """The bench step with the queue taken round-robin over the workspace
     slots, step by step, instead of longest remaining path first."""
-    from paper_2106_15740_gb300.energy import EnergyPlan
-    plan = EnergyPlan(n, edges, p, batch=B, dtype=WORKLOAD["dtype"], mode="persistent", device=dev,
-                      order_trials=WORKLOAD.get("order_trials", 0), lane_items=WORKLOAD.get("lane_items", 0),
-                      group_rows=WORKLOAD.get("group_rows", 0), queue_order="round_robin")
-    ms = _time_calls(plan, g, b, False, 5, torch)
-    out = {"value": len(edges) * B / (ms * 1e-3), "unit": "edge_evals/s", "ms_per_step": ms,
-           "achieved_gbs": plan.stats["alg_bytes"] / (ms * 1e-3) / 1e9,
-           "what": "same plan and tile, queue round-robin over slots step by step (direct calls)"}
-    plan.close()
-    return out
+    return _plan_variant(n, edges, p, B, g, b, dev, torch,
+                         "same plan and tile, queue round-robin over slots step by step (direct calls)",
+                         queue_order="round_robin")
+
+
+def unfused_comparison(n, edges, p, B, g, b, dev, torch):
+    """The bench step with every bucket a step of its own (fuse_chains off):
+    each chained bucket's result is written and read back."""
+    return _plan_variant(n, edges, p, B, g, b, dev, torch,
+                         "same orders and tile, every bucket a step of its own (no chained steps; direct calls)",
+                         fuse_chains=False)
 
 
 def gradient_and_comparator(dev, torch):
@@ -454,7 +463,15 @@ def large_config(dev, torch):
     out["energy_c64"] = {"value": len(edges) / (ms * 1e-3), "unit": "edge_evals/s", "ms_per_call": ms,
                          "max_width": int(plan.widths.max()), "sliced_edges": int((plan.slices > 0).sum()),
                          "networks": int((2 ** plan.slices.astype(np.int64)).sum()),
-                         "roofline": _roofline(plan.stats["alg_bytes"], kms, peak, peak_kind, "persistent_kernel<float,1,true,false,2>")}
+                         "roofline": _roofline(plan.stats["alg_bytes"], kms, peak, peak_kind, "persistent_kernel<float,1,true,false,4>")}
+    plan.close()
+    torch.cuda.empty_cache()
+    plan = EnergyPlan(n, edges, p, dtype="c64", fuse_chains=0, **kw)
+    ms0, kms0 = _time_calls(plan, gd, bd, False, 2, torch, kernel=True)
+    out["energy_c64_unfused"] = {"value": len(edges) / (ms0 * 1e-3), "unit": "edge_evals/s", "ms_per_call": ms0,
+                                 "what": "the same plan with every bucket a step of its own (fuse_chains=0)",
+                                 "roofline": _roofline(plan.stats["alg_bytes"], kms0, peak, peak_kind,
+                                                       "persistent_kernel<float,1,true,false,2>")}
     plan.close()
     torch.cuda.empty_cache()
     plan = EnergyPlan(n, edges, p, dtype="c64", gradient=True, **kw)
@@ -472,7 +489,7 @@ def large_config(dev, torch):
     plan.check()
     out["energy_c64x2"] = {"value": len(edges) / (msx2 * 1e-3), "unit": "edge_evals/s", "ms_per_call": msx2,
                            "roofline": _roofline(plan.stats["alg_bytes"], kmsx2, peak, peak_kind,
-                                                 "persistent_kernel<ff,1,true,false,2> (float pairs)")}
+                                                 "persistent_kernel<ff,1,true,false,4> (float pairs)")}
     plan.close()
     torch.cuda.empty_cache()
     plan = EnergyPlan(n, edges, p, dtype="c128", **kw)
@@ -679,7 +696,7 @@ def run_ours(args):
                        "alg_bytes_by_result_rank": bytes_by_rank(plan.plan, B, 8 if WORKLOAD["dtype"] == "c64" else 16)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": _traffic(B, alg, profile_only),
-                         "kernel": "persistent_kernel<float,2,false,false,2>",
+                         "kernel": "persistent_kernel<float,2,false,false,4>",
                          "kernel_ms": kms, "kernel_ms_from": "CUDA events around the persistent launch over "
                                                              "K direct calls after the graph-timed steps", "alg_bytes_per_launch": alg, "peak_kind": peak_kind},
             "e2e": {"value": units * world / e2e_s, "unit": "edge_evals/s",
@@ -702,6 +719,7 @@ def run_ours(args):
         if not profile_only:
             res["chained_steps"] = chain_comparison(n, edges, p, B, g, b, dev, torch)
             res["round_robin_queue"] = round_robin_comparison(n, edges, p, B, g, b, dev, torch)
+            res["unfused_chains"] = unfused_comparison(n, edges, p, B, g, b, dev, torch)
         if not args.no_cpu_baseline:
             e_gpu, zz = plan.energy(g, b, edge_zz=True)
             plan.check()

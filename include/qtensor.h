@@ -194,6 +194,17 @@ typedef struct {
                              chunk_tiles says.  The autotuner picks these per width band (§Results:
                              the width of a step sets its cost).  Results are bit-identical for
                              any choice */
+  int32_t fuse_chains;    /* persistent energy and amplitude plans (no gradient) on the row-wide
+                             tiles (B > 1 angle sets, one vector chunk per row): a bucket's result
+                             that the next bucket to use it only contracts with a leaf factor --
+                             that consumer has no other intermediate input and no variable beyond
+                             the result (§Tensor network contraction) -- is never stored: the
+                             bucket and up to fuse_chains such consumers in a row (each
+                             eliminating the previous one's result) are evaluated in one step,
+                             the results' rows contracted with the consumers' leaf factors as
+                             they are formed, which removes their writes and reads from the
+                             traffic.  0 .. 3 (default 3); 0: every bucket is a step of its own.
+                             Results are bit-identical for any value */
 } qt_plan_options;
 
 /* Fill `opt` with defaults: batch 1, QT_C128, QT_MODE_PER_BUCKET, no gradient,

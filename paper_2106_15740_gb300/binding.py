@@ -54,7 +54,7 @@ class qt_plan_options(C.Structure):
                 ("chunk_tiles", C.c_int32), ("order_trials", C.c_int32), ("order_seed", C.c_int32),
                 ("order_tau", C.c_double), ("checkpoint_bytes", C.c_int64),
                 ("chain_steps", C.c_int32), ("queue_order", C.c_int32),
-                ("chunk_tiles_by_rank", C.c_int32 * 32)]
+                ("chunk_tiles_by_rank", C.c_int32 * 32), ("fuse_chains", C.c_int32)]
 
 
 _lib = None

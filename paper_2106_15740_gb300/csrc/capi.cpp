@@ -260,6 +260,7 @@ void qt_plan_options_default(qt_plan_options* opt) {
   opt->chain_steps = 0;
   opt->queue_order = 1;
   for (int32_t r = 0; r < 32; ++r) opt->chunk_tiles_by_rank[r] = 0;
+  opt->fuse_chains = kMaxChain;
 }
 
 static qt_status check_options(const qt_plan_options* opt, qt_plan_options* out) {
@@ -287,6 +288,8 @@ static qt_status check_options(const qt_plan_options* opt, qt_plan_options* out)
   if (o.checkpoint_bytes < 0) return fail(QT_EINVAL, "checkpoint_bytes must be >= 0");
   if (o.chain_steps != 0 && o.chain_steps != 1) return fail(QT_EINVAL, "chain_steps must be 0 or 1");
   if (o.queue_order != 0 && o.queue_order != 1) return fail(QT_EINVAL, "queue_order must be 0 or 1");
+  if (o.fuse_chains < 0 || o.fuse_chains > kMaxChain)
+    return fail(QT_EINVAL, "fuse_chains must be 0 .. " + std::to_string(kMaxChain));
   for (int32_t r = 0; r < 32; ++r)
     if (o.chunk_tiles_by_rank[r] < 0 || o.chunk_tiles_by_rank[r] > (1 << 20))
       return fail(QT_EINVAL, "chunk_tiles_by_rank entries must be in [0, 2^20]");

@@ -378,10 +378,47 @@ qt_status compile_plan(Plan* P) {
   for (int32_t o = 0; o < P->n_orig; ++o)
     for (int32_t k = P->net_first[o]; k < P->net_first[o + 1]; ++k) orig_of[k] = o;
   P->flops = 0.0;
+  // Chained steps: bucket b fused with up to fuse_chains consumers c_1 .. c_m,
+  // c_1 eliminating b's result and c_j that of c_(j-1), each with no variable
+  // beyond its input and no other intermediate input.  Chains are taken
+  // greedily in execution order (a bucket absorbed into a chain starts none).
+  // The fused step runs at b's place: c_m's output is allocated there, the
+  // results of b and c_1 .. c_(m-1) never are.
+  const bool fuse = !grad && persistent && P->opt.fuse_chains > 0 && chain_fusion_ok(P->opt.dtype, B);
+  P->has_chains = false;
+  // (one angle set: one consumer at most, which the pair tile takes in lane shuffles)
+  const int32_t max_chain = B == 1 ? std::min<int32_t>(P->opt.fuse_chains, 1) : P->opt.fuse_chains;
+  std::vector<std::vector<std::vector<int32_t>>> chain_of(n_edges);  // per network and bucket: c_1 .. c_m
+  for (int32_t e = 0; e < n_edges; ++e) {
+    const EdgePlan& ep = P->edges[e];
+    const int32_t nb = (int32_t)ep.buckets.size();
+    chain_of[e].assign(nb, {});
+    if (!fuse) continue;
+    std::vector<char> absorbed(nb, 0);
+    for (int32_t i = 0; i < nb; ++i) {
+      if (absorbed[i]) continue;
+      const int32_t n_in = (int32_t)ep.buckets[i].in_src.size();
+      int32_t cur = i;
+      while ((int32_t)chain_of[e][i].size() < max_chain && n_in + (int32_t)chain_of[e][i].size() < kDevMaxIn) {
+        const int32_t c = ep.buckets[cur].consumer;
+        if (c < 0 || ep.buckets[cur].out_rank < 1) break;
+        const Bucket& bc = ep.buckets[c];
+        int32_t n_int = 0;
+        for (int32_t src : bc.in_src) n_int += src >= 0 ? 1 : 0;
+        if (bc.out_rank + 1 != ep.buckets[cur].out_rank || n_int != 1) break;
+        chain_of[e][i].push_back(c);
+        absorbed[c] = 1;
+        cur = c;
+      }
+    }
+  }
   for (int32_t e = 0; e < n_edges; ++e) {
     const EdgePlan& ep = P->edges[e];
     const int32_t nb = (int32_t)ep.buckets.size();
     const double bytes_before = P->alg_bytes;
+    std::vector<char> absorbed(nb, 0);
+    for (int32_t i = 0; i < nb; ++i)
+      for (int32_t c : chain_of[e][i]) absorbed[c] = 1;
 
     Arena arena;
     out_off[e].assign(nb, 0);
@@ -389,12 +426,20 @@ qt_status compile_plan(Plan* P) {
     double ebytes = 0.0;
     for (int32_t i = 0; i < nb; ++i) {
       const Bucket& bk = ep.buckets[i];
-      const int64_t rows = (int64_t)1 << bk.out_rank;
-      if (bk.out_rank == 0) {
-        out_off[e][i] = scal_pool;  // relative to the scalar pool
+      if (bk.leaf_rank > 0) {
+        leaf_off[e][i] = leaf_pool;
+        leaf_pool += align_el(((int64_t)1 << bk.leaf_rank) * B);
+      }
+      const double nin = (double)bk.in_src.size();
+      P->flops += (double)B * (double)((int64_t)1 << bk.out_rank) * (2.0 * 6.0 * (nin - 1.0) + 2.0);
+      if (absorbed[i]) continue;  // evaluated (and its output placed) with the bucket it is fused with
+      const int32_t o = chain_of[e][i].empty() ? i : chain_of[e][i].back();  // whose output this step writes
+      const int64_t rows = (int64_t)1 << ep.buckets[o].out_rank;
+      if (ep.buckets[o].out_rank == 0) {
+        out_off[e][o] = scal_pool;  // relative to the scalar pool
         scal_pool += align_el(B);
       } else {
-        out_off[e][i] = arena.alloc(align_el(rows * B));
+        out_off[e][o] = arena.alloc(align_el(rows * B));
       }
       double bytes = (double)rows;  // output write
       for (size_t k = 0; k < bk.in_src.size(); ++k) {
@@ -403,13 +448,7 @@ qt_status compile_plan(Plan* P) {
         if (!grad) arena.release(out_off[e][bk.in_src[k]], align_el(((int64_t)1 << src.out_rank) * B));
         bytes += (double)((int64_t)1 << bk.in_rank[k]);
       }
-      if (bk.leaf_rank > 0) {
-        leaf_off[e][i] = leaf_pool;
-        leaf_pool += align_el(((int64_t)1 << bk.leaf_rank) * B);
-      }
       ebytes += bytes;
-      const double nin = (double)bk.in_src.size();
-      P->flops += (double)B * (double)rows * (2.0 * 6.0 * (nin - 1.0) + 2.0);
     }
     region[e] = arena.peak;
     if (grad) {
@@ -563,11 +602,38 @@ qt_status compile_plan(Plan* P) {
       step_done();
     };
     if (!grad) {
+      std::vector<char> absorbed(ep.buckets.size(), 0);
+      for (int32_t i = 0; i < (int32_t)ep.buckets.size(); ++i)
+        for (int32_t c : chain_of[e][i]) absorbed[c] = 1;
       for (int32_t i = 0; i < (int32_t)ep.buckets.size(); ++i) {
         const Bucket& bk = ep.buckets[i];
         std::vector<int64_t> loc;
         for (int32_t c : bk.in_src) loc.push_back(c >= 0 ? out_off[e][c] : -1);
-        fwd_push(i, out_off[e][i], loc);
+        const std::vector<int32_t>& ch = chain_of[e][i];
+        if (!ch.empty()) {  // b = i fused with its chain: b's rows, c_m's output, the chain's leaf factors
+          const Bucket& bm = ep.buckets[ch.back()];
+          DevBucket d = fwd_record(i, 0, loc);
+          d.out_off = bm.out_rank == 0 ? scal_base + out_off[e][ch.back()] : rbase + out_off[e][ch.back()];
+          d.chain = (int32_t)ch.size();
+          P->has_chains = true;
+          for (int32_t j = 0; j < d.chain; ++j) {
+            const Bucket& bc = ep.buckets[ch[j]];
+            int32_t lk = -1;
+            for (int32_t k = 0; k < (int32_t)bc.in_src.size(); ++k)
+              if (bc.in_src[k] < 0) lk = k;
+            if (lk >= 0)  // over b's rows: bit j is c_(j+1)'s eliminated variable (index bit 0), bits j + 1.. its rows
+              d.in[d.n_in + j] = input_record((bc.in_mask[lk] << (j + 1)) | (1u << j), leaf_off[e][ch[j]], kInLeaf);
+            else
+              d.chain_noleaf |= 1 << j;
+          }
+          P->buckets.push_back(d);
+          for (size_t k = 0; k < bk.in_src.size(); ++k)
+            if (bk.in_src[k] >= 0) touch(rbase + loc[k], tensor_el(bk.in_src[k]), false);
+          touch(d.out_off, ((int64_t)1 << bm.out_rank) * B, true);
+          step_done();
+        } else if (!absorbed[i]) {
+          fwd_push(i, out_off[e][i], loc);
+        }
         if (bk.leaf_rank > 0) leaf_record(i);
       }
     }
@@ -987,11 +1053,12 @@ qt_status run_plan(Plan* P, const double* gamma, const double* beta, double* ene
   }
   if (P->opt.mode == QT_MODE_PERSISTENT) {
     int per_sm = 0;
-    QT_CUDA(persistent_occupancy(dtype, P->opt.gradient != 0, B, &per_sm));
+    QT_CUDA(persistent_occupancy(dtype, P->opt.gradient != 0, P->has_chains, B, &per_sm));
     int n_sm = 0;
     QT_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
     const int32_t grid = std::max(1, per_sm) * n_sm;
-    QT_CUDA(launch_persistent(dtype, P->opt.gradient != 0, dbk, (const DevTask*)(base + L.tasks), (int32_t)P->tasks.size(),
+    QT_CUDA(launch_persistent(dtype, P->opt.gradient != 0, P->has_chains, dbk, (const DevTask*)(base + L.tasks),
+                              (int32_t)P->tasks.size(),
                               (DevCtrl*)(base + L.ctrl), (int32_t*)(base + L.done), B, P->opt.lane_items, data,
                               P->data_elems, grid, P->spin_limit, (const DevDep*)(base + L.deps), P->trace, s));
   } else {

@@ -43,6 +43,7 @@ struct Plan {
   // device images (uploaded into the workspace)
   std::vector<DevBucket> buckets;          // steps of all edges (forward, then adjoint), concatenated
   std::vector<int32_t> edge_first;         // first step of each edge (n_edges + 1)
+  bool has_chains = false;                 // some forward step is chained (the launch takes the STAGE 4 kernel)
   std::vector<DevLeafFactor> leaf;
   std::vector<int32_t> leaf_first;         // first leaf factor of each edge (n_edges + 1)
   int64_t lbar_shift = 0;                  // leaf-adjoint element = leaf element + lbar_shift

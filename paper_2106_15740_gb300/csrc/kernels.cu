@@ -369,7 +369,7 @@ __device__ __forceinline__ int32_t ld_acquire(const int32_t* p) {
 // lean register tiles: every forward tile takes tile_rows_regs or
 // tile_pairs_regs and the generic forward tile is not compiled in.
 template <class Real, int VB, bool PAIR, bool GRAD, int STAGE>
-__global__ void __launch_bounds__(256, 4) persistent_kernel(const DevBucket* __restrict__ buckets,
+__global__ void __launch_bounds__(256, (STAGE == 4 && PAIR) ? 3 : 4) persistent_kernel(const DevBucket* __restrict__ buckets,
                                                             const DevTask* __restrict__ tasks, int32_t n_tasks,
                                                             DevCtrl* ctrl, int32_t* done, Real* __restrict__ data,
                                                             const TileGeom g, int32_t spin_limit,
@@ -765,6 +765,10 @@ bool row_wide(int dtype, int32_t B) {
   return g.RP == 1 && (g.VC == 1 || (g.VC == 2 && dtype == QT_C64X2));
 }
 
+bool chain_fusion_ok(int dtype, int32_t B) {
+  return B == 1 || (row_wide(dtype, B) && tile_geom(dtype, B, 0).VC == 1);  // the pair tiles or the row tiles
+}
+
 template <class Real, int VB, bool PAIR, bool GRAD, int ST>
 static const void* pk_fn() {
   return (const void*)dev::persistent_kernel<Real, VB, PAIR, GRAD, ST>;
@@ -794,26 +798,38 @@ static const void* persistent_fn_g(int dtype, int32_t B) {
   return lean ? pk_fn<double, 1, false, GRAD, 2>() : pk_fn<double, 1, false, GRAD, 0>();
 }
 
-static const void* persistent_fn(int dtype, bool grad, int32_t B) {
+// Forward plans with chained steps take the STAGE 4 variant of their lean
+// tile (chain_fusion_ok's shapes: one angle set, or row-wide with one
+// vector chunk per row).
+static const void* persistent_fn_chains(int dtype, int32_t B) {
+  if (!chain_fusion_ok(dtype, B)) return nullptr;
+  const bool pair = (B == 1);
+  if (dtype == QT_C64) return pair ? pk_fn<float, 1, true, false, 4>() : pk_fn<float, 2, false, false, 4>();
+  if (dtype == QT_C64X2) return pair ? pk_fn<dev::ff, 1, true, false, 4>() : pk_fn<dev::ff, 1, false, false, 4>();
+  return pair ? pk_fn<double, 1, true, false, 4>() : pk_fn<double, 1, false, false, 4>();
+}
+
+static const void* persistent_fn(int dtype, bool grad, int32_t B, bool chains) {
+  if (chains) return grad ? nullptr : persistent_fn_chains(dtype, B);
   return grad ? persistent_fn_g<true>(dtype, B) : persistent_fn_g<false>(dtype, B);
 }
 
-cudaError_t launch_persistent(int dtype, bool grad, const DevBucket* buckets, const DevTask* tasks, int32_t n_tasks,
-                              DevCtrl* ctrl, int32_t* done, int32_t B, int32_t lane_items, void* data,
+cudaError_t launch_persistent(int dtype, bool grad, bool chains, const DevBucket* buckets, const DevTask* tasks,
+                              int32_t n_tasks, DevCtrl* ctrl, int32_t* done, int32_t B, int32_t lane_items, void* data,
                               int64_t data_elems, int32_t grid, int32_t spin_limit, const DevDep* deps,
                               unsigned long long* trace, cudaStream_t s) {
   TileGeom g = tile_geom(dtype, B, lane_items);
   g.data_elems = data_elems;
   g.wait_limit = 1 << 22;
-  const void* fn = persistent_fn(dtype, grad, B);
+  const void* fn = persistent_fn(dtype, grad, B, chains);
   if (!fn) return cudaErrorInvalidValue;  // no such variant (float pairs have no adjoint sweep)
   void* args[] = {(void*)&buckets, (void*)&tasks, (void*)&n_tasks, (void*)&ctrl, (void*)&done, (void*)&data,
                   (void*)&g, (void*)&spin_limit, (void*)&deps, (void*)&trace};
   return cudaLaunchKernel(fn, dim3(grid), dim3(256), args, 0, s);
 }
 
-cudaError_t persistent_occupancy(int dtype, bool grad, int32_t B, int* blocks_per_sm) {
-  const void* fn = persistent_fn(dtype, grad, B);
+cudaError_t persistent_occupancy(int dtype, bool grad, bool chains, int32_t B, int* blocks_per_sm) {
+  const void* fn = persistent_fn(dtype, grad, B, chains);
   if (!fn) return cudaErrorInvalidValue;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, 256, 0);
 }

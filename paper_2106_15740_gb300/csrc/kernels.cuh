@@ -237,8 +237,13 @@ struct WarpTile {
   DevBucket d;
   uint32_t tab[kDevMaxIn][kLaneItems];
   uint32_t lpart[kDevMaxIn][32];  // pext(i_lane, mask) per input and lane
-  float redf[32][4];              // per-lane partial sums of a reduction step (complex64)
-  double redd[32][2];             // the same for complex128
+  union {  // an adjoint reduction step's partial sums or a chained forward step's held rows
+    struct {
+      float f[32][4];             // per-lane partial sums of a reduction step (complex64)
+      double d[32][2];            // the same for complex128
+    } red;
+    float4 chainh[kMaxChain - 1][32];  // per chain level below the last and lane: its held even row
+  } x;
   unsigned long long trace_t[2];        // queue trace: claim and ready clock of the current task
 };
 
@@ -264,6 +269,8 @@ __device__ __forceinline__ void load_bucket(DevBucket* dst, const DevBucket* src
     dst->comp_bits = src->comp_bits;
     dst->span = src->span;
     dst->n_dep = src->n_dep;
+    dst->chain = src->chain;
+    dst->chain_noleaf = src->chain_noleaf;
   }
 }
 
@@ -286,6 +293,8 @@ __device__ __forceinline__ void copy_bucket(DevBucket* dst, const DevBucket* src
     dst->comp_bits = src->comp_bits;
     dst->span = src->span;
     dst->n_dep = src->n_dep;
+    dst->chain = src->chain;
+    dst->chain_noleaf = src->chain_noleaf;
   }
 }
 
@@ -324,7 +333,7 @@ __device__ __forceinline__ void lane_parts(WarpTile* w, const TileGeom& g, int l
     for (int i = 0; i < w->d.n_in; ++i) w->lpart[i][lane] = pext_in(ylane, w->d.in[i]);
     return;
   }
-  const int n_rec = w->d.kind == kStepAdj || red_low ? w->d.n_in + 1 : w->d.n_in;
+  const int n_rec = w->d.kind == kStepAdj || red_low ? w->d.n_in + 1 : w->d.n_in + w->d.chain;
   for (int i = 0; i < n_rec; ++i) w->lpart[i][lane] = pext_in((uint32_t)rip, w->d.in[i]);
 }
 
@@ -485,6 +494,111 @@ __device__ __forceinline__ void tile_items(WarpTile* w, Real* __restrict__ data,
 // two rows per iteration 17.10 ms, with one 17.45 ms (bit-identical results); fan-in 4 spills.
 constexpr int kFixedRows = 2;      // output rows per iteration of tile_rows_fixed
 constexpr int kFixedMaxFanIn = 3;  // fan-in up to which steps take tile_rows_fixed
+static_assert(kFixedRows == 2, "chained steps combine the rows w = 0, 1 of one iteration");
+
+// Chained steps (chain = m > 0, STAGE 4 kernels), row-wide layout: one row y
+// of b per iteration.  Its value G_b[y] (the product-sum, never stored) times
+// c_1's leaf row L_1[pext(y, chain mask 1)] (the mask's bit 0 is bit 0 of y,
+// c_1's eliminated variable) is c_1's term for w_1 = bit 0 of y: an even row
+// keeps it (acc), an odd row adds it to the kept one, which completes c_1's
+// row y >> 1.  That row times c_2's leaf row at pext(y, chain mask 2) (bit 0
+// = bit 1 of y) is c_2's term, kept or added the same way (held per lane in
+// the warp's shared slot), and so on up to c_m, whose completed row is the
+// output.  Every term and sum takes the consumer's own operands in its own
+// order (the intermediate row, then the leaf; the term of w = 0 first), so a
+// chained step is bit-identical to the separate steps.  One row per
+// iteration and one kept term keep the tile within the 64-register budget
+// (two rows per iteration and their leaf rows spilled, and the spills slowed
+// every tile of the kernel).
+template <class T>
+__device__ __forceinline__ float4 as_float4(const T& x) {
+  static_assert(sizeof(T) <= sizeof(float4), "a held chain term is at most 16 bytes per lane");
+  float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+  memcpy(&r, &x, sizeof(T));
+  return r;
+}
+template <class T>
+__device__ __forceinline__ T from_float4(const float4& x) {
+  static_assert(sizeof(T) <= sizeof(float4), "a held chain term is at most 16 bytes per lane");
+  T r;
+  memcpy(&r, &x, sizeof(T));
+  return r;
+}
+
+template <class Real, int VB, int NIN, bool LEAF>
+__device__ __forceinline__ void tile_rows_chain(WarpTile* w, Real* __restrict__ data, const TileGeom& g, int64_t r0,
+                                                int64_t r1, int lane) {
+  using PK = Pack<Real, VB>;
+  const DevBucket& d = w->d;
+  const int n_in = NIN > 0 ? NIN : d.n_in;
+  const int nrows = (int)(r1 - r0);
+  const bool on = lane < g.Bv;
+  const int64_t B = g.B;
+  const int64_t lo = (int64_t)(on ? lane : 0) * VB;  // idle lanes read vector 0 and store nothing
+  const bool leaf1 = !(d.chain_noleaf & 1);
+  const int64_t lbase = d.in[n_in].off + lo;  // c_1's leaf factor (row 0 of the data if it has none)
+  PK acc;
+  for (int q = 0; q < nrows; ++q) {
+    const uint32_t y = (uint32_t)(r0 + q);
+    const PK L1 = ldv<Real, VB, false>(data, lbase + (int64_t)w->tab[n_in][q] * B);  // with the inputs
+    PK p0, p1;
+    if (NIN > 0) {
+      PK a0[NIN > 0 ? NIN : 1], a1[NIN > 0 ? NIN : 1];
+#pragma unroll
+      for (int i = 0; i < NIN; ++i) {
+        const int64_t e = d.in[i].off + lo + (int64_t)(2 * w->tab[i][q]) * B;
+        const bool cached = LEAF && i == NIN - 1;  // the leaf factor, written before the launch
+        a0[i] = cached ? ldv<Real, VB, false>(data, e) : ldv<Real, VB, true>(data, e);
+        a1[i] = cached ? ldv<Real, VB, false>(data, e + B) : ldv<Real, VB, true>(data, e + B);
+      }
+      p0 = a0[0];
+      p1 = a1[0];
+#pragma unroll
+      for (int i = 1; i < (NIN > 0 ? NIN : 1); ++i) {
+        pmul<Real, VB>(p0, a0[i]);
+        pmul<Real, VB>(p1, a1[i]);
+      }
+    } else {
+#pragma unroll 1
+      for (int i = 0; i < n_in; ++i) {
+        const bool leaf = d.in[i].flags & kInLeaf;
+        const int64_t e = d.in[i].off + lo + (int64_t)(2 * w->tab[i][q]) * B;
+        const PK a0 = ldv_in<Real, VB, true>(data, e, leaf);
+        const PK a1 = ldv_in<Real, VB, true>(data, e + B, leaf);
+        if (i == 0) {
+          p0 = a0;
+          p1 = a1;
+        } else {
+          pmul<Real, VB>(p0, a0);
+          pmul<Real, VB>(p1, a1);
+        }
+      }
+    }
+    PK t;
+#pragma unroll
+    for (int v = 0; v < VB; ++v) t.c[v] = cadd<Real>(p0.c[v], p1.c[v]);  // G_b[y]
+    if (leaf1) pmul<Real, VB>(t, L1);
+    if ((y & 1u) == 0) {  // c_1's term of w_1 = 0: keep it
+      acc = t;
+      continue;
+    }
+#pragma unroll
+    for (int v = 0; v < VB; ++v) t.c[v] = cadd<Real>(acc.c[v], t.c[v]);  // c_1's row y >> 1
+    int j = 1;
+    for (; j < d.chain; ++j) {  // c_(j+1): its term of w = bit j of y
+      if (!((d.chain_noleaf >> j) & 1))
+        pmul<Real, VB>(t, ldv<Real, VB, false>(data, d.in[n_in + j].off + lo + (int64_t)w->tab[n_in + j][q] * B));
+      if (((y >> j) & 1u) == 0) {
+        w->x.chainh[j - 1][lane] = as_float4(t);
+        break;
+      }
+      const PK h = from_float4<PK>(w->x.chainh[j - 1][lane]);
+#pragma unroll
+      for (int v = 0; v < VB; ++v) t.c[v] = cadd<Real>(h.c[v], t.c[v]);
+    }
+    if (j == d.chain && on) stv<Real, VB>(data, d.out_off + (int64_t)(y >> d.chain) * B + lo, t);
+  }
+}
 
 template <class Real, int VB, int NIN, bool LEAF>
 __device__ __forceinline__ void tile_rows_fixed(WarpTile* w, Real* __restrict__ data, const TileGeom& g, int64_t r0,
@@ -541,23 +655,11 @@ __device__ __forceinline__ void tile_rows_fixed(WarpTile* w, Real* __restrict__ 
 }
 
 template <class Real, int VB>
-__device__ __forceinline__ void tile_rows_regs(WarpTile* w, Real* __restrict__ data, const TileGeom& g, int64_t r0,
-                                               int64_t r1, int lane) {
+__device__ __forceinline__ void tile_rows_rolled(WarpTile* w, Real* __restrict__ data, const TileGeom& g, int64_t r0,
+                                                 int64_t r1, int lane) {
   using PK = Pack<Real, VB>;
   const DevBucket& d = w->d;
   const int n_in = d.n_in;
-  // (complex64 vectors only: with 16-byte complex numbers, complex128 and float pairs, the
-  // unrolled tile spills at the 64-register budget)
-  if (VB == 2 && n_in >= 2 && n_in <= kFixedMaxFanIn) {
-    const bool leaf = d.in[n_in - 1].flags & kInLeaf;
-    switch (n_in * 2 + (leaf ? 1 : 0)) {
-      case 4: return tile_rows_fixed<Real, VB, 2, false>(w, data, g, r0, r1, lane);
-      case 5: return tile_rows_fixed<Real, VB, 2, true>(w, data, g, r0, r1, lane);
-      case 6: return tile_rows_fixed<Real, VB, 3, false>(w, data, g, r0, r1, lane);
-      case 7: return tile_rows_fixed<Real, VB, 3, true>(w, data, g, r0, r1, lane);
-      default: break;
-    }
-  }
   const int nrows = (int)(r1 - r0);
   const bool on = lane < g.Bv;
   const int64_t B = g.B;
@@ -598,6 +700,45 @@ __device__ __forceinline__ void tile_rows_regs(WarpTile* w, Real* __restrict__ d
       }
     }
   }
+}
+
+// Chained steps (STAGE 4 kernels only), by fan-in as the unchained tiles.
+template <class Real, int VB>
+__device__ __forceinline__ void tile_rows_chained(WarpTile* w, Real* __restrict__ data, const TileGeom& g, int64_t r0,
+                                                  int64_t r1, int lane) {
+  const DevBucket& d = w->d;
+  const int n_in = d.n_in;
+  if (VB == 2 && n_in >= 2 && n_in <= kFixedMaxFanIn) {
+    const bool leaf = d.in[n_in - 1].flags & kInLeaf;
+    switch (n_in * 2 + (leaf ? 1 : 0)) {
+      case 4: return tile_rows_chain<Real, VB, 2, false>(w, data, g, r0, r1, lane);
+      case 5: return tile_rows_chain<Real, VB, 2, true>(w, data, g, r0, r1, lane);
+      case 6: return tile_rows_chain<Real, VB, 3, false>(w, data, g, r0, r1, lane);
+      case 7: return tile_rows_chain<Real, VB, 3, true>(w, data, g, r0, r1, lane);
+      default: break;
+    }
+  }
+  tile_rows_chain<Real, VB, 0, false>(w, data, g, r0, r1, lane);
+}
+
+template <class Real, int VB>
+__device__ __forceinline__ void tile_rows_regs(WarpTile* w, Real* __restrict__ data, const TileGeom& g, int64_t r0,
+                                               int64_t r1, int lane) {
+  const DevBucket& d = w->d;
+  const int n_in = d.n_in;
+  // (complex64 vectors only: with 16-byte complex numbers, complex128 and float pairs, the
+  // unrolled tile spills at the 64-register budget)
+  if (VB == 2 && n_in >= 2 && n_in <= kFixedMaxFanIn) {
+    const bool leaf = d.in[n_in - 1].flags & kInLeaf;
+    switch (n_in * 2 + (leaf ? 1 : 0)) {
+      case 4: return tile_rows_fixed<Real, VB, 2, false>(w, data, g, r0, r1, lane);
+      case 5: return tile_rows_fixed<Real, VB, 2, true>(w, data, g, r0, r1, lane);
+      case 6: return tile_rows_fixed<Real, VB, 3, false>(w, data, g, r0, r1, lane);
+      case 7: return tile_rows_fixed<Real, VB, 3, true>(w, data, g, r0, r1, lane);
+      default: break;
+    }
+  }
+  tile_rows_rolled<Real, VB>(w, data, g, r0, r1, lane);
 }
 
 // Row-wide forward tile with two vector chunks per row (RP = 1, VC = 2: 33 to
@@ -666,8 +807,64 @@ __device__ __forceinline__ void tile_rows_vc2(WarpTile* w, Real* __restrict__ da
 template <class Real> struct PairPasses { static constexpr int value = sizeof(Real) == 4 ? 4 : 2; };
 template <class Real> struct AdjPairPasses { static constexpr int value = 2; };
 
-template <class Real>
-__device__ __forceinline__ void tile_pairs_regs(WarpTile* w, Real* __restrict__ data, const TileGeom& g, int64_t r0,
+// Lane exchange of one complex number (all 32 lanes).
+__device__ __forceinline__ float2 shfl_xor_cx(float2 v, int m) {
+  v.x = __shfl_xor_sync(0xffffffffu, v.x, m);
+  v.y = __shfl_xor_sync(0xffffffffu, v.y, m);
+  return v;
+}
+__device__ __forceinline__ double2 shfl_xor_cx(double2 v, int m) {
+  v.x = __shfl_xor_sync(0xffffffffu, v.x, m);
+  v.y = __shfl_xor_sync(0xffffffffu, v.y, m);
+  return v;
+}
+__device__ __forceinline__ ff2 shfl_xor_cx(ff2 v, int m) {
+  v.x.hi = __shfl_xor_sync(0xffffffffu, v.x.hi, m);
+  v.x.lo = __shfl_xor_sync(0xffffffffu, v.x.lo, m);
+  v.y.hi = __shfl_xor_sync(0xffffffffu, v.y.hi, m);
+  v.y.lo = __shfl_xor_sync(0xffffffffu, v.y.lo, m);
+  return v;
+}
+
+// Chained step on the one-angle-set layout: lane l holds b's row y = r0 +
+// pass * 32 + l, so chain level j pairs lanes l and l ^ 2^(j-1) (bit j - 1 of
+// y is c_j's eliminated variable): each lane multiplies its row by its leaf
+// element L_j[pext(y, chain mask)] (loaded at the start of the iteration, with
+// the inputs), and the lane with that bit 0 adds its partner's product to its
+// own (w = 0 first, the consumer's order).  After m levels the lanes whose
+// low m bits are 0 hold c_m's rows y >> m.  A group of 2^m rows is either
+// inside the step or wholly past its end (n_rows is a power of two >= 2^m),
+// so idle lanes only meet idle lanes.
+template <class Real, int CM>
+__device__ __forceinline__ void chain_pair_leaves(const WarpTile* w, const Real* __restrict__ data, int pp, int lane,
+                                                  typename Cx<Real>::T (&L)[CM]) {
+  const DevBucket& d = w->d;
+#pragma unroll
+  for (int j = 0; j < CM; ++j)
+    if (!((d.chain_noleaf >> j) & 1)) {
+      const uint32_t t = w->tab[d.n_in + j][pp] + w->lpart[d.n_in + j][lane];
+      L[j] = ldv<Real, 1, false>(data, d.in[d.n_in + j].off + (int64_t)t).c[0];
+    }
+}
+
+template <class Real, int CM>
+__device__ __forceinline__ void chain_pair_rows(const WarpTile* w, Real* __restrict__ data, int64_t y, bool ok,
+                                                int lane, typename Cx<Real>::T o, const typename Cx<Real>::T (&L)[CM]) {
+  const DevBucket& d = w->d;
+#pragma unroll
+  for (int j = 0; j < CM; ++j) {
+    if (!((d.chain_noleaf >> j) & 1)) o = cmul<Real>(o, L[j]);
+    o = cadd<Real>(o, shfl_xor_cx(o, 1 << j));
+  }
+  if (ok && (lane & ((1 << CM) - 1)) == 0) {
+    Pack<Real, 1> v;
+    v.c[0] = o;
+    stv<Real, 1>(data, d.out_off + (y >> CM), v);
+  }
+}
+
+template <class Real, int CM>
+__device__ __forceinline__ void tile_pairs_loop(WarpTile* w, Real* __restrict__ data, const TileGeom& g, int64_t r0,
                                                 int64_t r1, int lane) {
   using P1 = Pack<Real, 1>;
   constexpr int U = PairPasses<Real>::value;
@@ -680,6 +877,12 @@ __device__ __forceinline__ void tile_pairs_regs(WarpTile* w, Real* __restrict__ 
     for (int u = 0; u < U; ++u) {
       y[u] = r0 + (int64_t)(pp + u) * 32 + lane;
       ok[u] = pp + u < g.P && y[u] < r1;
+    }
+    typename Cx<Real>::T L[CM > 0 ? U : 1][CM > 0 ? CM : 1];
+    if constexpr (CM > 0) {
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (pp + u < g.P) chain_pair_leaves<Real, CM>(w, data, pp + u, lane, L[u]);
     }
     P1 p0[U], p1[U];
 #pragma unroll 1
@@ -708,12 +911,23 @@ __device__ __forceinline__ void tile_pairs_regs(WarpTile* w, Real* __restrict__ 
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
+      if constexpr (CM > 0) {
+        if (pp + u >= g.P || r0 + (int64_t)(pp + u) * 32 >= r1) break;  // warp-uniform: past the tile
+        chain_pair_rows<Real, CM>(w, data, y[u], ok[u], lane, cadd<Real>(p0[u].c[0], p1[u].c[0]), L[u]);
+        continue;
+      }
       if (!ok[u]) continue;
       P1 o;
       o.c[0] = cadd<Real>(p0[u].c[0], p1[u].c[0]);
       stv<Real, 1>(data, d.out_off + y[u], o);
     }
   }
+}
+
+template <class Real>
+__device__ __forceinline__ void tile_pairs_regs(WarpTile* w, Real* __restrict__ data, const TileGeom& g, int64_t r0,
+                                                int64_t r1, int lane) {
+  tile_pairs_loop<Real, 0>(w, data, g, r0, r1, lane);
 }
 
 template <class Real>
@@ -947,10 +1161,10 @@ __device__ __forceinline__ void tile_zero(WarpTile* w, Real* __restrict__ data, 
 
 template <class Real> struct RedBuf;
 template <> struct RedBuf<float> {
-  static __device__ __forceinline__ float* get(WarpTile* w) { return &w->redf[0][0]; }
+  static __device__ __forceinline__ float* get(WarpTile* w) { return &w->x.red.f[0][0]; }
 };
 template <> struct RedBuf<double> {
-  static __device__ __forceinline__ double* get(WarpTile* w) { return &w->redd[0][0]; }
+  static __device__ __forceinline__ double* get(WarpTile* w) { return &w->x.red.d[0][0]; }
 };
 
 // Reduction adjoint step (kStepAdjRed).  The tile's rows q = kt * 2^comp_bits
@@ -1320,7 +1534,7 @@ template <class Real, int VB, bool PAIR, bool CG, bool GRAD = false, int STAGE =
 __device__ __forceinline__ void warp_tile(WarpTile* w, Real* __restrict__ data, const TileGeom& g, int64_t r0,
                                           int64_t r1, int lane, DevCtrl* ctrl = nullptr, int dbg_bucket = -1) {
   const DevBucket& d = w->d;
-  const int n_rec = d.kind == kStepAdj ? d.n_in + 1 : d.n_in;
+  const int n_rec = d.kind == kStepAdj ? d.n_in + 1 : d.n_in + (STAGE == 4 && d.kind == kStepFwd ? d.chain : 0);
   int rip, v0;
   bool lane_on;
   lane_slot(g, lane, &rip, &v0, &lane_on);
@@ -1349,10 +1563,25 @@ __device__ __forceinline__ void warp_tile(WarpTile* w, Real* __restrict__ data, 
   if (!GRAD || d.kind == kStepFwd) {  // (adjoint tiles below are compiled only into GRAD kernels)
     // STAGE 2: every forward tile of a row-wide or one-angle-set plan on the
     // lean row / pair path (the launcher picks STAGE 2 only for those
-    // shapes; any other shape is reported, not computed); STAGE 0: the
-    // generic register path
+    // shapes; any other shape is reported, not computed); STAGE 4: the same
+    // plus chained steps (a kernel of its own for plans that have them: the
+    // chained tiles compiled into the STAGE 2 kernel made its other tiles 20 %
+    // slower); STAGE 0: the generic register path
     bool done = false;
-    if (STAGE == 2) {
+    if (STAGE == 4 && d.chain > 0) {  // chained steps: the STAGE 4 lean tiles only (the launcher picks STAGE 4
+                                      // for every plan that has them)
+      if constexpr (STAGE == 4 && !GRAD) {
+        if (!PAIR && g.RP == 1 && g.VC == 1)
+          tile_rows_chained<Real, VB>(w, data, g, r0, r1, lane);
+        else if (PAIR && g.RP == 32 && g.VC == 1 && d.chain == 1)  // (one consumer: the planner's cap)
+          tile_pairs_loop<Real, 1>(w, data, g, r0, r1, lane);
+        else if (lane == 0 && ctrl != nullptr)
+          atomicCAS(&ctrl->status, 0, (int32_t)QT_EINVAL);
+      } else {
+        if (lane == 0 && ctrl != nullptr) atomicCAS(&ctrl->status, 0, (int32_t)QT_EINVAL);
+      }
+      done = true;
+    } else if (STAGE == 2 || STAGE == 4) {
       if (PAIR && g.RP == 32 && g.VC == 1)
         tile_pairs_regs<Real>(w, data, g, r0, r1, lane);
       else if (!PAIR && g.RP == 1 && g.VC == 1)
@@ -1361,7 +1590,7 @@ __device__ __forceinline__ void warp_tile(WarpTile* w, Real* __restrict__ data, 
         atomicCAS(&ctrl->status, 0, (int32_t)QT_EINVAL);
       done = true;
     }
-    if (STAGE == 3) {  // float pairs with two vector chunks per row (a kernel of its own: compiled
+    if (STAGE == 3 && !done) {  // float pairs with two vector chunks per row (a kernel of its own: compiled
                        // into the STAGE 2 kernel, this tile raised that kernel's spills)
       if (!PAIR && g.RP == 1 && g.VC == 2)
         tile_rows_vc2<Real, VB>(w, data, g, r0, r1, lane);

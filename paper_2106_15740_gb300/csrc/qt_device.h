@@ -75,8 +75,21 @@ struct TileGeom {
 //              count them).  Lanes sum over the passes of one k_h, then over
 //              their completion bits (a butterfly), and the lanes whose
 //              completion bits are 0 add one atomic per target element.
+//   kStepFwd with chain = m > 0: bucket b fused with the chain c_1 .. c_m
+//              that eliminates its result: c_1 is b's consumer, c_j the
+//              consumer of c_(j-1), each with no variable beyond its input's
+//              (U_(c_j) = the output variables of c_(j-1)) and no other
+//              intermediate input, so c_j eliminates bit j - 1 of b's rows.
+//              The step iterates b's rows y (n_rows = 2^out_rank of b) and
+//              writes c_m's row y >> m at out_off.  With G_0 = G_b (the
+//              product-sum above, never stored):
+//              G_j[y >> j] = sum_w G_(j-1)[(y >> (j-1)) | w] * L_j[pext(y', in[n_in + j - 1].mask)]
+//              for y' = y with bit j - 1 set to w: L_j is c_j's leaf factor,
+//              its mask over b's rows (bit j - 1 = w at bit 0 of the index),
+//              or 1 when bit j - 1 of chain_noleaf is set.
 constexpr int32_t kStepFwd = 0, kStepAdj = 1, kStepZero = 2, kStepAdjRed = 3;
 constexpr int32_t kAdjFull = 1, kAdjUnitG = 2, kAdjRedLow = 4;
+constexpr int kMaxChain = 3;  // consumers fused into one forward step at most
 
 struct DevBucket {
   int64_t out_off;             // element offset of the output
@@ -86,12 +99,14 @@ struct DevBucket {
   int32_t dep;                 // first entry of the step's list in the plan's dependency array
   int32_t ntask;               // chunks of this step in the persistent queue (its done count)
   int32_t kind;                // kStep*
-  int32_t aflags;              // kAdj* bits (kStepAdj)
+  int32_t aflags;              // kAdj* bits (adjoint steps)
   int32_t tgt_bits;            // kStepAdjRed: target rows 2^tgt_bits (times x = 0, 1); kAdjRedLow: target bits above bit 4
   int32_t comp_bits;           // kStepAdjRed: completions per target row 2^comp_bits (>= 5); kAdjRedLow: completion bits above bit 4
   int32_t span;                // warp tiles per queue task (chunk c covers tiles [c*span, (c+1)*span))
   int32_t n_dep;               // steps that must be complete before a task of this one starts:
                                // deps[dep .. dep + n_dep) (done count of each = its ntask)
+  int32_t chain;               // kStepFwd: consumers fused into the step (0 .. kMaxChain)
+  int32_t chain_noleaf;        // kStepFwd: bit j - 1 set if consumer c_j has no leaf factor
   DevInput in[kDevMaxIn];
 };
 

@@ -33,7 +33,7 @@ class EnergyPlan:
                  max_workspace=0, max_width=0, device="cuda:0", gradient=False, lane_items=0,
                  group_rows=0, edge_range=None, slice=False, chunk_tiles=0, order_trials=0, order_seed=0,
                  order_tau=1.0, checkpoint_bytes=0, chain_steps=False,
-                 queue_order="critical_path", chunk_tiles_by_rank=None):
+                 queue_order="critical_path", chunk_tiles_by_rank=None, fuse_chains=3):
         self.n_vertices, self.p, self.batch = int(n_vertices), int(p), int(batch)
         self.edges = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
         self.device = torch.device(device)
@@ -44,7 +44,8 @@ class EnergyPlan:
                             chunk_tiles=chunk_tiles, order_trials=order_trials, order_seed=order_seed,
                             order_tau=order_tau,
                             checkpoint_bytes=checkpoint_bytes, chain_steps=chain_steps,
-                            queue_order=queue_order, chunk_tiles_by_rank=chunk_tiles_by_rank)
+                            queue_order=queue_order, chunk_tiles_by_rank=chunk_tiles_by_rank,
+                            fuse_chains=fuse_chains)
         opt = qb.qt_plan_options_default()
         opt.batch = self.batch
         opt.dtype = DTYPES[dtype]
@@ -65,6 +66,7 @@ class EnergyPlan:
         opt.queue_order = QUEUE_ORDERS[queue_order]
         for r, t in (chunk_tiles_by_rank or {}).items():  # {output rank: warp tiles per queue task}
             opt.chunk_tiles_by_rank[int(r)] = int(t)
+        opt.fuse_chains = int(fuse_chains)  # consumers fused into a step at most (0: none)
         self.plan = qb.qt_plan_create(self.n_vertices, self.edges, self.p, opt)
         self.ws_bytes = qb.qt_plan_workspace_size(self.plan)
         self.stats = qb.qt_plan_stats(self.plan)

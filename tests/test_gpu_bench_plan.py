@@ -3,8 +3,8 @@
 The benchmark evaluates every edge lightcone of the 100-vertex p = 4 graph
 (150 edges) for 64 angle sets in complex64, with per-edge searched orders
 (100 randomised greedy trials), the tile its autotuner picked on the GB300
-(64 items per lane, no grouping of small steps), one persistent launch
-replayed from a CUDA graph.  Here that plan, in that launch form, is
+(64 items per lane, no grouping of small steps), chained buckets fused into
+one step, one persistent launch replayed from a CUDA graph.  Here that plan, in that launch form, is
 checked against the FP64 oracle (the lightcone contraction of
 oracle/lightcone.py) on every edge for two of the 64 angle sets:
 
@@ -58,11 +58,21 @@ def oracle_zz(bench_plan_run):
 
 
 def test_bench_plan_is_the_timed_plan(bench_plan_run):
-    """Searched orders: widths 10..20 and 82.7 GB of algorithmic traffic per
-    evaluation (the figure the benchmark's roofline divides)."""
+    """Searched orders: widths 10..20 and 34.1 GB of algorithmic traffic per
+    evaluation (the figure the benchmark's roofline divides); 82.7 GB with
+    every bucket a step of its own."""
+    from paper_2106_15740_gb300 import binding as qb
     r = bench_plan_run
     assert r["widths"].min() >= 10 and r["widths"].max() <= 20
-    assert abs(r["alg"] - 82730662912.0) / 82730662912.0 < 1e-9
+    assert abs(r["alg"] - 34051691520.0) / 34051691520.0 < 1e-9
+    opt = qb.qt_plan_options_default()
+    opt.batch, opt.dtype, opt.mode, opt.order_trials = 64, qb.QT_C64, qb.QT_MODE_PERSISTENT, 100
+    opt.lane_items, opt.group_rows, opt.fuse_chains = 64, -1, 0
+    plan = qb.qt_plan_create(r["n"], r["edges"], r["p"], opt)
+    try:
+        assert abs(qb.qt_plan_stats(plan)["alg_bytes"] - 82730662912.0) / 82730662912.0 < 1e-9
+    finally:
+        qb.qt_plan_free(plan)
 
 
 def test_every_edge_matches_oracle(bench_plan_run, oracle_zz):
