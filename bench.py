@@ -62,6 +62,19 @@ def _kernel_digest():
     return h.hexdigest()[:16]
 
 
+# Captures of the chained-step plan (which needs 34 or more angle sets, so a
+# B = 4 capture does not have its steps) are taken on two edge ranges of the
+# bench graph at B = 64 and give DRAM bytes per algorithmic byte; the two
+# ranges agree when traffic grows in proportion to the plan's bytes, and the
+# full launch's traffic is that ratio times its algorithmic bytes.
+TRAFFIC_RATIO_CAPTURES = [
+    # orders searched per edge (100 trials), chained steps of up to three consumers, the
+    # longest-path queue; edges 40-80 and 0-40 at B = 64 (profiles/persistent_kernel_n100p4_b64_dram.md)
+    {"sources_sha256_16": "615f58709fc2a191", "queue_order": "critical_path", "batch": 64, "fuse_chains": 3,
+     "dram_bytes_per_alg_byte": (4694877696 + 5017392896 + 5532984320 + 5726372864) / (8730376192 + 9919264768)},
+]
+
+
 def _traffic(B, alg_bytes, profile_only):
     if profile_only:
         return None
@@ -71,6 +84,10 @@ def _traffic(B, alg_bytes, profile_only):
         if (cap["sources_sha256_16"] == digest and cap["queue_order"] == order
                 and abs(alg_bytes / B / cap["alg_bytes_per_angle_set"] - 1) < 1e-9):
             return cap["bytes_per_angle_set"] * B
+    for cap in TRAFFIC_RATIO_CAPTURES:
+        if (cap["sources_sha256_16"] == digest and cap["queue_order"] == order and cap["batch"] == B
+                and cap["fuse_chains"] == WORKLOAD.get("fuse_chains", 3)):
+            return cap["dram_bytes_per_alg_byte"] * alg_bytes
     return None
 
 
@@ -284,10 +301,12 @@ def _plan_variant(n, edges, p, B, g, b, dev, torch, what, **kw):
     plan = EnergyPlan(n, edges, p, batch=B, dtype=WORKLOAD["dtype"], mode="persistent", device=dev,
                       order_trials=WORKLOAD.get("order_trials", 0), lane_items=WORKLOAD.get("lane_items", 0),
                       group_rows=WORKLOAD.get("group_rows", 0), **kw)
-    ms = _time_calls(plan, g, b, False, 5, torch)
+    ms, kms = _time_calls(plan, g, b, False, 5, torch, kernel=True)
+    peak, peak_kind = _peaks()
     out = {"value": len(edges) * B / (ms * 1e-3), "unit": "edge_evals/s", "ms_per_step": ms,
            "alg_bytes_per_step": plan.stats["alg_bytes"],
-           "achieved_gbs": plan.stats["alg_bytes"] / (ms * 1e-3) / 1e9, "what": what}
+           "achieved_gbs": plan.stats["alg_bytes"] / (ms * 1e-3) / 1e9, "what": what,
+           "roofline": _roofline(plan.stats["alg_bytes"], kms, peak, peak_kind, "persistent_kernel")}
     plan.close()
     torch.cuda.empty_cache()
     return out
