@@ -277,10 +277,21 @@ def _time_calls(plan, g, b, grad, reps, torch, kernel=False):
     return ms, sum(k) / max(1, len(k))
 
 
-def _roofline(alg_bytes, kernel_ms, peak, peak_kind, kernel):
+def _roofline(alg_bytes, kernel_ms, peak, peak_kind, kernel, stored_bytes=None):
+    """Roofline of one launch: algorithmic bytes counted bucket by bucket
+    (every bucket's intermediate inputs and result, the plan's per-unit figure
+    times its units) over the kernel time.  A plan with chained steps stores
+    and reads fewer bytes (`stored_bytes`), reported beside it."""
     achieved = alg_bytes / (kernel_ms * 1e-3) / 1e9
-    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "kernel": kernel, "kernel_ms": kernel_ms, "alg_bytes_per_launch": alg_bytes, "peak_kind": peak_kind}
+    out = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+           "kernel": kernel, "kernel_ms": kernel_ms, "alg_bytes_per_launch": alg_bytes, "peak_kind": peak_kind}
+    if stored_bytes is not None and stored_bytes != alg_bytes:
+        out["stored_bytes_per_launch"] = stored_bytes
+        out["frac_of_stored_bytes"] = stored_bytes / (kernel_ms * 1e-3) / 1e9 / peak
+        out["alg_bytes_what"] = ("bucket by bucket: every bucket's intermediate inputs and result; the chained "
+                                 "steps keep the results of the buckets they absorb in registers, so the launch "
+                                 "stores and reads stored_bytes_per_launch")
+    return out
 
 
 def min_fill_comparison(n, edges, p, B, g, b, dev, torch):
@@ -303,10 +314,11 @@ def _plan_variant(n, edges, p, B, g, b, dev, torch, what, **kw):
                       group_rows=WORKLOAD.get("group_rows", 0), **kw)
     ms, kms = _time_calls(plan, g, b, False, 5, torch, kernel=True)
     peak, peak_kind = _peaks()
+    alg = plan.bucket_bytes()
     out = {"value": len(edges) * B / (ms * 1e-3), "unit": "edge_evals/s", "ms_per_step": ms,
-           "alg_bytes_per_step": plan.stats["alg_bytes"],
-           "achieved_gbs": plan.stats["alg_bytes"] / (ms * 1e-3) / 1e9, "what": what,
-           "roofline": _roofline(plan.stats["alg_bytes"], kms, peak, peak_kind, "persistent_kernel")}
+           "alg_bytes_per_step": alg, "stored_bytes_per_step": plan.stats["alg_bytes"],
+           "achieved_gbs": alg / (ms * 1e-3) / 1e9, "what": what,
+           "roofline": _roofline(alg, kms, peak, peak_kind, "persistent_kernel", plan.stats["alg_bytes"])}
     plan.close()
     torch.cuda.empty_cache()
     return out
@@ -438,20 +450,23 @@ def complex128_counterparts(dev, torch):
             ms, kms = _time_calls(plan, gd, bd, False, 5, torch, kernel=True)
             e, zz = plan.energy(gd, bd, edge_zz=True)
             plan.check()
-            r[dt] = dict(ms=ms, kms=kms, alg=plan.stats["alg_bytes"], e=e.cpu().numpy(), zz=zz.cpu().numpy())
+            r[dt] = dict(ms=ms, kms=kms, alg=plan.bucket_bytes(), stored=plan.stats["alg_bytes"],
+                         e=e.cpu().numpy(), zz=zz.cpu().numpy())
             plan.close()
         key = "n100_p4_b64" if B == 64 else "n100_p3_b1"
         out[key] = {
             "c128": {"value": len(edges) * B / (r["c128"]["ms"] * 1e-3), "unit": "edge_evals/s",
                      "ms_per_call": r["c128"]["ms"],
-                     "roofline": _roofline(r["c128"]["alg"], r["c128"]["kms"], peak, peak_kind, "persistent_kernel<double,...>")},
+                     "roofline": _roofline(r["c128"]["alg"], r["c128"]["kms"], peak, peak_kind, "persistent_kernel<double,...>",
+                                           r["c128"]["stored"])},
             "c64": {"value": len(edges) * B / (r["c64"]["ms"] * 1e-3), "unit": "edge_evals/s",
                     "ms_per_call": r["c64"]["ms"],
-                    "roofline": _roofline(r["c64"]["alg"], r["c64"]["kms"], peak, peak_kind, "persistent_kernel<float,...>")},
+                    "roofline": _roofline(r["c64"]["alg"], r["c64"]["kms"], peak, peak_kind, "persistent_kernel<float,...>",
+                                           r["c64"]["stored"])},
             "c64x2": {"value": len(edges) * B / (r["c64x2"]["ms"] * 1e-3), "unit": "edge_evals/s",
                       "ms_per_call": r["c64x2"]["ms"],
                       "roofline": _roofline(r["c64x2"]["alg"], r["c64x2"]["kms"], peak, peak_kind,
-                                            "persistent_kernel<ff,...> (float pairs)")},
+                                            "persistent_kernel<ff,...> (float pairs)", r["c64x2"]["stored"])},
             "c64_vs_c128": {"max_abs_dzz": float(np.abs(r["c64"]["zz"][:, :, 0] - r["c128"]["zz"][:, :, 0]).max()),
                             "max_abs_dE": float(np.abs(r["c64"]["e"] - r["c128"]["e"]).max())},
             "c64x2_vs_c128": {"max_abs_dzz": float(np.abs(r["c64x2"]["zz"][:, :, 0] - r["c128"]["zz"][:, :, 0]).max()),
@@ -482,7 +497,8 @@ def large_config(dev, torch):
     out["energy_c64"] = {"value": len(edges) / (ms * 1e-3), "unit": "edge_evals/s", "ms_per_call": ms,
                          "max_width": int(plan.widths.max()), "sliced_edges": int((plan.slices > 0).sum()),
                          "networks": int((2 ** plan.slices.astype(np.int64)).sum()),
-                         "roofline": _roofline(plan.stats["alg_bytes"], kms, peak, peak_kind, "persistent_kernel<float,1,true,false,4>")}
+                         "roofline": _roofline(plan.bucket_bytes(), kms, peak, peak_kind,
+                                               "persistent_kernel<float,1,true,false,4>", plan.stats["alg_bytes"])}
     plan.close()
     torch.cuda.empty_cache()
     plan = EnergyPlan(n, edges, p, dtype="c64", fuse_chains=0, **kw)
@@ -507,8 +523,9 @@ def large_config(dev, torch):
     ex2, zzx2 = plan.energy(gd, bd, edge_zz=True)
     plan.check()
     out["energy_c64x2"] = {"value": len(edges) / (msx2 * 1e-3), "unit": "edge_evals/s", "ms_per_call": msx2,
-                           "roofline": _roofline(plan.stats["alg_bytes"], kmsx2, peak, peak_kind,
-                                                 "persistent_kernel<ff,1,true,false,4> (float pairs)")}
+                           "roofline": _roofline(plan.bucket_bytes(), kmsx2, peak, peak_kind,
+                                                 "persistent_kernel<ff,1,true,false,4> (float pairs)",
+                                                 plan.stats["alg_bytes"])}
     plan.close()
     torch.cuda.empty_cache()
     plan = EnergyPlan(n, edges, p, dtype="c128", **kw)
@@ -691,7 +708,8 @@ def run_ours(args):
 
     peak, peak_kind = _peaks()
     kms = sum(kernel_ms) / max(1, len(kernel_ms))
-    alg = plan.stats["alg_bytes"]
+    stored = plan.stats["alg_bytes"]  # what the plan's steps store and read
+    alg = plan.bucket_bytes()  # bucket by bucket (every bucket's inputs and result): the roofline's bytes
     achieved = alg / (kms * 1e-3) / 1e9
     if rank == 0:
         res = {
@@ -705,7 +723,7 @@ def run_ours(args):
                        "ordering": (f"per edge the cheapest of greedy min-fill and {WORKLOAD.get('order_trials', 0)} "
                                     "seeded randomised greedy orders (seed 0, tau 1), no wider than min-fill"
                                     if WORKLOAD.get("order_trials", 0) else "greedy min-fill"),
-                       "alg_bytes_per_step": alg,
+                       "alg_bytes_per_step": alg, "stored_bytes_per_step": stored,
                        "n_vertices": n, "p": p, "edges": len(edges), "angle_sets_per_gpu": B,
                        "max_width": int(plan.stats["max_width"]), "buckets": plan.stats["n_buckets"],
                        "width_histogram": {int(w): int(c) for w, c in zip(*np.unique(plan.widths, return_counts=True))},
@@ -713,11 +731,10 @@ def run_ours(args):
                        "l2": "working set larger than L2 (intermediates streamed through HBM every step)",
                        "plan_host_s": round(t_plan, 3),
                        "alg_bytes_by_result_rank": bytes_by_rank(plan.plan, B, 8 if WORKLOAD["dtype"] == "c64" else 16)},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": _traffic(B, alg, profile_only),
-                         "kernel": "persistent_kernel<float,2,false,false,4>",
-                         "kernel_ms": kms, "kernel_ms_from": "CUDA events around the persistent launch over "
-                                                             "K direct calls after the graph-timed steps", "alg_bytes_per_launch": alg, "peak_kind": peak_kind},
+            "roofline": dict(_roofline(alg, kms, peak, peak_kind, "persistent_kernel<float,2,false,false,4>", stored),
+                             traffic=_traffic(B, stored, profile_only),
+                             kernel_ms_from="CUDA events around the persistent launch over K direct calls after "
+                                            "the graph-timed steps"),
             "e2e": {"value": units * world / e2e_s, "unit": "edge_evals/s",
                     "h2d_bytes_per_step": int(2 * B * p * 8), "d2h_bytes_per_step": int(B * 8)},
             "gpu_launches": (7 if grad else 4) * args.steps,

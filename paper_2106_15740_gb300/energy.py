@@ -46,33 +46,54 @@ class EnergyPlan:
                             checkpoint_bytes=checkpoint_bytes, chain_steps=chain_steps,
                             queue_order=queue_order, chunk_tiles_by_rank=chunk_tiles_by_rank,
                             fuse_chains=fuse_chains)
-        opt = qb.qt_plan_options_default()
-        opt.batch = self.batch
-        opt.dtype = DTYPES[dtype]
-        opt.mode = MODES[mode]
-        opt.gradient = int(bool(gradient))
-        opt.max_width = int(max_width)
-        opt.max_workspace = int(max_workspace)
-        opt.lane_items = int(lane_items)
-        opt.group_rows = int(group_rows)
-        opt.edge_begin, opt.edge_end = self.edge_range
-        opt.slice = int(bool(slice))
-        opt.chunk_tiles = int(chunk_tiles)
-        opt.order_trials = int(order_trials)
-        opt.order_seed = int(order_seed)
-        opt.order_tau = float(order_tau)
-        opt.checkpoint_bytes = int(checkpoint_bytes)
-        opt.chain_steps = int(bool(chain_steps))
-        opt.queue_order = QUEUE_ORDERS[queue_order]
-        for r, t in (chunk_tiles_by_rank or {}).items():  # {output rank: warp tiles per queue task}
-            opt.chunk_tiles_by_rank[int(r)] = int(t)
-        opt.fuse_chains = int(fuse_chains)  # consumers fused into a step at most (0: none)
+        opt = self._plan_options()
         self.plan = qb.qt_plan_create(self.n_vertices, self.edges, self.p, opt)
         self.ws_bytes = qb.qt_plan_workspace_size(self.plan)
         self.stats = qb.qt_plan_stats(self.plan)
         self.widths = qb.qt_plan_edge_widths(self.plan, self.n_edges)
         self.slices = qb.qt_plan_edge_slices(self.plan, self.n_edges)
         self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+
+    def _plan_options(self, **override):
+        """The plan options of this plan (qt_plan_options), with any field overridden."""
+        o = dict(self.options, **override)
+        opt = qb.qt_plan_options_default()
+        opt.batch = self.batch
+        opt.dtype = DTYPES[o["dtype"]]
+        opt.mode = MODES[o["mode"]]
+        opt.gradient = int(bool(o["gradient"]))
+        opt.max_width = int(o["max_width"])
+        opt.max_workspace = int(o["max_workspace"])
+        opt.lane_items = int(o["lane_items"])
+        opt.group_rows = int(o["group_rows"])
+        opt.edge_begin, opt.edge_end = self.edge_range
+        opt.slice = int(bool(o["slice"]))
+        opt.chunk_tiles = int(o["chunk_tiles"])
+        opt.order_trials = int(o["order_trials"])
+        opt.order_seed = int(o["order_seed"])
+        opt.order_tau = float(o["order_tau"])
+        opt.checkpoint_bytes = int(o["checkpoint_bytes"])
+        opt.chain_steps = int(bool(o["chain_steps"]))
+        opt.queue_order = QUEUE_ORDERS[o["queue_order"]]
+        for r, t in (o["chunk_tiles_by_rank"] or {}).items():  # {output rank: warp tiles per queue task}
+            opt.chunk_tiles_by_rank[int(r)] = int(t)
+        opt.fuse_chains = int(o["fuse_chains"])  # consumers fused into a step at most (0: none)
+        return opt
+
+    def bucket_bytes(self):
+        """Algorithmic bytes of one evaluation counted bucket by bucket (every
+        bucket's intermediate inputs read and its result written), as if no
+        bucket were fused with its consumers: the figure a roofline divides.
+        The chained steps of this plan store and read fewer bytes
+        (``stats["alg_bytes"]``).  Plans the same orders on the host; no
+        device memory."""
+        if int(self.options["fuse_chains"]) == 0 or self.options["gradient"]:
+            return self.stats["alg_bytes"]
+        h = qb.qt_plan_create(self.n_vertices, self.edges, self.p, self._plan_options(fuse_chains=0))
+        try:
+            return qb.qt_plan_stats(h)["alg_bytes"]
+        finally:
+            qb.qt_plan_free(h)
 
     @property
     def n_edges(self):

@@ -183,3 +183,21 @@ def test_fuse_option_is_validated(qtlib, value):
     with pytest.raises(qb.QTError) as ei:
         qb.qt_plan_create(8, random_regular_graph(8, 3, 39), 1, opt)
     assert ei.value.status == qb.QT_EINVAL
+
+
+def test_bucket_bytes_count_every_bucket(qtlib):
+    """EnergyPlan.bucket_bytes: the roofline's bytes, bucket by bucket, equal
+    the unfused plan's algorithmic bytes whatever the chain length (a host
+    plan; the workspace here is host memory and nothing is evaluated)."""
+    from paper_2106_15740_gb300.energy import EnergyPlan
+    n = 16
+    edges = random_regular_graph(n, 3, 56)
+    plans = [EnergyPlan(n, edges, 3, batch=64, dtype="c64", mode="persistent", device="cpu", fuse_chains=f)
+             for f in (0, 1, 3)]
+    try:
+        unfused = plans[0].stats["alg_bytes"]
+        assert plans[2].stats["alg_bytes"] < plans[1].stats["alg_bytes"] < unfused
+        assert all(pl.bucket_bytes() == unfused for pl in plans)
+    finally:
+        for pl in plans:
+            pl.close()
