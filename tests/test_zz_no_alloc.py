@@ -112,3 +112,34 @@ def test_static_scratch_rejects_plans_above_its_size():
         assert ei.value.status == qb.QT_ENOMEM
     finally:
         qb.qt_plan_free(plan)
+
+
+def test_static_scratch_chained_plan():
+    """A plan with chained steps (complex64, one angle set: its kernel is the
+    chained-step instantiation) gives the workspace call's values bit for bit
+    through the static array."""
+    from paper_2106_15740_gb300 import binding as qb
+    plan, n_edges, p = _plan("n100_p3", 1, qb.QT_C64, qb.QT_MODE_PERSISTENT)
+    try:
+        assert qb.qt_plan_tasks(plan)["kind"].size > 0
+        ws_bytes = qb.qt_plan_workspace_size(plan)
+        assert ws_bytes <= qb.qt_static_scratch_bytes()
+        stream = torch.cuda.current_stream().cuda_stream
+        ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda:0")
+        g, b = random_angles(1, p, 9)
+        gd = torch.tensor(g, device="cuda:0")
+        bd = torch.tensor(b, device="cuda:0")
+        out = []
+        for static in (False, True):
+            e = torch.full((1,), np.nan, dtype=torch.float64, device="cuda:0")
+            zz = torch.full((n_edges, 1, 2), np.nan, dtype=torch.float64, device="cuda:0")
+            if static:
+                qb.qt_plan_energy_static(plan, gd.data_ptr(), bd.data_ptr(), e.data_ptr(), zz.data_ptr(), stream)
+            else:
+                qb.qt_plan_energy(plan, gd.data_ptr(), bd.data_ptr(), e.data_ptr(), zz.data_ptr(), 0,
+                                  ws.data_ptr(), ws_bytes, stream)
+            qb.qt_plan_check(plan, stream)
+            out.append((e.cpu().numpy(), zz.cpu().numpy()))
+        assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    finally:
+        qb.qt_plan_free(plan)
