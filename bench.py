@@ -79,7 +79,7 @@ def _traffic(B, alg_bytes, profile_only):
     if profile_only:
         return None
     digest = _kernel_digest()
-    order = WORKLOAD.get("queue_order", "critical_path")
+    order = WORKLOAD.get("queue_order", "simulated")
     for cap in TRAFFIC_CAPTURES:
         if (cap["sources_sha256_16"] == digest and cap["queue_order"] == order
                 and abs(alg_bytes / B / cap["alg_bytes_per_angle_set"] - 1) < 1e-9):
@@ -334,10 +334,18 @@ def chain_comparison(n, edges, p, B, g, b, dev, torch):
 
 def round_robin_comparison(n, edges, p, B, g, b, dev, torch):
     """The bench step with the queue taken round-robin over the workspace
-    slots, step by step, instead of longest remaining path first."""
+    slots, step by step, instead of the simulated list-scheduling order."""
     return _plan_variant(n, edges, p, B, g, b, dev, torch,
                          "same plan and tile, queue round-robin over slots step by step (direct calls)",
                          queue_order="round_robin")
+
+
+def critical_path_comparison(n, edges, p, B, g, b, dev, torch):
+    """The bench step with the queue sorted by longest remaining dependency
+    path alone (no simulation of the warps)."""
+    return _plan_variant(n, edges, p, B, g, b, dev, torch,
+                         "same plan and tile, queue sorted by longest remaining path (direct calls)",
+                         queue_order="critical_path")
 
 
 def unfused_comparison(n, edges, p, B, g, b, dev, torch):
@@ -631,7 +639,7 @@ def run_ours(args):
                       gradient=grad, max_width=WORKLOAD.get("max_width", 0), slice=WORKLOAD.get("slice", False),
                       max_workspace=WORKLOAD.get("max_workspace", 0), order_trials=WORKLOAD.get("order_trials", 0),
                       chain_steps=WORKLOAD.get("chain_steps", False),
-                      queue_order=WORKLOAD.get("queue_order", "critical_path"),
+                      queue_order=WORKLOAD.get("queue_order", "simulated"),
                       chunk_tiles_by_rank=WORKLOAD.get("chunk_tiles_by_rank"))
     t_plan = time.perf_counter() - t_plan
     from paper_2106_15740_gb300.schedule import bytes_by_rank
@@ -755,6 +763,7 @@ def run_ours(args):
         if not profile_only:
             res["chained_steps"] = chain_comparison(n, edges, p, B, g, b, dev, torch)
             res["round_robin_queue"] = round_robin_comparison(n, edges, p, B, g, b, dev, torch)
+            res["critical_path_queue"] = critical_path_comparison(n, edges, p, B, g, b, dev, torch)
             res["unfused_chains"] = unfused_comparison(n, edges, p, B, g, b, dev, torch)
         if not args.no_cpu_baseline:
             e_gpu, zz = plan.energy(g, b, edge_zz=True)
@@ -793,7 +802,7 @@ def main():
     ap.add_argument("--max-workspace-gb", type=float, default=0, help="profiling only: workspace cap")
     ap.add_argument("--chain-steps", action="store_true",
                     help="profiling only: chain every step of a workspace slot to the one before it")
-    ap.add_argument("--queue-order", default=None, choices=["round_robin", "critical_path"],
+    ap.add_argument("--queue-order", default=None, choices=["round_robin", "critical_path", "simulated"],
                     help="profiling only: order of the persistent queue")
     ap.add_argument("--order-trials", type=int, default=None,
                     help="profiling only: randomised greedy orders per edge (0: min-fill)")

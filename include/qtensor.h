@@ -183,11 +183,13 @@ typedef struct {
                              step waits for the step planned before it on its slot (one chain
                              per slot).  Energies are bit-identical either way; gradients agree
                              up to the order of the atomic additions some adjoint steps make */
-  int32_t queue_order;    /* persistent mode: 1 (default) the queue takes first the tasks with
-                             the longest remaining dependency path (estimated time through their
-                             dependents to the end of their slot), which starts long paths
-                             early; 0 it takes the slots round-robin, step by step.  Results are
-                             bit-identical either way */
+  int32_t queue_order;    /* persistent mode: 2 (default) the queue is the order in which a
+                             list-scheduling simulation of the launch's warps (estimated task
+                             times) starts the tasks, each warp taking the ready task with the
+                             longest remaining dependency path; 1 the queue takes first the tasks
+                             with the longest remaining dependency path (estimated time through
+                             their dependents to the end of their slot); 0 it takes the slots
+                             round-robin, step by step.  Results are bit-identical either way */
   int32_t chunk_tiles_by_rank[32]; /* persistent mode, per-width schedule: a step whose output rank
                              is r runs in queue tasks of chunk_tiles_by_rank[r] warp tiles when that
                              is > 0 (at least as many as the queue-length rule asks for), else as

@@ -258,7 +258,7 @@ void qt_plan_options_default(qt_plan_options* opt) {
   opt->order_tau = 1.0;
   opt->checkpoint_bytes = 0;
   opt->chain_steps = 0;
-  opt->queue_order = 1;
+  opt->queue_order = 2;
   for (int32_t r = 0; r < 32; ++r) opt->chunk_tiles_by_rank[r] = 0;
   opt->fuse_chains = kMaxChain;
 }
@@ -287,7 +287,7 @@ static qt_status check_options(const qt_plan_options* opt, qt_plan_options* out)
   if (!(o.order_tau >= 0.0) || !std::isfinite(o.order_tau)) return fail(QT_EINVAL, "order_tau must be finite and >= 0");
   if (o.checkpoint_bytes < 0) return fail(QT_EINVAL, "checkpoint_bytes must be >= 0");
   if (o.chain_steps != 0 && o.chain_steps != 1) return fail(QT_EINVAL, "chain_steps must be 0 or 1");
-  if (o.queue_order != 0 && o.queue_order != 1) return fail(QT_EINVAL, "queue_order must be 0 or 1");
+  if (o.queue_order < 0 || o.queue_order > 2) return fail(QT_EINVAL, "queue_order must be 0, 1 or 2");
   if (o.fuse_chains < 0 || o.fuse_chains > kMaxChain)
     return fail(QT_EINVAL, "fuse_chains must be 0 .. " + std::to_string(kMaxChain));
   for (int32_t r = 0; r < 32; ++r)

@@ -353,6 +353,9 @@ static int64_t plan_gradient_network(const EdgePlan& ep, int64_t B, int64_t budg
   return A.peak;
 }
 
+// Warps the queue's list-scheduling simulation assumes (152 SMs x 4 blocks x 8 warps).
+constexpr int64_t kSimWarps = 4864;
+
 qt_status compile_plan(Plan* P) {
   const int32_t B = P->opt.batch;
   const int32_t es = P->elem_bytes;
@@ -868,21 +871,21 @@ qt_status compile_plan(Plan* P) {
         }
       }
     }
-    if (P->opt.queue_order == 1) {
-      // List scheduling: the units (a step's chunks, or a group) whose
-      // remaining dependency path -- estimated time through their dependents
-      // to the end of the slot -- is longest go first.  A dependency's path
-      // is longer than each of its dependents', so it stays earlier in the
-      // queue.  Estimated time of a task: 4 + 0.6 per warp pass over its
-      // rows (RP rows a pass; in microseconds, from queue traces), times the
-      // rounds its chunks need on about 4096 warps.
+    if (P->opt.queue_order >= 1) {
+      // Priorities: the units (a step's chunks, or a group) whose remaining
+      // dependency path -- estimated time through their dependents to the end
+      // of the slot -- is longest go first.  A dependency's path is longer
+      // than each of its dependents', so it stays earlier in the queue.
+      // Estimated time of a task: 4 + 0.6 per warp pass over its rows (RP
+      // rows a pass; in microseconds, from queue traces), times the rounds
+      // its chunks need on about 4096 warps.
       std::vector<int64_t> ustart;
       for (int64_t t = 0; t < (int64_t)P->tasks.size(); ++t)
         if (t == 0 || P->tasks[t].bucket != P->tasks[t - 1].bucket) ustart.push_back(t);
       const int64_t nu = (int64_t)ustart.size();
       ustart.push_back((int64_t)P->tasks.size());
       std::vector<int32_t> unit_of(P->buckets.size(), -1);
-      std::vector<double> w(nu, 0.0), path(nu, 0.0), below(nu, 0.0);
+      std::vector<double> w(nu, 0.0), path(nu, 0.0), below(nu, 0.0), task_us(nu, 0.0);
       for (int64_t u = 0; u < nu; ++u) {
         const DevTask& t = P->tasks[ustart[u]];
         const int32_t k = t.chunk < 0 ? -t.chunk : 1;
@@ -891,7 +894,9 @@ qt_status compile_plan(Plan* P) {
           unit_of[t.bucket + j] = (int32_t)u;
           const int64_t rows = std::min<int64_t>(d.n_rows, (int64_t)d.span * geom.R);
           const double passes = (double)((rows + geom.RP - 1) / geom.RP);
-          w[u] += (4.0 + 0.6 * passes) * (double)((d.ntask + 4095) / 4096);
+          const double us = 4.0 + 0.6 * passes;
+          w[u] += us * (double)((d.ntask + 4095) / 4096);
+          task_us[u] += us;
         }
       }
       for (int64_t u = nu - 1; u >= 0; --u) {
@@ -902,12 +907,73 @@ qt_status compile_plan(Plan* P) {
           if (v >= 0) below[v] = std::max(below[v], path[u]);  // every queued step has a unit
         }
       }
-      std::vector<int64_t> order(nu);
-      for (int64_t u = 0; u < nu; ++u) order[u] = u;
-      std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return path[a] > path[b]; });
       std::vector<DevTask> sorted;
       sorted.reserve(P->tasks.size());
-      for (int64_t u : order) sorted.insert(sorted.end(), P->tasks.begin() + ustart[u], P->tasks.begin() + ustart[u + 1]);
+      if (P->opt.queue_order == 1) {
+        std::vector<int64_t> order(nu);
+        for (int64_t u = 0; u < nu; ++u) order[u] = u;
+        std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return path[a] > path[b]; });
+        for (int64_t u : order) sorted.insert(sorted.end(), P->tasks.begin() + ustart[u], P->tasks.begin() + ustart[u + 1]);
+      } else {
+        // queue_order 2: simulated list scheduling.  kSimWarps warps take the
+        // ready task of the longest path whenever one is free, each task
+        // taking its estimated time; a unit's tasks become ready when every
+        // unit it depends on has finished; the queue is the order in which
+        // the simulation starts the tasks.  A claimed task then waits less
+        // often for a dependency still running (with the path order alone, a
+        // dependent often sits right behind its dependency).  Every
+        // dependency still comes earlier in the queue.  (Weighing the
+        // estimate by step kind from queue traces, or the warp count of the
+        // 3-block kernel, measured slightly slower.)
+        std::vector<std::vector<int32_t>> dependents(nu);
+        std::vector<int32_t> pending(nu, 0), left(nu, 0);
+        for (int64_t u = 0; u < nu; ++u) {
+          const DevBucket& d = P->buckets[P->tasks[ustart[u]].bucket];
+          std::vector<int32_t> vs;
+          for (int32_t q = 0; q < d.n_dep; ++q) {
+            const int32_t v = unit_of[P->deps[d.dep + q]];
+            if (v >= 0 && v != (int32_t)u) vs.push_back(v);
+          }
+          std::sort(vs.begin(), vs.end());
+          vs.erase(std::unique(vs.begin(), vs.end()), vs.end());
+          pending[u] = (int32_t)vs.size();
+          for (int32_t v : vs) dependents[v].push_back((int32_t)u);
+          left[u] = (int32_t)(ustart[u + 1] - ustart[u]);
+        }
+        using Ready = std::pair<double, int64_t>;  // (path, unit), largest path first, then lower unit
+        auto ready_cmp = [](const Ready& a, const Ready& b) {
+          return a.first < b.first || (a.first == b.first && a.second > b.second);
+        };
+        std::priority_queue<Ready, std::vector<Ready>, decltype(ready_cmp)> ready(ready_cmp);
+        std::vector<int64_t> next_task(nu);  // next of the unit's tasks to start
+        for (int64_t u = 0; u < nu; ++u) {
+          next_task[u] = ustart[u];
+          if (pending[u] == 0) ready.push({path[u], u});
+        }
+        using Run = std::pair<double, int64_t>;  // (finish time, unit)
+        std::priority_queue<Run, std::vector<Run>, std::greater<Run>> running;
+        double now = 0.0;
+        int64_t busy = 0;
+        while (!ready.empty() || !running.empty()) {
+          while (busy < kSimWarps && !ready.empty()) {
+            const int64_t u = ready.top().second;
+            sorted.push_back(P->tasks[next_task[u]]);
+            running.push({now + task_us[u], u});
+            ++busy;
+            if (++next_task[u] == ustart[u + 1]) ready.pop();  // the unit's last task has started
+          }
+          if (running.empty()) break;
+          const Run r = running.top();
+          running.pop();
+          --busy;
+          now = r.first;
+          if (--left[r.second] == 0)
+            for (int32_t v : dependents[r.second])
+              if (--pending[v] == 0) ready.push({path[v], v});
+        }
+        if ((int64_t)sorted.size() != (int64_t)P->tasks.size())
+          return fail(QT_EINVAL, "internal: the simulated queue left tasks unscheduled");
+      }
       P->tasks.swap(sorted);
     }
   }

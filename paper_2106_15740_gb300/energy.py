@@ -14,7 +14,7 @@ from . import binding as qb
 
 DTYPES = {"c128": qb.QT_C128, "c64": qb.QT_C64, "c64x2": qb.QT_C64X2}
 MODES = {"per_bucket": qb.QT_MODE_PER_BUCKET, "persistent": qb.QT_MODE_PERSISTENT}
-QUEUE_ORDERS = {"round_robin": 0, "critical_path": 1}
+QUEUE_ORDERS = {"round_robin": 0, "critical_path": 1, "simulated": 2}
 
 
 def _stream_handle(device):
@@ -33,7 +33,7 @@ class EnergyPlan:
                  max_workspace=0, max_width=0, device="cuda:0", gradient=False, lane_items=0,
                  group_rows=0, edge_range=None, slice=False, chunk_tiles=0, order_trials=0, order_seed=0,
                  order_tau=1.0, checkpoint_bytes=0, chain_steps=False,
-                 queue_order="critical_path", chunk_tiles_by_rank=None, fuse_chains=3):
+                 queue_order="simulated", chunk_tiles_by_rank=None, fuse_chains=3):
         self.n_vertices, self.p, self.batch = int(n_vertices), int(p), int(batch)
         self.edges = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
         self.device = torch.device(device)

@@ -317,18 +317,20 @@ def test_tiny_graph_sweep_against_state_vector(n):
                         np.testing.assert_allclose(zz[:, k, 0], refs[k], atol=TOL[dtype], rtol=0)
 
 
-@pytest.mark.parametrize("dtype,batch", [("c64", 64), ("c128", 1)])
-def test_critical_path_queue_order_equals_round_robin_bitwise(dtype, batch):
-    """Taking the tasks with the longest remaining dependency path first
-    changes only when each step runs, not what it computes."""
+@pytest.mark.parametrize("dtype,batch", [("c64", 64), ("c128", 1), ("c64", 1)])
+def test_queue_orders_are_bitwise_identical(dtype, batch):
+    """Taking the tasks with the longest remaining dependency path first, or
+    in the order a list-scheduling simulation starts them, changes only when
+    each step runs, not what it computes."""
     n, edges, p, g, b = workload("n100_p3", batch=batch)
     out = {}
-    for order in ("round_robin", "critical_path"):
+    for order in ("round_robin", "critical_path", "simulated"):
         plan = _plan(n, edges, p, batch, dtype, "persistent", order_trials=4, queue_order=order)
         out[order] = _run(plan, g, b)
         plan.close()
-    assert np.array_equal(out["round_robin"][1], out["critical_path"][1])
-    assert np.array_equal(out["round_robin"][0], out["critical_path"][0])
+    for order in ("critical_path", "simulated"):
+        assert np.array_equal(out["round_robin"][1], out[order][1])
+        assert np.array_equal(out["round_robin"][0], out[order][0])
 
 
 def test_per_width_chunks_are_bitwise_identical():

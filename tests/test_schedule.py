@@ -113,7 +113,7 @@ def check_schedule(sch, tasks):
     return len(order), max(depth) + 1, pairs, cross
 
 
-@pytest.mark.parametrize("queue_order", [0, 1])
+@pytest.mark.parametrize("queue_order", [0, 1, 2])
 @pytest.mark.parametrize("group_rows", [0, -1, 1 << 20])
 def test_tree_schedule_is_race_free(qtlib, group_rows, queue_order):
     n = 16
@@ -129,7 +129,7 @@ def test_tree_schedule_is_race_free(qtlib, group_rows, queue_order):
         assert pairs > 0 and depth < units
 
 
-@pytest.mark.parametrize("queue_order", [0, 1])
+@pytest.mark.parametrize("queue_order", [0, 1, 2])
 def test_tree_schedule_with_shared_slots_is_race_free(qtlib, queue_order):
     """A workspace cap puts several networks on one slot: a network's first
     steps then reuse the arena of the network before it."""
@@ -148,7 +148,7 @@ def test_tree_schedule_with_shared_slots_is_race_free(qtlib, queue_order):
     assert pairs > 0 and depth < units
 
 
-@pytest.mark.parametrize("queue_order", [0, 1])
+@pytest.mark.parametrize("queue_order", [0, 1, 2])
 def test_chain_schedule_is_one_path_per_slot(qtlib, queue_order):
     from paper_2106_15740_gb300 import binding as qb
     n = 12
@@ -178,7 +178,7 @@ def test_tree_schedule_of_searched_orders_is_race_free(qtlib):
     assert pairs > 0 and depth < units
 
 
-@pytest.mark.parametrize("queue_order", [0, 1])
+@pytest.mark.parametrize("queue_order", [0, 1, 2])
 @pytest.mark.parametrize("checkpoint", [False, True])
 def test_gradient_schedule_is_race_free(qtlib, checkpoint, queue_order):
     """The adjoint sweep reads the forward intermediates again, writes output
@@ -284,12 +284,12 @@ def test_per_width_chunks_schedule_is_race_free(qtlib):
     assert pairs > 0 and depth < units
 
 
-@pytest.mark.parametrize("field,value", [("chain_steps", 2), ("chain_steps", -1), ("queue_order", 2),
+@pytest.mark.parametrize("field,value", [("chain_steps", 2), ("chain_steps", -1), ("queue_order", 3),
                                          ("queue_order", -1)])
 def test_schedule_options_are_validated(qtlib, field, value):
     from paper_2106_15740_gb300 import binding as qb
     opt = qb.qt_plan_options_default()
-    assert opt.chain_steps == 0 and opt.queue_order == 1
+    assert opt.chain_steps == 0 and opt.queue_order == 2
     opt.batch = 2
     opt.mode = qb.QT_MODE_PERSISTENT
     setattr(opt, field, value)
@@ -377,7 +377,7 @@ def test_schedule_sweep_of_random_configurations(qtlib):
         opt.dtype = int(rng.choice([qb.QT_C64, qb.QT_C128]))
         opt.mode = qb.QT_MODE_PERSISTENT
         opt.gradient = int(rng.integers(0, 2))
-        opt.queue_order = int(rng.integers(0, 2))
+        opt.queue_order = int(rng.integers(0, 3))
         opt.chain_steps = int(rng.random() < 0.2)
         opt.group_rows = int(rng.choice([0, -1, 64]))
         if opt.gradient and rng.integers(0, 2):
