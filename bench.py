@@ -72,6 +72,9 @@ TRAFFIC_RATIO_CAPTURES = [
     # longest-path queue; edges 40-80 and 0-40 at B = 64 (profiles/persistent_kernel_n100p4_b64_dram.md)
     {"sources_sha256_16": "615f58709fc2a191", "queue_order": "critical_path", "batch": 64, "fuse_chains": 3,
      "dram_bytes_per_alg_byte": (4694877696 + 5017392896 + 5532984320 + 5726372864) / (8730376192 + 9919264768)},
+    # the same with the simulated list-scheduling queue order (the default)
+    {"sources_sha256_16": "615f58709fc2a191", "queue_order": "simulated", "batch": 64, "fuse_chains": 3,
+     "dram_bytes_per_alg_byte": (4737643264 + 5048140544 + 5629047040 + 5748539136) / (8730376192 + 9919264768)},
 ]
 
 
