@@ -774,12 +774,32 @@ static const void* pk_fn() {
   return (const void*)dev::persistent_kernel<Real, VB, PAIR, GRAD, ST>;
 }
 
+// Shapes with 2 to 16 rows per warp pass and one vector chunk per row
+// (complex64 with an even number of angle sets up to 32, complex128 and float
+// pairs up to 16): the multi-row lean tiles (STAGE 5).
+static bool multi_row(int dtype, int32_t B) {
+  if (B <= 1 || row_wide(dtype, B) || (dtype == QT_C64 && vector_width(dtype, B) != 2)) return false;
+  const TileGeom g = tile_geom(dtype, B, 0);
+  return g.RP > 1 && g.VC == 1;
+}
+
 // Kernel variant of a launch: the lean pair tile (one angle set), the lean
-// row tile (row-wide shapes), else the generic register tile.
+// row tile (row-wide shapes), the multi-row lean tiles, else the generic
+// register tile.
 template <bool GRAD>
 static const void* persistent_fn_g(int dtype, int32_t B) {
   const bool pair = (B == 1);
   const bool lean = pair || row_wide(dtype, B);
+  if (multi_row(dtype, B)) {
+    if (dtype == QT_C64) return pk_fn<float, 2, false, GRAD, 5>();
+    if (dtype == QT_C64X2) {
+      if constexpr (GRAD) return nullptr;  // float pairs: energies and amplitudes only
+      else return pk_fn<dev::ff, 1, false, false, 5>();
+    }
+    // complex128 gradients keep the generic tile: the multi-row adjoint tiles spill there
+    // (60-vertex p = 4, 4 angle sets: 145.8 -> 160.5 ms)
+    if constexpr (!GRAD) return pk_fn<double, 1, false, false, 5>();
+  }
   if (dtype == QT_C64) {
     if (pair) return pk_fn<float, 1, true, GRAD, 2>();
     if (vector_width(dtype, B) == 2) return lean ? pk_fn<float, 2, false, GRAD, 2>() : pk_fn<float, 2, false, GRAD, 0>();
