@@ -77,3 +77,57 @@ def test_low_lane_reduction_covers_every_row_and_target(seed):
         assert len(seen) == 1 << r
         assert len(got) == 1 << bin(tmask).count("1")
         assert set(got.values()) == {1 << bin(comp).count("1")}
+
+
+@pytest.mark.parametrize("Bv", [1, 2, 3, 6, 8, 12, 16])
+def test_multi_row_reduction_covers_every_completion(Bv):
+    """The reduction adjoint on the multi-row layout (2 to 32 rows per warp
+    pass, Bv vectors per row, lane l on row l // Bv and vector l % Bv): rows
+    q = kt * 2^comp_bits + c with the lanes on the low completion bits, passes
+    summed while the target row stays the same, then the RP lanes of each
+    vector in a shuffle tree (lanes rip < off take rip + off, off = RP/2 .. 1).
+    Every target element (and vector) gets each of its completions once, and
+    the tree stays within the RP * Bv <= 32 busy lanes."""
+    rng = random.Random(Bv)
+    RP = 1
+    while RP * 2 <= 32 // Bv:
+        RP *= 2
+    for P in (8, 32):
+        for _ in range(12):
+            r = rng.randint(5, 11)
+            full = (1 << r) - 1
+            while True:
+                tmask = rng.getrandbits(r) & full
+                if bin(full & ~tmask).count("1") >= 5:
+                    break
+            comp = full & ~tmask
+            cb = bin(comp).count("1")
+            seg = (1 << cb) // RP
+            n_rows, R = 1 << r, P * RP
+            got = {}
+            for r0 in range(0, n_rows, R):
+                r1 = min(r0 + R, n_rows)
+                acc = {}
+                for q in range(P):
+                    if r0 + q * RP >= r1:
+                        break
+                    qq = r0 + q * RP
+                    yp = pdep(qq >> cb, tmask) | pdep(qq & ((1 << cb) - 1), comp)
+                    for lane in range(32):
+                        rip, v0 = lane // Bv, lane % Bv
+                        if rip < RP and qq + rip < r1:
+                            acc.setdefault(v0, []).append(yp | pdep(rip, comp))
+                    if (q + 1) % seg == 0 or q + 1 == P or r0 + (q + 1) * RP >= r1:
+                        kt = (r0 + q * RP) >> cb
+                        for v0, ys in acc.items():
+                            assert all(pext(y, tmask) == kt for y in ys)
+                            got[(kt, v0)] = got.get((kt, v0), 0) + len(ys)
+                        acc = {}
+            assert len(got) == (1 << bin(tmask).count("1")) * Bv
+            assert set(got.values()) == {1 << cb}
+    for lane in range(RP * Bv):
+        off = RP // 2
+        while off >= 1:
+            if lane // Bv < off:
+                assert lane + off * Bv < RP * Bv <= 32
+            off //= 2
