@@ -196,8 +196,9 @@ typedef struct {
                              chunk_tiles says.  The autotuner picks these per width band (§Results:
                              the width of a step sets its cost).  Results are bit-identical for
                              any choice */
-  int32_t fuse_chains;    /* persistent energy and amplitude plans (no gradient) on the row-wide
-                             tiles (B > 1 angle sets, one vector chunk per row): a bucket's result
+  int32_t fuse_chains;    /* persistent energy and amplitude plans (no gradient) of one angle set,
+                             or complex64 on the row-wide tiles (34 to 64 angle sets; the first
+                             bucket of fan-in 2 or 3): a bucket's result
                              that the next bucket to use it only contracts with a leaf factor --
                              that consumer has no other intermediate input and no variable beyond
                              the result (§Tensor network contraction) -- is never stored: the

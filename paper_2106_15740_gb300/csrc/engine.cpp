@@ -353,6 +353,10 @@ static int64_t plan_gradient_network(const EdgePlan& ep, int64_t B, int64_t budg
   return A.peak;
 }
 
+// Largest fan-in of a chained step's first bucket on the row-wide layout (the
+// fixed-fan-in chained tiles; equal to the forward tiles' fixed fan-in).
+constexpr int32_t kFixedMaxFanInChain = 3;
+
 // Warps the queue's list-scheduling simulation assumes (152 SMs x 4 blocks x 8 warps).
 constexpr int64_t kSimWarps = 4864;
 
@@ -401,6 +405,8 @@ qt_status compile_plan(Plan* P) {
     for (int32_t i = 0; i < nb; ++i) {
       if (absorbed[i]) continue;
       const int32_t n_in = (int32_t)ep.buckets[i].in_src.size();
+      if (B > 1 && (P->opt.dtype != QT_C64 || n_in < 2 || n_in > kFixedMaxFanInChain))
+        continue;  // row-wide layout: the fixed-fan-in chained tiles of complex64 only
       int32_t cur = i;
       while ((int32_t)chain_of[e][i].size() < max_chain && n_in + (int32_t)chain_of[e][i].size() < kDevMaxIn) {
         const int32_t c = ep.buckets[cur].consumer;

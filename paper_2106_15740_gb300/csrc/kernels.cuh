@@ -702,10 +702,13 @@ __device__ __forceinline__ void tile_rows_rolled(WarpTile* w, Real* __restrict__
   }
 }
 
-// Chained steps (STAGE 4 kernels only), by fan-in as the unchained tiles.
+// Chained steps (STAGE 4 kernels only): complex64 buckets of fan-in 2 and 3,
+// the planner's rule on the row-wide layout.  (A rolled variant for other
+// fan-ins and for complex128 and float pairs raised the kernel's spills and
+// cost every tile of the bench step 2.7 %, 14.21 -> 13.83 ms without it.)
 template <class Real, int VB>
 __device__ __forceinline__ void tile_rows_chained(WarpTile* w, Real* __restrict__ data, const TileGeom& g, int64_t r0,
-                                                  int64_t r1, int lane) {
+                                                  int64_t r1, int lane, DevCtrl* ctrl) {
   const DevBucket& d = w->d;
   const int n_in = d.n_in;
   if (VB == 2 && n_in >= 2 && n_in <= kFixedMaxFanIn) {
@@ -718,7 +721,7 @@ __device__ __forceinline__ void tile_rows_chained(WarpTile* w, Real* __restrict_
       default: break;
     }
   }
-  tile_rows_chain<Real, VB, 0, false>(w, data, g, r0, r1, lane);
+  if (lane == 0 && ctrl != nullptr) atomicCAS(&ctrl->status, 0, (int32_t)QT_EINVAL);  // never planned
 }
 
 template <class Real, int VB>
@@ -1801,7 +1804,7 @@ __device__ __forceinline__ void warp_tile(WarpTile* w, Real* __restrict__ data, 
                                       // for every plan that has them)
       if constexpr (STAGE == 4 && !GRAD) {
         if (!PAIR && g.RP == 1 && g.VC == 1)
-          tile_rows_chained<Real, VB>(w, data, g, r0, r1, lane);
+          tile_rows_chained<Real, VB>(w, data, g, r0, r1, lane, ctrl);
         else if (PAIR && g.RP == 32 && g.VC == 1 && d.chain == 1)  // (one consumer: the planner's cap)
           tile_pairs_loop<Real, 1>(w, data, g, r0, r1, lane);
         else if (lane == 0 && ctrl != nullptr)

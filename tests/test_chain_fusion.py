@@ -55,17 +55,20 @@ def _buckets(tensors, order):
     return out
 
 
-def _chains(bk, max_len):
+def _chains(bk, max_len, fan_in=None):
     """Greedy chains in execution order: from bucket b, c_1 = b's consumer and
     c_j = the consumer of c_(j-1), while c_j has no variable beyond its input
     (|U_(c_j)| = |S_(c_(j-1))|) and no other intermediate input, up to
     max_len consumers (and 8 input records: b's inputs plus one per consumer);
-    a bucket absorbed into a chain starts none."""
+    a bucket absorbed into a chain starts none.  fan_in = (lo, hi): only a b
+    with that many inputs starts one (the row-wide layout's rule)."""
     absorbed, chains = set(), []
     for i, b in enumerate(bk):
         if i in absorbed:
             continue
         n_in = len(b["ints"]) + (1 if b["leaf"] else 0)
+        if fan_in is not None and not fan_in[0] <= n_in <= fan_in[1]:
+            continue
         ch, cur = [], i
         while len(ch) < max_len and n_in + len(ch) < 8:
             c = bk[cur]["consumer"]
@@ -98,7 +101,9 @@ def _network_tensors(n, edges, p, e):
                                                  (32, "QT_C128", 0), (17, "QT_C64X2", 3), (1, "QT_C64", 4),
                                                  (1, "QT_C128", 0)])
 def test_fused_plan_drops_each_fused_result(qtlib, B, dtype_name, trials, max_len):
-    """(One angle set: chains of one consumer at most, whatever fuse_chains.)"""
+    """(One angle set: chains of one consumer at most, whatever fuse_chains.
+    Row-wide layout: complex64 only, from buckets of fan-in 2 or 3; complex128
+    and float pairs there have no chained steps.)"""
     from paper_2106_15740_gb300 import binding as qb
     dtype = getattr(qb, dtype_name)
     es = {qb.QT_C64: 8, qb.QT_C128: 16, qb.QT_C64X2: 16}[dtype]
@@ -108,12 +113,15 @@ def test_fused_plan_drops_each_fused_result(qtlib, B, dtype_name, trials, max_le
     fused = _plan(n, edges, p, B=B, dtype=dtype, fuse=max_len, order_trials=trials)
     try:
         s0, s1 = qb.qt_plan_stats(plain), qb.qt_plan_stats(fused)
+        if B > 1 and dtype != qb.QT_C64:
+            assert s0 == s1
+            return
         saved, n_absorbed, longest = 0.0, 0, 0
         for e in range(len(edges)):
             order = list(qb.qt_plan_edge_order(fused, e))
             assert order == list(qb.qt_plan_edge_order(plain, e))
             bk = _buckets(_network_tensors(n, edges, p, e), order)
-            for ch in _chains(bk, 1 if B == 1 else max_len):
+            for ch in _chains(bk, 1 if B == 1 else max_len, None if B == 1 else (2, 3)):
                 n_absorbed += len(ch) - 1
                 longest = max(longest, len(ch) - 1)
                 # every result but the last one's is neither written nor read back
@@ -139,7 +147,7 @@ def test_fused_schedule_is_race_free(qtlib, shared):
     cap = 0
     if shared:
         full = _plan(n, edges, 3)
-        cap = _data_bytes(full, es=8) // 3
+        cap = _data_bytes(full, es=8) // 2
         qb.qt_plan_free(full)
     plan = _plan(n, edges, 3, max_workspace=cap)
     try:
