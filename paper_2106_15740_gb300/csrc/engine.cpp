@@ -357,8 +357,12 @@ static int64_t plan_gradient_network(const EdgePlan& ep, int64_t B, int64_t budg
 // fixed-fan-in chained tiles; equal to the forward tiles' fixed fan-in).
 constexpr int32_t kFixedMaxFanInChain = 3;
 
-// Warps the queue's list-scheduling simulation assumes (152 SMs x 4 blocks x 8 warps).
-constexpr int64_t kSimWarps = 4864;
+// Warps the queue's list-scheduling simulation assumes: twice the resident
+// warps (152 SMs x 4 blocks x 8), the best of a sweep on the bench step, the
+// 60-vertex p = 4 gradient and its energy (3648 / 4864 / 6400 / 9728 / 14592 /
+// 19456 / 38912 warps: bench 13.75 / 13.66 / 13.54 / 13.31 / 13.25 / 13.25 /
+// 13.52 ms, gradient 7.89 / 7.81 / 7.70 / 7.67 / 7.77 / 7.92 / 8.27 ms).
+constexpr int64_t kSimWarps = 9728;
 
 qt_status compile_plan(Plan* P) {
   const int32_t B = P->opt.batch;
