@@ -75,9 +75,10 @@ TRAFFIC_RATIO_CAPTURES = [
     # the same with the simulated list-scheduling queue order (the default)
     {"sources_sha256_16": "615f58709fc2a191", "queue_order": "simulated", "batch": 64, "fuse_chains": 3,
      "dram_bytes_per_alg_byte": (4737643264 + 5048140544 + 5629047040 + 5748539136) / (8730376192 + 9919264768)},
-    # chains only from fan-in 2-3 buckets on the row-wide layout, multi-row tiles (per stored byte)
+    # chains only from fan-in 2-3 buckets on the row-wide layout, multi-row tiles (per stored byte);
+    # the simulated order with 9728 resident warps
     {"sources_sha256_16": "d95d15ebce694c8c", "queue_order": "simulated", "batch": 64, "fuse_chains": 3,
-     "dram_bytes_per_alg_byte": (5046766080 + 5198431232 + 5876619776 + 5927608064) / (9256767488 + 10513176576)},
+     "dram_bytes_per_alg_byte": (5102270464 + 5209602304 + 5970159360 + 5941778688) / (9256767488 + 10513176576)},
 ]
 
 
