@@ -79,6 +79,9 @@ TRAFFIC_RATIO_CAPTURES = [
     # the simulated order with 9728 resident warps
     {"sources_sha256_16": "d95d15ebce694c8c", "queue_order": "simulated", "batch": 64, "fuse_chains": 3,
      "dram_bytes_per_alg_byte": (5102270464 + 5209602304 + 5970159360 + 5941778688) / (9256767488 + 10513176576)},
+    # the same complex64 kernels after float-pair gradients (FP64 adjoints) were added to the sources
+    {"sources_sha256_16": "5adb50b0ff9645eb", "queue_order": "simulated", "batch": 64, "fuse_chains": 3,
+     "dram_bytes_per_alg_byte": (5105731840 + 5212003328 + 5965799424 + 5942155264) / (9256767488 + 10513176576)},
 ]
 
 
@@ -301,6 +304,26 @@ def _roofline(alg_bytes, kernel_ms, peak, peak_kind, kernel, stored_bytes=None):
     return out
 
 
+# This GPU's FP64 rate (nominal, dense, the same on the FP64 units and the
+# tensor pipe): 1.25 TFLOP/s, about 2 FP64 fused multiply-adds per SM per clock
+# at 152 SMs and 2.07 GHz.
+FP64_TFLOPS_NOMINAL = 1.25
+
+
+def _roofline_fp64(flops, kernel_ms):
+    """ALU roofline of a complex128 launch: the plan's real FLOPs (per bucket
+    6 (k - 1) 2^|U| for the products of its k inputs at both values of the
+    eliminated variable, plus 2^|U| for the sum over it, times the angle sets)
+    over the kernel time, against the nominal FP64 rate.  One complex product
+    is 6 FLOPs in 4 FP64 instructions (2 multiplies, 2 fused multiply-adds), so
+    a kernel that keeps the FP64 units busy with nothing else reaches about
+    0.72 of the nominal rate by this count."""
+    achieved = flops / (kernel_ms * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": FP64_TFLOPS_NOMINAL, "unit": "TFLOP/s",
+            "frac": achieved / FP64_TFLOPS_NOMINAL, "peak_kind": "nominal FP64 rate (dense)",
+            "flops_per_launch": flops, "kernel_ms": kernel_ms}
+
+
 def min_fill_comparison(n, edges, p, B, g, b, dev, torch):
     """The same step with the plain greedy min-fill order (more bytes)."""
     from paper_2106_15740_gb300.energy import EnergyPlan
@@ -365,7 +388,7 @@ def unfused_comparison(n, edges, p, B, g, b, dev, torch):
 
 def gradient_and_comparator(dev, torch):
     """Energy-gradient throughput on the 60-vertex p = 4 workload (8 angles,
-    one angle set, adjoint sweep) in complex64 and complex128, and the plain
+    one angle set, adjoint sweep) in complex64, complex128 and float pairs, and the plain
     per-edge complex128 contraction (one kernel launch per bucket, edge after
     edge, one angle set at a time) on the gradient workload and on the bench
     workload (all 64 angle sets of one bench step, measured)."""
@@ -384,7 +407,7 @@ def gradient_and_comparator(dev, torch):
                                       order_trials=trials, **best)
     tuned = dict(best, chunk_tiles_by_rank=by_rank)
     res = {}
-    for dt in ("c64", "c128"):
+    for dt in ("c64", "c128", "c64x2"):
         plan = EnergyPlan(n, edges, p, batch=1, dtype=dt, mode="persistent", gradient=True, device=dev,
                           order_trials=trials, **tuned)
         ms, kms = _time_calls(plan, gd, bd, True, 5, torch, kernel=True)
@@ -402,7 +425,7 @@ def gradient_and_comparator(dev, torch):
                       order_trials=WORKLOAD.get("order_trials", 0))
     ms_grad16 = _time_calls(plan, torch.tensor(gb, device=dev), torch.tensor(bb, device=dev), True, 3, torch)
     plan.close()
-    c64, c128 = res["c64"], res["c128"]
+    c64, c128, c64x2 = res["c64"], res["c128"], res["c64x2"]
     out["grad"] = {"metric": "energy-grad evals/sec", "value": 1e3 / c64["ms"], "unit": "grad_evals/s",
                    "batched_16": {"value": 16e3 / ms_grad16, "ms_per_call": ms_grad16,
                                   "what": "16 angle sets per call (a multi-start optimiser's batch)"},
@@ -419,6 +442,11 @@ def gradient_and_comparator(dev, torch):
                    "c128": {"value": 1e3 / c128["ms"], "ms_per_eval": c128["ms"], "alg_bytes_per_eval": c128["alg"],
                             "roofline": _roofline(c128["alg"], c128["kms"], peak, peak_kind,
                                                   "persistent_kernel<double,1,true,true,2>")},
+                   "c64x2": {"value": 1e3 / c64x2["ms"], "ms_per_eval": c64x2["ms"],
+                             "alg_bytes_per_eval": c64x2["alg"],
+                             "roofline": _roofline(c64x2["alg"], c64x2["kms"], peak, peak_kind,
+                                                   "persistent_kernel<ff,1,true,true,2> (float pairs)"),
+                             "max_abs_dgrad_vs_c128": float(abs(c64x2["grad"] - c128["grad"]).max())},
                    "max_abs_dgrad_c64_vs_c128": float(abs(c64["grad"] - c128["grad"]).max()),
                    "max_abs_grad": float(abs(c128["grad"]).max()),
                    "min_fill_order_ms_per_eval": ms_grad_mf,
@@ -466,14 +494,15 @@ def complex128_counterparts(dev, torch):
             e, zz = plan.energy(gd, bd, edge_zz=True)
             plan.check()
             r[dt] = dict(ms=ms, kms=kms, alg=plan.bucket_bytes(), stored=plan.stats["alg_bytes"],
-                         e=e.cpu().numpy(), zz=zz.cpu().numpy())
+                         flops=plan.stats["flops"], e=e.cpu().numpy(), zz=zz.cpu().numpy())
             plan.close()
         key = "n100_p4_b64" if B == 64 else "n100_p3_b1"
         out[key] = {
             "c128": {"value": len(edges) * B / (r["c128"]["ms"] * 1e-3), "unit": "edge_evals/s",
                      "ms_per_call": r["c128"]["ms"],
                      "roofline": _roofline(r["c128"]["alg"], r["c128"]["kms"], peak, peak_kind, "persistent_kernel<double,...>",
-                                           r["c128"]["stored"])},
+                                           r["c128"]["stored"]),
+                     "roofline_fp64": _roofline_fp64(r["c128"]["flops"], r["c128"]["kms"])},
             "c64": {"value": len(edges) * B / (r["c64"]["ms"] * 1e-3), "unit": "edge_evals/s",
                     "ms_per_call": r["c64"]["ms"],
                     "roofline": _roofline(r["c64"]["alg"], r["c64"]["kms"], peak, peak_kind, "persistent_kernel<float,...>",

@@ -650,6 +650,8 @@ qt_status compile_plan(Plan* P) {
         if (bk.leaf_rank > 0) leaf_record(i);
       }
     }
+    // float-pair plans keep every adjoint tensor in FP64 (native atomic adds; see kInF64)
+    const int32_t adj_f64 = P->opt.dtype == QT_C64X2 ? kInF64 : 0;
     for (const GradOp& op : gops[e]) {
       const Bucket& bk = ep.buckets[op.bucket];
       for (size_t k = 0; k < op.loc.size(); ++k)  // every intermediate operand is resident
@@ -675,7 +677,7 @@ qt_status compile_plan(Plan* P) {
             if (n + 1 >= kDevMaxIn) return fail(QT_EINVAL, "too many network components for the gradient");
             d.in[n++] = input_record(0u, scal_base + out_off[e][sb], kInNoPair);
           }
-        d.in[n] = input_record(0u, d.out_off, 0);
+        d.in[n] = input_record(0u, d.out_off, adj_f64);
         d.n_in = n;
         P->buckets.push_back(d);
         for (int32_t sb : ep.scalars)
@@ -704,14 +706,14 @@ qt_status compile_plan(Plan* P) {
       const uint32_t all = bk.out_rank ? (1u << bk.out_rank) - 1u : 0u;
       int32_t n = 0;
       if (op.gbar >= 0) {  // rank > 0, or a scalar of a multi-component network
-        d.in[n++] = input_record(all, rbase + op.gbar, kInNoPair);
+        d.in[n++] = input_record(all, rbase + op.gbar, kInNoPair | adj_f64);
       } else {
         d.aflags |= kAdjUnitG;
       }
       for (int32_t j = 0; j < (int32_t)bk.in_src.size(); ++j)
         if (j != op.input) d.in[n++] = in_record(op.bucket, j, op.loc[j]);
       const uint32_t tmask = bk.in_mask[op.input];
-      d.in[n] = input_record(tmask, d.out_off, 0);  // target record
+      d.in[n] = input_record(tmask, d.out_off, adj_f64);  // target record
       d.n_in = n;
       if (!op.full && __builtin_popcount(all & ~tmask) >= 5 && geom_bv <= 32 && n + 2 <= kDevMaxIn) {
         // reduction form (32 or more completions per target element): one warp

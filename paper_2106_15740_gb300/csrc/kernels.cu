@@ -559,7 +559,11 @@ __global__ void leafgrad_kernel(const DevLeafFactor* __restrict__ lf, int32_t n_
   for (int32_t l = 0; l < kDevMaxLeaves; ++l) acc[l] = make_double2(0.0, 0.0);
   for (uint32_t z = (uint32_t)lane; z < (1u << F.rank); z += 32u) {
     const int64_t o = F.off + lbar_shift + (int64_t)z * B + b;
-    double2 run = make_double2((double)data[2 * o], (double)data[2 * o + 1]);  // Lbar_F[z]
+    double2 run;  // Lbar_F[z] (float-pair plans keep adjoints in FP64)
+    if constexpr (std::is_same<Real, ff>::value)
+      run = reinterpret_cast<const double2*>(data)[o];
+    else
+      run = make_double2((double)data[2 * o], (double)data[2 * o + 1]);
     for (int32_t l = 0; l < n; ++l) {  // prefix: Lbar times the leaves before l
       const uint32_t w = F.leaf[l];
       const int32_t layer = leaf_layer(w);
@@ -793,7 +797,7 @@ static const void* persistent_fn_g(int dtype, int32_t B) {
   if (multi_row(dtype, B)) {
     if (dtype == QT_C64) return pk_fn<float, 2, false, GRAD, 5>();
     if (dtype == QT_C64X2) {
-      if constexpr (GRAD) return nullptr;  // float pairs: energies and amplitudes only
+      if constexpr (GRAD) return nullptr;  // float-pair gradients: one angle set only
       else return pk_fn<dev::ff, 1, false, false, 5>();
     }
     // complex128 gradients keep the generic tile: the multi-row adjoint tiles spill there
@@ -805,9 +809,9 @@ static const void* persistent_fn_g(int dtype, int32_t B) {
     if (vector_width(dtype, B) == 2) return lean ? pk_fn<float, 2, false, GRAD, 2>() : pk_fn<float, 2, false, GRAD, 0>();
     return pk_fn<float, 1, false, GRAD, 0>();
   }
-  if (dtype == QT_C64X2) {  // float pairs: energies and amplitudes only
+  if (dtype == QT_C64X2) {  // float pairs: gradients for one angle set only
     if constexpr (GRAD) {
-      return nullptr;
+      return pair ? pk_fn<dev::ff, 1, true, true, 2>() : nullptr;
     } else {
       if (pair) return pk_fn<dev::ff, 1, true, false, 2>();
       if (!lean) return pk_fn<dev::ff, 1, false, false, 0>();
@@ -878,6 +882,9 @@ cudaError_t launch_gradient(int dtype, const DevLeafFactor* lf, int32_t n_lf, co
     if (dtype == QT_C64)
       dev::leafgrad_kernel<float><<<(int)((n1 * 32 + 127) / 128), 128, 0, s>>>(
           lf, n_lf, lbar_shift, trig, counts, p, B, (const float*)data, (double2*)part);
+    else if (dtype == QT_C64X2)
+      dev::leafgrad_kernel<dev::ff><<<(int)((n1 * 32 + 127) / 128), 128, 0, s>>>(
+          lf, n_lf, lbar_shift, trig, counts, p, B, (const dev::ff*)data, (double2*)part);
     else
       dev::leafgrad_kernel<double><<<(int)((n1 * 32 + 127) / 128), 128, 0, s>>>(
           lf, n_lf, lbar_shift, trig, counts, p, B, (const double*)data, (double2*)part);

@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "qt_device.h"
 #include "qtensor.h"
@@ -305,6 +306,25 @@ __device__ __forceinline__ Pack<Real, 2> ldpair_in(const Real* data, int64_t e, 
 template <class Real, int VB, bool CG>
 __device__ __forceinline__ Pack<Real, VB> ldv_in(const Real* data, int64_t e, bool leaf) {
   return leaf ? ldv<Real, VB, false>(data, e) : ldv<Real, VB, CG>(data, e);
+}
+
+// One row of a factor flagged kInNoPair (one value for x = 0 and x = 1) on
+// the one-angle-set layout.  Float-pair plans keep every adjoint tensor in
+// FP64 (flag kInF64: FP64 has native atomic adds, a float pair only a
+// compare-and-swap loop, and FP64 carries at least a float pair's precision);
+// such a factor is read as FP64 and split into a float pair here.
+template <class Real>
+__device__ __forceinline__ Pack<Real, 1> ld_nopair(const Real* data, int64_t e, int32_t fl) {
+  if constexpr (std::is_same<Real, ff>::value) {
+    if (fl & kInF64) {
+      const double2 v = __ldcg(reinterpret_cast<const double2*>(data) + e);
+      Pack<ff, 1> r;
+      r.c[0].x = ff(v.x);
+      r.c[0].y = ff(v.y);
+      return r;
+    }
+  }
+  return ldv_in<Real, 1, true>(data, e, fl & kInLeaf);
 }
 
 // Lane -> (row within a pass, vector) of the tile geometry.
@@ -828,6 +848,23 @@ __device__ __forceinline__ ff2 shfl_xor_cx(ff2 v, int m) {
   v.y.lo = __shfl_xor_sync(0xffffffffu, v.y.lo, m);
   return v;
 }
+__device__ __forceinline__ float2 shfl_down_cx(float2 v, int d) {
+  v.x = __shfl_down_sync(0xffffffffu, v.x, d);
+  v.y = __shfl_down_sync(0xffffffffu, v.y, d);
+  return v;
+}
+__device__ __forceinline__ double2 shfl_down_cx(double2 v, int d) {
+  v.x = __shfl_down_sync(0xffffffffu, v.x, d);
+  v.y = __shfl_down_sync(0xffffffffu, v.y, d);
+  return v;
+}
+__device__ __forceinline__ ff2 shfl_down_cx(ff2 v, int d) {
+  v.x.hi = __shfl_down_sync(0xffffffffu, v.x.hi, d);
+  v.x.lo = __shfl_down_sync(0xffffffffu, v.x.lo, d);
+  v.y.hi = __shfl_down_sync(0xffffffffu, v.y.hi, d);
+  v.y.lo = __shfl_down_sync(0xffffffffu, v.y.lo, d);
+  return v;
+}
 
 // Chained step on the one-angle-set layout: lane l holds b's row y = r0 +
 // pass * 32 + l, so chain level j pairs lanes l and l ^ 2^(j-1) (bit j - 1 of
@@ -939,6 +976,69 @@ __device__ __forceinline__ void atomic_add_cx(Real* data, int64_t e, typename Cx
   atomicAdd(data + 2 * e + 1, v.y);
 }
 
+// Float pairs have no hardware atomic add: a compare-and-swap loop on the
+// pair's 8 bytes (hi in the low word) adds with the float-pair sum.  The first
+// swap expects 0 (targets are cleared before their first add, so a first add
+// needs one atomic); every failed swap returns the current value and means
+// another lane's add went in, so the loop ends after at most as many retries
+// as there are adds to the element in flight.  The retry limit only guards
+// that argument: past it the element is set to NaN, so that an add left out
+// cannot pass unseen.
+constexpr int kFfCasLimit = 1 << 20;
+__device__ __forceinline__ void atomic_add_ff(ff* a, ff v) {
+  unsigned long long* p = reinterpret_cast<unsigned long long*>(a);
+  unsigned long long old = 0ull;
+  for (int it = 0; it < kFfCasLimit; ++it) {
+    ff cur;
+    cur.hi = __uint_as_float((unsigned)old);
+    cur.lo = __uint_as_float((unsigned)(old >> 32));
+    const ff nv = cur + v;
+    const unsigned long long nb =
+        (unsigned long long)__float_as_uint(nv.hi) | ((unsigned long long)__float_as_uint(nv.lo) << 32);
+    const unsigned long long seen = atomicCAS(p, old, nb);
+    if (seen == old) return;
+    old = seen;
+  }
+  atomicExch(p, 0x7fc000007fc00000ull);
+}
+template <>
+__device__ __forceinline__ void atomic_add_cx<ff>(ff* data, int64_t e, ff2 v) {
+  atomic_add_ff(data + 2 * e, v.x);
+  atomic_add_ff(data + 2 * e + 1, v.y);
+}
+
+// Adjoint targets of float-pair plans (target record flag kInF64): every
+// adjoint tensor is kept in FP64.  Many tiles add into the same target
+// elements (all of a leaf factor's few elements, or a reduction target's
+// completions), and a float pair can only be added by the compare-and-swap
+// loop above, which serialises under that contention, while FP64 has a
+// native atomic add and at least the float pair's precision.  The element
+// slots are 16 bytes either way.
+template <class Real>
+__device__ __forceinline__ bool f64_target(const DevBucket& d) {
+  if constexpr (std::is_same<Real, ff>::value) return (d.in[d.n_in].flags & kInF64) != 0;
+  else return false;
+}
+template <class Real>
+__device__ __forceinline__ void put_f64_pair(Real* data, int64_t e0, typename Cx<Real>::T c0,
+                                             typename Cx<Real>::T c1, bool full) {
+  if constexpr (std::is_same<Real, ff>::value) {
+    double* q = reinterpret_cast<double*>(data) + 2 * e0;
+    const double v0 = (double)c0.x, v1 = (double)c0.y, v2 = (double)c1.x, v3 = (double)c1.y;
+    if (full) {
+      q[0] = v0;
+      q[1] = v1;
+      q[2] = v2;
+      q[3] = v3;
+    } else {
+      atomicAdd(q, v0);
+      atomicAdd(q + 1, v1);
+      atomicAdd(q + 2, v2);
+      atomicAdd(q + 3, v3);
+    }
+  }
+}
+
 // Atomic add of two adjacent complex numbers (elements e0, e0 + 1).  In
 // complex64 at an even e0 (the pair's 16 bytes aligned: every tensor starts
 // 256-byte aligned and a pair row at an even element) this is one 16-byte
@@ -995,7 +1095,7 @@ __device__ __forceinline__ void tile_adjoint_pairs(WarpTile* w, Real* __restrict
       for (int u = 0; u < U; ++u) {
         const uint32_t k = ok[u] ? w->tab[i][pp + u] + lp : 0u;  // idle items read row 0
         if (fl & kInNoPair) {
-          a0[u] = ldv_in<Real, 1, true>(data, d.in[i].off + (int64_t)k, leaf);
+          a0[u] = ld_nopair<Real>(data, d.in[i].off + (int64_t)k, fl);
           a1[u] = a0[u];
         } else {
           const Pack<Real, 2> q = ldpair_in<Real, true>(data, d.in[i].off + 2 * (int64_t)k, leaf);
@@ -1013,7 +1113,9 @@ __device__ __forceinline__ void tile_adjoint_pairs(WarpTile* w, Real* __restrict
     for (int u = 0; u < U; ++u) {
       if (!ok[u]) continue;
       const int64_t e0 = d.out_off + 2 * (int64_t)(w->tab[n_in][pp + u] + lp_t);
-      if (full) {
+      if (f64_target<Real>(d)) {
+        put_f64_pair<Real>(data, e0, p0[u].c[0], p1[u].c[0], full);
+      } else if (full) {
         stv<Real, 1>(data, e0, p0[u]);
         stv<Real, 1>(data, e0 + 1, p1[u]);
       } else {
@@ -1169,6 +1271,9 @@ template <> struct RedBuf<float> {
 template <> struct RedBuf<double> {
   static __device__ __forceinline__ double* get(WarpTile* w) { return &w->x.red.d[0][0]; }
 };
+template <> struct RedBuf<ff> {  // (8-byte elements, the complex128 slots)
+  static __device__ __forceinline__ ff* get(WarpTile* w) { return reinterpret_cast<ff*>(&w->x.red.d[0][0]); }
+};
 
 // Reduction adjoint step (kStepAdjRed).  The tile's rows q = kt * 2^comp_bits
 // + c run over target rows kt and their completions c; since 2^comp_bits >=
@@ -1189,10 +1294,8 @@ __device__ __forceinline__ void flush_target(WarpTile* w, Real* __restrict__ dat
 #pragma unroll
     for (int v = 0; v < VB; ++v) {
       for (int off = 16; off >= g.Bv; off >>= 1) {
-        s0.c[v].x += __shfl_xor_sync(0xffffffffu, s0.c[v].x, off);
-        s0.c[v].y += __shfl_xor_sync(0xffffffffu, s0.c[v].y, off);
-        s1.c[v].x += __shfl_xor_sync(0xffffffffu, s1.c[v].x, off);
-        s1.c[v].y += __shfl_xor_sync(0xffffffffu, s1.c[v].y, off);
+        s0.c[v] = cadd<Real>(s0.c[v], shfl_xor_cx(s0.c[v], off));
+        s1.c[v] = cadd<Real>(s1.c[v], shfl_xor_cx(s1.c[v], off));
       }
     }
   } else {
@@ -1211,8 +1314,8 @@ __device__ __forceinline__ void flush_target(WarpTile* w, Real* __restrict__ dat
           t.x = 0;
           t.y = 0;
           for (int r = 0; r < g.RP; ++r) {
-            t.x += red[(r * g.Bv + v0) * per + 0];
-            t.y += red[(r * g.Bv + v0) * per + 1];
+            t.x = t.x + red[(r * g.Bv + v0) * per + 0];
+            t.y = t.y + red[(r * g.Bv + v0) * per + 1];
           }
           sv = t;
         }
@@ -1313,24 +1416,29 @@ __device__ __forceinline__ void adjred_pairs_flush(const WarpTile* w, Real* __re
 #pragma unroll
     for (int b = 0; b < 5; ++b) {
       if (!((cl >> b) & 1u)) continue;
-      s0.c[0].x += __shfl_xor_sync(0xffffffffu, s0.c[0].x, 1 << b);
-      s0.c[0].y += __shfl_xor_sync(0xffffffffu, s0.c[0].y, 1 << b);
-      s1.c[0].x += __shfl_xor_sync(0xffffffffu, s1.c[0].x, 1 << b);
-      s1.c[0].y += __shfl_xor_sync(0xffffffffu, s1.c[0].y, 1 << b);
+      s0.c[0] = cadd<Real>(s0.c[0], shfl_xor_cx(s0.c[0], 1 << b));
+      s1.c[0] = cadd<Real>(s1.c[0], shfl_xor_cx(s1.c[0], 1 << b));
     }
-    if (((uint32_t)lane & cl) == 0u)
-      atomic_add_pair<Real>(data, d.out_off + 2 * (int64_t)(w->tab[d.n_in][q] + w->lpart[d.n_in][lane]), s0.c[0],
-                            s1.c[0]);
+    if (((uint32_t)lane & cl) == 0u) {
+      const int64_t e0 = d.out_off + 2 * (int64_t)(w->tab[d.n_in][q] + w->lpart[d.n_in][lane]);
+      if (f64_target<Real>(d))
+        put_f64_pair<Real>(data, e0, s0.c[0], s1.c[0], false);
+      else
+        atomic_add_pair<Real>(data, e0, s0.c[0], s1.c[0]);
+    }
   } else {
     const uint32_t kt = (uint32_t)((r0 + (int64_t)q * 32) >> d.comp_bits);
 #pragma unroll
     for (int off = 16; off >= 1; off >>= 1) {
-      s0.c[0].x += __shfl_xor_sync(0xffffffffu, s0.c[0].x, off);
-      s0.c[0].y += __shfl_xor_sync(0xffffffffu, s0.c[0].y, off);
-      s1.c[0].x += __shfl_xor_sync(0xffffffffu, s1.c[0].x, off);
-      s1.c[0].y += __shfl_xor_sync(0xffffffffu, s1.c[0].y, off);
+      s0.c[0] = cadd<Real>(s0.c[0], shfl_xor_cx(s0.c[0], off));
+      s1.c[0] = cadd<Real>(s1.c[0], shfl_xor_cx(s1.c[0], off));
     }
-    if (lane == 0) atomic_add_pair<Real>(data, d.out_off + 2 * (int64_t)kt, s0.c[0], s1.c[0]);
+    if (lane == 0) {
+      if (f64_target<Real>(d))
+        put_f64_pair<Real>(data, d.out_off + 2 * (int64_t)kt, s0.c[0], s1.c[0], false);
+      else
+        atomic_add_pair<Real>(data, d.out_off + 2 * (int64_t)kt, s0.c[0], s1.c[0]);
+    }
   }
   s0.c[0].x = 0;
   s0.c[0].y = 0;
@@ -1379,7 +1487,7 @@ __device__ __forceinline__ void tile_adjred_pairs(WarpTile* w, Real* __restrict_
       for (int u = 0; u < U; ++u) {
         const uint32_t k = ok[u] ? w->tab[i][pp + u] + lp : 0u;  // idle items read row 0
         if (fl & kInNoPair) {
-          a0[u] = ldv_in<Real, 1, true>(data, d.in[i].off + (int64_t)k, leaf);
+          a0[u] = ld_nopair<Real>(data, d.in[i].off + (int64_t)k, fl);
           a1[u] = a0[u];
         } else {
           const Pack<Real, 2> q = ldpair_in<Real, true>(data, d.in[i].off + 2 * (int64_t)k, leaf);
@@ -1429,7 +1537,7 @@ __device__ __forceinline__ void load_factors_nf(const WarpTile* w, const Real* _
 #pragma unroll
   for (int u = 0; u < U; ++u) {
     const uint32_t k = ok[u] ? w->tab[0][pp + u] + lp[0] : 0u;  // idle items read row 0
-    g0[u] = ldv_in<Real, 1, true>(data, d.in[0].off + (int64_t)k, d.in[0].flags & kInLeaf);
+    g0[u] = ld_nopair<Real>(data, d.in[0].off + (int64_t)k, d.in[0].flags);
   }
 #pragma unroll
   for (int i = 1; i < NF; ++i) {
@@ -1485,7 +1593,9 @@ __device__ __forceinline__ void tile_adjoint_pairs_nf(WarpTile* w, Real* __restr
     for (int u = 0; u < U; ++u) {
       if (!ok[u]) continue;
       const int64_t e0 = d.out_off + 2 * (int64_t)(w->tab[NF][pp + u] + lp_t);
-      if (full) {
+      if (f64_target<Real>(d)) {
+        put_f64_pair<Real>(data, e0, p0[u].c[0], p1[u].c[0], full);
+      } else if (full) {
         stv<Real, 1>(data, e0, p0[u]);
         stv<Real, 1>(data, e0 + 1, p1[u]);
       } else {
@@ -1729,10 +1839,8 @@ __device__ __forceinline__ void tile_adjred_mrows(WarpTile* w, Real* __restrict_
         for (int off = g.RP / 2; off >= 1; off >>= 1)  // (warp-uniform; lanes rip < off take rip + off's sums)
 #pragma unroll
           for (int v = 0; v < VB; ++v) {
-            s0.c[v].x += __shfl_down_sync(0xffffffffu, s0.c[v].x, off * g.Bv);
-            s0.c[v].y += __shfl_down_sync(0xffffffffu, s0.c[v].y, off * g.Bv);
-            s1.c[v].x += __shfl_down_sync(0xffffffffu, s1.c[v].x, off * g.Bv);
-            s1.c[v].y += __shfl_down_sync(0xffffffffu, s1.c[v].y, off * g.Bv);
+            s0.c[v] = cadd<Real>(s0.c[v], shfl_down_cx(s0.c[v], off * g.Bv));
+            s1.c[v] = cadd<Real>(s1.c[v], shfl_down_cx(s1.c[v], off * g.Bv));
           }
         if (on && rip == 0) {
           const int64_t e0 = d.out_off + (int64_t)(2 * kt) * B + lo;
@@ -1839,6 +1947,11 @@ __device__ __forceinline__ void warp_tile(WarpTile* w, Real* __restrict__ data, 
     if (!done) tile_items<Real, VB, PAIR, CG, 2, 0>(w, data, g, r0, r1, lane, rip, v0, lane_on, ctrl, dbg_bucket);
   } else {
     if constexpr (GRAD) {
+      if (std::is_same<Real, ff>::value && !(STAGE == 2 && PAIR && g.RP == 32 && g.VC == 1)) {
+        // float-pair gradients run on the one-angle-set pair tiles only (they write the FP64 leaf-factor targets)
+        if (lane == 0 && ctrl != nullptr) atomicCAS(&ctrl->status, 0, (int32_t)QT_EINVAL);
+        return;
+      }
       if (d.kind == kStepAdj) {
         if (STAGE == 2 && PAIR && g.RP == 32 && g.VC == 1) {
           const bool nf = adj_nf_form(d);

@@ -29,6 +29,8 @@ struct DevInput {
 };
 constexpr int32_t kInLeaf = 1;    // written before the launch, read through L1
 constexpr int32_t kInNoPair = 2;  // one row per output row (no eliminated-variable bit): an adjoint
+constexpr int32_t kInF64 = 4;     // float-pair plans: an adjoint tensor (output adjoint or adjoint step
+                                  // target), stored, accumulated and read as FP64
 
 // Work split of a bucket into warp tiles (same for every bucket of a plan,
 // fixed by B).  A warp tile covers R = P * RP consecutive output rows,

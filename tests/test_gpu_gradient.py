@@ -10,7 +10,8 @@ a few thousand FP64 products and sums); against finite differences the FD
 truncation error O(h^2 |E'''|) ~ 1e-8 dominates.  complex64: 1e-5 per unit of
 gradient scale (FP32 rounding, about 100 bucket steps of 2^-24 each; the
 stored gates' norm is divided out per network).  Energies: 1e-9 (complex128)
-and 1e-5 (complex64) for the whole graph.
+and 1e-5 (complex64) for the whole graph.  Float pairs (one angle set) take
+the complex128 tolerances.
 """
 import numpy as np
 import pytest
@@ -59,6 +60,34 @@ def test_gradient_matches_parameter_shift(dtype, n, p, B, seed):
         tol = 1e-9 if dtype == "c128" else 1e-5 * scale
         np.testing.assert_allclose(grad[k], ref, atol=tol, rtol=0)
         assert abs(e[k] - sv.energy(n, edges, g[k], b[k])) <= (1e-9 if dtype == "c128" else 1e-5)
+
+
+@pytest.mark.parametrize("n,p,seed", [(14, 3, 6), (12, 2, 5), (16, 3, 8)])
+def test_float_pair_gradient_matches_parameter_shift(n, p, seed):
+    """Float pairs (one angle set): complex128-class, so the complex128
+    tolerances (1e-9 against the exact gradient and energy)."""
+    edges = random_regular_graph(n, 3, seed)
+    g, b = random_angles(1, p, 70 + seed)
+    e, grad = _run(_grad_plan(n, edges, p, 1, "c64x2"), g, b)
+    dg, db = gr.param_shift_gradient(n, edges, g[0], b[0])
+    np.testing.assert_allclose(grad[0], np.concatenate([dg, db]), atol=1e-9, rtol=0)
+    assert abs(e[0] - sv.energy(n, edges, g[0], b[0])) <= 1e-9
+
+
+@pytest.mark.parametrize("trials", [0, 100])
+def test_n60_p4_float_pair_gradient_equals_complex128(trials):
+    """Whole 60-vertex p = 4 graph (every adjoint tile shape of one angle set,
+    the reduction steps with lanes on completions and on the low variables,
+    atomic adds from many warps per target): float pairs against complex128
+    at 1e-10 per unit of gradient scale (both sum the same terms; float pairs
+    carry about 48 significant bits, and the complex128 gradient is pinned to
+    the oracle's finite differences above)."""
+    n, edges, p, g, b = workload("n60_p4")
+    e2, grad2 = _run(_grad_plan(n, edges, p, 1, "c64x2", order_trials=trials), g, b)
+    e1, grad1 = _run(_grad_plan(n, edges, p, 1, "c128", order_trials=trials), g, b)
+    scale = max(1.0, np.abs(grad1).max())
+    np.testing.assert_allclose(grad2, grad1, atol=1e-10 * scale, rtol=0)
+    np.testing.assert_allclose(e2, e1, atol=1e-10, rtol=0)
 
 
 def test_gradient_plan_energy_equals_forward_plan():

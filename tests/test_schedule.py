@@ -298,14 +298,16 @@ def test_schedule_options_are_validated(qtlib, field, value):
     assert ei.value.status == qb.QT_EINVAL
 
 
-def test_float_pairs_have_no_gradient_plans(qtlib):
+def test_float_pair_gradient_plans_take_one_angle_set(qtlib):
     from paper_2106_15740_gb300 import binding as qb
     opt = qb.qt_plan_options_default()
-    opt.mode, opt.dtype, opt.gradient = qb.QT_MODE_PERSISTENT, qb.QT_C64X2, 1
+    opt.mode, opt.dtype, opt.gradient, opt.batch = qb.QT_MODE_PERSISTENT, qb.QT_C64X2, 1, 2
     with pytest.raises(qb.QTError) as ei:
         qb.qt_plan_create(8, random_regular_graph(8, 3, 39), 1, opt)
     assert ei.value.status == qb.QT_EINVAL
-    opt.gradient = 0
+    opt.batch = 1
+    qb.qt_plan_free(qb.qt_plan_create(8, random_regular_graph(8, 3, 39), 1, opt))
+    opt.gradient, opt.batch = 0, 2
     qb.qt_plan_free(qb.qt_plan_create(8, random_regular_graph(8, 3, 39), 1, opt))
 
 
