@@ -846,7 +846,7 @@ cudaError_t launch_persistent(int dtype, bool grad, bool chains, const DevBucket
   g.data_elems = data_elems;
   g.wait_limit = 1 << 22;
   const void* fn = persistent_fn(dtype, grad, B, chains);
-  if (!fn) return cudaErrorInvalidValue;  // no such variant (float pairs have no adjoint sweep)
+  if (!fn) return cudaErrorInvalidValue;  // no such variant (float-pair gradients take one angle set)
   void* args[] = {(void*)&buckets, (void*)&tasks, (void*)&n_tasks, (void*)&ctrl, (void*)&done, (void*)&data,
                   (void*)&g, (void*)&spin_limit, (void*)&deps, (void*)&trace};
   return cudaLaunchKernel(fn, dim3(grid), dim3(256), args, 0, s);

@@ -23,3 +23,20 @@ def test_reference_arm_prints_one_json_line():
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
     assert "N=100 p=4" in d["config"]["workload"]
+
+
+def test_traffic_capture_key_ignores_comments_only():
+    """A DRAM traffic capture stays valid across a comment change and is
+    voided by any change to the kernel code."""
+    sys.path.insert(0, str(ROOT))
+    import bench
+    texts = [(ROOT / "paper_2106_15740_gb300" / "csrc" / f).read_text()
+             for f in ("kernels.cu", "kernels.cuh", "qt_device.h")]
+    base = bench.kernel_code_digest(texts)
+    assert base == bench.kernel_code_digest()
+    commented = [texts[0] + "\n// a remark\n/* another\n remark */\n", texts[1], texts[2]]
+    assert bench.kernel_code_digest(commented) == base
+    assert "constexpr int kFfCasLimit = 1 << 20;" in texts[1]
+    changed = [texts[0], texts[1].replace("constexpr int kFfCasLimit = 1 << 20;", "constexpr int kFfCasLimit = 1 << 21;"),
+               texts[2]]
+    assert bench.kernel_code_digest(changed) != base
