@@ -223,6 +223,24 @@ def test_checkpointed_gradient_matches_full_sweep_and_parameter_shift(dtype, bud
                                    rtol=0)
 
 
+@pytest.mark.parametrize("budget", [1 << 9, 1 << 12])
+def test_float_pair_checkpointed_gradient(budget):
+    """Float pairs (one angle set) with checkpoint segments: forward steps
+    re-run in the reverse sweep read float pairs, adjoints stay FP64; the
+    same gradient as the full sweep and the exact one at complex128
+    tolerances."""
+    n, p = 14, 3
+    edges = random_regular_graph(n, 3, 11)
+    g, b = random_angles(1, p, 91)
+    e0, g0 = _run(_grad_plan(n, edges, p, 1, "c64x2"), g, b)
+    plan = _grad_plan(n, edges, p, 1, "c64x2", checkpoint_bytes=budget)
+    e1, g1 = _run(plan, g, b)
+    np.testing.assert_allclose(e1, e0, atol=1e-12, rtol=0)
+    np.testing.assert_allclose(g1, g0, atol=1e-12 * max(1.0, np.abs(g0).max()), rtol=0)
+    ref = np.concatenate(gr.param_shift_gradient(n, edges, g[0], b[0]))
+    np.testing.assert_allclose(g1[0], ref, atol=1e-9, rtol=0)
+
+
 def test_checkpointed_gradient_on_n60_p4_edges():
     """A larger checkpointed plan (10 edges of the 60-vertex p = 4 graph,
     complex128) against the unsegmented sweep."""

@@ -104,3 +104,18 @@ def test_sliced_gradient_matches_parameter_shift(dtype, n, p, B, max_width, seed
         ref = np.concatenate(gr.param_shift_gradient(n, edges, g[k], b[k]))
         tol = 1e-9 if dtype == "c128" else 5e-5 * max(1.0, np.abs(ref).max())
         np.testing.assert_allclose(grad[k], ref, atol=tol, rtol=0)
+
+
+
+@pytest.mark.parametrize("n,p,max_width,seed", [(12, 2, 3, 5), (10, 3, 4, 7)])
+def test_sliced_float_pair_gradient_matches_parameter_shift(n, p, max_width, seed):
+    """Float-pair gradients (one angle set) on sliced networks: the slices'
+    leaf-factor adjoints are summed in FP64; complex128 tolerance."""
+    edges = random_regular_graph(n, 3, seed)
+    g, b = random_angles(1, p, 70 + seed)
+    plan = _plan(n, edges, p, 1, "c64x2", "persistent", max_width, gradient=True)
+    assert plan.slices.max() > 0
+    e, grad = plan.energy(_dev(g, plan), _dev(b, plan), grad=True)
+    plan.check()
+    ref = np.concatenate(gr.param_shift_gradient(n, edges, g[0], b[0]))
+    np.testing.assert_allclose(grad.cpu().numpy()[0], ref, atol=1e-9, rtol=0)
