@@ -983,7 +983,10 @@ __device__ __forceinline__ void atomic_add_cx(Real* data, int64_t e, typename Cx
 // another lane's add went in, so the loop ends after at most as many retries
 // as there are adds to the element in flight.  The retry limit only guards
 // that argument: past it the element is set to NaN, so that an add left out
-// cannot pass unseen.
+// cannot pass unseen.  Float-pair gradient plans keep their adjoint tensors
+// in FP64 (kInF64, below: under contention this loop serialises), so the
+// tiles they run never take this path; it completes the float-pair
+// instantiation of the generic tiles.
 constexpr int kFfCasLimit = 1 << 20;
 __device__ __forceinline__ void atomic_add_ff(ff* a, ff v) {
   unsigned long long* p = reinterpret_cast<unsigned long long*>(a);
