@@ -102,6 +102,9 @@ TRAFFIC_RATIO_CAPTURES = [
     # (digest of the code, comments ignored; as written: 5adb50b0ff9645eb)
     {"code_sha256_16": "9a5899f7577062f1", "queue_order": "simulated", "batch": 64, "fuse_chains": 3,
      "dram_bytes_per_alg_byte": (5105731840 + 5212003328 + 5965799424 + 5942155264) / (9256767488 + 10513176576)},
+    # the same complex64 kernels after float-pair gradients took the multi-row tiles (2 to 16 angle sets)
+    {"code_sha256_16": "f4d00e26317c1a4e", "queue_order": "simulated", "batch": 64, "fuse_chains": 3,
+     "dram_bytes_per_alg_byte": (5089897984 + 5210417408 + 5966610432 + 5941371648) / (9256767488 + 10513176576)},
 ]
 
 
@@ -446,10 +449,15 @@ def gradient_and_comparator(dev, torch):
                       order_trials=WORKLOAD.get("order_trials", 0))
     ms_grad16 = _time_calls(plan, torch.tensor(gb, device=dev), torch.tensor(bb, device=dev), True, 3, torch)
     plan.close()
+    plan = EnergyPlan(n, edges, p, batch=16, dtype="c64x2", mode="persistent", gradient=True, device=dev,
+                      order_trials=WORKLOAD.get("order_trials", 0))
+    ms_grad16_ff = _time_calls(plan, torch.tensor(gb, device=dev), torch.tensor(bb, device=dev), True, 3, torch)
+    plan.close()
     c64, c128, c64x2 = res["c64"], res["c128"], res["c64x2"]
     out["grad"] = {"metric": "energy-grad evals/sec", "value": 1e3 / c64["ms"], "unit": "grad_evals/s",
                    "batched_16": {"value": 16e3 / ms_grad16, "ms_per_call": ms_grad16,
-                                  "what": "16 angle sets per call (a multi-start optimiser's batch)"},
+                                  "what": "16 angle sets per call (a multi-start optimiser's batch)",
+                                  "c64x2": {"value": 16e3 / ms_grad16_ff, "ms_per_call": ms_grad16_ff}},
                    "ms_per_eval": c64["ms"], "dtype": "c64",
                    "workload": "random 3-regular N=60 p=4 (seed 3), 90 edge lightcones, dE/dgamma and dE/dbeta "
                                "(8 angles) by the adjoint bucket sweep, one angle set",

@@ -60,7 +60,7 @@ typedef enum {
   QT_C64X2 = 2      /* each real part and imaginary part an unevaluated sum of two floats
                        (hi + lo, about 48 significant bits, 16 bytes per complex number) with
                        error-free FP32 arithmetic: complex128-class results from the FP32 pipes.
-                       Gradient plans take it with one angle set (batch 1) only */
+                       Gradient plans take it with at most 16 angle sets */
 } qt_dtype;
 
 typedef enum {
@@ -140,7 +140,7 @@ typedef struct {
   int32_t dtype;          /* qt_dtype */
   int32_t mode;           /* qt_mode */
   int32_t gradient;       /* 1: plan also computes dE/dgamma, dE/dbeta (adjoint sweep; persistent
-                             mode; QT_C64X2 with batch 1 only) */
+                             mode; QT_C64X2 with batch <= 16) */
   int32_t max_width;      /* width budget; an edge above it fails with QT_EWIDTH unless sliced
                              (<=0: 31) */
   int32_t lane_items;     /* work items per lane in one warp tile: 8, 16, 32 or 64 (<=0: by batch) */

@@ -269,8 +269,8 @@ static qt_status check_options(const qt_plan_options* opt, qt_plan_options* out)
   if (opt) o = *opt;
   if (o.batch < 1) return fail(QT_EINVAL, "batch must be >= 1");
   if (o.dtype != QT_C128 && o.dtype != QT_C64 && o.dtype != QT_C64X2) return fail(QT_EINVAL, "unknown dtype");
-  if (o.dtype == QT_C64X2 && o.gradient && o.batch != 1)
-    return fail(QT_EINVAL, "float-pair (QT_C64X2) gradient plans take one angle set (batch 1)");
+  if (o.dtype == QT_C64X2 && o.gradient && o.batch > 16)
+    return fail(QT_EINVAL, "float-pair (QT_C64X2) gradient plans take at most 16 angle sets");
   if (o.mode != QT_MODE_PER_BUCKET && o.mode != QT_MODE_PERSISTENT) return fail(QT_EINVAL, "unknown mode");
   if (o.max_width <= 0 || o.max_width > 31) o.max_width = 31;
   if (o.lane_items > 0 && o.lane_items != 8 && o.lane_items != 16 && o.lane_items != 32 && o.lane_items != 64)

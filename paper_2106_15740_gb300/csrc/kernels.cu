@@ -796,10 +796,7 @@ static const void* persistent_fn_g(int dtype, int32_t B) {
   const bool lean = pair || row_wide(dtype, B);
   if (multi_row(dtype, B)) {
     if (dtype == QT_C64) return pk_fn<float, 2, false, GRAD, 5>();
-    if (dtype == QT_C64X2) {
-      if constexpr (GRAD) return nullptr;  // float-pair gradients: one angle set only
-      else return pk_fn<dev::ff, 1, false, false, 5>();
-    }
+    if (dtype == QT_C64X2) return pk_fn<dev::ff, 1, false, GRAD, 5>();
     // complex128 gradients keep the generic tile: the multi-row adjoint tiles spill there
     // (60-vertex p = 4, 4 angle sets: 145.8 -> 160.5 ms)
     if constexpr (!GRAD) return pk_fn<double, 1, false, false, 5>();
@@ -809,7 +806,7 @@ static const void* persistent_fn_g(int dtype, int32_t B) {
     if (vector_width(dtype, B) == 2) return lean ? pk_fn<float, 2, false, GRAD, 2>() : pk_fn<float, 2, false, GRAD, 0>();
     return pk_fn<float, 1, false, GRAD, 0>();
   }
-  if (dtype == QT_C64X2) {  // float pairs: gradients for one angle set only
+  if (dtype == QT_C64X2) {  // float pairs: gradients for 1 to 16 angle sets (the pair and multi-row tiles)
     if constexpr (GRAD) {
       return pair ? pk_fn<dev::ff, 1, true, true, 2>() : nullptr;
     } else {
@@ -846,7 +843,7 @@ cudaError_t launch_persistent(int dtype, bool grad, bool chains, const DevBucket
   g.data_elems = data_elems;
   g.wait_limit = 1 << 22;
   const void* fn = persistent_fn(dtype, grad, B, chains);
-  if (!fn) return cudaErrorInvalidValue;  // no such variant (float-pair gradients take one angle set)
+  if (!fn) return cudaErrorInvalidValue;  // no such variant (float-pair gradients take at most 16 angle sets)
   void* args[] = {(void*)&buckets, (void*)&tasks, (void*)&n_tasks, (void*)&ctrl, (void*)&done, (void*)&data,
                   (void*)&g, (void*)&spin_limit, (void*)&deps, (void*)&trace};
   return cudaLaunchKernel(fn, dim3(grid), dim3(256), args, 0, s);

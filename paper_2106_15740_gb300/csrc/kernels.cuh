@@ -1042,6 +1042,21 @@ __device__ __forceinline__ void put_f64_pair(Real* data, int64_t e0, typename Cx
   }
 }
 
+template <class Real>
+__device__ __forceinline__ void put_f64_cx(Real* data, int64_t e, typename Cx<Real>::T c, bool full) {
+  if constexpr (std::is_same<Real, ff>::value) {
+    double* q = reinterpret_cast<double*>(data) + 2 * e;
+    const double v0 = (double)c.x, v1 = (double)c.y;
+    if (full) {
+      q[0] = v0;
+      q[1] = v1;
+    } else {
+      atomicAdd(q, v0);
+      atomicAdd(q + 1, v1);
+    }
+  }
+}
+
 // Atomic add of two adjacent complex numbers (elements e0, e0 + 1).  In
 // complex64 at an even e0 (the pair's 16 bytes aligned: every tensor starts
 // 256-byte aligned and a pair row at an even element) this is one 16-byte
@@ -1737,7 +1752,10 @@ __device__ __forceinline__ void mrows_factors(const WarpTile* w, const Real* __r
       const uint32_t k = ok[u] ? w->tab[i][pp + u] + lp : 0u;
       const int64_t l = ok[u] ? lo : 0;
       if (fl & kInNoPair) {
-        a0[u] = ldv_in<Real, VB, true>(data, d.in[i].off + (int64_t)k * B + l, leaf);
+        if constexpr (VB == 1)
+          a0[u] = ld_nopair<Real>(data, d.in[i].off + (int64_t)k * B + l, fl);
+        else
+          a0[u] = ldv_in<Real, VB, true>(data, d.in[i].off + (int64_t)k * B + l, leaf);
         a1[u] = a0[u];
       } else {
         const int64_t e = d.in[i].off + (int64_t)(2 * k) * B + l;
@@ -1778,7 +1796,13 @@ __device__ __forceinline__ void tile_adjoint_mrows(WarpTile* w, Real* __restrict
       if (!ok[u]) continue;
       const uint32_t kt = w->tab[n_in][pp + u] + lp_t;
       const int64_t e0 = d.out_off + (int64_t)(2 * kt) * B + lo;
-      if (full) {
+      if (f64_target<Real>(d)) {
+#pragma unroll
+        for (int v = 0; v < VB; ++v) {
+          put_f64_cx<Real>(data, e0 + v, p0[u].c[v], full);
+          put_f64_cx<Real>(data, e0 + B + v, p1[u].c[v], full);
+        }
+      } else if (full) {
         stv<Real, VB>(data, e0, p0[u]);
         stv<Real, VB>(data, e0 + B, p1[u]);
       } else if (VB == 2) {  // a lane's two angle sets are adjacent elements
@@ -1847,7 +1871,13 @@ __device__ __forceinline__ void tile_adjred_mrows(WarpTile* w, Real* __restrict_
           }
         if (on && rip == 0) {
           const int64_t e0 = d.out_off + (int64_t)(2 * kt) * B + lo;
-          if (VB == 2) {
+          if (f64_target<Real>(d)) {
+#pragma unroll
+            for (int v = 0; v < VB; ++v) {
+              put_f64_cx<Real>(data, e0 + v, s0.c[v], false);
+              put_f64_cx<Real>(data, e0 + B + v, s1.c[v], false);
+            }
+          } else if (VB == 2) {
             atomic_add_pair<Real>(data, e0, s0.c[0], s0.c[VB - 1]);
             atomic_add_pair<Real>(data, e0 + B, s1.c[0], s1.c[VB - 1]);
           } else {
@@ -1950,8 +1980,11 @@ __device__ __forceinline__ void warp_tile(WarpTile* w, Real* __restrict__ data, 
     if (!done) tile_items<Real, VB, PAIR, CG, 2, 0>(w, data, g, r0, r1, lane, rip, v0, lane_on, ctrl, dbg_bucket);
   } else {
     if constexpr (GRAD) {
-      if (std::is_same<Real, ff>::value && !(STAGE == 2 && PAIR && g.RP == 32 && g.VC == 1)) {
-        // float-pair gradients run on the one-angle-set pair tiles only (they write the FP64 leaf-factor targets)
+      if (std::is_same<Real, ff>::value &&
+          !(STAGE == 2 ? PAIR && g.RP == 32 && g.VC == 1
+                       : STAGE == 5 && !PAIR && g.RP > 1 && g.VC == 1 &&
+                             (d.kind == kStepZero || !(d.aflags & kAdjRedLow)))) {
+        // float-pair gradients run on the pair and multi-row tiles only (those take the FP64 adjoint tensors)
         if (lane == 0 && ctrl != nullptr) atomicCAS(&ctrl->status, 0, (int32_t)QT_EINVAL);
         return;
       }

@@ -62,16 +62,19 @@ def test_gradient_matches_parameter_shift(dtype, n, p, B, seed):
         assert abs(e[k] - sv.energy(n, edges, g[k], b[k])) <= (1e-9 if dtype == "c128" else 1e-5)
 
 
-@pytest.mark.parametrize("n,p,seed", [(14, 3, 6), (12, 2, 5), (16, 3, 8)])
-def test_float_pair_gradient_matches_parameter_shift(n, p, seed):
-    """Float pairs (one angle set): complex128-class, so the complex128
-    tolerances (1e-9 against the exact gradient and energy)."""
+@pytest.mark.parametrize("n,p,B,seed", [(14, 3, 1, 6), (12, 2, 1, 5), (16, 3, 1, 8), (12, 2, 2, 5), (10, 3, 3, 7),
+                                        (12, 2, 5, 9)])
+def test_float_pair_gradient_matches_parameter_shift(n, p, B, seed):
+    """Float pairs (one angle set on the pair tiles, 2 to 16 on the
+    multi-row tiles): complex128-class, so the complex128 tolerances (1e-9
+    against the exact gradient and energy)."""
     edges = random_regular_graph(n, 3, seed)
-    g, b = random_angles(1, p, 70 + seed)
-    e, grad = _run(_grad_plan(n, edges, p, 1, "c64x2"), g, b)
-    dg, db = gr.param_shift_gradient(n, edges, g[0], b[0])
-    np.testing.assert_allclose(grad[0], np.concatenate([dg, db]), atol=1e-9, rtol=0)
-    assert abs(e[0] - sv.energy(n, edges, g[0], b[0])) <= 1e-9
+    g, b = random_angles(B, p, 70 + seed)
+    e, grad = _run(_grad_plan(n, edges, p, B, "c64x2"), g, b)
+    for k in range(B):
+        dg, db = gr.param_shift_gradient(n, edges, g[k], b[k])
+        np.testing.assert_allclose(grad[k], np.concatenate([dg, db]), atol=1e-9, rtol=0)
+        assert abs(e[k] - sv.energy(n, edges, g[k], b[k])) <= 1e-9
 
 
 @pytest.mark.parametrize("trials", [0, 100])
@@ -221,6 +224,22 @@ def test_checkpointed_gradient_matches_full_sweep_and_parameter_shift(dtype, bud
         ref = np.concatenate(gr.param_shift_gradient(n, edges, g[k], b[k]))
         np.testing.assert_allclose(g1[k], ref, atol=1e-9 if dtype == "c128" else 1e-5 * max(1.0, np.abs(ref).max()),
                                    rtol=0)
+
+
+@pytest.mark.parametrize("B", [4, 16])
+def test_n60_p4_batched_float_pair_gradient_equals_complex128(B):
+    """The multi-row float-pair gradient (4 and 16 angle sets: 8 and 2 rows
+    per warp pass) on the whole 60-vertex p = 4 graph against complex128 at
+    1e-10 per unit of gradient scale.  Searched orders (100 trials per edge):
+    at 16 angle sets a min-fill plan would need 658 GiB of workspace, the
+    searched one 81 GiB."""
+    n, edges, p, _, _ = workload("n60_p4")
+    g, b = random_angles(B, p, 1003)
+    e2, grad2 = _run(_grad_plan(n, edges, p, B, "c64x2", order_trials=100), g, b)
+    e1, grad1 = _run(_grad_plan(n, edges, p, B, "c128", order_trials=100), g, b)
+    scale = max(1.0, np.abs(grad1).max())
+    np.testing.assert_allclose(grad2, grad1, atol=1e-10 * scale, rtol=0)
+    np.testing.assert_allclose(e2, e1, atol=1e-10, rtol=0)
 
 
 @pytest.mark.parametrize("budget", [1 << 9, 1 << 12])

@@ -298,16 +298,17 @@ def test_schedule_options_are_validated(qtlib, field, value):
     assert ei.value.status == qb.QT_EINVAL
 
 
-def test_float_pair_gradient_plans_take_one_angle_set(qtlib):
+def test_float_pair_gradient_plans_take_at_most_16_angle_sets(qtlib):
     from paper_2106_15740_gb300 import binding as qb
     opt = qb.qt_plan_options_default()
-    opt.mode, opt.dtype, opt.gradient, opt.batch = qb.QT_MODE_PERSISTENT, qb.QT_C64X2, 1, 2
+    opt.mode, opt.dtype, opt.gradient, opt.batch = qb.QT_MODE_PERSISTENT, qb.QT_C64X2, 1, 17
     with pytest.raises(qb.QTError) as ei:
         qb.qt_plan_create(8, random_regular_graph(8, 3, 39), 1, opt)
     assert ei.value.status == qb.QT_EINVAL
-    opt.batch = 1
-    qb.qt_plan_free(qb.qt_plan_create(8, random_regular_graph(8, 3, 39), 1, opt))
-    opt.gradient, opt.batch = 0, 2
+    for B in (1, 2, 16):
+        opt.batch = B
+        qb.qt_plan_free(qb.qt_plan_create(8, random_regular_graph(8, 3, 39), 1, opt))
+    opt.gradient, opt.batch = 0, 17
     qb.qt_plan_free(qb.qt_plan_create(8, random_regular_graph(8, 3, 39), 1, opt))
 
 
