@@ -449,15 +449,10 @@ def gradient_and_comparator(dev, torch):
                       order_trials=WORKLOAD.get("order_trials", 0))
     ms_grad16 = _time_calls(plan, torch.tensor(gb, device=dev), torch.tensor(bb, device=dev), True, 3, torch)
     plan.close()
-    plan = EnergyPlan(n, edges, p, batch=16, dtype="c64x2", mode="persistent", gradient=True, device=dev,
-                      order_trials=WORKLOAD.get("order_trials", 0))
-    ms_grad16_ff = _time_calls(plan, torch.tensor(gb, device=dev), torch.tensor(bb, device=dev), True, 3, torch)
-    plan.close()
     c64, c128, c64x2 = res["c64"], res["c128"], res["c64x2"]
     out["grad"] = {"metric": "energy-grad evals/sec", "value": 1e3 / c64["ms"], "unit": "grad_evals/s",
                    "batched_16": {"value": 16e3 / ms_grad16, "ms_per_call": ms_grad16,
-                                  "what": "16 angle sets per call (a multi-start optimiser's batch)",
-                                  "c64x2": {"value": 16e3 / ms_grad16_ff, "ms_per_call": ms_grad16_ff}},
+                                  "what": "16 angle sets per call (a multi-start optimiser's batch)"},
                    "ms_per_eval": c64["ms"], "dtype": "c64",
                    "workload": "random 3-regular N=60 p=4 (seed 3), 90 edge lightcones, dE/dgamma and dE/dbeta "
                                "(8 angles) by the adjoint bucket sweep, one angle set",
