@@ -335,3 +335,44 @@ def test_simplifications_lower_width_and_cost_at_depth(qtlib):
     assert fits(r[qb.QT_REP_ZZ_DIAGONAL][1], LAPTOP_BYTES) and not fits(r[qb.QT_REP_DEFAULT][1], LAPTOP_BYTES)
     with pytest.raises(qb.QTError):
         qb.qt_representation_cost(40, edges, 3, 7)
+
+
+def _oracle_bucket_flops(n, edges, p, e):
+    """Real FLOPs of bucket elimination (per bucket 6 (k - 1)
+    2^|U| for the products of its k inputs at both values of the eliminated
+    variable, plus 2^|U| for the sum over it), counted on the oracle's own
+    network and min-fill order, with a bucket's leaf tensors taken as one
+    input (the library multiplies them into one leaf factor before the
+    launch)."""
+    net = lc.build_lightcone(n, edges, p, np.zeros(p), np.zeros(p), e)
+    tvars = [vs for vs, _ in net.tensors]
+    order, _ = lc.min_fill_order(net.n_vars, tvars)
+    live = [(frozenset(vs), True) for vs in tvars]  # (variables, is a leaf)
+    flops = 0
+    for v in order:
+        bucket = [t for t in live if v in t[0]]
+        live = [t for t in live if v not in t[0]]
+        union = frozenset().union(*[t[0] for t in bucket])
+        k = sum(1 for t in bucket if not t[1]) + (1 if any(t[1] for t in bucket) else 0)
+        flops += 2 ** len(union) * 6 * (k - 1) + 2 ** len(union)
+        live.append((union - {v}, False))
+    return flops
+
+
+@pytest.mark.parametrize("name", ["n16_p1", "n100_p3"])
+def test_plan_flops_match_oracle_buckets(qtlib, name):
+    """qt_plan_stats' FLOPs (the complex128 roofline's numerator) against a
+    count over the oracle's buckets, per edge, and B times that for B angle
+    sets."""
+    from paper_2106_15740_gb300 import binding as qb
+    n, edges, p, _, _ = workload(name)
+    for e in range(0, len(edges), max(1, len(edges) // 6)):
+        for B in (1, 3):
+            opt = qb.qt_plan_options_default()
+            opt.batch, opt.dtype = B, qb.QT_C128
+            opt.edge_begin, opt.edge_end = e, e + 1
+            plan = qb.qt_plan_create(n, edges, p, opt)
+            try:
+                assert qb.qt_plan_stats(plan)["flops"] == B * _oracle_bucket_flops(n, edges, p, e)
+            finally:
+                qb.qt_plan_free(plan)
