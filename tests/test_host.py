@@ -376,3 +376,53 @@ def test_plan_flops_match_oracle_buckets(qtlib, name):
                 assert qb.qt_plan_stats(plan)["flops"] == B * _oracle_bucket_flops(n, edges, p, e)
             finally:
                 qb.qt_plan_free(plan)
+
+
+def _oracle_bucket_elems(n, edges, p, e):
+    """Complex elements moved per angle set, counted on the oracle's buckets
+    (min-fill order): forward, every bucket's intermediate inputs read and
+    its result written; reverse sweep, one adjoint step per
+    input of every bucket (the leaf factor, a bucket's leaf tensors taken as
+    one, included), each reading the output adjoint and the other
+    intermediate inputs and writing its target."""
+    net = lc.build_lightcone(n, edges, p, np.zeros(p), np.zeros(p), e)
+    tvars = [vs for vs, _ in net.tensors]
+    order, _ = lc.min_fill_order(net.n_vars, tvars)
+    live = [(frozenset(vs), True) for vs in tvars]  # (variables, is a leaf)
+    fwd = rev = 0
+    for v in order:
+        bucket = [t for t in live if v in t[0]]
+        live = [t for t in live if v not in t[0]]
+        union = frozenset().union(*[t[0] for t in bucket])
+        out = len(union) - 1
+        inputs = [(len(t[0]), True) for t in bucket if not t[1]]  # (rank, intermediate)
+        leaves = [t[0] for t in bucket if t[1]]
+        if leaves:
+            inputs.append((len(frozenset().union(*leaves)), False))
+        fwd += 2 ** out + sum(2 ** r for r, inter in inputs if inter)
+        for i, (ri, _) in enumerate(inputs):
+            rev += 2 ** out + 2 ** ri + sum(2 ** r for j, (r, inter) in enumerate(inputs) if j != i and inter)
+        live.append((union - {v}, False))
+    return fwd, rev
+
+
+@pytest.mark.parametrize("name", ["n16_p1", "n100_p3"])
+def test_plan_bytes_match_oracle_buckets(qtlib, name):
+    """qt_plan_stats' algorithmic bytes (the rooflines' numerators) of energy
+    and gradient plans against a count over the oracle's buckets, per edge,
+    for complex128 (16 bytes per element) and complex64 (8)."""
+    from paper_2106_15740_gb300 import binding as qb
+    n, edges, p, _, _ = workload(name)
+    for e in range(0, len(edges), max(1, len(edges) // 6)):
+        fwd, rev = _oracle_bucket_elems(n, edges, p, e)
+        for dtype, es in ((qb.QT_C128, 16), (qb.QT_C64, 8)):
+            for grad in (0, 1):
+                opt = qb.qt_plan_options_default()
+                opt.batch, opt.dtype, opt.mode, opt.gradient = 2, dtype, qb.QT_MODE_PERSISTENT, grad
+                opt.fuse_chains = 0
+                opt.edge_begin, opt.edge_end = e, e + 1
+                plan = qb.qt_plan_create(n, edges, p, opt)
+                try:
+                    assert qb.qt_plan_stats(plan)["alg_bytes"] == 2 * es * (fwd + rev * grad)
+                finally:
+                    qb.qt_plan_free(plan)
