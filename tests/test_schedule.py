@@ -178,21 +178,24 @@ def test_tree_schedule_of_searched_orders_is_race_free(qtlib):
     assert pairs > 0 and depth < units
 
 
+@pytest.mark.parametrize("dtype", ["c64", "c64x2"])
 @pytest.mark.parametrize("queue_order", [0, 1, 2])
 @pytest.mark.parametrize("checkpoint", [False, True])
-def test_gradient_schedule_is_race_free(qtlib, checkpoint, queue_order):
+def test_gradient_schedule_is_race_free(qtlib, checkpoint, queue_order, dtype):
     """The adjoint sweep reads the forward intermediates again, writes output
     adjoints (zeroed first where it accumulates them) and reuses the arena;
     with checkpointing it also re-runs forward steps.  Several networks share
-    a slot under a workspace cap."""
+    a slot under a workspace cap.  Float pairs (FP64 adjoints, 16-byte
+    elements) take the same schedule rules."""
     from paper_2106_15740_gb300 import binding as qb
     n = 14
     edges = random_regular_graph(n, 3, 35)
+    es = 8 if dtype == "c64" else 16
 
     def grad_plan(cap, ckpt):
         opt = qb.qt_plan_options_default()
         opt.batch = 2
-        opt.dtype = qb.QT_C64
+        opt.dtype = qb.QT_C64 if dtype == "c64" else qb.QT_C64X2
         opt.mode = qb.QT_MODE_PERSISTENT
         opt.gradient = 1
         opt.max_workspace = cap
@@ -201,9 +204,9 @@ def test_gradient_schedule_is_race_free(qtlib, checkpoint, queue_order):
         return qb.qt_plan_create(n, edges, 2, opt)
 
     full = grad_plan(0, 0)
-    data = _data_bytes(full)
+    data = _data_bytes(full, es)
     qb.qt_plan_free(full)
-    plan = grad_plan(data * 2 // 3, 4096 if checkpoint else 0)
+    plan = grad_plan(data * 2 // 3, (4096 if checkpoint else 0) * es // 8)
     try:
         units, depth, pairs, cross = check_schedule(*_schedule(plan))
     finally:
@@ -365,9 +368,10 @@ def test_amplitude_schedule_is_race_free(qtlib):
 
 def test_schedule_sweep_of_random_configurations(qtlib):
     """A seeded sweep over small plans: graph size and seed, depth, batch,
-    dtype, energy or gradient, checkpoint budget, workspace cap, queue order,
-    chained or dependency-list schedule and grouping.  Every schedule must
-    pass the check."""
+    dtype (complex64, complex128, float pairs), energy or gradient,
+    checkpoint budget, workspace cap, queue order, chained or
+    dependency-list schedule and grouping.  Every schedule must pass the
+    check."""
     from paper_2106_15740_gb300 import binding as qb
     rng = np.random.default_rng(2106)
     checked = 0
@@ -377,9 +381,11 @@ def test_schedule_sweep_of_random_configurations(qtlib):
         edges = random_regular_graph(n, 3, int(rng.integers(0, 1000)))
         opt = qb.qt_plan_options_default()
         opt.batch = int(rng.choice([1, 2, 3, 8, 64]))
-        opt.dtype = int(rng.choice([qb.QT_C64, qb.QT_C128]))
+        opt.dtype = int(rng.choice([qb.QT_C64, qb.QT_C128, qb.QT_C64X2]))
         opt.mode = qb.QT_MODE_PERSISTENT
         opt.gradient = int(rng.integers(0, 2))
+        if opt.gradient and opt.dtype == qb.QT_C64X2 and opt.batch > 16:
+            opt.batch = 8  # float-pair gradients take at most 16 angle sets
         opt.queue_order = int(rng.integers(0, 3))
         opt.chain_steps = int(rng.random() < 0.2)
         opt.group_rows = int(rng.choice([0, -1, 64]))
