@@ -58,3 +58,40 @@ def test_bench_uses_the_oracle_only_for_its_cpu_arms():
     callers = {name for name, fn in funcs.items() for sub in ast.walk(fn)
                if isinstance(sub, ast.Name) and sub.id == "_oracle_eval"}
     assert callers <= {"cpu_baseline", "run_reference"}
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    """A copy of the binding whose shared library is not built raises on
+    first use: there is no pure-Python or CPU path behind it."""
+    import importlib.util
+    import shutil
+    import pytest
+    pkg = tmp_path / "unbuilt"
+    pkg.mkdir()
+    shutil.copy(ROOT / "paper_2106_15740_gb300" / "binding.py", pkg / "binding.py")
+    spec = importlib.util.spec_from_file_location("unbuilt_binding", pkg / "binding.py")
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    with pytest.raises(ImportError, match="not built"):
+        mod.lib()
+
+
+def test_no_cpu_fallback_without_a_gpu(qtlib):
+    """On a host without a usable CUDA device an evaluation reports
+    QT_ECUDA instead of computing anywhere else.  (Skipped where a device
+    exists: the call is given placeholder device pointers.)"""
+    import pytest
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    from paper_2106_15740_gb300 import binding as qb
+    from workloads import random_regular_graph
+    opt = qb.qt_plan_options_default()
+    opt.mode = qb.QT_MODE_PERSISTENT
+    plan = qb.qt_plan_create(8, random_regular_graph(8, 3, 39), 1, opt)
+    try:
+        with pytest.raises(qb.QTError) as ei:
+            qb.qt_plan_energy_static(plan, 8, 8, 8, 0, 0)
+        assert ei.value.status == qb.QT_ECUDA
+    finally:
+        qb.qt_plan_free(plan)
